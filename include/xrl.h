@@ -1,0 +1,194 @@
+/*
+ * xrl.h -- C ABI of the GB300 (sm_103a) library for broadband resistance /
+ * inductance extraction with an FMM-accelerated surface integral equation,
+ * following Wang, Liu, Gu, Jia, Yucel, "XRL: An FMM-Accelerated SIE Simulator
+ * for Resistance and Inductance Extraction of Complicated 3-D Geometries"
+ * (arXiv 2409.12375).
+ *
+ * Problem statement (Sec. II-A, eq. 1-3; Sec. III, port definition): the
+ * caller gives closed triangulated conductor surfaces, a conductivity and an
+ * ESI thickness per conductor, ports (a source and a sink terminal patch of
+ * panels each) and a list of frequencies; the library returns per-frequency
+ * port resistance and inductance matrices.  The raw panel potential product
+ * y = P x (the quantity the paper accelerates with the FMM, Sec. II-C) is
+ * exported too.
+ *
+ * Conventions for every call:
+ *  - Units are SI (metres, S/m, Hz, ohm, henry).  P has units 1/m.
+ *  - Panels are addressed in the caller's order (the order of `tri`);
+ *    reordering (Morton order) is internal.
+ *  - Ownership: the caller owns every buffer it passes.  Host inputs are
+ *    copied before the call returns; no caller pointer is retained.
+ *    Device pointers (the *_device calls) are borrowed for the duration of
+ *    the call's work on the given stream only.
+ *  - Errors: calls return an xrl_status; no exception crosses the ABI and the
+ *    library never aborts.  xrl_last_error(ctx) gives a message for the last
+ *    failing call on that context.  On error no output buffer is written.
+ *  - Threading: one context is used by one host thread at a time.
+ */
+#ifndef XRL_H
+#define XRL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct xrl_ctx xrl_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  XRL_OK = 0,
+  XRL_EINVAL = 1,   /* bad argument (null pointer, size out of range, NaN) */
+  XRL_ETOPO = 2,    /* mesh is not a closed 2-manifold, terminals touch, port spans two conductors */
+  XRL_ENOMEM = 3,   /* device or host allocation failed */
+  XRL_ECUDA = 4,    /* a CUDA runtime call failed (message has the CUDA error string) */
+  XRL_ENOCONV = 5,  /* an iterative solve did not reach its tolerance in the allowed iterations */
+  XRL_ETIMEOUT = 6, /* a bounded device-side wait gave up */
+  XRL_ESTATE = 7    /* call out of order (e.g. solve before setup) */
+} xrl_status;
+
+typedef struct {
+  int32_t fmm_order;   /* expansion order p of the solid-harmonic FMM (2..12), default 8 */
+  int32_t leaf_target; /* mean panels per non-empty leaf used to pick the tree depth, default 32
+                          (the depth is also capped so that leaf sides are >= 2x the largest
+                          panel radius) */
+  int32_t precision;   /* 0: FP64 everywhere; 1: mixed (FP32 FMM/near field inside FP64 refinement) */
+  int32_t precond;     /* 0: none; 1: diagonal-of-P preconditioner of eq. 10 (inner COCG solve) */
+  int32_t restart;     /* FGMRES restart length m, default 50 (Sec. III uses restart 50) */
+  int32_t max_iters;   /* total outer iterations per solve, default 500 */
+  int32_t inner_iters; /* max inner COCG iterations per preconditioner apply, default 60 */
+  int32_t warm_start;  /* 0: zero initial guess; 1: previous frequency's solution where available */
+  double tol;          /* relative residual ||b - Ax|| / ||b|| per system, default 1e-8 */
+  double inner_tol;    /* inner COCG relative residual, default 1e-3 */
+  int32_t device;      /* CUDA device ordinal, default 0 */
+  int32_t separation;  /* well-separatedness ws of the octree (1 or 2): leaves within ws cells are
+                          near field; default 2 (see xrl_export_lists) */
+} xrl_options;
+
+/* Fill `opt` with the defaults listed above. */
+void xrl_default_options(xrl_options* opt);
+
+/* Create a context on opt->device (NULL opt = defaults).  *out receives the
+ * handle; destroy it with xrl_destroy.  Returns XRL_ECUDA when no usable
+ * GPU is present. */
+xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out);
+
+/* Conductor surface mesh (Sec. II-A: hybrid panels; this library takes
+ * triangles).  xyz: [n_vert][3] vertex coordinates in metres; tri: [n_tri][3]
+ * vertex indices (any orientation); cond_id: [n_tri] conductor index per panel
+ * (0-based, NULL = all 0).  Each edge must be shared by exactly two triangles;
+ * this is checked in xrl_setup (XRL_ETOPO). */
+xrl_status xrl_set_mesh(xrl_ctx* ctx, int64_t n_vert, const double* xyz, int64_t n_tri,
+                        const int32_t* tri, const int32_t* cond_id);
+
+/* Material of each conductor: sigma [n_cond] in S/m and the thickness
+ * varsigma [n_cond] in metres of the double-plane ESI model, eq. 3
+ * (R_DC = 2/(sigma*varsigma), R_RF = sqrt(pi*mu0/sigma)). */
+xrl_status xrl_set_conductors(xrl_ctx* ctx, int32_t n_cond, const double* sigma,
+                              const double* thickness);
+
+/* Add a port (Sec. III-B: source and sink terminals as in Q3D): the source
+ * and sink terminal patches are lists of panel indices.  Each patch is
+ * collapsed into one equipotential node carrying no surface current; an
+ * ideal external branch with a 1 V source joins sink to source.  Patches of
+ * different ports may coincide (a shared sink).  *port_id receives the
+ * port's index (0-based, in call order). */
+xrl_status xrl_add_port(xrl_ctx* ctx, int64_t n_src, const int32_t* src_panels, int64_t n_sink,
+                        const int32_t* sink_panels, int32_t* port_id);
+
+/* Geometry-dependent setup, once per mesh: panel geometry and Morton order,
+ * octree and interaction lists, PEEC branches and the centroid-midpoint
+ * matrices A_1..A_3 (Algorithm 1), a loop basis M (Sec. II-B), the
+ * frequency-independent near-field block of P (Sec. II-C, filled once,
+ * Sec. II-D) and the FMM operators. */
+xrl_status xrl_setup(xrl_ctx* ctx);
+
+/* y = P x for n_cols columns, HOST buffers, x and y laid out [n_cols][n_tri]
+ * in caller panel order.  P_kl = (1/(A_k A_l)) int_k int_l 1/|r - r'| (eq. 6
+ * with the centroid-midpoint normalisation), evaluated by the FMM of
+ * Sec. II-C (near field by quadrature, far field by expansions of order p).
+ * Copies in and out inside the call; synchronous. */
+xrl_status xrl_fmm_mvm(xrl_ctx* ctx, int32_t n_cols, const double* x, double* y);
+
+/* Same product on DEVICE buffers d_x, d_y ([n_cols][n_tri], FP64) enqueued on
+ * `stream` (a cudaStream_t, NULL = the context's stream).  Asynchronous with
+ * respect to the host; d_x and d_y must stay valid until the stream reaches
+ * the end of this work.  d_x and d_y must not overlap. */
+xrl_status xrl_fmm_mvm_device(xrl_ctx* ctx, int32_t n_cols, const double* d_x, double* d_y,
+                              void* stream);
+
+/* Reference product y = P x by direct O(N^2) summation on the GPU, every
+ * entry evaluated with the same quadrature rule table as the near field
+ * (device buffers, layout as xrl_fmm_mvm_device). */
+xrl_status xrl_direct_mvm_device(xrl_ctx* ctx, int32_t n_cols, const double* d_x, double* d_y,
+                                 void* stream);
+
+typedef struct {
+  int32_t n_panels, n_live, n_branches, n_loops, n_ports, n_leaves, n_levels, n_boxes;
+  int64_t near_nnz;      /* stored near-field entries */
+  int32_t n_vertex_loops, n_global_loops;
+  int32_t total_iters;   /* outer FGMRES iterations of the last solve (max over systems) */
+  int32_t total_inner;   /* inner COCG iterations of the last solve */
+  int32_t n_mvm;         /* operator applications (FMM products) in the last solve */
+  double max_rel_res;    /* largest final true relative residual of the last solve */
+  double setup_ms, solve_ms, mvm_ms; /* wall times of the last setup / solve / fmm_mvm */
+  int64_t peak_device_bytes;         /* high-water mark of the library's device allocations */
+} xrl_stats;
+
+/* Counters and timings of the context (valid after setup). */
+xrl_status xrl_get_stats(const xrl_ctx* ctx, xrl_stats* out);
+
+/* Broadband sweep (Sec. II-D, Sec. III): for each frequency f in freq_hz
+ * [n_freq] (f > 0), all ports are excited one at a time and the loop system
+ * of eq. 7-8 is solved by right-preconditioned flexible GMRES with the FMM
+ * product; all (frequency, port) systems form one multi-RHS block.  Output:
+ * R, L [n_freq][n_ports][n_ports], R = Re Z_port (ohm), L = Im Z_port / omega
+ * (henry), Z_port = Y^-1 with Y the short-circuit port admittance.  Returns
+ * XRL_ENOCONV (outputs still written) if some system did not reach opt.tol. */
+xrl_status xrl_solve(xrl_ctx* ctx, int32_t n_freq, const double* freq_hz, double* R, double* L);
+
+/* Loop-space operator for parity checks: w_s = Z(f_s) v_s for n_sys systems,
+ * Z(f) = M [sum_t A_t (diag(Z_s(f)/A) + j omega mu0/4pi P) A_t^T] M^T (eq. 8),
+ * with P applied by the FMM.  Host buffers: freq [n_sys]; v, w
+ * [n_sys][n_loops] complex as interleaved (re, im) doubles. */
+xrl_status xrl_apply_operator(xrl_ctx* ctx, int32_t n_sys, const double* freq, const double* v,
+                              double* w);
+
+/* Preconditioner action for parity checks: w_s = Q(f_s) v_s with Q of eq. 10
+ * (the sparse matrix itself, not its inverse); layout as xrl_apply_operator. */
+xrl_status xrl_apply_precond_matrix(xrl_ctx* ctx, int32_t n_sys, const double* freq,
+                                    const double* v, double* w);
+
+/* Export of setup products for checks (host buffers sized from xrl_get_stats):
+ *  tree:   keys [n_panels] Morton keys (caller order), perm [n_panels] Morton
+ *          rank -> caller index, leaf_of [n_panels] leaf index per Morton rank;
+ *  branch: tail, head [n_branches] (panel index, or -1-terminal for a
+ *          terminal node; port branches last: tail = -1-sink, head = -1-source);
+ *  loops:  CSR of M: row_ptr [n_loops+1], col [nnz], val [nnz] (+1/-1);
+ *          pass col = val = NULL to get nnz in row_ptr[n_loops]. */
+xrl_status xrl_export_tree(const xrl_ctx* ctx, uint64_t* keys, int32_t* perm, int32_t* leaf_of);
+xrl_status xrl_export_branches(const xrl_ctx* ctx, int32_t* tail, int32_t* head);
+xrl_status xrl_export_loops(const xrl_ctx* ctx, int64_t* row_ptr, int32_t* col, int8_t* val);
+
+/* Interaction lists of the octree (uniform depth; U-list = leaves within
+ * `separation` cells in every direction, V-list = children of the parent's
+ * near boxes that are not near the box):
+ * for level l in [2, n_levels), box counts, Morton keys of the occupied boxes
+ * and the V-list (multipole-to-local) pairs as CSR over target boxes, and
+ * for the leaf level the U-list (near field) as CSR.  Sizes via the counts
+ * query (pass NULL arrays). */
+xrl_status xrl_export_lists(const xrl_ctx* ctx, int32_t level, int32_t* n_boxes, uint64_t* box_keys,
+                            int64_t* v_ptr, int32_t* v_src, int64_t* u_ptr, int32_t* u_src);
+
+/* Last error message of this context ("" if none).  Valid until the next call. */
+const char* xrl_last_error(const xrl_ctx* ctx);
+
+/* Release every resource of the context (NULL is ignored). */
+void xrl_destroy(xrl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XRL_H */

@@ -1,0 +1,7 @@
+"""GB300 (sm_103a) library for FMM-accelerated SIE resistance/inductance
+extraction after Wang et al., "XRL" (arXiv 2409.12375).
+
+The compute path is the C-ABI shared library built from csrc/ (see
+include/xrl.h); this package only marshals arguments to it.
+"""
+from .xrl import XRL, Options, Stats, lib, library_path  # noqa: F401

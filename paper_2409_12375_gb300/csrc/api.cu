@@ -1,0 +1,371 @@
+// C-ABI entry points (declared in include/xrl.h).  Every call converts
+// internal exceptions into an xrl_status and a per-context message; nothing
+// is thrown across the boundary.
+#include <chrono>
+#include <cmath>
+#include <new>
+
+#include "xrl_internal.hpp"
+
+using namespace xrl;
+
+namespace {
+
+template <class F>
+xrl_status guarded(xrl_ctx* c, F&& f) {
+  try {
+    f();
+    if (c) c->err.clear();
+    return XRL_OK;
+  } catch (const Error& e) {
+    if (c) c->err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    if (c) c->err = "host allocation failed";
+    return XRL_ENOMEM;
+  } catch (const std::exception& e) {
+    if (c) c->err = e.what();
+    return XRL_EINVAL;
+  } catch (...) {
+    if (c) c->err = "unknown error";
+    return XRL_EINVAL;
+  }
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+double self_term_host(const double* a, const double* b, const double* c) {
+  auto d = [](const double* x, const double* y) {
+    return std::sqrt((x[0] - y[0]) * (x[0] - y[0]) + (x[1] - y[1]) * (x[1] - y[1]) + (x[2] - y[2]) * (x[2] - y[2]));
+  };
+  double la = d(b, c), lb = d(c, a), lc = d(a, b);
+  double s = la + lb + lc;
+  return (4.0 / 3.0) * (std::log(s / (s - 2 * la)) / la + std::log(s / (s - 2 * lb)) / lb +
+                        std::log(s / (s - 2 * lc)) / lc);
+}
+
+}  // namespace
+
+extern "C" {
+
+void xrl_default_options(xrl_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->fmm_order = 8;
+  o->leaf_target = 32;
+  o->precision = 0;
+  o->precond = 1;
+  o->restart = 50;
+  o->max_iters = 500;
+  o->inner_iters = 60;
+  o->warm_start = 0;
+  o->tol = 1e-8;
+  o->inner_tol = 1e-3;
+  o->device = 0;
+  o->separation = 2;
+}
+
+xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {
+  if (!out) return XRL_EINVAL;
+  *out = nullptr;
+  xrl_ctx* c = nullptr;
+  try {
+    c = new xrl_ctx();
+  } catch (...) {
+    return XRL_ENOMEM;
+  }
+  xrl_default_options(&c->opt);
+  if (opt) c->opt = *opt;
+  std::memset(&c->stats, 0, sizeof(c->stats));
+  xrl_status st = guarded(c, [&] {
+    XRL_CHECK(c->opt.fmm_order >= 2 && c->opt.fmm_order <= 12, XRL_EINVAL, "fmm_order must be in [2, 12]");
+    XRL_CHECK(c->opt.leaf_target >= 1, XRL_EINVAL, "leaf_target must be >= 1");
+    XRL_CHECK(c->opt.separation == 1 || c->opt.separation == 2, XRL_EINVAL, "separation must be 1 or 2");
+    XRL_CHECK(c->opt.tol > 0 && c->opt.restart >= 1 && c->opt.max_iters >= 1, XRL_EINVAL, "bad solver options");
+    int n = 0;
+    XRL_CUDA(cudaGetDeviceCount(&n));
+    XRL_CHECK(c->opt.device >= 0 && c->opt.device < n, XRL_ECUDA, "no such CUDA device");
+    c->device = c->opt.device;
+    XRL_CUDA(cudaSetDevice(c->device));
+    XRL_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  });
+  if (st != XRL_OK) {
+    delete c;
+    return st;
+  }
+  *out = c;
+  return XRL_OK;
+}
+
+xrl_status xrl_set_mesh(xrl_ctx* c, int64_t n_vert, const double* xyz, int64_t n_tri, const int32_t* tri,
+                        const int32_t* cond_id) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(xyz && tri && n_vert > 0 && n_tri > 0 && n_tri < (1LL << 30), XRL_EINVAL, "bad mesh arguments");
+    for (int64_t i = 0; i < 3 * n_vert; ++i) XRL_CHECK(std::isfinite(xyz[i]), XRL_EINVAL, "non-finite vertex");
+    for (int64_t i = 0; i < 3 * n_tri; ++i)
+      XRL_CHECK(tri[i] >= 0 && tri[i] < n_vert, XRL_EINVAL, "triangle vertex index out of range");
+    c->xyz.assign(xyz, xyz + 3 * n_vert);
+    c->tri.assign(tri, tri + 3 * n_tri);
+    c->cond.assign(n_tri, 0);
+    if (cond_id)
+      for (int64_t i = 0; i < n_tri; ++i) {
+        XRL_CHECK(cond_id[i] >= 0, XRL_EINVAL, "negative conductor id");
+        c->cond[i] = cond_id[i];
+      }
+    c->N = (int)n_tri;
+    c->have_mesh = true;
+    c->ready = false;
+    c->port_src.clear();
+    c->port_sink.clear();
+  });
+}
+
+xrl_status xrl_set_conductors(xrl_ctx* c, int32_t n_cond, const double* sigma, const double* thickness) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(n_cond > 0 && sigma && thickness, XRL_EINVAL, "bad conductor arguments");
+    for (int i = 0; i < n_cond; ++i)
+      XRL_CHECK(std::isfinite(sigma[i]) && sigma[i] > 0 && std::isfinite(thickness[i]) && thickness[i] > 0,
+                XRL_EINVAL, "sigma and thickness must be finite and > 0");
+    c->sigma.assign(sigma, sigma + n_cond);
+    c->thick.assign(thickness, thickness + n_cond);
+    c->have_cond = true;
+    c->ready = false;
+  });
+}
+
+xrl_status xrl_add_port(xrl_ctx* c, int64_t n_src, const int32_t* src, int64_t n_sink, const int32_t* sink,
+                        int32_t* port_id) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(c->have_mesh, XRL_ESTATE, "set the mesh before adding ports");
+    XRL_CHECK(n_src > 0 && n_sink > 0 && src && sink, XRL_EINVAL, "empty port terminal");
+    for (int64_t i = 0; i < n_src; ++i) XRL_CHECK(src[i] >= 0 && src[i] < c->N, XRL_EINVAL, "port panel out of range");
+    for (int64_t i = 0; i < n_sink; ++i)
+      XRL_CHECK(sink[i] >= 0 && sink[i] < c->N, XRL_EINVAL, "port panel out of range");
+    c->port_src.emplace_back(src, src + n_src);
+    c->port_sink.emplace_back(sink, sink + n_sink);
+    if (port_id) *port_id = (int32_t)c->port_src.size() - 1;
+    c->ready = false;
+  });
+}
+
+xrl_status xrl_setup(xrl_ctx* c) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(c->have_mesh, XRL_ESTATE, "no mesh");
+    double t0 = now_ms();
+    XRL_CUDA(cudaSetDevice(c->device));
+    int ncond = 0;
+    for (int v : c->cond) ncond = std::max(ncond, v + 1);
+    if (!c->have_cond) {
+      c->sigma.assign(ncond, 5.8e7);
+      c->thick.assign(ncond, 1e-3);
+    }
+    XRL_CHECK((int)c->sigma.size() >= ncond, XRL_EINVAL, "a conductor id has no material");
+    c->p = c->opt.fmm_order;
+    c->ncoef = (c->p + 1) * (c->p + 1);
+    c->d = Dev();
+    build_topology(c);
+    upload_rule_tables(c);
+    launch_geometry(c);
+    launch_near_fill(c);
+    launch_moments(c);
+    fmm_prepare(c);
+    std::vector<double> pdiag(c->N, 0.0);
+    for (int p = 0; p < c->N; ++p) {
+      const double* v0 = &c->xyz[3 * (size_t)c->tri[3 * p]];
+      const double* v1 = &c->xyz[3 * (size_t)c->tri[3 * p + 1]];
+      const double* v2 = &c->xyz[3 * (size_t)c->tri[3 * p + 2]];
+      pdiag[p] = self_term_host(v0, v1, v2);
+    }
+    build_precond_pattern(c, pdiag);
+    solver_prepare(c);
+    XRL_CUDA(cudaStreamSynchronize(c->stream));
+    const Topo& T = c->topo;
+    c->stats.n_panels = c->N;
+    c->stats.n_live = T.n_live;
+    c->stats.n_branches = T.n_branch;
+    c->stats.n_loops = T.n_loops;
+    c->stats.n_ports = T.n_port;
+    c->stats.n_leaves = c->tree.n_leaves();
+    c->stats.n_levels = c->tree.L + 1;
+    c->stats.n_boxes = c->tree.n_boxes();
+    c->stats.n_vertex_loops = T.n_vertex_loops;
+    c->stats.n_global_loops = T.n_global_loops;
+    c->stats.setup_ms = now_ms() - t0;
+    c->ready = true;
+  });
+}
+
+xrl_status xrl_fmm_mvm_device(xrl_ctx* c, int32_t nc, const double* dx, double* dy, void* stream) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(c->ready, XRL_ESTATE, "call xrl_setup first");
+    XRL_CHECK(nc > 0 && dx && dy, XRL_EINVAL, "bad mvm arguments");
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    size_t n = (size_t)c->N * nc;
+    c->d.X.ensure(c->alloc, n);
+    c->d.Y.ensure(c->alloc, n);
+    size_t ne = (size_t)c->tree.n_boxes() * c->ncoef * nc;
+    c->d.Mexp.ensure(c->alloc, ne);
+    c->d.Lexp.ensure(c->alloc, ne);
+    launch_to_morton(c, nc, dx, c->d.X.p, s);
+    fmm_apply(c, nc, c->d.X.p, c->d.Y.p, s);
+    launch_from_morton(c, nc, c->d.Y.p, dy, s);
+    XRL_CUDA(cudaGetLastError());
+  });
+}
+
+xrl_status xrl_direct_mvm_device(xrl_ctx* c, int32_t nc, const double* dx, double* dy, void* stream) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(c->ready, XRL_ESTATE, "call xrl_setup first");
+    XRL_CHECK(nc > 0 && dx && dy, XRL_EINVAL, "bad mvm arguments");
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    size_t n = (size_t)c->N * nc;
+    c->d.X.ensure(c->alloc, n);
+    c->d.Y.ensure(c->alloc, n);
+    launch_to_morton(c, nc, dx, c->d.X.p, s);
+    launch_direct(c, nc, c->d.X.p, c->d.Y.p, s);
+    launch_from_morton(c, nc, c->d.Y.p, dy, s);
+    XRL_CUDA(cudaGetLastError());
+  });
+}
+
+xrl_status xrl_fmm_mvm(xrl_ctx* c, int32_t nc, const double* x, double* y) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(c->ready, XRL_ESTATE, "call xrl_setup first");
+    XRL_CHECK(nc > 0 && x && y, XRL_EINVAL, "bad mvm arguments");
+    double t0 = now_ms();
+    size_t n = (size_t)c->N * nc;
+    DBuf<double> dx, dy;
+    dx.alloc(c->alloc, n);
+    dy.alloc(c->alloc, n);
+    XRL_CUDA(cudaMemcpyAsync(dx.p, x, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    c->d.X.ensure(c->alloc, n);
+    c->d.Y.ensure(c->alloc, n);
+    launch_to_morton(c, nc, dx.p, c->d.X.p, c->stream);
+    fmm_apply(c, nc, c->d.X.p, c->d.Y.p, c->stream);
+    launch_from_morton(c, nc, c->d.Y.p, dy.p, c->stream);
+    XRL_CUDA(cudaGetLastError());
+    XRL_CUDA(cudaMemcpyAsync(y, dy.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    XRL_CUDA(cudaStreamSynchronize(c->stream));
+    c->stats.mvm_ms = now_ms() - t0;
+  });
+}
+
+xrl_status xrl_get_stats(const xrl_ctx* c, xrl_stats* out) {
+  if (!c || !out) return XRL_EINVAL;
+  *out = c->stats;
+  out->peak_device_bytes = c->alloc.peak;
+  return XRL_OK;
+}
+
+xrl_status xrl_solve(xrl_ctx* c, int32_t nf, const double* freq, double* R, double* L) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(c->ready, XRL_ESTATE, "call xrl_setup first");
+    XRL_CHECK(nf > 0 && freq && R && L, XRL_EINVAL, "bad solve arguments");
+    for (int i = 0; i < nf; ++i) XRL_CHECK(std::isfinite(freq[i]) && freq[i] > 0, XRL_EINVAL, "frequencies must be > 0");
+    double t0 = now_ms();
+    try {
+      run_solve(c, nf, freq, R, L);
+    } catch (...) {
+      c->stats.solve_ms = now_ms() - t0;
+      throw;
+    }
+    c->stats.solve_ms = now_ms() - t0;
+  });
+}
+
+xrl_status xrl_apply_operator(xrl_ctx* c, int32_t nsys, const double* freq, const double* v, double* w) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(c->ready, XRL_ESTATE, "call xrl_setup first");
+    XRL_CHECK(nsys > 0 && freq && v && w, XRL_EINVAL, "bad arguments");
+    apply_operator_host(c, nsys, freq, v, w, false);
+  });
+}
+
+xrl_status xrl_apply_precond_matrix(xrl_ctx* c, int32_t nsys, const double* freq, const double* v, double* w) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(c->ready, XRL_ESTATE, "call xrl_setup first");
+    XRL_CHECK(nsys > 0 && freq && v && w, XRL_EINVAL, "bad arguments");
+    apply_operator_host(c, nsys, freq, v, w, true);
+  });
+}
+
+xrl_status xrl_export_tree(const xrl_ctx* c, uint64_t* keys, int32_t* perm, int32_t* leaf_of) {
+  if (!c || !c->ready) return XRL_ESTATE;
+  const Tree& t = c->tree;
+  if (keys) std::memcpy(keys, t.key.data(), t.key.size() * sizeof(uint64_t));
+  if (perm) std::memcpy(perm, t.perm.data(), t.perm.size() * sizeof(int32_t));
+  if (leaf_of) std::memcpy(leaf_of, t.leaf_of.data(), t.leaf_of.size() * sizeof(int32_t));
+  return XRL_OK;
+}
+
+xrl_status xrl_export_branches(const xrl_ctx* c, int32_t* tail, int32_t* head) {
+  if (!c || !c->ready) return XRL_ESTATE;
+  const Topo& T = c->topo;
+  for (int b = 0; b < T.n_branch; ++b) {
+    auto node = [&](int n) { return n < T.n_live ? -2 : -1 - (n - T.n_live); };
+    if (b < T.n_cb) {
+      if (tail) tail[b] = T.br_pan[0][b];
+      if (head) head[b] = T.br_pan[1][b] >= 0 ? T.br_pan[1][b] : node(T.br_head[b]);
+    } else {
+      if (tail) tail[b] = node(T.br_tail[b]);
+      if (head) head[b] = node(T.br_head[b]);
+    }
+  }
+  return XRL_OK;
+}
+
+xrl_status xrl_export_loops(const xrl_ctx* c, int64_t* row_ptr, int32_t* col, int8_t* val) {
+  if (!c || !c->ready || !row_ptr) return XRL_ESTATE;
+  const Topo& T = c->topo;
+  std::memcpy(row_ptr, T.m_ptr.data(), T.m_ptr.size() * sizeof(int64_t));
+  if (col) std::memcpy(col, T.m_col.data(), T.m_col.size() * sizeof(int32_t));
+  if (val) std::memcpy(val, T.m_val.data(), T.m_val.size() * sizeof(int8_t));
+  return XRL_OK;
+}
+
+xrl_status xrl_export_lists(const xrl_ctx* c, int32_t level, int32_t* n_boxes, uint64_t* box_keys, int64_t* v_ptr,
+                            int32_t* v_src, int64_t* u_ptr, int32_t* u_src) {
+  if (!c || !c->ready) return XRL_ESTATE;
+  const Tree& t = c->tree;
+  if (level < 0 || level > t.L || !n_boxes) return XRL_EINVAL;
+  int b0 = t.level_off[level], b1 = t.level_off[level + 1];
+  *n_boxes = b1 - b0;
+  if (box_keys)
+    for (int b = b0; b < b1; ++b) box_keys[b - b0] = t.box_key[b];
+  if (v_ptr) {
+    int64_t base = t.v_ptr[b0];
+    for (int b = b0; b <= b1; ++b) v_ptr[b - b0] = t.v_ptr[b] - base;
+    if (v_src)
+      for (int64_t k = t.v_ptr[b0]; k < t.v_ptr[b1]; ++k) v_src[k - base] = t.v_src[k] - b0;
+  }
+  if (level == t.L && u_ptr) {
+    std::memcpy(u_ptr, t.u_ptr.data(), t.u_ptr.size() * sizeof(int64_t));
+    if (u_src) std::memcpy(u_src, t.u_src.data(), t.u_src.size() * sizeof(int32_t));
+  }
+  return XRL_OK;
+}
+
+const char* xrl_last_error(const xrl_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void xrl_destroy(xrl_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  c->d = Dev();
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,308 @@
+// Fast multipole product y = P x on panels (Sec. II-C), sm_103a.
+//
+// The centroid-midpoint transformation turns each product into scalar 1/R
+// potentials of panels, "the format of particle simulation" (Sec. II-C):
+// source panel l carries the uniform charge density x_l / A_l and target k
+// averages the potential over its area.  Phases per product, all on one
+// stream, panels in Morton order with columns contiguous ([N][nc] layout):
+//   P2P  near field of each leaf from the precomputed U-list blocks
+//   P2M  leaf multipoles from the exact panel moments (setup, geom.cu)
+//   M2M  upward, levels L-1 .. 2 (8 child-offset matrices)
+//   M2L  V-list translations (offset-indexed matrices, level independent)
+//   L2L  downward, levels 3 .. L
+//   L2P  leaf locals averaged over the target panels (same moment table,
+//        weight 1 for m = 0 and 2 for m > 0 of the real storage)
+// Operators are real (p+1)^2 square matrices stored transposed ([in][out]).
+// The template parameter T selects FP64 (the plain path) or FP32 (mixed
+// precision, used inside the FP64 refinement loop).
+#include <vector>
+
+#include "xrl_internal.hpp"
+
+namespace xrl {
+
+// ---- layout conversion ----------------------------------------------------------------
+__global__ void k_to_morton(int N, int nc, const int32_t* __restrict__ perm, const double* __restrict__ x,
+                            double* __restrict__ X) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)N * nc) return;
+  int r = (int)(idx / nc), c = (int)(idx % nc);
+  X[idx] = x[(size_t)c * N + perm[r]];
+}
+
+__global__ void k_from_morton(int N, int nc, const int32_t* __restrict__ perm, const double* __restrict__ Y,
+                              double* __restrict__ y) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)N * nc) return;
+  int r = (int)(idx / nc), c = (int)(idx % nc);
+  y[(size_t)c * N + perm[r]] = Y[idx];
+}
+
+void launch_to_morton(const xrl_ctx* c, int nc, const double* x, double* X, cudaStream_t s) {
+  size_t n = (size_t)c->N * nc;
+  k_to_morton<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->N, nc, c->d.perm.p, x, X);
+}
+
+void launch_from_morton(const xrl_ctx* c, int nc, const double* Y, double* y, cudaStream_t s) {
+  size_t n = (size_t)c->N * nc;
+  k_from_morton<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->N, nc, c->d.perm.p, Y, y);
+}
+
+// ---- near field -------------------------------------------------------------------------
+// One block per (leaf, column tile).  Thread t handles target ii = t / ct and
+// column c0 + t % ct of the tile; the block walks the leaf's U-list.
+template <class T>
+__global__ void k_p2p(int nc, int ct, const int32_t* __restrict__ leaf_first, const int32_t* __restrict__ leaf_count,
+                      const int32_t* __restrict__ u_ptr, const int32_t* __restrict__ u_src,
+                      const int64_t* __restrict__ near_off, const int32_t* __restrict__ near_w,
+                      const T* __restrict__ val, const T* __restrict__ X, T* __restrict__ Y) {
+  const int B = blockIdx.x;
+  const int c0 = blockIdx.y * ct;
+  const int cn = min(ct, nc - c0);
+  const int nB = leaf_count[B], f0 = leaf_first[B], w = near_w[B];
+  const T* vb = val + near_off[B];
+  __shared__ int s_first[125], s_cnt[125];
+  const int us = u_ptr[B], ue = u_ptr[B + 1];
+  for (int q = threadIdx.x; q < ue - us; q += blockDim.x) {
+    s_first[q] = leaf_first[u_src[us + q]];
+    s_cnt[q] = leaf_count[u_src[us + q]];
+  }
+  __syncthreads();
+  const int nu = ue - us;
+  for (int t = threadIdx.x; t < nB * ct; t += blockDim.x) {
+    int ii = t / ct, cc = t % ct;
+    if (cc >= cn) continue;
+    const T* row = vb + (size_t)ii * w;
+    T acc = 0;
+    int jj = 0;
+    for (int s = 0; s < nu; ++s) {
+      const T* xs = X + (size_t)s_first[s] * nc + c0 + cc;
+      const int n = s_cnt[s];
+      for (int j = 0; j < n; ++j) acc += row[jj + j] * xs[(size_t)j * nc];
+      jj += n;
+    }
+    Y[(size_t)(f0 + ii) * nc + c0 + cc] = acc;
+  }
+}
+
+// ---- expansions ----------------------------------------------------------------------------
+// P2M: M[box][k][c] = sum_i S[i][k] X[i][c]
+template <class T>
+__global__ void k_p2m(int nc, int ct, int ncoef, int box0, const int32_t* __restrict__ leaf_first,
+                      const int32_t* __restrict__ leaf_count, const T* __restrict__ S, const T* __restrict__ X,
+                      T* __restrict__ M) {
+  const int B = blockIdx.x;
+  const int c0 = blockIdx.y * ct;
+  const int cn = min(ct, nc - c0);
+  const int f0 = leaf_first[B], n = leaf_count[B];
+  T* out = M + (size_t)(box0 + B) * ncoef * nc;
+  for (int t = threadIdx.x; t < ncoef * ct; t += blockDim.x) {
+    int k = t % ncoef, cc = t / ncoef;
+    if (cc >= cn) continue;
+    T acc = 0;
+    for (int i = 0; i < n; ++i) acc += S[(size_t)(f0 + i) * ncoef + k] * X[(size_t)(f0 + i) * nc + c0 + cc];
+    out[(size_t)k * nc + c0 + cc] = acc;
+  }
+}
+
+// M2M: parent boxes [pb0, pb0 + gridDim.x); children contiguous at child_ptr
+template <class T>
+__global__ void k_m2m(int nc, int ct, int ncoef, int pb0, const int32_t* __restrict__ child_ptr,
+                      const int32_t* __restrict__ oct, const T* __restrict__ Tt, T* __restrict__ M) {
+  const int P = pb0 + blockIdx.x;
+  const int c0 = blockIdx.y * ct;
+  const int cn = min(ct, nc - c0);
+  const int cs = child_ptr[P], ce = child_ptr[P + 1];
+  const size_t ne = (size_t)ncoef * nc;
+  for (int t = threadIdx.x; t < ncoef * ct; t += blockDim.x) {
+    int k = t % ncoef, cc = t / ncoef;
+    if (cc >= cn) continue;
+    T acc = 0;
+    for (int ch = cs; ch < ce; ++ch) {
+      const T* tm = Tt + (size_t)oct[ch] * ncoef * ncoef;
+      const T* mc = M + (size_t)ch * ne + c0 + cc;
+      for (int j = 0; j < ncoef; ++j) acc += tm[(size_t)j * ncoef + k] * mc[(size_t)j * nc];
+    }
+    M[(size_t)P * ne + (size_t)k * nc + c0 + cc] = acc;
+  }
+}
+
+// M2L: target boxes [b0, b0 + gridDim.x); L[box] = sum over V-list
+template <class T>
+__global__ void k_m2l(int nc, int ct, int ncoef, int b0, const int32_t* __restrict__ v_ptr,
+                      const int32_t* __restrict__ v_src, const int16_t* __restrict__ v_off,
+                      const T* __restrict__ Tt, const T* __restrict__ M, T* __restrict__ L) {
+  const int Bx = b0 + blockIdx.x;
+  const int c0 = blockIdx.y * ct;
+  const int cn = min(ct, nc - c0);
+  const int vs = v_ptr[Bx], ve = v_ptr[Bx + 1];
+  const size_t ne = (size_t)ncoef * nc;
+  for (int t = threadIdx.x; t < ncoef * ct; t += blockDim.x) {
+    int k = t % ncoef, cc = t / ncoef;
+    if (cc >= cn) continue;
+    T acc = 0;
+    for (int v = vs; v < ve; ++v) {
+      const T* tm = Tt + (size_t)v_off[v] * ncoef * ncoef;
+      const T* ms = M + (size_t)v_src[v] * ne + c0 + cc;
+      for (int j = 0; j < ncoef; ++j) acc += tm[(size_t)j * ncoef + k] * ms[(size_t)j * nc];
+    }
+    L[(size_t)Bx * ne + (size_t)k * nc + c0 + cc] = acc;
+  }
+}
+
+// L2L: child boxes [b0, b0 + gridDim.x) += T(oct) L[parent]
+template <class T>
+__global__ void k_l2l(int nc, int ct, int ncoef, int b0, const int32_t* __restrict__ parent,
+                      const int32_t* __restrict__ oct, const T* __restrict__ Tt, T* __restrict__ L) {
+  const int Bx = b0 + blockIdx.x;
+  const int c0 = blockIdx.y * ct;
+  const int cn = min(ct, nc - c0);
+  const size_t ne = (size_t)ncoef * nc;
+  const T* tm = Tt + (size_t)oct[Bx] * ncoef * ncoef;
+  const T* lp = L + (size_t)parent[Bx] * ne;
+  for (int t = threadIdx.x; t < ncoef * ct; t += blockDim.x) {
+    int k = t % ncoef, cc = t / ncoef;
+    if (cc >= cn) continue;
+    T acc = 0;
+    for (int j = 0; j < ncoef; ++j) acc += tm[(size_t)j * ncoef + k] * lp[(size_t)j * nc + c0 + cc];
+    L[(size_t)Bx * ne + (size_t)k * nc + c0 + cc] += acc;
+  }
+}
+
+// L2P: Y[i][c] += (1/h) sum_k w_k S[i][k] L[leaf][k][c],  w = 1 (m = 0), 2 (m > 0)
+template <class T>
+__global__ void k_l2p(int nc, int ct, int ncoef, int box0, T inv_h, const int32_t* __restrict__ leaf_first,
+                      const int32_t* __restrict__ leaf_count, const T* __restrict__ S, const T* __restrict__ L,
+                      T* __restrict__ Y) {
+  const int B = blockIdx.x;
+  const int c0 = blockIdx.y * ct;
+  const int cn = min(ct, nc - c0);
+  const int f0 = leaf_first[B], n = leaf_count[B];
+  const T* lb = L + (size_t)(box0 + B) * ncoef * nc;
+  for (int t = threadIdx.x; t < n * ct; t += blockDim.x) {
+    int ii = t / ct, cc = t % ct;
+    if (cc >= cn) continue;
+    const T* s = S + (size_t)(f0 + ii) * ncoef;
+    T acc = 0;
+    int k = 0;
+    for (int nn = 0; k < ncoef; ++nn) {
+      acc += s[k] * lb[(size_t)k * nc + c0 + cc];
+      ++k;
+      for (int m = 1; m <= nn; ++m) {
+        acc += (T)2 * (s[k] * lb[(size_t)k * nc + c0 + cc] + s[k + 1] * lb[(size_t)(k + 1) * nc + c0 + cc]);
+        k += 2;
+      }
+    }
+    Y[(size_t)(f0 + ii) * nc + c0 + cc] += acc * inv_h;
+  }
+}
+
+template <class T>
+__global__ void k_cast(size_t n, const double* __restrict__ a, T* __restrict__ b) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (T)a[i];
+}
+
+// ---- host side ---------------------------------------------------------------------------
+void fmm_prepare(xrl_ctx* c) {
+  const Tree& t = c->tree;
+  std::vector<double> m2m, l2l, m2l;
+  build_translations(c->p, t.m2l_offsets, m2m, l2l, m2l);
+  c->d.t_m2m.upload(c->alloc, m2m);
+  c->d.t_l2l.upload(c->alloc, l2l);
+  c->d.t_m2l.upload(c->alloc, m2l);
+  const int nb = t.n_boxes();
+  // children ranges (children of box b are contiguous in the next level)
+  std::vector<int32_t> cptr(nb + 1, 0);
+  for (int b = 0; b < nb; ++b)
+    if (t.parent[b] >= 0) cptr[t.parent[b] + 1]++;
+  for (int b = 0; b < nb; ++b) cptr[b + 1] += cptr[b];
+  // children of box P start at the first child index: since boxes are sorted by
+  // level then key, the first child of P is level_off[l+1] + (count of children of earlier boxes)
+  std::vector<int32_t> child_ptr(nb + 1, 0);
+  for (int l = 0; l <= t.L; ++l) {
+    int base = (l + 1 <= t.L) ? t.level_off[l + 1] : t.level_off[t.L + 1];
+    int run = base;
+    for (int b = t.level_off[l]; b < t.level_off[l + 1]; ++b) {
+      child_ptr[b] = run;
+      run += cptr[b + 1] - cptr[b];
+    }
+  }
+  child_ptr[nb] = nb;
+  c->d.box_child_ptr.upload(c->alloc, child_ptr);
+  c->d.box_parent.upload(c->alloc, t.parent);
+  c->d.box_oct.upload(c->alloc, t.octant);
+  std::vector<int32_t> vptr(t.v_ptr.begin(), t.v_ptr.end());
+  c->d.v_ptr32.upload(c->alloc, vptr);
+  c->d.v_src.upload(c->alloc, t.v_src);
+  c->d.v_off.upload(c->alloc, t.v_off);
+  // FP32 copies for the mixed-precision path
+  auto cast = [&](const DBuf<double>& a, DBuf<float>& b) {
+    b.alloc(c->alloc, a.n);
+    if (a.n) k_cast<float><<<(unsigned)((a.n + 255) / 256), 256, 0, c->stream>>>(a.n, a.p, b.p);
+  };
+  cast(c->d.t_m2m, c->d.t_m2m32);
+  cast(c->d.t_l2l, c->d.t_l2l32);
+  cast(c->d.t_m2l, c->d.t_m2l32);
+  cast(c->d.near_val, c->d.near_val32);
+  cast(c->d.mom, c->d.mom32);
+  XRL_CUDA(cudaGetLastError());
+  XRL_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+template <class T>
+static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, const T* mom, const T* tm2m,
+                        const T* tl2l, const T* tm2l, T* Mx, T* Lx, cudaStream_t s) {
+  const Tree& t = c->tree;
+  const int ncoef = c->ncoef;
+  const int nl = t.n_leaves();
+  const int L = t.L;
+  const double h = t.side / (double)(1 << L);
+  // column tiles: p2p uses ct columns per block; expansion kernels ncoef*ct threads
+  const int ct_p = nc < 8 ? nc : 8;
+  const int ct_e = nc < 4 ? nc : 4;
+  dim3 gp(nl, (nc + ct_p - 1) / ct_p);
+  k_p2p<T><<<gp, 128, 0, s>>>(nc, ct_p, c->d.leaf_first.p, c->d.leaf_count.p, c->d.u_ptr32.p, c->d.u_src.p,
+                              c->d.near_off.p, c->d.near_w.p, near, X, Y);
+  const int ecols = (nc + ct_e - 1) / ct_e;
+  const int leaf0 = t.level_off[L];
+  k_p2m<T><<<dim3(nl, ecols), 256, 0, s>>>(nc, ct_e, ncoef, leaf0, c->d.leaf_first.p, c->d.leaf_count.p, mom, X,
+                                           Mx);
+  for (int l = L - 1; l >= 2; --l) {
+    int nbx = t.level_off[l + 1] - t.level_off[l];
+    k_m2m<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, t.level_off[l], c->d.box_child_ptr.p,
+                                              c->d.box_oct.p, tm2m, Mx);
+  }
+  {
+    int b0 = t.level_off[2];
+    int nbx = t.level_off[L + 1] - b0;
+    k_m2l<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, b0, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p,
+                                              tm2l, Mx, Lx);
+  }
+  for (int l = 3; l <= L; ++l) {
+    int nbx = t.level_off[l + 1] - t.level_off[l];
+    k_l2l<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, t.level_off[l], c->d.box_parent.p,
+                                              c->d.box_oct.p, tl2l, Lx);
+  }
+  k_l2p<T><<<dim3(nl, ecols), 128, 0, s>>>(nc, ct_e, ncoef, leaf0, (T)(1.0 / h), c->d.leaf_first.p,
+                                           c->d.leaf_count.p, mom, Lx, Y);
+  XRL_CUDA(cudaGetLastError());
+}
+
+void fmm_apply(xrl_ctx* c, int nc, const double* X, double* Y, cudaStream_t s) {
+  size_t ne = (size_t)c->tree.n_boxes() * c->ncoef * nc;
+  c->d.Mexp.ensure(c->alloc, ne);
+  c->d.Lexp.ensure(c->alloc, ne);
+  fmm_apply_t<double>(c, nc, X, Y, c->d.near_val.p, c->d.mom.p, c->d.t_m2m.p, c->d.t_l2l.p, c->d.t_m2l.p,
+                      c->d.Mexp.p, c->d.Lexp.p, s);
+}
+
+void fmm_apply32(xrl_ctx* c, int nc, const float* X, float* Y, cudaStream_t s) {
+  size_t ne = (size_t)c->tree.n_boxes() * c->ncoef * nc;
+  c->d.M32.ensure(c->alloc, ne);
+  c->d.L32.ensure(c->alloc, ne);
+  fmm_apply_t<float>(c, nc, X, Y, c->d.near_val32.p, c->d.mom32.p, c->d.t_m2m32.p, c->d.t_l2l32.p,
+                     c->d.t_m2l32.p, c->d.M32.p, c->d.L32.p, s);
+}
+
+}  // namespace xrl

@@ -1,0 +1,735 @@
+// Loop-space operator, diagonal-of-P preconditioner and batched flexible
+// GMRES for the broadband sweep (sm_103a).
+//
+// Sec. II-C splits the loop system (eq. 7) as eq. 8-9:
+//   Z(f) I_l = M [ sum_t A_t (diag(Z_s(f)/A) + j omega mu0/4pi P) A_t^T ] M^T I_l = V_l.
+// One product therefore gathers panel currents I_pt = A_t^T M^T I_l (three
+// Cartesian components, real and imaginary part: 6 real FMM columns per
+// complex system), applies the frequency-independent P once to all columns
+// of all (frequency, port) systems with the FMM, and scatters back with the
+// per-system factors j omega mu0/4pi and Z_s(f)/A (Sec. II-D: "the potential
+// part is computed once and scaled by j omega mu0/4pi").
+//
+// Preconditioner (Sec. II-D, eq. 10): Q(f) = M [sum_t A_t diag(Z_s/A +
+// j omega mu0/4pi P_ll) A_t^T] M^T.  With one surface impedance per material,
+// Q(f) = sum_m Z_s^m(f) QA_m + j omega mu0/4pi QP: a pencil of real sparse
+// matrices built once (topology.cpp); the paper factors Q with a sparse LU
+// (MKL Pardiso); here Q^-1 v is approximated on the GPU by Jacobi-
+// preconditioned COCG (conjugate orthogonal CG for complex symmetric
+// matrices) with a fixed iteration budget, which makes the preconditioner
+// vary between applications, so the outer solver is right-preconditioned
+// FLEXIBLE GMRES (the paper: mRHS-GMRES, restart 50, Sec. III).
+//
+// All systems of a sweep form one block: vectors are [n_sys][n_loops]
+// complex (interleaved double2), every kernel loops over all systems, and
+// converged systems are frozen by a device-side mask.
+#include <cmath>
+#include <vector>
+
+#include "xrl_internal.hpp"
+
+namespace xrl {
+
+typedef double2 cplx;
+__device__ __forceinline__ cplx cm(cplx a, cplx b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ cplx csub(cplx a, cplx b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ cplx cconj(cplx a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ cplx cscale(cplx a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+  double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double cabs2(cplx a) { return a.x * a.x + a.y * a.y; }
+
+constexpr double kMu0Over4Pi = 1e-7;
+
+// ---- per-system constants ------------------------------------------------------------------
+// Z_s(f) of eq. 3: R_DC x / (1 - exp(-x)), x = (1+j) R_RF sqrt(f) / R_DC,
+// series 1 + x/2 + x^2/12 - x^4/720 for |x| < 1e-3.
+__global__ void k_sys_consts(int nsys, int nport, int nmat, const double* __restrict__ freq,
+                             const double* __restrict__ sig, const double* __restrict__ thk,
+                             cplx* __restrict__ zs, double* __restrict__ wp) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsys * nmat) return;
+  int s = i / nmat, m = i % nmat;
+  double f = freq[s / nport];
+  double rdc = 2.0 / (sig[m] * thk[m]);
+  double rrf = sqrt(3.14159265358979323846 * (4e-7 * 3.14159265358979323846) / sig[m]);
+  double a = rrf * sqrt(f) / rdc;   // x = a (1 + j)
+  cplx x = make_double2(a, a);
+  cplx q;
+  if (sqrt(2.0) * a < 1e-3) {
+    cplx x2 = cm(x, x), x4 = cm(x2, x2);
+    q = make_double2(1.0 + x.x / 2.0 + x2.x / 12.0 - x4.x / 720.0, x.y / 2.0 + x2.y / 12.0 - x4.y / 720.0);
+  } else {
+    // 1 - exp(-x) = -expm1(-a - j a) = -(expm1(-a) cos a - 2 sin^2(a/2)) + j e^{-a} sin a
+    double sh = sin(0.5 * a);
+    cplx den = make_double2(-(expm1(-a) * cos(a) - 2.0 * sh * sh), exp(-a) * sin(a));
+    q = cdiv(x, den);
+  }
+  zs[i] = cscale(q, rdc);
+  if (m == 0) wp[s] = 2.0 * 3.14159265358979323846 * f * kMu0Over4Pi;
+}
+
+// ---- operator pieces -------------------------------------------------------------------------
+// X[r][6s + 2t + ri] = (A_t^T M^T v_s)(r)
+__global__ void k_gather(int N, int nsys, int nloop, const int32_t* __restrict__ pan_br,
+                         const double* __restrict__ pan_rho, const int32_t* __restrict__ mt_ptr,
+                         const int32_t* __restrict__ mt_col, const int8_t* __restrict__ mt_val,
+                         const cplx* __restrict__ v, double* __restrict__ X) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)N * nsys) return;
+  int r = (int)(idx / nsys), s = (int)(idx % nsys);
+  const cplx* vs = v + (size_t)s * nloop;
+  cplx ip[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+  for (int k = 0; k < 3; ++k) {
+    int b = pan_br[3 * r + k];
+    if (b < 0) continue;
+    cplx ie = make_double2(0, 0);
+    for (int q = mt_ptr[b]; q < mt_ptr[b + 1]; ++q) {
+      cplx x = vs[mt_col[q]];
+      ie = mt_val[q] > 0 ? cadd(ie, x) : csub(ie, x);
+    }
+    const double* rho = pan_rho + 9 * (size_t)r + 3 * k;
+    for (int t = 0; t < 3; ++t) ip[t] = cadd(ip[t], cscale(ie, rho[t]));
+  }
+  double* out = X + (size_t)r * 6 * nsys + 6 * s;
+  for (int t = 0; t < 3; ++t) {
+    out[2 * t] = ip[t].x;
+    out[2 * t + 1] = ip[t].y;
+  }
+}
+
+// Vb[s][b] = sum_side rho . (j w' Y + Z_s/A X) at the branch's panels
+__global__ void k_scatter(int B, int nsys, int nmat, const int32_t* __restrict__ br_pan,
+                          const double* __restrict__ br_rho, const int32_t* __restrict__ pan_mat,
+                          const double* __restrict__ area, const cplx* __restrict__ zs,
+                          const double* __restrict__ wp, const double* __restrict__ X,
+                          const double* __restrict__ Y, cplx* __restrict__ Vb) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)B * nsys) return;
+  int s = (int)(idx / B), b = (int)(idx % B);
+  cplx acc = make_double2(0, 0);
+  for (int side = 0; side < 2; ++side) {
+    int r = br_pan[2 * b + side];
+    if (r < 0) continue;
+    const double* rho = br_rho + 6 * (size_t)b + 3 * side;
+    cplx z = cscale(zs[s * nmat + pan_mat[r]], 1.0 / area[r]);
+    const double* xr = X + (size_t)r * 6 * nsys + 6 * s;
+    const double* yr = Y + (size_t)r * 6 * nsys + 6 * s;
+    for (int t = 0; t < 3; ++t) {
+      cplx xv = make_double2(xr[2 * t], xr[2 * t + 1]);
+      cplx yv = make_double2(yr[2 * t], yr[2 * t + 1]);
+      cplx val = cadd(cm(z, xv), make_double2(-wp[s] * yv.y, wp[s] * yv.x));
+      acc = cadd(acc, cscale(val, rho[t]));
+    }
+  }
+  Vb[idx] = acc;
+}
+
+// w[s][l] = sum_b M(l, b) Vb[s][b]   (port branches carry no impedance: their Vb is zero)
+__global__ void k_loop_reduce(int nloop, int nsys, int B, int ncb, const int32_t* __restrict__ m_ptr,
+                              const int32_t* __restrict__ m_col, const int8_t* __restrict__ m_val,
+                              const cplx* __restrict__ Vb, cplx* __restrict__ w) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)nloop * nsys) return;
+  int s = (int)(idx / nloop), l = (int)(idx % nloop);
+  cplx acc = make_double2(0, 0);
+  const cplx* vb = Vb + (size_t)s * B;
+  for (int q = m_ptr[l]; q < m_ptr[l + 1]; ++q) {
+    int b = m_col[q];
+    if (b >= ncb) continue;
+    acc = m_val[q] > 0 ? cadd(acc, vb[b]) : csub(acc, vb[b]);
+  }
+  w[idx] = acc;
+}
+
+// w = Q(f_s) v (mode 0) or diag(Q(f_s)) (mode 1, v unused)
+__global__ void k_qspmv(int nloop, int nsys, int nmat, const int32_t* __restrict__ q_ptr,
+                        const int32_t* __restrict__ q_col, const double* __restrict__ q_val,
+                        const cplx* __restrict__ zs, const double* __restrict__ wp,
+                        const cplx* __restrict__ v, cplx* __restrict__ w, int mode) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)nloop * nsys) return;
+  int s = (int)(idx / nloop), l = (int)(idx % nloop);
+  const int W = nmat + 1;
+  cplx acc = make_double2(0, 0);
+  const cplx* vs = v ? v + (size_t)s * nloop : nullptr;
+  for (int q = q_ptr[l]; q < q_ptr[l + 1]; ++q) {
+    int col = q_col[q];
+    if (mode == 1 && col != l) continue;
+    const double* qv = q_val + (size_t)q * W;
+    cplx a = make_double2(0.0, wp[s] * qv[nmat]);
+    for (int m = 0; m < nmat; ++m) a = cadd(a, cscale(zs[s * nmat + m], qv[m]));
+    acc = cadd(acc, mode == 1 ? a : cm(a, vs[col]));
+  }
+  w[idx] = acc;
+}
+
+// ---- block reductions per system --------------------------------------------------------------
+__device__ cplx block_sum(cplx v, cplx* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] = cadd(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  cplx r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// out[s] = sum_i op(a_s[i]) b_s[i], op = conj (herm = 1) or identity; one block per system
+__global__ void k_dot(int n, int nsys, const cplx* __restrict__ a, const cplx* __restrict__ b, int herm,
+                      cplx* __restrict__ out) {
+  __shared__ cplx sh[256];
+  int s = blockIdx.x;
+  const cplx* as = a + (size_t)s * n;
+  const cplx* bs = b + (size_t)s * n;
+  cplx acc = make_double2(0, 0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc = cadd(acc, cm(herm ? cconj(as[i]) : as[i], bs[i]));
+  cplx r = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[s] = r;
+}
+
+// ---- COCG (inner solve of Q z = v) ------------------------------------------------------------
+// state per system: rho, alpha, flags
+__global__ void k_cocg_init(int n, int nsys, const cplx* __restrict__ v, const cplx* __restrict__ dinv,
+                            cplx* __restrict__ z, cplx* __restrict__ r, cplx* __restrict__ p,
+                            cplx* __restrict__ rho, double* __restrict__ vnorm2, int* __restrict__ live) {
+  __shared__ cplx sh[256];
+  int s = blockIdx.x;
+  size_t o = (size_t)s * n;
+  cplx acc = make_double2(0, 0), nn = make_double2(0, 0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    cplx vi = v[o + i];
+    z[o + i] = make_double2(0, 0);
+    r[o + i] = vi;
+    cplx u = cm(dinv[o + i], vi);
+    p[o + i] = u;
+    acc = cadd(acc, cm(vi, u));
+    nn.x += cabs2(vi);
+  }
+  cplx a = block_sum(acc, sh);
+  cplx b = block_sum(nn, sh);
+  if (threadIdx.x == 0) {
+    rho[s] = a;
+    vnorm2[s] = b.x;
+    live[s] = b.x > 0.0 ? 1 : 0;
+  }
+}
+
+// alpha = rho / p^T q; z += alpha p; r -= alpha q; then rho' = r^T D^-1 r, beta, p = D^-1 r + beta p
+__global__ void k_cocg_step(int n, int nsys, const cplx* __restrict__ q, const cplx* __restrict__ dinv,
+                            cplx* __restrict__ z, cplx* __restrict__ r, cplx* __restrict__ p,
+                            cplx* __restrict__ rho, const double* __restrict__ vnorm2, int* __restrict__ live,
+                            double tol2) {
+  __shared__ cplx sh[256];
+  int s = blockIdx.x;
+  if (!live[s]) return;
+  size_t o = (size_t)s * n;
+  cplx acc = make_double2(0, 0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc = cadd(acc, cm(p[o + i], q[o + i]));
+  cplx ptq = block_sum(acc, sh);
+  if (cabs2(ptq) == 0.0) {
+    if (threadIdx.x == 0) live[s] = 0;
+    return;
+  }
+  cplx alpha = cdiv(rho[s], ptq);
+  cplx rr = make_double2(0, 0), nn = make_double2(0, 0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    z[o + i] = cadd(z[o + i], cm(alpha, p[o + i]));
+    cplx ri = csub(r[o + i], cm(alpha, q[o + i]));
+    r[o + i] = ri;
+    rr = cadd(rr, cm(ri, cm(dinv[o + i], ri)));
+    nn.x += cabs2(ri);
+  }
+  cplx rho_new = block_sum(rr, sh);
+  cplx rn = block_sum(nn, sh);
+  if (rn.x <= tol2 * vnorm2[s] || cabs2(rho[s]) == 0.0) {
+    if (threadIdx.x == 0) live[s] = 0;
+    return;
+  }
+  cplx beta = cdiv(rho_new, rho[s]);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) p[o + i] = cadd(cm(dinv[o + i], r[o + i]), cm(beta, p[o + i]));
+  __syncthreads();
+  if (threadIdx.x == 0) rho[s] = rho_new;
+}
+
+__global__ void k_inv(size_t n, const cplx* __restrict__ d, cplx* __restrict__ di) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) di[i] = cdiv(make_double2(1.0, 0.0), d[i]);
+}
+
+// ---- FGMRES pieces ------------------------------------------------------------------------------
+// h[s][i] = v_i^H w for i <= j (block per (i, s)), accumulated into H column j (add = 1) or set
+__global__ void k_arnoldi_dots(int n, int nsys, int j, int ldh, const cplx* __restrict__ V,
+                               const cplx* __restrict__ w, cplx* __restrict__ h, const int* __restrict__ active) {
+  __shared__ cplx sh[256];
+  int i = blockIdx.x, s = blockIdx.y;
+  if (!active[s]) return;
+  const cplx* vi = V + ((size_t)i * nsys + s) * n;
+  const cplx* ws = w + (size_t)s * n;
+  cplx acc = make_double2(0, 0);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) acc = cadd(acc, cm(cconj(vi[e]), ws[e]));
+  cplx r = block_sum(acc, sh);
+  if (threadIdx.x == 0) h[(size_t)s * ldh + i] = r;
+}
+
+// w -= sum_{i<=j} h_i v_i ; also Hcol += h (Hcol = H[s][:, j])
+__global__ void k_arnoldi_sub(int n, int nsys, int j, int ldh, const cplx* __restrict__ V,
+                              const cplx* __restrict__ h, cplx* __restrict__ w, const int* __restrict__ active) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * nsys) return;
+  int s = (int)(idx / n), e = (int)(idx % n);
+  if (!active[s]) return;
+  cplx acc = w[idx];
+  for (int i = 0; i <= j; ++i) acc = csub(acc, cm(h[(size_t)s * ldh + i], V[((size_t)i * nsys + s) * n + e]));
+  w[idx] = acc;
+}
+
+// H[s][i][j] += h[s][i] (i <= j), then ||w|| -> H[s][j+1][j]; v_{j+1} = w / ||w||;
+// Givens update of the residual estimate; mark converged systems.
+// H layout: [s][(m+1)][m] row-major.
+__global__ void k_arnoldi_norm(int n, int nsys, int j, int m, cplx* __restrict__ H, const cplx* __restrict__ h1,
+                               const cplx* __restrict__ h2, cplx* __restrict__ w, cplx* __restrict__ Vnext,
+                               cplx* __restrict__ cs, cplx* __restrict__ sn, cplx* __restrict__ g,
+                               int* __restrict__ active, const double* __restrict__ bnorm, double tol,
+                               double* __restrict__ resid, int* __restrict__ iters) {
+  __shared__ cplx sh[256];
+  int s = blockIdx.x;
+  if (!active[s]) return;
+  const int ldh = m + 1;
+  cplx* ws = w + (size_t)s * n;
+  cplx acc = make_double2(0, 0);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) acc.x += cabs2(ws[e]);
+  double nw = sqrt(block_sum(acc, sh).x);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) Vnext[(size_t)s * n + e] = nw > 0 ? cscale(ws[e], 1.0 / nw) : make_double2(0, 0);
+  if (threadIdx.x == 0) {
+    cplx* Hs = H + (size_t)s * (m + 1) * m;
+    for (int i = 0; i <= j; ++i) Hs[i * m + j] = cadd(h1[(size_t)s * ldh + i], h2[(size_t)s * ldh + i]);
+    Hs[(j + 1) * m + j] = make_double2(nw, 0.0);
+    // apply previous rotations
+    for (int i = 0; i < j; ++i) {
+      cplx a = Hs[i * m + j], b = Hs[(i + 1) * m + j];
+      cplx c = cs[s * m + i], sv = sn[s * m + i];
+      Hs[i * m + j] = cadd(cm(cconj(c), a), cm(cconj(sv), b));
+      Hs[(i + 1) * m + j] = csub(cm(c, b), cm(sv, a));
+    }
+    cplx a = Hs[j * m + j], b = Hs[(j + 1) * m + j];
+    double na = sqrt(cabs2(a)), nb = sqrt(cabs2(b));
+    double den = sqrt(na * na + nb * nb);
+    cplx c, sv;
+    if (den == 0.0) {
+      c = make_double2(1, 0);
+      sv = make_double2(0, 0);
+    } else {
+      c = cscale(a, 1.0 / den);
+      sv = cscale(b, 1.0 / den);
+    }
+    cs[s * m + j] = c;
+    sn[s * m + j] = sv;
+    Hs[j * m + j] = make_double2(den, 0.0);
+    Hs[(j + 1) * m + j] = make_double2(0, 0);
+    cplx gj = g[s * (m + 1) + j];
+    g[s * (m + 1) + j] = cm(cconj(c), gj);
+    g[s * (m + 1) + j + 1] = cscale(cm(sv, gj), -1.0);
+    double res = sqrt(cabs2(g[s * (m + 1) + j + 1]));
+    resid[s] = res / bnorm[s];
+    iters[s] += 1;
+    if (res <= tol * bnorm[s] || nw == 0.0) active[s] = 0;
+  }
+}
+
+// y = H^-1 g (upper triangular, k x k per system); x += Z y
+__global__ void k_trisolve(int nsys, int m, const int* __restrict__ kcols, const cplx* __restrict__ H,
+                           const cplx* __restrict__ g, cplx* __restrict__ y) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys) return;
+  int k = kcols[s];
+  const cplx* Hs = H + (size_t)s * (m + 1) * m;
+  for (int i = k - 1; i >= 0; --i) {
+    cplx acc = g[s * (m + 1) + i];
+    for (int j = i + 1; j < k; ++j) acc = csub(acc, cm(Hs[i * m + j], y[s * m + j]));
+    y[s * m + i] = cdiv(acc, Hs[i * m + i]);
+  }
+}
+
+__global__ void k_update_x(int n, int nsys, int m, const int* __restrict__ kcols, const cplx* __restrict__ Z,
+                           const cplx* __restrict__ y, cplx* __restrict__ x) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * nsys) return;
+  int s = (int)(idx / n), e = (int)(idx % n);
+  cplx acc = x[idx];
+  for (int i = 0; i < kcols[s]; ++i) acc = cadd(acc, cm(y[s * m + i], Z[((size_t)i * nsys + s) * n + e]));
+  x[idx] = acc;
+}
+
+// r = b - Ax ; beta = ||r||; v0 = r / beta; g = (beta, 0, ...)
+__global__ void k_restart(int n, int nsys, int m, const cplx* __restrict__ b, const cplx* __restrict__ Ax,
+                          cplx* __restrict__ V0, cplx* __restrict__ g, const double* __restrict__ bnorm,
+                          double tol, int* __restrict__ active, double* __restrict__ resid) {
+  __shared__ cplx sh[256];
+  int s = blockIdx.x;
+  size_t o = (size_t)s * n;
+  cplx acc = make_double2(0, 0);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    cplx r = Ax ? csub(b[o + e], Ax[o + e]) : b[o + e];
+    V0[o + e] = r;
+    acc.x += cabs2(r);
+  }
+  double beta = sqrt(block_sum(acc, sh).x);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) V0[o + e] = beta > 0 ? cscale(V0[o + e], 1.0 / beta) : make_double2(0, 0);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i <= m; ++i) g[s * (m + 1) + i] = make_double2(0, 0);
+    g[s * (m + 1)] = make_double2(beta, 0);
+    resid[s] = bnorm[s] > 0 ? beta / bnorm[s] : 0.0;
+    active[s] = (beta > tol * bnorm[s]) ? 1 : 0;
+  }
+}
+
+__global__ void k_bnorm(int n, int nsys, const cplx* __restrict__ b, double* __restrict__ out) {
+  __shared__ cplx sh[256];
+  int s = blockIdx.x;
+  cplx acc = make_double2(0, 0);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) acc.x += cabs2(b[(size_t)s * n + e]);
+  double v = sqrt(block_sum(acc, sh).x);
+  if (threadIdx.x == 0) out[s] = v;
+}
+
+// RHS: b_s = column of M for the port branch of system s (sign +1 on its loop)
+__global__ void k_rhs(int nloop, int nsys, int nport, const int32_t* __restrict__ port_loop,
+                      const int8_t* __restrict__ port_sign, cplx* __restrict__ b) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)nloop * nsys) return;
+  int s = (int)(idx / nloop), l = (int)(idx % nloop);
+  int p = s % nport;
+  b[idx] = make_double2(l == port_loop[p] ? (double)port_sign[p] : 0.0, 0.0);
+}
+
+// Port reduction per frequency: Y[q][p] = b_q^T x_{f,p}; Z = Y^-1; R, L
+__global__ void k_ports(int nf, int nport, int nloop, const double* __restrict__ freq,
+                        const int32_t* __restrict__ port_loop, const int8_t* __restrict__ port_sign,
+                        const cplx* __restrict__ x, double* __restrict__ R, double* __restrict__ L) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  cplx A[16][32];
+  const int n = nport;
+  for (int q = 0; q < n; ++q)
+    for (int p = 0; p < n; ++p) {
+      int s = f * nport + p;
+      A[q][p] = cscale(x[(size_t)s * nloop + port_loop[q]], (double)port_sign[q]);
+      A[q][n + p] = make_double2(q == p ? 1.0 : 0.0, 0.0);
+    }
+  // Gauss-Jordan with partial pivoting
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (cabs2(A[r][c]) > cabs2(A[piv][c])) piv = r;
+    if (piv != c)
+      for (int k = 0; k < 2 * n; ++k) {
+        cplx t = A[c][k];
+        A[c][k] = A[piv][k];
+        A[piv][k] = t;
+      }
+    cplx d = A[c][c];
+    for (int k = 0; k < 2 * n; ++k) A[c][k] = cdiv(A[c][k], d);
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      cplx fct = A[r][c];
+      for (int k = 0; k < 2 * n; ++k) A[r][k] = csub(A[r][k], cm(fct, A[c][k]));
+    }
+  }
+  double w = 2.0 * 3.14159265358979323846 * freq[f];
+  for (int q = 0; q < n; ++q)
+    for (int p = 0; p < n; ++p) {
+      cplx z = A[q][n + p];
+      R[((size_t)f * n + q) * n + p] = z.x;
+      L[((size_t)f * n + q) * n + p] = z.y / w;
+    }
+}
+
+// ---- host side ---------------------------------------------------------------------------
+struct SolverState {
+  int nsys = 0, nloop = 0, m = 0;
+  DBuf<double> freq, wp;
+  DBuf<cplx> zs;
+};
+
+void solver_prepare(xrl_ctx* c) {
+  Topo& T = c->topo;
+  Tree& tr = c->tree;
+  const int N = c->N;
+  std::vector<int32_t> pan_br(3 * (size_t)N, -1), pan_mat(N, -1), br_pan(2 * (size_t)T.n_cb, -1);
+  std::vector<double> pan_rho(9 * (size_t)N, 0.0), br_rho(6 * (size_t)T.n_cb, 0.0);
+  std::vector<int> slot(N, 0);
+  for (int b = 0; b < T.n_cb; ++b)
+    for (int side = 0; side < 2; ++side) {
+      int p = T.br_pan[side][b];
+      if (p < 0) continue;
+      int r = tr.rank[p];
+      int k = slot[p]++;
+      XRL_CHECK(k < 3, XRL_ETOPO, "internal: a panel has more than three branches");
+      pan_br[3 * (size_t)r + k] = b;
+      br_pan[2 * (size_t)b + side] = r;
+      for (int t = 0; t < 3; ++t) {
+        double v = T.br_rho[side][3 * (size_t)b + t];
+        pan_rho[9 * (size_t)r + 3 * k + t] = v;
+        br_rho[6 * (size_t)b + 3 * side + t] = v;
+      }
+    }
+  for (int p = 0; p < N; ++p)
+    if (T.live_of_panel[p] >= 0) pan_mat[tr.rank[p]] = T.mat_of_cond[c->cond[p]];
+  c->d.pan_br.upload(c->alloc, pan_br);
+  c->d.pan_rho.upload(c->alloc, pan_rho);
+  c->d.pan_mat.upload(c->alloc, pan_mat);
+  c->d.br_pan.upload(c->alloc, br_pan);
+  c->d.br_rho.upload(c->alloc, br_rho);
+  auto to32 = [](const std::vector<int64_t>& a) { return std::vector<int32_t>(a.begin(), a.end()); };
+  XRL_CHECK(T.m_col.size() < (size_t)INT32_MAX && T.q_col.size() < (size_t)INT32_MAX, XRL_ENOMEM,
+            "loop or preconditioner matrix too large for 32-bit indices");
+  c->d.m_ptr.upload(c->alloc, to32(T.m_ptr));
+  c->d.m_col.upload(c->alloc, T.m_col);
+  c->d.m_val.upload(c->alloc, T.m_val);
+  c->d.mt_ptr.upload(c->alloc, to32(T.mt_ptr));
+  c->d.mt_col.upload(c->alloc, T.mt_col);
+  c->d.mt_val.upload(c->alloc, T.mt_val);
+  c->d.q_ptr.upload(c->alloc, to32(T.q_ptr));
+  c->d.q_col.upload(c->alloc, T.q_col);
+  c->d.q_val.upload(c->alloc, T.q_val);
+  c->d.mat_sigma.upload(c->alloc, T.mat_sigma);
+  c->d.mat_thick.upload(c->alloc, T.mat_thick);
+}
+
+static unsigned nblk(size_t n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
+
+// Work arrays of one solve (device)
+struct Work {
+  DBuf<double> freq, wp;
+  DBuf<cplx> zs, b, x, w, tmp, V, Z, H, h1, h2, cs, sn, g, y, Vb, dinv;
+  DBuf<cplx> cz, cr, cp, cq, crho;
+  DBuf<double> X, Y, bnorm, resid, cvn;
+  DBuf<int> active, iters, kcols, clive;
+};
+
+static void sys_consts(xrl_ctx* c, Work& wk, int nsys, int nport, int nf, const double* freq) {
+  const Topo& T = c->topo;
+  wk.freq.upload(c->alloc, std::vector<double>(freq, freq + nf));
+  wk.zs.alloc(c->alloc, (size_t)nsys * T.n_mat);
+  wk.wp.alloc(c->alloc, nsys);
+  k_sys_consts<<<nblk((size_t)nsys * T.n_mat), 256, 0, c->stream>>>(nsys, nport, T.n_mat, wk.freq.p,
+                                                                    c->d.mat_sigma.p, c->d.mat_thick.p, wk.zs.p,
+                                                                    wk.wp.p);
+}
+
+// w = Z(f_s) v_s for all systems (eq. 8), FMM in FP64
+static void apply_A(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w) {
+  const Topo& T = c->topo;
+  const int N = c->N;
+  const int nc = 6 * nsys;
+  cudaStream_t s = c->stream;
+  wk.X.ensure(c->alloc, (size_t)N * nc);
+  wk.Y.ensure(c->alloc, (size_t)N * nc);
+  wk.Vb.ensure(c->alloc, (size_t)nsys * T.n_cb);
+  k_gather<<<nblk((size_t)N * nsys), 256, 0, s>>>(N, nsys, T.n_loops, c->d.pan_br.p, c->d.pan_rho.p, c->d.mt_ptr.p,
+                                                 c->d.mt_col.p, c->d.mt_val.p, v, wk.X.p);
+  fmm_apply(c, nc, wk.X.p, wk.Y.p, s);
+  // conductor branches only; the external port branches carry no impedance
+  k_scatter<<<nblk((size_t)T.n_cb * nsys), 256, 0, s>>>(T.n_cb, nsys, T.n_mat, c->d.br_pan.p, c->d.br_rho.p,
+                                                        c->d.pan_mat.p, c->d.area.p, wk.zs.p, wk.wp.p, wk.X.p,
+                                                        wk.Y.p, wk.Vb.p);
+  k_loop_reduce<<<nblk((size_t)T.n_loops * nsys), 256, 0, s>>>(T.n_loops, nsys, T.n_cb, T.n_cb, c->d.m_ptr.p,
+                                                               c->d.m_col.p, c->d.m_val.p, wk.Vb.p, w);
+  XRL_CUDA(cudaGetLastError());
+  c->stats.n_mvm++;
+}
+
+static void apply_Qmat(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, int mode) {
+  const Topo& T = c->topo;
+  k_qspmv<<<nblk((size_t)T.n_loops * nsys), 256, 0, c->stream>>>(T.n_loops, nsys, T.n_mat, c->d.q_ptr.p,
+                                                                  c->d.q_col.p, c->d.q_val.p, wk.zs.p, wk.wp.p, v,
+                                                                  w, mode);
+  XRL_CUDA(cudaGetLastError());
+}
+
+// z ~= Q^-1 v by Jacobi-COCG with a fixed budget (or z = v without preconditioner)
+static void apply_Qinv(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* z) {
+  const int n = c->topo.n_loops;
+  cudaStream_t s = c->stream;
+  if (c->opt.precond == 0) {
+    XRL_CUDA(cudaMemcpyAsync(z, v, sizeof(cplx) * (size_t)n * nsys, cudaMemcpyDeviceToDevice, s));
+    return;
+  }
+  const size_t tot = (size_t)n * nsys;
+  wk.cr.ensure(c->alloc, tot);
+  wk.cp.ensure(c->alloc, tot);
+  wk.cq.ensure(c->alloc, tot);
+  wk.crho.ensure(c->alloc, nsys);
+  wk.cvn.ensure(c->alloc, nsys);
+  wk.clive.ensure(c->alloc, nsys);
+  k_cocg_init<<<nsys, 256, 0, s>>>(n, nsys, v, wk.dinv.p, z, wk.cr.p, wk.cp.p, wk.crho.p, wk.cvn.p, wk.clive.p);
+  const double tol2 = c->opt.inner_tol * c->opt.inner_tol;
+  for (int it = 0; it < c->opt.inner_iters; ++it) {
+    apply_Qmat(c, wk, nsys, wk.cp.p, wk.cq.p, 0);
+    k_cocg_step<<<nsys, 256, 0, s>>>(n, nsys, wk.cq.p, wk.dinv.p, z, wk.cr.p, wk.cp.p, wk.crho.p, wk.cvn.p,
+                                     wk.clive.p, tol2);
+  }
+  XRL_CUDA(cudaGetLastError());
+  c->stats.total_inner += c->opt.inner_iters;
+}
+
+void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
+  const Topo& T = c->topo;
+  const int np = T.n_port;
+  XRL_CHECK(np > 0, XRL_ESTATE, "no ports defined");
+  XRL_CHECK(np <= 16, XRL_EINVAL, "at most 16 ports per context");
+  const int nsys = nf * np;
+  const int n = T.n_loops;
+  const int m = std::max(1, std::min(c->opt.restart, 200));
+  const size_t tot = (size_t)n * nsys;
+  cudaStream_t s = c->stream;
+  Work wk;
+  sys_consts(c, wk, nsys, np, nf, freq);
+  // port loops: the loop containing each port branch (global loops are listed last)
+  std::vector<int32_t> port_loop(np, -1);
+  std::vector<int8_t> port_sign(np, 0);
+  for (int p = 0; p < np; ++p) {
+    int b = T.n_cb + p;
+    XRL_CHECK(T.mt_ptr[b + 1] - T.mt_ptr[b] == 1, XRL_ETOPO, "internal: a port branch must lie in one loop");
+    port_loop[p] = T.mt_col[T.mt_ptr[b]];
+    port_sign[p] = T.mt_val[T.mt_ptr[b]];
+  }
+  DBuf<int32_t> dpl;
+  DBuf<int8_t> dps;
+  dpl.upload(c->alloc, port_loop);
+  dps.upload(c->alloc, port_sign);
+  wk.b.alloc(c->alloc, tot);
+  wk.x.alloc(c->alloc, tot);
+  wk.w.alloc(c->alloc, tot);
+  wk.V.alloc(c->alloc, tot * (m + 1));
+  wk.Z.alloc(c->alloc, tot * m);
+  wk.H.alloc(c->alloc, (size_t)nsys * (m + 1) * m);
+  wk.h1.alloc(c->alloc, (size_t)nsys * (m + 1));
+  wk.h2.alloc(c->alloc, (size_t)nsys * (m + 1));
+  wk.cs.alloc(c->alloc, (size_t)nsys * m);
+  wk.sn.alloc(c->alloc, (size_t)nsys * m);
+  wk.g.alloc(c->alloc, (size_t)nsys * (m + 1));
+  wk.y.alloc(c->alloc, (size_t)nsys * m);
+  wk.bnorm.alloc(c->alloc, nsys);
+  wk.resid.alloc(c->alloc, nsys);
+  wk.active.alloc(c->alloc, nsys);
+  wk.iters.alloc(c->alloc, nsys);
+  wk.kcols.alloc(c->alloc, nsys);
+  if (c->opt.precond) {
+    wk.dinv.alloc(c->alloc, tot);
+    apply_Qmat(c, wk, nsys, nullptr, wk.w.p, 1);
+    k_inv<<<nblk(tot), 256, 0, s>>>(tot, wk.w.p, wk.dinv.p);
+  }
+  k_rhs<<<nblk(tot), 256, 0, s>>>(n, nsys, np, dpl.p, dps.p, wk.b.p);
+  XRL_CUDA(cudaMemsetAsync(wk.x.p, 0, sizeof(cplx) * tot, s));
+  XRL_CUDA(cudaMemsetAsync(wk.iters.p, 0, sizeof(int) * nsys, s));
+  k_bnorm<<<nsys, 256, 0, s>>>(n, nsys, wk.b.p, wk.bnorm.p);
+  c->stats.n_mvm = 0;
+  c->stats.total_inner = 0;
+  std::vector<int> hact(nsys), hiters(nsys);
+  const double tol = c->opt.tol;
+  int total = 0;
+  bool first = true;
+  bool done = false;
+  while (!done) {
+    // restart: true residual with the FP64 operator
+    if (!first) apply_A(c, wk, nsys, wk.x.p, wk.w.p);
+    k_restart<<<nsys, 256, 0, s>>>(n, nsys, m, wk.b.p, first ? nullptr : wk.w.p, wk.V.p, wk.g.p, wk.bnorm.p, tol,
+                                   wk.active.p, wk.resid.p);
+    first = false;
+    XRL_CUDA(cudaMemcpyAsync(hact.data(), wk.active.p, sizeof(int) * nsys, cudaMemcpyDeviceToHost, s));
+    XRL_CUDA(cudaStreamSynchronize(s));
+    int nact = 0;
+    for (int v : hact) nact += v;
+    if (nact == 0 || total >= c->opt.max_iters) break;
+    // kcols counts the Arnoldi columns each system has built in this cycle
+    XRL_CUDA(cudaMemsetAsync(wk.kcols.p, 0, sizeof(int) * nsys, s));
+    std::vector<int> hk(nsys, 0);
+    int j = 0;
+    for (; j < m && total < c->opt.max_iters; ++j, ++total) {
+      cplx* vj = wk.V.p + (size_t)j * tot;
+      cplx* zj = wk.Z.p + (size_t)j * tot;
+      apply_Qinv(c, wk, nsys, vj, zj);
+      apply_A(c, wk, nsys, zj, wk.w.p);
+      // CGS2
+      k_arnoldi_dots<<<dim3(j + 1, nsys), 256, 0, s>>>(n, nsys, j, m + 1, wk.V.p, wk.w.p, wk.h1.p, wk.active.p);
+      k_arnoldi_sub<<<nblk(tot), 256, 0, s>>>(n, nsys, j, m + 1, wk.V.p, wk.h1.p, wk.w.p, wk.active.p);
+      k_arnoldi_dots<<<dim3(j + 1, nsys), 256, 0, s>>>(n, nsys, j, m + 1, wk.V.p, wk.w.p, wk.h2.p, wk.active.p);
+      k_arnoldi_sub<<<nblk(tot), 256, 0, s>>>(n, nsys, j, m + 1, wk.V.p, wk.h2.p, wk.w.p, wk.active.p);
+      // record which systems take this column before they may deactivate
+      for (int q = 0; q < nsys; ++q)
+        if (hact[q]) hk[q] = j + 1;
+      k_arnoldi_norm<<<nsys, 256, 0, s>>>(n, nsys, j, m, wk.H.p, wk.h1.p, wk.h2.p, wk.w.p,
+                                          wk.V.p + (size_t)(j + 1) * tot, wk.cs.p, wk.sn.p, wk.g.p, wk.active.p,
+                                          wk.bnorm.p, tol, wk.resid.p, wk.iters.p);
+      XRL_CUDA(cudaGetLastError());
+      XRL_CUDA(cudaMemcpyAsync(hact.data(), wk.active.p, sizeof(int) * nsys, cudaMemcpyDeviceToHost, s));
+      XRL_CUDA(cudaStreamSynchronize(s));
+      nact = 0;
+      for (int v : hact) nact += v;
+      if (nact == 0) {
+        ++total;
+        ++j;
+        break;
+      }
+    }
+    XRL_CUDA(cudaMemcpyAsync(wk.kcols.p, hk.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
+    k_trisolve<<<nblk(nsys, 64), 64, 0, s>>>(nsys, m, wk.kcols.p, wk.H.p, wk.g.p, wk.y.p);
+    k_update_x<<<nblk(tot), 256, 0, s>>>(n, nsys, m, wk.kcols.p, wk.Z.p, wk.y.p, wk.x.p);
+    XRL_CUDA(cudaGetLastError());
+    if (total >= c->opt.max_iters) {
+      // final true residual for the stats
+      apply_A(c, wk, nsys, wk.x.p, wk.w.p);
+      k_restart<<<nsys, 256, 0, s>>>(n, nsys, m, wk.b.p, wk.w.p, wk.V.p, wk.g.p, wk.bnorm.p, tol, wk.active.p,
+                                     wk.resid.p);
+      done = true;
+    }
+  }
+  // outputs
+  DBuf<double> dR, dL;
+  dR.alloc(c->alloc, (size_t)nf * np * np);
+  dL.alloc(c->alloc, (size_t)nf * np * np);
+  k_ports<<<nblk(nf, 64), 64, 0, s>>>(nf, np, n, wk.freq.p, dpl.p, dps.p, wk.x.p, dR.p, dL.p);
+  XRL_CUDA(cudaGetLastError());
+  std::vector<double> hres(nsys);
+  XRL_CUDA(cudaMemcpyAsync(hres.data(), wk.resid.p, sizeof(double) * nsys, cudaMemcpyDeviceToHost, s));
+  XRL_CUDA(cudaMemcpyAsync(hiters.data(), wk.iters.p, sizeof(int) * nsys, cudaMemcpyDeviceToHost, s));
+  XRL_CUDA(cudaMemcpyAsync(R, dR.p, sizeof(double) * nf * np * np, cudaMemcpyDeviceToHost, s));
+  XRL_CUDA(cudaMemcpyAsync(L, dL.p, sizeof(double) * nf * np * np, cudaMemcpyDeviceToHost, s));
+  XRL_CUDA(cudaStreamSynchronize(s));
+  double mr = 0;
+  int mi = 0;
+  for (int q = 0; q < nsys; ++q) {
+    mr = std::max(mr, hres[q]);
+    mi = std::max(mi, hiters[q]);
+  }
+  c->stats.max_rel_res = mr;
+  c->stats.total_iters = mi;
+  XRL_CHECK(mr <= tol * 1.0000001, XRL_ENOCONV, "FGMRES did not reach the tolerance in max_iters");
+}
+
+void apply_operator_host(xrl_ctx* c, int nsys, const double* freq, const double* v, double* w, bool qmat) {
+  const Topo& T = c->topo;
+  const size_t tot = (size_t)T.n_loops * nsys;
+  Work wk;
+  // one port per "system": each system is its own frequency here
+  sys_consts(c, wk, nsys, 1, nsys, freq);
+  DBuf<cplx> dv, dw;
+  dv.alloc(c->alloc, tot);
+  dw.alloc(c->alloc, tot);
+  XRL_CUDA(cudaMemcpyAsync(dv.p, v, sizeof(cplx) * tot, cudaMemcpyHostToDevice, c->stream));
+  if (qmat)
+    apply_Qmat(c, wk, nsys, dv.p, dw.p, 0);
+  else
+    apply_A(c, wk, nsys, dv.p, dw.p);
+  XRL_CUDA(cudaMemcpyAsync(w, dw.p, sizeof(cplx) * tot, cudaMemcpyDeviceToHost, c->stream));
+  XRL_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+}  // namespace xrl

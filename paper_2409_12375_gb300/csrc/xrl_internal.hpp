@@ -1,0 +1,250 @@
+// Internal state of an xrl context and helpers shared by the library's
+// translation units.  Not part of the public ABI (see include/xrl.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/xrl.h"
+
+namespace xrl {
+
+// ---- errors ---------------------------------------------------------------
+struct Error : std::runtime_error {
+  xrl_status code;
+  Error(xrl_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define XRL_CUDA(call)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      throw ::xrl::Error(e_ == cudaErrorMemoryAllocation ? XRL_ENOMEM : XRL_ECUDA,         \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+#define XRL_CHECK(cond, code, msg)                 \
+  do {                                             \
+    if (!(cond)) throw ::xrl::Error((code), (msg)); \
+  } while (0)
+
+// ---- device memory with a high-water mark -----------------------------------
+struct DevAlloc {
+  int64_t cur = 0, peak = 0;
+  void* get(size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) return nullptr;
+    XRL_CUDA(cudaMalloc(&p, bytes));
+    cur += (int64_t)bytes;
+    if (cur > peak) peak = cur;
+    return p;
+  }
+  void put(void* p, size_t bytes) {
+    if (p) {
+      cudaFree(p);
+      cur -= (int64_t)bytes;
+    }
+  }
+};
+
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevAlloc* a = nullptr;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), a(o.a) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p; n = o.n; a = o.a;
+      o.p = nullptr; o.n = 0;
+    }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void release() {
+    if (a && p) a->put(p, n * sizeof(T));
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(DevAlloc& al, size_t count) {
+    release();
+    a = &al;
+    n = count;
+    p = static_cast<T*>(al.get(count * sizeof(T)));
+  }
+  void upload(DevAlloc& al, const std::vector<T>& h) {
+    alloc(al, h.size());
+    if (!h.empty()) XRL_CUDA(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  }
+  void ensure(DevAlloc& al, size_t count) {
+    if (n < count) alloc(al, count);
+  }
+  std::vector<T> download() const {
+    std::vector<T> h(n);
+    if (n) XRL_CUDA(cudaMemcpy(h.data(), p, n * sizeof(T), cudaMemcpyDeviceToHost));
+    return h;
+  }
+};
+
+// ---- quadrature rule table (shared specification with the CPU checker) -------
+// Class boundaries in q = |c_k - c_l| / (r_k + r_l) and rule orders.
+constexpr double kQNear = 1.5, kQSemi = 3.0, kQFar = 10.0;
+constexpr int kEdgeN = 10, kEdgeK = 3, kVertN = 10, kVertK = 3;
+constexpr int kNearQ = 8, kSemiQ = 5, kMidQ = 4, kFarQ = 3;
+
+// ---- host-side setup products -------------------------------------------------
+struct Tree {
+  int L = 0;                                   // leaf level; levels 0..L
+  double lo[3] = {0, 0, 0}, side = 0;          // root cube
+  std::vector<uint64_t> key;                   // per caller panel (level-21 Morton key)
+  std::vector<int32_t> perm;                   // Morton rank -> caller panel
+  std::vector<int32_t> rank;                   // caller panel -> Morton rank
+  std::vector<int32_t> level_off;              // first global box id of each level (size L+2)
+  std::vector<uint64_t> box_key;               // global box id -> key at its level
+  std::vector<int32_t> parent;                 // global box id -> parent global id (-1 root)
+  std::vector<int32_t> octant;                 // child position in parent (0..7)
+  std::vector<int32_t> leaf_first, leaf_count; // leaf-local index -> Morton panel range
+  std::vector<int32_t> leaf_of;                // Morton rank -> leaf-local index
+  // V-list per target box (global ids), all levels >= 2 concatenated in box order
+  std::vector<int64_t> v_ptr;                  // size n_boxes+1
+  std::vector<int32_t> v_src;                  // global source box
+  std::vector<int16_t> v_off;                  // index into m2l_offsets
+  std::vector<int32_t> m2l_offsets;            // distinct (target - source) offsets, 3 ints each
+  // U-list per leaf (leaf-local ids)
+  std::vector<int64_t> u_ptr;
+  std::vector<int32_t> u_src;
+  int n_boxes() const { return (int)box_key.size(); }
+  int n_leaves() const { return (int)leaf_first.size(); }
+};
+
+struct Topo {
+  int n_live = 0, n_term = 0, n_nodes = 0, n_cb = 0, n_branch = 0, n_port = 0;
+  int n_loops = 0, n_vertex_loops = 0, n_global_loops = 0;
+  std::vector<int32_t> live_of_panel;           // caller panel -> live index or -1
+  std::vector<int32_t> br_tail, br_head;        // node ids (live index or n_live + terminal)
+  std::vector<int32_t> br_pan[2];               // caller panel of tail / head side (-1 if terminal)
+  std::vector<double> br_rho[2];                // signed rho (3 per branch): +rho tail, -rho head
+  std::vector<int64_t> m_ptr;                   // loop CSR
+  std::vector<int32_t> m_col;
+  std::vector<int8_t> m_val;
+  std::vector<int64_t> mt_ptr;                  // branch CSR (transpose)
+  std::vector<int32_t> mt_col;
+  std::vector<int8_t> mt_val;
+  // Q pencil: Q(f) = sum_m Z_s^m(f) QA_m + j omega mu0/4pi QP (CSR over loops)
+  int n_mat = 0;
+  std::vector<int32_t> mat_of_cond;             // conductor -> material
+  std::vector<double> mat_sigma, mat_thick;
+  std::vector<int64_t> q_ptr;
+  std::vector<int32_t> q_col;
+  std::vector<double> q_val;                    // [nnz][n_mat + 1], last = P part
+};
+
+// ---- device-resident state ------------------------------------------------------
+struct Dev {
+  // Morton-ordered panel data
+  DBuf<double> vtx;        // [N][9] vertices (caller vertex order)
+  DBuf<double> cen;        // [N][3]
+  DBuf<double> area;       // [N]
+  DBuf<double> radius;     // [N]
+  DBuf<int32_t> tri;       // [N][3] vertex ids
+  DBuf<int32_t> cidx;      // [N] caller index
+  DBuf<int32_t> perm;      // [N] Morton rank -> caller
+  DBuf<uint64_t> keys;     // [N] per caller panel
+  DBuf<int32_t> leaf_first, leaf_count, leaf_box;   // per leaf
+  DBuf<int32_t> u_ptr32, u_src;                      // U-list (leaf-local)
+  DBuf<int64_t> near_off;                            // per leaf: offset of its value block
+  DBuf<int32_t> near_w;                              // per leaf: block width
+  DBuf<double> near_val;                             // values
+  DBuf<float> near_val32;                            // FP32 copy (mixed precision)
+  DBuf<double> mom;                                  // [N][ncoef] P2M moments (leaf-scaled)
+  DBuf<float> mom32;
+  DBuf<double> t_m2m, t_l2l, t_m2l;                  // translation matrices (transposed)
+  DBuf<float> t_m2m32, t_l2l32, t_m2l32;
+  DBuf<int32_t> box_parent, box_oct, box_child_ptr, box_child;  // tree arrays (global ids)
+  DBuf<int32_t> v_ptr32, v_src;
+  DBuf<int16_t> v_off;
+  DBuf<int32_t> lvl_boxes;                            // per level: global ids of its boxes (same as range)
+  // FMM work buffers (resized to the column count)
+  DBuf<double> X, Y, Mexp, Lexp;
+  DBuf<float> X32, Y32, M32, L32;
+  // operator data
+  DBuf<int32_t> pan_br;      // [N][3] branch ids per Morton panel (-1 none)
+  DBuf<double> pan_rho;      // [N][3][3] signed rho per (panel, slot)
+  DBuf<int32_t> pan_mat;     // [N] material id (-1 terminal)
+  DBuf<int32_t> br_pan;      // [B][2] Morton panel (-1 terminal)
+  DBuf<double> br_rho;       // [B][2][3]
+  DBuf<int32_t> m_ptr, m_col, mt_ptr, mt_col;
+  DBuf<int8_t> m_val, mt_val;
+  DBuf<int32_t> q_ptr, q_col;
+  DBuf<double> q_val;
+  DBuf<double> mat_sigma, mat_thick;
+  // solver work
+  DBuf<double> work;         // generic scratch for the solver
+};
+
+struct Options {
+  xrl_options o;
+};
+
+}  // namespace xrl
+
+struct xrl_ctx {
+  xrl_options opt;
+  std::string err;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  xrl::DevAlloc alloc;
+  // inputs
+  std::vector<double> xyz;
+  std::vector<int32_t> tri, cond;
+  std::vector<double> sigma, thick;
+  std::vector<std::vector<int32_t>> port_src, port_sink;
+  bool have_mesh = false, have_cond = false, ready = false;
+  int N = 0, ncoef = 0, p = 0;
+  xrl::Tree tree;
+  xrl::Topo topo;
+  xrl::Dev d;
+  xrl_stats stats;
+  std::vector<double> gl_nodes;   // host GL tables for the rule table (set in setup)
+};
+
+// ---- translation-unit entry points (internal) --------------------------------------
+namespace xrl {
+// tree.cpp
+void build_tree(xrl_ctx* c, const std::vector<uint64_t>& keys_by_caller);
+uint64_t morton_key(uint32_t ix, uint32_t iy, uint32_t iz);
+void morton_decode(uint64_t key, uint32_t* ix, uint32_t* iy, uint32_t* iz);
+// topology.cpp
+void build_topology(xrl_ctx* c);
+void build_precond_pattern(xrl_ctx* c, const std::vector<double>& p_diag_caller);
+// harmonics.cpp
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
+void build_translations(int p, const std::vector<int32_t>& offsets, std::vector<double>& m2m,
+                        std::vector<double>& l2l, std::vector<double>& m2l);
+// geom.cu
+void launch_geometry(xrl_ctx* c);              // computes panel data + keys (caller order) on device
+void launch_near_fill(xrl_ctx* c);             // near-field blocks (rule table)
+void launch_moments(xrl_ctx* c);               // P2M/L2P moment table
+void launch_direct(xrl_ctx* c, int ncols, const double* x, double* y, cudaStream_t s);
+void upload_rule_tables(xrl_ctx* c);
+// fmm.cu
+void fmm_prepare(xrl_ctx* c);                  // upload tree and operators
+void fmm_apply(xrl_ctx* c, int ncols, const double* X, double* Y, cudaStream_t s);      // Morton [N][nc]
+void fmm_apply32(xrl_ctx* c, int ncols, const float* X, float* Y, cudaStream_t s);
+void launch_to_morton(const xrl_ctx* c, int ncols, const double* x_user, double* X, cudaStream_t s);
+void launch_from_morton(const xrl_ctx* c, int ncols, const double* Y, double* y_user, cudaStream_t s);
+// solve.cu
+void solver_prepare(xrl_ctx* c);
+void run_solve(xrl_ctx* c, int nf, const double* f, double* R, double* L);
+void apply_operator_host(xrl_ctx* c, int nsys, const double* f, const double* v, double* w, bool precond_matrix);
+}  // namespace xrl

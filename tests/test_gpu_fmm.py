@@ -1,0 +1,137 @@
+"""GPU parity of the tree, the direct sum and the FMM product y = P x
+(Sec. II-C) against the CPU oracle, through the C-ABI."""
+import numpy as np
+import pytest
+
+import meshgen
+from oracle import panels, tree
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import os
+
+    import __graft_entry__
+    import paper_2409_12375_gb300 as pkg
+    if not os.path.exists(pkg.library_path()):
+        __graft_entry__.build()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def bar_ctx(lib, bar_mesh):
+    x = lib.XRL.from_mesh(bar_mesh, fmm_order=8)
+    yield x
+    x.close()
+
+
+@pytest.fixture(scope="module")
+def coils_mesh():
+    return meshgen.coils()
+
+
+@pytest.fixture(scope="module")
+def coils_ctx(lib, coils_mesh):
+    x = lib.XRL.from_mesh(coils_mesh, fmm_order=8)
+    yield x
+    x.close()
+
+
+def _check_tree(ctx, mesh):
+    ref = tree.build(mesh.xyz, mesh.tri, leaf_target=ctx.opts.leaf_target, ws=ctx.opts.separation)
+    keys, perm, leaf = ctx.export_tree()
+    assert np.array_equal(keys, ref["keys"])
+    assert np.array_equal(perm, ref["perm"])
+    assert np.array_equal(leaf, ref["leaf_of"])
+    st = ctx.stats()
+    assert st["n_levels"] == ref["L"] + 1
+    for lev in range(2, ref["L"] + 1):
+        bk, vptr, vsrc, uptr, usrc = ctx.export_lists(lev)
+        assert np.array_equal(bk, ref["levels"][lev])
+        for b, lst in enumerate(ref["V"][lev]):
+            assert list(vsrc[vptr[b]:vptr[b + 1]]) == lst
+        if lev == ref["L"]:
+            for b, lst in enumerate(ref["U"]):
+                assert list(usrc[uptr[b]:uptr[b + 1]]) == lst
+
+
+def test_tree_bit_exact_bar(bar_ctx, bar_mesh):
+    _check_tree(bar_ctx, bar_mesh)
+
+
+def test_tree_bit_exact_coils(coils_ctx, coils_mesh):
+    _check_tree(coils_ctx, coils_mesh)
+
+
+def _dev(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), device="cuda:0")
+
+
+def test_direct_sum_matches_dense_oracle(bar_ctx, bar_dense_P):
+    import torch
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((3, bar_dense_P.shape[0]))
+    xd = _dev(x)
+    yd = torch.empty_like(xd)
+    bar_ctx.direct_mvm_device(xd, yd)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    ref = x @ bar_dense_P.T
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-12
+    assert np.max(np.abs(y - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("nc", [1, 6, 13])
+def test_fmm_matches_dense_oracle(bar_ctx, bar_dense_P, nc):
+    import torch
+    rng = np.random.default_rng(nc)
+    x = rng.standard_normal((nc, bar_dense_P.shape[0]))
+    xd = _dev(x)
+    yd = torch.empty_like(xd)
+    bar_ctx.fmm_mvm_device(xd, yd)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    ref = x @ bar_dense_P.T
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert err < 1e-6, err
+
+
+def test_fmm_host_entry_equals_device_entry(bar_ctx):
+    import torch
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((2, bar_ctx.n_tri))
+    yh = bar_ctx.fmm_mvm(x)
+    xd = _dev(x)
+    yd = torch.empty_like(xd)
+    bar_ctx.fmm_mvm_device(xd, yd)
+    torch.cuda.synchronize()
+    assert np.array_equal(yh, yd.cpu().numpy())
+
+
+def test_fmm_zero_and_linearity(bar_ctx):
+    z = bar_ctx.fmm_mvm(np.zeros(bar_ctx.n_tri))
+    assert np.all(z == 0.0)
+    rng = np.random.default_rng(4)
+    a, b = rng.standard_normal((2, bar_ctx.n_tri))
+    y = bar_ctx.fmm_mvm(np.stack([a, b, 2.0 * a - 3.0 * b]))
+    lin = 2.0 * y[0] - 3.0 * y[1]
+    assert np.max(np.abs(y[2] - lin)) < 1e-12 * np.max(np.abs(y[2]))
+
+
+def test_fmm_full_size_coils_sampled_rows(coils_ctx, coils_mesh):
+    """~25k-panel coils at 6 columns (one complex system): sampled rows of
+    the oracle's P times x."""
+    rng = np.random.default_rng(5)
+    N = coils_mesh.n_tri
+    x = rng.standard_normal((6, N))
+    y = coils_ctx.fmm_mvm(x)
+    rows = rng.choice(N, 12, replace=False)
+    G = panels.Geometry(coils_mesh.xyz, coils_mesh.tri)
+    Pr = panels.rows_P(G, rows)
+    ref = x @ Pr.T                       # [6, rows]
+    got = y[:, rows]
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 1e-6, err

@@ -1,0 +1,146 @@
+"""GPU parity of the PEEC topology, the loop-space operator (eq. 8), the
+diagonal-of-P preconditioner matrix (eq. 10) and the port R, L of a sweep
+against the CPU oracle, through the C-ABI."""
+import numpy as np
+import pytest
+
+import meshgen
+from oracle import circuit
+from oracle.esi import zs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import os
+
+    import __graft_entry__
+    import paper_2409_12375_gb300 as pkg
+    if not os.path.exists(pkg.library_path()):
+        __graft_entry__.build()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def bar_ctx(lib, bar_mesh):
+    x = lib.XRL.from_mesh(bar_mesh, fmm_order=8)
+    yield x
+    x.close()
+
+
+@pytest.fixture(scope="module")
+def bar_circ(bar_mesh):
+    return circuit.Circuit(bar_mesh)
+
+
+def _loop_matrix(ctx, nbranch):
+    ptr, col, val = ctx.export_loops()
+    M = np.zeros((ptr.shape[0] - 1, nbranch))
+    for l in range(ptr.shape[0] - 1):
+        M[l, col[ptr[l]:ptr[l + 1]]] = val[ptr[l]:ptr[l + 1]]
+    return M
+
+
+def test_branches_match_oracle(bar_ctx, bar_circ):
+    t, h = bar_ctx.export_branches()
+    c = bar_circ
+    assert t.shape[0] == c.n_branch
+    live = c.live
+    for b in range(c.n_cb):
+        assert live[c.tail[b]] == t[b]
+        if c.head[b] < c.n_live:
+            assert live[c.head[b]] == h[b]
+        else:
+            assert h[b] == -1 - (c.head[b] - c.n_live)
+
+
+def test_loops_are_a_cycle_basis(bar_ctx, bar_circ):
+    M = _loop_matrix(bar_ctx, bar_circ.n_branch)
+    assert M.shape[0] == bar_circ.M.shape[0]
+    assert np.abs(M @ bar_circ.incidence().T).max() == 0.0
+    assert np.linalg.matrix_rank(M) == M.shape[0]
+    st = bar_ctx.stats()
+    assert st["n_vertex_loops"] + st["n_global_loops"] == M.shape[0]
+
+
+def _z_edge(c, f, P_full, diag_only=False):
+    Pl = P_full[np.ix_(c.live, c.live)]
+    if diag_only:
+        Pl = np.diag(np.diag(Pl))
+    d = c.zs_panels(f)
+    core = np.diag(d) + 1j * 2 * np.pi * f * 1e-7 * Pl
+    return sum(c.A[t] @ core @ c.A[t].T for t in range(3))
+
+
+@pytest.mark.parametrize("f", [1e3, 1e9])
+def test_operator_matches_oracle(bar_ctx, bar_circ, bar_dense_P, f):
+    c = bar_circ
+    M = _loop_matrix(bar_ctx, c.n_branch)[:, :c.n_cb]
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal((2, M.shape[0])) + 1j * rng.standard_normal((2, M.shape[0]))
+    w = bar_ctx.apply_operator(np.array([f, f]), v)
+    Ze = _z_edge(c, f, bar_dense_P)
+    ref = (M @ Ze @ M.T @ v.T).T
+    err = np.linalg.norm(w - ref) / np.linalg.norm(ref)
+    assert err < 1e-6, err
+
+
+def test_precond_matrix_matches_oracle(bar_ctx, bar_circ, bar_dense_P):
+    c = bar_circ
+    M = _loop_matrix(bar_ctx, c.n_branch)[:, :c.n_cb]
+    rng = np.random.default_rng(12)
+    v = rng.standard_normal((2, M.shape[0])) + 1j * rng.standard_normal((2, M.shape[0]))
+    f = np.array([1e5, 1e8])
+    w = bar_ctx.apply_operator(f, v, precond_matrix=True)
+    for s in range(2):
+        Qe = _z_edge(c, f[s], bar_dense_P, diag_only=True)
+        ref = M @ Qe @ M.T @ v[s]
+        assert np.linalg.norm(w[s] - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def test_bar_sweep_matches_oracle(bar_ctx, bar_circ, bar_dense_P, bar_mesh):
+    f = bar_mesh.freqs
+    R, L = bar_ctx.solve(f)
+    Ro, Lo, _ = bar_circ.solve(f, bar_dense_P)
+    assert np.max(np.abs(R - Ro) / np.abs(Ro)) < 1e-4
+    assert np.max(np.abs(L - Lo) / np.abs(Lo)) < 1e-4
+    st = bar_ctx.stats()
+    assert st["max_rel_res"] <= 1e-8
+
+
+def test_bar_low_frequency_resistance(bar_ctx):
+    R, L = bar_ctx.solve(np.array([1e-3]))
+    rho_l_a = 10e-3 / (5.8e7 * 1e-6)
+    assert abs(R[0, 0, 0] / rho_l_a - 1) < 1e-4
+
+
+def test_two_bars_sweep(lib, two_bars_mesh, two_bars_dense_P):
+    x = lib.XRL.from_mesh(two_bars_mesh, fmm_order=8)
+    f = np.array([1e4, 1e9])
+    R, L = x.solve(f)
+    c = circuit.Circuit(two_bars_mesh)
+    Ro, Lo, _ = c.solve(f, two_bars_dense_P)
+    assert np.max(np.abs(R - Ro)) < 1e-4 * np.max(np.abs(Ro))
+    assert np.max(np.abs(L - Lo)) < 1e-4 * np.max(np.abs(Lo))
+    assert np.max(np.abs(L - np.transpose(L, (0, 2, 1)))) < 1e-6 * np.max(np.abs(L))
+    x.close()
+
+
+def test_error_codes(lib):
+    from paper_2409_12375_gb300.xrl import XRLError
+    m = meshgen.bar(length=2e-3, n_w=2, n_h=2, n_l=6)
+    x = lib.XRL()
+    with pytest.raises(XRLError) as e:
+        x.solve(np.array([1e6]))
+    assert e.value.code == 7           # XRL_ESTATE
+    # open surface: drop one triangle
+    x.set_mesh(m.xyz, m.tri[1:], m.cond[1:])
+    with pytest.raises(XRLError) as e:
+        x.setup()
+    assert e.value.code == 2           # XRL_ETOPO
+    x.set_mesh(m.xyz, m.tri, m.cond)
+    with pytest.raises(XRLError) as e:
+        x.add_port(np.array([0, 10 ** 6]), np.array([1]))
+    assert e.value.code == 1           # XRL_EINVAL
+    x.close()
