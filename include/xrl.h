@@ -54,7 +54,10 @@ typedef struct {
                           (the depth is also capped so that leaf sides are >= 2x the largest
                           panel radius) */
   int32_t precision;   /* 0: FP64 everywhere; 1: mixed (FP32 FMM/near field inside FP64 refinement) */
-  int32_t precond;     /* 0: none; 1: diagonal-of-P preconditioner of eq. 10 (inner COCG solve) */
+  int32_t precond;     /* 0: none; 1: diagonal-of-P preconditioner of eq. 10 applied exactly (banded
+                          LDL^T of the RCM-ordered vertex loops + Schur border; falls back to 2 when
+                          the band is wider than 63 or there are more than 16 global loops);
+                          2: eq. 10 applied inexactly by Jacobi-preconditioned COCG */
   int32_t restart;     /* FGMRES restart length m, default 50 (Sec. III uses restart 50) */
   int32_t max_iters;   /* total outer iterations per solve, default 500 */
   int32_t inner_iters; /* max inner COCG iterations per preconditioner apply, default 60 */
@@ -160,6 +163,12 @@ xrl_status xrl_apply_operator(xrl_ctx* ctx, int32_t n_sys, const double* freq, c
 xrl_status xrl_apply_precond_matrix(xrl_ctx* ctx, int32_t n_sys, const double* freq,
                                     const double* v, double* w);
 
+/* Preconditioner solve for parity checks: w_s = Q(f_s)^-1 v_s by the banded
+ * LDL^T + Schur border factorisation (XRL_EINVAL if the band form is not
+ * usable for this mesh); layout as xrl_apply_operator. */
+xrl_status xrl_apply_precond_inverse(xrl_ctx* ctx, int32_t n_sys, const double* freq, const double* v,
+                                     double* w);
+
 /* Export of setup products for checks (host buffers sized from xrl_get_stats):
  *  tree:   keys [n_panels] Morton keys (caller order), perm [n_panels] Morton
  *          rank -> caller index, leaf_of [n_panels] leaf index per Morton rank;
@@ -180,6 +189,24 @@ xrl_status xrl_export_loops(const xrl_ctx* ctx, int64_t* row_ptr, int32_t* col, 
  * query (pass NULL arrays). */
 xrl_status xrl_export_lists(const xrl_ctx* ctx, int32_t level, int32_t* n_boxes, uint64_t* box_keys,
                             int64_t* v_ptr, int32_t* v_src, int64_t* u_ptr, int32_t* u_src);
+
+/* Per-phase device timing, recorded with CUDA events on the stream each
+ * phase's kernels run on, while profiling is switched on (xrl_set_profiling).
+ * phase: 0 P2P near field, 1 P2M, 2 M2M, 3 M2L, 4 L2L, 5 L2P, 6 operator
+ * gather/scatter, 7 preconditioner (inner COCG), 8 Arnoldi/FGMRES updates.
+ * ms = summed event time, launches = kernel launches, flops / bytes =
+ * algorithmic work (not counters) summed over those launches.  Reading
+ * synchronises the context's stream.  xrl_kernel_launches returns every
+ * kernel launch of the library on this context since creation. */
+xrl_status xrl_set_profiling(xrl_ctx* ctx, int32_t on);
+xrl_status xrl_get_profile(xrl_ctx* ctx, int32_t phase, double* ms, int64_t* launches, double* flops,
+                           double* bytes);
+xrl_status xrl_reset_profile(xrl_ctx* ctx);
+int64_t xrl_kernel_launches(const xrl_ctx* ctx);
+
+/* The cudaStream_t (as void*) on which the context enqueues its own work
+ * (setup, xrl_fmm_mvm, xrl_solve); NULL for a NULL context. */
+void* xrl_get_stream(const xrl_ctx* ctx);
 
 /* Last error message of this context ("" if none).  Valid until the next call. */
 const char* xrl_last_error(const xrl_ctx* ctx);

@@ -48,7 +48,78 @@ double self_term_host(const double* a, const double* b, const double* c) {
 
 }  // namespace
 
+namespace xrl {
+
+cudaEvent_t prof_begin(xrl_ctx* c, cudaStream_t s) {
+  if (!c->prof.on) return nullptr;
+  cudaEvent_t a;
+  XRL_CUDA(cudaEventCreate(&a));
+  XRL_CUDA(cudaEventRecord(a, s));
+  return a;
+}
+
+void prof_end(xrl_ctx* c, cudaStream_t s, cudaEvent_t a, int phase, int launches, double flops, double bytes) {
+  count_launch(c, launches);
+  if (!c->prof.on || !a) return;
+  cudaEvent_t b;
+  XRL_CUDA(cudaEventCreate(&b));
+  XRL_CUDA(cudaEventRecord(b, s));
+  c->prof.pending.push_back({a, b, phase});
+  c->prof.launches[phase] += launches;
+  c->prof.flops[phase] += flops;
+  c->prof.bytes[phase] += bytes;
+}
+
+static void prof_collect(xrl_ctx* c) {
+  for (auto& r : c->prof.pending) {
+    XRL_CUDA(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    XRL_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    c->prof.ms[r.phase] += ms;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  c->prof.pending.clear();
+}
+
+}  // namespace xrl
+
 extern "C" {
+
+xrl_status xrl_set_profiling(xrl_ctx* c, int32_t on) {
+  if (!c) return XRL_EINVAL;
+  c->prof.on = on != 0;
+  return XRL_OK;
+}
+
+xrl_status xrl_get_profile(xrl_ctx* c, int32_t phase, double* ms, int64_t* launches, double* flops,
+                           double* bytes) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(phase >= 0 && phase < PH_COUNT, XRL_EINVAL, "bad phase");
+    prof_collect(c);
+    if (ms) *ms = c->prof.ms[phase];
+    if (launches) *launches = c->prof.launches[phase];
+    if (flops) *flops = c->prof.flops[phase];
+    if (bytes) *bytes = c->prof.bytes[phase];
+  });
+}
+
+xrl_status xrl_reset_profile(xrl_ctx* c) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    prof_collect(c);
+    for (int i = 0; i < PH_COUNT; ++i) {
+      c->prof.ms[i] = c->prof.flops[i] = c->prof.bytes[i] = 0.0;
+      c->prof.launches[i] = 0;
+    }
+  });
+}
+
+int64_t xrl_kernel_launches(const xrl_ctx* c) { return c ? c->prof.total_launches : 0; }
+
+void* xrl_get_stream(const xrl_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
 
 void xrl_default_options(xrl_options* o) {
   if (!o) return;
@@ -183,7 +254,9 @@ xrl_status xrl_setup(xrl_ctx* c) {
       pdiag[p] = self_term_host(v0, v1, v2);
     }
     build_precond_pattern(c, pdiag);
+    build_band(c);
     solver_prepare(c);
+    band_prepare(c);
     XRL_CUDA(cudaStreamSynchronize(c->stream));
     const Topo& T = c->topo;
     c->stats.n_panels = c->N;
@@ -288,7 +361,7 @@ xrl_status xrl_apply_operator(xrl_ctx* c, int32_t nsys, const double* freq, cons
   return guarded(c, [&] {
     XRL_CHECK(c->ready, XRL_ESTATE, "call xrl_setup first");
     XRL_CHECK(nsys > 0 && freq && v && w, XRL_EINVAL, "bad arguments");
-    apply_operator_host(c, nsys, freq, v, w, false);
+    apply_operator_host(c, nsys, freq, v, w, 0);
   });
 }
 
@@ -297,7 +370,17 @@ xrl_status xrl_apply_precond_matrix(xrl_ctx* c, int32_t nsys, const double* freq
   return guarded(c, [&] {
     XRL_CHECK(c->ready, XRL_ESTATE, "call xrl_setup first");
     XRL_CHECK(nsys > 0 && freq && v && w, XRL_EINVAL, "bad arguments");
-    apply_operator_host(c, nsys, freq, v, w, true);
+    apply_operator_host(c, nsys, freq, v, w, 1);
+  });
+}
+
+xrl_status xrl_apply_precond_inverse(xrl_ctx* c, int32_t nsys, const double* freq, const double* v, double* w) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(c->ready, XRL_ESTATE, "call xrl_setup first");
+    XRL_CHECK(nsys > 0 && freq && v && w, XRL_EINVAL, "bad arguments");
+    XRL_CHECK(band_usable(c), XRL_EINVAL, "the banded form of Q is not usable for this mesh");
+    apply_operator_host(c, nsys, freq, v, w, 2);
   });
 }
 
@@ -363,6 +446,10 @@ void xrl_destroy(xrl_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  try {
+    prof_collect(c);
+  } catch (...) {
+  }
   c->d = Dev();
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -15,6 +15,7 @@
 // Operators are real (p+1)^2 square matrices stored transposed ([in][out]).
 // The template parameter T selects FP64 (the plain path) or FP32 (mixed
 // precision, used inside the FP64 refinement loop).
+#include <algorithm>
 #include <vector>
 
 #include "xrl_internal.hpp"
@@ -40,11 +41,13 @@ __global__ void k_from_morton(int N, int nc, const int32_t* __restrict__ perm, c
 
 void launch_to_morton(const xrl_ctx* c, int nc, const double* x, double* X, cudaStream_t s) {
   size_t n = (size_t)c->N * nc;
+  count_launch(const_cast<xrl_ctx*>(c));
   k_to_morton<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->N, nc, c->d.perm.p, x, X);
 }
 
 void launch_from_morton(const xrl_ctx* c, int nc, const double* Y, double* y, cudaStream_t s) {
   size_t n = (size_t)c->N * nc;
+  count_launch(const_cast<xrl_ctx*>(c));
   k_from_morton<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->N, nc, c->d.perm.p, Y, y);
 }
 
@@ -258,34 +261,58 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   const int nl = t.n_leaves();
   const int L = t.L;
   const double h = t.side / (double)(1 << L);
+  const double sz = sizeof(T);
+  const double N = c->N;
+  const double nne = (double)c->stats.near_nnz;
+  const double e2 = 2.0 * ncoef * ncoef * (double)nc;       // flops of one translation (all columns)
+  const double ebytes = (double)ncoef * nc * sz;            // one expansion (all columns)
   // column tiles: p2p uses ct columns per block; expansion kernels ncoef*ct threads
   const int ct_p = nc < 8 ? nc : 8;
   const int ct_e = nc < 4 ? nc : 4;
   dim3 gp(nl, (nc + ct_p - 1) / ct_p);
+  cudaEvent_t ev = prof_begin(c, s);
   k_p2p<T><<<gp, 128, 0, s>>>(nc, ct_p, c->d.leaf_first.p, c->d.leaf_count.p, c->d.u_ptr32.p, c->d.u_src.p,
                               c->d.near_off.p, c->d.near_w.p, near, X, Y);
+  prof_end(c, s, ev, PH_P2P, 1, 2.0 * nne * nc, nne * sz + 2.0 * N * nc * sz);
   const int ecols = (nc + ct_e - 1) / ct_e;
   const int leaf0 = t.level_off[L];
+  ev = prof_begin(c, s);
   k_p2m<T><<<dim3(nl, ecols), 256, 0, s>>>(nc, ct_e, ncoef, leaf0, c->d.leaf_first.p, c->d.leaf_count.p, mom, X,
                                            Mx);
+  prof_end(c, s, ev, PH_P2M, 1, 2.0 * N * ncoef * nc, N * ncoef * sz + N * nc * sz + nl * ebytes);
+  ev = prof_begin(c, s);
   for (int l = L - 1; l >= 2; --l) {
     int nbx = t.level_off[l + 1] - t.level_off[l];
     k_m2m<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, t.level_off[l], c->d.box_child_ptr.p,
                                               c->d.box_oct.p, tm2m, Mx);
   }
   {
+    double nch = (double)(t.level_off[L + 1] - t.level_off[std::min(3, L + 1)]);
+    double npar = (double)(t.level_off[L] - t.level_off[2]);
+    prof_end(c, s, ev, PH_M2M, std::max(0, L - 2), e2 * nch, (nch + npar) * ebytes);
+  }
+  {
     int b0 = t.level_off[2];
     int nbx = t.level_off[L + 1] - b0;
+    ev = prof_begin(c, s);
     k_m2l<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, b0, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p,
                                               tm2l, Mx, Lx);
+    prof_end(c, s, ev, PH_M2L, 1, e2 * (double)t.v_src.size(), 2.0 * nbx * ebytes);
   }
+  ev = prof_begin(c, s);
   for (int l = 3; l <= L; ++l) {
     int nbx = t.level_off[l + 1] - t.level_off[l];
     k_l2l<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, t.level_off[l], c->d.box_parent.p,
                                               c->d.box_oct.p, tl2l, Lx);
   }
+  {
+    double nch = (double)(t.level_off[L + 1] - t.level_off[std::min(3, L + 1)]);
+    prof_end(c, s, ev, PH_L2L, std::max(0, L - 2), e2 * nch, 2.0 * nch * ebytes);
+  }
+  ev = prof_begin(c, s);
   k_l2p<T><<<dim3(nl, ecols), 128, 0, s>>>(nc, ct_e, ncoef, leaf0, (T)(1.0 / h), c->d.leaf_first.p,
                                            c->d.leaf_count.p, mom, Lx, Y);
+  prof_end(c, s, ev, PH_L2P, 1, 2.0 * N * ncoef * nc, N * ncoef * sz + 2.0 * N * nc * sz + nl * ebytes);
   XRL_CUDA(cudaGetLastError());
 }
 

@@ -26,21 +26,10 @@
 #include <cmath>
 #include <vector>
 
+#include "cplx.cuh"
 #include "xrl_internal.hpp"
 
 namespace xrl {
-
-typedef double2 cplx;
-__device__ __forceinline__ cplx cm(cplx a, cplx b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ cplx csub(cplx a, cplx b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ cplx cconj(cplx a) { return make_double2(a.x, -a.y); }
-__device__ __forceinline__ cplx cscale(cplx a, double s) { return make_double2(a.x * s, a.y * s); }
-__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
-  double d = b.x * b.x + b.y * b.y;
-  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
-}
-__device__ __forceinline__ double cabs2(cplx a) { return a.x * a.x + a.y * a.y; }
 
 constexpr double kMu0Over4Pi = 1e-7;
 
@@ -506,8 +495,11 @@ static unsigned nblk(size_t n, int bs = 256) { return (unsigned)((n + bs - 1) / 
 
 // Work arrays of one solve (device)
 struct Work {
-  DBuf<double> freq, wp;
-  DBuf<cplx> zs, b, x, w, tmp, V, Z, H, h1, h2, cs, sn, g, y, Vb, dinv;
+  DBuf<double> freq, wp, wpf;
+  DBuf<cplx> zs, zsf, fac, Wb, Sinv, bscr;
+  int nport = 1;
+  bool banded = false;
+  DBuf<cplx> b, x, w, tmp, V, Z, H, h1, h2, cs, sn, g, y, Vb, dinv;
   DBuf<cplx> cz, cr, cp, cq, crho;
   DBuf<double> X, Y, bnorm, resid, cvn;
   DBuf<int> active, iters, kcols, clive;
@@ -515,12 +507,19 @@ struct Work {
 
 static void sys_consts(xrl_ctx* c, Work& wk, int nsys, int nport, int nf, const double* freq) {
   const Topo& T = c->topo;
+  wk.nport = nport;
   wk.freq.upload(c->alloc, std::vector<double>(freq, freq + nf));
   wk.zs.alloc(c->alloc, (size_t)nsys * T.n_mat);
   wk.wp.alloc(c->alloc, nsys);
   k_sys_consts<<<nblk((size_t)nsys * T.n_mat), 256, 0, c->stream>>>(nsys, nport, T.n_mat, wk.freq.p,
                                                                     c->d.mat_sigma.p, c->d.mat_thick.p, wk.zs.p,
                                                                     wk.wp.p);
+  // per-frequency copies (one "system" per frequency) for the preconditioner factors
+  wk.zsf.alloc(c->alloc, (size_t)nf * T.n_mat);
+  wk.wpf.alloc(c->alloc, nf);
+  k_sys_consts<<<nblk((size_t)nf * T.n_mat), 256, 0, c->stream>>>(nf, 1, T.n_mat, wk.freq.p, c->d.mat_sigma.p,
+                                                                  c->d.mat_thick.p, wk.zsf.p, wk.wpf.p);
+  count_launch(c, 2);
 }
 
 // w = Z(f_s) v_s for all systems (eq. 8), FMM in FP64
@@ -532,24 +531,34 @@ static void apply_A(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w) {
   wk.X.ensure(c->alloc, (size_t)N * nc);
   wk.Y.ensure(c->alloc, (size_t)N * nc);
   wk.Vb.ensure(c->alloc, (size_t)nsys * T.n_cb);
+  cudaEvent_t ev = prof_begin(c, s);
   k_gather<<<nblk((size_t)N * nsys), 256, 0, s>>>(N, nsys, T.n_loops, c->d.pan_br.p, c->d.pan_rho.p, c->d.mt_ptr.p,
                                                  c->d.mt_col.p, c->d.mt_val.p, v, wk.X.p);
+  const double nnzm = (double)T.m_col.size();
+  prof_end(c, s, ev, PH_OPER, 1, 8.0 * nnzm * nsys + 18.0 * N * nsys, nsys * (16.0 * nnzm + 48.0 * N));
   fmm_apply(c, nc, wk.X.p, wk.Y.p, s);
+  ev = prof_begin(c, s);
   // conductor branches only; the external port branches carry no impedance
   k_scatter<<<nblk((size_t)T.n_cb * nsys), 256, 0, s>>>(T.n_cb, nsys, T.n_mat, c->d.br_pan.p, c->d.br_rho.p,
                                                         c->d.pan_mat.p, c->d.area.p, wk.zs.p, wk.wp.p, wk.X.p,
                                                         wk.Y.p, wk.Vb.p);
   k_loop_reduce<<<nblk((size_t)T.n_loops * nsys), 256, 0, s>>>(T.n_loops, nsys, T.n_cb, T.n_cb, c->d.m_ptr.p,
                                                                c->d.m_col.p, c->d.m_val.p, wk.Vb.p, w);
+  prof_end(c, s, ev, PH_OPER, 2, nsys * (2.0 * T.n_cb * 30.0 + 2.0 * nnzm),
+           nsys * (T.n_cb * (2.0 * 96.0 + 16.0) + 16.0 * nnzm + 16.0 * T.n_loops));
   XRL_CUDA(cudaGetLastError());
   c->stats.n_mvm++;
 }
 
 static void apply_Qmat(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, int mode) {
   const Topo& T = c->topo;
+  cudaEvent_t ev = prof_begin(c, c->stream);
   k_qspmv<<<nblk((size_t)T.n_loops * nsys), 256, 0, c->stream>>>(T.n_loops, nsys, T.n_mat, c->d.q_ptr.p,
                                                                   c->d.q_col.p, c->d.q_val.p, wk.zs.p, wk.wp.p, v,
                                                                   w, mode);
+  const double nnzq = (double)T.q_col.size();
+  prof_end(c, c->stream, ev, PH_PREC, 1, nsys * nnzq * (8.0 + 4.0 * T.n_mat),
+           nnzq * (4.0 + 8.0 * (T.n_mat + 1)) + nsys * 32.0 * T.n_loops);
   XRL_CUDA(cudaGetLastError());
 }
 
@@ -561,6 +570,11 @@ static void apply_Qinv(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* z) {
     XRL_CUDA(cudaMemcpyAsync(z, v, sizeof(cplx) * (size_t)n * nsys, cudaMemcpyDeviceToDevice, s));
     return;
   }
+  if (wk.banded) {
+    band_apply(c, nsys, wk.nport, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.Wb.p, wk.Sinv.p, v, z, wk.bscr.p,
+               wk.active.p, s);
+    return;
+  }
   const size_t tot = (size_t)n * nsys;
   wk.cr.ensure(c->alloc, tot);
   wk.cp.ensure(c->alloc, tot);
@@ -568,12 +582,16 @@ static void apply_Qinv(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* z) {
   wk.crho.ensure(c->alloc, nsys);
   wk.cvn.ensure(c->alloc, nsys);
   wk.clive.ensure(c->alloc, nsys);
+  cudaEvent_t ev = prof_begin(c, s);
   k_cocg_init<<<nsys, 256, 0, s>>>(n, nsys, v, wk.dinv.p, z, wk.cr.p, wk.cp.p, wk.crho.p, wk.cvn.p, wk.clive.p);
+  prof_end(c, s, ev, PH_PREC, 1, 16.0 * tot, 80.0 * tot);
   const double tol2 = c->opt.inner_tol * c->opt.inner_tol;
   for (int it = 0; it < c->opt.inner_iters; ++it) {
     apply_Qmat(c, wk, nsys, wk.cp.p, wk.cq.p, 0);
+    ev = prof_begin(c, s);
     k_cocg_step<<<nsys, 256, 0, s>>>(n, nsys, wk.cq.p, wk.dinv.p, z, wk.cr.p, wk.cp.p, wk.crho.p, wk.cvn.p,
                                      wk.clive.p, tol2);
+    prof_end(c, s, ev, PH_PREC, 1, 40.0 * tot, 16.0 * 9.0 * tot);
   }
   XRL_CUDA(cudaGetLastError());
   c->stats.total_inner += c->opt.inner_iters;
@@ -621,12 +639,22 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
   wk.active.alloc(c->alloc, nsys);
   wk.iters.alloc(c->alloc, nsys);
   wk.kcols.alloc(c->alloc, nsys);
-  if (c->opt.precond) {
+  wk.banded = c->opt.precond == 1 && band_usable(c);
+  if (wk.banded) {
+    const Topo& TT = c->topo;
+    wk.fac.alloc(c->alloc, (size_t)nf * TT.n_band * (TT.band + 1));
+    wk.Wb.alloc(c->alloc, (size_t)nf * std::max(1, TT.n_border) * TT.n_band);
+    wk.Sinv.alloc(c->alloc, (size_t)nf * std::max(1, TT.n_border * TT.n_border));
+    wk.bscr.alloc(c->alloc, (size_t)nsys * TT.n_band);
+    band_factor(c, nf, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.Wb.p, wk.Sinv.p, s);
+  } else if (c->opt.precond) {
     wk.dinv.alloc(c->alloc, tot);
     apply_Qmat(c, wk, nsys, nullptr, wk.w.p, 1);
     k_inv<<<nblk(tot), 256, 0, s>>>(tot, wk.w.p, wk.dinv.p);
+    count_launch(c);
   }
   k_rhs<<<nblk(tot), 256, 0, s>>>(n, nsys, np, dpl.p, dps.p, wk.b.p);
+  count_launch(c, 2);
   XRL_CUDA(cudaMemsetAsync(wk.x.p, 0, sizeof(cplx) * tot, s));
   XRL_CUDA(cudaMemsetAsync(wk.iters.p, 0, sizeof(int) * nsys, s));
   k_bnorm<<<nsys, 256, 0, s>>>(n, nsys, wk.b.p, wk.bnorm.p);
@@ -642,6 +670,7 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
     if (!first) apply_A(c, wk, nsys, wk.x.p, wk.w.p);
     k_restart<<<nsys, 256, 0, s>>>(n, nsys, m, wk.b.p, first ? nullptr : wk.w.p, wk.V.p, wk.g.p, wk.bnorm.p, tol,
                                    wk.active.p, wk.resid.p);
+    count_launch(c);
     first = false;
     XRL_CUDA(cudaMemcpyAsync(hact.data(), wk.active.p, sizeof(int) * nsys, cudaMemcpyDeviceToHost, s));
     XRL_CUDA(cudaStreamSynchronize(s));
@@ -658,6 +687,7 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
       apply_Qinv(c, wk, nsys, vj, zj);
       apply_A(c, wk, nsys, zj, wk.w.p);
       // CGS2
+      cudaEvent_t evk = prof_begin(c, s);
       k_arnoldi_dots<<<dim3(j + 1, nsys), 256, 0, s>>>(n, nsys, j, m + 1, wk.V.p, wk.w.p, wk.h1.p, wk.active.p);
       k_arnoldi_sub<<<nblk(tot), 256, 0, s>>>(n, nsys, j, m + 1, wk.V.p, wk.h1.p, wk.w.p, wk.active.p);
       k_arnoldi_dots<<<dim3(j + 1, nsys), 256, 0, s>>>(n, nsys, j, m + 1, wk.V.p, wk.w.p, wk.h2.p, wk.active.p);
@@ -668,6 +698,8 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
       k_arnoldi_norm<<<nsys, 256, 0, s>>>(n, nsys, j, m, wk.H.p, wk.h1.p, wk.h2.p, wk.w.p,
                                           wk.V.p + (size_t)(j + 1) * tot, wk.cs.p, wk.sn.p, wk.g.p, wk.active.p,
                                           wk.bnorm.p, tol, wk.resid.p, wk.iters.p);
+      prof_end(c, s, evk, PH_KRYLOV, 5, 4.0 * 8.0 * (j + 1) * tot + 10.0 * tot,
+               16.0 * (4.0 * (j + 1) * tot + 4.0 * tot));
       XRL_CUDA(cudaGetLastError());
       XRL_CUDA(cudaMemcpyAsync(hact.data(), wk.active.p, sizeof(int) * nsys, cudaMemcpyDeviceToHost, s));
       XRL_CUDA(cudaStreamSynchronize(s));
@@ -680,8 +712,10 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
       }
     }
     XRL_CUDA(cudaMemcpyAsync(wk.kcols.p, hk.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
+    cudaEvent_t evu = prof_begin(c, s);
     k_trisolve<<<nblk(nsys, 64), 64, 0, s>>>(nsys, m, wk.kcols.p, wk.H.p, wk.g.p, wk.y.p);
     k_update_x<<<nblk(tot), 256, 0, s>>>(n, nsys, m, wk.kcols.p, wk.Z.p, wk.y.p, wk.x.p);
+    prof_end(c, s, evu, PH_KRYLOV, 2, 8.0 * j * tot, 16.0 * (j + 2) * tot);
     XRL_CUDA(cudaGetLastError());
     if (total >= c->opt.max_iters) {
       // final true residual for the stats
@@ -696,6 +730,7 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
   dR.alloc(c->alloc, (size_t)nf * np * np);
   dL.alloc(c->alloc, (size_t)nf * np * np);
   k_ports<<<nblk(nf, 64), 64, 0, s>>>(nf, np, n, wk.freq.p, dpl.p, dps.p, wk.x.p, dR.p, dL.p);
+  count_launch(c);
   XRL_CUDA(cudaGetLastError());
   std::vector<double> hres(nsys);
   XRL_CUDA(cudaMemcpyAsync(hres.data(), wk.resid.p, sizeof(double) * nsys, cudaMemcpyDeviceToHost, s));
@@ -714,7 +749,8 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
   XRL_CHECK(mr <= tol * 1.0000001, XRL_ENOCONV, "FGMRES did not reach the tolerance in max_iters");
 }
 
-void apply_operator_host(xrl_ctx* c, int nsys, const double* freq, const double* v, double* w, bool qmat) {
+// mode 0: w = Z(f) v (eq. 8); 1: w = Q(f) v (eq. 10); 2: w = Q(f)^-1 v (banded factors)
+void apply_operator_host(xrl_ctx* c, int nsys, const double* freq, const double* v, double* w, int mode) {
   const Topo& T = c->topo;
   const size_t tot = (size_t)T.n_loops * nsys;
   Work wk;
@@ -724,10 +760,20 @@ void apply_operator_host(xrl_ctx* c, int nsys, const double* freq, const double*
   dv.alloc(c->alloc, tot);
   dw.alloc(c->alloc, tot);
   XRL_CUDA(cudaMemcpyAsync(dv.p, v, sizeof(cplx) * tot, cudaMemcpyHostToDevice, c->stream));
-  if (qmat)
+  if (mode == 1) {
     apply_Qmat(c, wk, nsys, dv.p, dw.p, 0);
-  else
+  } else if (mode == 2) {
+    const Topo& TT = c->topo;
+    wk.fac.alloc(c->alloc, (size_t)nsys * TT.n_band * (TT.band + 1));
+    wk.Wb.alloc(c->alloc, (size_t)nsys * std::max(1, TT.n_border) * TT.n_band);
+    wk.Sinv.alloc(c->alloc, (size_t)nsys * std::max(1, TT.n_border * TT.n_border));
+    wk.bscr.alloc(c->alloc, (size_t)nsys * TT.n_band);
+    band_factor(c, nsys, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.Wb.p, wk.Sinv.p, c->stream);
+    band_apply(c, nsys, 1, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.Wb.p, wk.Sinv.p, dv.p, dw.p, wk.bscr.p, nullptr,
+               c->stream);
+  } else {
     apply_A(c, wk, nsys, dv.p, dw.p);
+  }
   XRL_CUDA(cudaMemcpyAsync(w, dw.p, sizeof(cplx) * tot, cudaMemcpyDeviceToHost, c->stream));
   XRL_CUDA(cudaStreamSynchronize(c->stream));
 }

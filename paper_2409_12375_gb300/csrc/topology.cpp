@@ -457,3 +457,107 @@ void build_precond_pattern(xrl_ctx* c, const std::vector<double>& pdiag) {
 }
 
 }  // namespace xrl
+
+namespace xrl {
+
+// Reverse Cuthill-McKee order of the vertex-loop block of Q (the paper
+// applies Q^-1 with a sparse LU, Sec. II-D; a vertex loop couples only to
+// the loops of neighbouring vertices, so after RCM the block is banded),
+// then the band and border values of every pencil member.
+void build_band(xrl_ctx* c) {
+  Topo& T = c->topo;
+  const int nv = T.n_vertex_loops;
+  const int ng = T.n_loops - nv;
+  const int W = T.n_mat + 1;
+  T.n_band = nv;
+  T.n_border = ng;
+  // adjacency among vertex loops
+  std::vector<std::vector<int>> adj(nv);
+  for (int r = 0; r < nv; ++r)
+    for (int64_t k = T.q_ptr[r]; k < T.q_ptr[r + 1]; ++k) {
+      int cidx = T.q_col[k];
+      if (cidx != r && cidx < nv) adj[r].push_back(cidx);
+    }
+  for (auto& a : adj) std::sort(a.begin(), a.end());
+  std::vector<int> order;
+  order.reserve(nv);
+  std::vector<char> seen(nv, 0);
+  std::vector<int> deg(nv);
+  for (int i = 0; i < nv; ++i) deg[i] = (int)adj[i].size();
+  auto bfs_last = [&](int s, std::vector<int>& lvl) {
+    lvl.assign(nv, -1);
+    std::deque<int> dq{s};
+    lvl[s] = 0;
+    int last = s;
+    while (!dq.empty()) {
+      int u = dq.front();
+      dq.pop_front();
+      last = u;
+      for (int v : adj[u])
+        if (lvl[v] < 0) {
+          lvl[v] = lvl[u] + 1;
+          dq.push_back(v);
+        }
+    }
+    return last;
+  };
+  std::vector<int> lvl;
+  for (int start = 0; start < nv; ++start) {
+    if (seen[start]) continue;
+    // pseudo-peripheral node of this component: a few BFS sweeps from the minimum degree node
+    int s = start;
+    {
+      std::vector<int> l0;
+      bfs_last(start, l0);
+      for (int i = 0; i < nv; ++i)
+        if (l0[i] >= 0 && deg[i] < deg[s]) s = i;
+      for (int it = 0; it < 3; ++it) s = bfs_last(s, lvl);
+    }
+    std::deque<int> dq{s};
+    seen[s] = 1;
+    while (!dq.empty()) {
+      int u = dq.front();
+      dq.pop_front();
+      order.push_back(u);
+      std::vector<int> nb;
+      for (int v : adj[u])
+        if (!seen[v]) {
+          seen[v] = 1;
+          nb.push_back(v);
+        }
+      std::sort(nb.begin(), nb.end(), [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; });
+      for (int v : nb) dq.push_back(v);
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  T.band_perm = order;
+  std::vector<int> pos(nv);
+  for (int i = 0; i < nv; ++i) pos[order[i]] = i;
+  int b = 0;
+  for (int r = 0; r < nv; ++r)
+    for (int64_t k = T.q_ptr[r]; k < T.q_ptr[r + 1]; ++k) {
+      int cidx = T.q_col[k];
+      if (cidx < nv) b = std::max(b, std::abs(pos[r] - pos[cidx]));
+    }
+  T.band = b;
+  T.band_val.assign((size_t)W * nv * (b + 1), 0.0);
+  T.border_vg.assign((size_t)W * nv * ng, 0.0);
+  T.border_gg.assign((size_t)W * ng * ng, 0.0);
+  for (int r = 0; r < T.n_loops; ++r)
+    for (int64_t k = T.q_ptr[r]; k < T.q_ptr[r + 1]; ++k) {
+      int cidx = T.q_col[k];
+      for (int w = 0; w < W; ++w) {
+        double v = T.q_val[(size_t)k * W + w];
+        if (r < nv && cidx < nv) {
+          int i = pos[r], j = pos[cidx];
+          if (j <= i) T.band_val[((size_t)w * nv + i) * (b + 1) + (j - i + b)] = v;
+        } else if (r < nv && cidx >= nv) {
+          T.border_vg[((size_t)w * nv + pos[r]) * ng + (cidx - nv)] = v;
+        } else if (r >= nv && cidx >= nv) {
+          T.border_gg[((size_t)w * ng + (r - nv)) * ng + (cidx - nv)] = v;
+        }
+      }
+    }
+}
+
+}  // namespace xrl

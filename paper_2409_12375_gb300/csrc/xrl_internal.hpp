@@ -147,6 +147,14 @@ struct Topo {
   std::vector<int64_t> q_ptr;
   std::vector<int32_t> q_col;
   std::vector<double> q_val;                    // [nnz][n_mat + 1], last = P part
+  // banded direct form of Q (exact preconditioner): vertex loops in reverse
+  // Cuthill-McKee order form a band of half-width `band`; the global loops
+  // (homology and ports, numbered last) form a dense border.
+  int n_band = 0, band = 0, n_border = 0;
+  std::vector<int32_t> band_perm;               // band position -> loop index
+  std::vector<double> band_val;                 // [(n_mat+1)][n_band][band+1], column j = i - band + k
+  std::vector<double> border_vg;                // [(n_mat+1)][n_band][n_border]
+  std::vector<double> border_gg;                // [(n_mat+1)][n_border][n_border]
 };
 
 // ---- device-resident state ------------------------------------------------------
@@ -188,12 +196,24 @@ struct Dev {
   DBuf<int32_t> q_ptr, q_col;
   DBuf<double> q_val;
   DBuf<double> mat_sigma, mat_thick;
+  DBuf<int32_t> band_perm;
+  DBuf<double> band_val, border_vg, border_gg;
   // solver work
   DBuf<double> work;         // generic scratch for the solver
 };
 
-struct Options {
-  xrl_options o;
+// Phase profiler: CUDA event pairs on the launching stream plus algorithmic work.
+enum Phase { PH_P2P = 0, PH_P2M, PH_M2M, PH_M2L, PH_L2L, PH_L2P, PH_OPER, PH_PREC, PH_KRYLOV, PH_COUNT };
+struct Prof {
+  bool on = false;
+  struct Rec {
+    cudaEvent_t a, b;
+    int phase;
+  };
+  std::vector<Rec> pending;
+  double ms[PH_COUNT] = {0}, flops[PH_COUNT] = {0}, bytes[PH_COUNT] = {0};
+  int64_t launches[PH_COUNT] = {0};
+  int64_t total_launches = 0;
 };
 
 }  // namespace xrl
@@ -215,11 +235,16 @@ struct xrl_ctx {
   xrl::Topo topo;
   xrl::Dev d;
   xrl_stats stats;
+  xrl::Prof prof;
   std::vector<double> gl_nodes;   // host GL tables for the rule table (set in setup)
 };
 
 // ---- translation-unit entry points (internal) --------------------------------------
 namespace xrl {
+// profiling helpers (api.cu): begin returns an event recorded on s (or null)
+cudaEvent_t prof_begin(xrl_ctx* c, cudaStream_t s);
+void prof_end(xrl_ctx* c, cudaStream_t s, cudaEvent_t a, int phase, int launches, double flops, double bytes);
+inline void count_launch(xrl_ctx* c, int n = 1) { c->prof.total_launches += n; }
 // tree.cpp
 void build_tree(xrl_ctx* c, const std::vector<uint64_t>& keys_by_caller);
 uint64_t morton_key(uint32_t ix, uint32_t iy, uint32_t iz);
@@ -227,6 +252,7 @@ void morton_decode(uint64_t key, uint32_t* ix, uint32_t* iy, uint32_t* iz);
 // topology.cpp
 void build_topology(xrl_ctx* c);
 void build_precond_pattern(xrl_ctx* c, const std::vector<double>& p_diag_caller);
+void build_band(xrl_ctx* c);
 // harmonics.cpp
 void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
 void build_translations(int p, const std::vector<int32_t>& offsets, std::vector<double>& m2m,
@@ -246,5 +272,13 @@ void launch_from_morton(const xrl_ctx* c, int ncols, const double* Y, double* y_
 // solve.cu
 void solver_prepare(xrl_ctx* c);
 void run_solve(xrl_ctx* c, int nf, const double* f, double* R, double* L);
-void apply_operator_host(xrl_ctx* c, int nsys, const double* f, const double* v, double* w, bool precond_matrix);
+void apply_operator_host(xrl_ctx* c, int nsys, const double* f, const double* v, double* w, int mode);
+// precond.cu
+bool band_usable(const xrl_ctx* c);
+void band_prepare(xrl_ctx* c);
+void band_factor(xrl_ctx* c, int nf, const double2* zs, const double* wp, double2* fac, double2* Wb, double2* Sinv,
+                 cudaStream_t s);
+void band_apply(xrl_ctx* c, int nsys, int nport, const double2* zs, const double* wp, const double2* fac,
+                const double2* Wb, const double2* Sinv, const double2* v, double2* z, double2* scratch,
+                const int* active, cudaStream_t s);
 }  // namespace xrl

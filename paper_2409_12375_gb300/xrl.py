@@ -67,11 +67,17 @@ SIGNATURES = {
     "xrl_solve": (ctypes.c_int, [_P, ctypes.c_int32, _D, _D, _D]),
     "xrl_apply_operator": (ctypes.c_int, [_P, ctypes.c_int32, _D, _D, _D]),
     "xrl_apply_precond_matrix": (ctypes.c_int, [_P, ctypes.c_int32, _D, _D, _D]),
+    "xrl_apply_precond_inverse": (ctypes.c_int, [_P, ctypes.c_int32, _D, _D, _D]),
     "xrl_export_tree": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), _I, _I]),
     "xrl_export_branches": (ctypes.c_int, [_P, _I, _I]),
     "xrl_export_loops": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), _I, ctypes.POINTER(ctypes.c_int8)]),
     "xrl_export_lists": (ctypes.c_int, [_P, ctypes.c_int32, _I, ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_int64), _I, ctypes.POINTER(ctypes.c_int64), _I]),
+    "xrl_set_profiling": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "xrl_get_profile": (ctypes.c_int, [_P, ctypes.c_int32, _D, ctypes.POINTER(ctypes.c_int64), _D, _D]),
+    "xrl_reset_profile": (ctypes.c_int, [_P]),
+    "xrl_kernel_launches": (ctypes.c_int64, [_P]),
+    "xrl_get_stream": (ctypes.c_void_p, [_P]),
     "xrl_last_error": (ctypes.c_char_p, [_P]),
     "xrl_destroy": (None, [_P]),
 }
@@ -203,14 +209,47 @@ class XRL:
         self._check(code, self.h)
         return R, L
 
-    def apply_operator(self, freqs, v, precond_matrix=False):
-        """w_s = Z(f_s) v_s (or Q(f_s) v_s); v complex [n_sys][n_loops]."""
+    def apply_operator(self, freqs, v, precond_matrix=False, precond_inverse=False):
+        """w_s = Z(f_s) v_s (or Q(f_s) v_s, or Q(f_s)^-1 v_s); v complex [n_sys][n_loops]."""
         f = np.ascontiguousarray(freqs, np.float64)
         v = np.ascontiguousarray(v, np.complex128)
         w = np.empty_like(v)
-        fn = lib().xrl_apply_precond_matrix if precond_matrix else lib().xrl_apply_operator
+        fn = lib().xrl_apply_operator
+        if precond_matrix:
+            fn = lib().xrl_apply_precond_matrix
+        if precond_inverse:
+            fn = lib().xrl_apply_precond_inverse
         self._check(fn(self.h, f.shape[0], _dp(f), v.ctypes.data_as(_D), w.ctypes.data_as(_D)), self.h)
         return w
+
+    # ---- profiling ---------------------------------------------------------------
+    PHASES = ["p2p", "p2m", "m2m", "m2l", "l2l", "l2p", "operator", "precond", "krylov"]
+
+    def set_profiling(self, on=True):
+        self._check(lib().xrl_set_profiling(self.h, 1 if on else 0), self.h)
+
+    def reset_profile(self):
+        self._check(lib().xrl_reset_profile(self.h), self.h)
+
+    def profile(self):
+        """{phase: dict(ms, launches, flops, bytes)} since the last reset."""
+        out = {}
+        for i, name in enumerate(self.PHASES):
+            ms = ctypes.c_double()
+            n = ctypes.c_int64()
+            fl = ctypes.c_double()
+            by = ctypes.c_double()
+            self._check(lib().xrl_get_profile(self.h, i, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl),
+                                              ctypes.byref(by)), self.h)
+            out[name] = {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
+        return out
+
+    def stream_handle(self):
+        """The library's own cudaStream_t as an int (for torch.cuda.ExternalStream)."""
+        return int(lib().xrl_get_stream(self.h) or 0)
+
+    def kernel_launches(self):
+        return int(lib().xrl_kernel_launches(self.h))
 
     # ---- introspection ---------------------------------------------------------
     def stats(self):

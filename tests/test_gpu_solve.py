@@ -99,6 +99,24 @@ def test_precond_matrix_matches_oracle(bar_ctx, bar_circ, bar_dense_P):
         assert np.linalg.norm(w[s] - ref) / np.linalg.norm(ref) < 1e-12
 
 
+@pytest.mark.parametrize("mesh_name", ["bar", "coils"])
+def test_banded_precond_inverse(lib, bar_ctx, mesh_name):
+    """Q(f)^-1 by the banded LDL^T + border factorisation, checked by
+    applying Q (the sparse matrix of eq. 10) to the result."""
+    ctx = bar_ctx
+    if mesh_name == "coils":
+        ctx = lib.XRL.from_mesh(meshgen.coils(), fmm_order=4)
+    n = ctx.stats()["n_loops"]
+    rng = np.random.default_rng(13)
+    f = np.array([1e2, 1e6, 1e10])
+    v = rng.standard_normal((3, n)) + 1j * rng.standard_normal((3, n))
+    z = ctx.apply_operator(f, v, precond_inverse=True)
+    back = ctx.apply_operator(f, z, precond_matrix=True)
+    assert np.linalg.norm(back - v) / np.linalg.norm(v) < 1e-10
+    if mesh_name == "coils":
+        ctx.close()
+
+
 def test_bar_sweep_matches_oracle(bar_ctx, bar_circ, bar_dense_P, bar_mesh):
     f = bar_mesh.freqs
     R, L = bar_ctx.solve(f)
