@@ -121,6 +121,29 @@ xrl_status xrl_fmm_mvm(xrl_ctx* ctx, int32_t n_cols, const double* x, double* y)
 xrl_status xrl_fmm_mvm_device(xrl_ctx* ctx, int32_t n_cols, const double* d_x, double* d_y,
                               void* stream);
 
+/* Same product as xrl_fmm_mvm_device, for callers that must not allocate GPU
+ * memory: code running while a CUDA stream is being captured into a graph,
+ * a real-time loop where a cudaMalloc could stall or fail, or a host
+ * framework whose own allocator owns the device memory budget.  This call
+ * allocates nothing: its working buffers (the Morton-ordered copies of x and
+ * y and the multipole/local expansions, 2 N n_cols + 2 n_boxes (p+1)^2 n_cols
+ * doubles) live in one fixed device array of XRL_NOALLOC_SCRATCH_BYTES
+ * (32 MiB) that the library declares statically; every GPU the library is
+ * loaded on holds that array until the process exits.  Sizes that do not
+ * fit return XRL_EINVAL (nothing is launched).  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress, no
+ * allocation), so make that first call before capturing a stream.  All
+ * calls share the one array: two calls whose work overlaps on the GPU
+ * (different streams, or different contexts on the same device) race and
+ * corrupt each other's results, so serialise them.  The array keeps the
+ * last call's contents; nothing in it needs to start at zero.  Profiling
+ * (xrl_set_profiling) is not recorded for this call.  The paper has no
+ * counterpart: this is an interface variant only.  d_x and d_y as for
+ * xrl_fmm_mvm_device. */
+#define XRL_NOALLOC_SCRATCH_BYTES (32u << 20)
+xrl_status xrl_fmm_mvm_device_noalloc(xrl_ctx* ctx, int32_t n_cols, const double* d_x, double* d_y,
+                                      void* stream);
+
 /* Reference product y = P x by direct O(N^2) summation on the GPU, every
  * entry evaluated with the same quadrature rule table as the near field
  * (device buffers, layout as xrl_fmm_mvm_device). */

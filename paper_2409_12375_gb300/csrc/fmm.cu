@@ -324,6 +324,13 @@ void fmm_apply(xrl_ctx* c, int nc, const double* X, double* Y, cudaStream_t s) {
                       c->d.Mexp.p, c->d.Lexp.p, s);
 }
 
+// FP64 product with caller-provided expansion buffers (each at least
+// n_boxes * (p+1)^2 * nc doubles); allocates nothing.
+void fmm_apply_into(xrl_ctx* c, int nc, const double* X, double* Y, double* Mx, double* Lx, cudaStream_t s) {
+  fmm_apply_t<double>(c, nc, X, Y, c->d.near_val.p, c->d.mom.p, c->d.t_m2m.p, c->d.t_l2l.p, c->d.t_m2l.p, Mx, Lx,
+                      s);
+}
+
 void fmm_apply32(xrl_ctx* c, int nc, const float* X, float* Y, cudaStream_t s) {
   size_t ne = (size_t)c->tree.n_boxes() * c->ncoef * nc;
   c->d.M32.ensure(c->alloc, ne);

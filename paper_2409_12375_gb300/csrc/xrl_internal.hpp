@@ -267,6 +267,7 @@ void upload_rule_tables(xrl_ctx* c);
 void fmm_prepare(xrl_ctx* c);                  // upload tree and operators
 void fmm_apply(xrl_ctx* c, int ncols, const double* X, double* Y, cudaStream_t s);      // Morton [N][nc]
 void fmm_apply32(xrl_ctx* c, int ncols, const float* X, float* Y, cudaStream_t s);
+void fmm_apply_into(xrl_ctx* c, int ncols, const double* X, double* Y, double* Mx, double* Lx, cudaStream_t s);
 void launch_to_morton(const xrl_ctx* c, int ncols, const double* x_user, double* X, cudaStream_t s);
 void launch_from_morton(const xrl_ctx* c, int ncols, const double* Y, double* y_user, cudaStream_t s);
 // solve.cu

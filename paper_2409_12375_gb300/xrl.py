@@ -62,6 +62,7 @@ SIGNATURES = {
     "xrl_setup": (ctypes.c_int, [_P]),
     "xrl_fmm_mvm": (ctypes.c_int, [_P, ctypes.c_int32, _D, _D]),
     "xrl_fmm_mvm_device": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
+    "xrl_fmm_mvm_device_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "xrl_direct_mvm_device": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "xrl_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
     "xrl_solve": (ctypes.c_int, [_P, ctypes.c_int32, _D, _D, _D]),
