@@ -88,6 +88,75 @@ __global__ void k_p2p(int nc, int ct, const int32_t* __restrict__ leaf_first, co
   }
 }
 
+// FP32 near field, shared-memory tiled: one block per (leaf, 64-column tile,
+// 64-row block), 128 threads as 16 row groups x 8 column groups; thread
+// (ty, tx) owns rows ty + 16 i (i < 4) and columns 8 tx .. 8 tx + 7.  The
+// leaf's value block (row-major, width w) and the gathered source rows of X
+// stream through shared memory in K-chunks of 32 near columns.
+__global__ void __launch_bounds__(128) k_p2p_tiled(int nc, const int32_t* __restrict__ leaf_first,
+                                                   const int32_t* __restrict__ leaf_count,
+                                                   const int64_t* __restrict__ near_off, const int32_t* __restrict__ near_w,
+                                                   const int64_t* __restrict__ col_off, const int32_t* __restrict__ near_src,
+                                                   const float* __restrict__ val, const float* __restrict__ X,
+                                                   float* __restrict__ Y) {
+  constexpr int CT = 64, KC = 32, RB = 64;
+  __shared__ __align__(16) float Vs[KC][RB];     // transposed value chunk: [near column][row]
+  __shared__ __align__(16) float Xs[KC][CT];
+  const int B = blockIdx.x;
+  const int c0 = blockIdx.y * CT;
+  const int rb0 = blockIdx.z * RB;
+  const int nB = leaf_count[B], f0 = leaf_first[B], w = near_w[B];
+  if (rb0 >= nB) return;
+  const int nr = min(RB, nB - rb0);
+  const float* vb = val + near_off[B] + (size_t)rb0 * w;
+  const int32_t* src = near_src + col_off[B];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < w; k0 += KC) {
+    const int kn = min(KC, w - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < KC * RB; e += 128) {
+      int r = e / KC, kk = e % KC;
+      Vs[kk][r] = (r < nr && kk < kn) ? vb[(size_t)r * w + k0 + kk] : 0.f;
+    }
+    for (int e = threadIdx.x; e < KC * CT; e += 128) {
+      int kk = e / CT, cc = e % CT;
+      Xs[kk][cc] = (kk < kn && c0 + cc < nc) ? X[(size_t)src[k0 + kk] * nc + c0 + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      const float4 x0 = *reinterpret_cast<const float4*>(&Xs[kk][8 * tx]);
+      const float4 x1 = *reinterpret_cast<const float4*>(&Xs[kk][8 * tx + 4]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float v = Vs[kk][ty + 16 * i];
+        acc[i][0] += v * x0.x;
+        acc[i][1] += v * x0.y;
+        acc[i][2] += v * x0.z;
+        acc[i][3] += v * x0.w;
+        acc[i][4] += v * x1.x;
+        acc[i][5] += v * x1.y;
+        acc[i][6] += v * x1.z;
+        acc[i][7] += v * x1.w;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int r = ty + 16 * i;
+    if (r >= nr) continue;
+    float* yr = Y + (size_t)(f0 + rb0 + r) * nc + c0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (c0 + 8 * tx + j < nc) yr[8 * tx + j] = acc[i][j];
+  }
+}
+
 // ---- expansions ----------------------------------------------------------------------------
 // P2M: M[box][k][c] = sum_i S[i][k] X[i][c]
 template <class T>
@@ -150,6 +219,113 @@ __global__ void k_m2l(int nc, int ct, int ncoef, int b0, const int32_t* __restri
       for (int j = 0; j < ncoef; ++j) acc += tm[(size_t)j * ncoef + k] * ms[(size_t)j * nc];
     }
     L[(size_t)Bx * ne + (size_t)k * nc + c0 + cc] = acc;
+  }
+}
+
+// M2L, FP32, shared-memory tiled: one block per (target box, 64-column tile),
+// 128 threads as 16 row groups x 8 column groups; thread (ty, tx) owns rows
+// ty + 16 i (i < RI) and the 8 consecutive columns 8 tx .. 8 tx + 7.  Per
+// V-list pair the translation matrix (stored [in][out]) and the source
+// multipole tile are staged in shared memory; the inner loop does 8 RI FMAs
+// per RI + 2 shared loads (float4 for the columns).
+template <int RI>
+__global__ void __launch_bounds__(128) k_m2l_tiled(int nc, int ncoef, int b0, const int32_t* __restrict__ v_ptr,
+                                                   const int32_t* __restrict__ v_src, const int16_t* __restrict__ v_off,
+                                                   const float* __restrict__ Tt, const float* __restrict__ M,
+                                                   float* __restrict__ L) {
+  constexpr int CT = 64;
+  extern __shared__ float sm32[];
+  float* Ts = sm32;                       // [ncoef][16 * RI] (padded rows)
+  float* Ms = sm32 + ncoef * 16 * RI;     // [ncoef][CT]
+  const int Bx = b0 + blockIdx.x;
+  const int c0 = blockIdx.y * CT;
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  const int vs = v_ptr[Bx], ve = v_ptr[Bx + 1];
+  const size_t ne = (size_t)ncoef * nc;
+  const int ld = 16 * RI;
+  float acc[RI][8];
+#pragma unroll
+  for (int i = 0; i < RI; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  for (int v = vs; v < ve; ++v) {
+    const float* tm = Tt + (size_t)v_off[v] * ncoef * ncoef;
+    const float* ms = M + (size_t)v_src[v] * ne + c0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < ncoef * ld; e += 128) {
+      int j = e / ld, k = e % ld;
+      Ts[e] = k < ncoef ? tm[(size_t)j * ncoef + k] : 0.f;
+    }
+    for (int e = threadIdx.x; e < ncoef * CT; e += 128) {
+      int j = e / CT, cc = e % CT;
+      Ms[e] = (c0 + cc < nc) ? ms[(size_t)j * nc + cc] : 0.f;
+    }
+    __syncthreads();
+    for (int j = 0; j < ncoef; ++j) {
+      const float4 m0 = *reinterpret_cast<const float4*>(Ms + j * CT + 8 * tx);
+      const float4 m1 = *reinterpret_cast<const float4*>(Ms + j * CT + 8 * tx + 4);
+      const float* tr = Ts + j * ld + ty;
+#pragma unroll
+      for (int i = 0; i < RI; ++i) {
+        const float t = tr[16 * i];
+        acc[i][0] += t * m0.x;
+        acc[i][1] += t * m0.y;
+        acc[i][2] += t * m0.z;
+        acc[i][3] += t * m0.w;
+        acc[i][4] += t * m1.x;
+        acc[i][5] += t * m1.y;
+        acc[i][6] += t * m1.z;
+        acc[i][7] += t * m1.w;
+      }
+    }
+  }
+  float* out = L + (size_t)Bx * ne + c0;
+#pragma unroll
+  for (int i = 0; i < RI; ++i) {
+    int k = ty + 16 * i;
+    if (k >= ncoef) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      int cc = 8 * tx + j;
+      if (c0 + cc < nc) out[(size_t)k * nc + cc] = acc[i][j];
+    }
+  }
+}
+
+template <class T>
+static void launch_m2l(int nbx, int b0, int nc, int ct_e, int ncoef, const int32_t* vptr, const int32_t* vsrc,
+                       const int16_t* voff, const T* tm2l, const T* Mx, T* Lx, cudaStream_t s) {
+  k_m2l<T><<<dim3(nbx, (nc + ct_e - 1) / ct_e), 256, 0, s>>>(nc, ct_e, ncoef, b0, vptr, vsrc, voff, tm2l, Mx, Lx);
+}
+
+template <>
+void launch_m2l<float>(int nbx, int b0, int nc, int ct_e, int ncoef, const int32_t* vptr, const int32_t* vsrc,
+                       const int16_t* voff, const float* tm2l, const float* Mx, float* Lx, cudaStream_t s) {
+  if (nc < 32 || ncoef > 16 * 11) {
+    k_m2l<float><<<dim3(nbx, (nc + ct_e - 1) / ct_e), 256, 0, s>>>(nc, ct_e, ncoef, b0, vptr, vsrc, voff, tm2l, Mx,
+                                                                   Lx);
+    return;
+  }
+  dim3 g(nbx, (nc + 63) / 64);
+  if (ncoef <= 64) {
+    size_t sm = sizeof(float) * (size_t)ncoef * (16 * 4 + 64);
+    k_m2l_tiled<4><<<g, 128, sm, s>>>(nc, ncoef, b0, vptr, vsrc, voff, tm2l, Mx, Lx);
+  } else if (ncoef <= 96) {
+    size_t sm = sizeof(float) * (size_t)ncoef * (16 * 6 + 64);
+    static bool set6 = false;
+    if (!set6) {
+      XRL_CUDA(cudaFuncSetAttribute(k_m2l_tiled<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 160 * 4));
+      set6 = true;
+    }
+    k_m2l_tiled<6><<<g, 128, sm, s>>>(nc, ncoef, b0, vptr, vsrc, voff, tm2l, Mx, Lx);
+  } else {
+    size_t sm = sizeof(float) * (size_t)ncoef * (16 * 11 + 64);
+    static bool set11 = false;
+    if (!set11) {
+      XRL_CUDA(cudaFuncSetAttribute(k_m2l_tiled<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, 176 * 240 * 4));
+      set11 = true;
+    }
+    k_m2l_tiled<11><<<g, 128, sm, s>>>(nc, ncoef, b0, vptr, vsrc, voff, tm2l, Mx, Lx);
   }
 }
 
@@ -271,8 +447,15 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   const int ct_e = nc < 4 ? nc : 4;
   dim3 gp(nl, (nc + ct_p - 1) / ct_p);
   cudaEvent_t ev = prof_begin(c, s);
-  k_p2p<T><<<gp, 128, 0, s>>>(nc, ct_p, c->d.leaf_first.p, c->d.leaf_count.p, c->d.u_ptr32.p, c->d.u_src.p,
-                              c->d.near_off.p, c->d.near_w.p, near, X, Y);
+  if (sizeof(T) == 4 && nc >= 32) {
+    dim3 gt(nl, (nc + 63) / 64, (c->max_leaf + 63) / 64);
+    k_p2p_tiled<<<gt, 128, 0, s>>>(nc, c->d.leaf_first.p, c->d.leaf_count.p, c->d.near_off.p, c->d.near_w.p,
+                                   c->d.near_col_off.p, c->d.near_src.p, (const float*)near, (const float*)X,
+                                   (float*)Y);
+  } else {
+    k_p2p<T><<<gp, 128, 0, s>>>(nc, ct_p, c->d.leaf_first.p, c->d.leaf_count.p, c->d.u_ptr32.p, c->d.u_src.p,
+                                c->d.near_off.p, c->d.near_w.p, near, X, Y);
+  }
   prof_end(c, s, ev, PH_P2P, 1, 2.0 * nne * nc, nne * sz + 2.0 * N * nc * sz);
   const int ecols = (nc + ct_e - 1) / ct_e;
   const int leaf0 = t.level_off[L];
@@ -295,8 +478,7 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     int b0 = t.level_off[2];
     int nbx = t.level_off[L + 1] - b0;
     ev = prof_begin(c, s);
-    k_m2l<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, b0, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p,
-                                              tm2l, Mx, Lx);
+    launch_m2l<T>(nbx, b0, nc, ct_e, ncoef, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p, tm2l, Mx, Lx, s);
     prof_end(c, s, ev, PH_M2L, 1, e2 * (double)t.v_src.size(), 2.0 * nbx * ebytes);
   }
   ev = prof_begin(c, s);

@@ -18,6 +18,7 @@
 //   q >= 10        point product rule 3x3 x 3x3
 // The analytic potential of a uniformly charged flat triangle is the closed
 // form of Wilton et al. (1984) / Graglia (1993).
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -467,6 +468,20 @@ void launch_near_fill(xrl_ctx* c) {
     off[i + 1] = off[i] + (int64_t)width * t.leaf_count[i];
   }
   c->stats.near_nnz = off[nl];
+  // Morton index of every near column of every leaf (for the tiled P2P)
+  std::vector<int64_t> coff(nl + 1, 0);
+  std::vector<int32_t> nsrc;
+  for (int i = 0; i < nl; ++i) {
+    for (int64_t s = t.u_ptr[i]; s < t.u_ptr[i + 1]; ++s) {
+      int S = t.u_src[s];
+      for (int q = 0; q < t.leaf_count[S]; ++q) nsrc.push_back(t.leaf_first[S] + q);
+    }
+    coff[i + 1] = (int64_t)nsrc.size();
+  }
+  c->d.near_col_off.upload(c->alloc, coff);
+  c->max_leaf = 0;
+  for (int i = 0; i < nl; ++i) c->max_leaf = std::max(c->max_leaf, t.leaf_count[i]);
+  c->d.near_src.upload(c->alloc, nsrc);
   std::vector<int32_t> uptr32(t.u_ptr.begin(), t.u_ptr.end());
   c->d.leaf_first.upload(c->alloc, t.leaf_first);
   c->d.leaf_count.upload(c->alloc, t.leaf_count);

@@ -76,58 +76,227 @@ __global__ void k_band_factor(int n, int b, int nmat, const double* __restrict__
   }
 }
 
-// One warp solves Q_vv x = r for one right-hand side (band order).  rhs and
-// x may alias.  Lanes hold band positions; y values of the last b rows are
-// kept in a shared ring.
-__device__ void band_solve_warp(int n, int b, const cplx* __restrict__ fac, const cplx* rhs, cplx* x, cplx* ring) {
+// ---- asynchronous global -> shared copies (16 bytes each) ----------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// rows per streamed chunk: >= b so that the backward pass needs at most two chunks
+__host__ __device__ inline int band_chunk(int b) { return b <= 32 ? 32 : 64; }
+constexpr int kRing = 64;   // power of two > kMaxBand
+// row stride of a stored factor: b + 1, rounded up to even for 8-byte elements
+template <class C>
+__host__ __device__ inline int band_rs(int b) { return sizeof(C) == 8 ? ((b + 2) & ~1) : b + 1; }
+template <class C>
+__host__ __device__ inline size_t band_smem_bytes(int b) {
+  const int ch = band_chunk(b);
+  return sizeof(C) * ((size_t)2 * ch * band_rs<C>(b) + 2 * (size_t)ch);
+}
+
+// complex helpers for both precisions
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return cm(a, b); }
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+template <class C> __device__ __forceinline__ C czero();
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ float2 wsum(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+__device__ __forceinline__ double2 wsum(double2 v) { return warp_sum(v); }
+__device__ __forceinline__ float2 csubT(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 caddT(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 caddT(double2 a, double2 b) { return cadd(a, b); }
+__device__ __forceinline__ double2 csubT(double2 a, double2 b) { return csub(a, b); }
+
+// copy rows [r0, r1) of the factor (row stride rs) and entries [r0, r1) of vec
+// into shared buffers with 16-byte asynchronous copies.  For 8-byte elements
+// rs and r0 are even and vec has a readable element past its end.
+template <class C>
+__device__ __forceinline__ void band_issue(const C* fac, const C* vec, int r0, int r1, int rs, C* fb, C* vb) {
+  constexpr int per = 16 / sizeof(C);
   const int lane = threadIdx.x & 31;
-  const int nb1 = b + 1;
-  // forward: y_i = r_i - sum_{k<i} L_ik y_k ; store w_i = y_i / D_i
-  for (int i = 0; i < n; ++i) {
-    cplx acc = make_double2(0, 0);
-    for (int t = lane; t < b; t += 32) {
-      int k = i - b + t;            // column of entry t of row i
-      if (k >= 0) acc = cadd(acc, cm(fac[(size_t)i * nb1 + t], ring[k % nb1]));
-    }
-    acc = warp_sum(acc);
-    cplx y = csub(rhs[i], acc);
+  const int nf = (r1 - r0) * rs;
+  const C* src = fac + (size_t)r0 * rs;
+  for (int e = per * lane; e < nf; e += 32 * per) cp_async16(fb + e, src + e);
+  for (int e = per * lane; e < r1 - r0; e += 32 * per) cp_async16(vb + e, vec + r0 + e);
+  cp_commit();
+}
+
+// One warp solves Q_vv x = r (band order) in place: rhs in x on entry.  The
+// factor holds L below the diagonal and 1/D on it.  Factor rows and the
+// right-hand side stream through shared memory in chunks of `ch` rows
+// (cp.async, one chunk ahead), so the sequential substitution waits on
+// shared memory only.  smem: 3 factor chunks, 2 vector chunks, a ring of the
+// last kRing solution values.  C = float2 (mixed precision) or double2.
+// One warp solves Q_vv x = r (band order) in place: rhs in x on entry.
+// facT holds the factor by columns (facT[i][t] = L[i+1+t][i], facT[i][b] =
+// 1/D_i) and fac by rows (fac[i][t] = L[i][i-b+t]); both stream through
+// shared memory in chunks (cp.async, one chunk ahead).  The substitution is
+// column oriented: row k's pending sum lives in lane k % 32 (slot (k/32)%2),
+// (the sum of L_ki times the unknowns already found), so a step is one
+// broadcast of the new unknown and at most two complex FMAs per lane.  smem: 2 factor chunks + 2 vector chunks.
+template <class C>
+__device__ __forceinline__ C csel(bool s, C a, C b) { return s ? a : b; }
+
+template <class C>
+__device__ void band_solve_warp(int n, int b, int rs, const C* __restrict__ facT, const C* __restrict__ fac, C* x,
+                                C* smem) {
+  const int lane = threadIdx.x & 31;
+  const int ch = band_chunk(b);
+  const size_t fstride = (size_t)ch * rs;
+  C* fbuf = smem;                       // [2][ch * rs]
+  C* vbuf = smem + 2 * fstride;         // [2][ch]
+  const int nchunk = (n + ch - 1) / ch;
+  __threadfence();   // x was written by this warp's plain stores; cp.async reads L2
+  __syncwarp();
+  C acc0 = czero<C>(), acc1 = czero<C>();
+  // forward: y_i = r_i - sum_{k<i} L_ik y_k ; x_i <- w_i = y_i / D_i
+  band_issue<C>(facT, x, 0, min(n, ch), rs, fbuf, vbuf);
+  for (int c = 0; c < nchunk; ++c) {
+    const int r0 = c * ch, r1 = min(n, r0 + ch);
+    const bool more = c + 1 < nchunk;
+    if (more) band_issue<C>(facT, x, r1, min(n, r1 + ch), rs, fbuf + ((c + 1) & 1) * fstride, vbuf + ((c + 1) & 1) * ch);
+    if (more) cp_wait_all_but_one(); else cp_wait_all();
     __syncwarp();
-    if (lane == 0) {
-      ring[i % nb1] = y;
-      x[i] = cdiv(y, fac[(size_t)i * nb1 + b]);
+    const C* fr = fbuf + (c & 1) * fstride;
+    const C* vr = vbuf + (c & 1) * ch;
+    for (int i = r0; i < r1; ++i) {
+      const C* col = fr + (size_t)(i - r0) * rs;
+      const int own = i & 31;
+      const bool s1 = (i >> 5) & 1;
+      C y = czero<C>();
+      if (lane == own) {
+        y = csubT(vr[i - r0], csel(s1, acc1, acc0));
+        if (s1) acc1 = czero<C>(); else acc0 = czero<C>();
+      }
+      y.x = __shfl_sync(0xffffffffu, y.x, own);
+      y.y = __shfl_sync(0xffffffffu, y.y, own);
+      if (lane == own) x[i] = cmul(y, col[b]);
+      const int t = (lane - i - 1) & 31;
+      int k = i + 1 + t;
+      if (t < b && k < n) {
+        C d = cmul(col[t], y);
+        if ((k >> 5) & 1) acc1 = caddT(acc1, d); else acc0 = caddT(acc0, d);
+      }
+      k += 32;
+      if (t + 32 < b && k < n) {
+        C d = cmul(col[t + 32], y);
+        if ((k >> 5) & 1) acc1 = caddT(acc1, d); else acc0 = caddT(acc0, d);
+      }
     }
     __syncwarp();
   }
-  // backward: z_i = w_i - sum_{k>i} L_ki z_k
-  for (int i = n - 1; i >= 0; --i) {
-    cplx acc = make_double2(0, 0);
-    for (int t = lane; t < b; t += 32) {
-      int k = i + 1 + t;
-      if (k < n) acc = cadd(acc, cm(fac[(size_t)k * nb1 + (i - k + b)], ring[k % nb1]));
-    }
-    acc = warp_sum(acc);
-    cplx zi = csub(x[i], acc);
+  __syncwarp();
+  __threadfence();
+  __syncwarp();
+  // backward: z_i = w_i - sum_{k>i} L_ki z_k, rows of fac in descending chunks
+  acc0 = czero<C>();
+  acc1 = czero<C>();
+  {
+    const int c = nchunk - 1;
+    band_issue<C>(fac, x, c * ch, n, rs, fbuf + (c & 1) * fstride, vbuf + (c & 1) * ch);
+  }
+  for (int c = nchunk - 1; c >= 0; --c) {
+    const int r0 = c * ch, r1 = min(n, r0 + ch);
+    const bool more = c > 0;
+    if (more) band_issue<C>(fac, x, r0 - ch, r0, rs, fbuf + ((c - 1) & 1) * fstride, vbuf + ((c - 1) & 1) * ch);
+    if (more) cp_wait_all_but_one(); else cp_wait_all();
     __syncwarp();
-    if (lane == 0) {
-      ring[i % nb1] = zi;
-      x[i] = zi;
+    const C* fr = fbuf + (c & 1) * fstride;
+    const C* vr = vbuf + (c & 1) * ch;
+    for (int i = r1 - 1; i >= r0; --i) {
+      const C* row = fr + (size_t)(i - r0) * rs;
+      const int own = i & 31;
+      const bool s1 = (i >> 5) & 1;
+      C z = czero<C>();
+      if (lane == own) {
+        z = csubT(vr[i - r0], csel(s1, acc1, acc0));
+        if (s1) acc1 = czero<C>(); else acc0 = czero<C>();
+      }
+      z.x = __shfl_sync(0xffffffffu, z.x, own);
+      z.y = __shfl_sync(0xffffffffu, z.y, own);
+      if (lane == own) x[i] = z;
+      // rows k in [i-b, i-1] owned by this lane: k = i - 1 - ((i - 1 - lane) & 31), then k - 32
+      int k = i - 1 - ((i - 1 - lane) & 31);
+      if (k >= 0 && k >= i - b) {
+        C d = cmul(row[k - i + b], z);
+        if ((k >> 5) & 1) acc1 = caddT(acc1, d); else acc0 = caddT(acc0, d);
+      }
+      k -= 32;
+      if (k >= 0 && k >= i - b) {
+        C d = cmul(row[k - i + b], z);
+        if ((k >> 5) & 1) acc1 = caddT(acc1, d); else acc0 = caddT(acc0, d);
+      }
     }
     __syncwarp();
   }
 }
 
+// 1/D on the diagonal; the column-form copy facT (facT[i][t] = L[i+1+t][i],
+// facT[i][b] = 1/D_i); optional FP32 copies of both (row stride even).
+// One thread per (frequency row, entry).
+__global__ void k_band_finish(int nf, int n, int b, cplx* __restrict__ fac, cplx* __restrict__ facT,
+                              float2* __restrict__ fac32, float2* __restrict__ facT32) {
+  const size_t nb1 = b + 1;
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)nf * n * nb1) return;
+  const size_t rowg = e / nb1;          // global row (f * n + i)
+  const int t = (int)(e % nb1);
+  const int i = (int)(rowg % n);
+  const size_t fbase = rowg - i;        // f * n
+  const int rs32 = band_rs<float2>(b);
+  if (t == b) {
+    cplx inv = cdiv(make_double2(1.0, 0.0), fac[e]);
+    fac[e] = inv;
+    facT[e] = inv;
+    if (fac32) {
+      fac32[rowg * rs32 + b] = make_float2((float)inv.x, (float)inv.y);
+      facT32[rowg * rs32 + b] = make_float2((float)inv.x, (float)inv.y);
+      if (rs32 > (int)nb1) {
+        fac32[rowg * rs32 + nb1] = make_float2(0.f, 0.f);
+        facT32[rowg * rs32 + nb1] = make_float2(0.f, 0.f);
+      }
+    }
+    return;
+  }
+  // row form entry (i, t) = L[i][i-b+t]
+  cplx v = fac[e];
+  if (fac32) fac32[rowg * rs32 + t] = make_float2((float)v.x, (float)v.y);
+  // column form entry (i, t) = L[i+1+t][i] = row i+1+t, index b-1-t
+  const int k = i + 1 + t;
+  cplx w = make_double2(0.0, 0.0);
+  if (k < n) w = fac[(fbase + k) * nb1 + (b - 1 - t)];
+  facT[e] = w;
+  if (fac32) facT32[rowg * rs32 + t] = make_float2((float)w.x, (float)w.y);
+}
+
 // W[f][g][:] = Q_vv(f)^-1 Q_vg(f)[:, g]: one warp per (f, g)
 __global__ void k_border_solve(int n, int b, int ng, int nmat, const double* __restrict__ border_vg,
                                const cplx* __restrict__ zs, const double* __restrict__ wp_f,
-                               const cplx* __restrict__ fac, cplx* __restrict__ Wb) {
-  __shared__ cplx ring[kMaxBand + 1];
+                               const cplx* __restrict__ fac, const cplx* __restrict__ facT, cplx* __restrict__ Wb) {
+  extern __shared__ cplx bsm[];
   const int f = blockIdx.x / ng, g = blockIdx.x % ng;
   const size_t vstride = (size_t)n * ng;
   cplx* x = Wb + ((size_t)f * ng + g) * n;
   for (int i = threadIdx.x; i < n; i += 32)
     x[i] = pencil(border_vg + (size_t)i * ng + g, vstride, nmat, zs + (size_t)f * nmat, wp_f[f]);
   __syncwarp();
-  band_solve_warp(n, b, fac + (size_t)f * n * (b + 1), x, x, ring);
+  band_solve_warp<cplx>(n, b, b + 1, facT + (size_t)f * n * (b + 1), fac + (size_t)f * n * (b + 1), x, bsm);
 }
 
 // S = Q_gg - Q_vg^T W, then S^-1 in place (Gauss-Jordan, partial pivoting); one warp per f
@@ -177,13 +346,16 @@ __global__ void k_schur(int n, int ng, int nmat, const double* __restrict__ bord
   }
 }
 
-// z = Q(f_s)^-1 v for every system; one warp per system.  scratch: [nsys][n] complex
+// z = Q(f_s)^-1 v for every system; one warp per system; C = float2 (mixed
+// precision triangular solves from an FP64-computed factor) or double2.
+template <class C>
 __global__ void k_band_apply(int nloop, int n, int b, int ng, int nport, int nmat, const int32_t* __restrict__ perm,
                              const double* __restrict__ border_vg, const cplx* __restrict__ zs,
-                             const double* __restrict__ wp_f, const cplx* __restrict__ fac,
+                             const double* __restrict__ wp_f, const C* __restrict__ fac, const C* __restrict__ facT,
                              const cplx* __restrict__ Wb, const cplx* __restrict__ Sinv, const cplx* __restrict__ v,
-                             cplx* __restrict__ z, cplx* __restrict__ scratch, const int* __restrict__ active) {
-  __shared__ cplx ring[kMaxBand + 1];
+                             cplx* __restrict__ z, C* __restrict__ scratch, const int* __restrict__ active) {
+  extern __shared__ __align__(16) unsigned char bsm_raw[];
+  C* bsm = reinterpret_cast<C*>(bsm_raw);
   __shared__ cplx tg[kMaxBorder], zg[kMaxBorder];
   const int s = blockIdx.x;
   if (active && !active[s]) return;
@@ -191,17 +363,32 @@ __global__ void k_band_apply(int nloop, int n, int b, int ng, int nport, int nma
   const int lane = threadIdx.x & 31;
   const cplx* vs = v + (size_t)s * nloop;
   cplx* zs_out = z + (size_t)s * nloop;
-  cplx* x = scratch + (size_t)s * n;
-  for (int i = lane; i < n; i += 32) x[i] = vs[perm[i]];
+  C* x = scratch + (size_t)s * (size_t)((n + 2) & ~1);
+  for (int i = lane; i < n; i += 32) {
+    cplx vi = vs[perm[i]];
+    if (sizeof(C) == 8) {
+      reinterpret_cast<float2*>(x)[i] = make_float2((float)vi.x, (float)vi.y);
+    } else {
+      reinterpret_cast<cplx*>(x)[i] = vi;
+    }
+  }
   __syncwarp();
-  band_solve_warp(n, b, fac + (size_t)f * n * (b + 1), x, x, ring);
+  band_solve_warp<C>(n, b, band_rs<C>(b), facT + (size_t)f * n * band_rs<C>(b), fac + (size_t)f * n * band_rs<C>(b),
+                     x, bsm);
+  auto xval = [&](int i) -> cplx {
+    if (sizeof(C) == 8) {
+      float2 t = reinterpret_cast<const float2*>(x)[i];
+      return make_double2(t.x, t.y);
+    }
+    return reinterpret_cast<const cplx*>(x)[i];
+  };
   if (ng > 0) {
     const cplx* zf = zs + (size_t)f * nmat;
     const double wp = wp_f[f];
     const size_t vstride = (size_t)n * ng;
     for (int g = 0; g < ng; ++g) {
       cplx acc = make_double2(0, 0);
-      for (int i = lane; i < n; i += 32) acc = cadd(acc, cm(pencil(border_vg + (size_t)i * ng + g, vstride, nmat, zf, wp), x[i]));
+      for (int i = lane; i < n; i += 32) acc = cadd(acc, cm(pencil(border_vg + (size_t)i * ng + g, vstride, nmat, zf, wp), xval(i)));
       acc = warp_sum(acc);
       if (lane == 0) tg[g] = csub(vs[n + g], acc);
     }
@@ -213,14 +400,15 @@ __global__ void k_band_apply(int nloop, int n, int b, int ng, int nport, int nma
     }
     __syncwarp();
     for (int i = lane; i < n; i += 32) {
-      cplx acc = x[i];
+      cplx acc = xval(i);
       for (int g = 0; g < ng; ++g) acc = csub(acc, cm(Wb[((size_t)f * ng + g) * n + i], zg[g]));
-      x[i] = acc;
+      zs_out[perm[i]] = acc;
     }
     __syncwarp();
     if (lane < ng) zs_out[n + lane] = zg[lane];
+  } else {
+    for (int i = lane; i < n; i += 32) zs_out[perm[i]] = xval(i);
   }
-  for (int i = lane; i < n; i += 32) zs_out[perm[i]] = x[i];
 }
 
 // ---- host ---------------------------------------------------------------------------------
@@ -237,8 +425,8 @@ void band_prepare(xrl_ctx* c) {
 }
 
 // factor Q(f) for nf frequencies (zs [nf][nmat], wp [nf]) into fac, W, Sinv
-void band_factor(xrl_ctx* c, int nf, const cplx* zs, const double* wp, cplx* fac, cplx* Wb, cplx* Sinv,
-                 cudaStream_t s) {
+void band_factor(xrl_ctx* c, int nf, const cplx* zs, const double* wp, cplx* fac, cplx* facT, float2* fac32,
+                 float2* facT32, cplx* Wb, cplx* Sinv, cudaStream_t s) {
   const Topo& T = c->topo;
   const int n = T.n_band, b = T.band, ng = T.n_border;
   size_t smem = sizeof(cplx) * (b + 1) * (b + 1);
@@ -246,8 +434,17 @@ void band_factor(xrl_ctx* c, int nf, const cplx* zs, const double* wp, cplx* fac
   cudaEvent_t ev = prof_begin(c, s);
   k_band_factor<<<nf, 256, smem, s>>>(n, b, T.n_mat, c->d.band_val.p, zs, wp, fac);
   int launches = 1;
+  const size_t bsd = band_smem_bytes<cplx>(b);
+  if (bsd > 48 * 1024)
+    XRL_CUDA(cudaFuncSetAttribute(k_border_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsd));
+  // 1/D on the diagonal (and the FP32 copy for mixed-precision solves)
+  {
+    size_t tot = (size_t)nf * n * (b + 1);
+    k_band_finish<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nf, n, b, fac, facT, fac32, facT32);
+    ++launches;
+  }
   if (ng > 0) {
-    k_border_solve<<<nf * ng, 32, 0, s>>>(n, b, ng, T.n_mat, c->d.border_vg.p, zs, wp, fac, Wb);
+    k_border_solve<<<nf * ng, 32, bsd, s>>>(n, b, ng, T.n_mat, c->d.border_vg.p, zs, wp, fac, facT, Wb);
     k_schur<<<nf, 32, 0, s>>>(n, ng, T.n_mat, c->d.border_vg.p, c->d.border_gg.p, zs, wp, Wb, Sinv);
     launches += 2;
   }
@@ -255,14 +452,29 @@ void band_factor(xrl_ctx* c, int nf, const cplx* zs, const double* wp, cplx* fac
   XRL_CUDA(cudaGetLastError());
 }
 
-void band_apply(xrl_ctx* c, int nsys, int nport, const cplx* zs, const double* wp, const cplx* fac, const cplx* Wb,
-                const cplx* Sinv, const cplx* v, cplx* z, cplx* scratch, const int* active, cudaStream_t s) {
+void band_apply(xrl_ctx* c, int nsys, int nport, const cplx* zs, const double* wp, const cplx* fac,
+                const cplx* facT, const float2* fac32, const float2* facT32, const cplx* Wb, const cplx* Sinv,
+                const cplx* v, cplx* z, void* scratch, const int* active, cudaStream_t s) {
   const Topo& T = c->topo;
   cudaEvent_t ev = prof_begin(c, s);
-  k_band_apply<<<nsys, 32, 0, s>>>(T.n_loops, T.n_band, T.band, T.n_border, nport, T.n_mat, c->d.band_perm.p,
-                                   c->d.border_vg.p, zs, wp, fac, Wb, Sinv, v, z, scratch, active);
+  if (fac32) {
+    const size_t bs = band_smem_bytes<float2>(T.band) + 64;
+    if (bs > 48 * 1024)
+      XRL_CUDA(cudaFuncSetAttribute(k_band_apply<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs));
+    k_band_apply<float2><<<nsys, 32, bs, s>>>(T.n_loops, T.n_band, T.band, T.n_border, nport, T.n_mat,
+                                              c->d.band_perm.p, c->d.border_vg.p, zs, wp, fac32, facT32, Wb, Sinv, v, z,
+                                              (float2*)scratch, active);
+  } else {
+    const size_t bs = band_smem_bytes<cplx>(T.band) + 64;
+    if (bs > 48 * 1024)
+      XRL_CUDA(cudaFuncSetAttribute(k_band_apply<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs));
+    k_band_apply<cplx><<<nsys, 32, bs, s>>>(T.n_loops, T.n_band, T.band, T.n_border, nport, T.n_mat,
+                                            c->d.band_perm.p, c->d.border_vg.p, zs, wp, fac, facT, Wb, Sinv, v, z,
+                                            (cplx*)scratch, active);
+  }
+  const double es = fac32 ? 8.0 : 16.0;
   prof_end(c, s, ev, PH_PREC, 1, 16.0 * nsys * (double)T.n_band * T.band,
-           16.0 * nsys * (double)T.n_band * (2.0 * T.band + 4.0));
+           es * nsys * (double)T.n_band * (2.0 * T.band + 4.0));
   XRL_CUDA(cudaGetLastError());
 }
 

@@ -63,10 +63,11 @@ __global__ void k_sys_consts(int nsys, int nport, int nmat, const double* __rest
 
 // ---- operator pieces -------------------------------------------------------------------------
 // X[r][6s + 2t + ri] = (A_t^T M^T v_s)(r)
+template <class T>
 __global__ void k_gather(int N, int nsys, int nloop, const int32_t* __restrict__ pan_br,
                          const double* __restrict__ pan_rho, const int32_t* __restrict__ mt_ptr,
                          const int32_t* __restrict__ mt_col, const int8_t* __restrict__ mt_val,
-                         const cplx* __restrict__ v, double* __restrict__ X) {
+                         const cplx* __restrict__ v, T* __restrict__ X) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)N * nsys) return;
   int r = (int)(idx / nsys), s = (int)(idx % nsys);
@@ -83,19 +84,20 @@ __global__ void k_gather(int N, int nsys, int nloop, const int32_t* __restrict__
     const double* rho = pan_rho + 9 * (size_t)r + 3 * k;
     for (int t = 0; t < 3; ++t) ip[t] = cadd(ip[t], cscale(ie, rho[t]));
   }
-  double* out = X + (size_t)r * 6 * nsys + 6 * s;
+  T* out = X + (size_t)r * 6 * nsys + 6 * s;
   for (int t = 0; t < 3; ++t) {
-    out[2 * t] = ip[t].x;
-    out[2 * t + 1] = ip[t].y;
+    out[2 * t] = (T)ip[t].x;
+    out[2 * t + 1] = (T)ip[t].y;
   }
 }
 
 // Vb[s][b] = sum_side rho . (j w' Y + Z_s/A X) at the branch's panels
+template <class T>
 __global__ void k_scatter(int B, int nsys, int nmat, const int32_t* __restrict__ br_pan,
                           const double* __restrict__ br_rho, const int32_t* __restrict__ pan_mat,
                           const double* __restrict__ area, const cplx* __restrict__ zs,
-                          const double* __restrict__ wp, const double* __restrict__ X,
-                          const double* __restrict__ Y, cplx* __restrict__ Vb) {
+                          const double* __restrict__ wp, const T* __restrict__ X,
+                          const T* __restrict__ Y, cplx* __restrict__ Vb) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)B * nsys) return;
   int s = (int)(idx / B), b = (int)(idx % B);
@@ -105,8 +107,8 @@ __global__ void k_scatter(int B, int nsys, int nmat, const int32_t* __restrict__
     if (r < 0) continue;
     const double* rho = br_rho + 6 * (size_t)b + 3 * side;
     cplx z = cscale(zs[s * nmat + pan_mat[r]], 1.0 / area[r]);
-    const double* xr = X + (size_t)r * 6 * nsys + 6 * s;
-    const double* yr = Y + (size_t)r * 6 * nsys + 6 * s;
+    const T* xr = X + (size_t)r * 6 * nsys + 6 * s;
+    const T* yr = Y + (size_t)r * 6 * nsys + 6 * s;
     for (int t = 0; t < 3; ++t) {
       cplx xv = make_double2(xr[2 * t], xr[2 * t + 1]);
       cplx yv = make_double2(yr[2 * t], yr[2 * t + 1]);
@@ -284,8 +286,9 @@ __global__ void k_arnoldi_sub(int n, int nsys, int j, int ldh, const cplx* __res
 __global__ void k_arnoldi_norm(int n, int nsys, int j, int m, cplx* __restrict__ H, const cplx* __restrict__ h1,
                                const cplx* __restrict__ h2, cplx* __restrict__ w, cplx* __restrict__ Vnext,
                                cplx* __restrict__ cs, cplx* __restrict__ sn, cplx* __restrict__ g,
-                               int* __restrict__ active, const double* __restrict__ bnorm, double tol,
-                               double* __restrict__ resid, int* __restrict__ iters) {
+                               int* __restrict__ active, const double* __restrict__ bnorm,
+                               const double* __restrict__ thr, double* __restrict__ resid,
+                               int* __restrict__ iters) {
   __shared__ cplx sh[256];
   int s = blockIdx.x;
   if (!active[s]) return;
@@ -327,7 +330,7 @@ __global__ void k_arnoldi_norm(int n, int nsys, int j, int m, cplx* __restrict__
     double res = sqrt(cabs2(g[s * (m + 1) + j + 1]));
     resid[s] = res / bnorm[s];
     iters[s] += 1;
-    if (res <= tol * bnorm[s] || nw == 0.0) active[s] = 0;
+    if (res <= thr[s] || nw == 0.0) active[s] = 0;
   }
 }
 
@@ -356,9 +359,12 @@ __global__ void k_update_x(int n, int nsys, int m, const int* __restrict__ kcols
 }
 
 // r = b - Ax ; beta = ||r||; v0 = r / beta; g = (beta, 0, ...)
+// thr[s] = max(tol ||b||, tau ||r||): the inner cycle's stopping level (tau > 0 in
+// the mixed-precision mode, where the cycle's operator is only FP32-accurate)
 __global__ void k_restart(int n, int nsys, int m, const cplx* __restrict__ b, const cplx* __restrict__ Ax,
                           cplx* __restrict__ V0, cplx* __restrict__ g, const double* __restrict__ bnorm,
-                          double tol, int* __restrict__ active, double* __restrict__ resid) {
+                          double tol, double tau, int* __restrict__ active, double* __restrict__ resid,
+                          double* __restrict__ thr) {
   __shared__ cplx sh[256];
   int s = blockIdx.x;
   size_t o = (size_t)s * n;
@@ -375,6 +381,7 @@ __global__ void k_restart(int n, int nsys, int m, const cplx* __restrict__ b, co
     g[s * (m + 1)] = make_double2(beta, 0);
     resid[s] = bnorm[s] > 0 ? beta / bnorm[s] : 0.0;
     active[s] = (beta > tol * bnorm[s]) ? 1 : 0;
+    thr[s] = fmax(tol * bnorm[s], tau * beta);
   }
 }
 
@@ -496,12 +503,14 @@ static unsigned nblk(size_t n, int bs = 256) { return (unsigned)((n + bs - 1) / 
 // Work arrays of one solve (device)
 struct Work {
   DBuf<double> freq, wp, wpf;
-  DBuf<cplx> zs, zsf, fac, Wb, Sinv, bscr;
+  DBuf<cplx> zs, zsf, fac, facT, Wb, Sinv, bscr;
+  DBuf<float2> fac32, facT32;
   int nport = 1;
   bool banded = false;
   DBuf<cplx> b, x, w, tmp, V, Z, H, h1, h2, cs, sn, g, y, Vb, dinv;
   DBuf<cplx> cz, cr, cp, cq, crho;
-  DBuf<double> X, Y, bnorm, resid, cvn;
+  DBuf<double> X, Y, bnorm, resid, cvn, thr;
+  DBuf<float> X32, Y32;
   DBuf<int> active, iters, kcols, clive;
 };
 
@@ -522,32 +531,48 @@ static void sys_consts(xrl_ctx* c, Work& wk, int nsys, int nport, int nf, const 
   count_launch(c, 2);
 }
 
-// w = Z(f_s) v_s for all systems (eq. 8), FMM in FP64
-static void apply_A(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w) {
-  const Topo& T = c->topo;
+// w = Z(f_s) v_s for all systems (eq. 8); the FMM runs in FP64, or in FP32
+// for the inner iterations of the mixed-precision mode (low = true)
+template <class T>
+static void apply_A_t(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, T* X, T* Y) {
+  const Topo& T_ = c->topo;
   const int N = c->N;
   const int nc = 6 * nsys;
   cudaStream_t s = c->stream;
-  wk.X.ensure(c->alloc, (size_t)N * nc);
-  wk.Y.ensure(c->alloc, (size_t)N * nc);
-  wk.Vb.ensure(c->alloc, (size_t)nsys * T.n_cb);
+  wk.Vb.ensure(c->alloc, (size_t)nsys * T_.n_cb);
   cudaEvent_t ev = prof_begin(c, s);
-  k_gather<<<nblk((size_t)N * nsys), 256, 0, s>>>(N, nsys, T.n_loops, c->d.pan_br.p, c->d.pan_rho.p, c->d.mt_ptr.p,
-                                                 c->d.mt_col.p, c->d.mt_val.p, v, wk.X.p);
-  const double nnzm = (double)T.m_col.size();
-  prof_end(c, s, ev, PH_OPER, 1, 8.0 * nnzm * nsys + 18.0 * N * nsys, nsys * (16.0 * nnzm + 48.0 * N));
-  fmm_apply(c, nc, wk.X.p, wk.Y.p, s);
+  k_gather<T><<<nblk((size_t)N * nsys), 256, 0, s>>>(N, nsys, T_.n_loops, c->d.pan_br.p, c->d.pan_rho.p,
+                                                     c->d.mt_ptr.p, c->d.mt_col.p, c->d.mt_val.p, v, X);
+  const double nnzm = (double)T_.m_col.size();
+  prof_end(c, s, ev, PH_OPER, 1, 8.0 * nnzm * nsys + 18.0 * N * nsys, nsys * (16.0 * nnzm + 6.0 * sizeof(T) * N));
+  if (sizeof(T) == 8)
+    fmm_apply(c, nc, (const double*)X, (double*)Y, s);
+  else
+    fmm_apply32(c, nc, (const float*)X, (float*)Y, s);
   ev = prof_begin(c, s);
   // conductor branches only; the external port branches carry no impedance
-  k_scatter<<<nblk((size_t)T.n_cb * nsys), 256, 0, s>>>(T.n_cb, nsys, T.n_mat, c->d.br_pan.p, c->d.br_rho.p,
-                                                        c->d.pan_mat.p, c->d.area.p, wk.zs.p, wk.wp.p, wk.X.p,
-                                                        wk.Y.p, wk.Vb.p);
-  k_loop_reduce<<<nblk((size_t)T.n_loops * nsys), 256, 0, s>>>(T.n_loops, nsys, T.n_cb, T.n_cb, c->d.m_ptr.p,
-                                                               c->d.m_col.p, c->d.m_val.p, wk.Vb.p, w);
-  prof_end(c, s, ev, PH_OPER, 2, nsys * (2.0 * T.n_cb * 30.0 + 2.0 * nnzm),
-           nsys * (T.n_cb * (2.0 * 96.0 + 16.0) + 16.0 * nnzm + 16.0 * T.n_loops));
+  k_scatter<T><<<nblk((size_t)T_.n_cb * nsys), 256, 0, s>>>(T_.n_cb, nsys, T_.n_mat, c->d.br_pan.p, c->d.br_rho.p,
+                                                            c->d.pan_mat.p, c->d.area.p, wk.zs.p, wk.wp.p, X, Y,
+                                                            wk.Vb.p);
+  k_loop_reduce<<<nblk((size_t)T_.n_loops * nsys), 256, 0, s>>>(T_.n_loops, nsys, T_.n_cb, T_.n_cb, c->d.m_ptr.p,
+                                                                c->d.m_col.p, c->d.m_val.p, wk.Vb.p, w);
+  prof_end(c, s, ev, PH_OPER, 2, nsys * (2.0 * T_.n_cb * 30.0 + 2.0 * nnzm),
+           nsys * (T_.n_cb * (2.0 * 12.0 * sizeof(T) + 16.0) + 16.0 * nnzm + 16.0 * T_.n_loops));
   XRL_CUDA(cudaGetLastError());
   c->stats.n_mvm++;
+}
+
+static void apply_A(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, bool low = false) {
+  const size_t n = (size_t)c->N * 6 * nsys;
+  if (low) {
+    wk.X32.ensure(c->alloc, n);
+    wk.Y32.ensure(c->alloc, n);
+    apply_A_t<float>(c, wk, nsys, v, w, wk.X32.p, wk.Y32.p);
+  } else {
+    wk.X.ensure(c->alloc, n);
+    wk.Y.ensure(c->alloc, n);
+    apply_A_t<double>(c, wk, nsys, v, w, wk.X.p, wk.Y.p);
+  }
 }
 
 static void apply_Qmat(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, int mode) {
@@ -571,8 +596,8 @@ static void apply_Qinv(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* z) {
     return;
   }
   if (wk.banded) {
-    band_apply(c, nsys, wk.nport, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.Wb.p, wk.Sinv.p, v, z, wk.bscr.p,
-               wk.active.p, s);
+    band_apply(c, nsys, wk.nport, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.facT.p, wk.fac32.p, wk.facT32.p, wk.Wb.p,
+               wk.Sinv.p, v, z, wk.bscr.p, wk.active.p, s);
     return;
   }
   const size_t tot = (size_t)n * nsys;
@@ -635,6 +660,9 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
   wk.g.alloc(c->alloc, (size_t)nsys * (m + 1));
   wk.y.alloc(c->alloc, (size_t)nsys * m);
   wk.bnorm.alloc(c->alloc, nsys);
+  wk.thr.alloc(c->alloc, nsys);
+  const bool mixed = c->opt.precision == 1;
+  const double tau = mixed ? 1e-5 : 0.0;
   wk.resid.alloc(c->alloc, nsys);
   wk.active.alloc(c->alloc, nsys);
   wk.iters.alloc(c->alloc, nsys);
@@ -643,10 +671,15 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
   if (wk.banded) {
     const Topo& TT = c->topo;
     wk.fac.alloc(c->alloc, (size_t)nf * TT.n_band * (TT.band + 1));
+    wk.facT.alloc(c->alloc, (size_t)nf * TT.n_band * (TT.band + 1));
     wk.Wb.alloc(c->alloc, (size_t)nf * std::max(1, TT.n_border) * TT.n_band);
     wk.Sinv.alloc(c->alloc, (size_t)nf * std::max(1, TT.n_border * TT.n_border));
-    wk.bscr.alloc(c->alloc, (size_t)nsys * TT.n_band);
-    band_factor(c, nf, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.Wb.p, wk.Sinv.p, s);
+    wk.bscr.alloc(c->alloc, (size_t)nsys * (TT.n_band + 2));
+    if (mixed) {
+      wk.fac32.alloc(c->alloc, (size_t)nf * TT.n_band * ((TT.band + 2) & ~1));
+      wk.facT32.alloc(c->alloc, (size_t)nf * TT.n_band * ((TT.band + 2) & ~1));
+    }
+    band_factor(c, nf, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.facT.p, wk.fac32.p, wk.facT32.p, wk.Wb.p, wk.Sinv.p, s);
   } else if (c->opt.precond) {
     wk.dinv.alloc(c->alloc, tot);
     apply_Qmat(c, wk, nsys, nullptr, wk.w.p, 1);
@@ -669,7 +702,7 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
     // restart: true residual with the FP64 operator
     if (!first) apply_A(c, wk, nsys, wk.x.p, wk.w.p);
     k_restart<<<nsys, 256, 0, s>>>(n, nsys, m, wk.b.p, first ? nullptr : wk.w.p, wk.V.p, wk.g.p, wk.bnorm.p, tol,
-                                   wk.active.p, wk.resid.p);
+                                   tau, wk.active.p, wk.resid.p, wk.thr.p);
     count_launch(c);
     first = false;
     XRL_CUDA(cudaMemcpyAsync(hact.data(), wk.active.p, sizeof(int) * nsys, cudaMemcpyDeviceToHost, s));
@@ -685,7 +718,7 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
       cplx* vj = wk.V.p + (size_t)j * tot;
       cplx* zj = wk.Z.p + (size_t)j * tot;
       apply_Qinv(c, wk, nsys, vj, zj);
-      apply_A(c, wk, nsys, zj, wk.w.p);
+      apply_A(c, wk, nsys, zj, wk.w.p, mixed);
       // CGS2
       cudaEvent_t evk = prof_begin(c, s);
       k_arnoldi_dots<<<dim3(j + 1, nsys), 256, 0, s>>>(n, nsys, j, m + 1, wk.V.p, wk.w.p, wk.h1.p, wk.active.p);
@@ -697,7 +730,7 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
         if (hact[q]) hk[q] = j + 1;
       k_arnoldi_norm<<<nsys, 256, 0, s>>>(n, nsys, j, m, wk.H.p, wk.h1.p, wk.h2.p, wk.w.p,
                                           wk.V.p + (size_t)(j + 1) * tot, wk.cs.p, wk.sn.p, wk.g.p, wk.active.p,
-                                          wk.bnorm.p, tol, wk.resid.p, wk.iters.p);
+                                          wk.bnorm.p, wk.thr.p, wk.resid.p, wk.iters.p);
       prof_end(c, s, evk, PH_KRYLOV, 5, 4.0 * 8.0 * (j + 1) * tot + 10.0 * tot,
                16.0 * (4.0 * (j + 1) * tot + 4.0 * tot));
       XRL_CUDA(cudaGetLastError());
@@ -720,8 +753,8 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
     if (total >= c->opt.max_iters) {
       // final true residual for the stats
       apply_A(c, wk, nsys, wk.x.p, wk.w.p);
-      k_restart<<<nsys, 256, 0, s>>>(n, nsys, m, wk.b.p, wk.w.p, wk.V.p, wk.g.p, wk.bnorm.p, tol, wk.active.p,
-                                     wk.resid.p);
+      k_restart<<<nsys, 256, 0, s>>>(n, nsys, m, wk.b.p, wk.w.p, wk.V.p, wk.g.p, wk.bnorm.p, tol, tau,
+                                     wk.active.p, wk.resid.p, wk.thr.p);
       done = true;
     }
   }
@@ -765,12 +798,13 @@ void apply_operator_host(xrl_ctx* c, int nsys, const double* freq, const double*
   } else if (mode == 2) {
     const Topo& TT = c->topo;
     wk.fac.alloc(c->alloc, (size_t)nsys * TT.n_band * (TT.band + 1));
+    wk.facT.alloc(c->alloc, (size_t)nsys * TT.n_band * (TT.band + 1));
     wk.Wb.alloc(c->alloc, (size_t)nsys * std::max(1, TT.n_border) * TT.n_band);
     wk.Sinv.alloc(c->alloc, (size_t)nsys * std::max(1, TT.n_border * TT.n_border));
-    wk.bscr.alloc(c->alloc, (size_t)nsys * TT.n_band);
-    band_factor(c, nsys, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.Wb.p, wk.Sinv.p, c->stream);
-    band_apply(c, nsys, 1, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.Wb.p, wk.Sinv.p, dv.p, dw.p, wk.bscr.p, nullptr,
-               c->stream);
+    wk.bscr.alloc(c->alloc, (size_t)nsys * (TT.n_band + 2));
+    band_factor(c, nsys, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.facT.p, nullptr, nullptr, wk.Wb.p, wk.Sinv.p, c->stream);
+    band_apply(c, nsys, 1, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.facT.p, nullptr, nullptr, wk.Wb.p, wk.Sinv.p, dv.p,
+               dw.p, wk.bscr.p, nullptr, c->stream);
   } else {
     apply_A(c, wk, nsys, dv.p, dw.p);
   }

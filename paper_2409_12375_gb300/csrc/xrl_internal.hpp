@@ -174,6 +174,8 @@ struct Dev {
   DBuf<int32_t> near_w;                              // per leaf: block width
   DBuf<double> near_val;                             // values
   DBuf<float> near_val32;                            // FP32 copy (mixed precision)
+  DBuf<int64_t> near_col_off;                         // per leaf: offset into near_src
+  DBuf<int32_t> near_src;                             // per leaf: Morton index of each near column
   DBuf<double> mom;                                  // [N][ncoef] P2M moments (leaf-scaled)
   DBuf<float> mom32;
   DBuf<double> t_m2m, t_l2l, t_m2l;                  // translation matrices (transposed)
@@ -230,7 +232,7 @@ struct xrl_ctx {
   std::vector<double> sigma, thick;
   std::vector<std::vector<int32_t>> port_src, port_sink;
   bool have_mesh = false, have_cond = false, ready = false;
-  int N = 0, ncoef = 0, p = 0;
+  int N = 0, ncoef = 0, p = 0, max_leaf = 0;
   xrl::Tree tree;
   xrl::Topo topo;
   xrl::Dev d;
@@ -277,9 +279,9 @@ void apply_operator_host(xrl_ctx* c, int nsys, const double* f, const double* v,
 // precond.cu
 bool band_usable(const xrl_ctx* c);
 void band_prepare(xrl_ctx* c);
-void band_factor(xrl_ctx* c, int nf, const double2* zs, const double* wp, double2* fac, double2* Wb, double2* Sinv,
-                 cudaStream_t s);
+void band_factor(xrl_ctx* c, int nf, const double2* zs, const double* wp, double2* fac, double2* facT, float2* fac32,
+                 float2* facT32, double2* Wb, double2* Sinv, cudaStream_t s);
 void band_apply(xrl_ctx* c, int nsys, int nport, const double2* zs, const double* wp, const double2* fac,
-                const double2* Wb, const double2* Sinv, const double2* v, double2* z, double2* scratch,
-                const int* active, cudaStream_t s);
+                const double2* facT, const float2* fac32, const float2* facT32, const double2* Wb,
+                const double2* Sinv, const double2* v, double2* z, void* scratch, const int* active, cudaStream_t s);
 }  // namespace xrl

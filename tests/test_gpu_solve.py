@@ -127,6 +127,19 @@ def test_bar_sweep_matches_oracle(bar_ctx, bar_circ, bar_dense_P, bar_mesh):
     assert st["max_rel_res"] <= 1e-8
 
 
+def test_mixed_precision_sweep_matches_oracle(lib, bar_circ, bar_dense_P, bar_mesh):
+    """FP32 FMM inside FP64 FGMRES-IR: the final FP64 residual still reaches
+    1e-8 and R, L match the oracle to 1e-4."""
+    x = lib.XRL.from_mesh(bar_mesh, fmm_order=8, precision=1)
+    f = bar_mesh.freqs
+    R, L = x.solve(f)
+    Ro, Lo, _ = bar_circ.solve(f, bar_dense_P)
+    assert np.max(np.abs(R - Ro) / np.abs(Ro)) < 1e-4
+    assert np.max(np.abs(L - Lo) / np.abs(Lo)) < 1e-4
+    assert x.stats()["max_rel_res"] <= 1e-8
+    x.close()
+
+
 def test_bar_low_frequency_resistance(bar_ctx):
     R, L = bar_ctx.solve(np.array([1e-3]))
     rho_l_a = 10e-3 / (5.8e7 * 1e-6)
