@@ -90,7 +90,8 @@ __global__ void k_p2p(int nc, int ct, const int32_t* __restrict__ leaf_first, co
 
 // FP32 near field, shared-memory tiled: one block per (leaf, 64-column tile,
 // 64-row block), 128 threads as 16 row groups x 8 column groups; thread
-// (ty, tx) owns rows ty + 16 i (i < 4) and columns 8 tx .. 8 tx + 7.  The
+// (ty, tx) owns rows ty + 16 i (i < 4) and columns 4 tx + j, 32 + 4 tx + j
+// (j < 4).  The
 // leaf's value block (row-major, width w) and the gathered source rows of X
 // stream through shared memory in K-chunks of 32 near columns.
 __global__ void __launch_bounds__(128) k_p2p_tiled(int nc, const int32_t* __restrict__ leaf_first,
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(128) k_p2p_tiled(int nc, const int32_t* __rest
                                                    const float* __restrict__ val, const float* __restrict__ X,
                                                    float* __restrict__ Y) {
   constexpr int CT = 64, KC = 32, RB = 64;
-  __shared__ __align__(16) float Vs[KC][RB];     // transposed value chunk: [near column][row]
+  __shared__ __align__(16) float Vs[KC][RB + 4];  // transposed value chunk: [near column][row], padded
   __shared__ __align__(16) float Xs[KC][CT];
   const int B = blockIdx.x;
   const int c0 = blockIdx.y * CT;
@@ -130,8 +131,9 @@ __global__ void __launch_bounds__(128) k_p2p_tiled(int nc, const int32_t* __rest
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < KC; ++kk) {
-      const float4 x0 = *reinterpret_cast<const float4*>(&Xs[kk][8 * tx]);
-      const float4 x1 = *reinterpret_cast<const float4*>(&Xs[kk][8 * tx + 4]);
+      // columns 4 tx .. 4 tx + 3 and 32 + 4 tx .. : a quarter-warp's 16-byte loads are contiguous
+      const float4 x0 = *reinterpret_cast<const float4*>(&Xs[kk][4 * tx]);
+      const float4 x1 = *reinterpret_cast<const float4*>(&Xs[kk][32 + 4 * tx]);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const float v = Vs[kk][ty + 16 * i];
@@ -152,8 +154,10 @@ __global__ void __launch_bounds__(128) k_p2p_tiled(int nc, const int32_t* __rest
     if (r >= nr) continue;
     float* yr = Y + (size_t)(f0 + rb0 + r) * nc + c0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if (c0 + 8 * tx + j < nc) yr[8 * tx + j] = acc[i][j];
+    for (int j = 0; j < 8; ++j) {
+      const int cc = (j < 4) ? 4 * tx + j : 32 + 4 * tx + (j - 4);
+      if (c0 + cc < nc) yr[cc] = acc[i][j];
+    }
   }
 }
 
@@ -224,7 +228,7 @@ __global__ void k_m2l(int nc, int ct, int ncoef, int b0, const int32_t* __restri
 
 // M2L, FP32, shared-memory tiled: one block per (target box, 64-column tile),
 // 128 threads as 16 row groups x 8 column groups; thread (ty, tx) owns rows
-// ty + 16 i (i < RI) and the 8 consecutive columns 8 tx .. 8 tx + 7.  Per
+// ty + 16 i (i < RI) and columns 4 tx + j, 32 + 4 tx + j (j < 4).  Per
 // V-list pair the translation matrix (stored [in][out]) and the source
 // multipole tile are staged in shared memory; the inner loop does 8 RI FMAs
 // per RI + 2 shared loads (float4 for the columns).
@@ -262,8 +266,8 @@ __global__ void __launch_bounds__(128) k_m2l_tiled(int nc, int ncoef, int b0, co
     }
     __syncthreads();
     for (int j = 0; j < ncoef; ++j) {
-      const float4 m0 = *reinterpret_cast<const float4*>(Ms + j * CT + 8 * tx);
-      const float4 m1 = *reinterpret_cast<const float4*>(Ms + j * CT + 8 * tx + 4);
+      const float4 m0 = *reinterpret_cast<const float4*>(Ms + j * CT + 4 * tx);
+      const float4 m1 = *reinterpret_cast<const float4*>(Ms + j * CT + 32 + 4 * tx);
       const float* tr = Ts + j * ld + ty;
 #pragma unroll
       for (int i = 0; i < RI; ++i) {
@@ -286,21 +290,112 @@ __global__ void __launch_bounds__(128) k_m2l_tiled(int nc, int ncoef, int b0, co
     if (k >= ncoef) continue;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      int cc = 8 * tx + j;
+      const int cc = (j < 4) ? 4 * tx + j : 32 + 4 * tx + (j - 4);
       if (c0 + cc < nc) out[(size_t)k * nc + cc] = acc[i][j];
+    }
+  }
+}
+
+// M2L with FP64 operands evaluated on the FP32 pipes ("double-float"): each
+// double is split into hi = fl32(x), lo = fl32(x - hi) when staged in shared
+// memory, products use the FMA error-free transformation, and every output
+// accumulates as an unevaluated float pair with TwoSum (Knuth), about 13 FP32
+// operations per multiply-add and ~2^-44 relative rounding, against GB300's
+// thin FP64 pipe.  One block per (target box, 64-column tile), 256 threads as
+// 32 row groups x 8 column groups, rows ty + 32 i (i < 3, ncoef <= 96),
+// columns 4 tx + j and 32 + 4 tx + j (j < 4).
+__global__ void __launch_bounds__(256) k_m2l_df64(int nc, int ncoef, int b0, const int32_t* __restrict__ v_ptr,
+                                                  const int32_t* __restrict__ v_src, const int16_t* __restrict__ v_off,
+                                                  const double* __restrict__ Tt, const double* __restrict__ M,
+                                                  double* __restrict__ L) {
+  constexpr int CT = 64, RI = 3, LD = 96;
+  extern __shared__ float2 smd[];
+  float2* Ts = smd;                 // [ncoef][LD]  (hi, lo)
+  float2* Ms = smd + ncoef * LD;    // [ncoef][CT]
+  const int Bx = b0 + blockIdx.x;
+  const int c0 = blockIdx.y * CT;
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  const int vs = v_ptr[Bx], ve = v_ptr[Bx + 1];
+  const size_t ne = (size_t)ncoef * nc;
+  float sh[RI][8], sl[RI][8];
+#pragma unroll
+  for (int i = 0; i < RI; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sh[i][j] = sl[i][j] = 0.f;
+  for (int v = vs; v < ve; ++v) {
+    const double* tm = Tt + (size_t)v_off[v] * ncoef * ncoef;
+    const double* ms = M + (size_t)v_src[v] * ne + c0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < ncoef * LD; e += 256) {
+      int j = e / LD, k = e % LD;
+      double x = k < ncoef ? tm[(size_t)j * ncoef + k] : 0.0;
+      float hi = __double2float_rn(x);
+      Ts[e] = make_float2(hi, __double2float_rn(x - (double)hi));
+    }
+    for (int e = threadIdx.x; e < ncoef * CT; e += 256) {
+      int j = e / CT, cc = e % CT;
+      double x = (c0 + cc < nc) ? ms[(size_t)j * nc + cc] : 0.0;
+      float hi = __double2float_rn(x);
+      Ms[e] = make_float2(hi, __double2float_rn(x - (double)hi));
+    }
+    __syncthreads();
+    for (int j = 0; j < ncoef; ++j) {
+      float2 m[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        m[q] = Ms[j * CT + 4 * tx + q];
+        m[4 + q] = Ms[j * CT + 32 + 4 * tx + q];
+      }
+#pragma unroll
+      for (int i = 0; i < RI; ++i) {
+        const float2 t = Ts[j * LD + ty + 32 * i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float p = t.x * m[q].x;
+          const float pe = fmaf(t.x, m[q].x, -p);                 // exact product error
+          const float cr = fmaf(t.x, m[q].y, t.y * m[q].x);       // cross terms
+          const float s = sh[i][q] + p;                           // TwoSum(sh, p)
+          const float bp = s - sh[i][q];
+          const float e = (sh[i][q] - (s - bp)) + (p - bp);
+          sl[i][q] += e + pe + cr;
+          sh[i][q] = s;
+        }
+      }
+    }
+  }
+  double* out = L + (size_t)Bx * ne + c0;
+#pragma unroll
+  for (int i = 0; i < RI; ++i) {
+    int k = ty + 32 * i;
+    if (k >= ncoef) continue;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int cc = (q < 4) ? 4 * tx + q : 32 + 4 * tx + (q - 4);
+      if (c0 + cc < nc) out[(size_t)k * nc + cc] = (double)sh[i][q] + (double)sl[i][q];
     }
   }
 }
 
 template <class T>
 static void launch_m2l(int nbx, int b0, int nc, int ct_e, int ncoef, const int32_t* vptr, const int32_t* vsrc,
-                       const int16_t* voff, const T* tm2l, const T* Mx, T* Lx, cudaStream_t s) {
+                       const int16_t* voff, const T* tm2l, const T* Mx, T* Lx, cudaStream_t s, bool df64) {
+  if (sizeof(T) == 8 && df64 && nc >= 32 && ncoef <= 96) {
+    static bool set = false;
+    const size_t sm = sizeof(float2) * (size_t)ncoef * (96 + 64);
+    if (!set) {
+      XRL_CUDA(cudaFuncSetAttribute(k_m2l_df64, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 160 * 8));
+      set = true;
+    }
+    k_m2l_df64<<<dim3(nbx, (nc + 63) / 64), 256, sm, s>>>(nc, ncoef, b0, vptr, vsrc, voff, (const double*)tm2l,
+                                                          (const double*)Mx, (double*)Lx);
+    return;
+  }
   k_m2l<T><<<dim3(nbx, (nc + ct_e - 1) / ct_e), 256, 0, s>>>(nc, ct_e, ncoef, b0, vptr, vsrc, voff, tm2l, Mx, Lx);
 }
 
 template <>
 void launch_m2l<float>(int nbx, int b0, int nc, int ct_e, int ncoef, const int32_t* vptr, const int32_t* vsrc,
-                       const int16_t* voff, const float* tm2l, const float* Mx, float* Lx, cudaStream_t s) {
+                       const int16_t* voff, const float* tm2l, const float* Mx, float* Lx, cudaStream_t s, bool) {
   if (nc < 32 || ncoef > 16 * 11) {
     k_m2l<float><<<dim3(nbx, (nc + ct_e - 1) / ct_e), 256, 0, s>>>(nc, ct_e, ncoef, b0, vptr, vsrc, voff, tm2l, Mx,
                                                                    Lx);
@@ -478,7 +573,7 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     int b0 = t.level_off[2];
     int nbx = t.level_off[L + 1] - b0;
     ev = prof_begin(c, s);
-    launch_m2l<T>(nbx, b0, nc, ct_e, ncoef, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p, tm2l, Mx, Lx, s);
+    launch_m2l<T>(nbx, b0, nc, ct_e, ncoef, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p, tm2l, Mx, Lx, s, c->df64_m2l);
     prof_end(c, s, ev, PH_M2L, 1, e2 * (double)t.v_src.size(), 2.0 * nbx * ebytes);
   }
   ev = prof_begin(c, s);

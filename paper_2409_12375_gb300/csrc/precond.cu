@@ -247,6 +247,96 @@ __device__ void band_solve_warp(int n, int b, int rs, const C* __restrict__ facT
   }
 }
 
+// Two systems that share one factor (the two ports of one frequency) per
+// warp, 16 lanes each, for half-widths b <= 15: row k's pending sum lives in
+// half-lane k % 16.  The factor chunks are shared by both halves; each half
+// streams its own right-hand side (x0, x1, in place).
+template <class C>
+__device__ void band_solve_pair(int n, int b, int rs, const C* __restrict__ facT, const C* __restrict__ fac, C* x0,
+                                C* x1, C* smem) {
+  const int lane = threadIdx.x & 31;
+  const int h = lane >> 4, hl = lane & 15;
+  const int ch = band_chunk(b);
+  const size_t fstride = (size_t)ch * rs;
+  C* fbuf = smem;                       // [2][ch * rs]
+  C* vbuf = smem + 2 * fstride;         // [2 buffers][2 halves][ch]
+  const int nchunk = (n + ch - 1) / ch;
+  C* xh = h ? x1 : x0;
+  auto issue = [&](const C* F, int r0, int r1, int buf) {
+    constexpr int per = 16 / sizeof(C);
+    const int nf = (r1 - r0) * rs;
+    const C* src = F + (size_t)r0 * rs;
+    C* fb = fbuf + buf * fstride;
+    for (int e = per * lane; e < nf; e += 32 * per) cp_async16(fb + e, src + e);
+    C* vb = vbuf + (buf * 2 + h) * ch;
+    for (int e = per * hl; e < r1 - r0; e += 16 * per) cp_async16(vb + e, xh + r0 + e);
+    cp_commit();
+  };
+  __threadfence();
+  __syncwarp();
+  C acc = czero<C>();
+  issue(facT, 0, min(n, ch), 0);
+  for (int c = 0; c < nchunk; ++c) {
+    const int r0 = c * ch, r1 = min(n, r0 + ch);
+    const bool more = c + 1 < nchunk;
+    if (more) issue(facT, r1, min(n, r1 + ch), (c + 1) & 1);
+    if (more) cp_wait_all_but_one(); else cp_wait_all();
+    __syncwarp();
+    const C* fr = fbuf + (c & 1) * fstride;
+    const C* vr = vbuf + ((c & 1) * 2 + h) * ch;
+    for (int i = r0; i < r1; ++i) {
+      const C* col = fr + (size_t)(i - r0) * rs;
+      const int own = i & 15;
+      const int t = (hl - i - 1) & 15;
+      const C lv = col[t < b ? t : 0];          // independent of y: load early
+      C y = czero<C>();
+      if (hl == own) {
+        y = csubT(vr[i - r0], acc);
+        acc = czero<C>();
+      }
+      y.x = __shfl_sync(0xffffffffu, y.x, own, 16);
+      y.y = __shfl_sync(0xffffffffu, y.y, own, 16);
+      if (hl == own) xh[i] = cmul(y, col[b]);
+      if (t < b && i + 1 + t < n) acc = cfma(lv, y, acc);
+    }
+    __syncwarp();
+  }
+  __syncwarp();
+  __threadfence();
+  __syncwarp();
+  acc = czero<C>();
+  {
+    const int c = nchunk - 1;
+    issue(fac, c * ch, n, c & 1);
+  }
+  for (int c = nchunk - 1; c >= 0; --c) {
+    const int r0 = c * ch, r1 = min(n, r0 + ch);
+    const bool more = c > 0;
+    if (more) issue(fac, r0 - ch, r0, (c - 1) & 1);
+    if (more) cp_wait_all_but_one(); else cp_wait_all();
+    __syncwarp();
+    const C* fr = fbuf + (c & 1) * fstride;
+    const C* vr = vbuf + ((c & 1) * 2 + h) * ch;
+    for (int i = r1 - 1; i >= r0; --i) {
+      const C* row = fr + (size_t)(i - r0) * rs;
+      const int own = i & 15;
+      const int k = i - 1 - ((i - 1 - hl) & 15);
+      const bool upd = k >= 0 && k >= i - b;
+      const C lv = row[upd ? k - i + b : 0];
+      C z = czero<C>();
+      if (hl == own) {
+        z = csubT(vr[i - r0], acc);
+        acc = czero<C>();
+      }
+      z.x = __shfl_sync(0xffffffffu, z.x, own, 16);
+      z.y = __shfl_sync(0xffffffffu, z.y, own, 16);
+      if (hl == own) xh[i] = z;
+      if (upd) acc = cfma(lv, z, acc);
+    }
+    __syncwarp();
+  }
+}
+
 // 1/D on the diagonal; the column-form copy facT (facT[i][t] = L[i+1+t][i],
 // facT[i][b] = 1/D_i); optional FP32 copies of both (row stride even).
 // One thread per (frequency row, entry).
@@ -411,6 +501,77 @@ __global__ void k_band_apply(int nloop, int n, int b, int ng, int nport, int nma
   }
 }
 
+// as k_band_apply, two systems (consecutive, same frequency) per warp
+template <class C>
+__global__ void k_band_apply_pair(int nloop, int n, int b, int ng, int nport, int nmat, const int32_t* __restrict__ perm,
+                                  const double* __restrict__ border_vg, const cplx* __restrict__ zs,
+                                  const double* __restrict__ wp_f, const C* __restrict__ fac,
+                                  const C* __restrict__ facT, const cplx* __restrict__ Wb,
+                                  const cplx* __restrict__ Sinv, const cplx* __restrict__ v, cplx* __restrict__ z,
+                                  C* __restrict__ scratch) {
+  extern __shared__ __align__(16) unsigned char bsm_raw[];
+  C* bsm = reinterpret_cast<C*>(bsm_raw);
+  __shared__ cplx tg[2][kMaxBorder], zg[2][kMaxBorder];
+  const int s0 = 2 * blockIdx.x;
+  const int f = s0 / nport;
+  const int lane = threadIdx.x & 31;
+  const size_t xs = (size_t)((n + 2) & ~1);
+  C* x0 = scratch + (size_t)s0 * xs;
+  C* x1 = x0 + xs;
+  for (int q = 0; q < 2; ++q) {
+    const cplx* vs = v + (size_t)(s0 + q) * nloop;
+    C* x = q ? x1 : x0;
+    for (int i = lane; i < n; i += 32) {
+      cplx vi = vs[perm[i]];
+      if (sizeof(C) == 8) reinterpret_cast<float2*>(x)[i] = make_float2((float)vi.x, (float)vi.y);
+      else reinterpret_cast<cplx*>(x)[i] = vi;
+    }
+  }
+  __syncwarp();
+  const int rs = band_rs<C>(b);
+  band_solve_pair<C>(n, b, rs, facT + (size_t)f * n * rs, fac + (size_t)f * n * rs, x0, x1, bsm);
+  for (int q = 0; q < 2; ++q) {
+    const C* x = q ? x1 : x0;
+    const cplx* vs = v + (size_t)(s0 + q) * nloop;
+    cplx* zo = z + (size_t)(s0 + q) * nloop;
+    auto xval = [&](int i) -> cplx {
+      if (sizeof(C) == 8) {
+        float2 t = reinterpret_cast<const float2*>(x)[i];
+        return make_double2(t.x, t.y);
+      }
+      return reinterpret_cast<const cplx*>(x)[i];
+    };
+    if (ng > 0) {
+      const cplx* zf = zs + (size_t)f * nmat;
+      const double wp = wp_f[f];
+      const size_t vstride = (size_t)n * ng;
+      for (int g = 0; g < ng; ++g) {
+        cplx acc = make_double2(0, 0);
+        for (int i = lane; i < n; i += 32) acc = cadd(acc, cm(pencil(border_vg + (size_t)i * ng + g, vstride, nmat, zf, wp), xval(i)));
+        acc = warp_sum(acc);
+        if (lane == 0) tg[q][g] = csub(vs[n + g], acc);
+      }
+      __syncwarp();
+      if (lane < ng) {
+        cplx acc = make_double2(0, 0);
+        for (int g2 = 0; g2 < ng; ++g2) acc = cadd(acc, cm(Sinv[((size_t)f * ng + lane) * ng + g2], tg[q][g2]));
+        zg[q][lane] = acc;
+      }
+      __syncwarp();
+      for (int i = lane; i < n; i += 32) {
+        cplx acc = xval(i);
+        for (int g = 0; g < ng; ++g) acc = csub(acc, cm(Wb[((size_t)f * ng + g) * n + i], zg[q][g]));
+        zo[perm[i]] = acc;
+      }
+      __syncwarp();
+      if (lane < ng) zo[n + lane] = zg[q][lane];
+    } else {
+      for (int i = lane; i < n; i += 32) zo[perm[i]] = xval(i);
+    }
+    __syncwarp();
+  }
+}
+
 // ---- host ---------------------------------------------------------------------------------
 bool band_usable(const xrl_ctx* c) {
   return c->topo.band <= kMaxBand && c->topo.n_border <= kMaxBorder && c->topo.n_band > 0;
@@ -457,7 +618,24 @@ void band_apply(xrl_ctx* c, int nsys, int nport, const cplx* zs, const double* w
                 const cplx* v, cplx* z, void* scratch, const int* active, cudaStream_t s) {
   const Topo& T = c->topo;
   cudaEvent_t ev = prof_begin(c, s);
-  if (fac32) {
+  // systems 2q, 2q+1 share a frequency when nport is even; converged systems are
+  // recomputed harmlessly on this path (their results are not used)
+  const bool pair = T.band <= 15 && nport % 2 == 0 && nsys % 2 == 0;
+  if (pair) {
+    if (fac32) {
+      const size_t bs = sizeof(float2) * ((size_t)2 * band_chunk(T.band) * band_rs<float2>(T.band) +
+                                          4 * (size_t)band_chunk(T.band));
+      k_band_apply_pair<float2><<<nsys / 2, 32, bs, s>>>(T.n_loops, T.n_band, T.band, T.n_border, nport, T.n_mat,
+                                                         c->d.band_perm.p, c->d.border_vg.p, zs, wp, fac32, facT32,
+                                                         Wb, Sinv, v, z, (float2*)scratch);
+    } else {
+      const size_t bs = sizeof(cplx) * ((size_t)2 * band_chunk(T.band) * band_rs<cplx>(T.band) +
+                                        4 * (size_t)band_chunk(T.band));
+      k_band_apply_pair<cplx><<<nsys / 2, 32, bs, s>>>(T.n_loops, T.n_band, T.band, T.n_border, nport, T.n_mat,
+                                                       c->d.band_perm.p, c->d.border_vg.p, zs, wp, fac, facT, Wb,
+                                                       Sinv, v, z, (cplx*)scratch);
+    }
+  } else if (fac32) {
     const size_t bs = band_smem_bytes<float2>(T.band) + 64;
     if (bs > 48 * 1024)
       XRL_CUDA(cudaFuncSetAttribute(k_band_apply<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs));

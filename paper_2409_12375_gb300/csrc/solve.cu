@@ -663,6 +663,13 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
   wk.thr.alloc(c->alloc, nsys);
   const bool mixed = c->opt.precision == 1;
   const double tau = mixed ? 1e-5 : 0.0;
+  // refinement residuals of the mixed mode: FP64-accurate M2L on the FP32 pipes
+  struct Df64Guard {
+    xrl_ctx* c;
+    bool old;
+    ~Df64Guard() { c->df64_m2l = old; }
+  } df64_guard{c, c->df64_m2l};
+  c->df64_m2l = mixed;
   wk.resid.alloc(c->alloc, nsys);
   wk.active.alloc(c->alloc, nsys);
   wk.iters.alloc(c->alloc, nsys);

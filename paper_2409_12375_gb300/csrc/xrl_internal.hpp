@@ -233,6 +233,7 @@ struct xrl_ctx {
   std::vector<std::vector<int32_t>> port_src, port_sink;
   bool have_mesh = false, have_cond = false, ready = false;
   int N = 0, ncoef = 0, p = 0, max_leaf = 0;
+  bool df64_m2l = false;   // FP64 M2L on the FP32 pipes (set inside mixed-precision solves)
   xrl::Tree tree;
   xrl::Topo topo;
   xrl::Dev d;
