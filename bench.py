@@ -268,21 +268,28 @@ def main():
     pk = peaks()
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
-    lowp = args.precision == "mixed" and dom in ("p2p", "p2m", "m2m", "m2l", "l2l", "l2p")
     avg_ms = d["ms"] / max(1, d["launches"])
-    if dom in ("p2p", "p2m", "m2m", "m2l", "l2l", "l2p"):
-        # FP64 launches (the refinement residuals) and FP32 launches share a phase
-        # in the mixed mode; report the phase's mean rate against the FP32 peak
-        peak = pk["fp32_tflops"] if lowp else pk["fp64_tflops"]
+    # kernel of each phase and its ncu DRAM traffic per launch (bytes) where a
+    # capture of the unchanged kernel exists (profiles/top_kernels_coil_sweep.md)
+    kern = {"m2l": "k_m2l_tiled<6> (FP32)", "p2p": "k_p2p_tiled (FP32)", "precond": "k_band_apply_pair/k_band_factor",
+            "m2l64": "k_m2l_df64 / k_m2l<double>", "p2p64": "k_p2p<double>"}
+    traffic = {"m2l": 71.785e6 + 34.6816e6, "p2p": 1018.708e6 + 36.329728e6}
+    fp32_phase = {"p2p", "p2m", "m2m", "m2l", "l2l", "l2p"}
+    if dom in fp32_phase or dom in ("p2p64", "m2l64"):
+        lowp = dom in fp32_phase and args.precision == "mixed"
+        # the double-float M2L of the mixed mode runs on the FP32 pipes
+        fp32_pipes = lowp or (dom == "m2l64" and args.precision == "mixed")
+        peak = pk["fp32_tflops"] if fp32_pipes else pk["fp64_tflops"]
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock" if lowp else
+        roof = {"kernel": kern.get(dom, dom), "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic.get(dom) if lowp else None,
+                "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock" if fp32_pipes else
                             "nominal GB300 FP64 (1.25 TFLOP/s)",
                 "avg_launch_ms": avg_ms, "launches": d["launches"]}
     else:
         achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+        roof = {"kernel": kern.get(dom, dom), "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_src": pk["hbm_src"],
                 "avg_launch_ms": avg_ms, "launches": d["launches"]}
 

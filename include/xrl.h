@@ -215,8 +215,10 @@ xrl_status xrl_export_lists(const xrl_ctx* ctx, int32_t level, int32_t* n_boxes,
 
 /* Per-phase device timing, recorded with CUDA events on the stream each
  * phase's kernels run on, while profiling is switched on (xrl_set_profiling).
- * phase: 0 P2P near field, 1 P2M, 2 M2M, 3 M2L, 4 L2L, 5 L2P, 6 operator
- * gather/scatter, 7 preconditioner (inner COCG), 8 Arnoldi/FGMRES updates.
+ * phase: 0 P2P near field (FP32), 1 P2M, 2 M2M, 3 M2L (FP32), 4 L2L, 5 L2P,
+ * 6 operator gather/scatter, 7 preconditioner (factor and solves), 8
+ * Arnoldi/FGMRES updates, 9 P2P near field (FP64), 10 M2L (FP64: native, or
+ * double-float on the FP32 pipes inside mixed-precision solves).
  * ms = summed event time, launches = kernel launches, flops / bytes =
  * algorithmic work (not counters) summed over those launches.  Reading
  * synchronises the context's stream.  xrl_kernel_launches returns every

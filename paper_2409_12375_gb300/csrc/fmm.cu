@@ -551,7 +551,7 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     k_p2p<T><<<gp, 128, 0, s>>>(nc, ct_p, c->d.leaf_first.p, c->d.leaf_count.p, c->d.u_ptr32.p, c->d.u_src.p,
                                 c->d.near_off.p, c->d.near_w.p, near, X, Y);
   }
-  prof_end(c, s, ev, PH_P2P, 1, 2.0 * nne * nc, nne * sz + 2.0 * N * nc * sz);
+  prof_end(c, s, ev, sizeof(T) == 8 ? PH_P2P64 : PH_P2P, 1, 2.0 * nne * nc, nne * sz + 2.0 * N * nc * sz);
   const int ecols = (nc + ct_e - 1) / ct_e;
   const int leaf0 = t.level_off[L];
   ev = prof_begin(c, s);
@@ -574,7 +574,7 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     int nbx = t.level_off[L + 1] - b0;
     ev = prof_begin(c, s);
     launch_m2l<T>(nbx, b0, nc, ct_e, ncoef, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p, tm2l, Mx, Lx, s, c->df64_m2l);
-    prof_end(c, s, ev, PH_M2L, 1, e2 * (double)t.v_src.size(), 2.0 * nbx * ebytes);
+    prof_end(c, s, ev, sizeof(T) == 8 ? PH_M2L64 : PH_M2L, 1, e2 * (double)t.v_src.size(), 2.0 * nbx * ebytes);
   }
   ev = prof_begin(c, s);
   for (int l = 3; l <= L; ++l) {

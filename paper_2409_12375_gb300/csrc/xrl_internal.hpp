@@ -205,7 +205,8 @@ struct Dev {
 };
 
 // Phase profiler: CUDA event pairs on the launching stream plus algorithmic work.
-enum Phase { PH_P2P = 0, PH_P2M, PH_M2M, PH_M2L, PH_L2L, PH_L2P, PH_OPER, PH_PREC, PH_KRYLOV, PH_COUNT };
+enum Phase { PH_P2P = 0, PH_P2M, PH_M2M, PH_M2L, PH_L2L, PH_L2P, PH_OPER, PH_PREC, PH_KRYLOV, PH_P2P64, PH_M2L64,
+             PH_COUNT };
 struct Prof {
   bool on = false;
   struct Rec {

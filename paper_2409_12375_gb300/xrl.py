@@ -224,7 +224,7 @@ class XRL:
         return w
 
     # ---- profiling ---------------------------------------------------------------
-    PHASES = ["p2p", "p2m", "m2m", "m2l", "l2l", "l2p", "operator", "precond", "krylov"]
+    PHASES = ["p2p", "p2m", "m2m", "m2l", "l2l", "l2p", "operator", "precond", "krylov", "p2p64", "m2l64"]
 
     def set_profiling(self, on=True):
         self._check(lib().xrl_set_profiling(self.h, 1 if on else 0), self.h)
