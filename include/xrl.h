@@ -213,6 +213,67 @@ xrl_status xrl_export_loops(const xrl_ctx* ctx, int64_t* row_ptr, int32_t* col, 
 xrl_status xrl_export_lists(const xrl_ctx* ctx, int32_t level, int32_t* n_boxes, uint64_t* box_keys,
                             int64_t* v_ptr, int32_t* v_src, int64_t* u_ptr, int32_t* u_src);
 
+/* ---- learned initial guess -------------------------------------------------
+ * Not part of the paper: a per-panel network predicts the panel current
+ * distribution of a sweep from its lowest frequency, and the prediction is
+ * used only as the FGMRES starting point, judged by the FP64 residual. */
+
+/* Panel currents of the last xrl_solve: Ip [n_sys][n_panels][6] (caller
+ * panel order, system s = freq index * n_ports + port), entries
+ * (Re, Im) of I_x, I_y, I_z with I_p = J * area (A m).  normalize != 0
+ * divides each system by its complex port current (per unit port current). */
+xrl_status xrl_get_panel_currents(xrl_ctx* ctx, int32_t normalize, double* Ip);
+
+/* Per-panel features for the network, DEVICE buffers: d_ip0 [n_ports][n_panels][6]
+ * (FP64, per unit port current at the reference frequency f0, caller order),
+ * d_feat [n_freq * n_ports][n_panels][24] (FP32, caller order).  The reference
+ * currents of port q enter scaled by scale[q] = 1 / max_p |I_p| (written to
+ * the host array `scale` [n_ports] when not NULL; training targets use the
+ * same scale).  Features:
+ * 0-2 centroid in the root cube, 3-5 unit normal, 6 log(A / mean A)/4,
+ * 7 4 x mean (1 - |n . n_j|) over edge neighbours, 8 (log10 f - 5)/5,
+ * 9 log10(f/f0)/10, 10-15 the reference currents, 16 log10(skin depth /
+ * ESI thickness)/3, 17 |reference current|, 18 terminal flag, 19-20
+ * sin/cos(log10 f), 21 one, 22 port / n_ports, 23 zero.  Synchronous. */
+xrl_status xrl_panel_features(xrl_ctx* ctx, int32_t n_freq, const double* freq_hz, double f0,
+                              const double* d_ip0, float* d_feat, double* scale, void* stream);
+
+/* xrl_solve starting from predicted panel current SHAPES d_shape
+ * [n_freq * n_ports][n_panels][6] (device, FP32, caller order): each is
+ * projected onto loop space by weighted least squares (weights 1/area, the
+ * resistive energy norm; solved with the banded factorisation of the pencil
+ * at Z_s = 1), scaled by the complex factor minimising the FP64 residual, and
+ * kept only where it lowers ||b - A x0|| by more than 1 % (else x0 = 0).
+ * accepted [n_sys] and guess_res [n_sys] (||b - A x0|| / ||b||) are host
+ * outputs (may be NULL).  Needs precond = 1 with a usable band. */
+xrl_status xrl_solve_guess(xrl_ctx* ctx, int32_t n_freq, const double* freq_hz, const float* d_shape, double* R,
+                           double* L, int32_t* accepted, double* guess_res);
+
+typedef struct xrl_mlp xrl_mlp; /* opaque network: n_in -> width (GELU) x n_hidden -> n_out */
+
+/* Create a network on `device`; weights He-uniform from `seed`.  Parameters
+ * (FP32 master copy) are laid out per layer l: W_l [in_l][out_l] row-major,
+ * then b_l [out_l].  Forward and backward use the weights rounded to BF16
+ * (nearest even) and accumulate in FP32. */
+xrl_status xrl_mlp_create(int32_t n_in, int32_t width, int32_t n_hidden, int32_t n_out, uint64_t seed,
+                          int32_t device, xrl_mlp** out);
+int64_t xrl_mlp_num_params(const xrl_mlp* mlp);
+/* d_y [rows][n_out] = network(d_x [rows][n_in]); device buffers, enqueued on stream. */
+xrl_status xrl_mlp_forward(xrl_mlp* mlp, int64_t rows, const float* d_x, float* d_y, void* stream);
+/* One AdamW step (beta 0.9 / 0.999, eps 1e-8; weight decay on weights only)
+ * on the mean squared error of d_x against targets d_t [rows][n_out]; *loss
+ * receives the loss before the step.  Synchronises the stream. */
+xrl_status xrl_mlp_train_step(xrl_mlp* mlp, int64_t rows, const float* d_x, const float* d_t, float lr,
+                              float weight_decay, double* loss, void* stream);
+/* Gradient of the mean squared error w.r.t. the parameters into h_grads
+ * (host, parameter layout); no update. */
+xrl_status xrl_mlp_gradients(xrl_mlp* mlp, int64_t rows, const float* d_x, const float* d_t, float* h_grads,
+                             double* loss);
+xrl_status xrl_mlp_get_params(const xrl_mlp* mlp, float* h_params);
+xrl_status xrl_mlp_set_params(xrl_mlp* mlp, const float* h_params);
+const char* xrl_mlp_last_error(const xrl_mlp* mlp);
+void xrl_mlp_destroy(xrl_mlp* mlp);
+
 /* Per-phase device timing, recorded with CUDA events on the stream each
  * phase's kernels run on, while profiling is switched on (xrl_set_profiling).
  * phase: 0 P2P near field (FP32), 1 P2M, 2 M2M, 3 M2L (FP32), 4 L2L, 5 L2P,

@@ -356,6 +356,41 @@ xrl_status xrl_solve(xrl_ctx* c, int32_t nf, const double* freq, double* R, doub
   });
 }
 
+xrl_status xrl_solve_guess(xrl_ctx* c, int32_t nf, const double* freq, const float* d_shape, double* R, double* L,
+                           int32_t* accepted, double* guess_res) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(c->ready, XRL_ESTATE, "call xrl_setup first");
+    XRL_CHECK(nf > 0 && freq && d_shape && R && L, XRL_EINVAL, "bad solve arguments");
+    for (int i = 0; i < nf; ++i) XRL_CHECK(std::isfinite(freq[i]) && freq[i] > 0, XRL_EINVAL, "frequencies must be > 0");
+    double t0 = now_ms();
+    try {
+      run_solve(c, nf, freq, R, L, d_shape, accepted, guess_res);
+    } catch (...) {
+      c->stats.solve_ms = now_ms() - t0;
+      throw;
+    }
+    c->stats.solve_ms = now_ms() - t0;
+  });
+}
+
+xrl_status xrl_get_panel_currents(xrl_ctx* c, int32_t normalize, double* Ip) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(c->ready && Ip, XRL_EINVAL, "bad arguments");
+    panel_currents(c, normalize != 0, Ip);
+  });
+}
+
+xrl_status xrl_panel_features(xrl_ctx* c, int32_t nf, const double* freq, double f0, const double* d_ip0,
+                              float* d_feat, double* scale, void* stream) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(c->ready && nf > 0 && freq && d_ip0 && d_feat && f0 > 0, XRL_EINVAL, "bad feature arguments");
+    panel_features(c, nf, freq, f0, d_ip0, d_feat, scale, stream ? (cudaStream_t)stream : c->stream);
+  });
+}
+
 xrl_status xrl_apply_operator(xrl_ctx* c, int32_t nsys, const double* freq, const double* v, double* w) {
   if (!c) return XRL_EINVAL;
   return guarded(c, [&] {

@@ -404,6 +404,47 @@ __global__ void k_rhs(int nloop, int nsys, int nport, const int32_t* __restrict_
   b[idx] = make_double2(l == port_loop[p] ? (double)port_sign[p] : 0.0, 0.0);
 }
 
+// initial-guess shapes [nsys][N caller][6] (FP32) -> FMM columns X[r][6 s + c]
+__global__ void k_shape_to_X(int N, int nsys, const int32_t* __restrict__ perm, const float* __restrict__ shape,
+                             double* __restrict__ X) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)N * nsys * 6) return;
+  int c = (int)(idx % 6);
+  size_t rs = idx / 6;
+  int s = (int)(rs % nsys), r = (int)(rs / nsys);
+  X[(size_t)r * 6 * nsys + 6 * s + c] = (double)shape[((size_t)s * N + perm[r]) * 6 + c];
+}
+
+// alpha_s = (w^H b) / (w^H w) fitted per system; x = alpha x_s and Ax = alpha w
+// when that lowers ||b - A x|| by more than 1 %, else x = Ax = 0
+__global__ void k_guess_scale(int n, int nsys, const cplx* __restrict__ b, cplx* __restrict__ xs,
+                              cplx* __restrict__ w, int* __restrict__ accepted, double* __restrict__ gain) {
+  __shared__ cplx sh[256];
+  const int s = blockIdx.x;
+  const size_t o = (size_t)s * n;
+  cplx wb = make_double2(0, 0), ww = make_double2(0, 0), bb = make_double2(0, 0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    cplx wi = w[o + i], bi = b[o + i];
+    wb = cadd(wb, cm(cconj(wi), bi));
+    ww.x += cabs2(wi);
+    bb.x += cabs2(bi);
+  }
+  wb = block_sum(wb, sh);
+  ww = block_sum(ww, sh);
+  bb = block_sum(bb, sh);
+  const double red = (ww.x > 0.0 && bb.x > 0.0) ? cabs2(wb) / (ww.x * bb.x) : 0.0;   // 1 - |r|^2/|b|^2
+  const bool ok = red > 0.01;
+  const cplx alpha = ok ? cscale(wb, 1.0 / ww.x) : make_double2(0, 0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    xs[o + i] = cm(alpha, xs[o + i]);
+    w[o + i] = cm(alpha, w[o + i]);
+  }
+  if (threadIdx.x == 0) {
+    accepted[s] = ok ? 1 : 0;
+    gain[s] = ok ? sqrt(fmax(0.0, 1.0 - red)) : 1.0;   // ||b - A x0|| / ||b||
+  }
+}
+
 // Port reduction per frequency: Y[q][p] = b_q^T x_{f,p}; Z = Y^-1; R, L
 __global__ void k_ports(int nf, int nport, int nloop, const double* __restrict__ freq,
                         const int32_t* __restrict__ port_loop, const int8_t* __restrict__ port_sign,
@@ -622,7 +663,8 @@ static void apply_Qinv(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* z) {
   c->stats.total_inner += c->opt.inner_iters;
 }
 
-void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
+void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, const float* shape, int* accepted,
+               double* guess_res) {
   const Topo& T = c->topo;
   const int np = T.n_port;
   XRL_CHECK(np > 0, XRL_ESTATE, "no ports defined");
@@ -700,6 +742,50 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
   k_bnorm<<<nsys, 256, 0, s>>>(n, nsys, wk.b.p, wk.bnorm.p);
   c->stats.n_mvm = 0;
   c->stats.total_inner = 0;
+  bool have_guess = false;
+  if (shape) {
+    // learned initial guess: project the predicted panel currents onto loop space
+    // by weighted least squares, min sum_l |I_p(l) - I^(l)|^2 / A_l, i.e.
+    // (sum_m QA_m) x = M A diag(1/A) I^ -- the pencil at Z_s = 1, no P part --
+    // then fit one complex scale per system against the FP64 residual
+    XRL_CHECK(wk.banded, XRL_EINVAL, "the learned initial guess needs the banded preconditioner");
+    const Topo& TT = c->topo;
+    const int N = c->N;
+    wk.X.ensure(c->alloc, (size_t)N * 6 * nsys);
+    k_shape_to_X<<<nblk((size_t)N * nsys * 6), 256, 0, s>>>(N, nsys, c->d.perm.p, shape, wk.X.p);
+    std::vector<cplx> ones((size_t)nsys * TT.n_mat, make_double2(1.0, 0.0));
+    DBuf<cplx> zs1;
+    DBuf<double> wp0;
+    zs1.upload(c->alloc, ones);
+    wp0.upload(c->alloc, std::vector<double>(nsys, 0.0));
+    wk.Vb.ensure(c->alloc, (size_t)nsys * TT.n_cb);
+    k_scatter<double><<<nblk((size_t)TT.n_cb * nsys), 256, 0, s>>>(TT.n_cb, nsys, TT.n_mat, c->d.br_pan.p,
+                                                                   c->d.br_rho.p, c->d.pan_mat.p, c->d.area.p, zs1.p,
+                                                                   wp0.p, wk.X.p, wk.X.p, wk.Vb.p);
+    k_loop_reduce<<<nblk(tot), 256, 0, s>>>(n, nsys, TT.n_cb, TT.n_cb, c->d.m_ptr.p, c->d.m_col.p, c->d.m_val.p,
+                                            wk.Vb.p, wk.w.p);
+    DBuf<cplx> pf, pfT, pW, pS, pscr;
+    pf.alloc(c->alloc, (size_t)TT.n_band * (TT.band + 1));
+    pfT.alloc(c->alloc, (size_t)TT.n_band * (TT.band + 1));
+    pW.alloc(c->alloc, (size_t)std::max(1, TT.n_border) * TT.n_band);
+    pS.alloc(c->alloc, (size_t)std::max(1, TT.n_border * TT.n_border));
+    pscr.alloc(c->alloc, (size_t)nsys * (TT.n_band + 2));
+    band_factor(c, 1, zs1.p, wp0.p, pf.p, pfT.p, nullptr, nullptr, pW.p, pS.p, s);
+    band_apply(c, nsys, nsys, zs1.p, wp0.p, pf.p, pfT.p, nullptr, nullptr, pW.p, pS.p, wk.w.p, wk.x.p, pscr.p,
+               nullptr, s);
+    count_launch(c, 3);
+    apply_A(c, wk, nsys, wk.x.p, wk.w.p);
+    DBuf<int> dacc;
+    DBuf<double> dgain;
+    dacc.alloc(c->alloc, nsys);
+    dgain.alloc(c->alloc, nsys);
+    k_guess_scale<<<nsys, 256, 0, s>>>(n, nsys, wk.b.p, wk.x.p, wk.w.p, dacc.p, dgain.p);
+    count_launch(c);
+    if (accepted) XRL_CUDA(cudaMemcpyAsync(accepted, dacc.p, sizeof(int) * nsys, cudaMemcpyDeviceToHost, s));
+    if (guess_res) XRL_CUDA(cudaMemcpyAsync(guess_res, dgain.p, sizeof(double) * nsys, cudaMemcpyDeviceToHost, s));
+    XRL_CUDA(cudaStreamSynchronize(s));
+    have_guess = true;
+  }
   std::vector<int> hact(nsys), hiters(nsys);
   const double tol = c->opt.tol;
   int total = 0;
@@ -708,8 +794,8 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
   while (!done) {
     // restart: true residual with the FP64 operator
     if (!first) apply_A(c, wk, nsys, wk.x.p, wk.w.p);
-    k_restart<<<nsys, 256, 0, s>>>(n, nsys, m, wk.b.p, first ? nullptr : wk.w.p, wk.V.p, wk.g.p, wk.bnorm.p, tol,
-                                   tau, wk.active.p, wk.resid.p, wk.thr.p);
+    k_restart<<<nsys, 256, 0, s>>>(n, nsys, m, wk.b.p, (first && !have_guess) ? nullptr : wk.w.p, wk.V.p, wk.g.p,
+                                   wk.bnorm.p, tol, tau, wk.active.p, wk.resid.p, wk.thr.p);
     count_launch(c);
     first = false;
     XRL_CUDA(cudaMemcpyAsync(hact.data(), wk.active.p, sizeof(int) * nsys, cudaMemcpyDeviceToHost, s));
@@ -765,6 +851,12 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L) {
       done = true;
     }
   }
+  // keep the solution for xrl_get_panel_currents
+  c->d.last_x.ensure(c->alloc, tot);
+  XRL_CUDA(cudaMemcpyAsync(c->d.last_x.p, wk.x.p, sizeof(cplx) * tot, cudaMemcpyDeviceToDevice, s));
+  c->last_nsys = nsys;
+  c->last_nport = np;
+  c->last_port_loop = port_loop;
   // outputs
   DBuf<double> dR, dL;
   dR.alloc(c->alloc, (size_t)nf * np * np);

@@ -191,6 +191,7 @@ struct Dev {
   DBuf<int32_t> pan_br;      // [N][3] branch ids per Morton panel (-1 none)
   DBuf<double> pan_rho;      // [N][3][3] signed rho per (panel, slot)
   DBuf<int32_t> pan_mat;     // [N] material id (-1 terminal)
+  DBuf<int32_t> pan_cond_mat;  // [N] material id of every panel (features)
   DBuf<int32_t> br_pan;      // [B][2] Morton panel (-1 terminal)
   DBuf<double> br_rho;       // [B][2][3]
   DBuf<int32_t> m_ptr, m_col, mt_ptr, mt_col;
@@ -202,6 +203,7 @@ struct Dev {
   DBuf<double> band_val, border_vg, border_gg;
   // solver work
   DBuf<double> work;         // generic scratch for the solver
+  DBuf<double2> last_x;      // loop currents of the last solve [nsys][n_loops]
 };
 
 // Phase profiler: CUDA event pairs on the launching stream plus algorithmic work.
@@ -235,6 +237,8 @@ struct xrl_ctx {
   bool have_mesh = false, have_cond = false, ready = false;
   int N = 0, ncoef = 0, p = 0, max_leaf = 0;
   bool df64_m2l = false;   // FP64 M2L on the FP32 pipes (set inside mixed-precision solves)
+  int last_nsys = 0, last_nport = 0;
+  std::vector<int32_t> last_port_loop;
   xrl::Tree tree;
   xrl::Topo topo;
   xrl::Dev d;
@@ -276,7 +280,11 @@ void launch_to_morton(const xrl_ctx* c, int ncols, const double* x_user, double*
 void launch_from_morton(const xrl_ctx* c, int ncols, const double* Y, double* y_user, cudaStream_t s);
 // solve.cu
 void solver_prepare(xrl_ctx* c);
-void run_solve(xrl_ctx* c, int nf, const double* f, double* R, double* L);
+void run_solve(xrl_ctx* c, int nf, const double* f, double* R, double* L, const float* shape = nullptr,
+               int* accepted = nullptr, double* guess_res = nullptr);
+void panel_currents(xrl_ctx* c, bool normalize, double* host_out);
+void panel_features(xrl_ctx* c, int nf, const double* freq, double f0, const double* d_ip0, float* d_feat,
+                    double* h_scale, cudaStream_t s);
 void apply_operator_host(xrl_ctx* c, int nsys, const double* f, const double* v, double* w, int mode);
 // precond.cu
 bool band_usable(const xrl_ctx* c);

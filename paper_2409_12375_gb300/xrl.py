@@ -79,6 +79,21 @@ SIGNATURES = {
     "xrl_reset_profile": (ctypes.c_int, [_P]),
     "xrl_kernel_launches": (ctypes.c_int64, [_P]),
     "xrl_get_stream": (ctypes.c_void_p, [_P]),
+    "xrl_get_panel_currents": (ctypes.c_int, [_P, ctypes.c_int32, _D]),
+    "xrl_panel_features": (ctypes.c_int, [_P, ctypes.c_int32, _D, ctypes.c_double, _P, _P, _D, _P]),
+    "xrl_solve_guess": (ctypes.c_int, [_P, ctypes.c_int32, _D, _P, _D, _D, _I, _D]),
+    "xrl_mlp_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "xrl_mlp_num_params": (ctypes.c_int64, [_P]),
+    "xrl_mlp_forward": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
+    "xrl_mlp_train_step": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_float, ctypes.c_float,
+                                          ctypes.POINTER(ctypes.c_double), _P]),
+    "xrl_mlp_gradients": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_float),
+                                         ctypes.POINTER(ctypes.c_double)]),
+    "xrl_mlp_get_params": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "xrl_mlp_set_params": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "xrl_mlp_last_error": (ctypes.c_char_p, [_P]),
+    "xrl_mlp_destroy": (None, [_P]),
     "xrl_last_error": (ctypes.c_char_p, [_P]),
     "xrl_destroy": (None, [_P]),
 }
@@ -123,6 +138,7 @@ class XRL:
         self.h = h
         self.opts = o
         self.n_tri = 0
+        self._last_nsys = 0
 
     def _check(self, code, h):
         if code != 0:
@@ -208,6 +224,7 @@ class XRL:
         L = np.empty_like(R)
         code = lib().xrl_solve(self.h, f.shape[0], _dp(f), _dp(R), _dp(L))
         self._check(code, self.h)
+        self._last_nsys = f.shape[0] * npt
         return R, L
 
     def apply_operator(self, freqs, v, precond_matrix=False, precond_inverse=False):
@@ -222,6 +239,44 @@ class XRL:
             fn = lib().xrl_apply_precond_inverse
         self._check(fn(self.h, f.shape[0], _dp(f), v.ctypes.data_as(_D), w.ctypes.data_as(_D)), self.h)
         return w
+
+    # ---- learned initial guess -------------------------------------------------------
+    def panel_currents(self, normalize=True):
+        """[n_sys][n_panels][6] panel currents of the last solve (per unit port current if normalize)."""
+        st = self.stats()
+        n = st["n_panels"]
+        # n_sys of the last solve is inferred from the buffer the library fills
+        nsys = self._last_nsys
+        out = np.empty((nsys, n, 6))
+        self._check(lib().xrl_get_panel_currents(self.h, 1 if normalize else 0, _dp(out)), self.h)
+        return out
+
+    def features(self, freqs, f0, ip0):
+        """ip0: torch CUDA float64 [n_ports][n_panels][6] -> (torch float32 [n_f*n_p][n_panels][24],
+        per-port reference scale [n_ports])."""
+        import torch
+        f = np.ascontiguousarray(freqs, np.float64)
+        npt = self.stats()["n_ports"]
+        feat = torch.empty((f.shape[0] * npt, self.n_tri, 24), device=ip0.device, dtype=torch.float32)
+        scale = np.empty(npt)
+        self._check(lib().xrl_panel_features(self.h, f.shape[0], _dp(f), float(f0),
+                                             ctypes.c_void_p(ip0.data_ptr()), ctypes.c_void_p(feat.data_ptr()),
+                                             _dp(scale), None), self.h)
+        return feat, scale
+
+    def solve_guess(self, freqs, shape):
+        """xrl_solve from predicted current shapes (torch CUDA float32 [n_sys][n_panels][6])."""
+        f = np.ascontiguousarray(freqs, np.float64)
+        npt = self.stats()["n_ports"]
+        nsys = f.shape[0] * npt
+        R = np.empty((f.shape[0], npt, npt))
+        L = np.empty_like(R)
+        acc = np.zeros(nsys, np.int32)
+        gr = np.zeros(nsys)
+        self._check(lib().xrl_solve_guess(self.h, f.shape[0], _dp(f), ctypes.c_void_p(shape.data_ptr()), _dp(R),
+                                          _dp(L), _ip(acc), _dp(gr)), self.h)
+        self._last_nsys = nsys
+        return R, L, acc, gr
 
     # ---- profiling ---------------------------------------------------------------
     PHASES = ["p2p", "p2m", "m2m", "m2l", "l2l", "l2p", "operator", "precond", "krylov", "p2p64", "m2l64"]
@@ -309,3 +364,65 @@ class XRL:
             self._check(lib().xrl_export_lists(self.h, level, ctypes.byref(nb), None, None, None,
                                                uptr.ctypes.data_as(P64), _ip(usrc)), self.h)
         return keys, vptr, vsrc, uptr, usrc
+
+
+class MLP:
+    """Per-panel network of the library (BF16 weights, FP32 accumulation)."""
+
+    def __init__(self, n_in=24, width=128, n_hidden=3, n_out=6, seed=0, device=0):
+        h = _P()
+        code = lib().xrl_mlp_create(n_in, width, n_hidden, n_out, seed, device, ctypes.byref(h))
+        if code != 0:
+            raise XRLError(code, "xrl_mlp_create")
+        self.h = h
+        self.n_in, self.n_out = n_in, n_out
+
+    def _check(self, code):
+        if code != 0:
+            raise XRLError(code, lib().xrl_mlp_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().xrl_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_params(self):
+        return int(lib().xrl_mlp_num_params(self.h))
+
+    def forward(self, x):
+        import torch
+        y = torch.empty((x.shape[0], self.n_out), device=x.device, dtype=torch.float32)
+        self._check(lib().xrl_mlp_forward(self.h, x.shape[0], ctypes.c_void_p(x.data_ptr()),
+                                          ctypes.c_void_p(y.data_ptr()), None))
+        return y
+
+    def train_step(self, x, t, lr=1e-3, weight_decay=1e-4):
+        loss = ctypes.c_double()
+        self._check(lib().xrl_mlp_train_step(self.h, x.shape[0], ctypes.c_void_p(x.data_ptr()),
+                                             ctypes.c_void_p(t.data_ptr()), lr, weight_decay, ctypes.byref(loss),
+                                             None))
+        return loss.value
+
+    def gradients(self, x, t):
+        g = np.empty(self.n_params, np.float32)
+        loss = ctypes.c_double()
+        self._check(lib().xrl_mlp_gradients(self.h, x.shape[0], ctypes.c_void_p(x.data_ptr()),
+                                            ctypes.c_void_p(t.data_ptr()),
+                                            g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss)))
+        return g, loss.value
+
+    def get_params(self):
+        p = np.empty(self.n_params, np.float32)
+        self._check(lib().xrl_mlp_get_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        self._check(lib().xrl_mlp_set_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
