@@ -67,6 +67,9 @@ typedef struct {
   int32_t device;      /* CUDA device ordinal, default 0 */
   int32_t separation;  /* well-separatedness ws of the octree (1 or 2): leaves within ws cells are
                           near field; default 2 (see xrl_export_lists) */
+  int32_t use_graphs;  /* 1 (default): the inner operator of every Arnoldi step is replayed from a
+                          CUDA graph captured once per solve; 0: plain launches */
+  int32_t reserved;
 } xrl_options;
 
 /* Fill `opt` with the defaults listed above. */
@@ -161,6 +164,20 @@ typedef struct {
   double setup_ms, solve_ms, mvm_ms; /* wall times of the last setup / solve / fmm_mvm */
   int64_t peak_device_bytes;         /* high-water mark of the library's device allocations */
 } xrl_stats;
+
+/* FMM autotuner: tries leaf_target in {16, 32, 64} x fmm_order in {6, 7, 8}
+ * (separation 2), re-running xrl_setup for each.  A candidate is admissible
+ * when its FP64 product matches the FP64 direct sum (xrl_direct_mvm_device) on
+ * two seeded random columns to mvm_tol (relative 2-norm).  Among admissible
+ * candidates, the one with the fastest product at n_cols columns is kept,
+ * timed with CUDA events in the precision the solver's inner iterations use
+ * (FP32 if `precision` = 1, else FP64).  The context ends set up with it, and
+ * its options are updated.  Outputs (host, may be NULL): the chosen
+ * leaf_target, fmm_order, its product time in ms, and its error.
+ * XRL_ENOCONV if no candidate meets mvm_tol (the context is left set up with
+ * the most accurate one). */
+xrl_status xrl_autotune(xrl_ctx* ctx, int32_t n_cols, double mvm_tol, int32_t precision, int32_t* leaf_target,
+                        int32_t* fmm_order, double* product_ms, double* product_err);
 
 /* Counters and timings of the context (valid after setup). */
 xrl_status xrl_get_stats(const xrl_ctx* ctx, xrl_stats* out);

@@ -50,11 +50,20 @@ double self_term_host(const double* a, const double* b, const double* c) {
 
 namespace xrl {
 
+// Inside a stream capture a plain record only marks a dependency; an
+// external record becomes a graph node that fires on every replay.
+static void record_event(xrl_ctx* c, cudaEvent_t e, cudaStream_t s) {
+  if (c->prof.capturing)
+    XRL_CUDA(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+  else
+    XRL_CUDA(cudaEventRecord(e, s));
+}
+
 cudaEvent_t prof_begin(xrl_ctx* c, cudaStream_t s) {
   if (!c->prof.on) return nullptr;
   cudaEvent_t a;
   XRL_CUDA(cudaEventCreate(&a));
-  XRL_CUDA(cudaEventRecord(a, s));
+  record_event(c, a, s);
   return a;
 }
 
@@ -63,11 +72,38 @@ void prof_end(xrl_ctx* c, cudaStream_t s, cudaEvent_t a, int phase, int launches
   if (!c->prof.on || !a) return;
   cudaEvent_t b;
   XRL_CUDA(cudaEventCreate(&b));
-  XRL_CUDA(cudaEventRecord(b, s));
+  record_event(c, b, s);
+  if (c->prof.capturing) {
+    c->prof.graph_recs.push_back({a, b, phase, launches, flops, bytes});
+    return;
+  }
   c->prof.pending.push_back({a, b, phase});
   c->prof.launches[phase] += launches;
   c->prof.flops[phase] += flops;
   c->prof.bytes[phase] += bytes;
+}
+
+void prof_graph_replayed(xrl_ctx* c) {
+  c->prof.total_launches += c->prof.graph_launches;
+  for (auto& r : c->prof.graph_recs) {
+    XRL_CUDA(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    XRL_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    c->prof.ms[r.phase] += ms;
+    c->prof.launches[r.phase] += r.launches;
+    c->prof.flops[r.phase] += r.flops;
+    c->prof.bytes[r.phase] += r.bytes;
+  }
+}
+
+void prof_graph_release(xrl_ctx* c) {
+  for (auto& r : c->prof.graph_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  c->prof.graph_recs.clear();
+  c->prof.graph_launches = 0;
+  c->prof.capturing = false;
 }
 
 static void prof_collect(xrl_ctx* c) {
@@ -136,6 +172,7 @@ void xrl_default_options(xrl_options* o) {
   o->inner_tol = 1e-3;
   o->device = 0;
   o->separation = 2;
+  o->use_graphs = 1;
 }
 
 xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {
@@ -330,6 +367,124 @@ xrl_status xrl_fmm_mvm(xrl_ctx* c, int32_t nc, const double* x, double* y) {
     XRL_CUDA(cudaStreamSynchronize(c->stream));
     c->stats.mvm_ms = now_ms() - t0;
   });
+}
+
+xrl_status xrl_autotune(xrl_ctx* c, int32_t nc, double tol, int32_t precision, int32_t* best_leaf,
+                        int32_t* best_order, double* best_ms, double* best_err) {
+  if (!c) return XRL_EINVAL;
+  bool none_ok = false;
+  xrl_status st = guarded(c, [&] {
+    XRL_CHECK(c->have_mesh && nc > 0 && tol > 0, XRL_EINVAL, "bad autotune arguments");
+    const int N = c->N;
+    // reference: FP64 direct sum on two seeded random columns
+    const int nref = 2;
+    std::vector<double> hx((size_t)nref * N);
+    uint64_t z = 0x9e3779b97f4a7c15ull;
+    for (auto& v : hx) {   // splitmix64 -> uniform [-1, 1)
+      z += 0x9e3779b97f4a7c15ull;
+      uint64_t t = z;
+      t = (t ^ (t >> 30)) * 0xbf58476d1ce4e5b9ull;
+      t = (t ^ (t >> 27)) * 0x94d049bb133111ebull;
+      t ^= t >> 31;
+      v = (double)(t >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    }
+    c->opt.separation = 2;
+    if (!c->ready) {
+      if (xrl_setup(c) != XRL_OK) throw Error(XRL_EINVAL, c->err);
+    }
+    DBuf<double> dx, dref, dy;
+    dx.upload(c->alloc, hx);
+    dref.alloc(c->alloc, hx.size());
+    dy.alloc(c->alloc, hx.size());
+    XRL_CHECK(xrl_direct_mvm_device(c, nref, dx.p, dref.p, nullptr) == XRL_OK, XRL_ECUDA, c->err);
+    XRL_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<double> ref = dref.download();
+    double rn = 0.0;
+    for (double v : ref) rn += v * v;
+    rn = std::sqrt(rn);
+    struct Cand {
+      int leaf, p;
+      double err, ms;
+    };
+    std::vector<Cand> res;
+    for (int p : {6, 7, 8})
+      for (int leaf : {16, 32, 64}) {
+        c->opt.fmm_order = p;
+        c->opt.leaf_target = leaf;
+        c->ready = false;
+        if (xrl_setup(c) != XRL_OK) throw Error(XRL_EINVAL, c->err);
+        XRL_CHECK(xrl_fmm_mvm_device(c, nref, dx.p, dy.p, nullptr) == XRL_OK, XRL_ECUDA, c->err);
+        XRL_CUDA(cudaStreamSynchronize(c->stream));
+        std::vector<double> y = dy.download();
+        double en = 0.0;
+        for (size_t k = 0; k < y.size(); ++k) en += (y[k] - ref[k]) * (y[k] - ref[k]);
+        double err = std::sqrt(en) / rn;
+        double ms = -1.0;
+        if (err <= tol) {
+          // time the product at nc columns in the solver's inner precision
+          size_t n = (size_t)N * nc;
+          cudaEvent_t a, b;
+          XRL_CUDA(cudaEventCreate(&a));
+          XRL_CUDA(cudaEventCreate(&b));
+          if (precision == 1) {
+            DBuf<float> X, Y;
+            X.alloc(c->alloc, n);
+            Y.alloc(c->alloc, n);
+            XRL_CUDA(cudaMemsetAsync(X.p, 0, n * sizeof(float), c->stream));
+            fmm_apply32(c, nc, X.p, Y.p, c->stream);
+            XRL_CUDA(cudaEventRecord(a, c->stream));
+            for (int r = 0; r < 3; ++r) fmm_apply32(c, nc, X.p, Y.p, c->stream);
+            XRL_CUDA(cudaEventRecord(b, c->stream));
+          } else {
+            DBuf<double> X, Y;
+            X.alloc(c->alloc, n);
+            Y.alloc(c->alloc, n);
+            XRL_CUDA(cudaMemsetAsync(X.p, 0, n * sizeof(double), c->stream));
+            fmm_apply(c, nc, X.p, Y.p, c->stream);
+            XRL_CUDA(cudaEventRecord(a, c->stream));
+            for (int r = 0; r < 3; ++r) fmm_apply(c, nc, X.p, Y.p, c->stream);
+            XRL_CUDA(cudaEventRecord(b, c->stream));
+          }
+          XRL_CUDA(cudaEventSynchronize(b));
+          float f = 0.f;
+          XRL_CUDA(cudaEventElapsedTime(&f, a, b));
+          ms = f / 3.0;
+          cudaEventDestroy(a);
+          cudaEventDestroy(b);
+          c->d.X32.release();
+          c->d.Y32.release();
+          c->d.M32.release();
+          c->d.L32.release();
+          c->d.Mexp.release();
+          c->d.Lexp.release();
+        }
+        res.push_back({leaf, p, err, ms});
+      }
+    int best = -1;
+    for (size_t k = 0; k < res.size(); ++k)
+      if (res[k].ms >= 0 && (best < 0 || res[k].ms < res[best].ms)) best = (int)k;
+    if (best < 0) {
+      none_ok = true;
+      for (size_t k = 0; k < res.size(); ++k)
+        if (best < 0 || res[k].err < res[best].err) best = (int)k;
+    }
+    c->opt.fmm_order = res[best].p;
+    c->opt.leaf_target = res[best].leaf;
+    c->ready = false;
+    if (xrl_setup(c) != XRL_OK) throw Error(XRL_EINVAL, c->err);
+    if (best_leaf) *best_leaf = res[best].leaf;
+    if (best_order) *best_order = res[best].p;
+    if (best_ms) *best_ms = res[best].ms;
+    if (best_err) *best_err = res[best].err;
+  });
+  if (st == XRL_OK && none_ok) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "no autotune candidate met the accuracy bound (best %.3g at leaf %d, order %d)",
+             best_err ? *best_err : -1.0, c->opt.leaf_target, c->opt.fmm_order);
+    c->err = msg;
+    return XRL_ENOCONV;
+  }
+  return st;
 }
 
 xrl_status xrl_get_stats(const xrl_ctx* c, xrl_stats* out) {

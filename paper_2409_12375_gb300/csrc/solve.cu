@@ -548,7 +548,7 @@ struct Work {
   DBuf<float2> fac32, facT32;
   int nport = 1;
   bool banded = false;
-  DBuf<cplx> b, x, w, tmp, V, Z, H, h1, h2, cs, sn, g, y, Vb, dinv;
+  DBuf<cplx> b, x, w, tmp, V, Z, H, h1, h2, cs, sn, g, y, Vb, dinv, zst;
   DBuf<cplx> cz, cr, cp, cq, crho;
   DBuf<double> X, Y, bnorm, resid, cvn, thr;
   DBuf<float> X32, Y32;
@@ -786,6 +786,33 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
     XRL_CUDA(cudaStreamSynchronize(s));
     have_guess = true;
   }
+  // The inner operator (gather -> FMM -> scatter -> loop reduce, ~14 kernels)
+  // is captured once into a CUDA graph and replayed for every later Arnoldi
+  // step; its input is staged through a fixed buffer.  The first application
+  // runs eagerly so that every buffer exists before the capture.
+  const bool use_graph = c->opt.use_graphs != 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_state = 0;
+  struct GraphGuard {
+    xrl_ctx* c;
+    cudaStream_t s;
+    cudaGraph_t* g;
+    cudaGraphExec_t* e;
+    ~GraphGuard() {
+      if (c->prof.capturing) {   // an error inside the capture: close it
+        cudaGraph_t partial = nullptr;
+        cudaStreamEndCapture(s, &partial);
+        if (partial) cudaGraphDestroy(partial);
+        cudaGetLastError();
+        c->prof.capturing = false;
+      }
+      if (*e) cudaGraphExecDestroy(*e);
+      if (*g) cudaGraphDestroy(*g);
+      prof_graph_release(c);
+    }
+  } graph_guard{c, s, &graph, &gexec};
+  if (use_graph) wk.zst.alloc(c->alloc, tot);
   std::vector<int> hact(nsys), hiters(nsys);
   const double tol = c->opt.tol;
   int total = 0;
@@ -811,7 +838,30 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
       cplx* vj = wk.V.p + (size_t)j * tot;
       cplx* zj = wk.Z.p + (size_t)j * tot;
       apply_Qinv(c, wk, nsys, vj, zj);
-      apply_A(c, wk, nsys, zj, wk.w.p, mixed);
+      bool replayed = false;
+      if (!use_graph) {
+        apply_A(c, wk, nsys, zj, wk.w.p, mixed);
+      } else {
+        XRL_CUDA(cudaMemcpyAsync(wk.zst.p, zj, sizeof(cplx) * tot, cudaMemcpyDeviceToDevice, s));
+        if (graph_state == 0) {
+          apply_A(c, wk, nsys, wk.zst.p, wk.w.p, mixed);
+          graph_state = 1;
+        } else {
+          if (graph_state == 1) {
+            c->prof.capturing = true;
+            XRL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            apply_A(c, wk, nsys, wk.zst.p, wk.w.p, mixed);
+            XRL_CUDA(cudaStreamEndCapture(s, &graph));
+            c->prof.capturing = false;
+            XRL_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
+            graph_state = 2;
+          } else {
+            c->stats.n_mvm++;
+          }
+          XRL_CUDA(cudaGraphLaunch(gexec, s));
+          replayed = true;
+        }
+      }
       // CGS2
       cudaEvent_t evk = prof_begin(c, s);
       k_arnoldi_dots<<<dim3(j + 1, nsys), 256, 0, s>>>(n, nsys, j, m + 1, wk.V.p, wk.w.p, wk.h1.p, wk.active.p);
@@ -829,6 +879,7 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
       XRL_CUDA(cudaGetLastError());
       XRL_CUDA(cudaMemcpyAsync(hact.data(), wk.active.p, sizeof(int) * nsys, cudaMemcpyDeviceToHost, s));
       XRL_CUDA(cudaStreamSynchronize(s));
+      if (replayed) prof_graph_replayed(c);
       nact = 0;
       for (int v : hact) nact += v;
       if (nact == 0) {

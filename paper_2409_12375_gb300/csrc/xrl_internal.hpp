@@ -84,14 +84,23 @@ struct DBuf {
   }
   void upload(DevAlloc& al, const std::vector<T>& h) {
     alloc(al, h.size());
-    if (!h.empty()) XRL_CUDA(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (!h.empty()) {
+      // A pageable copy may return before its DMA lands, and the library's
+      // streams do not wait on the legacy stream: wait for it here.
+      XRL_CUDA(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+      XRL_CUDA(cudaStreamSynchronize(cudaStreamLegacy));
+    }
   }
   void ensure(DevAlloc& al, size_t count) {
     if (n < count) alloc(al, count);
   }
   std::vector<T> download() const {
     std::vector<T> h(n);
-    if (n) XRL_CUDA(cudaMemcpy(h.data(), p, n * sizeof(T), cudaMemcpyDeviceToHost));
+    if (n) {
+      // the writer may be a kernel on a non-blocking stream
+      XRL_CUDA(cudaDeviceSynchronize());
+      XRL_CUDA(cudaMemcpy(h.data(), p, n * sizeof(T), cudaMemcpyDeviceToHost));
+    }
     return h;
   }
 };
@@ -219,6 +228,15 @@ struct Prof {
   double ms[PH_COUNT] = {0}, flops[PH_COUNT] = {0}, bytes[PH_COUNT] = {0};
   int64_t launches[PH_COUNT] = {0};
   int64_t total_launches = 0;
+  // while a CUDA graph is being captured: its event pairs and work, read back after every replay
+  bool capturing = false;
+  struct GRec {
+    cudaEvent_t a, b;
+    int phase, launches;
+    double flops, bytes;
+  };
+  std::vector<GRec> graph_recs;
+  int64_t graph_launches = 0;
 };
 
 }  // namespace xrl
@@ -252,7 +270,14 @@ namespace xrl {
 // profiling helpers (api.cu): begin returns an event recorded on s (or null)
 cudaEvent_t prof_begin(xrl_ctx* c, cudaStream_t s);
 void prof_end(xrl_ctx* c, cudaStream_t s, cudaEvent_t a, int phase, int launches, double flops, double bytes);
-inline void count_launch(xrl_ctx* c, int n = 1) { c->prof.total_launches += n; }
+void prof_graph_replayed(xrl_ctx* c);   // after a replay of the captured graph has completed
+void prof_graph_release(xrl_ctx* c);
+inline void count_launch(xrl_ctx* c, int n = 1) {
+  if (c->prof.capturing)
+    c->prof.graph_launches += n;
+  else
+    c->prof.total_launches += n;
+}
 // tree.cpp
 void build_tree(xrl_ctx* c, const std::vector<uint64_t>& keys_by_caller);
 uint64_t morton_key(uint32_t ix, uint32_t iy, uint32_t iz);

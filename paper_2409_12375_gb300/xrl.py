@@ -29,7 +29,8 @@ class Options(ctypes.Structure):
                 ("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("inner_iters", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("device", ctypes.c_int32), ("separation", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("separation", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -65,6 +66,7 @@ SIGNATURES = {
     "xrl_fmm_mvm_device_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "xrl_direct_mvm_device": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "xrl_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
+    "xrl_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _I, _I, _D, _D]),
     "xrl_solve": (ctypes.c_int, [_P, ctypes.c_int32, _D, _D, _D]),
     "xrl_apply_operator": (ctypes.c_int, [_P, ctypes.c_int32, _D, _D, _D]),
     "xrl_apply_precond_matrix": (ctypes.c_int, [_P, ctypes.c_int32, _D, _D, _D]),
@@ -239,6 +241,18 @@ class XRL:
             fn = lib().xrl_apply_precond_inverse
         self._check(fn(self.h, f.shape[0], _dp(f), v.ctypes.data_as(_D), w.ctypes.data_as(_D)), self.h)
         return w
+
+    def autotune(self, n_cols, mvm_tol=1e-6, precision=1):
+        """Pick leaf_target and fmm_order (see xrl_autotune); returns (leaf, order, ms, err)."""
+        leaf = ctypes.c_int32()
+        order = ctypes.c_int32()
+        ms = ctypes.c_double()
+        err = ctypes.c_double()
+        self._check(lib().xrl_autotune(self.h, n_cols, mvm_tol, precision, ctypes.byref(leaf), ctypes.byref(order),
+                                       ctypes.byref(ms), ctypes.byref(err)), self.h)
+        self.opts.leaf_target = leaf.value
+        self.opts.fmm_order = order.value
+        return leaf.value, order.value, ms.value, err.value
 
     # ---- learned initial guess -------------------------------------------------------
     def panel_currents(self, normalize=True):
