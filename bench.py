@@ -271,9 +271,10 @@ def main():
     avg_ms = d["ms"] / max(1, d["launches"])
     # kernel of each phase and its ncu DRAM traffic per launch (bytes) where a
     # capture of the unchanged kernel exists (profiles/top_kernels_coil_sweep.md)
-    kern = {"m2l": "k_m2l_tiled<6> (FP32)", "p2p": "k_p2p_tiled (FP32)", "precond": "k_band_apply_pair/k_band_factor",
-            "m2l64": "k_m2l_df64 / k_m2l<double>", "p2p64": "k_p2p<double>"}
-    traffic = {"m2l": 71.785e6 + 34.6816e6, "p2p": 1018.708e6 + 36.329728e6}
+    kern = {"m2l": "k_tc_pack_a + k_xlate_tc<96> (tcgen05, 3-piece BF16)", "p2p": "k_p2p_tiled (FP32)",
+            "precond": "k_band_apply_pair/k_band_factor", "m2l64": "k_m2l_df64 / k_m2l<double>",
+            "p2p64": "k_p2p<double>"}
+    traffic = {"p2p": 1018.708e6 + 36.329728e6}
     fp32_phase = {"p2p", "p2m", "m2m", "m2l", "l2l", "l2p"}
     if dom in fp32_phase or dom in ("p2p64", "m2l64"):
         lowp = dom in fp32_phase and args.precision == "mixed"

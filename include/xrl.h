@@ -69,7 +69,9 @@ typedef struct {
                           near field; default 2 (see xrl_export_lists) */
   int32_t use_graphs;  /* 1 (default): the inner operator of every Arnoldi step is replayed from a
                           CUDA graph captured once per solve; 0: plain launches */
-  int32_t reserved;
+  int32_t tensor_cores; /* 1 (default): the M2L translations of the FP32 products (precision 1) run
+                           on the tcgen05 tensor cores in split TF32 (hi/lo, three products,
+                           ~FP32 accuracy) for n_cols >= 64; 0: FP32 CUDA-core kernels only */
 } xrl_options;
 
 /* Fill `opt` with the defaults listed above. */
@@ -123,6 +125,15 @@ xrl_status xrl_fmm_mvm(xrl_ctx* ctx, int32_t n_cols, const double* x, double* y)
  * the end of this work.  d_x and d_y must not overlap. */
 xrl_status xrl_fmm_mvm_device(xrl_ctx* ctx, int32_t n_cols, const double* d_x, double* d_y,
                               void* stream);
+
+/* The FP32 product of the mixed-precision solver's inner iterations (Sec.
+ * II-C evaluated in FP32: near field and expansions in FP32, M2L on the
+ * tensor cores when opt.tensor_cores and n_cols >= 64): y = P x on DEVICE
+ * buffers d_x, d_y ([n_cols][n_tri], float32) enqueued on `stream` (NULL =
+ * the context's stream).  Relative accuracy ~1e-6 (FP32 rounding plus the
+ * order-p truncation).  Synchronises the stream on return to check the
+ * tensor-core kernels' wait status (XRL_ETIMEOUT if one gave up). */
+xrl_status xrl_fmm_mvm32_device(xrl_ctx* ctx, int32_t n_cols, const float* d_x, float* d_y, void* stream);
 
 /* Same product as xrl_fmm_mvm_device, for callers that must not allocate GPU
  * memory: code running while a CUDA stream is being captured into a graph,

@@ -173,6 +173,7 @@ void xrl_default_options(xrl_options* o) {
   o->device = 0;
   o->separation = 2;
   o->use_graphs = 1;
+  o->tensor_cores = 1;
 }
 
 xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {
@@ -327,6 +328,23 @@ xrl_status xrl_fmm_mvm_device(xrl_ctx* c, int32_t nc, const double* dx, double* 
     fmm_apply(c, nc, c->d.X.p, c->d.Y.p, s);
     launch_from_morton(c, nc, c->d.Y.p, dy, s);
     XRL_CUDA(cudaGetLastError());
+  });
+}
+
+xrl_status xrl_fmm_mvm32_device(xrl_ctx* c, int32_t nc, const float* dx, float* dy, void* stream) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] {
+    XRL_CHECK(c->ready, XRL_ESTATE, "call xrl_setup first");
+    XRL_CHECK(nc > 0 && dx && dy, XRL_EINVAL, "bad mvm arguments");
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    size_t n = (size_t)c->N * nc;
+    c->d.X32.ensure(c->alloc, n);
+    c->d.Y32.ensure(c->alloc, n);
+    launch_to_morton32(c, nc, dx, c->d.X32.p, s);
+    fmm_apply32(c, nc, c->d.X32.p, c->d.Y32.p, s);
+    launch_from_morton32(c, nc, c->d.Y32.p, dy, s);
+    XRL_CUDA(cudaGetLastError());
+    tc_check(c, s);
   });
 }
 

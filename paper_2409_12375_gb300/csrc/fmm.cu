@@ -23,16 +23,18 @@
 namespace xrl {
 
 // ---- layout conversion ----------------------------------------------------------------
-__global__ void k_to_morton(int N, int nc, const int32_t* __restrict__ perm, const double* __restrict__ x,
-                            double* __restrict__ X) {
+template <class T>
+__global__ void k_to_morton(int N, int nc, const int32_t* __restrict__ perm, const T* __restrict__ x,
+                            T* __restrict__ X) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)N * nc) return;
   int r = (int)(idx / nc), c = (int)(idx % nc);
   X[idx] = x[(size_t)c * N + perm[r]];
 }
 
-__global__ void k_from_morton(int N, int nc, const int32_t* __restrict__ perm, const double* __restrict__ Y,
-                              double* __restrict__ y) {
+template <class T>
+__global__ void k_from_morton(int N, int nc, const int32_t* __restrict__ perm, const T* __restrict__ Y,
+                              T* __restrict__ y) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)N * nc) return;
   int r = (int)(idx / nc), c = (int)(idx % nc);
@@ -42,13 +44,25 @@ __global__ void k_from_morton(int N, int nc, const int32_t* __restrict__ perm, c
 void launch_to_morton(const xrl_ctx* c, int nc, const double* x, double* X, cudaStream_t s) {
   size_t n = (size_t)c->N * nc;
   count_launch(const_cast<xrl_ctx*>(c));
-  k_to_morton<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->N, nc, c->d.perm.p, x, X);
+  k_to_morton<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->N, nc, c->d.perm.p, x, X);
 }
 
 void launch_from_morton(const xrl_ctx* c, int nc, const double* Y, double* y, cudaStream_t s) {
   size_t n = (size_t)c->N * nc;
   count_launch(const_cast<xrl_ctx*>(c));
-  k_from_morton<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->N, nc, c->d.perm.p, Y, y);
+  k_from_morton<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->N, nc, c->d.perm.p, Y, y);
+}
+
+void launch_to_morton32(const xrl_ctx* c, int nc, const float* x, float* X, cudaStream_t s) {
+  size_t n = (size_t)c->N * nc;
+  count_launch(const_cast<xrl_ctx*>(c));
+  k_to_morton<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->N, nc, c->d.perm.p, x, X);
+}
+
+void launch_from_morton32(const xrl_ctx* c, int nc, const float* Y, float* y, cudaStream_t s) {
+  size_t n = (size_t)c->N * nc;
+  count_launch(const_cast<xrl_ctx*>(c));
+  k_from_morton<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->N, nc, c->d.perm.p, Y, y);
 }
 
 // ---- near field -------------------------------------------------------------------------
@@ -232,7 +246,7 @@ __global__ void k_m2l(int nc, int ct, int ncoef, int b0, const int32_t* __restri
 // V-list pair the translation matrix (stored [in][out]) and the source
 // multipole tile are staged in shared memory; the inner loop does 8 RI FMAs
 // per RI + 2 shared loads (float4 for the columns).
-template <int RI>
+template <int RI, bool ACC>
 __global__ void __launch_bounds__(128) k_m2l_tiled(int nc, int ncoef, int b0, const int32_t* __restrict__ v_ptr,
                                                    const int32_t* __restrict__ v_src, const int16_t* __restrict__ v_off,
                                                    const float* __restrict__ Tt, const float* __restrict__ M,
@@ -291,7 +305,7 @@ __global__ void __launch_bounds__(128) k_m2l_tiled(int nc, int ncoef, int b0, co
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int cc = (j < 4) ? 4 * tx + j : 32 + 4 * tx + (j - 4);
-      if (c0 + cc < nc) out[(size_t)k * nc + cc] = acc[i][j];
+      if (c0 + cc < nc) out[(size_t)k * nc + cc] = ACC ? out[(size_t)k * nc + cc] + acc[i][j] : acc[i][j];
     }
   }
 }
@@ -304,6 +318,7 @@ __global__ void __launch_bounds__(128) k_m2l_tiled(int nc, int ncoef, int b0, co
 // thin FP64 pipe.  One block per (target box, 64-column tile), 256 threads as
 // 32 row groups x 8 column groups, rows ty + 32 i (i < 3, ncoef <= 96),
 // columns 4 tx + j and 32 + 4 tx + j (j < 4).
+template <bool ACC>
 __global__ void __launch_bounds__(256) k_m2l_df64(int nc, int ncoef, int b0, const int32_t* __restrict__ v_ptr,
                                                   const int32_t* __restrict__ v_src, const int16_t* __restrict__ v_off,
                                                   const double* __restrict__ Tt, const double* __restrict__ M,
@@ -371,56 +386,78 @@ __global__ void __launch_bounds__(256) k_m2l_df64(int nc, int ncoef, int b0, con
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int cc = (q < 4) ? 4 * tx + q : 32 + 4 * tx + (q - 4);
-      if (c0 + cc < nc) out[(size_t)k * nc + cc] = (double)sh[i][q] + (double)sl[i][q];
+      if (c0 + cc < nc) {
+        const double r = (double)sh[i][q] + (double)sl[i][q];
+        out[(size_t)k * nc + cc] = ACC ? out[(size_t)k * nc + cc] + r : r;
+      }
     }
   }
+}
+
+// List-form translation out[b] (=, or += with acc) sum_v T[off[v]] in[src[v]]
+// over v in [ptr[b], ptr[b+1]) for boxes b in [b0, b0 + nbx): M2L over the
+// V-lists, M2M over the children, L2L from the parent.  Shared-memory tiled
+// FP32 (or double-float FP64) kernels; callers check xlate_tiled() first.
+template <int RI, bool ACC>
+static void run_tiled(dim3 g, int nc, int ncoef, int b0, const int32_t* ptr, const int32_t* src,
+                      const int16_t* off, const float* tm, const float* in, float* out, cudaStream_t s) {
+  static bool set = false;
+  const size_t sm = sizeof(float) * (size_t)ncoef * (16 * RI + 64);
+  if (!set) {
+    XRL_CUDA(cudaFuncSetAttribute(k_m2l_tiled<RI, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(float) * 16 * RI * (16 * RI + 64))));
+    set = true;
+  }
+  k_m2l_tiled<RI, ACC><<<g, 128, sm, s>>>(nc, ncoef, b0, ptr, src, off, tm, in, out);
+}
+
+template <bool ACC>
+static void run_df64(dim3 g, int nc, int ncoef, int b0, const int32_t* ptr, const int32_t* src,
+                     const int16_t* off, const double* tm, const double* in, double* out, cudaStream_t s) {
+  static bool set = false;
+  const size_t sm = sizeof(float2) * (size_t)ncoef * (96 + 64);
+  if (!set) {
+    XRL_CUDA(cudaFuncSetAttribute(k_m2l_df64<ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 160 * 8));
+    set = true;
+  }
+  k_m2l_df64<ACC><<<g, 256, sm, s>>>(nc, ncoef, b0, ptr, src, off, tm, in, out);
 }
 
 template <class T>
-static void launch_m2l(int nbx, int b0, int nc, int ct_e, int ncoef, const int32_t* vptr, const int32_t* vsrc,
-                       const int16_t* voff, const T* tm2l, const T* Mx, T* Lx, cudaStream_t s, bool df64) {
-  if (sizeof(T) == 8 && df64 && nc >= 32 && ncoef <= 96) {
-    static bool set = false;
-    const size_t sm = sizeof(float2) * (size_t)ncoef * (96 + 64);
-    if (!set) {
-      XRL_CUDA(cudaFuncSetAttribute(k_m2l_df64, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 160 * 8));
-      set = true;
-    }
-    k_m2l_df64<<<dim3(nbx, (nc + 63) / 64), 256, sm, s>>>(nc, ncoef, b0, vptr, vsrc, voff, (const double*)tm2l,
-                                                          (const double*)Mx, (double*)Lx);
-    return;
-  }
-  k_m2l<T><<<dim3(nbx, (nc + ct_e - 1) / ct_e), 256, 0, s>>>(nc, ct_e, ncoef, b0, vptr, vsrc, voff, tm2l, Mx, Lx);
+static bool xlate_tiled(const xrl_ctx* c, int nc) {
+  if (sizeof(T) == 4) return nc >= 32 && c->ncoef <= 16 * 11;
+  return c->df64_m2l && nc >= 32 && c->ncoef <= 96;
+}
+
+template <class T>
+static void launch_xlate(int nbx, int b0, int nc, int ncoef, const int32_t* ptr, const int32_t* src,
+                         const int16_t* off, const T* tm, const T* in, T* out, bool acc, cudaStream_t s);
+
+template <>
+void launch_xlate<double>(int nbx, int b0, int nc, int ncoef, const int32_t* ptr, const int32_t* src,
+                          const int16_t* off, const double* tm, const double* in, double* out, bool acc,
+                          cudaStream_t s) {
+  dim3 g(nbx, (nc + 63) / 64);
+  if (acc)
+    run_df64<true>(g, nc, ncoef, b0, ptr, src, off, tm, in, out, s);
+  else
+    run_df64<false>(g, nc, ncoef, b0, ptr, src, off, tm, in, out, s);
 }
 
 template <>
-void launch_m2l<float>(int nbx, int b0, int nc, int ct_e, int ncoef, const int32_t* vptr, const int32_t* vsrc,
-                       const int16_t* voff, const float* tm2l, const float* Mx, float* Lx, cudaStream_t s, bool) {
-  if (nc < 32 || ncoef > 16 * 11) {
-    k_m2l<float><<<dim3(nbx, (nc + ct_e - 1) / ct_e), 256, 0, s>>>(nc, ct_e, ncoef, b0, vptr, vsrc, voff, tm2l, Mx,
-                                                                   Lx);
-    return;
-  }
+void launch_xlate<float>(int nbx, int b0, int nc, int ncoef, const int32_t* ptr, const int32_t* src,
+                         const int16_t* off, const float* tm, const float* in, float* out, bool acc,
+                         cudaStream_t s) {
   dim3 g(nbx, (nc + 63) / 64);
   if (ncoef <= 64) {
-    size_t sm = sizeof(float) * (size_t)ncoef * (16 * 4 + 64);
-    k_m2l_tiled<4><<<g, 128, sm, s>>>(nc, ncoef, b0, vptr, vsrc, voff, tm2l, Mx, Lx);
+    if (acc) run_tiled<4, true>(g, nc, ncoef, b0, ptr, src, off, tm, in, out, s);
+    else run_tiled<4, false>(g, nc, ncoef, b0, ptr, src, off, tm, in, out, s);
   } else if (ncoef <= 96) {
-    size_t sm = sizeof(float) * (size_t)ncoef * (16 * 6 + 64);
-    static bool set6 = false;
-    if (!set6) {
-      XRL_CUDA(cudaFuncSetAttribute(k_m2l_tiled<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 160 * 4));
-      set6 = true;
-    }
-    k_m2l_tiled<6><<<g, 128, sm, s>>>(nc, ncoef, b0, vptr, vsrc, voff, tm2l, Mx, Lx);
+    if (acc) run_tiled<6, true>(g, nc, ncoef, b0, ptr, src, off, tm, in, out, s);
+    else run_tiled<6, false>(g, nc, ncoef, b0, ptr, src, off, tm, in, out, s);
   } else {
-    size_t sm = sizeof(float) * (size_t)ncoef * (16 * 11 + 64);
-    static bool set11 = false;
-    if (!set11) {
-      XRL_CUDA(cudaFuncSetAttribute(k_m2l_tiled<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, 176 * 240 * 4));
-      set11 = true;
-    }
-    k_m2l_tiled<11><<<g, 128, sm, s>>>(nc, ncoef, b0, vptr, vsrc, voff, tm2l, Mx, Lx);
+    if (acc) run_tiled<11, true>(g, nc, ncoef, b0, ptr, src, off, tm, in, out, s);
+    else run_tiled<11, false>(g, nc, ncoef, b0, ptr, src, off, tm, in, out, s);
   }
 }
 
@@ -506,10 +543,19 @@ void fmm_prepare(xrl_ctx* c) {
   c->d.box_child_ptr.upload(c->alloc, child_ptr);
   c->d.box_parent.upload(c->alloc, t.parent);
   c->d.box_oct.upload(c->alloc, t.octant);
+  // list-form arrays: M2M lists are the children (source = box id), L2L
+  // lists the single parent (one entry per box)
+  std::vector<int32_t> iota(nb + 1);
+  std::vector<int16_t> oct16(nb);
+  for (int b = 0; b <= nb; ++b) iota[b] = b;
+  for (int b = 0; b < nb; ++b) oct16[b] = (int16_t)std::max(0, t.octant[b]);
+  c->d.box_iota.upload(c->alloc, iota);
+  c->d.box_oct16.upload(c->alloc, oct16);
   std::vector<int32_t> vptr(t.v_ptr.begin(), t.v_ptr.end());
   c->d.v_ptr32.upload(c->alloc, vptr);
   c->d.v_src.upload(c->alloc, t.v_src);
   c->d.v_off.upload(c->alloc, t.v_off);
+  tc_prepare(c);
   // FP32 copies for the mixed-precision path
   auto cast = [&](const DBuf<double>& a, DBuf<float>& b) {
     b.alloc(c->alloc, a.n);
@@ -559,10 +605,15 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
                                            Mx);
   prof_end(c, s, ev, PH_P2M, 1, 2.0 * N * ncoef * nc, N * ncoef * sz + N * nc * sz + nl * ebytes);
   ev = prof_begin(c, s);
+  const bool tiled = xlate_tiled<T>(c, nc);
   for (int l = L - 1; l >= 2; --l) {
     int nbx = t.level_off[l + 1] - t.level_off[l];
-    k_m2m<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, t.level_off[l], c->d.box_child_ptr.p,
-                                              c->d.box_oct.p, tm2m, Mx);
+    if (tiled)
+      launch_xlate<T>(nbx, t.level_off[l], nc, ncoef, c->d.box_child_ptr.p, c->d.box_iota.p, c->d.box_oct16.p, tm2m,
+                      Mx, Mx, false, s);
+    else
+      k_m2m<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, t.level_off[l], c->d.box_child_ptr.p,
+                                                c->d.box_oct.p, tm2m, Mx);
   }
   {
     double nch = (double)(t.level_off[L + 1] - t.level_off[std::min(3, L + 1)]);
@@ -573,14 +624,28 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     int b0 = t.level_off[2];
     int nbx = t.level_off[L + 1] - b0;
     ev = prof_begin(c, s);
-    launch_m2l<T>(nbx, b0, nc, ct_e, ncoef, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p, tm2l, Mx, Lx, s, c->df64_m2l);
-    prof_end(c, s, ev, sizeof(T) == 8 ? PH_M2L64 : PH_M2L, 1, e2 * (double)t.v_src.size(), 2.0 * nbx * ebytes);
+    int nl_m2l = 1;
+    if (sizeof(T) == 4 && tc_usable(c, nc)) {
+      tc_m2l(c, nbx, b0, nc, (const float*)Mx, (float*)Lx, s);
+      nl_m2l = 2;
+    } else if (tiled) {
+      launch_xlate<T>(nbx, b0, nc, ncoef, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p, tm2l, Mx, Lx, false, s);
+    } else {
+      k_m2l<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, b0, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p,
+                                                tm2l, Mx, Lx);
+    }
+    prof_end(c, s, ev, sizeof(T) == 8 ? PH_M2L64 : PH_M2L, nl_m2l, e2 * (double)t.v_src.size(),
+             2.0 * nbx * ebytes);
   }
   ev = prof_begin(c, s);
   for (int l = 3; l <= L; ++l) {
     int nbx = t.level_off[l + 1] - t.level_off[l];
-    k_l2l<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, t.level_off[l], c->d.box_parent.p,
-                                              c->d.box_oct.p, tl2l, Lx);
+    if (tiled)
+      launch_xlate<T>(nbx, t.level_off[l], nc, ncoef, c->d.box_iota.p, c->d.box_parent.p, c->d.box_oct16.p, tl2l,
+                      Lx, Lx, true, s);
+    else
+      k_l2l<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, t.level_off[l], c->d.box_parent.p,
+                                                c->d.box_oct.p, tl2l, Lx);
   }
   {
     double nch = (double)(t.level_off[L + 1] - t.level_off[std::min(3, L + 1)]);

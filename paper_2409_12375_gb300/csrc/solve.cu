@@ -921,6 +921,7 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
   XRL_CUDA(cudaMemcpyAsync(R, dR.p, sizeof(double) * nf * np * np, cudaMemcpyDeviceToHost, s));
   XRL_CUDA(cudaMemcpyAsync(L, dL.p, sizeof(double) * nf * np * np, cudaMemcpyDeviceToHost, s));
   XRL_CUDA(cudaStreamSynchronize(s));
+  tc_check(c, s);
   double mr = 0;
   int mi = 0;
   for (int q = 0; q < nsys; ++q) {

@@ -1,0 +1,450 @@
+// Tensor-core (tcgen05) list-form translation for the FP32 FMM pass
+// (Sec. II-C): out[b] (=, or +=) sum_v T[off[v]] in[src[v]] over the V-list of
+// target box b, for 128-column tiles of the right-hand sides.
+//
+// Per (target box, 128-column tile) one CTA accumulates D[c][n] (c = column,
+// n = output coefficient) in tensor memory: D = sum_v A_v B_v with
+// A_v[c][k] = in[src[v]][k][c] (128 x Kp) and B_v[k][n] = T[off[v]][k][n]
+// (Kp x Np), Kp, Np the coefficient count (p+1)^2 padded to 16.  FP32
+// accuracy comes from a three-piece BF16 split x = x0 + x1 + x2 (x0 = bf16(x),
+// x1 = bf16(x - x0), x2 = bf16(x - x0 - x1); residual ~2^-27 |x|) and the six
+// products x_i y_j with i + j <= 2 (the dropped ones are ~2^-27 relative), all
+// exact in FP32 and accumulated in FP32 by the tensor core.  (A two-piece TF32
+// split keeps only ~2^-21 per product, measurably worse than FP32.)
+//
+// Operands live in global memory as "packed images" in the tensor core's
+// K-major, no-swizzle shared-memory layout, so that one pipeline stage is two
+// plain bulk copies (cp.async.bulk) and no thread touches the operand bytes:
+//   per operand of R rows: K chunks of 32 (the last one kc = Kp - 32 c),
+//   each chunk [x0 | x1 | x2], each piece [R/8 row groups][kc/8 core columns]
+//   of 8 x 16-byte core matrices (row r at +16 (r % 8), column k at +2 (k % 8)).
+// The translation tables are packed once per context (from FP64, so the
+// split is that of the exact table); the expansions once per product.
+//
+// Warp roles: warp 0 lane 0 issues the bulk copies, warp 1 lane 0 issues the
+// MMAs (one thread, as tcgen05.mma requires), warps 2..5 drain the
+// accumulators (warp w reads TMEM lanes 32 (w % 4) .. + 31).  Every wait is
+// bounded; on a timeout the kernel raises *err, drains its own copies and
+// frees its tensor memory.
+#include <cuda_bf16.h>
+
+#include "xrl_internal.hpp"
+
+namespace xrl {
+
+namespace {
+
+constexpr int TC_ROWS = 128;     // columns per tile (MMA M)
+constexpr int TC_KC = 32;        // K chunk per pipeline stage (elements)
+constexpr int TC_STAGES = 4;
+constexpr int TC_PIECES = 3;
+constexpr long long TC_WAIT_CYCLES = 4000000000ll;   // ~2 s at the maximum SM clock
+
+// bytes of one K chunk (all pieces) of an operand of R rows
+__host__ __device__ inline int tc_chunk_bytes(int R, int kc) { return TC_PIECES * R * kc * 2; }
+
+// byte offset of element (r, k), piece h, in the packed image of R rows x Kp
+__host__ __device__ inline size_t tc_img_off(int R, int Kp, int r, int k, int h) {
+  const int c = k >> 5;
+  const int kc = (Kp - 32 * c) < 32 ? (Kp - 32 * c) : 32;
+  const int kq = (k & 31) >> 3;
+  return (size_t)tc_chunk_bytes(R, 32) * c + (size_t)h * R * kc * 2 + ((size_t)(r >> 3) * (kc >> 3) + kq) * 128 +
+         (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint32_t sm_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf16_val(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(sm_u32(b)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait for the phase of parity `parity`; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  if (mbar_try(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(b, parity))
+    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+  return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   sm_u32(dst)),
+               "l"(src), "r"(bytes), "r"(sm_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, no swizzle; lbo = byte step
+// between the two core matrices along K, sbo = byte step between 8-row groups
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sm_u32(bar))
+               : "memory");
+}
+
+}  // namespace
+
+// Pack FP32 expansions in[box][k][col] (boxes [b0, b0 + gridDim.x), column
+// tile blockIdx.y) into the A image; columns >= nc and k >= ncoef are zero.
+// One thread per (row, 8-element core row): three 16-byte stores.
+__global__ void k_tc_pack_a(int nc, int ncoef, int Kp, int b0, const float* __restrict__ in,
+                            uint16_t* __restrict__ img) {
+  const int ct = blockIdx.y;
+  const float* src = in + (size_t)(b0 + blockIdx.x) * ncoef * nc + (size_t)ct * TC_ROWS;
+  char* dst = reinterpret_cast<char*>(img) + ((size_t)blockIdx.x * gridDim.y + ct) * (size_t)(TC_PIECES * 2 * TC_ROWS * Kp);
+  const int nq = Kp >> 3;
+  for (int e = threadIdx.x; e < TC_ROWS * nq; e += blockDim.x) {
+    const int r = e & (TC_ROWS - 1), kq = e >> 7;
+    const bool col_ok = ct * TC_ROWS + r < nc;
+    uint16_t p0[8], p1[8], p2[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = 8 * kq + q;
+      const float x = (col_ok && k < ncoef) ? src[(size_t)k * nc + r] : 0.f;
+      p0[q] = bf16_bits(x);
+      const float r1 = x - bf16_val(p0[q]);
+      p1[q] = bf16_bits(r1);
+      p2[q] = bf16_bits(r1 - bf16_val(p1[q]));
+    }
+    uint4 v0, v1, v2;
+    v0.x = p0[0] | (uint32_t)p0[1] << 16; v0.y = p0[2] | (uint32_t)p0[3] << 16;
+    v0.z = p0[4] | (uint32_t)p0[5] << 16; v0.w = p0[6] | (uint32_t)p0[7] << 16;
+    v1.x = p1[0] | (uint32_t)p1[1] << 16; v1.y = p1[2] | (uint32_t)p1[3] << 16;
+    v1.z = p1[4] | (uint32_t)p1[5] << 16; v1.w = p1[6] | (uint32_t)p1[7] << 16;
+    v2.x = p2[0] | (uint32_t)p2[1] << 16; v2.y = p2[2] | (uint32_t)p2[3] << 16;
+    v2.z = p2[4] | (uint32_t)p2[5] << 16; v2.w = p2[6] | (uint32_t)p2[7] << 16;
+    *reinterpret_cast<uint4*>(dst + tc_img_off(TC_ROWS, Kp, r, 8 * kq, 0)) = v0;
+    *reinterpret_cast<uint4*>(dst + tc_img_off(TC_ROWS, Kp, r, 8 * kq, 1)) = v1;
+    *reinterpret_cast<uint4*>(dst + tc_img_off(TC_ROWS, Kp, r, 8 * kq, 2)) = v2;
+  }
+}
+
+// Pack translation tables T[o][k_in][n_out] (FP64, [in][out]) into B images
+// of Np rows (n) by Kp (k), one per table (blockIdx.x); split from FP64.
+__global__ void k_tc_pack_b(int ncoef, int Kp, int Np, const double* __restrict__ T, uint16_t* __restrict__ img) {
+  const int o = blockIdx.x;
+  const double* tm = T + (size_t)o * ncoef * ncoef;
+  char* dst = reinterpret_cast<char*>(img) + (size_t)o * (size_t)(TC_PIECES * 2 * Np * Kp);
+  for (int e = threadIdx.x; e < Np * Kp; e += blockDim.x) {
+    const int r = e % Np, k = e / Np;
+    const double x = (r < ncoef && k < ncoef) ? tm[(size_t)k * ncoef + r] : 0.0;
+    const uint16_t b0 = bf16_bits(__double2float_rn(x));
+    const double r1 = x - (double)bf16_val(b0);
+    const uint16_t b1 = bf16_bits(__double2float_rn(r1));
+    const double r2 = r1 - (double)bf16_val(b1);
+    const uint16_t b2 = bf16_bits(__double2float_rn(r2));
+    *reinterpret_cast<uint16_t*>(dst + tc_img_off(Np, Kp, r, k, 0)) = b0;
+    *reinterpret_cast<uint16_t*>(dst + tc_img_off(Np, Kp, r, k, 1)) = b1;
+    *reinterpret_cast<uint16_t*>(dst + tc_img_off(Np, Kp, r, k, 2)) = b2;
+  }
+}
+
+struct TcArgs {
+  int nc, ncoef, Kp, Np, b0, src0, nct;
+  const int32_t* ptr;
+  const int32_t* src;
+  const int16_t* off;
+  const char* aimg;
+  const char* bimg;
+  float* out;
+  int32_t* err;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(b)) : "memory");
+}
+
+// Warps: 0 = bulk-copy producer (lane 0; the whole warp owns the TMEM
+// allocation), 1 = MMA issuer (lane 0), 2..5 = accumulator drain/epilogue.
+// TMEM (512 columns): for the pair buffer q in {0, 1} the x0 y0 products go to
+// columns 256 q and the five small products to 256 q + 128.  After every
+// V-list pair the epilogue warps add both into FP32 registers (IEEE
+// round-to-nearest), so the tensor core only ever accumulates the 6 (resp.
+// 30) MMAs of one pair: its truncating block accumulation would otherwise
+// bias sums over thousands of MMAs.
+template <int NP>
+__global__ void __launch_bounds__(192, 1) k_xlate_tc(TcArgs a) {
+  extern __shared__ uint8_t tc_smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
+  const int a_stage = tc_chunk_bytes(TC_ROWS, TC_KC);
+  const int stage_bytes = a_stage + tc_chunk_bytes(NP, TC_KC);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + TC_STAGES * stage_bytes);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* tfull = empty + TC_STAGES;   // [2]: pair buffer written
+  uint64_t* tfree = tfull + 2;           // [2]: pair buffer drained
+  uint64_t* mdone = tfree + 2;           // all MMAs of this CTA complete
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
+  int* bad = reinterpret_cast<int*>(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int Bx = a.b0 + blockIdx.x, ct = blockIdx.y;
+  const int vs = a.ptr[Bx], ve = a.ptr[Bx + 1];
+  const int nv = ve - vs;
+  const int nch = (a.Kp + TC_KC - 1) / TC_KC;
+  const int items = nv * nch;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&tfull[q], 1);
+      mbar_init(&tfree[q], 4);
+    }
+    mbar_init(mdone, 1);
+    *bad = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_u32(tslot)), "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  int issued = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int it = 0; it < items; ++it) {
+        const int st = it % TC_STAGES, u = it / TC_STAGES;
+        if (u > 0 && !mbar_wait(&empty[st], (u - 1) & 1)) {
+          atomicExch(bad, 1);
+          break;
+        }
+        const int v = vs + it / nch, c = it % nch;
+        const int kc = min(TC_KC, a.Kp - TC_KC * c);
+        const char* asrc = a.aimg +
+                           ((size_t)(a.src[v] - a.src0) * a.nct + ct) * (size_t)(TC_PIECES * 2 * TC_ROWS * a.Kp) +
+                           (size_t)a_stage * c;
+        const char* bsrc =
+            a.bimg + (size_t)a.off[v] * (size_t)(TC_PIECES * 2 * NP * a.Kp) + (size_t)tc_chunk_bytes(NP, TC_KC) * c;
+        const uint32_t ab = tc_chunk_bytes(TC_ROWS, kc), bb = tc_chunk_bytes(NP, kc);
+        uint8_t* sa = base + (size_t)st * stage_bytes;
+        mbar_expect_tx(&full[st], ab + bb);
+        bulk_g2s(sa, asrc, ab, &full[st]);
+        bulk_g2s(sa + a_stage, bsrc, bb, &full[st]);
+        issued = it + 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // D f32, A and B bf16, K-major both, N = NP, M = 128
+      const uint32_t idesc =
+          (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
+      for (int it = 0; it < items; ++it) {
+        const int st = it % TC_STAGES, u = it / TC_STAGES;
+        const int j = it / nch, c = it % nch, q = j & 1;
+        if (c == 0 && j >= 2 && !mbar_wait(&tfree[q], ((j >> 1) - 1) & 1)) {
+          atomicExch(bad, 1);
+          break;
+        }
+        if (!mbar_wait(&full[st], u & 1)) {
+          atomicExch(bad, 1);
+          break;
+        }
+        tc_fence_after();
+        const int kc = min(TC_KC, a.Kp - TC_KC * c);
+        const uint32_t sa = sm_u32(base + (size_t)st * stage_bytes);
+        const uint32_t sb = sa + a_stage;
+        const uint32_t pa = TC_ROWS * kc * 2, pb = NP * kc * 2;   // piece strides
+        const uint32_t sbo = 16 * kc;                             // (kc / 8) cores of 128 B
+        const uint32_t dbig = tbase + 256u * q, dsmall = dbig + 128u;
+        for (int ks = 0; ks < kc / 16; ++ks) {
+          uint64_t da[3], db[3];
+#pragma unroll
+          for (int h = 0; h < 3; ++h) {
+            da[h] = sdesc(sa + h * pa + 256 * ks, 128, sbo);
+            db[h] = sdesc(sb + h * pb + 256 * ks, 128, sbo);
+          }
+          const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
+          mma_bf16(dbig, da[0], db[0], idesc, accum);
+          mma_bf16(dsmall, da[1], db[1], idesc, accum);
+          mma_bf16(dsmall, da[0], db[2], idesc, 1u);
+          mma_bf16(dsmall, da[2], db[0], idesc, 1u);
+          mma_bf16(dsmall, da[0], db[1], idesc, 1u);
+          mma_bf16(dsmall, da[1], db[0], idesc, 1u);
+        }
+        tc_commit(&empty[st]);
+        if (c == nch - 1) tc_commit(&tfull[q]);
+      }
+      tc_commit(mdone);
+      if (!mbar_wait(mdone, 0)) atomicExch(bad, 1);
+    }
+    __syncwarp();
+  } else {
+    // epilogue warps: TMEM lane quarter warp % 4 = columns of this thread
+    const int quarter = warp & 3;
+    const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+    float acc[NP];
+#pragma unroll
+    for (int n = 0; n < NP; ++n) acc[n] = 0.f;
+    for (int j = 0; j < nv; ++j) {
+      const int q = j & 1;
+      bool ok = mbar_wait(&tfull[q], (j >> 1) & 1);
+      ok = __all_sync(0xffffffffu, ok);   // the loads below need the whole warp
+      if (!ok) {
+        atomicExch(bad, 1);
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int s = 1; s >= 0; --s) {
+        uint32_t r[NP];
+#pragma unroll
+        for (int n0 = 0; n0 < NP; n0 += 16)
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];"
+              : "=r"(r[n0 + 0]), "=r"(r[n0 + 1]), "=r"(r[n0 + 2]), "=r"(r[n0 + 3]), "=r"(r[n0 + 4]),
+                "=r"(r[n0 + 5]), "=r"(r[n0 + 6]), "=r"(r[n0 + 7]), "=r"(r[n0 + 8]), "=r"(r[n0 + 9]),
+                "=r"(r[n0 + 10]), "=r"(r[n0 + 11]), "=r"(r[n0 + 12]), "=r"(r[n0 + 13]), "=r"(r[n0 + 14]),
+                "=r"(r[n0 + 15])
+              : "r"(tbase + lane_base + 256u * q + 128u * s + (uint32_t)n0)
+              : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int n = 0; n < NP; ++n) acc[n] += __uint_as_float(r[n]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tfree[q]);
+    }
+    const int col = ct * TC_ROWS + 32 * quarter + lane;
+    if (col < a.nc) {
+      float* outp = a.out + (size_t)Bx * a.ncoef * a.nc + col;
+#pragma unroll
+      for (int n = 0; n < NP; ++n)
+        if (n < a.ncoef) outp[(size_t)n * a.nc] = acc[n];
+    }
+  }
+  __syncthreads();
+  if (*bad) {
+    if (threadIdx.x == 0) atomicExch(a.err, 1);
+    // drain this CTA's own copies still in flight
+    if (warp == 0 && lane == 0)
+      for (int it = issued > TC_STAGES ? issued - TC_STAGES : 0; it < issued; ++it)
+        mbar_wait(&full[it % TC_STAGES], (it / TC_STAGES) & 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512) : "memory");
+  }
+}
+
+// ---- host side ---------------------------------------------------------------------------
+
+static int tc_kpad(int ncoef) { return (ncoef + 15) & ~15; }
+static int tc_npad(int ncoef) { return (ncoef + 15) & ~15; }
+
+bool tc_usable(const xrl_ctx* c, int nc) {
+  return c->opt.tensor_cores != 0 && nc >= 64 && tc_npad(c->ncoef) <= 96 && c->d.tc_bimg.n > 0;
+}
+
+void tc_prepare(xrl_ctx* c) {
+  const int ncoef = c->ncoef;
+  if (c->opt.tensor_cores == 0 || tc_npad(ncoef) > 96) return;
+  const int Kp = tc_kpad(ncoef), Np = tc_npad(ncoef);
+  const int noff = (int)(c->tree.m2l_offsets.size() / 3);
+  if (noff == 0) return;
+  c->d.tc_bimg.alloc(c->alloc, (size_t)noff * TC_PIECES * Np * Kp);
+  k_tc_pack_b<<<noff, 256, 0, c->stream>>>(ncoef, Kp, Np, c->d.t_m2l.p, c->d.tc_bimg.p);
+  XRL_CUDA(cudaGetLastError());
+  c->d.tc_err.alloc(c->alloc, 1);
+  XRL_CUDA(cudaMemsetAsync(c->d.tc_err.p, 0, sizeof(int32_t), c->stream));
+}
+
+// M2L of the FP32 pass: in = M, out = L over all target boxes [b0, b0 + nbx);
+// two launches (pack, translate)
+void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cudaStream_t s) {
+  const Tree& t = c->tree;
+  const int ncoef = c->ncoef, Kp = tc_kpad(ncoef), Np = tc_npad(ncoef);
+  const int nct = (nc + TC_ROWS - 1) / TC_ROWS;
+  const int src0 = t.level_off[2];
+  const int nsrc = t.n_boxes() - src0;
+  c->d.tc_aimg.ensure(c->alloc, (size_t)nsrc * nct * TC_PIECES * TC_ROWS * Kp);
+  k_tc_pack_a<<<dim3(nsrc, nct), 256, 0, s>>>(nc, ncoef, Kp, src0, Mx, c->d.tc_aimg.p);
+  TcArgs a;
+  a.nc = nc;
+  a.ncoef = ncoef;
+  a.Kp = Kp;
+  a.Np = Np;
+  a.b0 = b0;
+  a.src0 = src0;
+  a.nct = nct;
+  a.ptr = c->d.v_ptr32.p;
+  a.src = c->d.v_src.p;
+  a.off = c->d.v_off.p;
+  a.aimg = reinterpret_cast<const char*>(c->d.tc_aimg.p);
+  a.bimg = reinterpret_cast<const char*>(c->d.tc_bimg.p);
+  a.out = Lx;
+  a.err = c->d.tc_err.p;
+  const size_t smem = (size_t)TC_STAGES * (tc_chunk_bytes(TC_ROWS, TC_KC) + tc_chunk_bytes(Np, TC_KC)) + 1024 + 128;
+  if (Np <= 64) {
+    static bool set = false;
+    if (!set) {
+      XRL_CUDA(cudaFuncSetAttribute(k_xlate_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      set = true;
+    }
+    k_xlate_tc<64><<<dim3(nbx, nct), 192, smem, s>>>(a);
+  } else {
+    static bool set = false;
+    if (!set) {
+      XRL_CUDA(cudaFuncSetAttribute(k_xlate_tc<96>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      set = true;
+    }
+    k_xlate_tc<96><<<dim3(nbx, nct), 192, smem, s>>>(a);
+  }
+}
+
+// raises XRL_ETIMEOUT if a tensor-core kernel gave up a wait since the last check
+void tc_check(xrl_ctx* c, cudaStream_t s) {
+  if (c->d.tc_err.n == 0) return;
+  int32_t h = 0;
+  XRL_CUDA(cudaMemcpyAsync(&h, c->d.tc_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  XRL_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    XRL_CUDA(cudaMemsetAsync(c->d.tc_err.p, 0, sizeof(int32_t), s));
+    throw Error(XRL_ETIMEOUT, "a tensor-core translation kernel timed out waiting on its pipeline");
+  }
+}
+
+}  // namespace xrl

@@ -190,6 +190,11 @@ struct Dev {
   DBuf<double> t_m2m, t_l2l, t_m2l;                  // translation matrices (transposed)
   DBuf<float> t_m2m32, t_l2l32, t_m2l32;
   DBuf<int32_t> box_parent, box_oct, box_child_ptr, box_child;  // tree arrays (global ids)
+  DBuf<int32_t> box_iota;   // 0..n_boxes (list pointers / sources of the list-form M2M, L2L)
+  DBuf<int16_t> box_oct16;  // octant as a translation index
+  DBuf<uint16_t> tc_bimg;   // packed 3-piece BF16 images of the M2L tables (tensor-core path)
+  DBuf<uint16_t> tc_aimg;   // packed 3-piece BF16 images of the FP32 multipoles, per product
+  DBuf<int32_t> tc_err;     // set by a tensor-core kernel that timed out
   DBuf<int32_t> v_ptr32, v_src;
   DBuf<int16_t> v_off;
   DBuf<int32_t> lvl_boxes;                            // per level: global ids of its boxes (same as range)
@@ -303,6 +308,13 @@ void fmm_apply32(xrl_ctx* c, int ncols, const float* X, float* Y, cudaStream_t s
 void fmm_apply_into(xrl_ctx* c, int ncols, const double* X, double* Y, double* Mx, double* Lx, cudaStream_t s);
 void launch_to_morton(const xrl_ctx* c, int ncols, const double* x_user, double* X, cudaStream_t s);
 void launch_from_morton(const xrl_ctx* c, int ncols, const double* Y, double* y_user, cudaStream_t s);
+void launch_to_morton32(const xrl_ctx* c, int ncols, const float* x_user, float* X, cudaStream_t s);
+void launch_from_morton32(const xrl_ctx* c, int ncols, const float* Y, float* y_user, cudaStream_t s);
+// tc.cu: tensor-core (tcgen05) M2L of the FP32 products
+bool tc_usable(const xrl_ctx* c, int ncols);
+void tc_prepare(xrl_ctx* c);
+void tc_m2l(xrl_ctx* c, int nbx, int b0, int ncols, const float* M, float* L, cudaStream_t s);
+void tc_check(xrl_ctx* c, cudaStream_t s);
 // solve.cu
 void solver_prepare(xrl_ctx* c);
 void run_solve(xrl_ctx* c, int nf, const double* f, double* R, double* L, const float* shape = nullptr,

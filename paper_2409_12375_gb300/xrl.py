@@ -30,7 +30,7 @@ class Options(ctypes.Structure):
                 ("inner_iters", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("device", ctypes.c_int32), ("separation", ctypes.c_int32),
-                ("use_graphs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("use_graphs", ctypes.c_int32), ("tensor_cores", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -66,6 +66,7 @@ SIGNATURES = {
     "xrl_fmm_mvm_device_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "xrl_direct_mvm_device": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "xrl_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
+    "xrl_fmm_mvm32_device": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "xrl_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _I, _I, _D, _D]),
     "xrl_solve": (ctypes.c_int, [_P, ctypes.c_int32, _D, _D, _D]),
     "xrl_apply_operator": (ctypes.c_int, [_P, ctypes.c_int32, _D, _D, _D]),
@@ -211,6 +212,14 @@ class XRL:
         s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
         self._check(lib().xrl_fmm_mvm_device(self.h, nc, ctypes.c_void_p(x.data_ptr()),
                                              ctypes.c_void_p(y.data_ptr()), s), self.h)
+
+    def fmm_mvm32_device(self, x, y, stream=None):
+        """y = P x in the FP32 inner-iteration product on torch CUDA float32 tensors [n_cols][N]."""
+        assert x.is_cuda and x.is_contiguous() and y.is_contiguous()
+        nc = 1 if x.dim() == 1 else x.shape[0]
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        self._check(lib().xrl_fmm_mvm32_device(self.h, nc, ctypes.c_void_p(x.data_ptr()),
+                                               ctypes.c_void_p(y.data_ptr()), s), self.h)
 
     def direct_mvm_device(self, x, y, stream=None):
         assert x.is_cuda and x.is_contiguous() and y.is_contiguous()

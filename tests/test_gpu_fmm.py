@@ -135,3 +135,63 @@ def test_fmm_full_size_coils_sampled_rows(coils_ctx, coils_mesh):
     got = y[:, rows]
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err < 1e-6, err
+
+
+# ---- FP32 product of the inner iterations (tensor-core M2L and CUDA-core M2L) ----------
+# Tolerance: FP32 unit roundoff 6e-8 grown over sums of ~1e3-1e4 terms (near-field
+# rows, 81-term translations over ~100 V-list entries) gives a few 1e-7; the order-8
+# truncation adds ~1e-7.  2e-6 leaves an order of magnitude over what a correct
+# kernel reaches while a wrong operand layout or split gives O(1e-3) or worse.
+FP32_TOL = 2e-6
+
+
+def _fp32_product(ctx, x):
+    import torch
+    xd = torch.tensor(np.ascontiguousarray(x, np.float32), device="cuda:0")
+    yd = torch.empty_like(xd)
+    ctx.fmm_mvm32_device(xd, yd)
+    torch.cuda.synchronize()
+    return yd.cpu().numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def bar_ctx_scalar(lib, bar_mesh):
+    x = lib.XRL.from_mesh(bar_mesh, fmm_order=8, tensor_cores=0)
+    yield x
+    x.close()
+
+
+@pytest.mark.parametrize("nc", [1, 40, 64, 200, 384])
+def test_fp32_product_matches_dense_oracle(bar_ctx, bar_ctx_scalar, bar_dense_P, nc):
+    """nc >= 64 takes the tcgen05 M2L on the default context (ragged last
+    128-column tile at 200); the scalar context runs the CUDA-core kernels."""
+    rng = np.random.default_rng(100 + nc)
+    x = rng.standard_normal((nc, bar_dense_P.shape[0])).astype(np.float32).astype(np.float64)
+    ref = x @ bar_dense_P.T
+    for ctx in (bar_ctx, bar_ctx_scalar):
+        y = _fp32_product(ctx, x)
+        err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+        assert err < FP32_TOL, (ctx.opts.tensor_cores, err)
+
+
+def test_fp32_tensor_core_m2l_full_size_coils(coils_ctx, coils_mesh, lib):
+    """Coils (24,792 panels) at 384 columns, the launch configuration of the
+    solver's 64-system block: the tensor-core FP32 product against the FP64
+    product (itself checked on sampled oracle rows above), column by column.
+    With random-sign x the FP32 error of a row sum is ~u sqrt(n) |y|-relative
+    (n ~ 5e3 near-field terms: ~4e-6), so the bound here is 2e-5 and the
+    tensor-core path must be no worse than 1.5x the CUDA-core FP32 path."""
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((384, coils_mesh.n_tri)).astype(np.float32).astype(np.float64)
+    y64 = coils_ctx.fmm_mvm(x)
+    y32 = _fp32_product(coils_ctx, x)
+    sc = lib.XRL.from_mesh(coils_mesh, fmm_order=8, tensor_cores=0)
+    try:
+        ys = _fp32_product(sc, x)
+    finally:
+        sc.close()
+    nrm = np.linalg.norm(y64, axis=1)
+    e_tc = (np.linalg.norm(y32 - y64, axis=1) / nrm).max()
+    e_sc = (np.linalg.norm(ys - y64, axis=1) / nrm).max()
+    assert e_tc < 2e-5 and e_sc < 2e-5, (e_tc, e_sc)
+    assert e_tc < 1.5 * e_sc, (e_tc, e_sc)
