@@ -9,10 +9,24 @@
 // Q(f) = sum_m Z_s^m(f) QA_m + j omega mu0/4pi QP is complex symmetric with
 // positive definite real and imaginary parts, so LDL^T (transpose, not
 // conjugate transpose) without pivoting is stable (Higham, 1998).
-//  * factor: one CTA per frequency, right-looking over the band with the
-//    active (b+1) x (b+1) window in shared memory as a ring of rows;
-//  * apply: one warp per system, forward and backward substitution with the
-//    warp's lanes spanning the band, then the border correction.
+//
+// The band is solved by partitioning (the SPIKE scheme of Polizzi and Sameh,
+// 2006), exactly up to rounding: Q_vv splits into P diagonal blocks A_j of m
+// rows coupled through b x b corners B_j (rows of block j, columns of block
+// j+1) and C_j = B_{j-1}^T.  With y_j = A_j^-1 f_j and the spikes
+// V_j = A_j^-1 [0; B_j], W_j = A_j^-1 [C_j; 0] (m x b each),
+//   x_j = y_j - V_j t_{j+1} - W_j u_{j-1},
+// t_j, u_j the first and last b unknowns of block j.  Their 2b(P-1) values
+// solve a block-tridiagonal system in z_j = (u_j, t_{j+1}):
+//   E_j z_j + F_j z_{j-1} + G_j z_{j+1} = (y_j^bot, y_{j+1}^top),
+//   E_j = [I, V_j^bot; W_{j+1}^top, I], F_j = [W_j^bot 0; 0 0], G_j = [0 0; 0 V_{j+1}^top],
+// factored once by block LU (E^_j = E_j - F_j E^_{j-1}^-1 G_{j-1}, which only
+// changes the top-right block, stored as E^_j^-1).  So
+//  * factor: one warp per (frequency, block) for A_j = L D L^T, one warp per
+//    spike column, one CTA per frequency for the reduced system;
+//  * apply: one warp per (system pair, block) for y_j, one warp per system
+//    for the reduced forward/backward substitution, one CTA per system for the
+//    spike correction, the border correction and the scatter to loop order.
 #include <vector>
 
 #include "cplx.cuh"
@@ -22,59 +36,6 @@ namespace xrl {
 
 constexpr int kMaxBand = 63;     // window (b+1)^2 complex in shared memory
 constexpr int kMaxBorder = 16;
-
-// fac[f][i][k]: k < b strictly lower L (column i - b + k), k = b the diagonal D
-__global__ void k_band_factor(int n, int b, int nmat, const double* __restrict__ band_val,
-                              const cplx* __restrict__ zs, const double* __restrict__ wp_f, cplx* __restrict__ fac) {
-  extern __shared__ cplx win[];    // [(b+1)][(b+1)]
-  const int f = blockIdx.x;
-  const int nb1 = b + 1;
-  const size_t stride = (size_t)n * nb1;
-  const cplx* z = zs + (size_t)f * nmat;
-  const double wp = wp_f[f];
-  cplx* out = fac + (size_t)f * stride;
-  // load rows 0..b
-  for (int e = threadIdx.x; e < nb1 * nb1; e += blockDim.x) {
-    int r = e / nb1, k = e % nb1;
-    win[r * nb1 + k] = r < n ? pencil(band_val + (size_t)r * nb1 + k, stride, nmat, z, wp) : make_double2(0, 0);
-  }
-  __syncthreads();
-  const int npair = b * (b + 1) / 2;
-  for (int k = 0; k < n; ++k) {
-    const int sk = k % nb1;
-    const cplx Dk = win[sk * nb1 + b];
-    for (int t = threadIdx.x; t < b; t += blockDim.x) {
-      int i = k + 1 + t;
-      if (i < n) {
-        int si = i % nb1;
-        win[si * nb1 + (b - 1 - t)] = cdiv(win[si * nb1 + (b - 1 - t)], Dk);
-      }
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < npair; q += blockDim.x) {
-      // pair (ti, tj), 0 <= tj <= ti < b
-      int ti = (int)((sqrt(8.0 * q + 1.0) - 1.0) * 0.5);
-      while ((ti + 1) * (ti + 2) / 2 <= q) ++ti;
-      while (ti * (ti + 1) / 2 > q) --ti;
-      int tj = q - ti * (ti + 1) / 2;
-      int i = k + 1 + ti, j = k + 1 + tj;
-      if (i < n) {
-        int si = i % nb1, sj = j % nb1;
-        cplx lik = win[si * nb1 + (b - 1 - ti)];
-        cplx ljk = win[sj * nb1 + (b - 1 - tj)];
-        int idx = j - i + b;
-        win[si * nb1 + idx] = csub(win[si * nb1 + idx], cm(cm(lik, Dk), ljk));
-      }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb1; e += blockDim.x) out[(size_t)k * nb1 + e] = win[sk * nb1 + e];
-    __syncthreads();
-    const int r = k + nb1;
-    for (int e = threadIdx.x; e < nb1; e += blockDim.x)
-      win[sk * nb1 + e] = r < n ? pencil(band_val + (size_t)r * nb1 + e, stride, nmat, z, wp) : make_double2(0, 0);
-    __syncthreads();
-  }
-}
 
 // ---- asynchronous global -> shared copies (16 bytes each) ----------------------------------
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -375,20 +336,6 @@ __global__ void k_band_finish(int nf, int n, int b, cplx* __restrict__ fac, cplx
   if (fac32) facT32[rowg * rs32 + t] = make_float2((float)w.x, (float)w.y);
 }
 
-// W[f][g][:] = Q_vv(f)^-1 Q_vg(f)[:, g]: one warp per (f, g)
-__global__ void k_border_solve(int n, int b, int ng, int nmat, const double* __restrict__ border_vg,
-                               const cplx* __restrict__ zs, const double* __restrict__ wp_f,
-                               const cplx* __restrict__ fac, const cplx* __restrict__ facT, cplx* __restrict__ Wb) {
-  extern __shared__ cplx bsm[];
-  const int f = blockIdx.x / ng, g = blockIdx.x % ng;
-  const size_t vstride = (size_t)n * ng;
-  cplx* x = Wb + ((size_t)f * ng + g) * n;
-  for (int i = threadIdx.x; i < n; i += 32)
-    x[i] = pencil(border_vg + (size_t)i * ng + g, vstride, nmat, zs + (size_t)f * nmat, wp_f[f]);
-  __syncwarp();
-  band_solve_warp<cplx>(n, b, b + 1, facT + (size_t)f * n * (b + 1), fac + (size_t)f * n * (b + 1), x, bsm);
-}
-
 // S = Q_gg - Q_vg^T W, then S^-1 in place (Gauss-Jordan, partial pivoting); one warp per f
 __global__ void k_schur(int n, int ng, int nmat, const double* __restrict__ border_vg,
                         const double* __restrict__ border_gg, const cplx* __restrict__ zs,
@@ -436,139 +383,407 @@ __global__ void k_schur(int n, int ng, int nmat, const double* __restrict__ bord
   }
 }
 
-// z = Q(f_s)^-1 v for every system; one warp per system; C = float2 (mixed
-// precision triangular solves from an FP64-computed factor) or double2.
-template <class C>
-__global__ void k_band_apply(int nloop, int n, int b, int ng, int nport, int nmat, const int32_t* __restrict__ perm,
-                             const double* __restrict__ border_vg, const cplx* __restrict__ zs,
-                             const double* __restrict__ wp_f, const C* __restrict__ fac, const C* __restrict__ facT,
-                             const cplx* __restrict__ Wb, const cplx* __restrict__ Sinv, const cplx* __restrict__ v,
-                             cplx* __restrict__ z, C* __restrict__ scratch, const int* __restrict__ active) {
-  extern __shared__ __align__(16) unsigned char bsm_raw[];
-  C* bsm = reinterpret_cast<C*>(bsm_raw);
-  __shared__ cplx tg[kMaxBorder], zg[kMaxBorder];
-  const int s = blockIdx.x;
-  if (active && !active[s]) return;
-  const int f = s / nport;
-  const int lane = threadIdx.x & 31;
-  const cplx* vs = v + (size_t)s * nloop;
-  cplx* zs_out = z + (size_t)s * nloop;
-  C* x = scratch + (size_t)s * (size_t)((n + 2) & ~1);
-  for (int i = lane; i < n; i += 32) {
-    cplx vi = vs[perm[i]];
-    if (sizeof(C) == 8) {
-      reinterpret_cast<float2*>(x)[i] = make_float2((float)vi.x, (float)vi.y);
-    } else {
-      reinterpret_cast<cplx*>(x)[i] = vi;
-    }
+// ---- partitioned (SPIKE) factor --------------------------------------------------------------
+
+// LDL^T of the diagonal block j of Q_vv(f) (rows [s0, e0)), couplings to other
+// blocks dropped; one warp per (f, j), the active (b+1) x (b+1) window in
+// shared memory as a ring of rows.  fac[f][i][k]: k < b strictly lower L
+// (column i - b + k), k = b the diagonal D.
+__global__ void k_band_factor_blk(int n, int b, int P, int m, int nmat, const double* __restrict__ band_val,
+                                  const cplx* __restrict__ zs, const double* __restrict__ wp_f,
+                                  cplx* __restrict__ fac) {
+  extern __shared__ cplx win[];   // [(b+1)][(b+1)] ring, then orig[b], then the pair table
+  const int f = blockIdx.x / P, j = blockIdx.x % P;
+  const int s0 = j * m, e0 = (j == P - 1) ? n : min(n, s0 + m);
+  const int mm = e0 - s0;
+  const int lane = threadIdx.x;
+  const int nb1 = b + 1;
+  const size_t stride = (size_t)n * nb1;
+  const cplx* z = zs + (size_t)f * nmat;
+  const double wp = wp_f[f];
+  cplx* out = fac + (size_t)f * stride + (size_t)s0 * nb1;
+  cplx* orig = win + nb1 * nb1;
+  short2* pairs = reinterpret_cast<short2*>(orig + b);
+  const int npair = b * (b + 1) / 2;
+  for (int q = lane; q < npair; q += 32) {
+    int ti = 0;
+    while ((ti + 1) * (ti + 2) / 2 <= q) ++ti;
+    pairs[q] = make_short2((short)ti, (short)(q - ti * (ti + 1) / 2));
   }
-  __syncwarp();
-  band_solve_warp<C>(n, b, band_rs<C>(b), facT + (size_t)f * n * band_rs<C>(b), fac + (size_t)f * n * band_rs<C>(b),
-                     x, bsm);
-  auto xval = [&](int i) -> cplx {
-    if (sizeof(C) == 8) {
-      float2 t = reinterpret_cast<const float2*>(x)[i];
-      return make_double2(t.x, t.y);
+  auto load_row = [&](int r, int slot) {
+    for (int e = lane; e < nb1; e += 32) {
+      cplx v = make_double2(0.0, 0.0);
+      if (r < mm && e >= b - r) v = pencil(band_val + (size_t)(s0 + r) * nb1 + e, stride, nmat, z, wp);
+      win[slot * nb1 + e] = v;
     }
-    return reinterpret_cast<const cplx*>(x)[i];
   };
-  if (ng > 0) {
-    const cplx* zf = zs + (size_t)f * nmat;
-    const double wp = wp_f[f];
-    const size_t vstride = (size_t)n * ng;
-    for (int g = 0; g < ng; ++g) {
-      cplx acc = make_double2(0, 0);
-      for (int i = lane; i < n; i += 32) acc = cadd(acc, cm(pencil(border_vg + (size_t)i * ng + g, vstride, nmat, zf, wp), xval(i)));
-      acc = warp_sum(acc);
-      if (lane == 0) tg[g] = csub(vs[n + g], acc);
+  for (int r = 0; r < nb1; ++r) load_row(r, r);
+  __syncwarp();
+  for (int k = 0; k < mm; ++k) {
+    const int sk = k % nb1;
+    const cplx inv = cdiv(make_double2(1.0, 0.0), win[sk * nb1 + b]);
+    for (int t = lane; t < b; t += 32) {
+      const int i = k + 1 + t;
+      cplx o = make_double2(0.0, 0.0);
+      if (i < mm) {
+        cplx* w = win + (i % nb1) * nb1 + (b - 1 - t);
+        o = *w;
+        *w = cm(o, inv);
+      }
+      orig[t] = o;
     }
     __syncwarp();
-    if (lane < ng) {
-      cplx acc = make_double2(0, 0);
-      for (int g2 = 0; g2 < ng; ++g2) acc = cadd(acc, cm(Sinv[((size_t)f * ng + lane) * ng + g2], tg[g2]));
-      zg[lane] = acc;
+    for (int q = lane; q < npair; q += 32) {
+      const short2 pq = pairs[q];
+      const int i = k + 1 + pq.x;
+      if (i < mm) {
+        cplx* row = win + (i % nb1) * nb1;
+        row[b - (pq.x - pq.y)] = csub(row[b - (pq.x - pq.y)], cm(row[b - 1 - pq.x], orig[pq.y]));
+      }
     }
     __syncwarp();
-    for (int i = lane; i < n; i += 32) {
-      cplx acc = xval(i);
-      for (int g = 0; g < ng; ++g) acc = csub(acc, cm(Wb[((size_t)f * ng + g) * n + i], zg[g]));
-      zs_out[perm[i]] = acc;
-    }
+    for (int e = lane; e < nb1; e += 32) out[(size_t)k * nb1 + e] = win[sk * nb1 + e];
     __syncwarp();
-    if (lane < ng) zs_out[n + lane] = zg[lane];
-  } else {
-    for (int i = lane; i < n; i += 32) zs_out[perm[i]] = xval(i);
+    load_row(k + nb1, sk);
+    __syncwarp();
   }
 }
 
-// as k_band_apply, two systems (consecutive, same frequency) per warp
+// Spike columns: V_j[:, c] = A_j^-1 [0; B_j[:, c]] (col = c < b, j < P-1) and
+// W_j[:, c] = A_j^-1 [C_j[:, c]; 0] (col = b + c, j > 0), stored by column,
+// Vsp[f][c][i] for the rows i of block j.  B_j[r][c] = Q[e0-b+r][e0+c]
+// (r >= c) and C_j[r][c] = Q[s0+r][s0-b+c] (c >= r) read from the band rows.
+// One warp per (f, j, col).
+__global__ void k_spike_cols(int n, int b, int P, int m, int nmat, const double* __restrict__ band_val,
+                             const cplx* __restrict__ zs, const double* __restrict__ wp_f,
+                             const cplx* __restrict__ fac, const cplx* __restrict__ facT, cplx* __restrict__ Vsp,
+                             cplx* __restrict__ Wsp) {
+  extern __shared__ __align__(16) unsigned char ssm_raw[];
+  cplx* ssm = reinterpret_cast<cplx*>(ssm_raw);
+  const int col = blockIdx.x % (2 * b);
+  const int j = (blockIdx.x / (2 * b)) % P;
+  const int f = blockIdx.x / (2 * b * P);
+  const int s0 = j * m, e0 = (j == P - 1) ? n : min(n, s0 + m);
+  const int mm = e0 - s0;
+  const int lane = threadIdx.x;
+  const int nb1 = b + 1;
+  const size_t stride = (size_t)n * nb1;
+  const cplx* z = zs + (size_t)f * nmat;
+  const double wp = wp_f[f];
+  const bool isV = col < b;
+  const int c = isV ? col : col - b;
+  if (isV ? (j == P - 1) : (j == 0)) return;
+  cplx* x = (isV ? Vsp : Wsp) + ((size_t)f * b + c) * n + s0;
+  for (int i = lane; i < mm; i += 32) {
+    cplx v = make_double2(0.0, 0.0);
+    if (isV) {
+      const int r = i - (mm - b);
+      if (r >= c && r < b) v = pencil(band_val + (size_t)(e0 + c) * nb1 + (r - c), stride, nmat, z, wp);
+    } else {
+      const int r = i;
+      if (r <= c) v = pencil(band_val + (size_t)(s0 + r) * nb1 + (c - r), stride, nmat, z, wp);
+    }
+    x[i] = v;
+  }
+  __syncwarp();
+  const size_t fo = (size_t)f * stride + (size_t)s0 * nb1;
+  band_solve_warp<cplx>(mm, b, nb1, facT + fo, fac + fo, x, ssm);
+}
+
+// In-place inverse of the n x n complex matrix A (row-major, leading dimension
+// lda, shared memory) by Gauss-Jordan elimination with partial pivoting; all
+// threads of the CTA.  piv: n ints of shared memory.
+__device__ void gj_inverse(cplx* A, int n, int lda, int* piv, cplx* colk) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ cplx pinv_s;
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      int p = k;
+      double best = cabs2(A[k * lda + k]);
+      for (int i = k + 1; i < n; ++i) {
+        double v = cabs2(A[i * lda + k]);
+        if (v > best) {
+          best = v;
+          p = i;
+        }
+      }
+      piv[k] = p;
+    }
+    __syncthreads();
+    const int p = piv[k];
+    if (p != k)
+      for (int cc = tid; cc < n; cc += nt) {
+        cplx t = A[k * lda + cc];
+        A[k * lda + cc] = A[p * lda + cc];
+        A[p * lda + cc] = t;
+      }
+    __syncthreads();
+    if (tid == 0) pinv_s = cdiv(make_double2(1.0, 0.0), A[k * lda + k]);
+    for (int i = tid; i < n; i += nt) colk[i] = A[i * lda + k];
+    __syncthreads();
+    const cplx pinv = pinv_s;
+    for (int cc = tid; cc < n; cc += nt) A[k * lda + cc] = cm(cc == k ? make_double2(1.0, 0.0) : A[k * lda + cc], pinv);
+    __syncthreads();
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e / n, cc = e % n;
+      if (i == k) continue;
+      const cplx a = cc == k ? make_double2(0.0, 0.0) : A[i * lda + cc];
+      A[i * lda + cc] = csub(a, cm(A[k * lda + cc], colk[i]));
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = tid; i < n; i += nt) {
+        cplx t = A[i * lda + k];
+        A[i * lda + k] = A[i * lda + p];
+        A[i * lda + p] = t;
+      }
+    __syncthreads();
+  }
+}
+
+// Block LU of the reduced system: Einv[f][j] = E^_j^-1 (2b x 2b, column-major)
+// for j < P-1; one CTA per frequency, sequential over j.
+__global__ void k_spike_reduce(int n, int b, int P, int m, const cplx* __restrict__ Vsp, const cplx* __restrict__ Wsp,
+                               cplx* __restrict__ Einv) {
+  extern __shared__ cplx rsm[];
+  const int B2 = 2 * b;
+  cplx* E = rsm;                  // [B2][B2]
+  cplx* X01 = E + B2 * B2;        // [b][b] top-right block of the previous inverse
+  cplx* T = X01 + b * b;          // [b][b]
+  cplx* colk = T + b * b;         // [B2]
+  int* piv = reinterpret_cast<int*>(colk + B2);
+  const int f = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const cplx* V = Vsp + (size_t)f * b * n;
+  const cplx* W = Wsp + (size_t)f * b * n;
+  for (int j = 0; j + 1 < P; ++j) {
+    const int sj = j * m, e = (j + 1) * m;
+    for (int q = tid; q < B2 * B2; q += nt) {
+      const int r = q / B2, cc = q % B2;
+      cplx v = make_double2(r == cc ? 1.0 : 0.0, 0.0);
+      if (r < b && cc >= b) v = V[(size_t)(cc - b) * n + e - b + r];
+      if (r >= b && cc < b) v = W[(size_t)cc * n + e + (r - b)];
+      E[q] = v;
+    }
+    if (j > 0) {
+      // T = X01 V_j^top, then E_tr -= W_j^bot T
+      for (int q = tid; q < b * b; q += nt) {
+        const int r = q / b, cc = q % b;
+        cplx acc = make_double2(0.0, 0.0);
+        for (int k = 0; k < b; ++k) acc = cadd(acc, cm(X01[r * b + k], V[(size_t)cc * n + sj + k]));
+        T[q] = acc;
+      }
+      __syncthreads();
+      for (int q = tid; q < b * b; q += nt) {
+        const int r = q / b, cc = q % b;
+        cplx acc = make_double2(0.0, 0.0);
+        for (int k = 0; k < b; ++k) acc = cadd(acc, cm(W[(size_t)k * n + e - b + r], T[k * b + cc]));
+        E[r * B2 + b + cc] = csub(E[r * B2 + b + cc], acc);
+      }
+    }
+    __syncthreads();
+    gj_inverse(E, B2, B2, piv, colk);
+    cplx* out = Einv + ((size_t)f * (P - 1) + j) * B2 * B2;
+    for (int q = tid; q < B2 * B2; q += nt) {
+      const int r = q / B2, cc = q % B2;
+      out[(size_t)cc * B2 + r] = E[q];
+    }
+    for (int q = tid; q < b * b; q += nt) X01[q] = E[(q / b) * B2 + b + q % b];
+    __syncthreads();
+  }
+}
+
+__global__ void k_to_f32(size_t n, const double* __restrict__ a, float* __restrict__ b) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// ---- partitioned (SPIKE) apply ---------------------------------------------------------------
 template <class C>
-__global__ void k_band_apply_pair(int nloop, int n, int b, int ng, int nport, int nmat, const int32_t* __restrict__ perm,
-                                  const double* __restrict__ border_vg, const cplx* __restrict__ zs,
-                                  const double* __restrict__ wp_f, const C* __restrict__ fac,
-                                  const C* __restrict__ facT, const cplx* __restrict__ Wb,
-                                  const cplx* __restrict__ Sinv, const cplx* __restrict__ v, cplx* __restrict__ z,
-                                  C* __restrict__ scratch) {
-  extern __shared__ __align__(16) unsigned char bsm_raw[];
-  C* bsm = reinterpret_cast<C*>(bsm_raw);
-  __shared__ cplx tg[2][kMaxBorder], zg[2][kMaxBorder];
-  const int s0 = 2 * blockIdx.x;
-  const int f = s0 / nport;
-  const int lane = threadIdx.x & 31;
-  const size_t xs = (size_t)((n + 2) & ~1);
-  C* x0 = scratch + (size_t)s0 * xs;
-  C* x1 = x0 + xs;
-  for (int q = 0; q < 2; ++q) {
-    const cplx* vs = v + (size_t)(s0 + q) * nloop;
-    C* x = q ? x1 : x0;
-    for (int i = lane; i < n; i += 32) {
-      cplx vi = vs[perm[i]];
-      if (sizeof(C) == 8) reinterpret_cast<float2*>(x)[i] = make_float2((float)vi.x, (float)vi.y);
-      else reinterpret_cast<cplx*>(x)[i] = vi;
+__device__ __forceinline__ C to_c(cplx v);
+template <>
+__device__ __forceinline__ float2 to_c<float2>(cplx v) { return make_float2((float)v.x, (float)v.y); }
+template <>
+__device__ __forceinline__ double2 to_c<double2>(cplx v) { return v; }
+__device__ __forceinline__ cplx to_d(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ cplx to_d(double2 v) { return v; }
+
+// Stage 1: y_j = A_j^-1 f_j for block j = blockIdx.y.  mode 0: the right-hand
+// side is v[s][perm[i]] of system s (two systems sharing a frequency per warp
+// when `pair`), stored in x[s] (stride xs); mode 1: it is column g of Q_vg(f),
+// s = f * ng + g, solved in place in x = Wb.
+template <class C>
+__global__ void k_spike_y(int n, int b, int P, int m, int nper, int pair, int mode, int nloop, int ng, int nmat,
+                          const int32_t* __restrict__ perm, const double* __restrict__ border_vg,
+                          const cplx* __restrict__ zs, const double* __restrict__ wp_f, const C* __restrict__ fac,
+                          const C* __restrict__ facT, const cplx* __restrict__ v, C* __restrict__ xb, size_t xs,
+                          const int* __restrict__ active) {
+  extern __shared__ __align__(16) unsigned char ysm_raw[];
+  C* ysm = reinterpret_cast<C*>(ysm_raw);
+  const int lane = threadIdx.x;
+  const int s0 = pair ? 2 * blockIdx.x : blockIdx.x;
+  if (active && !active[s0] && (!pair || !active[s0 + 1])) return;
+  const int f = s0 / nper, j = blockIdx.y;
+  const int j0 = j * m, e0 = (j == P - 1) ? n : min(n, j0 + m);
+  const int mm = e0 - j0;
+  for (int q = 0; q < (pair ? 2 : 1); ++q) {
+    C* x = xb + (size_t)(s0 + q) * xs + j0;
+    if (mode == 0) {
+      const cplx* vs = v + (size_t)(s0 + q) * nloop;
+      for (int i = lane; i < mm; i += 32) x[i] = to_c<C>(vs[perm[j0 + i]]);
+    } else {
+      const int g = (s0 + q) % ng;
+      const size_t vstride = (size_t)n * ng;
+      for (int i = lane; i < mm; i += 32)
+        x[i] = to_c<C>(pencil(border_vg + (size_t)(j0 + i) * ng + g, vstride, nmat, zs + (size_t)f * nmat, wp_f[f]));
     }
   }
   __syncwarp();
   const int rs = band_rs<C>(b);
-  band_solve_pair<C>(n, b, rs, facT + (size_t)f * n * rs, fac + (size_t)f * n * rs, x0, x1, bsm);
-  for (int q = 0; q < 2; ++q) {
-    const C* x = q ? x1 : x0;
-    const cplx* vs = v + (size_t)(s0 + q) * nloop;
-    cplx* zo = z + (size_t)(s0 + q) * nloop;
-    auto xval = [&](int i) -> cplx {
-      if (sizeof(C) == 8) {
-        float2 t = reinterpret_cast<const float2*>(x)[i];
-        return make_double2(t.x, t.y);
+  const size_t fo = ((size_t)f * n + j0) * rs;
+  C* x0 = xb + (size_t)s0 * xs + j0;
+  if (pair)
+    band_solve_pair<C>(mm, b, rs, facT + fo, fac + fo, x0, x0 + xs, ysm);
+  else
+    band_solve_warp<C>(mm, b, rs, facT + fo, fac + fo, x0, ysm);
+}
+
+// Stage 2: the reduced block-tridiagonal system for z_j = (u_j, t_{j+1}),
+// forward then backward; one warp per system, h[s][j][2b] holds h_j and then z_j.
+template <class C>
+__global__ void k_spike_z(int n, int b, int P, int m, int nper, const C* __restrict__ Vsp, const C* __restrict__ Wsp,
+                          const C* __restrict__ Einv, const C* __restrict__ xb, size_t xs, C* __restrict__ hb,
+                          const int* __restrict__ active) {
+  __shared__ C g[128], hp[64], tt[64];
+  const int s = blockIdx.x;
+  if (P < 2 || (active && !active[s])) return;
+  const int f = s / nper, lane = threadIdx.x, B2 = 2 * b;
+  const C* x = xb + (size_t)s * xs;
+  const C* V = Vsp + (size_t)f * b * n;
+  const C* W = Wsp + (size_t)f * b * n;
+  const C* E = Einv + (size_t)f * (P - 1) * B2 * B2;
+  C* h = hb + (size_t)s * (P - 1) * B2;
+  for (int j = 0; j + 1 < P; ++j) {
+    const int e = (j + 1) * m;
+    for (int r = lane; r < B2; r += 32) g[r] = x[e - b + r];
+    __syncwarp();
+    if (j > 0)
+      for (int r = lane; r < b; r += 32) {
+        C acc = czero<C>();
+        for (int c = 0; c < b; ++c) acc = cfma(W[(size_t)c * n + e - b + r], hp[c], acc);
+        g[r] = csubT(g[r], acc);
       }
-      return reinterpret_cast<const cplx*>(x)[i];
-    };
-    if (ng > 0) {
-      const cplx* zf = zs + (size_t)f * nmat;
-      const double wp = wp_f[f];
-      const size_t vstride = (size_t)n * ng;
-      for (int g = 0; g < ng; ++g) {
-        cplx acc = make_double2(0, 0);
-        for (int i = lane; i < n; i += 32) acc = cadd(acc, cm(pencil(border_vg + (size_t)i * ng + g, vstride, nmat, zf, wp), xval(i)));
-        acc = warp_sum(acc);
-        if (lane == 0) tg[q][g] = csub(vs[n + g], acc);
-      }
-      __syncwarp();
-      if (lane < ng) {
-        cplx acc = make_double2(0, 0);
-        for (int g2 = 0; g2 < ng; ++g2) acc = cadd(acc, cm(Sinv[((size_t)f * ng + lane) * ng + g2], tg[q][g2]));
-        zg[q][lane] = acc;
-      }
-      __syncwarp();
-      for (int i = lane; i < n; i += 32) {
-        cplx acc = xval(i);
-        for (int g = 0; g < ng; ++g) acc = csub(acc, cm(Wb[((size_t)f * ng + g) * n + i], zg[q][g]));
-        zo[perm[i]] = acc;
-      }
-      __syncwarp();
-      if (lane < ng) zo[n + lane] = zg[q][lane];
-    } else {
-      for (int i = lane; i < n; i += 32) zo[perm[i]] = xval(i);
+    __syncwarp();
+    const C* Ej = E + (size_t)j * B2 * B2;
+    for (int r = lane; r < B2; r += 32) {
+      C acc = czero<C>();
+      for (int c = 0; c < B2; ++c) acc = cfma(Ej[(size_t)c * B2 + r], g[c], acc);
+      h[(size_t)j * B2 + r] = acc;
+      if (r < b) hp[r] = acc;
     }
     __syncwarp();
+  }
+  for (int j = P - 3; j >= 0; --j) {
+    const int sn = (j + 1) * m;   // first row of block j+1
+    for (int r = lane; r < b; r += 32) g[r] = h[(size_t)(j + 1) * B2 + b + r];
+    __syncwarp();
+    for (int r = lane; r < b; r += 32) {
+      C acc = czero<C>();
+      for (int c = 0; c < b; ++c) acc = cfma(V[(size_t)c * n + sn + r], g[c], acc);
+      tt[r] = acc;
+    }
+    __syncwarp();
+    const C* Ej = E + (size_t)j * B2 * B2;
+    for (int r = lane; r < B2; r += 32) {
+      C acc = czero<C>();
+      for (int c = 0; c < b; ++c) acc = cfma(Ej[(size_t)(b + c) * B2 + r], tt[c], acc);
+      h[(size_t)j * B2 + r] = csubT(h[(size_t)j * B2 + r], acc);
+    }
+    __syncwarp();
+  }
+}
+
+// Stage 3: x_j = y_j - V_j t_{j+1} - W_j u_{j-1} in place; mode 0 then applies
+// the border (t_g = v_g - Q_vg^T x, z_g = S^-1 t_g, x -= W_b z_g) and scatters
+// to loop order into z[s]; one CTA per system.
+template <class C>
+__global__ void __launch_bounds__(256) k_spike_x(int n, int b, int P, int m, int nper, int mode, int nloop, int ng,
+                                                 int nmat, const int32_t* __restrict__ perm,
+                                                 const double* __restrict__ border_vg, const cplx* __restrict__ zs,
+                                                 const double* __restrict__ wp_f, const C* __restrict__ Vsp,
+                                                 const C* __restrict__ Wsp, const C* __restrict__ hb, C* __restrict__ xb,
+                                                 size_t xs, const cplx* __restrict__ Wb, const cplx* __restrict__ Sinv,
+                                                 const cplx* __restrict__ v, cplx* __restrict__ z,
+                                                 const int* __restrict__ active) {
+  extern __shared__ __align__(16) unsigned char xsm_raw[];
+  C* hs = reinterpret_cast<C*>(xsm_raw);   // [(P-1)][2b]
+  __shared__ cplx red[8][kMaxBorder];
+  __shared__ cplx zg[kMaxBorder];
+  const int s = blockIdx.x;
+  if (active && !active[s]) return;
+  const int f = s / nper, tid = threadIdx.x, B2 = 2 * b;
+  C* x = xb + (size_t)s * xs;
+  if (P > 1) {
+    const C* V = Vsp + (size_t)f * b * n;
+    const C* W = Wsp + (size_t)f * b * n;
+    for (int e = tid; e < (P - 1) * B2; e += blockDim.x) hs[e] = hb[(size_t)s * (P - 1) * B2 + e];
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) {
+      const int j = min(i / m, P - 1);
+      C y = x[i];
+      if (j < P - 1) {
+        const C* t = hs + j * B2 + b;
+        for (int c = 0; c < b; ++c) y = csubT(y, cmul(V[(size_t)c * n + i], t[c]));
+      }
+      if (j > 0) {
+        const C* u = hs + (j - 1) * B2;
+        for (int c = 0; c < b; ++c) y = csubT(y, cmul(W[(size_t)c * n + i], u[c]));
+      }
+      x[i] = y;
+    }
+  }
+  if (mode == 1) return;
+  const cplx* vs = v + (size_t)s * nloop;
+  cplx* zo = z + (size_t)s * nloop;
+  if (ng > 0) {
+    const cplx* zf = zs + (size_t)f * nmat;
+    const double wp = wp_f[f];
+    const size_t vstride = (size_t)n * ng;
+    cplx acc[kMaxBorder];
+    for (int g = 0; g < ng; ++g) acc[g] = make_double2(0.0, 0.0);
+    for (int i = tid; i < n; i += blockDim.x) {
+      const cplx xi = to_d(x[i]);
+      for (int g = 0; g < ng; ++g)
+        acc[g] = cadd(acc[g], cm(pencil(border_vg + (size_t)i * ng + g, vstride, nmat, zf, wp), xi));
+    }
+    const int w = tid >> 5, lane = tid & 31;
+    for (int g = 0; g < ng; ++g) {
+      cplx t = warp_sum(acc[g]);
+      if (lane == 0) red[w][g] = t;
+    }
+    __syncthreads();
+    if (tid < ng) {
+      cplx t = make_double2(0.0, 0.0);
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = cadd(t, red[q][tid]);
+      red[0][tid] = csub(vs[n + tid], t);   // t_g
+    }
+    __syncthreads();
+    if (tid < ng) {
+      cplx t = make_double2(0.0, 0.0);
+      for (int g2 = 0; g2 < ng; ++g2) t = cadd(t, cm(Sinv[((size_t)f * ng + tid) * ng + g2], red[0][g2]));
+      zg[tid] = t;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) {
+      cplx a = to_d(x[i]);
+      for (int g = 0; g < ng; ++g) a = csub(a, cm(Wb[((size_t)f * ng + g) * n + i], zg[g]));
+      zo[perm[i]] = a;
+    }
+    if (tid < ng) zo[n + tid] = zg[tid];
+  } else {
+    for (int i = tid; i < n; i += blockDim.x) zo[perm[i]] = to_d(x[i]);
   }
 }
 
@@ -585,75 +800,145 @@ void band_prepare(xrl_ctx* c) {
   c->d.border_gg.upload(c->alloc, T.border_gg);
 }
 
-// factor Q(f) for nf frequencies (zs [nf][nmat], wp [nf]) into fac, W, Sinv
-void band_factor(xrl_ctx* c, int nf, const cplx* zs, const double* wp, cplx* fac, cplx* facT, float2* fac32,
-                 float2* facT32, cplx* Wb, cplx* Sinv, cudaStream_t s) {
+// Blocks of m rows (even, >= 4b; the last block takes the remainder and has
+// at least 2b rows), at most 64 of them and at most 1024 / b (the stage-3
+// shared copy of the interface values); one block (the plain band solve) for
+// short bands or b > 40 (the reduced-system inverse lives in shared memory).
+static void band_blocks(int n, int b, int* P, int* m) {
+  int pm = std::max(1, std::min(64, 1024 / std::max(1, b)));
+  if (n < 8 * b || pm < 2 || b > 40) {
+    *P = 1;
+    *m = n;
+    return;
+  }
+  int mm = std::max(4 * b, (n + pm - 1) / pm);
+  mm = (mm + 1) & ~1;
+  int p = (n + mm - 1) / mm;
+  if (n - (p - 1) * mm < 2 * b) --p;
+  *P = std::max(1, p);
+  *m = *P == 1 ? n : mm;
+}
+
+void band_alloc(xrl_ctx* c, BandWork& bw, int nf, int nsys, bool mixed) {
   const Topo& T = c->topo;
   const int n = T.n_band, b = T.band, ng = T.n_border;
-  size_t smem = sizeof(cplx) * (b + 1) * (b + 1);
-  if (smem > 48 * 1024) XRL_CUDA(cudaFuncSetAttribute(k_band_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  band_blocks(n, b, &bw.P, &bw.m);
+  bw.nf = nf;
+  bw.mixed = mixed;
+  const int P1 = std::max(1, bw.P - 1);
+  bw.fac.alloc(c->alloc, (size_t)nf * n * (b + 1));
+  bw.facT.alloc(c->alloc, (size_t)nf * n * (b + 1));
+  bw.Wb.alloc(c->alloc, (size_t)nf * std::max(1, ng) * n);
+  bw.Sinv.alloc(c->alloc, (size_t)nf * std::max(1, ng * ng));
+  bw.Vsp.alloc(c->alloc, (size_t)nf * b * n);
+  bw.Wsp.alloc(c->alloc, (size_t)nf * b * n);
+  bw.Einv.alloc(c->alloc, (size_t)nf * P1 * 4 * b * b);
+  bw.hbB.alloc(c->alloc, (size_t)nf * std::max(1, ng) * P1 * 2 * b);
+  const size_t xs = (size_t)((n + 2) & ~1);
+  if (mixed) {
+    const int rs = band_rs<float2>(b);
+    bw.fac32.alloc(c->alloc, (size_t)nf * n * rs);
+    bw.facT32.alloc(c->alloc, (size_t)nf * n * rs);
+    bw.Vsp32.alloc(c->alloc, (size_t)nf * b * n);
+    bw.Wsp32.alloc(c->alloc, (size_t)nf * b * n);
+    bw.Einv32.alloc(c->alloc, (size_t)nf * P1 * 4 * b * b);
+    bw.scr32.alloc(c->alloc, (size_t)nsys * xs);
+    bw.hb32.alloc(c->alloc, (size_t)nsys * P1 * 2 * b);
+  } else {
+    bw.scr.alloc(c->alloc, (size_t)nsys * xs);
+    bw.hb.alloc(c->alloc, (size_t)nsys * P1 * 2 * b);
+  }
+}
+
+template <class C>
+static void spike_stages(xrl_ctx* c, const BandWork& bw, int nsys, int nper, int mode, const cplx* zs,
+                         const double* wp, const C* fac, const C* facT, const C* Vsp, const C* Wsp, const C* Einv,
+                         C* xb, size_t xs, C* hb, const cplx* v, cplx* z, const int* active, cudaStream_t s) {
+  const Topo& T = c->topo;
+  const int n = T.n_band, b = T.band, ng = T.n_border, P = bw.P, m = bw.m;
+  const bool pair = mode == 0 && b <= 15 && nper % 2 == 0 && nsys % 2 == 0;
+  const int ch = band_chunk(b);
+  const size_t ys = pair ? sizeof(C) * ((size_t)2 * ch * band_rs<C>(b) + 4 * (size_t)ch) : band_smem_bytes<C>(b);
+  if (ys > 48 * 1024)
+    XRL_CUDA(cudaFuncSetAttribute(k_spike_y<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys));
+  k_spike_y<C><<<dim3(pair ? nsys / 2 : nsys, P), 32, ys, s>>>(n, b, P, m, nper, pair ? 1 : 0, mode, T.n_loops, ng,
+                                                              T.n_mat, c->d.band_perm.p, c->d.border_vg.p, zs, wp, fac,
+                                                              facT, v, xb, xs, active);
+  if (P > 1) k_spike_z<C><<<nsys, 32, 0, s>>>(n, b, P, m, nper, Vsp, Wsp, Einv, xb, xs, hb, active);
+  const size_t hs = sizeof(C) * (size_t)std::max(1, P - 1) * 2 * b;
+  if (mode == 0 || P > 1)
+    k_spike_x<C><<<nsys, 256, hs, s>>>(n, b, P, m, nper, mode, T.n_loops, ng, T.n_mat, c->d.band_perm.p,
+                                       c->d.border_vg.p, zs, wp, Vsp, Wsp, hb, xb, xs, bw.Wb.p, bw.Sinv.p, v, z,
+                                       active);
+  XRL_CUDA(cudaGetLastError());
+}
+
+// factor Q(f) for bw.nf frequencies (zs [nf][nmat], wp [nf])
+void band_factor(xrl_ctx* c, BandWork& bw, const cplx* zs, const double* wp, cudaStream_t s) {
+  const Topo& T = c->topo;
+  const int n = T.n_band, b = T.band, ng = T.n_border, nf = bw.nf, P = bw.P, m = bw.m;
+  const int nb1 = b + 1;
   cudaEvent_t ev = prof_begin(c, s);
-  k_band_factor<<<nf, 256, smem, s>>>(n, b, T.n_mat, c->d.band_val.p, zs, wp, fac);
+  size_t smem = sizeof(cplx) * ((size_t)nb1 * nb1 + b) + sizeof(short2) * (size_t)b * nb1 / 2 + 16;
+  if (smem > 48 * 1024)
+    XRL_CUDA(cudaFuncSetAttribute(k_band_factor_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_band_factor_blk<<<nf * P, 32, smem, s>>>(n, b, P, m, T.n_mat, c->d.band_val.p, zs, wp, bw.fac.p);
   int launches = 1;
-  const size_t bsd = band_smem_bytes<cplx>(b);
-  if (bsd > 48 * 1024)
-    XRL_CUDA(cudaFuncSetAttribute(k_border_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsd));
-  // 1/D on the diagonal (and the FP32 copy for mixed-precision solves)
   {
-    size_t tot = (size_t)nf * n * (b + 1);
-    k_band_finish<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nf, n, b, fac, facT, fac32, facT32);
+    size_t tot = (size_t)nf * n * nb1;
+    k_band_finish<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nf, n, b, bw.fac.p, bw.facT.p, bw.fac32.p,
+                                                                bw.facT32.p);
     ++launches;
   }
-  if (ng > 0) {
-    k_border_solve<<<nf * ng, 32, bsd, s>>>(n, b, ng, T.n_mat, c->d.border_vg.p, zs, wp, fac, facT, Wb);
-    k_schur<<<nf, 32, 0, s>>>(n, ng, T.n_mat, c->d.border_vg.p, c->d.border_gg.p, zs, wp, Wb, Sinv);
+  if (P > 1) {
+    const size_t bsd = band_smem_bytes<cplx>(b);
+    if (bsd > 48 * 1024)
+      XRL_CUDA(cudaFuncSetAttribute(k_spike_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsd));
+    k_spike_cols<<<nf * P * 2 * b, 32, bsd, s>>>(n, b, P, m, T.n_mat, c->d.band_val.p, zs, wp, bw.fac.p, bw.facT.p,
+                                                 bw.Vsp.p, bw.Wsp.p);
+    const size_t rsm = sizeof(cplx) * ((size_t)4 * b * b + 2 * (size_t)b * b + 2 * b) + sizeof(int) * 2 * b;
+    if (rsm > 48 * 1024)
+      XRL_CUDA(cudaFuncSetAttribute(k_spike_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+    k_spike_reduce<<<nf, 256, rsm, s>>>(n, b, P, m, bw.Vsp.p, bw.Wsp.p, bw.Einv.p);
     launches += 2;
+    if (bw.mixed) {
+      auto cast = [&](const DBuf<cplx>& a, DBuf<float2>& o) {
+        size_t e = 2 * a.n;
+        k_to_f32<<<(unsigned)((e + 255) / 256), 256, 0, s>>>(e, reinterpret_cast<const double*>(a.p),
+                                                                   reinterpret_cast<float*>(o.p));
+      };
+      cast(bw.Vsp, bw.Vsp32);
+      cast(bw.Wsp, bw.Wsp32);
+      cast(bw.Einv, bw.Einv32);
+      launches += 3;
+    }
+  }
+  if (ng > 0) {
+    // W_b = Q_vv^-1 Q_vg in FP64, in place in Wb (one "system" per (f, g))
+    spike_stages<cplx>(c, bw, nf * ng, ng, 1, zs, wp, bw.fac.p, bw.facT.p, bw.Vsp.p, bw.Wsp.p, bw.Einv.p, bw.Wb.p,
+                       (size_t)n, bw.hbB.p, nullptr, nullptr, nullptr, s);
+    k_schur<<<nf, 32, 0, s>>>(n, ng, T.n_mat, c->d.border_vg.p, c->d.border_gg.p, zs, wp, bw.Wb.p, bw.Sinv.p);
+    launches += 4;
   }
   prof_end(c, s, ev, PH_PREC, launches, 8.0 * nf * (double)n * b * b / 2.0, 16.0 * nf * (double)n * (b + 1) * 2.0);
   XRL_CUDA(cudaGetLastError());
 }
 
-void band_apply(xrl_ctx* c, int nsys, int nport, const cplx* zs, const double* wp, const cplx* fac,
-                const cplx* facT, const float2* fac32, const float2* facT32, const cplx* Wb, const cplx* Sinv,
-                const cplx* v, cplx* z, void* scratch, const int* active, cudaStream_t s) {
+// z = Q(f_s)^-1 v for nsys systems, f_s = s / nport (loop order in and out)
+void band_apply(xrl_ctx* c, BandWork& bw, int nsys, int nport, const cplx* zs, const double* wp, const cplx* v,
+                cplx* z, const int* active, cudaStream_t s) {
   const Topo& T = c->topo;
   cudaEvent_t ev = prof_begin(c, s);
-  // systems 2q, 2q+1 share a frequency when nport is even; converged systems are
-  // recomputed harmlessly on this path (their results are not used)
-  const bool pair = T.band <= 15 && nport % 2 == 0 && nsys % 2 == 0;
-  if (pair) {
-    if (fac32) {
-      const size_t bs = sizeof(float2) * ((size_t)2 * band_chunk(T.band) * band_rs<float2>(T.band) +
-                                          4 * (size_t)band_chunk(T.band));
-      k_band_apply_pair<float2><<<nsys / 2, 32, bs, s>>>(T.n_loops, T.n_band, T.band, T.n_border, nport, T.n_mat,
-                                                         c->d.band_perm.p, c->d.border_vg.p, zs, wp, fac32, facT32,
-                                                         Wb, Sinv, v, z, (float2*)scratch);
-    } else {
-      const size_t bs = sizeof(cplx) * ((size_t)2 * band_chunk(T.band) * band_rs<cplx>(T.band) +
-                                        4 * (size_t)band_chunk(T.band));
-      k_band_apply_pair<cplx><<<nsys / 2, 32, bs, s>>>(T.n_loops, T.n_band, T.band, T.n_border, nport, T.n_mat,
-                                                       c->d.band_perm.p, c->d.border_vg.p, zs, wp, fac, facT, Wb,
-                                                       Sinv, v, z, (cplx*)scratch);
-    }
-  } else if (fac32) {
-    const size_t bs = band_smem_bytes<float2>(T.band) + 64;
-    if (bs > 48 * 1024)
-      XRL_CUDA(cudaFuncSetAttribute(k_band_apply<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs));
-    k_band_apply<float2><<<nsys, 32, bs, s>>>(T.n_loops, T.n_band, T.band, T.n_border, nport, T.n_mat,
-                                              c->d.band_perm.p, c->d.border_vg.p, zs, wp, fac32, facT32, Wb, Sinv, v, z,
-                                              (float2*)scratch, active);
-  } else {
-    const size_t bs = band_smem_bytes<cplx>(T.band) + 64;
-    if (bs > 48 * 1024)
-      XRL_CUDA(cudaFuncSetAttribute(k_band_apply<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs));
-    k_band_apply<cplx><<<nsys, 32, bs, s>>>(T.n_loops, T.n_band, T.band, T.n_border, nport, T.n_mat,
-                                            c->d.band_perm.p, c->d.border_vg.p, zs, wp, fac, facT, Wb, Sinv, v, z,
-                                            (cplx*)scratch, active);
-  }
-  const double es = fac32 ? 8.0 : 16.0;
-  prof_end(c, s, ev, PH_PREC, 1, 16.0 * nsys * (double)T.n_band * T.band,
+  const size_t xs = (size_t)((T.n_band + 2) & ~1);
+  if (bw.mixed)
+    spike_stages<float2>(c, bw, nsys, nport, 0, zs, wp, bw.fac32.p, bw.facT32.p, bw.Vsp32.p, bw.Wsp32.p,
+                         bw.Einv32.p, bw.scr32.p, xs, bw.hb32.p, v, z, active, s);
+  else
+    spike_stages<cplx>(c, bw, nsys, nport, 0, zs, wp, bw.fac.p, bw.facT.p, bw.Vsp.p, bw.Wsp.p, bw.Einv.p,
+                       bw.scr.p, xs, bw.hb.p, v, z, active, s);
+  const double es = bw.mixed ? 8.0 : 16.0;
+  prof_end(c, s, ev, PH_PREC, bw.P > 1 ? 3 : 2, 16.0 * nsys * (double)T.n_band * T.band * (bw.P > 1 ? 3 : 1),
            es * nsys * (double)T.n_band * (2.0 * T.band + 4.0));
-  XRL_CUDA(cudaGetLastError());
 }
 
 }  // namespace xrl

@@ -544,8 +544,8 @@ static unsigned nblk(size_t n, int bs = 256) { return (unsigned)((n + bs - 1) / 
 // Work arrays of one solve (device)
 struct Work {
   DBuf<double> freq, wp, wpf;
-  DBuf<cplx> zs, zsf, fac, facT, Wb, Sinv, bscr;
-  DBuf<float2> fac32, facT32;
+  DBuf<cplx> zs, zsf;
+  BandWork bw;
   int nport = 1;
   bool banded = false;
   DBuf<cplx> b, x, w, tmp, V, Z, H, h1, h2, cs, sn, g, y, Vb, dinv, zst;
@@ -637,8 +637,7 @@ static void apply_Qinv(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* z) {
     return;
   }
   if (wk.banded) {
-    band_apply(c, nsys, wk.nport, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.facT.p, wk.fac32.p, wk.facT32.p, wk.Wb.p,
-               wk.Sinv.p, v, z, wk.bscr.p, wk.active.p, s);
+    band_apply(c, wk.bw, nsys, wk.nport, wk.zsf.p, wk.wpf.p, v, z, wk.active.p, s);
     return;
   }
   const size_t tot = (size_t)n * nsys;
@@ -718,17 +717,8 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
   wk.kcols.alloc(c->alloc, nsys);
   wk.banded = c->opt.precond == 1 && band_usable(c);
   if (wk.banded) {
-    const Topo& TT = c->topo;
-    wk.fac.alloc(c->alloc, (size_t)nf * TT.n_band * (TT.band + 1));
-    wk.facT.alloc(c->alloc, (size_t)nf * TT.n_band * (TT.band + 1));
-    wk.Wb.alloc(c->alloc, (size_t)nf * std::max(1, TT.n_border) * TT.n_band);
-    wk.Sinv.alloc(c->alloc, (size_t)nf * std::max(1, TT.n_border * TT.n_border));
-    wk.bscr.alloc(c->alloc, (size_t)nsys * (TT.n_band + 2));
-    if (mixed) {
-      wk.fac32.alloc(c->alloc, (size_t)nf * TT.n_band * ((TT.band + 2) & ~1));
-      wk.facT32.alloc(c->alloc, (size_t)nf * TT.n_band * ((TT.band + 2) & ~1));
-    }
-    band_factor(c, nf, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.facT.p, wk.fac32.p, wk.facT32.p, wk.Wb.p, wk.Sinv.p, s);
+    band_alloc(c, wk.bw, nf, nsys, mixed);
+    band_factor(c, wk.bw, wk.zsf.p, wk.wpf.p, s);
   } else if (c->opt.precond) {
     wk.dinv.alloc(c->alloc, tot);
     apply_Qmat(c, wk, nsys, nullptr, wk.w.p, 1);
@@ -764,15 +754,10 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
                                                                    wp0.p, wk.X.p, wk.X.p, wk.Vb.p);
     k_loop_reduce<<<nblk(tot), 256, 0, s>>>(n, nsys, TT.n_cb, TT.n_cb, c->d.m_ptr.p, c->d.m_col.p, c->d.m_val.p,
                                             wk.Vb.p, wk.w.p);
-    DBuf<cplx> pf, pfT, pW, pS, pscr;
-    pf.alloc(c->alloc, (size_t)TT.n_band * (TT.band + 1));
-    pfT.alloc(c->alloc, (size_t)TT.n_band * (TT.band + 1));
-    pW.alloc(c->alloc, (size_t)std::max(1, TT.n_border) * TT.n_band);
-    pS.alloc(c->alloc, (size_t)std::max(1, TT.n_border * TT.n_border));
-    pscr.alloc(c->alloc, (size_t)nsys * (TT.n_band + 2));
-    band_factor(c, 1, zs1.p, wp0.p, pf.p, pfT.p, nullptr, nullptr, pW.p, pS.p, s);
-    band_apply(c, nsys, nsys, zs1.p, wp0.p, pf.p, pfT.p, nullptr, nullptr, pW.p, pS.p, wk.w.p, wk.x.p, pscr.p,
-               nullptr, s);
+    BandWork pw;
+    band_alloc(c, pw, 1, nsys, false);
+    band_factor(c, pw, zs1.p, wp0.p, s);
+    band_apply(c, pw, nsys, nsys, zs1.p, wp0.p, wk.w.p, wk.x.p, nullptr, s);
     count_launch(c, 3);
     apply_A(c, wk, nsys, wk.x.p, wk.w.p);
     DBuf<int> dacc;
@@ -947,15 +932,9 @@ void apply_operator_host(xrl_ctx* c, int nsys, const double* freq, const double*
   if (mode == 1) {
     apply_Qmat(c, wk, nsys, dv.p, dw.p, 0);
   } else if (mode == 2) {
-    const Topo& TT = c->topo;
-    wk.fac.alloc(c->alloc, (size_t)nsys * TT.n_band * (TT.band + 1));
-    wk.facT.alloc(c->alloc, (size_t)nsys * TT.n_band * (TT.band + 1));
-    wk.Wb.alloc(c->alloc, (size_t)nsys * std::max(1, TT.n_border) * TT.n_band);
-    wk.Sinv.alloc(c->alloc, (size_t)nsys * std::max(1, TT.n_border * TT.n_border));
-    wk.bscr.alloc(c->alloc, (size_t)nsys * (TT.n_band + 2));
-    band_factor(c, nsys, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.facT.p, nullptr, nullptr, wk.Wb.p, wk.Sinv.p, c->stream);
-    band_apply(c, nsys, 1, wk.zsf.p, wk.wpf.p, wk.fac.p, wk.facT.p, nullptr, nullptr, wk.Wb.p, wk.Sinv.p, dv.p,
-               dw.p, wk.bscr.p, nullptr, c->stream);
+    band_alloc(c, wk.bw, nsys, nsys, false);
+    band_factor(c, wk.bw, wk.zsf.p, wk.wpf.p, c->stream);
+    band_apply(c, wk.bw, nsys, 1, wk.zsf.p, wk.wpf.p, dv.p, dw.p, nullptr, c->stream);
   } else {
     apply_A(c, wk, nsys, dv.p, dw.p);
   }

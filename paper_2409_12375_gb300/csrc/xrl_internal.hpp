@@ -326,9 +326,16 @@ void apply_operator_host(xrl_ctx* c, int nsys, const double* f, const double* v,
 // precond.cu
 bool band_usable(const xrl_ctx* c);
 void band_prepare(xrl_ctx* c);
-void band_factor(xrl_ctx* c, int nf, const double2* zs, const double* wp, double2* fac, double2* facT, float2* fac32,
-                 float2* facT32, double2* Wb, double2* Sinv, cudaStream_t s);
-void band_apply(xrl_ctx* c, int nsys, int nport, const double2* zs, const double* wp, const double2* fac,
-                const double2* facT, const float2* fac32, const float2* facT32, const double2* Wb,
-                const double2* Sinv, const double2* v, double2* z, void* scratch, const int* active, cudaStream_t s);
+// Factor and work arrays of the banded preconditioner for nf frequencies,
+// partitioned into P blocks of m rows (see precond.cu).
+struct BandWork {
+  int nf = 0, P = 1, m = 0;
+  bool mixed = false;
+  DBuf<double2> fac, facT, Wb, Sinv, Vsp, Wsp, Einv, hbB, scr, hb;
+  DBuf<float2> fac32, facT32, Vsp32, Wsp32, Einv32, scr32, hb32;
+};
+void band_alloc(xrl_ctx* c, BandWork& bw, int nf, int nsys, bool mixed);
+void band_factor(xrl_ctx* c, BandWork& bw, const double2* zs, const double* wp, cudaStream_t s);
+void band_apply(xrl_ctx* c, BandWork& bw, int nsys, int nport, const double2* zs, const double* wp,
+                const double2* v, double2* z, const int* active, cudaStream_t s);
 }  // namespace xrl
