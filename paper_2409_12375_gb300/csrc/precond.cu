@@ -383,6 +383,26 @@ __global__ void k_schur(int n, int ng, int nmat, const double* __restrict__ bord
   }
 }
 
+template <class C>
+__device__ __forceinline__ C to_c(cplx v);
+template <>
+__device__ __forceinline__ float2 to_c<float2>(cplx v) { return make_float2((float)v.x, (float)v.y); }
+template <>
+__device__ __forceinline__ double2 to_c<double2>(cplx v) { return v; }
+__device__ __forceinline__ cplx to_d(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ cplx to_d(double2 v) { return v; }
+
+__device__ __forceinline__ float cabs2T(float2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double cabs2T(double2 a) { return cabs2(a); }
+__device__ __forceinline__ float2 crecipT(float2 a) {
+  const float d = a.x * a.x + a.y * a.y;
+  return make_float2(a.x / d, -a.y / d);
+}
+__device__ __forceinline__ double2 crecipT(double2 a) { return cdiv(make_double2(1.0, 0.0), a); }
+template <class C> __device__ __forceinline__ C cone();
+template <> __device__ __forceinline__ float2 cone<float2>() { return make_float2(1.f, 0.f); }
+template <> __device__ __forceinline__ double2 cone<double2>() { return make_double2(1.0, 0.0); }
+
 // ---- partitioned (SPIKE) factor --------------------------------------------------------------
 
 // LDL^T of the diagonal block j of Q_vv(f) (rows [s0, e0)), couplings to other
@@ -453,13 +473,14 @@ __global__ void k_band_factor_blk(int n, int b, int P, int m, int nmat, const do
 // W_j[:, c] = A_j^-1 [C_j[:, c]; 0] (col = b + c, j > 0), stored by column,
 // Vsp[f][c][i] for the rows i of block j.  B_j[r][c] = Q[e0-b+r][e0+c]
 // (r >= c) and C_j[r][c] = Q[s0+r][s0-b+c] (c >= r) read from the band rows.
-// One warp per (f, j, col).
-__global__ void k_spike_cols(int n, int b, int P, int m, int nmat, const double* __restrict__ band_val,
-                             const cplx* __restrict__ zs, const double* __restrict__ wp_f,
-                             const cplx* __restrict__ fac, const cplx* __restrict__ facT, cplx* __restrict__ Vsp,
-                             cplx* __restrict__ Wsp) {
+// One warp per (f, j, col); C = float2 (mixed precision, from the FP32
+// factor copies) or double2.
+template <class C>
+__global__ void k_spike_cols(int n, int ns, int b, int P, int m, int nmat, const double* __restrict__ band_val,
+                             const cplx* __restrict__ zs, const double* __restrict__ wp_f, const C* __restrict__ fac,
+                             const C* __restrict__ facT, C* __restrict__ Vsp, C* __restrict__ Wsp) {
   extern __shared__ __align__(16) unsigned char ssm_raw[];
-  cplx* ssm = reinterpret_cast<cplx*>(ssm_raw);
+  C* ssm = reinterpret_cast<C*>(ssm_raw);
   const int col = blockIdx.x % (2 * b);
   const int j = (blockIdx.x / (2 * b)) % P;
   const int f = blockIdx.x / (2 * b * P);
@@ -473,7 +494,7 @@ __global__ void k_spike_cols(int n, int b, int P, int m, int nmat, const double*
   const bool isV = col < b;
   const int c = isV ? col : col - b;
   if (isV ? (j == P - 1) : (j == 0)) return;
-  cplx* x = (isV ? Vsp : Wsp) + ((size_t)f * b + c) * n + s0;
+  C* x = (isV ? Vsp : Wsp) + ((size_t)f * b + c) * ns + s0;
   for (int i = lane; i < mm; i += 32) {
     cplx v = make_double2(0.0, 0.0);
     if (isV) {
@@ -483,25 +504,26 @@ __global__ void k_spike_cols(int n, int b, int P, int m, int nmat, const double*
       const int r = i;
       if (r <= c) v = pencil(band_val + (size_t)(s0 + r) * nb1 + (c - r), stride, nmat, z, wp);
     }
-    x[i] = v;
+    x[i] = to_c<C>(v);
   }
   __syncwarp();
-  const size_t fo = (size_t)f * stride + (size_t)s0 * nb1;
-  band_solve_warp<cplx>(mm, b, nb1, facT + fo, fac + fo, x, ssm);
+  const int rs = band_rs<C>(b);
+  const size_t fo = ((size_t)f * n + s0) * rs;
+  band_solve_warp<C>(mm, b, rs, facT + fo, fac + fo, x, ssm);
 }
 
 // In-place inverse of the n x n complex matrix A (row-major, leading dimension
 // lda, shared memory) by Gauss-Jordan elimination with partial pivoting; all
-// threads of the CTA.  piv: n ints of shared memory.
-__device__ void gj_inverse(cplx* A, int n, int lda, int* piv, cplx* colk) {
+// threads of the CTA.  piv: n ints of shared memory, colk: n elements.
+template <class C>
+__device__ void gj_inverse(C* A, int n, int lda, int* piv, C* colk, C* pinv_s) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  __shared__ cplx pinv_s;
   for (int k = 0; k < n; ++k) {
     if (tid == 0) {
       int p = k;
-      double best = cabs2(A[k * lda + k]);
+      auto best = cabs2T(A[k * lda + k]);
       for (int i = k + 1; i < n; ++i) {
-        double v = cabs2(A[i * lda + k]);
+        auto v = cabs2T(A[i * lda + k]);
         if (v > best) {
           best = v;
           p = i;
@@ -513,22 +535,22 @@ __device__ void gj_inverse(cplx* A, int n, int lda, int* piv, cplx* colk) {
     const int p = piv[k];
     if (p != k)
       for (int cc = tid; cc < n; cc += nt) {
-        cplx t = A[k * lda + cc];
+        C t = A[k * lda + cc];
         A[k * lda + cc] = A[p * lda + cc];
         A[p * lda + cc] = t;
       }
     __syncthreads();
-    if (tid == 0) pinv_s = cdiv(make_double2(1.0, 0.0), A[k * lda + k]);
+    if (tid == 0) *pinv_s = crecipT(A[k * lda + k]);
     for (int i = tid; i < n; i += nt) colk[i] = A[i * lda + k];
     __syncthreads();
-    const cplx pinv = pinv_s;
-    for (int cc = tid; cc < n; cc += nt) A[k * lda + cc] = cm(cc == k ? make_double2(1.0, 0.0) : A[k * lda + cc], pinv);
+    const C pinv = *pinv_s;
+    for (int cc = tid; cc < n; cc += nt) A[k * lda + cc] = cmul(cc == k ? cone<C>() : A[k * lda + cc], pinv);
     __syncthreads();
     for (int e = tid; e < n * n; e += nt) {
       const int i = e / n, cc = e % n;
       if (i == k) continue;
-      const cplx a = cc == k ? make_double2(0.0, 0.0) : A[i * lda + cc];
-      A[i * lda + cc] = csub(a, cm(A[k * lda + cc], colk[i]));
+      const C a = cc == k ? czero<C>() : A[i * lda + cc];
+      A[i * lda + cc] = csubT(a, cmul(A[k * lda + cc], colk[i]));
     }
     __syncthreads();
   }
@@ -536,7 +558,7 @@ __device__ void gj_inverse(cplx* A, int n, int lda, int* piv, cplx* colk) {
     const int p = piv[k];
     if (p != k)
       for (int i = tid; i < n; i += nt) {
-        cplx t = A[i * lda + k];
+        C t = A[i * lda + k];
         A[i * lda + k] = A[i * lda + p];
         A[i * lda + p] = t;
       }
@@ -544,51 +566,61 @@ __device__ void gj_inverse(cplx* A, int n, int lda, int* piv, cplx* colk) {
   }
 }
 
-// Block LU of the reduced system: Einv[f][j] = E^_j^-1 (2b x 2b, column-major)
-// for j < P-1; one CTA per frequency, sequential over j.
-__global__ void k_spike_reduce(int n, int b, int P, int m, const cplx* __restrict__ Vsp, const cplx* __restrict__ Wsp,
-                               cplx* __restrict__ Einv) {
-  extern __shared__ cplx rsm[];
+// Block LU of the reduced system, one CTA per frequency, sequential over j:
+// record R[f][j] (6 b^2 elements) = [E^_j^-1 (2b x 2b, column-major) |
+// W_j^bot ([c][r], zero for j = 0) | V_{j+1}^top ([c][r], zero for j = P-2)],
+// everything one step of the reduced substitution reads.
+template <class C>
+__global__ void k_spike_reduce(int ns, int b, int P, int m, const C* __restrict__ Vsp, const C* __restrict__ Wsp,
+                               C* __restrict__ R) {
+  extern __shared__ __align__(16) unsigned char rsm_raw[];
+  C* E = reinterpret_cast<C*>(rsm_raw);   // [B2][B2]
   const int B2 = 2 * b;
-  cplx* E = rsm;                  // [B2][B2]
-  cplx* X01 = E + B2 * B2;        // [b][b] top-right block of the previous inverse
-  cplx* T = X01 + b * b;          // [b][b]
-  cplx* colk = T + b * b;         // [B2]
-  int* piv = reinterpret_cast<int*>(colk + B2);
+  C* X01 = E + B2 * B2;        // [b][b] top-right block of the previous inverse
+  C* T = X01 + b * b;          // [b][b]
+  C* colk = T + b * b;         // [B2]
+  C* pinv = colk + B2;         // [1]
+  int* piv = reinterpret_cast<int*>(pinv + 1);
   const int f = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  const cplx* V = Vsp + (size_t)f * b * n;
-  const cplx* W = Wsp + (size_t)f * b * n;
+  const C* V = Vsp + (size_t)f * b * ns;
+  const C* W = Wsp + (size_t)f * b * ns;
+  const size_t RS = (size_t)6 * b * b;
   for (int j = 0; j + 1 < P; ++j) {
     const int sj = j * m, e = (j + 1) * m;
     for (int q = tid; q < B2 * B2; q += nt) {
       const int r = q / B2, cc = q % B2;
-      cplx v = make_double2(r == cc ? 1.0 : 0.0, 0.0);
-      if (r < b && cc >= b) v = V[(size_t)(cc - b) * n + e - b + r];
-      if (r >= b && cc < b) v = W[(size_t)cc * n + e + (r - b)];
+      C v = r == cc ? cone<C>() : czero<C>();
+      if (r < b && cc >= b) v = V[(size_t)(cc - b) * ns + e - b + r];
+      if (r >= b && cc < b) v = W[(size_t)cc * ns + e + (r - b)];
       E[q] = v;
     }
     if (j > 0) {
       // T = X01 V_j^top, then E_tr -= W_j^bot T
       for (int q = tid; q < b * b; q += nt) {
         const int r = q / b, cc = q % b;
-        cplx acc = make_double2(0.0, 0.0);
-        for (int k = 0; k < b; ++k) acc = cadd(acc, cm(X01[r * b + k], V[(size_t)cc * n + sj + k]));
+        C acc = czero<C>();
+        for (int k = 0; k < b; ++k) acc = cfma(X01[r * b + k], V[(size_t)cc * ns + sj + k], acc);
         T[q] = acc;
       }
       __syncthreads();
       for (int q = tid; q < b * b; q += nt) {
         const int r = q / b, cc = q % b;
-        cplx acc = make_double2(0.0, 0.0);
-        for (int k = 0; k < b; ++k) acc = cadd(acc, cm(W[(size_t)k * n + e - b + r], T[k * b + cc]));
-        E[r * B2 + b + cc] = csub(E[r * B2 + b + cc], acc);
+        C acc = czero<C>();
+        for (int k = 0; k < b; ++k) acc = cfma(W[(size_t)k * ns + e - b + r], T[k * b + cc], acc);
+        E[r * B2 + b + cc] = csubT(E[r * B2 + b + cc], acc);
       }
     }
     __syncthreads();
-    gj_inverse(E, B2, B2, piv, colk);
-    cplx* out = Einv + ((size_t)f * (P - 1) + j) * B2 * B2;
+    gj_inverse<C>(E, B2, B2, piv, colk, pinv);
+    C* out = R + ((size_t)f * (P - 1) + j) * RS;
     for (int q = tid; q < B2 * B2; q += nt) {
       const int r = q / B2, cc = q % B2;
       out[(size_t)cc * B2 + r] = E[q];
+    }
+    for (int q = tid; q < b * b; q += nt) {
+      const int cc = q / b, r = q % b;
+      out[(size_t)4 * b * b + q] = j > 0 ? W[(size_t)cc * ns + e - b + r] : czero<C>();
+      out[(size_t)5 * b * b + q] = j + 2 < P ? V[(size_t)cc * ns + e + r] : czero<C>();
     }
     for (int q = tid; q < b * b; q += nt) X01[q] = E[(q / b) * B2 + b + q % b];
     __syncthreads();
@@ -601,15 +633,6 @@ __global__ void k_to_f32(size_t n, const double* __restrict__ a, float* __restri
 }
 
 // ---- partitioned (SPIKE) apply ---------------------------------------------------------------
-template <class C>
-__device__ __forceinline__ C to_c(cplx v);
-template <>
-__device__ __forceinline__ float2 to_c<float2>(cplx v) { return make_float2((float)v.x, (float)v.y); }
-template <>
-__device__ __forceinline__ double2 to_c<double2>(cplx v) { return v; }
-__device__ __forceinline__ cplx to_d(float2 v) { return make_double2(v.x, v.y); }
-__device__ __forceinline__ cplx to_d(double2 v) { return v; }
-
 // Stage 1: y_j = A_j^-1 f_j for block j = blockIdx.y.  mode 0: the right-hand
 // side is v[s][perm[i]] of system s (two systems sharing a frequency per warp
 // when `pair`), stored in x[s] (stride xs); mode 1: it is column g of Q_vg(f),
@@ -650,52 +673,72 @@ __global__ void k_spike_y(int n, int b, int P, int m, int nper, int pair, int mo
     band_solve_warp<C>(mm, b, rs, facT + fo, fac + fo, x0, ysm);
 }
 
+// cp.async of `bytes` (a multiple of 16) from global to shared memory by one warp
+__device__ __forceinline__ void warp_copy_async(void* dst, const void* src, size_t bytes) {
+  const int lane = threadIdx.x & 31;
+  char* d = reinterpret_cast<char*>(dst);
+  const char* g = reinterpret_cast<const char*>(src);
+  for (size_t o = 16 * (size_t)lane; o < bytes; o += 32 * 16) cp_async16(d + o, g + o);
+  cp_commit();
+}
+
 // Stage 2: the reduced block-tridiagonal system for z_j = (u_j, t_{j+1}),
-// forward then backward; one warp per system, h[s][j][2b] holds h_j and then z_j.
+// forward then backward; one warp per system, h[s][j][2b] holds h_j and then
+// z_j.  The records R[f][j] stream through a double buffer in shared memory.
 template <class C>
-__global__ void k_spike_z(int n, int b, int P, int m, int nper, const C* __restrict__ Vsp, const C* __restrict__ Wsp,
-                          const C* __restrict__ Einv, const C* __restrict__ xb, size_t xs, C* __restrict__ hb,
-                          const int* __restrict__ active) {
-  __shared__ C g[128], hp[64], tt[64];
+__global__ void k_spike_z(int n, int b, int P, int m, int nper, const C* __restrict__ R, const C* __restrict__ xb,
+                          size_t xs, C* __restrict__ hb, const int* __restrict__ active) {
+  extern __shared__ __align__(16) unsigned char zsm_raw[];
+  C* rbuf = reinterpret_cast<C*>(zsm_raw);   // [2][6 b^2]
+  __shared__ C g[64], hp[32], tt[32];
   const int s = blockIdx.x;
   if (P < 2 || (active && !active[s])) return;
   const int f = s / nper, lane = threadIdx.x, B2 = 2 * b;
+  const size_t RS = (size_t)6 * b * b;
+  const C* Rf = R + (size_t)f * (P - 1) * RS;
   const C* x = xb + (size_t)s * xs;
-  const C* V = Vsp + (size_t)f * b * n;
-  const C* W = Wsp + (size_t)f * b * n;
-  const C* E = Einv + (size_t)f * (P - 1) * B2 * B2;
   C* h = hb + (size_t)s * (P - 1) * B2;
+  warp_copy_async(rbuf, Rf, RS * sizeof(C));
   for (int j = 0; j + 1 < P; ++j) {
+    const bool more = j + 2 < P;
+    if (more) warp_copy_async(rbuf + ((j + 1) & 1) * RS, Rf + (size_t)(j + 1) * RS, RS * sizeof(C));
     const int e = (j + 1) * m;
     for (int r = lane; r < B2; r += 32) g[r] = x[e - b + r];
+    if (more) cp_wait_all_but_one(); else cp_wait_all();
     __syncwarp();
+    const C* Ej = rbuf + (j & 1) * RS;
+    const C* Wj = Ej + 4 * b * b;
     if (j > 0)
       for (int r = lane; r < b; r += 32) {
         C acc = czero<C>();
-        for (int c = 0; c < b; ++c) acc = cfma(W[(size_t)c * n + e - b + r], hp[c], acc);
+        for (int c = 0; c < b; ++c) acc = cfma(Wj[c * b + r], hp[c], acc);
         g[r] = csubT(g[r], acc);
       }
     __syncwarp();
-    const C* Ej = E + (size_t)j * B2 * B2;
     for (int r = lane; r < B2; r += 32) {
       C acc = czero<C>();
-      for (int c = 0; c < B2; ++c) acc = cfma(Ej[(size_t)c * B2 + r], g[c], acc);
+      for (int c = 0; c < B2; ++c) acc = cfma(Ej[c * B2 + r], g[c], acc);
       h[(size_t)j * B2 + r] = acc;
       if (r < b) hp[r] = acc;
     }
     __syncwarp();
   }
-  for (int j = P - 3; j >= 0; --j) {
-    const int sn = (j + 1) * m;   // first row of block j+1
+  if (P < 3) return;
+  warp_copy_async(rbuf, Rf + (size_t)(P - 3) * RS, RS * sizeof(C));
+  for (int j = P - 3, q = 0; j >= 0; --j, ++q) {
+    const bool more = j > 0;
+    if (more) warp_copy_async(rbuf + ((q + 1) & 1) * RS, Rf + (size_t)(j - 1) * RS, RS * sizeof(C));
     for (int r = lane; r < b; r += 32) g[r] = h[(size_t)(j + 1) * B2 + b + r];
+    if (more) cp_wait_all_but_one(); else cp_wait_all();
     __syncwarp();
+    const C* Ej = rbuf + (q & 1) * RS;
+    const C* Vt = Ej + 5 * b * b;
     for (int r = lane; r < b; r += 32) {
       C acc = czero<C>();
-      for (int c = 0; c < b; ++c) acc = cfma(V[(size_t)c * n + sn + r], g[c], acc);
+      for (int c = 0; c < b; ++c) acc = cfma(Vt[c * b + r], g[c], acc);
       tt[r] = acc;
     }
     __syncwarp();
-    const C* Ej = E + (size_t)j * B2 * B2;
     for (int r = lane; r < B2; r += 32) {
       C acc = czero<C>();
       for (int c = 0; c < b; ++c) acc = cfma(Ej[(size_t)(b + c) * B2 + r], tt[c], acc);
@@ -705,85 +748,105 @@ __global__ void k_spike_z(int n, int b, int P, int m, int nper, const C* __restr
   }
 }
 
-// Stage 3: x_j = y_j - V_j t_{j+1} - W_j u_{j-1} in place; mode 0 then applies
-// the border (t_g = v_g - Q_vg^T x, z_g = S^-1 t_g, x -= W_b z_g) and scatters
-// to loop order into z[s]; one CTA per system.
+constexpr int kSpikeRows = 1024;   // rows per CTA of the correction kernels
+
+// Stage 3a: x_j = y_j - V_j t_{j+1} - W_j u_{j-1} in place for rows
+// [blockIdx.y * kSpikeRows, +kSpikeRows) of system blockIdx.x; in mode 0 also
+// the partial border sums part[s][chunk][g] = sum_i Q_vg[i][g] x_i.
 template <class C>
-__global__ void __launch_bounds__(256) k_spike_x(int n, int b, int P, int m, int nper, int mode, int nloop, int ng,
-                                                 int nmat, const int32_t* __restrict__ perm,
+__global__ void __launch_bounds__(256) k_spike_x(int n, int ns, int b, int P, int m, int nper, int mode, int ng,
+                                                 int nmat,
                                                  const double* __restrict__ border_vg, const cplx* __restrict__ zs,
                                                  const double* __restrict__ wp_f, const C* __restrict__ Vsp,
-                                                 const C* __restrict__ Wsp, const C* __restrict__ hb, C* __restrict__ xb,
-                                                 size_t xs, const cplx* __restrict__ Wb, const cplx* __restrict__ Sinv,
-                                                 const cplx* __restrict__ v, cplx* __restrict__ z,
+                                                 const C* __restrict__ Wsp, const C* __restrict__ hb,
+                                                 C* __restrict__ xb, size_t xs, cplx* __restrict__ part,
                                                  const int* __restrict__ active) {
   extern __shared__ __align__(16) unsigned char xsm_raw[];
   C* hs = reinterpret_cast<C*>(xsm_raw);   // [(P-1)][2b]
   __shared__ cplx red[8][kMaxBorder];
-  __shared__ cplx zg[kMaxBorder];
   const int s = blockIdx.x;
   if (active && !active[s]) return;
   const int f = s / nper, tid = threadIdx.x, B2 = 2 * b;
+  const int i0 = blockIdx.y * kSpikeRows, i1 = min(n, i0 + kSpikeRows);
   C* x = xb + (size_t)s * xs;
   if (P > 1) {
-    const C* V = Vsp + (size_t)f * b * n;
-    const C* W = Wsp + (size_t)f * b * n;
+    const C* V = Vsp + (size_t)f * b * ns;
+    const C* W = Wsp + (size_t)f * b * ns;
     for (int e = tid; e < (P - 1) * B2; e += blockDim.x) hs[e] = hb[(size_t)s * (P - 1) * B2 + e];
     __syncthreads();
-    for (int i = tid; i < n; i += blockDim.x) {
+    for (int i = i0 + tid; i < i1; i += blockDim.x) {
       const int j = min(i / m, P - 1);
       C y = x[i];
       if (j < P - 1) {
         const C* t = hs + j * B2 + b;
-        for (int c = 0; c < b; ++c) y = csubT(y, cmul(V[(size_t)c * n + i], t[c]));
+        for (int c = 0; c < b; ++c) y = csubT(y, cmul(V[(size_t)c * ns + i], t[c]));
       }
       if (j > 0) {
         const C* u = hs + (j - 1) * B2;
-        for (int c = 0; c < b; ++c) y = csubT(y, cmul(W[(size_t)c * n + i], u[c]));
+        for (int c = 0; c < b; ++c) y = csubT(y, cmul(W[(size_t)c * ns + i], u[c]));
       }
       x[i] = y;
     }
   }
-  if (mode == 1) return;
-  const cplx* vs = v + (size_t)s * nloop;
+  if (mode == 1 || ng == 0) return;
+  const cplx* zf = zs + (size_t)f * nmat;
+  const double wp = wp_f[f];
+  const size_t vstride = (size_t)n * ng;
+  cplx acc[kMaxBorder];
+  for (int g = 0; g < ng; ++g) acc[g] = make_double2(0.0, 0.0);
+  for (int i = i0 + tid; i < i1; i += blockDim.x) {
+    const cplx xi = to_d(x[i]);
+    for (int g = 0; g < ng; ++g)
+      acc[g] = cadd(acc[g], cm(pencil(border_vg + (size_t)i * ng + g, vstride, nmat, zf, wp), xi));
+  }
+  const int w = tid >> 5, lane = tid & 31;
+  for (int g = 0; g < ng; ++g) {
+    cplx t = warp_sum(acc[g]);
+    if (lane == 0) red[w][g] = t;
+  }
+  __syncthreads();
+  if (tid < ng) {
+    cplx t = make_double2(0.0, 0.0);
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = cadd(t, red[q][tid]);
+    part[((size_t)s * gridDim.y + blockIdx.y) * ng + tid] = t;
+  }
+}
+
+// Stage 3b (mode 0): t_g = v_g - sum of the partial border sums, z_g = S^-1 t_g,
+// then z[s][perm[i]] = x_i - sum_g W_b[g][i] z_g and z[s][n + g] = z_g.
+template <class C>
+__global__ void __launch_bounds__(256) k_spike_out(int n, int nper, int nloop, int ng, int nchunk,
+                                                   const int32_t* __restrict__ perm, const C* __restrict__ xb,
+                                                   size_t xs, const cplx* __restrict__ part,
+                                                   const cplx* __restrict__ Wb, const cplx* __restrict__ Sinv,
+                                                   const cplx* __restrict__ v, cplx* __restrict__ z,
+                                                   const int* __restrict__ active) {
+  __shared__ cplx tg[kMaxBorder], zg[kMaxBorder];
+  const int s = blockIdx.x;
+  if (active && !active[s]) return;
+  const int f = s / nper, tid = threadIdx.x;
+  const int i0 = blockIdx.y * kSpikeRows, i1 = min(n, i0 + kSpikeRows);
+  const C* x = xb + (size_t)s * xs;
   cplx* zo = z + (size_t)s * nloop;
   if (ng > 0) {
-    const cplx* zf = zs + (size_t)f * nmat;
-    const double wp = wp_f[f];
-    const size_t vstride = (size_t)n * ng;
-    cplx acc[kMaxBorder];
-    for (int g = 0; g < ng; ++g) acc[g] = make_double2(0.0, 0.0);
-    for (int i = tid; i < n; i += blockDim.x) {
-      const cplx xi = to_d(x[i]);
-      for (int g = 0; g < ng; ++g)
-        acc[g] = cadd(acc[g], cm(pencil(border_vg + (size_t)i * ng + g, vstride, nmat, zf, wp), xi));
-    }
-    const int w = tid >> 5, lane = tid & 31;
-    for (int g = 0; g < ng; ++g) {
-      cplx t = warp_sum(acc[g]);
-      if (lane == 0) red[w][g] = t;
+    if (tid < ng) {
+      cplx t = make_double2(0.0, 0.0);
+      for (int q = 0; q < nchunk; ++q) t = cadd(t, part[((size_t)s * nchunk + q) * ng + tid]);
+      tg[tid] = csub(v[(size_t)s * nloop + n + tid], t);
     }
     __syncthreads();
     if (tid < ng) {
       cplx t = make_double2(0.0, 0.0);
-      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = cadd(t, red[q][tid]);
-      red[0][tid] = csub(vs[n + tid], t);   // t_g
-    }
-    __syncthreads();
-    if (tid < ng) {
-      cplx t = make_double2(0.0, 0.0);
-      for (int g2 = 0; g2 < ng; ++g2) t = cadd(t, cm(Sinv[((size_t)f * ng + tid) * ng + g2], red[0][g2]));
+      for (int g2 = 0; g2 < ng; ++g2) t = cadd(t, cm(Sinv[((size_t)f * ng + tid) * ng + g2], tg[g2]));
       zg[tid] = t;
+      if (blockIdx.y == 0) zo[n + tid] = t;
     }
     __syncthreads();
-    for (int i = tid; i < n; i += blockDim.x) {
-      cplx a = to_d(x[i]);
-      for (int g = 0; g < ng; ++g) a = csub(a, cm(Wb[((size_t)f * ng + g) * n + i], zg[g]));
-      zo[perm[i]] = a;
-    }
-    if (tid < ng) zo[n + tid] = zg[tid];
-  } else {
-    for (int i = tid; i < n; i += blockDim.x) zo[perm[i]] = to_d(x[i]);
+  }
+  for (int i = i0 + tid; i < i1; i += blockDim.x) {
+    cplx a = to_d(x[i]);
+    for (int g = 0; g < ng; ++g) a = csub(a, cm(Wb[((size_t)f * ng + g) * n + i], zg[g]));
+    zo[perm[i]] = a;
   }
 }
 
@@ -801,12 +864,12 @@ void band_prepare(xrl_ctx* c) {
 }
 
 // Blocks of m rows (even, >= 4b; the last block takes the remainder and has
-// at least 2b rows), at most 64 of them and at most 1024 / b (the stage-3
-// shared copy of the interface values); one block (the plain band solve) for
-// short bands or b > 40 (the reduced-system inverse lives in shared memory).
+// at least 2b rows), at most 64 of them; one block (the plain band solve) for
+// short bands or b > 24 (the reduced substitution keeps two 6 b^2 records in
+// shared memory).
 static void band_blocks(int n, int b, int* P, int* m) {
-  int pm = std::max(1, std::min(64, 1024 / std::max(1, b)));
-  if (n < 8 * b || pm < 2 || b > 40) {
+  const int pm = 64;
+  if (n < 8 * b || b > 24) {
     *P = 1;
     *m = n;
     return;
@@ -819,6 +882,8 @@ static void band_blocks(int n, int b, int* P, int* m) {
   *m = *P == 1 ? n : mm;
 }
 
+static size_t spike_stride(int n) { return (size_t)((n + 1) & ~1); }
+
 void band_alloc(xrl_ctx* c, BandWork& bw, int nf, int nsys, bool mixed) {
   const Topo& T = c->topo;
   const int n = T.n_band, b = T.band, ng = T.n_border;
@@ -826,51 +891,103 @@ void band_alloc(xrl_ctx* c, BandWork& bw, int nf, int nsys, bool mixed) {
   bw.nf = nf;
   bw.mixed = mixed;
   const int P1 = std::max(1, bw.P - 1);
+  const size_t ns = spike_stride(n);
+  const size_t xs = (size_t)((n + 2) & ~1);
+  const int nchunk = (n + kSpikeRows - 1) / kSpikeRows;
+  const size_t nsb = (size_t)std::max(nsys, nf * std::max(1, ng));   // systems of either solve
   bw.fac.alloc(c->alloc, (size_t)nf * n * (b + 1));
   bw.facT.alloc(c->alloc, (size_t)nf * n * (b + 1));
   bw.Wb.alloc(c->alloc, (size_t)nf * std::max(1, ng) * n);
   bw.Sinv.alloc(c->alloc, (size_t)nf * std::max(1, ng * ng));
-  bw.Vsp.alloc(c->alloc, (size_t)nf * b * n);
-  bw.Wsp.alloc(c->alloc, (size_t)nf * b * n);
-  bw.Einv.alloc(c->alloc, (size_t)nf * P1 * 4 * b * b);
-  bw.hbB.alloc(c->alloc, (size_t)nf * std::max(1, ng) * P1 * 2 * b);
-  const size_t xs = (size_t)((n + 2) & ~1);
+  bw.part.alloc(c->alloc, (size_t)nsys * nchunk * std::max(1, ng));
   if (mixed) {
     const int rs = band_rs<float2>(b);
     bw.fac32.alloc(c->alloc, (size_t)nf * n * rs);
     bw.facT32.alloc(c->alloc, (size_t)nf * n * rs);
-    bw.Vsp32.alloc(c->alloc, (size_t)nf * b * n);
-    bw.Wsp32.alloc(c->alloc, (size_t)nf * b * n);
-    bw.Einv32.alloc(c->alloc, (size_t)nf * P1 * 4 * b * b);
+    if (bw.P > 1) {
+      bw.Vsp32.alloc(c->alloc, (size_t)nf * b * ns);
+      bw.Wsp32.alloc(c->alloc, (size_t)nf * b * ns);
+      bw.R32.alloc(c->alloc, (size_t)nf * P1 * 6 * b * b);
+    }
+    if (ng > 0) bw.Wb32.alloc(c->alloc, (size_t)nf * ng * xs);
     bw.scr32.alloc(c->alloc, (size_t)nsys * xs);
-    bw.hb32.alloc(c->alloc, (size_t)nsys * P1 * 2 * b);
+    bw.hb32.alloc(c->alloc, nsb * P1 * 2 * b);
   } else {
+    if (bw.P > 1) {
+      bw.Vsp.alloc(c->alloc, (size_t)nf * b * ns);
+      bw.Wsp.alloc(c->alloc, (size_t)nf * b * ns);
+      bw.R.alloc(c->alloc, (size_t)nf * P1 * 6 * b * b);
+    }
     bw.scr.alloc(c->alloc, (size_t)nsys * xs);
-    bw.hb.alloc(c->alloc, (size_t)nsys * P1 * 2 * b);
+    bw.hb.alloc(c->alloc, nsb * P1 * 2 * b);
   }
 }
 
+// the three (mode 1) or four (mode 0) stages of one partitioned solve
 template <class C>
-static void spike_stages(xrl_ctx* c, const BandWork& bw, int nsys, int nper, int mode, const cplx* zs,
-                         const double* wp, const C* fac, const C* facT, const C* Vsp, const C* Wsp, const C* Einv,
-                         C* xb, size_t xs, C* hb, const cplx* v, cplx* z, const int* active, cudaStream_t s) {
+static int spike_stages(xrl_ctx* c, const BandWork& bw, int nsys, int nper, int mode, const cplx* zs,
+                        const double* wp, const C* fac, const C* facT, const C* Vsp, const C* Wsp, const C* R, C* xb,
+                        size_t xs, C* hb, const cplx* v, cplx* z, const int* active, cudaStream_t s) {
   const Topo& T = c->topo;
   const int n = T.n_band, b = T.band, ng = T.n_border, P = bw.P, m = bw.m;
+  const int nchunk = (n + kSpikeRows - 1) / kSpikeRows;
   const bool pair = mode == 0 && b <= 15 && nper % 2 == 0 && nsys % 2 == 0;
   const int ch = band_chunk(b);
+  int launches = 0;
   const size_t ys = pair ? sizeof(C) * ((size_t)2 * ch * band_rs<C>(b) + 4 * (size_t)ch) : band_smem_bytes<C>(b);
   if (ys > 48 * 1024)
     XRL_CUDA(cudaFuncSetAttribute(k_spike_y<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys));
   k_spike_y<C><<<dim3(pair ? nsys / 2 : nsys, P), 32, ys, s>>>(n, b, P, m, nper, pair ? 1 : 0, mode, T.n_loops, ng,
                                                               T.n_mat, c->d.band_perm.p, c->d.border_vg.p, zs, wp, fac,
                                                               facT, v, xb, xs, active);
-  if (P > 1) k_spike_z<C><<<nsys, 32, 0, s>>>(n, b, P, m, nper, Vsp, Wsp, Einv, xb, xs, hb, active);
-  const size_t hs = sizeof(C) * (size_t)std::max(1, P - 1) * 2 * b;
-  if (mode == 0 || P > 1)
-    k_spike_x<C><<<nsys, 256, hs, s>>>(n, b, P, m, nper, mode, T.n_loops, ng, T.n_mat, c->d.band_perm.p,
-                                       c->d.border_vg.p, zs, wp, Vsp, Wsp, hb, xb, xs, bw.Wb.p, bw.Sinv.p, v, z,
-                                       active);
+  ++launches;
+  if (P > 1) {
+    const size_t zsm = sizeof(C) * 2 * (size_t)6 * b * b;
+    if (zsm > 48 * 1024)
+      XRL_CUDA(cudaFuncSetAttribute(k_spike_z<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm));
+    k_spike_z<C><<<nsys, 32, zsm, s>>>(n, b, P, m, nper, R, xb, xs, hb, active);
+    ++launches;
+  }
+  if (P > 1 || (mode == 0 && ng > 0)) {
+    const size_t hs = sizeof(C) * (size_t)std::max(1, P - 1) * 2 * b;
+    k_spike_x<C><<<dim3(nsys, nchunk), 256, hs, s>>>(n, (int)spike_stride(n), b, P, m, nper, mode, ng, T.n_mat,
+                                                     c->d.border_vg.p, zs, wp, Vsp, Wsp, hb, xb, xs, bw.part.p,
+                                                     active);
+    ++launches;
+  }
+  if (mode == 0) {
+    k_spike_out<C><<<dim3(nsys, nchunk), 256, 0, s>>>(n, nper, T.n_loops, ng, nchunk, c->d.band_perm.p, xb, xs,
+                                                      bw.part.p, bw.Wb.p, bw.Sinv.p, v, z, active);
+    ++launches;
+  }
   XRL_CUDA(cudaGetLastError());
+  return launches;
+}
+
+__global__ void k_wb_to_f64(size_t n, size_t xs, size_t tot, const float2* __restrict__ a, cplx* __restrict__ o) {
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= tot) return;
+  const size_t q = e / n, i = e % n;
+  const float2 v = a[q * xs + i];
+  o[e] = make_double2(v.x, v.y);
+}
+
+template <class C>
+static int spike_factor(xrl_ctx* c, BandWork& bw, const cplx* zs, const double* wp, const C* fac, const C* facT,
+                        C* Vsp, C* Wsp, C* R, cudaStream_t s) {
+  const Topo& T = c->topo;
+  const int n = T.n_band, b = T.band, nf = bw.nf, P = bw.P, m = bw.m;
+  const size_t ns = spike_stride(n);
+  const size_t bsd = band_smem_bytes<C>(b);
+  if (bsd > 48 * 1024)
+    XRL_CUDA(cudaFuncSetAttribute(k_spike_cols<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsd));
+  k_spike_cols<C><<<nf * P * 2 * b, 32, bsd, s>>>(n, (int)ns, b, P, m, T.n_mat, c->d.band_val.p, zs, wp, fac,
+                                                  facT, Vsp, Wsp);
+  const size_t rsm = sizeof(C) * ((size_t)4 * b * b + 2 * (size_t)b * b + 2 * b + 1) + sizeof(int) * 2 * b;
+  if (rsm > 48 * 1024)
+    XRL_CUDA(cudaFuncSetAttribute(k_spike_reduce<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+  k_spike_reduce<C><<<nf, 256, rsm, s>>>((int)ns, b, P, m, Vsp, Wsp, R);
+  return 2;
 }
 
 // factor Q(f) for bw.nf frequencies (zs [nf][nmat], wp [nf])
@@ -890,35 +1007,27 @@ void band_factor(xrl_ctx* c, BandWork& bw, const cplx* zs, const double* wp, cud
                                                                 bw.facT32.p);
     ++launches;
   }
-  if (P > 1) {
-    const size_t bsd = band_smem_bytes<cplx>(b);
-    if (bsd > 48 * 1024)
-      XRL_CUDA(cudaFuncSetAttribute(k_spike_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsd));
-    k_spike_cols<<<nf * P * 2 * b, 32, bsd, s>>>(n, b, P, m, T.n_mat, c->d.band_val.p, zs, wp, bw.fac.p, bw.facT.p,
-                                                 bw.Vsp.p, bw.Wsp.p);
-    const size_t rsm = sizeof(cplx) * ((size_t)4 * b * b + 2 * (size_t)b * b + 2 * b) + sizeof(int) * 2 * b;
-    if (rsm > 48 * 1024)
-      XRL_CUDA(cudaFuncSetAttribute(k_spike_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
-    k_spike_reduce<<<nf, 256, rsm, s>>>(n, b, P, m, bw.Vsp.p, bw.Wsp.p, bw.Einv.p);
-    launches += 2;
-    if (bw.mixed) {
-      auto cast = [&](const DBuf<cplx>& a, DBuf<float2>& o) {
-        size_t e = 2 * a.n;
-        k_to_f32<<<(unsigned)((e + 255) / 256), 256, 0, s>>>(e, reinterpret_cast<const double*>(a.p),
-                                                                   reinterpret_cast<float*>(o.p));
-      };
-      cast(bw.Vsp, bw.Vsp32);
-      cast(bw.Wsp, bw.Wsp32);
-      cast(bw.Einv, bw.Einv32);
-      launches += 3;
-    }
-  }
+  // spikes and the reduced system: FP32 from the FP32 factor copies when the
+  // solves run in FP32 (the preconditioner only needs to be close to Q^-1)
+  if (P > 1)
+    launches += bw.mixed ? spike_factor<float2>(c, bw, zs, wp, bw.fac32.p, bw.facT32.p, bw.Vsp32.p, bw.Wsp32.p,
+                                                bw.R32.p, s)
+                         : spike_factor<cplx>(c, bw, zs, wp, bw.fac.p, bw.facT.p, bw.Vsp.p, bw.Wsp.p, bw.R.p, s);
   if (ng > 0) {
-    // W_b = Q_vv^-1 Q_vg in FP64, in place in Wb (one "system" per (f, g))
-    spike_stages<cplx>(c, bw, nf * ng, ng, 1, zs, wp, bw.fac.p, bw.facT.p, bw.Vsp.p, bw.Wsp.p, bw.Einv.p, bw.Wb.p,
-                       (size_t)n, bw.hbB.p, nullptr, nullptr, nullptr, s);
+    // W_b = Q_vv^-1 Q_vg, one "system" per (f, g)
+    if (bw.mixed) {
+      const size_t xs = (size_t)((n + 2) & ~1);
+      launches += spike_stages<float2>(c, bw, nf * ng, ng, 1, zs, wp, bw.fac32.p, bw.facT32.p, bw.Vsp32.p,
+                                       bw.Wsp32.p, bw.R32.p, bw.Wb32.p, xs, bw.hb32.p, nullptr, nullptr, nullptr, s);
+      const size_t tot = (size_t)nf * ng * n;
+      k_wb_to_f64<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>((size_t)n, xs, tot, bw.Wb32.p, bw.Wb.p);
+      ++launches;
+    } else {
+      launches += spike_stages<cplx>(c, bw, nf * ng, ng, 1, zs, wp, bw.fac.p, bw.facT.p, bw.Vsp.p, bw.Wsp.p,
+                                     bw.R.p, bw.Wb.p, (size_t)n, bw.hb.p, nullptr, nullptr, nullptr, s);
+    }
     k_schur<<<nf, 32, 0, s>>>(n, ng, T.n_mat, c->d.border_vg.p, c->d.border_gg.p, zs, wp, bw.Wb.p, bw.Sinv.p);
-    launches += 4;
+    ++launches;
   }
   prof_end(c, s, ev, PH_PREC, launches, 8.0 * nf * (double)n * b * b / 2.0, 16.0 * nf * (double)n * (b + 1) * 2.0);
   XRL_CUDA(cudaGetLastError());
@@ -930,14 +1039,15 @@ void band_apply(xrl_ctx* c, BandWork& bw, int nsys, int nport, const cplx* zs, c
   const Topo& T = c->topo;
   cudaEvent_t ev = prof_begin(c, s);
   const size_t xs = (size_t)((T.n_band + 2) & ~1);
+  int launches;
   if (bw.mixed)
-    spike_stages<float2>(c, bw, nsys, nport, 0, zs, wp, bw.fac32.p, bw.facT32.p, bw.Vsp32.p, bw.Wsp32.p,
-                         bw.Einv32.p, bw.scr32.p, xs, bw.hb32.p, v, z, active, s);
+    launches = spike_stages<float2>(c, bw, nsys, nport, 0, zs, wp, bw.fac32.p, bw.facT32.p, bw.Vsp32.p, bw.Wsp32.p,
+                                    bw.R32.p, bw.scr32.p, xs, bw.hb32.p, v, z, active, s);
   else
-    spike_stages<cplx>(c, bw, nsys, nport, 0, zs, wp, bw.fac.p, bw.facT.p, bw.Vsp.p, bw.Wsp.p, bw.Einv.p,
-                       bw.scr.p, xs, bw.hb.p, v, z, active, s);
+    launches = spike_stages<cplx>(c, bw, nsys, nport, 0, zs, wp, bw.fac.p, bw.facT.p, bw.Vsp.p, bw.Wsp.p, bw.R.p,
+                                  bw.scr.p, xs, bw.hb.p, v, z, active, s);
   const double es = bw.mixed ? 8.0 : 16.0;
-  prof_end(c, s, ev, PH_PREC, bw.P > 1 ? 3 : 2, 16.0 * nsys * (double)T.n_band * T.band * (bw.P > 1 ? 3 : 1),
+  prof_end(c, s, ev, PH_PREC, launches, 16.0 * nsys * (double)T.n_band * T.band * (bw.P > 1 ? 3 : 1),
            es * nsys * (double)T.n_band * (2.0 * T.band + 4.0));
 }
 

@@ -91,7 +91,8 @@ __global__ void k_gather(int N, int nsys, int nloop, const int32_t* __restrict__
   }
 }
 
-// Vb[s][b] = sum_side rho . (j w' Y + Z_s/A X) at the branch's panels
+// Vb[b][s] = sum_side rho . (j w' Y + Z_s/A X) at the branch's panels
+// (branch-major, systems fastest: coalesced X, Y reads and Vb writes)
 template <class T>
 __global__ void k_scatter(int B, int nsys, int nmat, const int32_t* __restrict__ br_pan,
                           const double* __restrict__ br_rho, const int32_t* __restrict__ pan_mat,
@@ -100,7 +101,7 @@ __global__ void k_scatter(int B, int nsys, int nmat, const int32_t* __restrict__
                           const T* __restrict__ Y, cplx* __restrict__ Vb) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)B * nsys) return;
-  int s = (int)(idx / B), b = (int)(idx % B);
+  int b = (int)(idx / nsys), s = (int)(idx % nsys);
   cplx acc = make_double2(0, 0);
   for (int side = 0; side < 2; ++side) {
     int r = br_pan[2 * b + side];
@@ -119,21 +120,28 @@ __global__ void k_scatter(int B, int nsys, int nmat, const int32_t* __restrict__
   Vb[idx] = acc;
 }
 
-// w[s][l] = sum_b M(l, b) Vb[s][b]   (port branches carry no impedance: their Vb is zero)
-__global__ void k_loop_reduce(int nloop, int nsys, int B, int ncb, const int32_t* __restrict__ m_ptr,
+// w[s][l] = sum_b M(l, b) Vb[b][s]   (port branches carry no impedance: their Vb is zero)
+// One warp per (loop, 32 systems): the row walk is warp-uniform and the Vb
+// reads are contiguous over the systems.
+__global__ void k_loop_reduce(int nloop, int nsys, int ncb, const int32_t* __restrict__ m_ptr,
                               const int32_t* __restrict__ m_col, const int8_t* __restrict__ m_val,
                               const cplx* __restrict__ Vb, cplx* __restrict__ w) {
-  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (size_t)nloop * nsys) return;
-  int s = (int)(idx / nloop), l = (int)(idx % nloop);
+  const size_t wid = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int sg = (nsys + 31) >> 5;
+  if (wid >= (size_t)nloop * sg) return;
+  const int l = (int)(wid / sg);
+  const int s = (int)(wid % sg) * 32 + lane;
+  if (s >= nsys) return;
   cplx acc = make_double2(0, 0);
-  const cplx* vb = Vb + (size_t)s * B;
-  for (int q = m_ptr[l]; q < m_ptr[l + 1]; ++q) {
-    int b = m_col[q];
+  const int q1 = m_ptr[l + 1];
+  for (int q = m_ptr[l]; q < q1; ++q) {
+    const int b = m_col[q];
     if (b >= ncb) continue;
-    acc = m_val[q] > 0 ? cadd(acc, vb[b]) : csub(acc, vb[b]);
+    const cplx v = Vb[(size_t)b * nsys + s];
+    acc = m_val[q] > 0 ? cadd(acc, v) : csub(acc, v);
   }
-  w[idx] = acc;
+  w[(size_t)s * nloop + l] = acc;
 }
 
 // w = Q(f_s) v (mode 0) or diag(Q(f_s)) (mode 1, v unused)
@@ -595,8 +603,8 @@ static void apply_A_t(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, T*
   k_scatter<T><<<nblk((size_t)T_.n_cb * nsys), 256, 0, s>>>(T_.n_cb, nsys, T_.n_mat, c->d.br_pan.p, c->d.br_rho.p,
                                                             c->d.pan_mat.p, c->d.area.p, wk.zs.p, wk.wp.p, X, Y,
                                                             wk.Vb.p);
-  k_loop_reduce<<<nblk((size_t)T_.n_loops * nsys), 256, 0, s>>>(T_.n_loops, nsys, T_.n_cb, T_.n_cb, c->d.m_ptr.p,
-                                                                c->d.m_col.p, c->d.m_val.p, wk.Vb.p, w);
+  k_loop_reduce<<<nblk((size_t)T_.n_loops * ((nsys + 31) / 32) * 32), 256, 0, s>>>(
+      T_.n_loops, nsys, T_.n_cb, c->d.m_ptr.p, c->d.m_col.p, c->d.m_val.p, wk.Vb.p, w);
   prof_end(c, s, ev, PH_OPER, 2, nsys * (2.0 * T_.n_cb * 30.0 + 2.0 * nnzm),
            nsys * (T_.n_cb * (2.0 * 12.0 * sizeof(T) + 16.0) + 16.0 * nnzm + 16.0 * T_.n_loops));
   XRL_CUDA(cudaGetLastError());
@@ -752,8 +760,9 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
     k_scatter<double><<<nblk((size_t)TT.n_cb * nsys), 256, 0, s>>>(TT.n_cb, nsys, TT.n_mat, c->d.br_pan.p,
                                                                    c->d.br_rho.p, c->d.pan_mat.p, c->d.area.p, zs1.p,
                                                                    wp0.p, wk.X.p, wk.X.p, wk.Vb.p);
-    k_loop_reduce<<<nblk(tot), 256, 0, s>>>(n, nsys, TT.n_cb, TT.n_cb, c->d.m_ptr.p, c->d.m_col.p, c->d.m_val.p,
-                                            wk.Vb.p, wk.w.p);
+    k_loop_reduce<<<nblk((size_t)n * ((nsys + 31) / 32) * 32), 256, 0, s>>>(n, nsys, TT.n_cb, c->d.m_ptr.p,
+                                                                           c->d.m_col.p, c->d.m_val.p, wk.Vb.p,
+                                                                           wk.w.p);
     BandWork pw;
     band_alloc(c, pw, 1, nsys, false);
     band_factor(c, pw, zs1.p, wp0.p, s);

@@ -331,8 +331,8 @@ void band_prepare(xrl_ctx* c);
 struct BandWork {
   int nf = 0, P = 1, m = 0;
   bool mixed = false;
-  DBuf<double2> fac, facT, Wb, Sinv, Vsp, Wsp, Einv, hbB, scr, hb;
-  DBuf<float2> fac32, facT32, Vsp32, Wsp32, Einv32, scr32, hb32;
+  DBuf<double2> fac, facT, Wb, Sinv, Vsp, Wsp, R, scr, hb, part;
+  DBuf<float2> fac32, facT32, Vsp32, Wsp32, R32, scr32, hb32, Wb32;
 };
 void band_alloc(xrl_ctx* c, BandWork& bw, int nf, int nsys, bool mixed);
 void band_factor(xrl_ctx* c, BandWork& bw, const double2* zs, const double* wp, cudaStream_t s);
