@@ -204,7 +204,9 @@ xrl_status xrl_solve(xrl_ctx* ctx, int32_t n_freq, const double* freq_hz, double
 
 /* Loop-space operator for parity checks: w_s = Z(f_s) v_s for n_sys systems,
  * Z(f) = M [sum_t A_t (diag(Z_s(f)/A) + j omega mu0/4pi P) A_t^T] M^T (eq. 8),
- * with P applied by the FMM.  Host buffers: freq [n_sys]; v, w
+ * with P applied by the FMM in FP64 accuracy, computed as the solver's
+ * residuals compute it (opt.precision = 1: double-float arithmetic on the
+ * FP32 pipes for n_sys >= 6).  Host buffers: freq [n_sys]; v, w
  * [n_sys][n_loops] complex as interleaved (re, im) doubles. */
 xrl_status xrl_apply_operator(xrl_ctx* ctx, int32_t n_sys, const double* freq, const double* v,
                               double* w);

@@ -175,6 +175,92 @@ __global__ void __launch_bounds__(128) k_p2p_tiled(int nc, const int32_t* __rest
   }
 }
 
+// (hi, lo) = (fl32(x), fl32(x - hi)): the double-float split of FP64 values
+__global__ void k_split_df(size_t n, const double* __restrict__ a, float2* __restrict__ o) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = a[i];
+  const float hi = __double2float_rn(x);
+  o[i] = make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
+// Near field in FP64 accuracy on the FP32 pipes: the tiling of k_p2p_tiled
+// with double-float operands (near values and X pre-split into (hi, lo)),
+// exact products by FMA and accumulation as unevaluated float pairs with
+// TwoSum (Knuth), ~2^-44 relative rounding per step.
+__global__ void __launch_bounds__(128) k_p2p_df64(int nc, const int32_t* __restrict__ leaf_first,
+                                                  const int32_t* __restrict__ leaf_count,
+                                                  const int64_t* __restrict__ near_off,
+                                                  const int32_t* __restrict__ near_w,
+                                                  const int64_t* __restrict__ col_off,
+                                                  const int32_t* __restrict__ near_src, const float2* __restrict__ val,
+                                                  const float2* __restrict__ X, double* __restrict__ Y) {
+  constexpr int CT = 64, KC = 16, RB = 64;
+  __shared__ __align__(16) float2 Vs[KC][RB + 2];
+  __shared__ __align__(16) float2 Xs[KC][CT];
+  const int B = blockIdx.x;
+  const int c0 = blockIdx.y * CT;
+  const int rb0 = blockIdx.z * RB;
+  const int nB = leaf_count[B], f0 = leaf_first[B], w = near_w[B];
+  if (rb0 >= nB) return;
+  const int nr = min(RB, nB - rb0);
+  const float2* vb = val + near_off[B] + (size_t)rb0 * w;
+  const int32_t* src = near_src + col_off[B];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  float sh[4][8], sl[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sh[i][j] = sl[i][j] = 0.f;
+  for (int k0 = 0; k0 < w; k0 += KC) {
+    const int kn = min(KC, w - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < KC * RB; e += 128) {
+      int r = e / KC, kk = e % KC;
+      Vs[kk][r] = (r < nr && kk < kn) ? vb[(size_t)r * w + k0 + kk] : make_float2(0.f, 0.f);
+    }
+    for (int e = threadIdx.x; e < KC * CT; e += 128) {
+      int kk = e / CT, cc = e % CT;
+      Xs[kk][cc] = (kk < kn && c0 + cc < nc) ? X[(size_t)src[k0 + kk] * nc + c0 + cc] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int kk = 0; kk < KC; ++kk) {
+      float2 x[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        x[q] = Xs[kk][4 * tx + q];
+        x[4 + q] = Xs[kk][32 + 4 * tx + q];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float2 v = Vs[kk][ty + 16 * i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float p = v.x * x[q].x;
+          const float pe = fmaf(v.x, x[q].x, -p);                 // exact product error
+          const float cr = fmaf(v.x, x[q].y, v.y * x[q].x);       // cross terms
+          const float t = sh[i][q] + p;                           // TwoSum(sh, p)
+          const float bp = t - sh[i][q];
+          const float e = (sh[i][q] - (t - bp)) + (p - bp);
+          sl[i][q] += e + pe + cr;
+          sh[i][q] = t;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int r = ty + 16 * i;
+    if (r >= nr) continue;
+    double* yr = Y + (size_t)(f0 + rb0 + r) * nc + c0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int cc = (j < 4) ? 4 * tx + j : 32 + 4 * tx + (j - 4);
+      if (c0 + cc < nc) yr[cc] = (double)sh[i][j] + (double)sl[i][j];
+    }
+  }
+}
+
 // ---- expansions ----------------------------------------------------------------------------
 // P2M: M[box][k][c] = sum_i S[i][k] X[i][c]
 template <class T>
@@ -593,6 +679,20 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     k_p2p_tiled<<<gt, 128, 0, s>>>(nc, c->d.leaf_first.p, c->d.leaf_count.p, c->d.near_off.p, c->d.near_w.p,
                                    c->d.near_col_off.p, c->d.near_src.p, (const float*)near, (const float*)X,
                                    (float*)Y);
+  } else if (sizeof(T) == 8 && c->df64_m2l && nc >= 32) {
+    if (c->d.near_hl.n == 0) {
+      c->d.near_hl.alloc(c->alloc, c->d.near_val.n);
+      k_split_df<<<(unsigned)((c->d.near_val.n + 255) / 256), 256, 0, s>>>(c->d.near_val.n, c->d.near_val.p,
+                                                                         c->d.near_hl.p);
+      count_launch(c);
+    }
+    const size_t nx = (size_t)c->N * nc;
+    c->d.x_hl.ensure(c->alloc, nx);
+    k_split_df<<<(unsigned)((nx + 255) / 256), 256, 0, s>>>(nx, (const double*)X, c->d.x_hl.p);
+    dim3 gt(nl, (nc + 63) / 64, (c->max_leaf + 63) / 64);
+    k_p2p_df64<<<gt, 128, 0, s>>>(nc, c->d.leaf_first.p, c->d.leaf_count.p, c->d.near_off.p, c->d.near_w.p,
+                                  c->d.near_col_off.p, c->d.near_src.p, c->d.near_hl.p, c->d.x_hl.p, (double*)Y);
+    count_launch(c);
   } else {
     k_p2p<T><<<gp, 128, 0, s>>>(nc, ct_p, c->d.leaf_first.p, c->d.leaf_count.p, c->d.u_ptr32.p, c->d.u_src.p,
                                 c->d.near_off.p, c->d.near_w.p, near, X, Y);

@@ -931,6 +931,14 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
 void apply_operator_host(xrl_ctx* c, int nsys, const double* freq, const double* v, double* w, int mode) {
   const Topo& T = c->topo;
   const size_t tot = (size_t)T.n_loops * nsys;
+  // the operator of the solver's FP64 residuals: double-float on the FP32
+  // pipes in the mixed mode, as inside run_solve
+  struct Df64Guard {
+    xrl_ctx* c;
+    bool old;
+    ~Df64Guard() { c->df64_m2l = old; }
+  } df64_guard{c, c->df64_m2l};
+  c->df64_m2l = c->opt.precision == 1;
   Work wk;
   // one port per "system": each system is its own frequency here
   sys_consts(c, wk, nsys, 1, nsys, freq);

@@ -183,6 +183,8 @@ struct Dev {
   DBuf<int32_t> near_w;                              // per leaf: block width
   DBuf<double> near_val;                             // values
   DBuf<float> near_val32;                            // FP32 copy (mixed precision)
+  DBuf<float2> near_hl;                              // double-float (hi, lo) split, made on first use
+  DBuf<float2> x_hl;                                 // double-float split of an FP64 product's input
   DBuf<int64_t> near_col_off;                         // per leaf: offset into near_src
   DBuf<int32_t> near_src;                             // per leaf: Morton index of each near column
   DBuf<double> mom;                                  // [N][ncoef] P2M moments (leaf-scaled)

@@ -30,6 +30,11 @@ def bar_ctx(lib, bar_mesh):
 
 
 @pytest.fixture(scope="module")
+def coils_mesh_s():
+    return meshgen.coils()
+
+
+@pytest.fixture(scope="module")
 def bar_circ(bar_mesh):
     return circuit.Circuit(bar_mesh)
 
@@ -84,6 +89,27 @@ def test_operator_matches_oracle(bar_ctx, bar_circ, bar_dense_P, f):
     ref = (M @ Ze @ M.T @ v.T).T
     err = np.linalg.norm(w - ref) / np.linalg.norm(ref)
     assert err < 1e-6, err
+
+
+def test_double_float_operator_matches_fp64(lib, coils_mesh_s):
+    """The mixed mode's FP64 residual operator (double-float near field and
+    translations on the FP32 pipes) against the plain FP64 kernels on the
+    coils at 8 systems (48 columns): both evaluate the same FMM, so they agree
+    to rounding (~2^-44 per operation, far below the order-8 truncation)."""
+    rng = np.random.default_rng(13)
+    a = lib.XRL.from_mesh(coils_mesh_s, precision=0)
+    b = lib.XRL.from_mesh(coils_mesh_s, precision=1)
+    try:
+        n = a.stats()["n_loops"]
+        v = rng.standard_normal((8, n)) + 1j * rng.standard_normal((8, n))
+        f = np.geomspace(1e3, 1e9, 8)
+        w0 = a.apply_operator(f, v)
+        w1 = b.apply_operator(f, v)
+    finally:
+        a.close()
+        b.close()
+    err = np.linalg.norm(w1 - w0, axis=1) / np.linalg.norm(w0, axis=1)
+    assert err.max() < 1e-11, err.max()
 
 
 def test_precond_matrix_matches_oracle(bar_ctx, bar_circ, bar_dense_P):
