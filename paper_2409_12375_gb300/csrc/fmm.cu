@@ -728,6 +728,9 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     if (sizeof(T) == 4 && tc_usable(c, nc)) {
       tc_m2l(c, nbx, b0, nc, (const float*)Mx, (float*)Lx, s);
       nl_m2l = 2;
+    } else if (sizeof(T) == 8 && c->df64_m2l && tc64_usable(c, nc)) {
+      tc_m2l64(c, nbx, b0, nc, (const double*)Mx, (double*)Lx, s);
+      nl_m2l = 2;
     } else if (tiled) {
       launch_xlate<T>(nbx, b0, nc, ncoef, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p, tm2l, Mx, Lx, false, s);
     } else {

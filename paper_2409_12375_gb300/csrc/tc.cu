@@ -28,6 +28,9 @@
 // frees its tensor memory.
 #include <cuda_bf16.h>
 
+#include <cmath>
+#include <vector>
+
 #include "xrl_internal.hpp"
 
 namespace xrl {
@@ -51,6 +54,19 @@ __host__ __device__ inline size_t tc_img_off(int R, int Kp, int r, int k, int h)
   return (size_t)tc_chunk_bytes(R, 32) * c + (size_t)h * R * kc * 2 + ((size_t)(r >> 3) * (kc >> 3) + kq) * 128 +
          (r & 7) * 16 + (k & 7) * 2;
 }
+
+// the same layout with `pc` pieces per chunk
+__host__ __device__ inline int oz_chunk_bytes(int R, int kc, int pc) { return pc * R * kc * 2; }
+__host__ __device__ inline size_t oz_img_off(int R, int Kp, int r, int k, int h, int pc) {
+  const int c = k >> 5;
+  const int kc = (Kp - 32 * c) < 32 ? (Kp - 32 * c) : 32;
+  const int kq = (k & 31) >> 3;
+  return (size_t)oz_chunk_bytes(R, 32, pc) * c + (size_t)h * R * kc * 2 + ((size_t)(r >> 3) * (kc >> 3) + kq) * 128 +
+         (r & 7) * 16 + (k & 7) * 2;
+}
+
+constexpr int OZ_S = 5;          // integer slices of 7 bits
+constexpr int OZ_STAGES = 3;
 
 __device__ __forceinline__ uint32_t sm_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -370,6 +386,295 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc(TcArgs a) {
   }
 }
 
+// ---- FP64-accurate translation (Ozaki-style integer slices) ------------------------------
+// For the FP64 refinement residuals: each row of A (one column c of the
+// source multipoles, scale 2^eA = the power of two above max_k |M[k][c]|) and
+// each column of B (one output n of the table, 2^fB likewise) is cut into
+// OZ_S integer slices, x 2^-e = sum_i a_i 2^-7(i+1), |a_i| <= 128, stored in
+// BF16 as a_i 2^(e-7) (exact: 8 significant bits).  A product of two slices is
+// then a_i b_j 2^(eA+fB-14), and every sum over k and over the slice pairs of
+// one class s = i + j is an integer multiple of that power of two below
+// 5 * 81 * 2^14 < 2^24: the tensor core's FP32 accumulation is exact whatever
+// its rounding.  The classes s <= OZ_S - 1 (15 products) accumulate in five
+// TMEM accumulators; after every V-list pair the epilogue forms
+// sum_s 2^-7s D_s and adds it into double-float registers.  Truncation
+// (dropped slices and products) ~2^-35 of max|M| max|T| per row and column.
+// The solid-harmonic coefficients span many octaves across the order k, so
+// both operands are first equilibrated exactly by powers of two,
+// M'[k] = 2^-d_k M[k], T'[k] = 2^d_k T[k] (T'^T M' = T^T M), with 2^d_k the
+// size of the largest panel moment of index k.
+
+// Pack FP64 expansions in[box][k][col] into the OZ_S-slice A image.  One CTA
+// per (box, column tile); first the row scales, then the slices.
+__global__ void k_oz_pack_a(int nc, int ncoef, int Kp, int b0, const int32_t* __restrict__ dk,
+                            const double* __restrict__ in, uint16_t* __restrict__ img) {
+  __shared__ int eA[TC_ROWS];
+  const int ct = blockIdx.y;
+  const double* src = in + (size_t)(b0 + blockIdx.x) * ncoef * nc + (size_t)ct * TC_ROWS;
+  char* dst = reinterpret_cast<char*>(img) + ((size_t)blockIdx.x * gridDim.y + ct) * (size_t)(OZ_S * 2 * TC_ROWS * Kp);
+  for (int r = threadIdx.x; r < TC_ROWS; r += blockDim.x) {
+    double mx = 0.0;
+    if (ct * TC_ROWS + r < nc)
+      for (int k = 0; k < ncoef; ++k) mx = fmax(mx, fabs(ldexp(src[(size_t)k * nc + r], -dk[k])));
+    eA[r] = mx > 0.0 ? ilogb(mx) + 1 : 0;
+  }
+  __syncthreads();
+  const int nq = Kp >> 3;
+  for (int e = threadIdx.x; e < TC_ROWS * nq; e += blockDim.x) {
+    const int r = e & (TC_ROWS - 1), kq = e >> 7;
+    const bool col_ok = ct * TC_ROWS + r < nc;
+    const int ea = eA[r];
+    uint16_t sl[OZ_S][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = 8 * kq + q;
+      double x = (col_ok && k < ncoef) ? ldexp(src[(size_t)k * nc + r], -ea - dk[k]) : 0.0;
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i) {
+        const double a = rint(x * 128.0);
+        x = x * 128.0 - a;
+        sl[i][q] = bf16_bits(ldexpf((float)a, ea - 7));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < OZ_S; ++i) {
+      uint4 v;
+      v.x = sl[i][0] | (uint32_t)sl[i][1] << 16;
+      v.y = sl[i][2] | (uint32_t)sl[i][3] << 16;
+      v.z = sl[i][4] | (uint32_t)sl[i][5] << 16;
+      v.w = sl[i][6] | (uint32_t)sl[i][7] << 16;
+      *reinterpret_cast<uint4*>(dst + oz_img_off(TC_ROWS, Kp, r, 8 * kq, i, OZ_S)) = v;
+    }
+  }
+}
+
+// Pack FP64 tables T[o][k_in][n_out] into OZ_S-slice B images (Np rows n by Kp).
+__global__ void k_oz_pack_b(int ncoef, int Kp, int Np, const int32_t* __restrict__ dk, const double* __restrict__ T,
+                            uint16_t* __restrict__ img) {
+  __shared__ int fB[128];
+  const int o = blockIdx.x;
+  const double* tm = T + (size_t)o * ncoef * ncoef;
+  char* dst = reinterpret_cast<char*>(img) + (size_t)o * (size_t)(OZ_S * 2 * Np * Kp);
+  for (int r = threadIdx.x; r < Np; r += blockDim.x) {
+    double mx = 0.0;
+    if (r < ncoef)
+      for (int k = 0; k < ncoef; ++k) mx = fmax(mx, fabs(ldexp(tm[(size_t)k * ncoef + r], dk[k])));
+    fB[r] = mx > 0.0 ? ilogb(mx) + 1 : 0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < Np * Kp; e += blockDim.x) {
+    const int r = e % Np, k = e / Np;
+    const int fb = fB[r];
+    double x = (r < ncoef && k < ncoef) ? ldexp(tm[(size_t)k * ncoef + r], dk[k] - fb) : 0.0;
+    for (int i = 0; i < OZ_S; ++i) {
+      const double a = rint(x * 128.0);
+      x = x * 128.0 - a;
+      *reinterpret_cast<uint16_t*>(dst + oz_img_off(Np, Kp, r, k, i, OZ_S)) = bf16_bits(ldexpf((float)a, fb - 7));
+    }
+  }
+}
+
+struct OzArgs {
+  int nc, ncoef, Kp, b0, src0, nct;
+  const int32_t* ptr;
+  const int32_t* src;
+  const int16_t* off;
+  const char* aimg;
+  const char* bimg;
+  double* out;
+  int32_t* err;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Warps: 0 = bulk copies (lane 0; the whole warp owns TMEM), 1 = MMA issuer
+// (lane 0), 2..9 = epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and
+// outputs n in [48 h, 48 h + 48), h = (w - 2) / 4.  TMEM: class s at columns
+// 96 s (N = 96).  One accumulator set: the MMAs of pair j+1 start once every
+// epilogue warp has loaded pair j (tfree).
+__global__ void __launch_bounds__(320, 1) k_xlate_oz(OzArgs a) {
+  constexpr int NP = 96;
+  extern __shared__ uint8_t oz_smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(oz_smem_raw) + 1023) & ~uintptr_t(1023));
+  const int a_stage = oz_chunk_bytes(TC_ROWS, TC_KC, OZ_S);
+  const int stage_bytes = a_stage + oz_chunk_bytes(NP, TC_KC, OZ_S);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + OZ_STAGES * stage_bytes);
+  uint64_t* empty = full + OZ_STAGES;
+  uint64_t* tfull = empty + OZ_STAGES;
+  uint64_t* tfree = tfull + 1;
+  uint64_t* mdone = tfree + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
+  int* bad = reinterpret_cast<int*>(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int Bx = a.b0 + blockIdx.x, ct = blockIdx.y;
+  const int vs = a.ptr[Bx], ve = a.ptr[Bx + 1];
+  const int nv = ve - vs;
+  const int nch = (a.Kp + TC_KC - 1) / TC_KC;
+  const int items = nv * nch;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tfree, 8);
+    mbar_init(mdone, 1);
+    *bad = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_u32(tslot)), "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  int issued = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int it = 0; it < items; ++it) {
+        const int st = it % OZ_STAGES, u = it / OZ_STAGES;
+        if (u > 0 && !mbar_wait(&empty[st], (u - 1) & 1)) {
+          atomicExch(bad, 1);
+          break;
+        }
+        const int v = vs + it / nch, c = it % nch;
+        const int kc = min(TC_KC, a.Kp - TC_KC * c);
+        const char* asrc = a.aimg +
+                           ((size_t)(a.src[v] - a.src0) * a.nct + ct) * (size_t)(OZ_S * 2 * TC_ROWS * a.Kp) +
+                           (size_t)a_stage * c;
+        const char* bsrc = a.bimg + (size_t)a.off[v] * (size_t)(OZ_S * 2 * NP * a.Kp) +
+                           (size_t)oz_chunk_bytes(NP, TC_KC, OZ_S) * c;
+        const uint32_t ab = oz_chunk_bytes(TC_ROWS, kc, OZ_S), bb = oz_chunk_bytes(NP, kc, OZ_S);
+        uint8_t* sa = base + (size_t)st * stage_bytes;
+        mbar_expect_tx(&full[st], ab + bb);
+        bulk_g2s(sa, asrc, ab, &full[st]);
+        bulk_g2s(sa + a_stage, bsrc, bb, &full[st]);
+        issued = it + 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc =
+          (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
+      for (int it = 0; it < items; ++it) {
+        const int st = it % OZ_STAGES, u = it / OZ_STAGES;
+        const int j = it / nch, c = it % nch;
+        if (c == 0 && j >= 1 && !mbar_wait(tfree, (j - 1) & 1)) {
+          atomicExch(bad, 1);
+          break;
+        }
+        if (!mbar_wait(&full[st], u & 1)) {
+          atomicExch(bad, 1);
+          break;
+        }
+        tc_fence_after();
+        const int kc = min(TC_KC, a.Kp - TC_KC * c);
+        const uint32_t sa = sm_u32(base + (size_t)st * stage_bytes);
+        const uint32_t sb = sa + a_stage;
+        const uint32_t pa = TC_ROWS * kc * 2, pb = NP * kc * 2;
+        const uint32_t sbo = 16 * kc;
+        for (int ks = 0; ks < kc / 16; ++ks) {
+          uint64_t da[OZ_S], db[OZ_S];
+#pragma unroll
+          for (int h = 0; h < OZ_S; ++h) {
+            da[h] = sdesc(sa + h * pa + 256 * ks, 128, sbo);
+            db[h] = sdesc(sb + h * pb + 256 * ks, 128, sbo);
+          }
+          const bool first = c == 0 && ks == 0;
+#pragma unroll
+          for (int sc = 0; sc < OZ_S; ++sc)
+#pragma unroll
+            for (int i = 0; i <= sc; ++i)
+              mma_bf16(tbase + 96u * sc, da[i], db[sc - i], idesc, (first && i == 0) ? 0u : 1u);
+        }
+        tc_commit(&empty[st]);
+        if (c == nch - 1) tc_commit(tfull);
+      }
+      tc_commit(mdone);
+      if (!mbar_wait(mdone, 0)) atomicExch(bad, 1);
+    }
+    __syncwarp();
+  } else {
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+    float ah[48], al[48];
+#pragma unroll
+    for (int n = 0; n < 48; ++n) ah[n] = al[n] = 0.f;
+    for (int j = 0; j < nv; ++j) {
+      bool ok = mbar_wait(tfull, j & 1);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        atomicExch(bad, 1);
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int n0 = 0; n0 < 48; n0 += 8) {
+        uint32_t r[OZ_S][8];
+#pragma unroll
+        for (int sc = 0; sc < OZ_S; ++sc)
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(r[sc][0]), "=r"(r[sc][1]), "=r"(r[sc][2]), "=r"(r[sc][3]), "=r"(r[sc][4]),
+                         "=r"(r[sc][5]), "=r"(r[sc][6]), "=r"(r[sc][7])
+                       : "r"(tbase + lane_base + 96u * sc + (uint32_t)(48 * half + n0))
+                       : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (n0 == 40) {
+          // every value of this pair is in registers: let the next pair's MMAs start
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tfree);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          // sum_s 2^-7s D_s from the smallest class up, as a float pair
+          float h = ldexpf(__uint_as_float(r[4][q]), -28), l = 0.f, e;
+          two_sum(ldexpf(__uint_as_float(r[3][q]), -21), h, h, e);
+          l += e;
+          two_sum(ldexpf(__uint_as_float(r[2][q]), -14), h, h, e);
+          l += e;
+          two_sum(ldexpf(__uint_as_float(r[1][q]), -7), h, h, e);
+          l += e;
+          two_sum(__uint_as_float(r[0][q]), h, h, e);
+          l += e;
+          two_sum(ah[n0 + q], h, ah[n0 + q], e);
+          al[n0 + q] += e + l;
+        }
+      }
+    }
+    const int col = ct * TC_ROWS + 32 * quarter + lane;
+    if (col < a.nc) {
+      double* outp = a.out + (size_t)Bx * a.ncoef * a.nc + col;
+#pragma unroll
+      for (int q = 0; q < 48; ++q) {
+        const int n = 48 * half + q;
+        if (n < a.ncoef) outp[(size_t)n * a.nc] = (double)ah[q] + (double)al[q];
+      }
+    }
+  }
+  __syncthreads();
+  if (*bad) {
+    if (threadIdx.x == 0) atomicExch(a.err, 1);
+    if (warp == 0 && lane == 0)
+      for (int it = issued > OZ_STAGES ? issued - OZ_STAGES : 0; it < issued; ++it)
+        mbar_wait(&full[it % OZ_STAGES], (it / OZ_STAGES) & 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512) : "memory");
+  }
+}
+
 // ---- host side ---------------------------------------------------------------------------
 
 static int tc_kpad(int ncoef) { return (ncoef + 15) & ~15; }
@@ -433,6 +738,58 @@ void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cud
     }
     k_xlate_tc<96><<<dim3(nbx, nct), 192, smem, s>>>(a);
   }
+}
+
+bool tc64_usable(const xrl_ctx* c, int nc) {
+  return c->opt.tensor_cores != 0 && nc >= 64 && tc_npad(c->ncoef) == 96 && c->d.tc_err.n > 0;
+}
+
+// FP64-accurate M2L of the refinement residuals (in = M, out = L, FP64)
+void tc_m2l64(xrl_ctx* c, int nbx, int b0, int nc, const double* Mx, double* Lx, cudaStream_t s) {
+  const Tree& t = c->tree;
+  const int ncoef = c->ncoef, Kp = tc_kpad(ncoef), Np = 96;
+  const int nct = (nc + TC_ROWS - 1) / TC_ROWS;
+  const int src0 = t.level_off[2];
+  const int nsrc = t.n_boxes() - src0;
+  if (c->d.oz_bimg.n == 0) {
+    // d_k from the panel moments (the P2M operator): typical size of M[k]
+    std::vector<double> mom = c->d.mom.download();
+    std::vector<int32_t> dk(ncoef, 0);
+    for (int k = 0; k < ncoef; ++k) {
+      double mx = 0.0;
+      for (size_t i = 0; i < (size_t)c->N; ++i) mx = std::max(mx, std::fabs(mom[i * ncoef + k]));
+      dk[k] = mx > 0.0 ? std::ilogb(mx) : 0;
+    }
+    c->d.oz_dk.upload(c->alloc, dk);
+    const int noff = (int)(t.m2l_offsets.size() / 3);
+    c->d.oz_bimg.alloc(c->alloc, (size_t)noff * OZ_S * Np * Kp);
+    k_oz_pack_b<<<noff, 256, 0, s>>>(ncoef, Kp, Np, c->d.oz_dk.p, c->d.t_m2l.p, c->d.oz_bimg.p);
+    count_launch(c);
+  }
+  c->d.oz_aimg.ensure(c->alloc, (size_t)nsrc * nct * OZ_S * TC_ROWS * Kp);
+  k_oz_pack_a<<<dim3(nsrc, nct), 256, 0, s>>>(nc, ncoef, Kp, src0, c->d.oz_dk.p, Mx, c->d.oz_aimg.p);
+  OzArgs a;
+  a.nc = nc;
+  a.ncoef = ncoef;
+  a.Kp = Kp;
+  a.b0 = b0;
+  a.src0 = src0;
+  a.nct = nct;
+  a.ptr = c->d.v_ptr32.p;
+  a.src = c->d.v_src.p;
+  a.off = c->d.v_off.p;
+  a.aimg = reinterpret_cast<const char*>(c->d.oz_aimg.p);
+  a.bimg = reinterpret_cast<const char*>(c->d.oz_bimg.p);
+  a.out = Lx;
+  a.err = c->d.tc_err.p;
+  const size_t smem =
+      (size_t)OZ_STAGES * (oz_chunk_bytes(TC_ROWS, TC_KC, OZ_S) + oz_chunk_bytes(Np, TC_KC, OZ_S)) + 1024 + 128;
+  static bool set = false;
+  if (!set) {
+    XRL_CUDA(cudaFuncSetAttribute(k_xlate_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    set = true;
+  }
+  k_xlate_oz<<<dim3(nbx, nct), 320, smem, s>>>(a);
 }
 
 // raises XRL_ETIMEOUT if a tensor-core kernel gave up a wait since the last check

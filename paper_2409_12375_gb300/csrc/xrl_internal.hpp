@@ -197,6 +197,9 @@ struct Dev {
   DBuf<uint16_t> tc_bimg;   // packed 3-piece BF16 images of the M2L tables (tensor-core path)
   DBuf<uint16_t> tc_aimg;   // packed 3-piece BF16 images of the FP32 multipoles, per product
   DBuf<int32_t> tc_err;     // set by a tensor-core kernel that timed out
+  DBuf<uint16_t> oz_bimg;   // integer-slice BF16 images of the M2L tables (FP64-accurate path)
+  DBuf<uint16_t> oz_aimg;   // integer-slice BF16 images of the FP64 multipoles, per product
+  DBuf<int32_t> oz_dk;      // power-of-two equilibration exponents per coefficient index
   DBuf<int32_t> v_ptr32, v_src;
   DBuf<int16_t> v_off;
   DBuf<int32_t> lvl_boxes;                            // per level: global ids of its boxes (same as range)
@@ -317,6 +320,8 @@ bool tc_usable(const xrl_ctx* c, int ncols);
 void tc_prepare(xrl_ctx* c);
 void tc_m2l(xrl_ctx* c, int nbx, int b0, int ncols, const float* M, float* L, cudaStream_t s);
 void tc_check(xrl_ctx* c, cudaStream_t s);
+bool tc64_usable(const xrl_ctx* c, int ncols);
+void tc_m2l64(xrl_ctx* c, int nbx, int b0, int ncols, const double* M, double* L, cudaStream_t s);
 // solve.cu
 void solver_prepare(xrl_ctx* c);
 void run_solve(xrl_ctx* c, int nf, const double* f, double* R, double* L, const float* shape = nullptr,
