@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="profiling case: only the FMM products of one sweep's launch configuration "
+                         "(FP32 inner product and the mixed mode's FP64 residual operator, 64 systems), 3 each")
     return ap.parse_args()
 
 
@@ -201,11 +204,43 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- profiling case
+def kernel_case():
+    """The bench workload's context and its two product kinds at the solver's
+    launch configuration (384 columns = 64 systems x 6), a few GB on the device:
+    3 FP32 FMM products (tensor-core M2L, FP32 near field) and 3 applications of
+    the FP64 residual operator (integer-slice tensor-core M2L, double-float near
+    field)."""
+    import torch
+    import paper_2409_12375_gb300 as pkg
+    m = workload(0, 1)
+    x = pkg.XRL.from_mesh(m, fmm_order=8, separation=2, leaf_target=32, precision=1)
+    nsys = len(m.freqs) * len(m.ports)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    xv = torch.randn(6 * nsys, m.n_tri, device="cuda", dtype=torch.float32, generator=g)
+    yv = torch.empty_like(xv)
+    n = x.stats()["n_loops"]
+    rng = np.random.default_rng(2)
+    v = rng.standard_normal((nsys, n)) + 1j * rng.standard_normal((nsys, n))
+    f = np.repeat(m.freqs, len(m.ports))
+    for _ in range(3):
+        x.fmm_mvm32_device(xv, yv)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        x.apply_operator(f, v)
+    torch.cuda.synchronize()
+    x.close()
+    print(json.dumps({"kernel_case": "ok", "n_panels": int(m.n_tri), "n_cols": 6 * nsys}))
+    return 0
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel_case:
+        return kernel_case()
     import torch
     import torch.distributed as dist
 

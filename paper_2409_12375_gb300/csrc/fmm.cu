@@ -547,6 +547,141 @@ void launch_xlate<float>(int nbx, int b0, int nc, int ncoef, const int32_t* ptr,
   }
 }
 
+// P2M, FP32, shared-memory tiled: M[leaf][k][c] = sum_i S[i][k] X[i][c] as
+// one small GEMM per leaf.  One CTA per (leaf, 64-column tile), 128 threads
+// as 16 coefficient groups (k = ty + 16 i, i < RI) x 8 column groups; the
+// leaf's panels stream in chunks of 32 (S rows and X rows in shared memory).
+template <int RI>
+__global__ void __launch_bounds__(128) k_p2m_tiled(int nc, int ncoef, int box0, const int32_t* __restrict__ leaf_first,
+                                                   const int32_t* __restrict__ leaf_count, const float* __restrict__ S,
+                                                   const float* __restrict__ X, float* __restrict__ M) {
+  constexpr int CT = 64, KC = 32, LD = 16 * RI;
+  __shared__ __align__(16) float Ss[KC][LD];
+  __shared__ __align__(16) float Xs[KC][CT];
+  const int B = blockIdx.x, c0 = blockIdx.y * CT;
+  const int f0 = leaf_first[B], n = leaf_count[B];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  float acc[RI][8];
+#pragma unroll
+  for (int i = 0; i < RI; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  for (int j0 = 0; j0 < n; j0 += KC) {
+    const int kn = min(KC, n - j0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < KC * LD; e += 128) {
+      const int j = e / LD, k = e % LD;
+      Ss[j][k] = (j < kn && k < ncoef) ? S[(size_t)(f0 + j0 + j) * ncoef + k] : 0.f;
+    }
+    for (int e = threadIdx.x; e < KC * CT; e += 128) {
+      const int j = e / CT, cc = e % CT;
+      Xs[j][cc] = (j < kn && c0 + cc < nc) ? X[(size_t)(f0 + j0 + j) * nc + c0 + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int j = 0; j < KC; ++j) {
+      const float4 x0 = *reinterpret_cast<const float4*>(&Xs[j][4 * tx]);
+      const float4 x1 = *reinterpret_cast<const float4*>(&Xs[j][32 + 4 * tx]);
+#pragma unroll
+      for (int i = 0; i < RI; ++i) {
+        const float t = Ss[j][ty + 16 * i];
+        acc[i][0] += t * x0.x;
+        acc[i][1] += t * x0.y;
+        acc[i][2] += t * x0.z;
+        acc[i][3] += t * x0.w;
+        acc[i][4] += t * x1.x;
+        acc[i][5] += t * x1.y;
+        acc[i][6] += t * x1.z;
+        acc[i][7] += t * x1.w;
+      }
+    }
+  }
+  float* out = M + (size_t)(box0 + B) * ncoef * nc + c0;
+#pragma unroll
+  for (int i = 0; i < RI; ++i) {
+    const int k = ty + 16 * i;
+    if (k >= ncoef) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int cc = (j < 4) ? 4 * tx + j : 32 + 4 * tx + (j - 4);
+      if (c0 + cc < nc) out[(size_t)k * nc + cc] = acc[i][j];
+    }
+  }
+}
+
+// L2P, FP32, shared-memory tiled: Y[i][c] += (1/h) sum_k w_k S[i][k] L[leaf][k][c],
+// w = 1 for the m = 0 coefficients (k a perfect square n^2) and 2 otherwise.
+// One CTA per (leaf, 64-column tile, 64-panel block), 128 threads as 16 panel
+// groups (i = ty + 16 q, q < 4) x 8 column groups; coefficients in chunks of 32.
+__global__ void __launch_bounds__(128) k_l2p_tiled(int nc, int ncoef, int box0, float inv_h,
+                                                   const int32_t* __restrict__ leaf_first,
+                                                   const int32_t* __restrict__ leaf_count, const float* __restrict__ S,
+                                                   const float* __restrict__ L, float* __restrict__ Y) {
+  constexpr int CT = 64, KC = 32, RB = 64;
+  __shared__ __align__(16) float As[KC][RB];
+  __shared__ __align__(16) float Ls[KC][CT];
+  const int B = blockIdx.x, c0 = blockIdx.y * CT, rb0 = blockIdx.z * RB;
+  const int f0 = leaf_first[B], n = leaf_count[B];
+  if (rb0 >= n) return;
+  const int nr = min(RB, n - rb0);
+  const float* lb = L + (size_t)(box0 + B) * ncoef * nc;
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  float acc[4][8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[q][j] = 0.f;
+  for (int k0 = 0; k0 < ncoef; k0 += KC) {
+    const int kn = min(KC, ncoef - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < KC * RB; e += 128) {
+      const int i = e / KC, k = e % KC;
+      float v = 0.f;
+      if (i < nr && k < kn) {
+        const int kk = k0 + k;
+        int sq = (int)sqrtf((float)kk);
+        while ((sq + 1) * (sq + 1) <= kk) ++sq;
+        while (sq * sq > kk) --sq;
+        v = S[(size_t)(f0 + rb0 + i) * ncoef + kk] * (kk == sq * sq ? inv_h : 2.f * inv_h);
+      }
+      As[k][i] = v;
+    }
+    for (int e = threadIdx.x; e < KC * CT; e += 128) {
+      const int k = e / CT, cc = e % CT;
+      Ls[k][cc] = (k < kn && c0 + cc < nc) ? lb[(size_t)(k0 + k) * nc + c0 + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < KC; ++k) {
+      const float4 l0 = *reinterpret_cast<const float4*>(&Ls[k][4 * tx]);
+      const float4 l1 = *reinterpret_cast<const float4*>(&Ls[k][32 + 4 * tx]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float a = As[k][ty + 16 * q];
+        acc[q][0] += a * l0.x;
+        acc[q][1] += a * l0.y;
+        acc[q][2] += a * l0.z;
+        acc[q][3] += a * l0.w;
+        acc[q][4] += a * l1.x;
+        acc[q][5] += a * l1.y;
+        acc[q][6] += a * l1.z;
+        acc[q][7] += a * l1.w;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = ty + 16 * q;
+    if (i >= nr) continue;
+    float* yr = Y + (size_t)(f0 + rb0 + i) * nc + c0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int cc = (j < 4) ? 4 * tx + j : 32 + 4 * tx + (j - 4);
+      if (c0 + cc < nc) yr[cc] += acc[q][j];
+    }
+  }
+}
+
 // L2L: child boxes [b0, b0 + gridDim.x) += T(oct) L[parent]
 template <class T>
 __global__ void k_l2l(int nc, int ct, int ncoef, int b0, const int32_t* __restrict__ parent,
@@ -701,8 +836,12 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   const int ecols = (nc + ct_e - 1) / ct_e;
   const int leaf0 = t.level_off[L];
   ev = prof_begin(c, s);
-  k_p2m<T><<<dim3(nl, ecols), 256, 0, s>>>(nc, ct_e, ncoef, leaf0, c->d.leaf_first.p, c->d.leaf_count.p, mom, X,
-                                           Mx);
+  if (sizeof(T) == 4 && nc >= 32 && ncoef <= 96)
+    k_p2m_tiled<6><<<dim3(nl, (nc + 63) / 64), 128, 0, s>>>(nc, ncoef, leaf0, c->d.leaf_first.p, c->d.leaf_count.p,
+                                                            (const float*)mom, (const float*)X, (float*)Mx);
+  else
+    k_p2m<T><<<dim3(nl, ecols), 256, 0, s>>>(nc, ct_e, ncoef, leaf0, c->d.leaf_first.p, c->d.leaf_count.p, mom, X,
+                                             Mx);
   prof_end(c, s, ev, PH_P2M, 1, 2.0 * N * ncoef * nc, N * ncoef * sz + N * nc * sz + nl * ebytes);
   ev = prof_begin(c, s);
   const bool tiled = xlate_tiled<T>(c, nc);
@@ -755,8 +894,13 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     prof_end(c, s, ev, PH_L2L, std::max(0, L - 2), e2 * nch, 2.0 * nch * ebytes);
   }
   ev = prof_begin(c, s);
-  k_l2p<T><<<dim3(nl, ecols), 128, 0, s>>>(nc, ct_e, ncoef, leaf0, (T)(1.0 / h), c->d.leaf_first.p,
-                                           c->d.leaf_count.p, mom, Lx, Y);
+  if (sizeof(T) == 4 && nc >= 32)
+    k_l2p_tiled<<<dim3(nl, (nc + 63) / 64, (c->max_leaf + 63) / 64), 128, 0, s>>>(
+        nc, ncoef, leaf0, (float)(1.0 / h), c->d.leaf_first.p, c->d.leaf_count.p, (const float*)mom,
+        (const float*)Lx, (float*)Y);
+  else
+    k_l2p<T><<<dim3(nl, ecols), 128, 0, s>>>(nc, ct_e, ncoef, leaf0, (T)(1.0 / h), c->d.leaf_first.p,
+                                             c->d.leaf_count.p, mom, Lx, Y);
   prof_end(c, s, ev, PH_L2P, 1, 2.0 * N * ncoef * nc, N * ncoef * sz + 2.0 * N * nc * sz + nl * ebytes);
   XRL_CUDA(cudaGetLastError());
 }

@@ -62,32 +62,55 @@ __global__ void k_sys_consts(int nsys, int nport, int nmat, const double* __rest
 }
 
 // ---- operator pieces -------------------------------------------------------------------------
+// complex arithmetic in the precision of the product (FP32 for the inner
+// iterations, FP64 for the residuals)
+template <class T> struct CT;
+template <> struct CT<float> { typedef float2 type; };
+template <> struct CT<double> { typedef double2 type; };
+template <class C, class R>
+__device__ __forceinline__ C cmk(R a, R b) { C r; r.x = a; r.y = b; return r; }
+template <class C>
+__device__ __forceinline__ C cadd_t(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <class C>
+__device__ __forceinline__ C csub_t(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <class C>
+__device__ __forceinline__ C cmul_t(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <class C, class R>
+__device__ __forceinline__ C cscale_t(C a, R s) { a.x *= s; a.y *= s; return a; }
+
 // X[r][6s + 2t + ri] = (A_t^T M^T v_s)(r)
 template <class T>
 __global__ void k_gather(int N, int nsys, int nloop, const int32_t* __restrict__ pan_br,
                          const double* __restrict__ pan_rho, const int32_t* __restrict__ mt_ptr,
                          const int32_t* __restrict__ mt_col, const int8_t* __restrict__ mt_val,
                          const cplx* __restrict__ v, T* __restrict__ X) {
+  typedef typename CT<T>::type C;
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)N * nsys) return;
   int r = (int)(idx / nsys), s = (int)(idx % nsys);
   const cplx* vs = v + (size_t)s * nloop;
-  cplx ip[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+  C ip[3] = {cmk<C>((T)0, (T)0), cmk<C>((T)0, (T)0), cmk<C>((T)0, (T)0)};
   for (int k = 0; k < 3; ++k) {
     int b = pan_br[3 * r + k];
     if (b < 0) continue;
-    cplx ie = make_double2(0, 0);
+    C ie = cmk<C>((T)0, (T)0);
     for (int q = mt_ptr[b]; q < mt_ptr[b + 1]; ++q) {
-      cplx x = vs[mt_col[q]];
-      ie = mt_val[q] > 0 ? cadd(ie, x) : csub(ie, x);
+      const cplx x = vs[mt_col[q]];
+      const C xc = cmk<C>((T)x.x, (T)x.y);
+      ie = mt_val[q] > 0 ? cadd_t(ie, xc) : csub_t(ie, xc);
     }
     const double* rho = pan_rho + 9 * (size_t)r + 3 * k;
-    for (int t = 0; t < 3; ++t) ip[t] = cadd(ip[t], cscale(ie, rho[t]));
+    for (int t = 0; t < 3; ++t) ip[t] = cadd_t(ip[t], cscale_t(ie, (T)rho[t]));
   }
   T* out = X + (size_t)r * 6 * nsys + 6 * s;
   for (int t = 0; t < 3; ++t) {
-    out[2 * t] = (T)ip[t].x;
-    out[2 * t + 1] = (T)ip[t].y;
+    out[2 * t] = ip[t].x;
+    out[2 * t + 1] = ip[t].y;
   }
 }
 
@@ -99,30 +122,34 @@ __global__ void k_scatter(int B, int nsys, int nmat, const int32_t* __restrict__
                           const double* __restrict__ area, const cplx* __restrict__ zs,
                           const double* __restrict__ wp, const T* __restrict__ X,
                           const T* __restrict__ Y, cplx* __restrict__ Vb) {
+  typedef typename CT<T>::type C;
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)B * nsys) return;
   int b = (int)(idx / nsys), s = (int)(idx % nsys);
-  cplx acc = make_double2(0, 0);
+  C acc = cmk<C>((T)0, (T)0);
+  const T w = (T)wp[s];
   for (int side = 0; side < 2; ++side) {
     int r = br_pan[2 * b + side];
     if (r < 0) continue;
     const double* rho = br_rho + 6 * (size_t)b + 3 * side;
-    cplx z = cscale(zs[s * nmat + pan_mat[r]], 1.0 / area[r]);
+    const cplx zd = cscale(zs[s * nmat + pan_mat[r]], 1.0 / area[r]);
+    const C z = cmk<C>((T)zd.x, (T)zd.y);
     const T* xr = X + (size_t)r * 6 * nsys + 6 * s;
     const T* yr = Y + (size_t)r * 6 * nsys + 6 * s;
     for (int t = 0; t < 3; ++t) {
-      cplx xv = make_double2(xr[2 * t], xr[2 * t + 1]);
-      cplx yv = make_double2(yr[2 * t], yr[2 * t + 1]);
-      cplx val = cadd(cm(z, xv), make_double2(-wp[s] * yv.y, wp[s] * yv.x));
-      acc = cadd(acc, cscale(val, rho[t]));
+      const C xv = cmk<C>(xr[2 * t], xr[2 * t + 1]);
+      const C val = cadd_t(cmul_t(z, xv), cmk<C>(-w * yr[2 * t + 1], w * yr[2 * t]));
+      acc = cadd_t(acc, cscale_t(val, (T)rho[t]));
     }
   }
-  Vb[idx] = acc;
+  Vb[idx] = make_double2((double)acc.x, (double)acc.y);
 }
 
 // w[s][l] = sum_b M(l, b) Vb[b][s]   (port branches carry no impedance: their Vb is zero)
 // One warp per (loop, 32 systems): the row walk is warp-uniform and the Vb
-// reads are contiguous over the systems.
+// reads are contiguous over the systems.  Rows longer than kLongRow (the
+// homology and port loops) are left to k_loop_reduce_long.
+constexpr int kLongRow = 256;
 __global__ void k_loop_reduce(int nloop, int nsys, int ncb, const int32_t* __restrict__ m_ptr,
                               const int32_t* __restrict__ m_col, const int8_t* __restrict__ m_val,
                               const cplx* __restrict__ Vb, cplx* __restrict__ w) {
@@ -132,16 +159,46 @@ __global__ void k_loop_reduce(int nloop, int nsys, int ncb, const int32_t* __res
   if (wid >= (size_t)nloop * sg) return;
   const int l = (int)(wid / sg);
   const int s = (int)(wid % sg) * 32 + lane;
-  if (s >= nsys) return;
+  const int q0 = m_ptr[l], q1 = m_ptr[l + 1];
+  if (s >= nsys || q1 - q0 > kLongRow) return;
   cplx acc = make_double2(0, 0);
-  const int q1 = m_ptr[l + 1];
-  for (int q = m_ptr[l]; q < q1; ++q) {
+  for (int q = q0; q < q1; ++q) {
     const int b = m_col[q];
     if (b >= ncb) continue;
     const cplx v = Vb[(size_t)b * nsys + s];
     acc = m_val[q] > 0 ? cadd(acc, v) : csub(acc, v);
   }
   w[(size_t)s * nloop + l] = acc;
+}
+
+// The long rows: one CTA of 8 warps per (long row, 32 systems), warp k takes
+// entries q0 + k, q0 + k + 8, ...; partial sums combined in a fixed order.
+__global__ void __launch_bounds__(256) k_loop_reduce_long(int nloop, int nsys, int ncb,
+                                                          const int32_t* __restrict__ rows,
+                                                          const int32_t* __restrict__ m_ptr,
+                                                          const int32_t* __restrict__ m_col,
+                                                          const int8_t* __restrict__ m_val,
+                                                          const cplx* __restrict__ Vb, cplx* __restrict__ w) {
+  __shared__ cplx part[8][32];
+  const int l = rows[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y * 32 + lane;
+  const int q0 = m_ptr[l], q1 = m_ptr[l + 1];
+  cplx acc = make_double2(0, 0);
+  if (s < nsys)
+    for (int q = q0 + warp; q < q1; q += 8) {
+      const int b = m_col[q];
+      if (b >= ncb) continue;
+      const cplx v = Vb[(size_t)b * nsys + s];
+      acc = m_val[q] > 0 ? cadd(acc, v) : csub(acc, v);
+    }
+  part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && s < nsys) {
+    cplx t = part[0][lane];
+    for (int k = 1; k < 8; ++k) t = cadd(t, part[k][lane]);
+    w[(size_t)s * nloop + l] = t;
+  }
 }
 
 // w = Q(f_s) v (mode 0) or diag(Q(f_s)) (mode 1, v unused)
@@ -535,6 +592,12 @@ void solver_prepare(xrl_ctx* c) {
   XRL_CHECK(T.m_col.size() < (size_t)INT32_MAX && T.q_col.size() < (size_t)INT32_MAX, XRL_ENOMEM,
             "loop or preconditioner matrix too large for 32-bit indices");
   c->d.m_ptr.upload(c->alloc, to32(T.m_ptr));
+  {
+    std::vector<int32_t> longr;
+    for (int l = 0; l < T.n_loops; ++l)
+      if (T.m_ptr[l + 1] - T.m_ptr[l] > kLongRow) longr.push_back(l);
+    c->d.m_long.upload(c->alloc, longr);
+  }
   c->d.m_col.upload(c->alloc, T.m_col);
   c->d.m_val.upload(c->alloc, T.m_val);
   c->d.mt_ptr.upload(c->alloc, to32(T.mt_ptr));
@@ -548,6 +611,19 @@ void solver_prepare(xrl_ctx* c) {
 }
 
 static unsigned nblk(size_t n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
+
+// w = M Vb for nsys systems (loop rows short and long); returns the launches
+static int loop_reduce(xrl_ctx* c, int nsys, const cplx* Vb, cplx* w, cudaStream_t s) {
+  const Topo& T = c->topo;
+  const int sg = (nsys + 31) / 32;
+  k_loop_reduce<<<nblk((size_t)T.n_loops * sg * 32), 256, 0, s>>>(T.n_loops, nsys, T.n_cb, c->d.m_ptr.p,
+                                                                  c->d.m_col.p, c->d.m_val.p, Vb, w);
+  const int nlong = (int)c->d.m_long.n;
+  if (nlong == 0) return 1;
+  k_loop_reduce_long<<<dim3(nlong, sg), 256, 0, s>>>(T.n_loops, nsys, T.n_cb, c->d.m_long.p, c->d.m_ptr.p,
+                                                     c->d.m_col.p, c->d.m_val.p, Vb, w);
+  return 2;
+}
 
 // Work arrays of one solve (device)
 struct Work {
@@ -603,9 +679,8 @@ static void apply_A_t(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, T*
   k_scatter<T><<<nblk((size_t)T_.n_cb * nsys), 256, 0, s>>>(T_.n_cb, nsys, T_.n_mat, c->d.br_pan.p, c->d.br_rho.p,
                                                             c->d.pan_mat.p, c->d.area.p, wk.zs.p, wk.wp.p, X, Y,
                                                             wk.Vb.p);
-  k_loop_reduce<<<nblk((size_t)T_.n_loops * ((nsys + 31) / 32) * 32), 256, 0, s>>>(
-      T_.n_loops, nsys, T_.n_cb, c->d.m_ptr.p, c->d.m_col.p, c->d.m_val.p, wk.Vb.p, w);
-  prof_end(c, s, ev, PH_OPER, 2, nsys * (2.0 * T_.n_cb * 30.0 + 2.0 * nnzm),
+  const int nlr = loop_reduce(c, nsys, wk.Vb.p, w, s);
+  prof_end(c, s, ev, PH_OPER, 1 + nlr, nsys * (2.0 * T_.n_cb * 30.0 + 2.0 * nnzm),
            nsys * (T_.n_cb * (2.0 * 12.0 * sizeof(T) + 16.0) + 16.0 * nnzm + 16.0 * T_.n_loops));
   XRL_CUDA(cudaGetLastError());
   c->stats.n_mvm++;
@@ -760,9 +835,7 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
     k_scatter<double><<<nblk((size_t)TT.n_cb * nsys), 256, 0, s>>>(TT.n_cb, nsys, TT.n_mat, c->d.br_pan.p,
                                                                    c->d.br_rho.p, c->d.pan_mat.p, c->d.area.p, zs1.p,
                                                                    wp0.p, wk.X.p, wk.X.p, wk.Vb.p);
-    k_loop_reduce<<<nblk((size_t)n * ((nsys + 31) / 32) * 32), 256, 0, s>>>(n, nsys, TT.n_cb, c->d.m_ptr.p,
-                                                                           c->d.m_col.p, c->d.m_val.p, wk.Vb.p,
-                                                                           wk.w.p);
+    count_launch(c, loop_reduce(c, nsys, wk.Vb.p, wk.w.p, s) - 1);
     BandWork pw;
     band_alloc(c, pw, 1, nsys, false);
     band_factor(c, pw, zs1.p, wp0.p, s);

@@ -214,6 +214,7 @@ struct Dev {
   DBuf<int32_t> br_pan;      // [B][2] Morton panel (-1 terminal)
   DBuf<double> br_rho;       // [B][2][3]
   DBuf<int32_t> m_ptr, m_col, mt_ptr, mt_col;
+  DBuf<int32_t> m_long;     // loop rows longer than the warp-per-row reduce takes
   DBuf<int8_t> m_val, mt_val;
   DBuf<int32_t> q_ptr, q_col;
   DBuf<double> q_val;
