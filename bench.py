@@ -176,7 +176,66 @@ def peaks():
         # FP32 lanes x 2 flops; FP64 at the nominal GB300 rate
         "fp32_tflops": 152 * 128 * 2 * sm_max * 1e6 / 1e12,
         "fp64_tflops": 1.25,
+        "bf16_sust": float(p.get("bf16_tflops_sustained", 1700.0)),
     }
+
+
+# ---------------------------------------------------------------- rooflines
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of the unchanged kernel on this workload's launch
+# configuration (profiles/top_kernels_coil_sweep.md); None where none exists
+NCU_TRAFFIC = {"p2p": 1.021608e9 + 35.6032e6, "m2l": 130.051e6 + 48.901888e6,
+               "p2p64": 2.641835e9 + 77.224192e6, "m2l64": 295.576e6 + 125.270784e6}
+PHASE_KERNEL = {
+    "p2p": "k_p2p_tiled (FP32 CUDA cores)",
+    "m2l": "k_tc_pack_a + k_xlate_tc<96> (tcgen05, 3-piece BF16, 6 products)",
+    "p2p64": "k_split_df + k_p2p_df64 (double-float on the FP32 pipes)",
+    "m2l64": "k_oz_pack_a + k_xlate_oz (tcgen05, 5 integer slices, 15 products)",
+    "precond": "k_spike_y/z/x/out apply + k_band_factor_blk/k_spike_cols/k_spike_reduce factor",
+    "operator": "k_gather + k_scatter + k_loop_reduce(_long)",
+    "p2m": "k_p2m_tiled<6>", "l2p": "k_l2p_tiled", "m2m": "k_m2l_tiled<6,0> (list form)",
+    "l2l": "k_m2l_tiled<6,1> (list form)"}
+
+
+def phase_roofline(name, d, pk, precision, p, nc):
+    """Roofline entry of one profiling phase: algorithmic flops (or bytes) per
+    launch over the phase's CUDA-event time per launch, against the peak of the
+    unit that executes it."""
+    avg_ms = d["ms"] / max(1, d["launches"])
+    mixed = precision == "mixed"
+    alg = d["flops"] / (d["ms"] * 1e-3) / 1e12          # algorithmic TFLOP/s
+    out = {"kernel": PHASE_KERNEL.get(name, name), "avg_launch_ms": avg_ms, "launches": d["launches"],
+           "traffic": NCU_TRAFFIC.get(name) if mixed else None}
+    ncoef = (p + 1) ** 2
+    pad = lambda v: (v + 15) // 16 * 16
+    tile_pad = (pad(ncoef) * pad(ncoef)) / float(ncoef * ncoef) * (128 * ((nc + 127) // 128)) / float(nc)
+    if mixed and name in ("m2l", "m2l64"):
+        products = 6 if name == "m2l" else 15
+        issued = alg * products * tile_pad                # BF16 MMA TFLOP/s actually issued
+        out.update({"bound": "tensor", "achieved": issued, "peak": pk["bf16_sust"], "unit": "TFLOP/s",
+                    "frac": issued / pk["bf16_sust"], "algorithmic_tflops": alg,
+                    "peak_src": "measured bf16 sustained (MEASURED_PEAKS.json)",
+                    "note": "achieved = %d BF16 products x padded %dx%d tiles x algorithmic FP%s flops"
+                            % (products, pad(ncoef), pad(ncoef), "32" if name == "m2l" else "64")})
+    elif mixed and name == "p2p64":
+        ops = alg * 11.0 / 2.0                            # ~11 FP32 operations per double-float multiply-add
+        out.update({"bound": "alu", "achieved": ops, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+                    "frac": ops / pk["fp32_tflops"], "algorithmic_tflops": alg,
+                    "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                    "note": "achieved = FP32 operations/s, 11 per FP64-accurate multiply-add"})
+    elif name in ("precond", "operator"):
+        gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        out.update({"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": gbs / pk["hbm_gbs"], "peak_src": pk["hbm_src"],
+                    "note": "latency-bound chains (sequential substitutions); bytes are algorithmic"
+                    if name == "precond" else "gathers over the loop matrix"})
+    else:
+        fp64 = not mixed or name.endswith("64")
+        peak = pk["fp64_tflops"] if fp64 else pk["fp32_tflops"]
+        out.update({"bound": "alu", "achieved": alg, "peak": peak, "unit": "TFLOP/s", "frac": alg / peak,
+                    "peak_src": "nominal GB300 FP64 (1.25 TFLOP/s)" if fp64 else
+                    "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"})
+    return out
 
 
 # ---------------------------------------------------------------- reference arm
@@ -299,35 +358,13 @@ def main():
     value = (dev_ms / 1e3) / units
     e2e = host_s / units
 
-    # dominant phase roofline
+    # roofline of every major phase; "roofline" is the dominant one
     pk = peaks()
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    d = prof[dom]
-    avg_ms = d["ms"] / max(1, d["launches"])
-    # kernel of each phase and its ncu DRAM traffic per launch (bytes) where a
-    # capture of the unchanged kernel exists (profiles/top_kernels_coil_sweep.md)
-    kern = {"m2l": "k_tc_pack_a + k_xlate_tc<96> (tcgen05, 3-piece BF16)", "p2p": "k_p2p_tiled (FP32)",
-            "precond": "k_band_apply_pair/k_band_factor", "m2l64": "k_m2l_df64 / k_m2l<double>",
-            "p2p64": "k_p2p<double>"}
-    traffic = {"p2p": 1018.708e6 + 36.329728e6}
-    fp32_phase = {"p2p", "p2m", "m2m", "m2l", "l2l", "l2p"}
-    if dom in fp32_phase or dom in ("p2p64", "m2l64"):
-        lowp = dom in fp32_phase and args.precision == "mixed"
-        # the double-float M2L of the mixed mode runs on the FP32 pipes
-        fp32_pipes = lowp or (dom == "m2l64" and args.precision == "mixed")
-        peak = pk["fp32_tflops"] if fp32_pipes else pk["fp64_tflops"]
-        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-        roof = {"kernel": kern.get(dom, dom), "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic.get(dom) if lowp else None,
-                "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock" if fp32_pipes else
-                            "nominal GB300 FP64 (1.25 TFLOP/s)",
-                "avg_launch_ms": avg_ms, "launches": d["launches"]}
-    else:
-        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
-        roof = {"kernel": kern.get(dom, dom), "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_src": pk["hbm_src"],
-                "avg_launch_ms": avg_ms, "launches": d["launches"]}
+    roofs = {k: phase_roofline(k, prof[k], pk, args.precision, opts["fmm_order"], 6 * nsys)
+             for k in ("p2p", "m2l", "p2p64", "m2l64", "precond", "operator", "p2m", "l2p", "m2m", "l2l")
+             if k in prof and prof[k]["ms"] > 0}
+    dom = max(roofs, key=lambda k: prof[k]["ms"])
+    roof = roofs[dom]
 
     # FMM product throughput (FP64 entry point, device buffers), panel-columns/s
     mvm = {}
@@ -373,7 +410,7 @@ def main():
                 "data": "synthetic", "config": config_dict(m, args.precision, opts),
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * len(m.freqs),
                         "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * 4},
-                "gpu_launches": launches, "clocks": ck, "roofline": roof, "cpu_baseline": cb,
+                "gpu_launches": launches, "clocks": ck, "roofline": roof, "roofline_phases": roofs, "cpu_baseline": cb,
                 "fmm_mvm_panel_cols_per_s": mvm, "plain_fp64": plain,
                 "solve": {"fgmres_iters": iters, "max_rel_residual": res, "setup_ms": st["setup_ms"],
                           "n_loops": st["n_loops"], "peak_device_bytes": x.stats()["peak_device_bytes"]},
