@@ -184,12 +184,11 @@ def peaks():
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the unchanged kernel on this workload's launch
 # configuration (profiles/top_kernels_coil_sweep.md); None where none exists
-NCU_TRAFFIC = {"p2p": 1.021608e9 + 35.6032e6, "m2l": 130.051e6 + 48.901888e6,
-               "p2p64": 2.641835e9 + 77.224192e6, "m2l64": 295.576e6 + 125.270784e6}
+NCU_TRAFFIC = {"m2l": 130.051e6 + 48.901888e6, "m2l64": 295.576e6 + 125.270784e6}
 PHASE_KERNEL = {
-    "p2p": "k_p2p_tiled (FP32 CUDA cores)",
+    "p2p": "k_tcp_pack_x + k_xlate_tc<96> (tcgen05 near field, 3-piece BF16)",
     "m2l": "k_tc_pack_a + k_xlate_tc<96> (tcgen05, 3-piece BF16, 6 products)",
-    "p2p64": "k_split_df + k_p2p_df64 (double-float on the FP32 pipes)",
+    "p2p64": "k_ozp_pack_x + k_xlate_oz (tcgen05 near field, 5 integer slices)",
     "m2l64": "k_oz_pack_a + k_xlate_oz (tcgen05, 5 integer slices, 15 products)",
     "precond": "k_spike_y/z/x/out apply + k_band_factor_blk/k_spike_cols/k_spike_reduce factor",
     "operator": "k_gather + k_scatter + k_loop_reduce(_long)",
@@ -197,7 +196,7 @@ PHASE_KERNEL = {
     "l2l": "k_m2l_tiled<6,1> (list form)"}
 
 
-def phase_roofline(name, d, pk, precision, p, nc):
+def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0):
     """Roofline entry of one profiling phase: algorithmic flops (or bytes) per
     launch over the phase's CUDA-event time per launch, against the peak of the
     unit that executes it."""
@@ -209,14 +208,16 @@ def phase_roofline(name, d, pk, precision, p, nc):
     ncoef = (p + 1) ** 2
     pad = lambda v: (v + 15) // 16 * 16
     tile_pad = (pad(ncoef) * pad(ncoef)) / float(ncoef * ncoef) * (128 * ((nc + 127) // 128)) / float(nc)
-    if mixed and name in ("m2l", "m2l64"):
-        products = 6 if name == "m2l" else 15
-        issued = alg * products * tile_pad                # BF16 MMA TFLOP/s actually issued
+    col_pad = (128 * ((nc + 127) // 128)) / float(nc)
+    if mixed and (name in ("m2l", "m2l64") or (name in ("p2p", "p2p64") and near_pad > 0)):
+        products = 6 if name in ("m2l", "p2p") else 15
+        padf = tile_pad if name.startswith("m2l") else near_pad * col_pad
+        issued = alg * products * padf                    # BF16 MMA TFLOP/s actually issued
         out.update({"bound": "tensor", "achieved": issued, "peak": pk["bf16_sust"], "unit": "TFLOP/s",
                     "frac": issued / pk["bf16_sust"], "algorithmic_tflops": alg,
                     "peak_src": "measured bf16 sustained (MEASURED_PEAKS.json)",
-                    "note": "achieved = %d BF16 products x padded %dx%d tiles x algorithmic FP%s flops"
-                            % (products, pad(ncoef), pad(ncoef), "32" if name == "m2l" else "64")})
+                    "note": "achieved = %d BF16 products x padding %.3f x algorithmic FP%s flops"
+                            % (products, padf, "32" if name in ("m2l", "p2p") else "64")})
     elif mixed and name == "p2p64":
         ops = alg * 11.0 / 2.0                            # ~11 FP32 operations per double-float multiply-add
         out.update({"bound": "alu", "achieved": ops, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
@@ -360,7 +361,8 @@ def main():
 
     # roofline of every major phase; "roofline" is the dominant one
     pk = peaks()
-    roofs = {k: phase_roofline(k, prof[k], pk, args.precision, opts["fmm_order"], 6 * nsys)
+    near_pad = st["near_nnz_padded"] / float(st["near_nnz"]) if st.get("near_nnz_padded") else 0.0
+    roofs = {k: phase_roofline(k, prof[k], pk, args.precision, opts["fmm_order"], 6 * nsys, near_pad)
              for k in ("p2p", "m2l", "p2p64", "m2l64", "precond", "operator", "p2m", "l2p", "m2m", "l2l")
              if k in prof and prof[k]["ms"] > 0}
     dom = max(roofs, key=lambda k: prof[k]["ms"])

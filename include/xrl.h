@@ -174,6 +174,8 @@ typedef struct {
   double max_rel_res;    /* largest final true relative residual of the last solve */
   double setup_ms, solve_ms, mvm_ms; /* wall times of the last setup / solve / fmm_mvm */
   int64_t peak_device_bytes;         /* high-water mark of the library's device allocations */
+  int64_t near_nnz_padded;  /* near-field entries of the tensor-core near blocks (leaves padded to
+                               16 panels); 0 when that path is off */
 } xrl_stats;
 
 /* FMM autotuner: tries leaf_target in {16, 32, 64} x fmm_order in {6, 7, 8}

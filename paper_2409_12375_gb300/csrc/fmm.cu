@@ -809,7 +809,14 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   const int ct_e = nc < 4 ? nc : 4;
   dim3 gp(nl, (nc + ct_p - 1) / ct_p);
   cudaEvent_t ev = prof_begin(c, s);
-  if (sizeof(T) == 4 && nc >= 32) {
+  int nl_p2p = 1;
+  if (sizeof(T) == 4 && tcp_usable(c, nc)) {
+    tc_p2p(c, nc, (const float*)X, (float*)Y, s);
+    nl_p2p = 2;
+  } else if (sizeof(T) == 8 && c->df64_m2l && tcp_usable(c, nc)) {
+    tc_p2p64(c, nc, (const double*)X, (double*)Y, s);
+    nl_p2p = 2;
+  } else if (sizeof(T) == 4 && nc >= 32) {
     dim3 gt(nl, (nc + 63) / 64, (c->max_leaf + 63) / 64);
     k_p2p_tiled<<<gt, 128, 0, s>>>(nc, c->d.leaf_first.p, c->d.leaf_count.p, c->d.near_off.p, c->d.near_w.p,
                                    c->d.near_col_off.p, c->d.near_src.p, (const float*)near, (const float*)X,
@@ -832,7 +839,7 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     k_p2p<T><<<gp, 128, 0, s>>>(nc, ct_p, c->d.leaf_first.p, c->d.leaf_count.p, c->d.u_ptr32.p, c->d.u_src.p,
                                 c->d.near_off.p, c->d.near_w.p, near, X, Y);
   }
-  prof_end(c, s, ev, sizeof(T) == 8 ? PH_P2P64 : PH_P2P, 1, 2.0 * nne * nc, nne * sz + 2.0 * N * nc * sz);
+  prof_end(c, s, ev, sizeof(T) == 8 ? PH_P2P64 : PH_P2P, nl_p2p, 2.0 * nne * nc, nne * sz + 2.0 * N * nc * sz);
   const int ecols = (nc + ct_e - 1) / ct_e;
   const int leaf0 = t.level_off[L];
   ev = prof_begin(c, s);

@@ -190,11 +190,64 @@ __global__ void k_tc_pack_b(int ncoef, int Kp, int Np, const double* __restrict_
   }
 }
 
-struct TcArgs {
-  int nc, ncoef, Kp, Np, b0, src0, nct;
+// Pair sources of one translation launch.
+//  * M2L (mode 0): targets are boxes b0 + blockIdx.x, pairs their V-list
+//    entries; A = the multipole image of the source box, B = the table of the
+//    pair's offset, K = Kp, N = NP; out[box][k][col], ncoef rows.
+//  * P2P (mode 1): targets are leaves blockIdx.x, pairs their U-list entries;
+//    A = the transposed-X image of the source leaf (K = its panel count padded
+//    to 16), B = the pair's near-matrix block (N = the target's panel count
+//    padded to 16); out = Y[panel][col], one row per target panel.
+struct XlPairs {
+  int mode, b0, src0, nct, Kp, sum_pc, ncoef;
+  size_t a_img, b_img;   // mode 0: bytes of one (box, tile) A image and of one table image
+  int a_row_bytes;       // bytes per K element of an A image (pieces x 128 x 2)
   const int32_t* ptr;
   const int32_t* src;
   const int16_t* off;
+  const int32_t* leaf_a0;   // mode 1: padded panel offset of each leaf
+  const int32_t* leaf_pc;   // mode 1: padded panel count
+  const int32_t* leaf_f0;   // mode 1: first panel
+  const int32_t* leaf_n;    // mode 1: panel count
+  const int64_t* pair_boff; // mode 1: byte offset of each pair's B image
+};
+
+__device__ __forceinline__ void xl_pair(const XlPairs& p, int v, int ct, size_t& aoff, size_t& boff, int& K) {
+  if (p.mode == 0) {
+    aoff = ((size_t)(p.src[v] - p.src0) * p.nct + ct) * p.a_img;
+    boff = (size_t)p.off[v] * p.b_img;
+    K = p.Kp;
+  } else {
+    const int S = p.src[v];
+    aoff = ((size_t)ct * p.sum_pc + p.leaf_a0[S]) * (size_t)p.a_row_bytes;
+    boff = (size_t)p.pair_boff[v];
+    K = p.leaf_pc[S];
+  }
+}
+
+// target of this CTA: pair range, N, output rows and base row index
+__device__ __forceinline__ void xl_target(const XlPairs& p, int NPmax, int& vs, int& ve, int& N, int& nrows,
+                                          size_t& row0) {
+  if (p.mode == 0) {
+    const int Bx = p.b0 + blockIdx.x;
+    vs = p.ptr[Bx];
+    ve = p.ptr[Bx + 1];
+    N = NPmax;
+    nrows = p.ncoef;
+    row0 = (size_t)Bx * p.ncoef;
+  } else {
+    const int T = blockIdx.x;
+    vs = p.ptr[T];
+    ve = p.ptr[T + 1];
+    nrows = p.leaf_n[T];
+    N = (nrows + 15) & ~15;
+    row0 = (size_t)p.leaf_f0[T];
+  }
+}
+
+struct TcArgs {
+  XlPairs pr;
+  int nc;
   const char* aimg;
   const char* bimg;
   float* out;
@@ -209,10 +262,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 // allocation), 1 = MMA issuer (lane 0), 2..5 = accumulator drain/epilogue.
 // TMEM (512 columns): for the pair buffer q in {0, 1} the x0 y0 products go to
 // columns 256 q and the five small products to 256 q + 128.  After every
-// V-list pair the epilogue warps add both into FP32 registers (IEEE
-// round-to-nearest), so the tensor core only ever accumulates the 6 (resp.
-// 30) MMAs of one pair: its truncating block accumulation would otherwise
-// bias sums over thousands of MMAs.
+// pair the epilogue warps add both into FP32 registers (IEEE
+// round-to-nearest), so the tensor core only ever accumulates the MMAs of one
+// pair: its truncating block accumulation would otherwise bias sums over
+// thousands of MMAs.
 template <int NP>
 __global__ void __launch_bounds__(192, 1) k_xlate_tc(TcArgs a) {
   extern __shared__ uint8_t tc_smem_raw[];
@@ -227,11 +280,11 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc(TcArgs a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
   int* bad = reinterpret_cast<int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int Bx = a.b0 + blockIdx.x, ct = blockIdx.y;
-  const int vs = a.ptr[Bx], ve = a.ptr[Bx + 1];
+  const int ct = blockIdx.y;
+  int vs, ve, N, nrows;
+  size_t row0;
+  xl_target(a.pr, NP, vs, ve, N, nrows, row0);
   const int nv = ve - vs;
-  const int nch = (a.Kp + TC_KC - 1) / TC_KC;
-  const int items = nv * nch;
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -257,68 +310,82 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc(TcArgs a) {
   int issued = 0;
   if (warp == 0) {
     if (lane == 0) {
-      for (int it = 0; it < items; ++it) {
-        const int st = it % TC_STAGES, u = it / TC_STAGES;
-        if (u > 0 && !mbar_wait(&empty[st], (u - 1) & 1)) {
-          atomicExch(bad, 1);
-          break;
+      int it = 0;
+      bool stop = false;
+      for (int v = vs; v < ve && !stop; ++v) {
+        size_t aoff, boff;
+        int K;
+        xl_pair(a.pr, v, ct, aoff, boff, K);
+        const int nchv = (K + TC_KC - 1) / TC_KC;
+        for (int c = 0; c < nchv; ++c, ++it) {
+          const int st = it % TC_STAGES, u = it / TC_STAGES;
+          if (u > 0 && !mbar_wait(&empty[st], (u - 1) & 1)) {
+            atomicExch(bad, 1);
+            stop = true;
+            break;
+          }
+          const int kc = min(TC_KC, K - TC_KC * c);
+          const char* asrc = a.aimg + aoff + (size_t)a_stage * c;
+          const char* bsrc = a.bimg + boff + (size_t)tc_chunk_bytes(N, TC_KC) * c;
+          const uint32_t ab = tc_chunk_bytes(TC_ROWS, kc), bb = tc_chunk_bytes(N, kc);
+          uint8_t* sa = base + (size_t)st * stage_bytes;
+          mbar_expect_tx(&full[st], ab + bb);
+          bulk_g2s(sa, asrc, ab, &full[st]);
+          bulk_g2s(sa + a_stage, bsrc, bb, &full[st]);
+          issued = it + 1;
         }
-        const int v = vs + it / nch, c = it % nch;
-        const int kc = min(TC_KC, a.Kp - TC_KC * c);
-        const char* asrc = a.aimg +
-                           ((size_t)(a.src[v] - a.src0) * a.nct + ct) * (size_t)(TC_PIECES * 2 * TC_ROWS * a.Kp) +
-                           (size_t)a_stage * c;
-        const char* bsrc =
-            a.bimg + (size_t)a.off[v] * (size_t)(TC_PIECES * 2 * NP * a.Kp) + (size_t)tc_chunk_bytes(NP, TC_KC) * c;
-        const uint32_t ab = tc_chunk_bytes(TC_ROWS, kc), bb = tc_chunk_bytes(NP, kc);
-        uint8_t* sa = base + (size_t)st * stage_bytes;
-        mbar_expect_tx(&full[st], ab + bb);
-        bulk_g2s(sa, asrc, ab, &full[st]);
-        bulk_g2s(sa + a_stage, bsrc, bb, &full[st]);
-        issued = it + 1;
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      // D f32, A and B bf16, K-major both, N = NP, M = 128
+      // D f32, A and B bf16, K-major both, N, M = 128
       const uint32_t idesc =
-          (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
-      for (int it = 0; it < items; ++it) {
-        const int st = it % TC_STAGES, u = it / TC_STAGES;
-        const int j = it / nch, c = it % nch, q = j & 1;
-        if (c == 0 && j >= 2 && !mbar_wait(&tfree[q], ((j >> 1) - 1) & 1)) {
+          (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
+      int it = 0;
+      bool stop = false;
+      for (int v = vs, j = 0; v < ve && !stop; ++v, ++j) {
+        size_t aoff, boff;
+        int K;
+        xl_pair(a.pr, v, ct, aoff, boff, K);
+        const int nchv = (K + TC_KC - 1) / TC_KC;
+        const int q = j & 1;
+        if (j >= 2 && !mbar_wait(&tfree[q], ((j >> 1) - 1) & 1)) {
           atomicExch(bad, 1);
           break;
         }
-        if (!mbar_wait(&full[st], u & 1)) {
-          atomicExch(bad, 1);
-          break;
-        }
-        tc_fence_after();
-        const int kc = min(TC_KC, a.Kp - TC_KC * c);
-        const uint32_t sa = sm_u32(base + (size_t)st * stage_bytes);
-        const uint32_t sb = sa + a_stage;
-        const uint32_t pa = TC_ROWS * kc * 2, pb = NP * kc * 2;   // piece strides
-        const uint32_t sbo = 16 * kc;                             // (kc / 8) cores of 128 B
-        const uint32_t dbig = tbase + 256u * q, dsmall = dbig + 128u;
-        for (int ks = 0; ks < kc / 16; ++ks) {
-          uint64_t da[3], db[3];
-#pragma unroll
-          for (int h = 0; h < 3; ++h) {
-            da[h] = sdesc(sa + h * pa + 256 * ks, 128, sbo);
-            db[h] = sdesc(sb + h * pb + 256 * ks, 128, sbo);
+        for (int c = 0; c < nchv; ++c, ++it) {
+          const int st = it % TC_STAGES, u = it / TC_STAGES;
+          if (!mbar_wait(&full[st], u & 1)) {
+            atomicExch(bad, 1);
+            stop = true;
+            break;
           }
-          const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
-          mma_bf16(dbig, da[0], db[0], idesc, accum);
-          mma_bf16(dsmall, da[1], db[1], idesc, accum);
-          mma_bf16(dsmall, da[0], db[2], idesc, 1u);
-          mma_bf16(dsmall, da[2], db[0], idesc, 1u);
-          mma_bf16(dsmall, da[0], db[1], idesc, 1u);
-          mma_bf16(dsmall, da[1], db[0], idesc, 1u);
+          tc_fence_after();
+          const int kc = min(TC_KC, K - TC_KC * c);
+          const uint32_t sa = sm_u32(base + (size_t)st * stage_bytes);
+          const uint32_t sb = sa + a_stage;
+          const uint32_t pa = TC_ROWS * kc * 2, pb = N * kc * 2;   // piece strides
+          const uint32_t sbo = 16 * kc;                            // (kc / 8) cores of 128 B
+          const uint32_t dbig = tbase + 256u * q, dsmall = dbig + 128u;
+          for (int ks = 0; ks < kc / 16; ++ks) {
+            uint64_t da[3], db[3];
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+              da[h] = sdesc(sa + h * pa + 256 * ks, 128, sbo);
+              db[h] = sdesc(sb + h * pb + 256 * ks, 128, sbo);
+            }
+            const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
+            mma_bf16(dbig, da[0], db[0], idesc, accum);
+            mma_bf16(dsmall, da[1], db[1], idesc, accum);
+            mma_bf16(dsmall, da[0], db[2], idesc, 1u);
+            mma_bf16(dsmall, da[2], db[0], idesc, 1u);
+            mma_bf16(dsmall, da[0], db[1], idesc, 1u);
+            mma_bf16(dsmall, da[1], db[0], idesc, 1u);
+          }
+          tc_commit(&empty[st]);
+          if (c == nchv - 1) tc_commit(&tfull[q]);
         }
-        tc_commit(&empty[st]);
-        if (c == nch - 1) tc_commit(&tfull[q]);
       }
       tc_commit(mdone);
       if (!mbar_wait(mdone, 0)) atomicExch(bad, 1);
@@ -364,10 +431,10 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc(TcArgs a) {
     }
     const int col = ct * TC_ROWS + 32 * quarter + lane;
     if (col < a.nc) {
-      float* outp = a.out + (size_t)Bx * a.ncoef * a.nc + col;
+      float* outp = a.out + row0 * a.nc + col;
 #pragma unroll
       for (int n = 0; n < NP; ++n)
-        if (n < a.ncoef) outp[(size_t)n * a.nc] = acc[n];
+        if (n < nrows) outp[(size_t)n * a.nc] = acc[n];
     }
   }
   __syncthreads();
@@ -475,10 +542,8 @@ __global__ void k_oz_pack_b(int ncoef, int Kp, int Np, const int32_t* __restrict
 }
 
 struct OzArgs {
-  int nc, ncoef, Kp, b0, src0, nct;
-  const int32_t* ptr;
-  const int32_t* src;
-  const int16_t* off;
+  XlPairs pr;
+  int nc;
   const char* aimg;
   const char* bimg;
   double* out;
@@ -510,11 +575,11 @@ __global__ void __launch_bounds__(320, 1) k_xlate_oz(OzArgs a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
   int* bad = reinterpret_cast<int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int Bx = a.b0 + blockIdx.x, ct = blockIdx.y;
-  const int vs = a.ptr[Bx], ve = a.ptr[Bx + 1];
+  const int ct = blockIdx.y;
+  int vs, ve, N, nrows;
+  size_t row0;
+  xl_target(a.pr, NP, vs, ve, N, nrows, row0);
   const int nv = ve - vs;
-  const int nch = (a.Kp + TC_KC - 1) / TC_KC;
-  const int items = nv * nch;
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -538,65 +603,78 @@ __global__ void __launch_bounds__(320, 1) k_xlate_oz(OzArgs a) {
   int issued = 0;
   if (warp == 0) {
     if (lane == 0) {
-      for (int it = 0; it < items; ++it) {
-        const int st = it % OZ_STAGES, u = it / OZ_STAGES;
-        if (u > 0 && !mbar_wait(&empty[st], (u - 1) & 1)) {
-          atomicExch(bad, 1);
-          break;
+      int it = 0;
+      bool stop = false;
+      for (int v = vs; v < ve && !stop; ++v) {
+        size_t aoff, boff;
+        int K;
+        xl_pair(a.pr, v, ct, aoff, boff, K);
+        const int nchv = (K + TC_KC - 1) / TC_KC;
+        for (int c = 0; c < nchv; ++c, ++it) {
+          const int st = it % OZ_STAGES, u = it / OZ_STAGES;
+          if (u > 0 && !mbar_wait(&empty[st], (u - 1) & 1)) {
+            atomicExch(bad, 1);
+            stop = true;
+            break;
+          }
+          const int kc = min(TC_KC, K - TC_KC * c);
+          const char* asrc = a.aimg + aoff + (size_t)a_stage * c;
+          const char* bsrc = a.bimg + boff + (size_t)oz_chunk_bytes(N, TC_KC, OZ_S) * c;
+          const uint32_t ab = oz_chunk_bytes(TC_ROWS, kc, OZ_S), bb = oz_chunk_bytes(N, kc, OZ_S);
+          uint8_t* sa = base + (size_t)st * stage_bytes;
+          mbar_expect_tx(&full[st], ab + bb);
+          bulk_g2s(sa, asrc, ab, &full[st]);
+          bulk_g2s(sa + a_stage, bsrc, bb, &full[st]);
+          issued = it + 1;
         }
-        const int v = vs + it / nch, c = it % nch;
-        const int kc = min(TC_KC, a.Kp - TC_KC * c);
-        const char* asrc = a.aimg +
-                           ((size_t)(a.src[v] - a.src0) * a.nct + ct) * (size_t)(OZ_S * 2 * TC_ROWS * a.Kp) +
-                           (size_t)a_stage * c;
-        const char* bsrc = a.bimg + (size_t)a.off[v] * (size_t)(OZ_S * 2 * NP * a.Kp) +
-                           (size_t)oz_chunk_bytes(NP, TC_KC, OZ_S) * c;
-        const uint32_t ab = oz_chunk_bytes(TC_ROWS, kc, OZ_S), bb = oz_chunk_bytes(NP, kc, OZ_S);
-        uint8_t* sa = base + (size_t)st * stage_bytes;
-        mbar_expect_tx(&full[st], ab + bb);
-        bulk_g2s(sa, asrc, ab, &full[st]);
-        bulk_g2s(sa + a_stage, bsrc, bb, &full[st]);
-        issued = it + 1;
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc =
-          (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
-      for (int it = 0; it < items; ++it) {
-        const int st = it % OZ_STAGES, u = it / OZ_STAGES;
-        const int j = it / nch, c = it % nch;
-        if (c == 0 && j >= 1 && !mbar_wait(tfree, (j - 1) & 1)) {
+          (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
+      int it = 0;
+      bool stop = false;
+      for (int v = vs, j = 0; v < ve && !stop; ++v, ++j) {
+        size_t aoff, boff;
+        int K;
+        xl_pair(a.pr, v, ct, aoff, boff, K);
+        const int nchv = (K + TC_KC - 1) / TC_KC;
+        if (j >= 1 && !mbar_wait(tfree, (j - 1) & 1)) {
           atomicExch(bad, 1);
           break;
         }
-        if (!mbar_wait(&full[st], u & 1)) {
-          atomicExch(bad, 1);
-          break;
-        }
-        tc_fence_after();
-        const int kc = min(TC_KC, a.Kp - TC_KC * c);
-        const uint32_t sa = sm_u32(base + (size_t)st * stage_bytes);
-        const uint32_t sb = sa + a_stage;
-        const uint32_t pa = TC_ROWS * kc * 2, pb = NP * kc * 2;
-        const uint32_t sbo = 16 * kc;
-        for (int ks = 0; ks < kc / 16; ++ks) {
-          uint64_t da[OZ_S], db[OZ_S];
-#pragma unroll
-          for (int h = 0; h < OZ_S; ++h) {
-            da[h] = sdesc(sa + h * pa + 256 * ks, 128, sbo);
-            db[h] = sdesc(sb + h * pb + 256 * ks, 128, sbo);
+        for (int c = 0; c < nchv; ++c, ++it) {
+          const int st = it % OZ_STAGES, u = it / OZ_STAGES;
+          if (!mbar_wait(&full[st], u & 1)) {
+            atomicExch(bad, 1);
+            stop = true;
+            break;
           }
-          const bool first = c == 0 && ks == 0;
+          tc_fence_after();
+          const int kc = min(TC_KC, K - TC_KC * c);
+          const uint32_t sa = sm_u32(base + (size_t)st * stage_bytes);
+          const uint32_t sb = sa + a_stage;
+          const uint32_t pa = TC_ROWS * kc * 2, pb = N * kc * 2;
+          const uint32_t sbo = 16 * kc;
+          for (int ks = 0; ks < kc / 16; ++ks) {
+            uint64_t da[OZ_S], db[OZ_S];
 #pragma unroll
-          for (int sc = 0; sc < OZ_S; ++sc)
+            for (int h = 0; h < OZ_S; ++h) {
+              da[h] = sdesc(sa + h * pa + 256 * ks, 128, sbo);
+              db[h] = sdesc(sb + h * pb + 256 * ks, 128, sbo);
+            }
+            const bool first = c == 0 && ks == 0;
 #pragma unroll
-            for (int i = 0; i <= sc; ++i)
-              mma_bf16(tbase + 96u * sc, da[i], db[sc - i], idesc, (first && i == 0) ? 0u : 1u);
+            for (int sc = 0; sc < OZ_S; ++sc)
+#pragma unroll
+              for (int i = 0; i <= sc; ++i)
+                mma_bf16(tbase + 96u * sc, da[i], db[sc - i], idesc, (first && i == 0) ? 0u : 1u);
+          }
+          tc_commit(&empty[st]);
+          if (c == nchv - 1) tc_commit(tfull);
         }
-        tc_commit(&empty[st]);
-        if (c == nch - 1) tc_commit(tfull);
       }
       tc_commit(mdone);
       if (!mbar_wait(mdone, 0)) atomicExch(bad, 1);
@@ -652,11 +730,11 @@ __global__ void __launch_bounds__(320, 1) k_xlate_oz(OzArgs a) {
     }
     const int col = ct * TC_ROWS + 32 * quarter + lane;
     if (col < a.nc) {
-      double* outp = a.out + (size_t)Bx * a.ncoef * a.nc + col;
+      double* outp = a.out + row0 * a.nc + col;
 #pragma unroll
       for (int q = 0; q < 48; ++q) {
         const int n = 48 * half + q;
-        if (n < a.ncoef) outp[(size_t)n * a.nc] = (double)ah[q] + (double)al[q];
+        if (n < nrows) outp[(size_t)n * a.nc] = (double)ah[q] + (double)al[q];
       }
     }
   }
@@ -675,6 +753,146 @@ __global__ void __launch_bounds__(320, 1) k_xlate_oz(OzArgs a) {
   }
 }
 
+// ---- near field on the tensor cores: packing ----------------------------------------------
+// Transposed-X image (A operand of mode 1): for leaf S and column tile ct the
+// rows are the columns ct*128 + r and K runs over the leaf's panels (padded to
+// 16); images of all leaves of one tile are contiguous, [ct][padded panel].
+__global__ void k_tcp_pack_x(int nc, int sum_pc, const int32_t* __restrict__ leaf_f0,
+                             const int32_t* __restrict__ leaf_n, const int32_t* __restrict__ leaf_a0,
+                             const int32_t* __restrict__ leaf_pc, const float* __restrict__ X,
+                             uint16_t* __restrict__ img) {
+  const int S = blockIdx.x, ct = blockIdx.y;
+  const int pc = leaf_pc[S], n = leaf_n[S], f0 = leaf_f0[S];
+  char* dst = reinterpret_cast<char*>(img) + ((size_t)ct * sum_pc + leaf_a0[S]) * (size_t)(TC_PIECES * TC_ROWS * 2);
+  for (int e = threadIdx.x; e < TC_ROWS * (pc >> 3); e += blockDim.x) {
+    const int r = e & (TC_ROWS - 1), kq = e >> 7;
+    const int col = ct * TC_ROWS + r;
+    uint16_t p0[8], p1[8], p2[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = 8 * kq + q;
+      const float x = (col < nc && k < n) ? X[(size_t)(f0 + k) * nc + col] : 0.f;
+      p0[q] = bf16_bits(x);
+      const float r1 = x - bf16_val(p0[q]);
+      p1[q] = bf16_bits(r1);
+      p2[q] = bf16_bits(r1 - bf16_val(p1[q]));
+    }
+    uint4 v0, v1, v2;
+    v0.x = p0[0] | (uint32_t)p0[1] << 16; v0.y = p0[2] | (uint32_t)p0[3] << 16;
+    v0.z = p0[4] | (uint32_t)p0[5] << 16; v0.w = p0[6] | (uint32_t)p0[7] << 16;
+    v1.x = p1[0] | (uint32_t)p1[1] << 16; v1.y = p1[2] | (uint32_t)p1[3] << 16;
+    v1.z = p1[4] | (uint32_t)p1[5] << 16; v1.w = p1[6] | (uint32_t)p1[7] << 16;
+    v2.x = p2[0] | (uint32_t)p2[1] << 16; v2.y = p2[2] | (uint32_t)p2[3] << 16;
+    v2.z = p2[4] | (uint32_t)p2[5] << 16; v2.w = p2[6] | (uint32_t)p2[7] << 16;
+    *reinterpret_cast<uint4*>(dst + tc_img_off(TC_ROWS, pc, r, 8 * kq, 0)) = v0;
+    *reinterpret_cast<uint4*>(dst + tc_img_off(TC_ROWS, pc, r, 8 * kq, 1)) = v1;
+    *reinterpret_cast<uint4*>(dst + tc_img_off(TC_ROWS, pc, r, 8 * kq, 2)) = v2;
+  }
+}
+
+// Near-matrix block of U-list pair v (B operand of mode 1), from the FP64
+// values: rows n < N_T (target panels, padded to 16), K = the source leaf's
+// panels (padded to 16).  One CTA per pair.
+__global__ void k_tcp_pack_v(const int32_t* __restrict__ pair_tgt, const int32_t* __restrict__ u_src,
+                             const int32_t* __restrict__ pair_col, const int32_t* __restrict__ leaf_n,
+                             const int32_t* __restrict__ leaf_pc, const int64_t* __restrict__ near_off,
+                             const int32_t* __restrict__ near_w, const int64_t* __restrict__ pair_boff,
+                             const double* __restrict__ val, uint16_t* __restrict__ img) {
+  const int v = blockIdx.x;
+  const int T = pair_tgt[v], S = u_src[v];
+  const int nT = leaf_n[T], nS = leaf_n[S], N = (nT + 15) & ~15, pc = leaf_pc[S], w = near_w[T];
+  const double* vb = val + near_off[T] + pair_col[v];
+  char* dst = reinterpret_cast<char*>(img) + pair_boff[v];
+  for (int e = threadIdx.x; e < N * pc; e += blockDim.x) {
+    const int r = e % N, k = e / N;
+    const double x = (r < nT && k < nS) ? vb[(size_t)r * w + k] : 0.0;
+    const uint16_t b0 = bf16_bits(__double2float_rn(x));
+    const double r1 = x - (double)bf16_val(b0);
+    const uint16_t b1 = bf16_bits(__double2float_rn(r1));
+    const uint16_t b2 = bf16_bits(__double2float_rn(r1 - (double)bf16_val(b1)));
+    *reinterpret_cast<uint16_t*>(dst + tc_img_off(N, pc, r, k, 0)) = b0;
+    *reinterpret_cast<uint16_t*>(dst + tc_img_off(N, pc, r, k, 1)) = b1;
+    *reinterpret_cast<uint16_t*>(dst + tc_img_off(N, pc, r, k, 2)) = b2;
+  }
+}
+
+// The same two operands as integer slices for the FP64-accurate near field:
+// X rows scaled per (leaf, column), near blocks per (pair, target panel), each
+// by the power of two above its largest magnitude (see k_oz_pack_a).
+__global__ void k_ozp_pack_x(int nc, int sum_pc, const int32_t* __restrict__ leaf_f0,
+                             const int32_t* __restrict__ leaf_n, const int32_t* __restrict__ leaf_a0,
+                             const int32_t* __restrict__ leaf_pc, const double* __restrict__ X,
+                             uint16_t* __restrict__ img) {
+  __shared__ int eA[TC_ROWS];
+  const int S = blockIdx.x, ct = blockIdx.y;
+  const int pc = leaf_pc[S], n = leaf_n[S], f0 = leaf_f0[S];
+  char* dst = reinterpret_cast<char*>(img) + ((size_t)ct * sum_pc + leaf_a0[S]) * (size_t)(OZ_S * TC_ROWS * 2);
+  for (int r = threadIdx.x; r < TC_ROWS; r += blockDim.x) {
+    const int col = ct * TC_ROWS + r;
+    double mx = 0.0;
+    if (col < nc)
+      for (int k = 0; k < n; ++k) mx = fmax(mx, fabs(X[(size_t)(f0 + k) * nc + col]));
+    eA[r] = mx > 0.0 ? ilogb(mx) + 1 : 0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TC_ROWS * (pc >> 3); e += blockDim.x) {
+    const int r = e & (TC_ROWS - 1), kq = e >> 7;
+    const int col = ct * TC_ROWS + r;
+    const int ea = eA[r];
+    uint16_t sl[OZ_S][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = 8 * kq + q;
+      double x = (col < nc && k < n) ? ldexp(X[(size_t)(f0 + k) * nc + col], -ea) : 0.0;
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i) {
+        const double a = rint(x * 128.0);
+        x = x * 128.0 - a;
+        sl[i][q] = bf16_bits(ldexpf((float)a, ea - 7));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < OZ_S; ++i) {
+      uint4 v;
+      v.x = sl[i][0] | (uint32_t)sl[i][1] << 16;
+      v.y = sl[i][2] | (uint32_t)sl[i][3] << 16;
+      v.z = sl[i][4] | (uint32_t)sl[i][5] << 16;
+      v.w = sl[i][6] | (uint32_t)sl[i][7] << 16;
+      *reinterpret_cast<uint4*>(dst + oz_img_off(TC_ROWS, pc, r, 8 * kq, i, OZ_S)) = v;
+    }
+  }
+}
+
+__global__ void k_ozp_pack_v(const int32_t* __restrict__ pair_tgt, const int32_t* __restrict__ u_src,
+                             const int32_t* __restrict__ pair_col, const int32_t* __restrict__ leaf_n,
+                             const int32_t* __restrict__ leaf_pc, const int64_t* __restrict__ near_off,
+                             const int32_t* __restrict__ near_w, const int64_t* __restrict__ pair_boff,
+                             const double* __restrict__ val, uint16_t* __restrict__ img) {
+  __shared__ int fB[96];
+  const int v = blockIdx.x;
+  const int T = pair_tgt[v], S = u_src[v];
+  const int nT = leaf_n[T], nS = leaf_n[S], N = (nT + 15) & ~15, pc = leaf_pc[S], w = near_w[T];
+  const double* vb = val + near_off[T] + pair_col[v];
+  char* dst = reinterpret_cast<char*>(img) + pair_boff[v];
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    double mx = 0.0;
+    if (r < nT)
+      for (int k = 0; k < nS; ++k) mx = fmax(mx, fabs(vb[(size_t)r * w + k]));
+    fB[r] = mx > 0.0 ? ilogb(mx) + 1 : 0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * pc; e += blockDim.x) {
+    const int r = e % N, k = e / N;
+    const int fb = fB[r];
+    double x = (r < nT && k < nS) ? ldexp(vb[(size_t)r * w + k], -fb) : 0.0;
+    for (int i = 0; i < OZ_S; ++i) {
+      const double a = rint(x * 128.0);
+      x = x * 128.0 - a;
+      *reinterpret_cast<uint16_t*>(dst + oz_img_off(N, pc, r, k, i, OZ_S)) = bf16_bits(ldexpf((float)a, fb - 7));
+    }
+  }
+}
+
 // ---- host side ---------------------------------------------------------------------------
 
 static int tc_kpad(int ncoef) { return (ncoef + 15) & ~15; }
@@ -684,17 +902,124 @@ bool tc_usable(const xrl_ctx* c, int nc) {
   return c->opt.tensor_cores != 0 && nc >= 64 && tc_npad(c->ncoef) <= 96 && c->d.tc_bimg.n > 0;
 }
 
+static XlPairs m2l_pairs(const xrl_ctx* c, int b0, int nct, int pieces, size_t a_img, size_t b_img) {
+  XlPairs p = {};
+  p.mode = 0;
+  p.b0 = b0;
+  p.src0 = c->tree.level_off[2];
+  p.nct = nct;
+  p.Kp = tc_kpad(c->ncoef);
+  p.ncoef = c->ncoef;
+  p.a_img = a_img;
+  p.b_img = b_img;
+  p.a_row_bytes = pieces * TC_ROWS * 2;
+  p.ptr = c->d.v_ptr32.p;
+  p.src = c->d.v_src.p;
+  p.off = c->d.v_off.p;
+  return p;
+}
+
+static XlPairs p2p_pairs(const xrl_ctx* c, int nct, int pieces, const int64_t* boff) {
+  XlPairs p = {};
+  p.mode = 1;
+  p.nct = nct;
+  p.sum_pc = c->tcp_sum_pc;
+  p.a_row_bytes = pieces * TC_ROWS * 2;
+  p.ptr = c->d.u_ptr32.p;
+  p.src = c->d.u_src.p;
+  p.leaf_a0 = c->d.tcp_a0.p;
+  p.leaf_pc = c->d.tcp_pc.p;
+  p.leaf_f0 = c->d.leaf_first.p;
+  p.leaf_n = c->d.leaf_count.p;
+  p.pair_boff = boff;
+  return p;
+}
+
+template <int NP>
+static void launch_tc(dim3 g, const TcArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)TC_STAGES * (tc_chunk_bytes(TC_ROWS, TC_KC) + tc_chunk_bytes(NP, TC_KC)) + 1024 + 128;
+  static bool set = false;
+  if (!set) {
+    XRL_CUDA(cudaFuncSetAttribute(k_xlate_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    set = true;
+  }
+  k_xlate_tc<NP><<<g, 192, smem, s>>>(a);
+}
+
+static void launch_oz(dim3 g, const OzArgs& a, cudaStream_t s) {
+  const size_t smem =
+      (size_t)OZ_STAGES * (oz_chunk_bytes(TC_ROWS, TC_KC, OZ_S) + oz_chunk_bytes(96, TC_KC, OZ_S)) + 1024 + 128;
+  static bool set = false;
+  if (!set) {
+    XRL_CUDA(cudaFuncSetAttribute(k_xlate_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    set = true;
+  }
+  k_xlate_oz<<<g, 320, smem, s>>>(a);
+}
+
+// Near-field layout for the tensor cores: leaves padded to 16 panels, the
+// pair offsets of the near-block images, and the FP32 images themselves.
+static void tcp_prepare(xrl_ctx* c) {
+  const Tree& t = c->tree;
+  const int nl = t.n_leaves();
+  int maxn = 0;
+  for (int L = 0; L < nl; ++L) maxn = std::max(maxn, (int)t.leaf_count[L]);
+  if (maxn > 96 || nl == 0) return;
+  std::vector<int32_t> a0(nl), pc(nl);
+  int sum = 0;
+  for (int L = 0; L < nl; ++L) {
+    pc[L] = ((int)t.leaf_count[L] + 15) & ~15;
+    a0[L] = sum;
+    sum += pc[L];
+  }
+  const size_t np = t.u_src.size();
+  std::vector<int32_t> tgt(np), col(np);
+  std::vector<int64_t> boff(np), zoff(np);
+  int64_t b = 0, z = 0;
+  for (int T = 0; T < nl; ++T) {
+    int cacc = 0;
+    const int N = ((int)t.leaf_count[T] + 15) & ~15;
+    for (int64_t q = t.u_ptr[T]; q < t.u_ptr[T + 1]; ++q) {
+      const int S = t.u_src[q];
+      tgt[q] = T;
+      col[q] = cacc;
+      cacc += t.leaf_count[S];
+      boff[q] = b;
+      zoff[q] = z;
+      b += (int64_t)TC_PIECES * 2 * N * pc[S];
+      z += (int64_t)OZ_S * 2 * N * pc[S];
+    }
+  }
+  c->tcp_sum_pc = sum;
+  c->stats.near_nnz_padded = b / (TC_PIECES * 2);
+  c->tcp_img_bytes = b;
+  c->ozp_img_bytes = z;
+  c->d.tcp_a0.upload(c->alloc, a0);
+  c->d.tcp_pc.upload(c->alloc, pc);
+  c->d.tcp_tgt.upload(c->alloc, tgt);
+  c->d.tcp_col.upload(c->alloc, col);
+  c->d.tcp_boff.upload(c->alloc, boff);
+  c->d.ozp_boff.upload(c->alloc, zoff);
+  c->d.tcp_vimg.alloc(c->alloc, (size_t)(b / 2));
+  k_tcp_pack_v<<<(unsigned)np, 256, 0, c->stream>>>(c->d.tcp_tgt.p, c->d.u_src.p, c->d.tcp_col.p, c->d.leaf_count.p,
+                                                    c->d.tcp_pc.p, c->d.near_off.p, c->d.near_w.p, c->d.tcp_boff.p,
+                                                    c->d.near_val.p, c->d.tcp_vimg.p);
+  XRL_CUDA(cudaGetLastError());
+}
+
 void tc_prepare(xrl_ctx* c) {
   const int ncoef = c->ncoef;
-  if (c->opt.tensor_cores == 0 || tc_npad(ncoef) > 96) return;
+  if (c->opt.tensor_cores == 0) return;
+  c->d.tc_err.alloc(c->alloc, 1);
+  XRL_CUDA(cudaMemsetAsync(c->d.tc_err.p, 0, sizeof(int32_t), c->stream));
+  tcp_prepare(c);
+  if (tc_npad(ncoef) > 96) return;
   const int Kp = tc_kpad(ncoef), Np = tc_npad(ncoef);
   const int noff = (int)(c->tree.m2l_offsets.size() / 3);
   if (noff == 0) return;
   c->d.tc_bimg.alloc(c->alloc, (size_t)noff * TC_PIECES * Np * Kp);
   k_tc_pack_b<<<noff, 256, 0, c->stream>>>(ncoef, Kp, Np, c->d.t_m2l.p, c->d.tc_bimg.p);
   XRL_CUDA(cudaGetLastError());
-  c->d.tc_err.alloc(c->alloc, 1);
-  XRL_CUDA(cudaMemsetAsync(c->d.tc_err.p, 0, sizeof(int32_t), c->stream));
 }
 
 // M2L of the FP32 pass: in = M, out = L over all target boxes [b0, b0 + nbx);
@@ -708,36 +1033,16 @@ void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cud
   c->d.tc_aimg.ensure(c->alloc, (size_t)nsrc * nct * TC_PIECES * TC_ROWS * Kp);
   k_tc_pack_a<<<dim3(nsrc, nct), 256, 0, s>>>(nc, ncoef, Kp, src0, Mx, c->d.tc_aimg.p);
   TcArgs a;
+  a.pr = m2l_pairs(c, b0, nct, TC_PIECES, (size_t)TC_PIECES * 2 * TC_ROWS * Kp, (size_t)TC_PIECES * 2 * Np * Kp);
   a.nc = nc;
-  a.ncoef = ncoef;
-  a.Kp = Kp;
-  a.Np = Np;
-  a.b0 = b0;
-  a.src0 = src0;
-  a.nct = nct;
-  a.ptr = c->d.v_ptr32.p;
-  a.src = c->d.v_src.p;
-  a.off = c->d.v_off.p;
   a.aimg = reinterpret_cast<const char*>(c->d.tc_aimg.p);
   a.bimg = reinterpret_cast<const char*>(c->d.tc_bimg.p);
   a.out = Lx;
   a.err = c->d.tc_err.p;
-  const size_t smem = (size_t)TC_STAGES * (tc_chunk_bytes(TC_ROWS, TC_KC) + tc_chunk_bytes(Np, TC_KC)) + 1024 + 128;
-  if (Np <= 64) {
-    static bool set = false;
-    if (!set) {
-      XRL_CUDA(cudaFuncSetAttribute(k_xlate_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      set = true;
-    }
-    k_xlate_tc<64><<<dim3(nbx, nct), 192, smem, s>>>(a);
-  } else {
-    static bool set = false;
-    if (!set) {
-      XRL_CUDA(cudaFuncSetAttribute(k_xlate_tc<96>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      set = true;
-    }
-    k_xlate_tc<96><<<dim3(nbx, nct), 192, smem, s>>>(a);
-  }
+  if (Np <= 64)
+    launch_tc<64>(dim3(nbx, nct), a, s);
+  else
+    launch_tc<96>(dim3(nbx, nct), a, s);
 }
 
 bool tc64_usable(const xrl_ctx* c, int nc) {
@@ -769,27 +1074,60 @@ void tc_m2l64(xrl_ctx* c, int nbx, int b0, int nc, const double* Mx, double* Lx,
   c->d.oz_aimg.ensure(c->alloc, (size_t)nsrc * nct * OZ_S * TC_ROWS * Kp);
   k_oz_pack_a<<<dim3(nsrc, nct), 256, 0, s>>>(nc, ncoef, Kp, src0, c->d.oz_dk.p, Mx, c->d.oz_aimg.p);
   OzArgs a;
+  a.pr = m2l_pairs(c, b0, nct, OZ_S, (size_t)OZ_S * 2 * TC_ROWS * Kp, (size_t)OZ_S * 2 * Np * Kp);
   a.nc = nc;
-  a.ncoef = ncoef;
-  a.Kp = Kp;
-  a.b0 = b0;
-  a.src0 = src0;
-  a.nct = nct;
-  a.ptr = c->d.v_ptr32.p;
-  a.src = c->d.v_src.p;
-  a.off = c->d.v_off.p;
   a.aimg = reinterpret_cast<const char*>(c->d.oz_aimg.p);
   a.bimg = reinterpret_cast<const char*>(c->d.oz_bimg.p);
   a.out = Lx;
   a.err = c->d.tc_err.p;
-  const size_t smem =
-      (size_t)OZ_STAGES * (oz_chunk_bytes(TC_ROWS, TC_KC, OZ_S) + oz_chunk_bytes(Np, TC_KC, OZ_S)) + 1024 + 128;
-  static bool set = false;
-  if (!set) {
-    XRL_CUDA(cudaFuncSetAttribute(k_xlate_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    set = true;
+  launch_oz(dim3(nbx, nct), a, s);
+}
+
+bool tcp_usable(const xrl_ctx* c, int nc) {
+  return c->opt.tensor_cores != 0 && nc >= 64 && c->d.tcp_vimg.n > 0;
+}
+
+// FP32 near field Y = P_near X on the tensor cores (two launches)
+void tc_p2p(xrl_ctx* c, int nc, const float* X, float* Y, cudaStream_t s) {
+  const int nl = c->tree.n_leaves();
+  const int nct = (nc + TC_ROWS - 1) / TC_ROWS;
+  c->d.tcp_ximg.ensure(c->alloc, (size_t)nct * c->tcp_sum_pc * TC_PIECES * TC_ROWS);
+  k_tcp_pack_x<<<dim3(nl, nct), 256, 0, s>>>(nc, c->tcp_sum_pc, c->d.leaf_first.p, c->d.leaf_count.p, c->d.tcp_a0.p,
+                                             c->d.tcp_pc.p, X, c->d.tcp_ximg.p);
+  TcArgs a;
+  a.pr = p2p_pairs(c, nct, TC_PIECES, c->d.tcp_boff.p);
+  a.nc = nc;
+  a.aimg = reinterpret_cast<const char*>(c->d.tcp_ximg.p);
+  a.bimg = reinterpret_cast<const char*>(c->d.tcp_vimg.p);
+  a.out = Y;
+  a.err = c->d.tc_err.p;
+  launch_tc<96>(dim3(nl, nct), a, s);
+}
+
+// FP64-accurate near field on the tensor cores (integer slices; two launches,
+// plus the one-time packing of the near blocks)
+void tc_p2p64(xrl_ctx* c, int nc, const double* X, double* Y, cudaStream_t s) {
+  const int nl = c->tree.n_leaves();
+  const int nct = (nc + TC_ROWS - 1) / TC_ROWS;
+  if (c->d.ozp_vimg.n == 0) {
+    c->d.ozp_vimg.alloc(c->alloc, (size_t)(c->ozp_img_bytes / 2));
+    k_ozp_pack_v<<<(unsigned)c->d.u_src.n, 128, 0, s>>>(c->d.tcp_tgt.p, c->d.u_src.p, c->d.tcp_col.p,
+                                                         c->d.leaf_count.p, c->d.tcp_pc.p, c->d.near_off.p,
+                                                         c->d.near_w.p, c->d.ozp_boff.p, c->d.near_val.p,
+                                                         c->d.ozp_vimg.p);
+    count_launch(c);
   }
-  k_xlate_oz<<<dim3(nbx, nct), 320, smem, s>>>(a);
+  c->d.ozp_ximg.ensure(c->alloc, (size_t)nct * c->tcp_sum_pc * OZ_S * TC_ROWS);
+  k_ozp_pack_x<<<dim3(nl, nct), 256, 0, s>>>(nc, c->tcp_sum_pc, c->d.leaf_first.p, c->d.leaf_count.p, c->d.tcp_a0.p,
+                                             c->d.tcp_pc.p, X, c->d.ozp_ximg.p);
+  OzArgs a;
+  a.pr = p2p_pairs(c, nct, OZ_S, c->d.ozp_boff.p);
+  a.nc = nc;
+  a.aimg = reinterpret_cast<const char*>(c->d.ozp_ximg.p);
+  a.bimg = reinterpret_cast<const char*>(c->d.ozp_vimg.p);
+  a.out = Y;
+  a.err = c->d.tc_err.p;
+  launch_oz(dim3(nl, nct), a, s);
 }
 
 // raises XRL_ETIMEOUT if a tensor-core kernel gave up a wait since the last check

@@ -200,6 +200,12 @@ struct Dev {
   DBuf<uint16_t> oz_bimg;   // integer-slice BF16 images of the M2L tables (FP64-accurate path)
   DBuf<uint16_t> oz_aimg;   // integer-slice BF16 images of the FP64 multipoles, per product
   DBuf<int32_t> oz_dk;      // power-of-two equilibration exponents per coefficient index
+  // near field on the tensor cores: leaves padded to 16 panels
+  DBuf<int32_t> tcp_a0, tcp_pc;         // per leaf: padded panel offset and count
+  DBuf<int32_t> tcp_tgt, tcp_col;       // per U-list pair: target leaf, first near column of the source
+  DBuf<int64_t> tcp_boff, ozp_boff;     // per U-list pair: byte offset of its near-block image
+  DBuf<uint16_t> tcp_vimg, ozp_vimg;    // near-block images (3 BF16 pieces; 5 integer slices)
+  DBuf<uint16_t> tcp_ximg, ozp_ximg;    // transposed-X images, per product
   DBuf<int32_t> v_ptr32, v_src;
   DBuf<int16_t> v_off;
   DBuf<int32_t> lvl_boxes;                            // per level: global ids of its boxes (same as range)
@@ -266,6 +272,8 @@ struct xrl_ctx {
   bool have_mesh = false, have_cond = false, ready = false;
   int N = 0, ncoef = 0, p = 0, max_leaf = 0;
   bool df64_m2l = false;   // FP64 M2L on the FP32 pipes (set inside mixed-precision solves)
+  int tcp_sum_pc = 0;                   // padded panels of all leaves (tensor-core near field)
+  int64_t tcp_img_bytes = 0, ozp_img_bytes = 0;
   int last_nsys = 0, last_nport = 0;
   std::vector<int32_t> last_port_loop;
   xrl::Tree tree;
@@ -322,6 +330,9 @@ void tc_prepare(xrl_ctx* c);
 void tc_m2l(xrl_ctx* c, int nbx, int b0, int ncols, const float* M, float* L, cudaStream_t s);
 void tc_check(xrl_ctx* c, cudaStream_t s);
 bool tc64_usable(const xrl_ctx* c, int ncols);
+bool tcp_usable(const xrl_ctx* c, int ncols);
+void tc_p2p(xrl_ctx* c, int ncols, const float* X, float* Y, cudaStream_t s);
+void tc_p2p64(xrl_ctx* c, int ncols, const double* X, double* Y, cudaStream_t s);
 void tc_m2l64(xrl_ctx* c, int nbx, int b0, int ncols, const double* M, double* L, cudaStream_t s);
 // solve.cu
 void solver_prepare(xrl_ctx* c);
