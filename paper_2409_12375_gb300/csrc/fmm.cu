@@ -842,8 +842,15 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   prof_end(c, s, ev, sizeof(T) == 8 ? PH_P2P64 : PH_P2P, nl_p2p, 2.0 * nne * nc, nne * sz + 2.0 * N * nc * sz);
   const int ecols = (nc + ct_e - 1) / ct_e;
   const int leaf0 = t.level_off[L];
+  // FP32 pass: P2M and M2M on the tensor cores too (P2M reuses the
+  // transposed-X image that the near field just packed).  L2L and L2P stay on
+  // the CUDA cores: one pair per target, where the tensor-core pipeline's
+  // per-CTA setup measured slower than the tiled kernels.
+  const bool tcm = sizeof(T) == 4 && tcm_usable(c, nc);
   ev = prof_begin(c, s);
-  if (sizeof(T) == 4 && nc >= 32 && ncoef <= 96)
+  if (tcm)
+    tc_p2m(c, nc, (float*)Mx, s);
+  else if (sizeof(T) == 4 && nc >= 32 && ncoef <= 96)
     k_p2m_tiled<6><<<dim3(nl, (nc + 63) / 64), 128, 0, s>>>(nc, ncoef, leaf0, c->d.leaf_first.p, c->d.leaf_count.p,
                                                             (const float*)mom, (const float*)X, (float*)Mx);
   else
@@ -854,7 +861,9 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   const bool tiled = xlate_tiled<T>(c, nc);
   for (int l = L - 1; l >= 2; --l) {
     int nbx = t.level_off[l + 1] - t.level_off[l];
-    if (tiled)
+    if (tcm)
+      tc_m2m(c, l, nc, (float*)Mx, s);
+    else if (tiled)
       launch_xlate<T>(nbx, t.level_off[l], nc, ncoef, c->d.box_child_ptr.p, c->d.box_iota.p, c->d.box_oct16.p, tm2m,
                       Mx, Mx, false, s);
     else
@@ -864,7 +873,7 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   {
     double nch = (double)(t.level_off[L + 1] - t.level_off[std::min(3, L + 1)]);
     double npar = (double)(t.level_off[L] - t.level_off[2]);
-    prof_end(c, s, ev, PH_M2M, std::max(0, L - 2), e2 * nch, (nch + npar) * ebytes);
+    prof_end(c, s, ev, PH_M2M, std::max(0, L - 2) * (tcm ? 2 : 1), e2 * nch, (nch + npar) * ebytes);
   }
   {
     int b0 = t.level_off[2];

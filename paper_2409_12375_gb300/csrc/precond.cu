@@ -336,31 +336,32 @@ __global__ void k_band_finish(int nf, int n, int b, cplx* __restrict__ fac, cplx
   if (fac32) facT32[rowg * rs32 + t] = make_float2((float)w.x, (float)w.y);
 }
 
-// S = Q_gg - Q_vg^T W, then S^-1 in place (Gauss-Jordan, partial pivoting); one warp per f
+// S = Q_gg - Q_vg^T W, then S^-1 in place (Gauss-Jordan, partial pivoting); one CTA per f
 __global__ void k_schur(int n, int ng, int nmat, const double* __restrict__ border_vg,
                         const double* __restrict__ border_gg, const cplx* __restrict__ zs,
                         const double* __restrict__ wp_f, const cplx* __restrict__ Wb, cplx* __restrict__ Sinv) {
   const int f = blockIdx.x;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __shared__ cplx A[kMaxBorder][2 * kMaxBorder];
   const cplx* z = zs + (size_t)f * nmat;
   const double wp = wp_f[f];
   const size_t vstride = (size_t)n * ng;
-  for (int g1 = 0; g1 < ng; ++g1)
-    for (int g2 = 0; g2 < ng; ++g2) {
-      cplx acc = make_double2(0, 0);
-      const cplx* w = Wb + ((size_t)f * ng + g2) * n;
-      for (int i = lane; i < n; i += 32)
-        acc = cadd(acc, cm(pencil(border_vg + (size_t)i * ng + g1, vstride, nmat, z, wp), w[i]));
-      acc = warp_sum(acc);
-      if (lane == 0) {
-        cplx q = pencil(border_gg + (size_t)g1 * ng + g2, (size_t)ng * ng, nmat, z, wp);
-        A[g1][g2] = csub(q, acc);
-        A[g1][ng + g2] = make_double2(g1 == g2 ? 1.0 : 0.0, 0.0);
-      }
+  // one (g1, g2) entry per warp at a time
+  for (int pr = warp; pr < ng * ng; pr += nw) {
+    const int g1 = pr / ng, g2 = pr % ng;
+    cplx acc = make_double2(0, 0);
+    const cplx* w = Wb + ((size_t)f * ng + g2) * n;
+    for (int i = lane; i < n; i += 32)
+      acc = cadd(acc, cm(pencil(border_vg + (size_t)i * ng + g1, vstride, nmat, z, wp), w[i]));
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      cplx q = pencil(border_gg + (size_t)g1 * ng + g2, (size_t)ng * ng, nmat, z, wp);
+      A[g1][g2] = csub(q, acc);
+      A[g1][ng + g2] = make_double2(g1 == g2 ? 1.0 : 0.0, 0.0);
     }
-  __syncwarp();
-  if (lane == 0) {
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     for (int cc = 0; cc < ng; ++cc) {
       int piv = cc;
       for (int r = cc + 1; r < ng; ++r)
@@ -1026,7 +1027,7 @@ void band_factor(xrl_ctx* c, BandWork& bw, const cplx* zs, const double* wp, cud
       launches += spike_stages<cplx>(c, bw, nf * ng, ng, 1, zs, wp, bw.fac.p, bw.facT.p, bw.Vsp.p, bw.Wsp.p,
                                      bw.R.p, bw.Wb.p, (size_t)n, bw.hb.p, nullptr, nullptr, nullptr, s);
     }
-    k_schur<<<nf, 32, 0, s>>>(n, ng, T.n_mat, c->d.border_vg.p, c->d.border_gg.p, zs, wp, bw.Wb.p, bw.Sinv.p);
+    k_schur<<<nf, 256, 0, s>>>(n, ng, T.n_mat, c->d.border_vg.p, c->d.border_gg.p, zs, wp, bw.Wb.p, bw.Sinv.p);
     ++launches;
   }
   prof_end(c, s, ev, PH_PREC, launches, 8.0 * nf * (double)n * b * b / 2.0, 16.0 * nf * (double)n * (b + 1) * 2.0);

@@ -132,8 +132,9 @@ __global__ void k_scatter(int B, int nsys, int nmat, const int32_t* __restrict__
     int r = br_pan[2 * b + side];
     if (r < 0) continue;
     const double* rho = br_rho + 6 * (size_t)b + 3 * side;
-    const cplx zd = cscale(zs[s * nmat + pan_mat[r]], 1.0 / area[r]);
-    const C z = cmk<C>((T)zd.x, (T)zd.y);
+    const cplx zd = zs[s * nmat + pan_mat[r]];
+    const T ia = (T)1 / (T)area[r];   // in the product's precision: no FP64 divide in the FP32 pass
+    const C z = cmk<C>((T)zd.x * ia, (T)zd.y * ia);
     const T* xr = X + (size_t)r * 6 * nsys + 6 * s;
     const T* yr = Y + (size_t)r * 6 * nsys + 6 * s;
     for (int t = 0; t < 3; ++t) {
@@ -171,34 +172,47 @@ __global__ void k_loop_reduce(int nloop, int nsys, int ncb, const int32_t* __res
   w[(size_t)s * nloop + l] = acc;
 }
 
-// The long rows: one CTA of 8 warps per (long row, 32 systems), warp k takes
-// entries q0 + k, q0 + k + 8, ...; partial sums combined in a fixed order.
-__global__ void __launch_bounds__(256) k_loop_reduce_long(int nloop, int nsys, int ncb,
-                                                          const int32_t* __restrict__ rows,
+// The long rows: kLongSeg CTAs of 8 warps per (long row, 32 systems), each
+// summing one segment of the row into part[row][seg][s]; k_loop_reduce_fin
+// adds the segments in a fixed order.
+constexpr int kLongSeg = 32;
+__global__ void __launch_bounds__(256) k_loop_reduce_long(int nsys, int ncb, const int32_t* __restrict__ rows,
                                                           const int32_t* __restrict__ m_ptr,
                                                           const int32_t* __restrict__ m_col,
                                                           const int8_t* __restrict__ m_val,
-                                                          const cplx* __restrict__ Vb, cplx* __restrict__ w) {
-  __shared__ cplx part[8][32];
-  const int l = rows[blockIdx.x];
+                                                          const cplx* __restrict__ Vb, cplx* __restrict__ part) {
+  __shared__ cplx red[8][32];
+  const int l = rows[blockIdx.x], seg = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.y * 32 + lane;
+  const int s = blockIdx.z * 32 + lane;
   const int q0 = m_ptr[l], q1 = m_ptr[l + 1];
+  const int len = (q1 - q0 + kLongSeg - 1) / kLongSeg;
+  const int a = q0 + seg * len, b = min(q1, a + len);
   cplx acc = make_double2(0, 0);
   if (s < nsys)
-    for (int q = q0 + warp; q < q1; q += 8) {
-      const int b = m_col[q];
-      if (b >= ncb) continue;
-      const cplx v = Vb[(size_t)b * nsys + s];
+    for (int q = a + warp; q < b; q += 8) {
+      const int br = m_col[q];
+      if (br >= ncb) continue;
+      const cplx v = Vb[(size_t)br * nsys + s];
       acc = m_val[q] > 0 ? cadd(acc, v) : csub(acc, v);
     }
-  part[warp][lane] = acc;
+  red[warp][lane] = acc;
   __syncthreads();
   if (warp == 0 && s < nsys) {
-    cplx t = part[0][lane];
-    for (int k = 1; k < 8; ++k) t = cadd(t, part[k][lane]);
-    w[(size_t)s * nloop + l] = t;
+    cplx t = red[0][lane];
+    for (int k = 1; k < 8; ++k) t = cadd(t, red[k][lane]);
+    part[((size_t)blockIdx.x * kLongSeg + seg) * nsys + s] = t;
   }
+}
+
+__global__ void k_loop_reduce_fin(int nloop, int nsys, int nlong, const int32_t* __restrict__ rows,
+                                  const cplx* __restrict__ part, cplx* __restrict__ w) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nlong * nsys) return;
+  const int r = e / nsys, s = e % nsys;
+  cplx t = make_double2(0, 0);
+  for (int k = 0; k < kLongSeg; ++k) t = cadd(t, part[((size_t)r * kLongSeg + k) * nsys + s]);
+  w[(size_t)s * nloop + rows[r]] = t;
 }
 
 // w = Q(f_s) v (mode 0) or diag(Q(f_s)) (mode 1, v unused)
@@ -620,9 +634,12 @@ static int loop_reduce(xrl_ctx* c, int nsys, const cplx* Vb, cplx* w, cudaStream
                                                                   c->d.m_col.p, c->d.m_val.p, Vb, w);
   const int nlong = (int)c->d.m_long.n;
   if (nlong == 0) return 1;
-  k_loop_reduce_long<<<dim3(nlong, sg), 256, 0, s>>>(T.n_loops, nsys, T.n_cb, c->d.m_long.p, c->d.m_ptr.p,
-                                                     c->d.m_col.p, c->d.m_val.p, Vb, w);
-  return 2;
+  c->d.m_long_part.ensure(c->alloc, (size_t)nlong * kLongSeg * nsys);
+  k_loop_reduce_long<<<dim3(nlong, kLongSeg, sg), 256, 0, s>>>(nsys, T.n_cb, c->d.m_long.p, c->d.m_ptr.p,
+                                                               c->d.m_col.p, c->d.m_val.p, Vb, c->d.m_long_part.p);
+  k_loop_reduce_fin<<<nblk((size_t)nlong * nsys), 256, 0, s>>>(T.n_loops, nsys, nlong, c->d.m_long.p,
+                                                              c->d.m_long_part.p, w);
+  return 3;
 }
 
 // Work arrays of one solve (device)

@@ -190,14 +190,17 @@ __global__ void k_tc_pack_b(int ncoef, int Kp, int Np, const double* __restrict_
   }
 }
 
-// Pair sources of one translation launch.
-//  * M2L (mode 0): targets are boxes b0 + blockIdx.x, pairs their V-list
-//    entries; A = the multipole image of the source box, B = the table of the
-//    pair's offset, K = Kp, N = NP; out[box][k][col], ncoef rows.
-//  * P2P (mode 1): targets are leaves blockIdx.x, pairs their U-list entries;
-//    A = the transposed-X image of the source leaf (K = its panel count padded
-//    to 16), B = the pair's near-matrix block (N = the target's panel count
-//    padded to 16); out = Y[panel][col], one row per target panel.
+// Pair sources of one tensor-core launch (D[col][n] = sum over pairs A B).
+//  * mode 0 (M2L, M2M, L2L): targets are boxes b0 + blockIdx.x with pairs
+//    [ptr[b], ptr[b+1]); A = the expansion image of box src[v] (tile ct),
+//    B = table off[v], K = Kp, N = NP; out[box][k][col], ncoef rows.
+//  * mode 1 (P2P): targets are leaves blockIdx.x with their U-list pairs; A =
+//    the transposed-X image of leaf src[v] (K = its panels padded to 16),
+//    B = the pair's near block (N = the target's panels padded to 16);
+//    out = Y[panel][col], one row per target panel.
+//  * mode 2 (P2M): target leaf L = blockIdx.x, one pair: A = leaf L's
+//    transposed-X image, B = its moment image (pair_boff[L]), N = NP;
+//    out[box b0 + L][k][col].
 struct XlPairs {
   int mode, b0, src0, nct, Kp, sum_pc, ncoef;
   size_t a_img, b_img;   // mode 0: bytes of one (box, tile) A image and of one table image
@@ -205,11 +208,11 @@ struct XlPairs {
   const int32_t* ptr;
   const int32_t* src;
   const int16_t* off;
-  const int32_t* leaf_a0;   // mode 1: padded panel offset of each leaf
-  const int32_t* leaf_pc;   // mode 1: padded panel count
-  const int32_t* leaf_f0;   // mode 1: first panel
-  const int32_t* leaf_n;    // mode 1: panel count
-  const int64_t* pair_boff; // mode 1: byte offset of each pair's B image
+  const int32_t* leaf_a0;   // padded panel offset of each leaf
+  const int32_t* leaf_pc;   // padded panel count
+  const int32_t* leaf_f0;   // first panel
+  const int32_t* leaf_n;    // panel count
+  const int64_t* pair_boff; // byte offset of each pair's (mode 1) or leaf's (mode 2) B image
 };
 
 __device__ __forceinline__ void xl_pair(const XlPairs& p, int v, int ct, size_t& aoff, size_t& boff, int& K) {
@@ -218,7 +221,7 @@ __device__ __forceinline__ void xl_pair(const XlPairs& p, int v, int ct, size_t&
     boff = (size_t)p.off[v] * p.b_img;
     K = p.Kp;
   } else {
-    const int S = p.src[v];
+    const int S = p.mode == 1 ? p.src[v] : v;
     aoff = ((size_t)ct * p.sum_pc + p.leaf_a0[S]) * (size_t)p.a_row_bytes;
     boff = (size_t)p.pair_boff[v];
     K = p.leaf_pc[S];
@@ -235,13 +238,20 @@ __device__ __forceinline__ void xl_target(const XlPairs& p, int NPmax, int& vs, 
     N = NPmax;
     nrows = p.ncoef;
     row0 = (size_t)Bx * p.ncoef;
-  } else {
+  } else if (p.mode == 1) {
     const int T = blockIdx.x;
     vs = p.ptr[T];
     ve = p.ptr[T + 1];
     nrows = p.leaf_n[T];
     N = (nrows + 15) & ~15;
     row0 = (size_t)p.leaf_f0[T];
+  } else {
+    const int L = blockIdx.x;
+    vs = L;
+    ve = L + 1;
+    N = NPmax;
+    nrows = p.ncoef;
+    row0 = (size_t)(p.b0 + L) * p.ncoef;
   }
 }
 
@@ -893,6 +903,33 @@ __global__ void k_ozp_pack_v(const int32_t* __restrict__ pair_tgt, const int32_t
   }
 }
 
+// Moment images of the leaves for P2M on the tensor cores (mode 2), from the
+// FP64 moments S[panel][k] in 3 BF16 pieces: rows n = coefficients (Np),
+// K = the leaf's panels padded to 16, value S[f0 + k][n].
+__device__ __forceinline__ void put3(char* dst, size_t o0, size_t o1, size_t o2, double x) {
+  const uint16_t b0 = bf16_bits(__double2float_rn(x));
+  const double r1 = x - (double)bf16_val(b0);
+  const uint16_t b1 = bf16_bits(__double2float_rn(r1));
+  const uint16_t b2 = bf16_bits(__double2float_rn(r1 - (double)bf16_val(b1)));
+  *reinterpret_cast<uint16_t*>(dst + o0) = b0;
+  *reinterpret_cast<uint16_t*>(dst + o1) = b1;
+  *reinterpret_cast<uint16_t*>(dst + o2) = b2;
+}
+
+__global__ void k_tcm_pack_p2m(int ncoef, int Np, const int32_t* __restrict__ leaf_f0,
+                               const int32_t* __restrict__ leaf_n, const int32_t* __restrict__ leaf_pc,
+                               const int64_t* __restrict__ boff, const double* __restrict__ S,
+                               uint16_t* __restrict__ img) {
+  const int L = blockIdx.x;
+  const int f0 = leaf_f0[L], n = leaf_n[L], pc = leaf_pc[L];
+  char* dst = reinterpret_cast<char*>(img) + boff[L];
+  for (int e = threadIdx.x; e < Np * pc; e += blockDim.x) {
+    const int r = e % Np, k = e / Np;
+    const double x = (r < ncoef && k < n) ? S[(size_t)(f0 + k) * ncoef + r] : 0.0;
+    put3(dst, tc_img_off(Np, pc, r, k, 0), tc_img_off(Np, pc, r, k, 1), tc_img_off(Np, pc, r, k, 2), x);
+  }
+}
+
 // ---- host side ---------------------------------------------------------------------------
 
 static int tc_kpad(int ncoef) { return (ncoef + 15) & ~15; }
@@ -1007,6 +1044,28 @@ static void tcp_prepare(xrl_ctx* c) {
   XRL_CUDA(cudaGetLastError());
 }
 
+// Images of the upward pass of the FP32 product (the 8 M2M tables, the
+// leaves' P2M moment images); needs the near-field layout of tcp_prepare.
+static void tcm_prepare(xrl_ctx* c) {
+  const Tree& t = c->tree;
+  const int ncoef = c->ncoef, Kp = tc_kpad(ncoef), Np = tc_npad(ncoef);
+  const int nl = t.n_leaves();
+  c->d.tc_m2m_img.alloc(c->alloc, (size_t)8 * TC_PIECES * Np * Kp);
+  k_tc_pack_b<<<8, 256, 0, c->stream>>>(ncoef, Kp, Np, c->d.t_m2m.p, c->d.tc_m2m_img.p);
+  std::vector<int64_t> b2(nl);
+  int64_t o2 = 0;
+  for (int L = 0; L < nl; ++L) {
+    const int n = t.leaf_count[L], pc = (n + 15) & ~15;
+    b2[L] = o2;
+    o2 += (int64_t)TC_PIECES * 2 * Np * pc;
+  }
+  c->d.tcm_boff2.upload(c->alloc, b2);
+  c->d.tcm_p2m_img.alloc(c->alloc, (size_t)(o2 / 2));
+  k_tcm_pack_p2m<<<nl, 256, 0, c->stream>>>(ncoef, Np, c->d.leaf_first.p, c->d.leaf_count.p, c->d.tcp_pc.p,
+                                             c->d.tcm_boff2.p, c->d.mom.p, c->d.tcm_p2m_img.p);
+  XRL_CUDA(cudaGetLastError());
+}
+
 void tc_prepare(xrl_ctx* c) {
   const int ncoef = c->ncoef;
   if (c->opt.tensor_cores == 0) return;
@@ -1020,6 +1079,61 @@ void tc_prepare(xrl_ctx* c) {
   c->d.tc_bimg.alloc(c->alloc, (size_t)noff * TC_PIECES * Np * Kp);
   k_tc_pack_b<<<noff, 256, 0, c->stream>>>(ncoef, Kp, Np, c->d.t_m2l.p, c->d.tc_bimg.p);
   XRL_CUDA(cudaGetLastError());
+  if (c->d.tcp_vimg.n > 0) tcm_prepare(c);
+}
+
+bool tcm_usable(const xrl_ctx* c, int nc) {
+  return tc_usable(c, nc) && tcp_usable(c, nc) && c->d.tcm_p2m_img.n > 0;
+}
+
+static void launch_tc_np(int Np, dim3 g, const TcArgs& a, cudaStream_t s) {
+  if (Np <= 64)
+    launch_tc<64>(g, a, s);
+  else
+    launch_tc<96>(g, a, s);
+}
+
+// M = S^T X for the leaves (mode 2); the transposed-X image of the near
+// field's pass (tc_p2p) must already hold this product's X.  One launch.
+void tc_p2m(xrl_ctx* c, int nc, float* Mx, cudaStream_t s) {
+  const Tree& t = c->tree;
+  const int nct = (nc + TC_ROWS - 1) / TC_ROWS;
+  TcArgs a;
+  a.pr = p2p_pairs(c, nct, TC_PIECES, c->d.tcm_boff2.p);
+  a.pr.mode = 2;
+  a.pr.b0 = t.level_off[t.L];
+  a.pr.ncoef = c->ncoef;
+  a.nc = nc;
+  a.aimg = reinterpret_cast<const char*>(c->d.tcp_ximg.p);
+  a.bimg = reinterpret_cast<const char*>(c->d.tcm_p2m_img.p);
+  a.out = Mx;
+  a.err = c->d.tc_err.p;
+  launch_tc_np(tc_npad(c->ncoef), dim3(t.n_leaves(), nct), a, s);
+}
+
+// one level of M2M (parents at level l from their children at l + 1): pack
+// the children's multipoles, then translate; two launches
+void tc_m2m(xrl_ctx* c, int l, int nc, float* Mx, cudaStream_t s) {
+  const Tree& t = c->tree;
+  const int ncoef = c->ncoef, Kp = tc_kpad(ncoef), Np = tc_npad(ncoef);
+  const int nct = (nc + TC_ROWS - 1) / TC_ROWS;
+  const int s0 = t.level_off[l + 1], ns = t.level_off[l + 2] - s0;
+  const int nt = t.level_off[l + 1] - t.level_off[l];
+  c->d.tc_aimg.ensure(c->alloc, (size_t)ns * nct * TC_PIECES * TC_ROWS * Kp);
+  k_tc_pack_a<<<dim3(ns, nct), 256, 0, s>>>(nc, ncoef, Kp, s0, Mx, c->d.tc_aimg.p);
+  TcArgs a;
+  a.pr = m2l_pairs(c, t.level_off[l], nct, TC_PIECES, (size_t)TC_PIECES * 2 * TC_ROWS * Kp,
+                   (size_t)TC_PIECES * 2 * Np * Kp);
+  a.pr.src0 = s0;
+  a.pr.ptr = c->d.box_child_ptr.p;
+  a.pr.src = c->d.box_iota.p;
+  a.pr.off = c->d.box_oct16.p;
+  a.nc = nc;
+  a.aimg = reinterpret_cast<const char*>(c->d.tc_aimg.p);
+  a.bimg = reinterpret_cast<const char*>(c->d.tc_m2m_img.p);
+  a.out = Mx;
+  a.err = c->d.tc_err.p;
+  launch_tc_np(Np, dim3(nt, nct), a, s);
 }
 
 // M2L of the FP32 pass: in = M, out = L over all target boxes [b0, b0 + nbx);
@@ -1039,10 +1153,7 @@ void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cud
   a.bimg = reinterpret_cast<const char*>(c->d.tc_bimg.p);
   a.out = Lx;
   a.err = c->d.tc_err.p;
-  if (Np <= 64)
-    launch_tc<64>(dim3(nbx, nct), a, s);
-  else
-    launch_tc<96>(dim3(nbx, nct), a, s);
+  launch_tc_np(Np, dim3(nbx, nct), a, s);
 }
 
 bool tc64_usable(const xrl_ctx* c, int nc) {

@@ -206,6 +206,9 @@ struct Dev {
   DBuf<int64_t> tcp_boff, ozp_boff;     // per U-list pair: byte offset of its near-block image
   DBuf<uint16_t> tcp_vimg, ozp_vimg;    // near-block images (3 BF16 pieces; 5 integer slices)
   DBuf<uint16_t> tcp_ximg, ozp_ximg;    // transposed-X images, per product
+  DBuf<uint16_t> tc_m2m_img;   // BF16-piece images of the 8 M2M tables
+  DBuf<int64_t> tcm_boff2;      // per leaf: byte offset of its P2M moment image
+  DBuf<uint16_t> tcm_p2m_img;   // leaf moment images (coefficients x panels)
   DBuf<int32_t> v_ptr32, v_src;
   DBuf<int16_t> v_off;
   DBuf<int32_t> lvl_boxes;                            // per level: global ids of its boxes (same as range)
@@ -221,6 +224,7 @@ struct Dev {
   DBuf<double> br_rho;       // [B][2][3]
   DBuf<int32_t> m_ptr, m_col, mt_ptr, mt_col;
   DBuf<int32_t> m_long;     // loop rows longer than the warp-per-row reduce takes
+  DBuf<double2> m_long_part; // their segment partial sums
   DBuf<int8_t> m_val, mt_val;
   DBuf<int32_t> q_ptr, q_col;
   DBuf<double> q_val;
@@ -333,6 +337,9 @@ bool tc64_usable(const xrl_ctx* c, int ncols);
 bool tcp_usable(const xrl_ctx* c, int ncols);
 void tc_p2p(xrl_ctx* c, int ncols, const float* X, float* Y, cudaStream_t s);
 void tc_p2p64(xrl_ctx* c, int ncols, const double* X, double* Y, cudaStream_t s);
+bool tcm_usable(const xrl_ctx* c, int ncols);
+void tc_p2m(xrl_ctx* c, int ncols, float* M, cudaStream_t s);
+void tc_m2m(xrl_ctx* c, int level, int ncols, float* M, cudaStream_t s);
 void tc_m2l64(xrl_ctx* c, int nbx, int b0, int ncols, const double* M, double* L, cudaStream_t s);
 // solve.cu
 void solver_prepare(xrl_ctx* c);
