@@ -567,6 +567,57 @@ __device__ void gj_inverse(C* A, int n, int lda, int* piv, C* colk, C* pinv_s) {
   }
 }
 
+// The same inverse by one warp for n <= 32: lane r owns row r in the
+// elimination, the lanes span the columns in the row swaps and the scaling;
+// warp-synchronous (no block barriers).  Called by warp 0 only.
+template <class C>
+__device__ void gj_inverse_warp(C* A, int n, int lda, int* piv) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < n; ++k) {
+    auto best = (lane >= k && lane < n) ? cabs2T(A[lane * lda + k]) : decltype(cabs2T(A[0]))(-1);
+    int idx = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const auto ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (ob > best || (ob == best && oi < idx)) {
+        best = ob;
+        idx = oi;
+      }
+    }
+    const int p = idx;
+    if (lane == 0) piv[k] = p;
+    if (p != k)
+      for (int cc = lane; cc < n; cc += 32) {
+        C t = A[k * lda + cc];
+        A[k * lda + cc] = A[p * lda + cc];
+        A[p * lda + cc] = t;
+      }
+    __syncwarp();
+    const C pinv = crecipT(A[k * lda + k]);
+    const C colk = lane < n ? A[lane * lda + k] : czero<C>();
+    __syncwarp();
+    for (int cc = lane; cc < n; cc += 32) A[k * lda + cc] = cmul(cc == k ? cone<C>() : A[k * lda + cc], pinv);
+    __syncwarp();
+    if (lane < n && lane != k)
+      for (int cc = 0; cc < n; ++cc) {
+        const C a = cc == k ? czero<C>() : A[lane * lda + cc];
+        A[lane * lda + cc] = csubT(a, cmul(A[k * lda + cc], colk));
+      }
+    __syncwarp();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int r = lane; r < n; r += 32) {
+        C t = A[r * lda + k];
+        A[r * lda + k] = A[r * lda + p];
+        A[r * lda + p] = t;
+      }
+    __syncwarp();
+  }
+}
+
 // Block LU of the reduced system, one CTA per frequency, sequential over j:
 // record R[f][j] (6 b^2 elements) = [E^_j^-1 (2b x 2b, column-major) |
 // W_j^bot ([c][r], zero for j = 0) | V_{j+1}^top ([c][r], zero for j = P-2)],
@@ -575,9 +626,9 @@ template <class C>
 __global__ void k_spike_reduce(int ns, int b, int P, int m, const C* __restrict__ Vsp, const C* __restrict__ Wsp,
                                C* __restrict__ R) {
   extern __shared__ __align__(16) unsigned char rsm_raw[];
-  C* E = reinterpret_cast<C*>(rsm_raw);   // [B2][B2]
-  const int B2 = 2 * b;
-  C* X01 = E + B2 * B2;        // [b][b] top-right block of the previous inverse
+  C* E = reinterpret_cast<C*>(rsm_raw);   // [B2][B2 + 1]: odd row stride, no bank conflicts by row
+  const int B2 = 2 * b, ld = 2 * b + 1;
+  C* X01 = E + B2 * ld;        // [b][b] top-right block of the previous inverse
   C* T = X01 + b * b;          // [b][b]
   C* colk = T + b * b;         // [B2]
   C* pinv = colk + B2;         // [1]
@@ -593,7 +644,7 @@ __global__ void k_spike_reduce(int ns, int b, int P, int m, const C* __restrict_
       C v = r == cc ? cone<C>() : czero<C>();
       if (r < b && cc >= b) v = V[(size_t)(cc - b) * ns + e - b + r];
       if (r >= b && cc < b) v = W[(size_t)cc * ns + e + (r - b)];
-      E[q] = v;
+      E[r * ld + cc] = v;
     }
     if (j > 0) {
       // T = X01 V_j^top, then E_tr -= W_j^bot T
@@ -608,22 +659,27 @@ __global__ void k_spike_reduce(int ns, int b, int P, int m, const C* __restrict_
         const int r = q / b, cc = q % b;
         C acc = czero<C>();
         for (int k = 0; k < b; ++k) acc = cfma(W[(size_t)k * ns + e - b + r], T[k * b + cc], acc);
-        E[r * B2 + b + cc] = csubT(E[r * B2 + b + cc], acc);
+        E[r * ld + b + cc] = csubT(E[r * ld + b + cc], acc);
       }
     }
     __syncthreads();
-    gj_inverse<C>(E, B2, B2, piv, colk, pinv);
+    if (B2 <= 32) {
+      if (tid < 32) gj_inverse_warp<C>(E, B2, ld, piv);
+      __syncthreads();
+    } else {
+      gj_inverse<C>(E, B2, ld, piv, colk, pinv);
+    }
     C* out = R + ((size_t)f * (P - 1) + j) * RS;
     for (int q = tid; q < B2 * B2; q += nt) {
       const int r = q / B2, cc = q % B2;
-      out[(size_t)cc * B2 + r] = E[q];
+      out[(size_t)cc * B2 + r] = E[r * ld + cc];
     }
     for (int q = tid; q < b * b; q += nt) {
       const int cc = q / b, r = q % b;
       out[(size_t)4 * b * b + q] = j > 0 ? W[(size_t)cc * ns + e - b + r] : czero<C>();
       out[(size_t)5 * b * b + q] = j + 2 < P ? V[(size_t)cc * ns + e + r] : czero<C>();
     }
-    for (int q = tid; q < b * b; q += nt) X01[q] = E[(q / b) * B2 + b + q % b];
+    for (int q = tid; q < b * b; q += nt) X01[q] = E[(q / b) * ld + b + q % b];
     __syncthreads();
   }
 }
@@ -684,31 +740,47 @@ __device__ __forceinline__ void warp_copy_async(void* dst, const void* src, size
 }
 
 // Stage 2: the reduced block-tridiagonal system for z_j = (u_j, t_{j+1}),
-// forward then backward; one warp per system, h[s][j][2b] holds h_j and then
-// z_j.  The records R[f][j] stream through a double buffer in shared memory.
-template <class C>
+// forward then backward; one warp per system.  All interface rows of x and
+// h_j (then z_j) live in shared memory (h is written to hb[s][j][2b] at the
+// end); the records R[f][j] stream through a ring of kZDepth buffers with
+// cp.async (one commit group per step, empty at the tail), so a step waits on
+// shared memory only.  kZDepth = 4, or 2 where four records do not fit.
+template <class C, int kZDepth>
 __global__ void k_spike_z(int n, int b, int P, int m, int nper, const C* __restrict__ R, const C* __restrict__ xb,
                           size_t xs, C* __restrict__ hb, const int* __restrict__ active) {
   extern __shared__ __align__(16) unsigned char zsm_raw[];
-  C* rbuf = reinterpret_cast<C*>(zsm_raw);   // [2][6 b^2]
-  __shared__ C g[64], hp[32], tt[32];
+  const int B2 = 2 * b;
+  const size_t RS = (size_t)6 * b * b;
+  C* rbuf = reinterpret_cast<C*>(zsm_raw);   // [kZDepth][6 b^2]
+  C* hs = rbuf + kZDepth * RS;               // [(P-1)][2b]
+  C* gs = hs + (size_t)(P - 1) * B2;         // [(P-1)][2b] interface rows of x
+  __shared__ C hp[32], tt[32];
   const int s = blockIdx.x;
   if (P < 2 || (active && !active[s])) return;
-  const int f = s / nper, lane = threadIdx.x, B2 = 2 * b;
-  const size_t RS = (size_t)6 * b * b;
-  const C* Rf = R + (size_t)f * (P - 1) * RS;
+  const int f = s / nper, lane = threadIdx.x;
+  const int nst = P - 1;
+  const C* Rf = R + (size_t)f * nst * RS;
   const C* x = xb + (size_t)s * xs;
-  C* h = hb + (size_t)s * (P - 1) * B2;
-  warp_copy_async(rbuf, Rf, RS * sizeof(C));
-  for (int j = 0; j + 1 < P; ++j) {
-    const bool more = j + 2 < P;
-    if (more) warp_copy_async(rbuf + ((j + 1) & 1) * RS, Rf + (size_t)(j + 1) * RS, RS * sizeof(C));
-    const int e = (j + 1) * m;
-    for (int r = lane; r < B2; r += 32) g[r] = x[e - b + r];
-    if (more) cp_wait_all_but_one(); else cp_wait_all();
+  C* h = hb + (size_t)s * nst * B2;
+  // forward records 0 .. kZDepth-2 in flight, one group each
+  for (int q = 0; q < kZDepth - 1; ++q) {
+    if (q < nst) warp_copy_async(rbuf + (size_t)(q % kZDepth) * RS, Rf + (size_t)q * RS, RS * sizeof(C));
+    else cp_commit();
+  }
+  for (int e = lane; e < nst * B2; e += 32) {
+    const int j = e / B2, r = e % B2;
+    gs[e] = x[(j + 1) * m - b + r];
+  }
+  for (int j = 0; j < nst; ++j) {
+    // keep kZDepth - 1 groups ahead: issue record j + kZDepth - 1 (or an empty group)
+    const int jn = j + kZDepth - 1;
+    if (jn < nst) warp_copy_async(rbuf + (size_t)(jn % kZDepth) * RS, Rf + (size_t)jn * RS, RS * sizeof(C));
+    else cp_commit();
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kZDepth - 1) : "memory");
     __syncwarp();
-    const C* Ej = rbuf + (j & 1) * RS;
+    const C* Ej = rbuf + (size_t)(j % kZDepth) * RS;
     const C* Wj = Ej + 4 * b * b;
+    C* g = gs + j * B2;
     if (j > 0)
       for (int r = lane; r < b; r += 32) {
         C acc = czero<C>();
@@ -717,36 +789,62 @@ __global__ void k_spike_z(int n, int b, int P, int m, int nper, const C* __restr
       }
     __syncwarp();
     for (int r = lane; r < B2; r += 32) {
-      C acc = czero<C>();
-      for (int c = 0; c < B2; ++c) acc = cfma(Ej[c * B2 + r], g[c], acc);
-      h[(size_t)j * B2 + r] = acc;
+      C a0 = czero<C>(), a1 = czero<C>(), a2 = czero<C>(), a3 = czero<C>();
+      int c = 0;
+      for (; c + 4 <= B2; c += 4) {
+        a0 = cfma(Ej[c * B2 + r], g[c], a0);
+        a1 = cfma(Ej[(c + 1) * B2 + r], g[c + 1], a1);
+        a2 = cfma(Ej[(c + 2) * B2 + r], g[c + 2], a2);
+        a3 = cfma(Ej[(c + 3) * B2 + r], g[c + 3], a3);
+      }
+      for (; c < B2; ++c) a0 = cfma(Ej[c * B2 + r], g[c], a0);
+      const C acc = caddT(caddT(a0, a1), caddT(a2, a3));
+      hs[j * B2 + r] = acc;
       if (r < b) hp[r] = acc;
     }
     __syncwarp();
   }
-  if (P < 3) return;
-  warp_copy_async(rbuf, Rf + (size_t)(P - 3) * RS, RS * sizeof(C));
-  for (int j = P - 3, q = 0; j >= 0; --j, ++q) {
-    const bool more = j > 0;
-    if (more) warp_copy_async(rbuf + ((q + 1) & 1) * RS, Rf + (size_t)(j - 1) * RS, RS * sizeof(C));
-    for (int r = lane; r < b; r += 32) g[r] = h[(size_t)(j + 1) * B2 + b + r];
-    if (more) cp_wait_all_but_one(); else cp_wait_all();
-    __syncwarp();
-    const C* Ej = rbuf + (q & 1) * RS;
-    const C* Vt = Ej + 5 * b * b;
-    for (int r = lane; r < b; r += 32) {
-      C acc = czero<C>();
-      for (int c = 0; c < b; ++c) acc = cfma(Vt[c * b + r], g[c], acc);
-      tt[r] = acc;
+  cp_wait_all();
+  __syncwarp();
+  if (nst >= 2) {
+    // backward over j = nst - 2 .. 0 (record j), the same ring
+    const int nb = nst - 1;
+    for (int q = 0; q < kZDepth - 1; ++q) {
+      if (q < nb) warp_copy_async(rbuf + (size_t)(q % kZDepth) * RS, Rf + (size_t)(nb - 1 - q) * RS, RS * sizeof(C));
+      else cp_commit();
     }
-    __syncwarp();
-    for (int r = lane; r < B2; r += 32) {
-      C acc = czero<C>();
-      for (int c = 0; c < b; ++c) acc = cfma(Ej[(size_t)(b + c) * B2 + r], tt[c], acc);
-      h[(size_t)j * B2 + r] = csubT(h[(size_t)j * B2 + r], acc);
+    for (int q = 0; q < nb; ++q) {
+      const int j = nb - 1 - q;
+      const int qn = q + kZDepth - 1;
+      if (qn < nb) warp_copy_async(rbuf + (size_t)(qn % kZDepth) * RS, Rf + (size_t)(nb - 1 - qn) * RS, RS * sizeof(C));
+      else cp_commit();
+      asm volatile("cp.async.wait_group %0;\n" ::"n"(kZDepth - 1) : "memory");
+      __syncwarp();
+      const C* Ej = rbuf + (size_t)(q % kZDepth) * RS;
+      const C* Vt = Ej + 5 * b * b;
+      const C* zn = hs + (j + 1) * B2 + b;
+      for (int r = lane; r < b; r += 32) {
+        C acc = czero<C>();
+        for (int c = 0; c < b; ++c) acc = cfma(Vt[c * b + r], zn[c], acc);
+        tt[r] = acc;
+      }
+      __syncwarp();
+      for (int r = lane; r < B2; r += 32) {
+        C a0 = czero<C>(), a1 = czero<C>();
+        int c = 0;
+        for (; c + 2 <= b; c += 2) {
+          a0 = cfma(Ej[(size_t)(b + c) * B2 + r], tt[c], a0);
+          a1 = cfma(Ej[(size_t)(b + c + 1) * B2 + r], tt[c + 1], a1);
+        }
+        for (; c < b; ++c) a0 = cfma(Ej[(size_t)(b + c) * B2 + r], tt[c], a0);
+        hs[j * B2 + r] = csubT(hs[j * B2 + r], caddT(a0, a1));
+      }
+      __syncwarp();
     }
-    __syncwarp();
+    cp_wait_all();
   }
+  __syncwarp();
+  for (int e = lane; e < nst * B2; e += 32) h[e] = hs[e];
 }
 
 constexpr int kSpikeRows = 1024;   // rows per CTA of the correction kernels
@@ -943,10 +1041,18 @@ static int spike_stages(xrl_ctx* c, const BandWork& bw, int nsys, int nper, int 
                                                               facT, v, xb, xs, active);
   ++launches;
   if (P > 1) {
-    const size_t zsm = sizeof(C) * 2 * (size_t)6 * b * b;
-    if (zsm > 48 * 1024)
-      XRL_CUDA(cudaFuncSetAttribute(k_spike_z<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm));
-    k_spike_z<C><<<nsys, 32, zsm, s>>>(n, b, P, m, nper, R, xb, xs, hb, active);
+    const size_t rec = sizeof(C) * (size_t)6 * b * b, side = sizeof(C) * 2 * (size_t)(P - 1) * 2 * b;
+    const bool deep = 4 * rec + side <= 200 * 1024;
+    const size_t zsm = (deep ? 4 : 2) * rec + side;
+    if (deep) {
+      if (zsm > 48 * 1024)
+        XRL_CUDA(cudaFuncSetAttribute(k_spike_z<C, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm));
+      k_spike_z<C, 4><<<nsys, 32, zsm, s>>>(n, b, P, m, nper, R, xb, xs, hb, active);
+    } else {
+      if (zsm > 48 * 1024)
+        XRL_CUDA(cudaFuncSetAttribute(k_spike_z<C, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm));
+      k_spike_z<C, 2><<<nsys, 32, zsm, s>>>(n, b, P, m, nper, R, xb, xs, hb, active);
+    }
     ++launches;
   }
   if (P > 1 || (mode == 0 && ng > 0)) {
@@ -984,7 +1090,7 @@ static int spike_factor(xrl_ctx* c, BandWork& bw, const cplx* zs, const double* 
     XRL_CUDA(cudaFuncSetAttribute(k_spike_cols<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsd));
   k_spike_cols<C><<<nf * P * 2 * b, 32, bsd, s>>>(n, (int)ns, b, P, m, T.n_mat, c->d.band_val.p, zs, wp, fac,
                                                   facT, Vsp, Wsp);
-  const size_t rsm = sizeof(C) * ((size_t)4 * b * b + 2 * (size_t)b * b + 2 * b + 1) + sizeof(int) * 2 * b;
+  const size_t rsm = sizeof(C) * ((size_t)2 * b * (2 * b + 1) + 2 * (size_t)b * b + 2 * b + 1) + sizeof(int) * 2 * b;
   if (rsm > 48 * 1024)
     XRL_CUDA(cudaFuncSetAttribute(k_spike_reduce<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
   k_spike_reduce<C><<<nf, 256, rsm, s>>>((int)ns, b, P, m, Vsp, Wsp, R);
