@@ -4,12 +4,15 @@
 Workload (default): two stacked 4-turn square planar copper coils, about
 25,000 triangles, 2 ports x 32 log-spaced frequencies from 100 Hz to 10 GHz,
 all 64 (frequency, port) systems solved as one multi-RHS block to a relative
-residual of 1e-8.  One STEP = one full sweep (FMM products, preconditioner,
+residual of 1e-8.  The FMM's leaf size and order come from the library's
+autotuner (untimed, before the warm-up): the fastest inner product whose FP64
+product stays within 1e-6 of the direct sum.  One STEP = one full sweep (FMM products, preconditioner,
 FGMRES, port reduction to R and L).  The metric is seconds per
 (frequency, port) solve (lower is better); FMM product throughput in
 panel-columns per second is reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                  [--no-autotune --fmm-order P --leaf-target L]
   python bench.py --impl reference     # the CPU oracle on a bounded sample
 
 Under torchrun each rank solves its own frequency chunk of an N-times longer
@@ -42,6 +45,12 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--fmm-order", type=int, default=7,
+                    help="expansion order p of the FMM with --no-autotune (7: the autotuner's choice here)")
+    ap.add_argument("--leaf-target", type=int, default=32, help="target panels per octree leaf")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use --fmm-order/--leaf-target as given instead of xrl_autotune's choice (FP64 product "
+                         "within 1e-6 of the direct sum, fastest inner product at the sweep's column count)")
     ap.add_argument("--kernel-case", action="store_true",
                     help="profiling case: only the FMM products of one sweep's launch configuration "
                          "(FP32 inner product and the mixed mode's FP64 residual operator, 64 systems), 3 each")
@@ -265,7 +274,7 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- profiling case
-def kernel_case():
+def kernel_case(args):
     """The bench workload's context and its two product kinds at the solver's
     launch configuration (384 columns = 64 systems x 6), a few GB on the device:
     3 FP32 FMM products (tensor-core M2L, FP32 near field) and 3 applications of
@@ -274,7 +283,7 @@ def kernel_case():
     import torch
     import paper_2409_12375_gb300 as pkg
     m = workload(0, 1)
-    x = pkg.XRL.from_mesh(m, fmm_order=8, separation=2, leaf_target=32, precision=1)
+    x = pkg.XRL.from_mesh(m, fmm_order=args.fmm_order, separation=2, leaf_target=args.leaf_target, precision=1)
     nsys = len(m.freqs) * len(m.ports)
     g = torch.Generator(device="cuda").manual_seed(1)
     xv = torch.randn(6 * nsys, m.n_tri, device="cuda", dtype=torch.float32, generator=g)
@@ -300,7 +309,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.kernel_case:
-        return kernel_case()
+        return kernel_case(args)
     import torch
     import torch.distributed as dist
 
@@ -317,9 +326,14 @@ def main():
             dist.barrier()
 
     m = workload(rank, world)
-    opts = dict(fmm_order=8, separation=2, leaf_target=32, device=local,
+    opts = dict(fmm_order=args.fmm_order, separation=2, leaf_target=args.leaf_target, device=local,
                 precision=1 if args.precision == "mixed" else 0)
     x = pkg.XRL.from_mesh(m, **opts)
+    tuned = None
+    if not args.no_autotune:
+        leaf, order, ms, err = x.autotune(6 * len(m.freqs) * len(m.ports), 1e-6, opts["precision"])
+        opts["leaf_target"], opts["fmm_order"] = leaf, order
+        tuned = {"leaf_target": leaf, "fmm_order": order, "product_ms": ms, "product_err": err}
     st = x.stats()
     ext = torch.cuda.ExternalStream(x.stream_handle())
     nsys = len(m.freqs) * len(m.ports)
@@ -409,7 +423,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32/f64 mixed (FP32 FMM in FP64 FGMRES-IR)" if args.precision == "mixed" else "f64",
-                "data": "synthetic", "config": config_dict(m, args.precision, opts),
+                "data": "synthetic", "config": dict(config_dict(m, args.precision, opts), autotune=tuned),
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * len(m.freqs),
                         "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * 4},
                 "gpu_launches": launches, "clocks": ck, "roofline": roof, "roofline_phases": roofs, "cpu_baseline": cb,

@@ -191,14 +191,17 @@ __global__ void k_tc_pack_b(int ncoef, int Kp, int Np, const double* __restrict_
 }
 
 // Pair sources of one tensor-core launch (D[col][n] = sum over pairs A B).
-//  * mode 0 (M2L, M2M, L2L): targets are boxes b0 + blockIdx.x with pairs
+// Grids are (column tile, target): the tiles of one target are issued side by
+// side, so the operand both share (the table or the near block) is fetched
+// from DRAM once and served from L2 to the others.
+//  * mode 0 (M2L, M2M, L2L): targets are boxes b0 + blockIdx.y with pairs
 //    [ptr[b], ptr[b+1]); A = the expansion image of box src[v] (tile ct),
 //    B = table off[v], K = Kp, N = NP; out[box][k][col], ncoef rows.
-//  * mode 1 (P2P): targets are leaves blockIdx.x with their U-list pairs; A =
+//  * mode 1 (P2P): targets are leaves blockIdx.y with their U-list pairs; A =
 //    the transposed-X image of leaf src[v] (K = its panels padded to 16),
 //    B = the pair's near block (N = the target's panels padded to 16);
 //    out = Y[panel][col], one row per target panel.
-//  * mode 2 (P2M): target leaf L = blockIdx.x, one pair: A = leaf L's
+//  * mode 2 (P2M): target leaf L = blockIdx.y, one pair: A = leaf L's
 //    transposed-X image, B = its moment image (pair_boff[L]), N = NP;
 //    out[box b0 + L][k][col].
 struct XlPairs {
@@ -232,21 +235,21 @@ __device__ __forceinline__ void xl_pair(const XlPairs& p, int v, int ct, size_t&
 __device__ __forceinline__ void xl_target(const XlPairs& p, int NPmax, int& vs, int& ve, int& N, int& nrows,
                                           size_t& row0) {
   if (p.mode == 0) {
-    const int Bx = p.b0 + blockIdx.x;
+    const int Bx = p.b0 + blockIdx.y;
     vs = p.ptr[Bx];
     ve = p.ptr[Bx + 1];
     N = NPmax;
     nrows = p.ncoef;
     row0 = (size_t)Bx * p.ncoef;
   } else if (p.mode == 1) {
-    const int T = blockIdx.x;
+    const int T = blockIdx.y;
     vs = p.ptr[T];
     ve = p.ptr[T + 1];
     nrows = p.leaf_n[T];
     N = (nrows + 15) & ~15;
     row0 = (size_t)p.leaf_f0[T];
   } else {
-    const int L = blockIdx.x;
+    const int L = blockIdx.y;
     vs = L;
     ve = L + 1;
     N = NPmax;
@@ -266,6 +269,28 @@ struct TcArgs {
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(b)) : "memory");
+}
+
+// acc[n] += both accumulators of one pair buffer (small first), columns n < NL
+template <int NP, int NL>
+__device__ __forceinline__ void drain_pair(float (&acc)[NP], uint32_t taddr) {
+#pragma unroll
+  for (int s = 1; s >= 0; --s) {
+    uint32_t r[NL];
+#pragma unroll
+    for (int n0 = 0; n0 < NL; n0 += 16)
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+          "[%16];"
+          : "=r"(r[n0 + 0]), "=r"(r[n0 + 1]), "=r"(r[n0 + 2]), "=r"(r[n0 + 3]), "=r"(r[n0 + 4]), "=r"(r[n0 + 5]),
+            "=r"(r[n0 + 6]), "=r"(r[n0 + 7]), "=r"(r[n0 + 8]), "=r"(r[n0 + 9]), "=r"(r[n0 + 10]), "=r"(r[n0 + 11]),
+            "=r"(r[n0 + 12]), "=r"(r[n0 + 13]), "=r"(r[n0 + 14]), "=r"(r[n0 + 15])
+          : "r"(taddr + 128u * s + (uint32_t)n0)
+          : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int n = 0; n < NL; ++n) acc[n] += __uint_as_float(r[n]);
+  }
 }
 
 // Warps: 0 = bulk-copy producer (lane 0; the whole warp owns the TMEM
@@ -290,7 +315,7 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc(TcArgs a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
   int* bad = reinterpret_cast<int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ct = blockIdx.y;
+  const int ct = blockIdx.x;
   int vs, ve, N, nrows;
   size_t row0;
   xl_target(a.pr, NP, vs, ve, N, nrows, row0);
@@ -378,20 +403,23 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc(TcArgs a) {
           const uint32_t pa = TC_ROWS * kc * 2, pb = N * kc * 2;   // piece strides
           const uint32_t sbo = 16 * kc;                            // (kc / 8) cores of 128 B
           const uint32_t dbig = tbase + 256u * q, dsmall = dbig + 128u;
-          for (int ks = 0; ks < kc / 16; ++ks) {
-            uint64_t da[3], db[3];
+          // descriptors differ only in the start-address field (address >> 4,
+          // no carry below 256 KB): build two, offset the rest
+          const uint64_t dA = sdesc(sa, 128, sbo), dB = sdesc(sb, 128, sbo);
+          const uint64_t pa16 = pa >> 4, pb16 = pb >> 4;
 #pragma unroll
-            for (int h = 0; h < 3; ++h) {
-              da[h] = sdesc(sa + h * pa + 256 * ks, 128, sbo);
-              db[h] = sdesc(sb + h * pb + 256 * ks, 128, sbo);
-            }
+          for (int ks = 0; ks < TC_KC / 16; ++ks) {
+            if (ks * 16 >= kc) break;
+            const uint64_t k16 = 16u * ks;
+            const uint64_t a0 = dA + k16, a1 = a0 + pa16, a2 = a1 + pa16;
+            const uint64_t b0 = dB + k16, b1 = b0 + pb16, b2 = b1 + pb16;
             const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
-            mma_bf16(dbig, da[0], db[0], idesc, accum);
-            mma_bf16(dsmall, da[1], db[1], idesc, accum);
-            mma_bf16(dsmall, da[0], db[2], idesc, 1u);
-            mma_bf16(dsmall, da[2], db[0], idesc, 1u);
-            mma_bf16(dsmall, da[0], db[1], idesc, 1u);
-            mma_bf16(dsmall, da[1], db[0], idesc, 1u);
+            mma_bf16(dbig, a0, b0, idesc, accum);
+            mma_bf16(dsmall, a1, b1, idesc, accum);
+            mma_bf16(dsmall, a0, b2, idesc, 1u);
+            mma_bf16(dsmall, a2, b0, idesc, 1u);
+            mma_bf16(dsmall, a0, b1, idesc, 1u);
+            mma_bf16(dsmall, a1, b0, idesc, 1u);
           }
           tc_commit(&empty[st]);
           if (c == nchv - 1) tc_commit(&tfull[q]);
@@ -417,24 +445,11 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc(TcArgs a) {
         break;
       }
       tc_fence_after();
-#pragma unroll
-      for (int s = 1; s >= 0; --s) {
-        uint32_t r[NP];
-#pragma unroll
-        for (int n0 = 0; n0 < NP; n0 += 16)
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-              "[%16];"
-              : "=r"(r[n0 + 0]), "=r"(r[n0 + 1]), "=r"(r[n0 + 2]), "=r"(r[n0 + 3]), "=r"(r[n0 + 4]),
-                "=r"(r[n0 + 5]), "=r"(r[n0 + 6]), "=r"(r[n0 + 7]), "=r"(r[n0 + 8]), "=r"(r[n0 + 9]),
-                "=r"(r[n0 + 10]), "=r"(r[n0 + 11]), "=r"(r[n0 + 12]), "=r"(r[n0 + 13]), "=r"(r[n0 + 14]),
-                "=r"(r[n0 + 15])
-              : "r"(tbase + lane_base + 256u * q + 128u * s + (uint32_t)n0)
-              : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int n = 0; n < NP; ++n) acc[n] += __uint_as_float(r[n]);
-      }
+      if (NP > 64 && N <= 64)   // warp-uniform: only the columns this target's MMAs wrote
+        drain_pair<NP, 64>(acc, tbase + lane_base + 256u * q);
+      else
+        drain_pair<NP, NP>(acc, tbase + lane_base + 256u * q);
+
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tfree[q]);
@@ -568,11 +583,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 
 // Warps: 0 = bulk copies (lane 0; the whole warp owns TMEM), 1 = MMA issuer
 // (lane 0), 2..9 = epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and
-// outputs n in [48 h, 48 h + 48), h = (w - 2) / 4.  TMEM: class s at columns
-// 96 s (N = 96).  One accumulator set: the MMAs of pair j+1 start once every
+// outputs n in [NP/2 h, NP/2 (h + 1)), h = (w - 2) / 4.  TMEM: class s at
+// columns NP s (5 NP <= 480).  One accumulator set: the MMAs of pair j+1 start once every
 // epilogue warp has loaded pair j (tfree).
+template <int NP>
 __global__ void __launch_bounds__(320, 1) k_xlate_oz(OzArgs a) {
-  constexpr int NP = 96;
+  constexpr int NH = NP / 2;   // output columns per epilogue half
   extern __shared__ uint8_t oz_smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(oz_smem_raw) + 1023) & ~uintptr_t(1023));
   const int a_stage = oz_chunk_bytes(TC_ROWS, TC_KC, OZ_S);
@@ -585,7 +601,7 @@ __global__ void __launch_bounds__(320, 1) k_xlate_oz(OzArgs a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
   int* bad = reinterpret_cast<int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ct = blockIdx.y;
+  const int ct = blockIdx.x;
   int vs, ve, N, nrows;
   size_t row0;
   xl_target(a.pr, NP, vs, ve, N, nrows, row0);
@@ -668,19 +684,23 @@ __global__ void __launch_bounds__(320, 1) k_xlate_oz(OzArgs a) {
           const uint32_t sb = sa + a_stage;
           const uint32_t pa = TC_ROWS * kc * 2, pb = N * kc * 2;
           const uint32_t sbo = 16 * kc;
-          for (int ks = 0; ks < kc / 16; ++ks) {
+          const uint64_t dA = sdesc(sa, 128, sbo), dB = sdesc(sb, 128, sbo);
+          const uint64_t pa16 = pa >> 4, pb16 = pb >> 4;
+#pragma unroll
+          for (int ks = 0; ks < TC_KC / 16; ++ks) {
+            if (ks * 16 >= kc) break;
             uint64_t da[OZ_S], db[OZ_S];
 #pragma unroll
             for (int h = 0; h < OZ_S; ++h) {
-              da[h] = sdesc(sa + h * pa + 256 * ks, 128, sbo);
-              db[h] = sdesc(sb + h * pb + 256 * ks, 128, sbo);
+              da[h] = dA + 16u * ks + h * pa16;
+              db[h] = dB + 16u * ks + h * pb16;
             }
             const bool first = c == 0 && ks == 0;
 #pragma unroll
             for (int sc = 0; sc < OZ_S; ++sc)
 #pragma unroll
               for (int i = 0; i <= sc; ++i)
-                mma_bf16(tbase + 96u * sc, da[i], db[sc - i], idesc, (first && i == 0) ? 0u : 1u);
+                mma_bf16(tbase + (uint32_t)NP * sc, da[i], db[sc - i], idesc, (first && i == 0) ? 0u : 1u);
           }
           tc_commit(&empty[st]);
           if (c == nchv - 1) tc_commit(tfull);
@@ -693,9 +713,9 @@ __global__ void __launch_bounds__(320, 1) k_xlate_oz(OzArgs a) {
   } else {
     const int quarter = warp & 3, half = (warp - 2) >> 2;
     const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
-    float ah[48], al[48];
+    float ah[NH], al[NH];
 #pragma unroll
-    for (int n = 0; n < 48; ++n) ah[n] = al[n] = 0.f;
+    for (int n = 0; n < NH; ++n) ah[n] = al[n] = 0.f;
     for (int j = 0; j < nv; ++j) {
       bool ok = mbar_wait(tfull, j & 1);
       ok = __all_sync(0xffffffffu, ok);
@@ -705,17 +725,17 @@ __global__ void __launch_bounds__(320, 1) k_xlate_oz(OzArgs a) {
       }
       tc_fence_after();
 #pragma unroll
-      for (int n0 = 0; n0 < 48; n0 += 8) {
+      for (int n0 = 0; n0 < NH; n0 += 8) {
         uint32_t r[OZ_S][8];
 #pragma unroll
         for (int sc = 0; sc < OZ_S; ++sc)
           asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                        : "=r"(r[sc][0]), "=r"(r[sc][1]), "=r"(r[sc][2]), "=r"(r[sc][3]), "=r"(r[sc][4]),
                          "=r"(r[sc][5]), "=r"(r[sc][6]), "=r"(r[sc][7])
-                       : "r"(tbase + lane_base + 96u * sc + (uint32_t)(48 * half + n0))
+                       : "r"(tbase + lane_base + (uint32_t)NP * sc + (uint32_t)(NH * half + n0))
                        : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (n0 == 40) {
+        if (n0 == NH - 8) {
           // every value of this pair is in registers: let the next pair's MMAs start
           tc_fence_before();
           __syncwarp();
@@ -742,8 +762,8 @@ __global__ void __launch_bounds__(320, 1) k_xlate_oz(OzArgs a) {
     if (col < a.nc) {
       double* outp = a.out + row0 * a.nc + col;
 #pragma unroll
-      for (int q = 0; q < 48; ++q) {
-        const int n = 48 * half + q;
+      for (int q = 0; q < NH; ++q) {
+        const int n = NH * half + q;
         if (n < nrows) outp[(size_t)n * a.nc] = (double)ah[q] + (double)al[q];
       }
     }
@@ -983,15 +1003,23 @@ static void launch_tc(dim3 g, const TcArgs& a, cudaStream_t s) {
   k_xlate_tc<NP><<<g, 192, smem, s>>>(a);
 }
 
-static void launch_oz(dim3 g, const OzArgs& a, cudaStream_t s) {
+template <int NP>
+static void launch_oz_np(dim3 g, const OzArgs& a, cudaStream_t s) {
   const size_t smem =
-      (size_t)OZ_STAGES * (oz_chunk_bytes(TC_ROWS, TC_KC, OZ_S) + oz_chunk_bytes(96, TC_KC, OZ_S)) + 1024 + 128;
+      (size_t)OZ_STAGES * (oz_chunk_bytes(TC_ROWS, TC_KC, OZ_S) + oz_chunk_bytes(NP, TC_KC, OZ_S)) + 1024 + 128;
   static bool set = false;
   if (!set) {
-    XRL_CUDA(cudaFuncSetAttribute(k_xlate_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    XRL_CUDA(cudaFuncSetAttribute(k_xlate_oz<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     set = true;
   }
-  k_xlate_oz<<<g, 320, smem, s>>>(a);
+  k_xlate_oz<NP><<<g, 320, smem, s>>>(a);
+}
+
+static void launch_oz(int Np, dim3 g, const OzArgs& a, cudaStream_t s) {
+  if (Np <= 64)
+    launch_oz_np<64>(g, a, s);
+  else
+    launch_oz_np<96>(g, a, s);
 }
 
 // Near-field layout for the tensor cores: leaves padded to 16 panels, the
@@ -1108,7 +1136,7 @@ void tc_p2m(xrl_ctx* c, int nc, float* Mx, cudaStream_t s) {
   a.bimg = reinterpret_cast<const char*>(c->d.tcm_p2m_img.p);
   a.out = Mx;
   a.err = c->d.tc_err.p;
-  launch_tc_np(tc_npad(c->ncoef), dim3(t.n_leaves(), nct), a, s);
+  launch_tc_np(tc_npad(c->ncoef), dim3(nct, t.n_leaves()), a, s);
 }
 
 // one level of M2M (parents at level l from their children at l + 1): pack
@@ -1133,7 +1161,7 @@ void tc_m2m(xrl_ctx* c, int l, int nc, float* Mx, cudaStream_t s) {
   a.bimg = reinterpret_cast<const char*>(c->d.tc_m2m_img.p);
   a.out = Mx;
   a.err = c->d.tc_err.p;
-  launch_tc_np(Np, dim3(nt, nct), a, s);
+  launch_tc_np(Np, dim3(nct, nt), a, s);
 }
 
 // M2L of the FP32 pass: in = M, out = L over all target boxes [b0, b0 + nbx);
@@ -1153,17 +1181,17 @@ void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cud
   a.bimg = reinterpret_cast<const char*>(c->d.tc_bimg.p);
   a.out = Lx;
   a.err = c->d.tc_err.p;
-  launch_tc_np(Np, dim3(nbx, nct), a, s);
+  launch_tc_np(Np, dim3(nct, nbx), a, s);
 }
 
 bool tc64_usable(const xrl_ctx* c, int nc) {
-  return c->opt.tensor_cores != 0 && nc >= 64 && tc_npad(c->ncoef) == 96 && c->d.tc_err.n > 0;
+  return c->opt.tensor_cores != 0 && nc >= 64 && tc_npad(c->ncoef) <= 96 && c->d.tc_err.n > 0;
 }
 
 // FP64-accurate M2L of the refinement residuals (in = M, out = L, FP64)
 void tc_m2l64(xrl_ctx* c, int nbx, int b0, int nc, const double* Mx, double* Lx, cudaStream_t s) {
   const Tree& t = c->tree;
-  const int ncoef = c->ncoef, Kp = tc_kpad(ncoef), Np = 96;
+  const int ncoef = c->ncoef, Kp = tc_kpad(ncoef), Np = tc_npad(ncoef) <= 64 ? 64 : 96;
   const int nct = (nc + TC_ROWS - 1) / TC_ROWS;
   const int src0 = t.level_off[2];
   const int nsrc = t.n_boxes() - src0;
@@ -1191,7 +1219,7 @@ void tc_m2l64(xrl_ctx* c, int nbx, int b0, int nc, const double* Mx, double* Lx,
   a.bimg = reinterpret_cast<const char*>(c->d.oz_bimg.p);
   a.out = Lx;
   a.err = c->d.tc_err.p;
-  launch_oz(dim3(nbx, nct), a, s);
+  launch_oz(Np, dim3(nct, nbx), a, s);
 }
 
 bool tcp_usable(const xrl_ctx* c, int nc) {
@@ -1212,7 +1240,7 @@ void tc_p2p(xrl_ctx* c, int nc, const float* X, float* Y, cudaStream_t s) {
   a.bimg = reinterpret_cast<const char*>(c->d.tcp_vimg.p);
   a.out = Y;
   a.err = c->d.tc_err.p;
-  launch_tc<96>(dim3(nl, nct), a, s);
+  launch_tc<96>(dim3(nct, nl), a, s);
 }
 
 // FP64-accurate near field on the tensor cores (integer slices; two launches,
@@ -1238,7 +1266,7 @@ void tc_p2p64(xrl_ctx* c, int nc, const double* X, double* Y, cudaStream_t s) {
   a.bimg = reinterpret_cast<const char*>(c->d.ozp_vimg.p);
   a.out = Y;
   a.err = c->d.tc_err.p;
-  launch_oz(dim3(nl, nct), a, s);
+  launch_oz(96, dim3(nct, nl), a, s);
 }
 
 // raises XRL_ETIMEOUT if a tensor-core kernel gave up a wait since the last check

@@ -195,3 +195,20 @@ def test_fp32_tensor_core_m2l_full_size_coils(coils_ctx, coils_mesh, lib):
     e_sc = (np.linalg.norm(ys - y64, axis=1) / nrm).max()
     assert e_tc < 2e-5 and e_sc < 2e-5, (e_tc, e_sc)
     assert e_tc < 1.5 * e_sc, (e_tc, e_sc)
+
+
+@pytest.mark.parametrize("p", [6, 7])
+def test_fp32_product_lower_orders(lib, bar_mesh, bar_dense_P, p):
+    """Orders 6 and 7 (49 and 64 coefficients: the 64-wide tensor-core tiles)
+    at 200 columns: the FP32 product's error against the dense oracle exceeds
+    the same order's FP64 product error by at most the FP32 bound above."""
+    ctx = lib.XRL.from_mesh(bar_mesh, fmm_order=p)
+    try:
+        rng = np.random.default_rng(200 + p)
+        x = rng.standard_normal((200, bar_dense_P.shape[0])).astype(np.float32).astype(np.float64)
+        ref = x @ bar_dense_P.T
+        e64 = np.linalg.norm(ctx.fmm_mvm(x) - ref) / np.linalg.norm(ref)
+        e32 = np.linalg.norm(_fp32_product(ctx, x) - ref) / np.linalg.norm(ref)
+    finally:
+        ctx.close()
+    assert e64 < 1e-4 and e32 < e64 + FP32_TOL, (e64, e32)

@@ -91,18 +91,19 @@ def test_operator_matches_oracle(bar_ctx, bar_circ, bar_dense_P, f):
     assert err < 1e-6, err
 
 
-@pytest.mark.parametrize("nsys", [8, 16])
-def test_double_float_operator_matches_fp64(lib, coils_mesh_s, nsys):
+@pytest.mark.parametrize("nsys,p", [(8, 8), (16, 8), (16, 7)])
+def test_double_float_operator_matches_fp64(lib, coils_mesh_s, nsys, p):
     """The mixed mode's FP64 residual operator against the plain FP64 kernels
     on the coils.  At 8 systems (48 columns) the near field and translations
     run in double-float on the FP32 pipes (~2^-44 per operation); at 16 (96
     columns) the M2L runs on the tensor cores in 5 integer slices of 7 bits
-    (truncation ~2^-35 of max|M| max|T| per term).  Both evaluate the same FMM,
+    (truncation ~2^-35 of max|M| max|T| per term), with 96-wide tiles at order
+    8 and 64-wide ones at order 7.  Both evaluate the same FMM,
     so they agree far below the order-8 truncation (~1e-7) and the 1e-8
     residual target."""
     rng = np.random.default_rng(13)
-    a = lib.XRL.from_mesh(coils_mesh_s, precision=0)
-    b = lib.XRL.from_mesh(coils_mesh_s, precision=1)
+    a = lib.XRL.from_mesh(coils_mesh_s, precision=0, fmm_order=p)
+    b = lib.XRL.from_mesh(coils_mesh_s, precision=1, fmm_order=p)
     try:
         n = a.stats()["n_loops"]
         v = rng.standard_normal((nsys, n)) + 1j * rng.standard_normal((nsys, n))
@@ -157,10 +158,12 @@ def test_bar_sweep_matches_oracle(bar_ctx, bar_circ, bar_dense_P, bar_mesh):
     assert st["max_rel_res"] <= 1e-8
 
 
-def test_mixed_precision_sweep_matches_oracle(lib, bar_circ, bar_dense_P, bar_mesh):
-    """FP32 FMM inside FP64 FGMRES-IR: the final FP64 residual still reaches
-    1e-8 and R, L match the oracle to 1e-4."""
-    x = lib.XRL.from_mesh(bar_mesh, fmm_order=8, precision=1)
+@pytest.mark.parametrize("p", [8, 7])
+def test_mixed_precision_sweep_matches_oracle(lib, bar_circ, bar_dense_P, bar_mesh, p):
+    """FP32 FMM inside FP64 FGMRES-IR, at order 8 and at the autotuned order
+    7: the final FP64 residual still reaches 1e-8 and R, L match the oracle
+    to 1e-4."""
+    x = lib.XRL.from_mesh(bar_mesh, fmm_order=p, precision=1)
     f = bar_mesh.freqs
     R, L = x.solve(f)
     Ro, Lo, _ = bar_circ.solve(f, bar_dense_P)
