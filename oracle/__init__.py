@@ -26,7 +26,12 @@ Modules and what pins them (tests under tests/test_oracle_*.py):
   an independent nodal (MNA) formulation on small meshes.
 * precond     -- the diagonal-of-P preconditioner Q (eq. 10) built densely.
   Pinned by Q equalling the loop operator with P replaced by diag(P), and
-  by positive definiteness of its real and imaginary parts.
+  by positive definiteness of its real and imaginary parts.  The diagonal-of-L
+  comparison preconditioner of Sec. II-D and Table IV (circuit.precond_matrix_L:
+  the loop-space Z_s kept whole plus the branch diagonal of the inductance) is
+  pinned by the loop operator with its potential part switched off plus a
+  per-branch sum written out from the edge midpoints and panel centroids,
+  complex symmetry, positive definiteness and the sparsity of eq. 10.
 
 Parity unpinned: none of the functions above is without a pin; the paper
 prints no worked numeric example of A, P, Q or Z, so the pins are closed

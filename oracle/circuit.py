@@ -26,6 +26,10 @@ Readings taken where the paper is silent or garbled:
   L = Im Z_port / omega.
 * The loop matrix M is the fundamental-cycle basis of a breadth-first
   spanning forest (Sec. II-B leaves the loop search to refs [6], [14]).
+* The diagonal-of-L preconditioner "Z_s + j omega L_d" (Sec. II-D) is read
+  with Z_s the loop-space surface impedance matrix of eq. 8 (kept whole, as
+  in the operator) and L_d the diagonal of the branch-branch inductance
+  mu0/4pi sum_t A_t P A_t^T, projected by M.
 """
 from collections import deque
 
@@ -294,6 +298,23 @@ def mna_port_admittance(circ, f, P_full):
         rhs[nb + p, p] = 1.0
     sol, *_ = np.linalg.lstsq(Kfull, rhs, rcond=None)
     return sol[nb + nn:, :]                         # port currents: Y[q, p]
+
+
+def precond_matrix_L(circ, f, P_full):
+    """Diagonal-of-L preconditioner, the comparison of Sec. II-D and Table IV:
+    Z_s + j omega L_d, with Z_s the loop-space surface impedance matrix of
+    eq. 8 kept whole and L_d the diagonal of the edge-edge interaction matrix
+    mu0/4pi sum_t A_t P A_t^T, taken over conductor branches and projected by
+    the loop matrix:
+        Q_L(f) = sum_t (M A_t) diag(Z_s/A) (M A_t)^T
+                 + j omega mu0/4pi M_c diag(sum_t A_t P A_t^T) M_c^T."""
+    P_live = P_full[np.ix_(circ.live, circ.live)]
+    MA = circ.ma()
+    d = circ.zs_panels(f)
+    R = sum((MA[t] * d[None, :]) @ MA[t].T for t in range(3))
+    Ld = np.diag(sum(circ.A[t] @ P_live @ circ.A[t].T for t in range(3)))
+    Mc = circ.M[:, :circ.n_cb]
+    return R + 1j * 2 * np.pi * f * MU0_4PI * ((Mc * Ld[None, :]) @ Mc.T)
 
 
 def precond_matrix(circ, f, P_full):

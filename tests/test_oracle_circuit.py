@@ -161,3 +161,55 @@ def test_precond_is_operator_with_diagonal_P(two_circ, two_bars_dense_P):
     assert np.max(np.abs(Q - Zd)) < 1e-12 * np.max(np.abs(Q))
     assert np.linalg.eigvalsh(Q.real).min() > 0
     assert np.linalg.eigvalsh(Q.imag).min() > 0
+
+
+def _branch_potential_diagonal(circ, P_full):
+    """(sum_t A_t P A_t^T)_bb for every conductor branch, written out from the
+    geometry: the edge midpoint, the two panel centroids and the orientation
+    rule of Algorithm 1 (+rho on the tail panel, -rho on the head panel)."""
+    xyz = np.asarray(circ.mesh.xyz, float)
+    tri = np.asarray(circ.mesh.tri, np.int64)
+    cen = xyz[tri].mean(axis=1)
+    g = np.zeros(circ.n_cb)
+    for b in range(circ.n_cb):
+        ev = circ.edge_vertices[circ.branch_edge[b]]
+        mid = 0.5 * (xyz[ev[0]] + xyz[ev[1]])
+        sides = []
+        for node, sign in ((circ.tail[b], 1.0), (circ.head[b], -1.0)):
+            if node < circ.n_live:
+                p = circ.live[node]
+                sides.append((p, sign * (mid - cen[p])))
+        for p, r in sides:
+            for q, s in sides:
+                g[b] += (r @ s) * P_full[p, q]
+    return g
+
+
+@pytest.mark.parametrize("f", [1e3, 1e9])
+def test_precond_L_is_surface_impedance_plus_branch_diagonal(two_circ, two_bars_dense_P, f):
+    QL = C.precond_matrix_L(two_circ, f, two_bars_dense_P)
+    # the surface-impedance part is the operator's loop-space Z_s, whole (the
+    # loop matrix with the potential part switched off)
+    n = two_circ.M.shape[0]
+    Zs = two_circ.loop_matrix(f, np.zeros((n, n)))
+    # the rest keeps one inductive term per branch: j omega mu0/4pi M diag(g) M^T
+    g = _branch_potential_diagonal(two_circ, two_bars_dense_P)
+    Mc = two_circ.M[:, :two_circ.n_cb]
+    Li = 2 * np.pi * f * C.MU0_4PI * (Mc * g[None, :]) @ Mc.T
+    assert np.max(np.abs(QL - Zs - 1j * Li)) < 1e-12 * np.max(np.abs(QL))
+    assert np.all(g > 0)
+
+
+def test_precond_L_symmetric_positive_and_distinct_from_diag_P(two_circ, two_bars_dense_P):
+    f = 1e8
+    QL = C.precond_matrix_L(two_circ, f, two_bars_dense_P)
+    Q = C.precond_matrix(two_circ, f, two_bars_dense_P)
+    assert np.max(np.abs(QL - QL.T)) == 0.0
+    assert np.linalg.eigvalsh(QL.real).min() > 0
+    assert np.linalg.eigvalsh(QL.imag).min() > 0
+    # the sparsity of eq. 10 (loops touching a common panel), different values
+    Mc = np.abs(two_circ.M[:, :two_circ.n_cb])
+    touch = (Mc @ np.abs(two_circ.A).sum(axis=0)) > 0          # loop x panel
+    S = (touch.astype(float) @ touch.T.astype(float)) > 0
+    assert not np.any((QL != 0) & ~S) and not np.any((Q != 0) & ~S)
+    assert np.max(np.abs(QL.imag - Q.imag)) > 1e-3 * np.max(np.abs(Q.imag))
