@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--no-ablation", action="store_true",
+                    help="skip the preconditioner comparison (diagonal-of-P vs diagonal-of-L, untimed)")
     ap.add_argument("--fmm-order", type=int, default=7,
                     help="expansion order p of the FMM with --no-autotune (7: the autotuner's choice here)")
     ap.add_argument("--leaf-target", type=int, default=32, help="target panels per octree leaf")
@@ -415,6 +417,36 @@ def main():
                  "rel_err_R_chosen_vs_plain": float(eR), "rel_err_L_chosen_vs_plain": float(eL)}
         xp.close()
 
+    # preconditioner comparison outside the timed region (Sec. II-D, Table IV): the same sweep with
+    # the diagonal-of-P (eq. 10) and the diagonal-of-L preconditioners at the table's tolerance 1e-6
+    # and at the bench's 1e-8; setup = the pencil build (P entries, pattern, band ordering)
+    abl = None
+    if not args.no_ablation and world == 1:
+        abl = {}
+        for tol in (1e-6, 1e-8):
+            row = {}
+            for name, pc in (("diag_P", 1), ("diag_L", 3)):
+                xa = pkg.XRL.from_mesh(m, **dict(opts, precond=pc, tol=tol))
+                sa = xa.stats()
+                try:
+                    xa.solve(m.freqs)
+                    xa.reset_profile()
+                    xa.set_profiling(True)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    xa.solve(m.freqs)
+                    ta = time.perf_counter() - t0
+                    pa = xa.profile()
+                    sb = xa.stats()
+                    row[name] = {"fgmres_iters": sb["total_iters"], "s_per_freq_port": ta / nsys,
+                                 "precond_setup_ms": sa["precond_setup_ms"],
+                                 "precond_factor_apply_ms": pa["precond"]["ms"] if "precond" in pa else None,
+                                 "max_rel_residual": sb["max_rel_res"]}
+                except pkg.XRLError as e:
+                    row[name] = {"error": str(e), "precond_setup_ms": sa["precond_setup_ms"]}
+                xa.close()
+            abl["tol_%g" % tol] = row
+
     if rank == 0:
         cb = None
         if world == 1 and not args.no_cpu_baseline:
@@ -427,7 +459,7 @@ def main():
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * len(m.freqs),
                         "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * 4},
                 "gpu_launches": launches, "clocks": ck, "roofline": roof, "roofline_phases": roofs, "cpu_baseline": cb,
-                "fmm_mvm_panel_cols_per_s": mvm, "plain_fp64": plain,
+                "fmm_mvm_panel_cols_per_s": mvm, "plain_fp64": plain, "precond_ablation": abl,
                 "solve": {"fgmres_iters": iters, "max_rel_residual": res, "setup_ms": st["setup_ms"],
                           "n_loops": st["n_loops"], "peak_device_bytes": x.stats()["peak_device_bytes"]},
                 "phases_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}

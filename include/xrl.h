@@ -56,8 +56,11 @@ typedef struct {
   int32_t precision;   /* 0: FP64 everywhere; 1: mixed (FP32 FMM/near field inside FP64 refinement) */
   int32_t precond;     /* 0: none; 1: diagonal-of-P preconditioner of eq. 10 applied exactly (banded
                           LDL^T of the RCM-ordered vertex loops + Schur border; falls back to 2 when
-                          the band is wider than 63 or there are more than 16 global loops);
-                          2: eq. 10 applied inexactly by Jacobi-preconditioned COCG */
+                          the band is not usable); 2: eq. 10 applied inexactly by Jacobi-preconditioned
+                          COCG; 3: the diagonal-of-L preconditioner of Sec. II-D / Table IV,
+                          Z_s + j omega L_d (loop-space surface impedance of eq. 8 kept whole, L_d the
+                          diagonal of the branch-branch inductance sum_t A_t mu0/4pi P A_t^T), applied
+                          like 1 (COCG when the band is not usable) */
   int32_t restart;     /* FGMRES restart length m, default 50 (Sec. III uses restart 50) */
   int32_t max_iters;   /* total outer iterations per solve, default 500 */
   int32_t inner_iters; /* max inner COCG iterations per preconditioner apply, default 60 */
@@ -176,6 +179,8 @@ typedef struct {
   int64_t peak_device_bytes;         /* high-water mark of the library's device allocations */
   int64_t near_nnz_padded;  /* near-field entries of the tensor-core near blocks (leaves padded to
                                16 panels); 0 when that path is off */
+  double precond_setup_ms;  /* host + device time of the last setup spent building the preconditioner
+                               pencil (P entries, loop pattern, band ordering and band values) */
 } xrl_stats;
 
 /* FMM autotuner: tries leaf_target in {16, 32, 64} x fmm_order in {6, 7, 8}

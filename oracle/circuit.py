@@ -300,20 +300,21 @@ def mna_port_admittance(circ, f, P_full):
     return sol[nb + nn:, :]                         # port currents: Y[q, p]
 
 
-def precond_matrix_L(circ, f, P_full):
+def precond_matrix_L(circ, f, P_full, M=None):
     """Diagonal-of-L preconditioner, the comparison of Sec. II-D and Table IV:
     Z_s + j omega L_d, with Z_s the loop-space surface impedance matrix of
     eq. 8 kept whole and L_d the diagonal of the edge-edge interaction matrix
     mu0/4pi sum_t A_t P A_t^T, taken over conductor branches and projected by
     the loop matrix:
         Q_L(f) = sum_t (M A_t) diag(Z_s/A) (M A_t)^T
-                 + j omega mu0/4pi M_c diag(sum_t A_t P A_t^T) M_c^T."""
+                 + j omega mu0/4pi M_c diag(sum_t A_t P A_t^T) M_c^T.
+    M: another loop basis over the same branches (default: the oracle's)."""
     P_live = P_full[np.ix_(circ.live, circ.live)]
-    MA = circ.ma()
+    Mc = (circ.M if M is None else np.asarray(M))[:, :circ.n_cb]
+    MA = np.stack([Mc @ circ.A[t] for t in range(3)])
     d = circ.zs_panels(f)
     R = sum((MA[t] * d[None, :]) @ MA[t].T for t in range(3))
     Ld = np.diag(sum(circ.A[t] @ P_live @ circ.A[t].T for t in range(3)))
-    Mc = circ.M[:, :circ.n_cb]
     return R + 1j * 2 * np.pi * f * MU0_4PI * ((Mc * Ld[None, :]) @ Mc.T)
 
 

@@ -192,6 +192,7 @@ xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {
     XRL_CHECK(c->opt.fmm_order >= 2 && c->opt.fmm_order <= 12, XRL_EINVAL, "fmm_order must be in [2, 12]");
     XRL_CHECK(c->opt.leaf_target >= 1, XRL_EINVAL, "leaf_target must be >= 1");
     XRL_CHECK(c->opt.separation == 1 || c->opt.separation == 2, XRL_EINVAL, "separation must be 1 or 2");
+    XRL_CHECK(c->opt.precond >= 0 && c->opt.precond <= 3, XRL_EINVAL, "precond must be in [0, 3]");
     XRL_CHECK(c->opt.tol > 0 && c->opt.restart >= 1 && c->opt.max_iters >= 1, XRL_EINVAL, "bad solver options");
     int n = 0;
     XRL_CUDA(cudaGetDeviceCount(&n));
@@ -291,10 +292,29 @@ xrl_status xrl_setup(xrl_ctx* c) {
       const double* v2 = &c->xyz[3 * (size_t)c->tri[3 * p + 2]];
       pdiag[p] = self_term_host(v0, v1, v2);
     }
-    build_precond_pattern(c, pdiag);
+    const double tq = now_ms();
+    if (c->opt.precond == 3) {
+      // diagonal-of-L: the P entry between the two panels of every interior conductor branch
+      const Topo& T = c->topo;
+      std::vector<int32_t> pk, pl, which;
+      for (int b = 0; b < T.n_cb; ++b)
+        if (T.br_pan[0][b] >= 0 && T.br_pan[1][b] >= 0) {
+          pk.push_back(T.br_pan[0][b]);
+          pl.push_back(T.br_pan[1][b]);
+          which.push_back(b);
+        }
+      std::vector<double> pe = pair_entries(c, pk, pl);
+      std::vector<double> p12(T.n_cb, 0.0);
+      for (size_t i = 0; i < which.size(); ++i) p12[which[i]] = pe[i];
+      build_precond_pattern(c, pdiag, &p12);
+    } else {
+      build_precond_pattern(c, pdiag);
+    }
     build_band(c);
-    solver_prepare(c);
     band_prepare(c);
+    XRL_CUDA(cudaStreamSynchronize(c->stream));
+    c->stats.precond_setup_ms = now_ms() - tq;
+    solver_prepare(c);
     XRL_CUDA(cudaStreamSynchronize(c->stream));
     const Topo& T = c->topo;
     c->stats.n_panels = c->N;

@@ -526,6 +526,34 @@ void launch_moments(xrl_ctx* c) {
   XRL_CUDA(cudaStreamSynchronize(c->stream));
 }
 
+// P entries of a list of panel pairs (Morton ranks), with the rule table
+__global__ void k_pair_entries(PanelView pv, int n, const int32_t* __restrict__ pk, const int32_t* __restrict__ pl,
+                               double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = p_entry(pv, pk[i], pl[i]);
+}
+
+std::vector<double> pair_entries(xrl_ctx* c, const std::vector<int32_t>& k, const std::vector<int32_t>& l) {
+  XRL_CHECK(k.size() == l.size(), XRL_EINVAL, "pair list sizes differ");
+  const int n = (int)k.size();
+  if (n == 0) return {};
+  std::vector<int32_t> rk(n), rl(n);
+  for (int i = 0; i < n; ++i) {
+    XRL_CHECK(k[i] >= 0 && k[i] < c->N && l[i] >= 0 && l[i] < c->N, XRL_EINVAL, "pair panel out of range");
+    rk[i] = c->tree.rank[k[i]];
+    rl[i] = c->tree.rank[l[i]];
+  }
+  DBuf<int32_t> dk, dl;
+  DBuf<double> dv;
+  dk.upload(c->alloc, rk);
+  dl.upload(c->alloc, rl);
+  dv.alloc(c->alloc, n);
+  k_pair_entries<<<(n + 255) / 256, 256, 0, c->stream>>>(view(c), n, dk.p, dl.p, dv.p);
+  XRL_CUDA(cudaGetLastError());
+  XRL_CUDA(cudaStreamSynchronize(c->stream));
+  return dv.download();
+}
+
 void launch_direct(xrl_ctx* c, int nc, const double* X, double* Y, cudaStream_t s) {
   k_direct<<<c->N, 256, 256 * sizeof(double), s>>>(view(c), c->N, nc, X, Y);
   XRL_CUDA(cudaGetLastError());

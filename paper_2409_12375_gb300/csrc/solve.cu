@@ -815,7 +815,7 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
   wk.active.alloc(c->alloc, nsys);
   wk.iters.alloc(c->alloc, nsys);
   wk.kcols.alloc(c->alloc, nsys);
-  wk.banded = c->opt.precond == 1 && band_usable(c);
+  wk.banded = (c->opt.precond == 1 || c->opt.precond == 3) && band_usable(c);
   if (wk.banded) {
     band_alloc(c, wk.bw, nf, nsys, mixed);
     band_factor(c, wk.bw, wk.zsf.p, wk.wpf.p, s);

@@ -400,19 +400,45 @@ void build_topology(xrl_ctx* c) {
   T.n_mat = (int)T.mat_sigma.size();
 }
 
-void build_precond_pattern(xrl_ctx* c, const std::vector<double>& pdiag) {
+// Pencil of the preconditioner Q(f) over the loops: every stored entry keeps
+// n_mat + 1 coefficients, Q_ij(f) = sum_m Z_s,m(f) v_m + j omega mu0/4pi v_nm.
+// The surface-impedance part is the loop-space Z_s of eq. 8 in both forms,
+// sum_t (M A_t) diag(Z_s/A) (M A_t)^T, assembled panel by panel over the
+// pairs of branches that touch the panel.  The potential part is
+//  * p12 == NULL, diagonal-of-P (eq. 10): sum_t (M A_t) diag(P_ll) (M A_t)^T;
+//  * p12 != NULL, diagonal-of-L (the comparison preconditioner of Sec. II-D,
+//    Table IV): M diag(G_b) M^T with G_b = sum_t A_t P A_t^T on the branches.
+//    A branch touches at most two panels (tail s = 0, head s = 1), so with the
+//    signed rho of A_t, (G_b)_bb = sum_s |rho_s|^2 P_ss + 2 (rho_0 . rho_1) P_01.
+// Both have the sparsity of "loops that touch a common panel", so the banded
+// factorisation serves both.
+void build_precond_pattern(xrl_ctx* c, const std::vector<double>& pdiag, const std::vector<double>* p12) {
   Topo& T = c->topo;
   const int N = c->N;
   const int nm = T.n_mat;
   const int W = nm + 1;
+  auto X = [&](int v, int k) { return c->xyz[3 * (size_t)v + k]; };
+  auto dot3 = [](const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
+  std::unordered_map<uint64_t, std::vector<double>> acc;
+  acc.reserve((size_t)T.n_loops * 24);
+  // coefficient w0 (and w1 >= 0) of Q_ij += M_i,bi M_j,bj u0 (u1) for every loop i through bi
+  // and j through bj
+  auto scatter = [&](int bi, int bj, int w0, double u0, int w1, double u1) {
+    for (int64_t ki = T.mt_ptr[bi]; ki < T.mt_ptr[bi + 1]; ++ki)
+      for (int64_t kj = T.mt_ptr[bj]; kj < T.mt_ptr[bj + 1]; ++kj) {
+        uint64_t key = ((uint64_t)(uint32_t)T.mt_col[ki] << 32) | (uint32_t)T.mt_col[kj];
+        const double m = T.mt_val[ki] * T.mt_val[kj];
+        auto& v = acc[key];
+        if (v.empty()) v.assign(W, 0.0);
+        v[w0] += m * u0;
+        if (w1 >= 0) v[w1] += m * u1;
+      }
+  };
   // branches of each live panel with their signed rho
   std::vector<std::vector<std::pair<int, int>>> pb(N);   // (branch, side)
   for (int b = 0; b < T.n_cb; ++b)
     for (int s = 0; s < 2; ++s)
       if (T.br_pan[s][b] >= 0) pb[T.br_pan[s][b]].push_back({b, s});
-  std::unordered_map<uint64_t, std::vector<double>> acc;
-  acc.reserve((size_t)T.n_loops * 24);
-  auto X = [&](int v, int k) { return c->xyz[3 * (size_t)v + k]; };
   for (int p = 0; p < N; ++p) {
     if (T.live_of_panel[p] < 0) continue;
     const int32_t* t = &c->tri[3 * p];
@@ -422,23 +448,28 @@ void build_precond_pattern(xrl_ctx* c, const std::vector<double>& pdiag) {
       e2[k] = X(t[2], k) - X(t[0], k);
     }
     double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-    double area = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-    int mat = T.mat_of_cond[c->cond[p]];
+    const double area = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    const int mat = T.mat_of_cond[c->cond[p]];
     for (auto& bi : pb[p])
       for (auto& bj : pb[p]) {
-        const double* ri = &T.br_rho[bi.second][3 * (size_t)bi.first];
-        const double* rj = &T.br_rho[bj.second][3 * (size_t)bj.first];
-        double dot = ri[0] * rj[0] + ri[1] * rj[1] + ri[2] * rj[2];
-        for (int64_t ki = T.mt_ptr[bi.first]; ki < T.mt_ptr[bi.first + 1]; ++ki)
-          for (int64_t kj = T.mt_ptr[bj.first]; kj < T.mt_ptr[bj.first + 1]; ++kj) {
-            uint64_t key = ((uint64_t)(uint32_t)T.mt_col[ki] << 32) | (uint32_t)T.mt_col[kj];
-            double s = dot * T.mt_val[ki] * T.mt_val[kj];
-            auto& v = acc[key];
-            if (v.empty()) v.assign(W, 0.0);
-            v[mat] += s / area;
-            v[nm] += s * pdiag[p];
-          }
+        double dot = dot3(&T.br_rho[bi.second][3 * (size_t)bi.first], &T.br_rho[bj.second][3 * (size_t)bj.first]);
+        scatter(bi.first, bj.first, mat, dot / area, p12 ? -1 : nm, dot * pdiag[p]);
       }
+  }
+  if (p12) {
+    XRL_CHECK((int)p12->size() == T.n_cb, XRL_EINVAL, "one P entry per conductor branch");
+    for (int b = 0; b < T.n_cb; ++b) {
+      double g = 0.0;
+      for (int s = 0; s < 2; ++s) {
+        const int p = T.br_pan[s][b];
+        if (p < 0) continue;
+        const double* r = &T.br_rho[s][3 * (size_t)b];
+        g += dot3(r, r) * pdiag[p];
+      }
+      if (T.br_pan[0][b] >= 0 && T.br_pan[1][b] >= 0)
+        g += 2.0 * dot3(&T.br_rho[0][3 * (size_t)b], &T.br_rho[1][3 * (size_t)b]) * (*p12)[b];
+      scatter(b, b, nm, g, -1, 0.0);
+    }
   }
   std::vector<std::pair<uint64_t, const std::vector<double>*>> ent;
   ent.reserve(acc.size());

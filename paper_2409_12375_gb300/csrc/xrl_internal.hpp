@@ -307,7 +307,10 @@ uint64_t morton_key(uint32_t ix, uint32_t iy, uint32_t iz);
 void morton_decode(uint64_t key, uint32_t* ix, uint32_t* iy, uint32_t* iz);
 // topology.cpp
 void build_topology(xrl_ctx* c);
-void build_precond_pattern(xrl_ctx* c, const std::vector<double>& p_diag_caller);
+// p12 = NULL: diagonal-of-P pencil (eq. 10); else the diagonal-of-L pencil with p12[b] the
+// P entry between the tail and head panels of conductor branch b (0 where one side is a terminal)
+void build_precond_pattern(xrl_ctx* c, const std::vector<double>& p_diag_caller,
+                           const std::vector<double>* p12 = nullptr);
 void build_band(xrl_ctx* c);
 // harmonics.cpp
 void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
@@ -318,6 +321,8 @@ void launch_geometry(xrl_ctx* c);              // computes panel data + keys (ca
 void launch_near_fill(xrl_ctx* c);             // near-field blocks (rule table)
 void launch_moments(xrl_ctx* c);               // P2M/L2P moment table
 void launch_direct(xrl_ctx* c, int ncols, const double* x, double* y, cudaStream_t s);
+std::vector<double> pair_entries(xrl_ctx* c, const std::vector<int32_t>& k_caller,
+                                 const std::vector<int32_t>& l_caller);   // P entries of panel pairs
 void upload_rule_tables(xrl_ctx* c);
 // fmm.cu
 void fmm_prepare(xrl_ctx* c);                  // upload tree and operators
