@@ -1,9 +1,13 @@
-"""Seeded generators for closed, consistently oriented triangle meshes.
+"""Seeded generators for closed, consistently oriented panel meshes.
 
-Every surface is a closed 2-manifold (each edge in exactly two triangles) with
-outward-facing triangles.  Terminal patches are sets of triangles tagged with a
-terminal id; a port joins a source terminal to a sink terminal.  All lengths
-are metres, conductivities S/m, frequencies Hz.
+Every surface is a closed 2-manifold (each edge in exactly two panels) with
+outward-facing panels.  By default the panels are triangles (`tri` is
+[n, 3]); with rect=True every lattice quad that is a parallelogram is kept as
+one rectangular panel and only the others are split, which gives the hybrid
+triangle/rectangle meshes of Sec. II-A (`tri` is then [n, 4], triangles padded
+with -1).  Terminal patches are sets of panels tagged with a terminal id; a
+port joins a source terminal to a sink terminal.  All lengths are metres,
+conductivities S/m, frequencies Hz.
 
 Shapes follow the workloads of the paper's Sec. III (a straight conductor,
 two planar square coils); the sizes are the synthetic stand-ins stated in the
@@ -20,7 +24,8 @@ import numpy as np
 @dataclasses.dataclass
 class Mesh:
     xyz: np.ndarray          # float64 [n_vert, 3], metres
-    tri: np.ndarray          # int32 [n_tri, 3], outward (counter-clockwise seen from outside)
+    tri: np.ndarray          # int32 [n, 3] triangles or [n, 4] panels (rectangles; triangles
+                             # padded with -1), outward (counter-clockwise seen from outside)
     cond: np.ndarray         # int32 [n_tri], conductor id
     term: np.ndarray         # int32 [n_tri], terminal id or -1
     ports: list              # list of (source_terminal, sink_terminal)
@@ -46,13 +51,25 @@ class Mesh:
 
 
 class _Builder:
-    """Vertex de-duplication by integer key, triangle list with tags."""
+    """Vertex de-duplication by integer key, panel list with tags."""
 
-    def __init__(self):
+    def __init__(self, rect=False):
         self.key2id = {}
         self.pts = []
         self.tris = []
         self.tags = []
+        self.rect = rect
+
+    def panels(self):
+        """[n, 3] triangles, or [n, 4] with -1 padding when rectangles are kept."""
+        if not self.rect:
+            return np.array(self.tris, np.int32)
+        return np.array([t if len(t) == 4 else tuple(t) + (-1,) for t in self.tris], np.int32)
+
+    def _parallelogram(self, a, b, c, d):
+        pa, pb, pc, pd = (self.pts[i] for i in (a, b, c, d))
+        scale = max(np.linalg.norm(pc - pa), np.linalg.norm(pd - pb))
+        return np.linalg.norm(pa + pc - pb - pd) <= 1e-9 * scale
 
     def vid(self, key, pos):
         i = self.key2id.get(key)
@@ -64,6 +81,10 @@ class _Builder:
 
     def quad(self, a, b, c, d, tag, flip_diag=False):
         # a,b,c,d counter-clockwise seen from outside
+        if self.rect and self._parallelogram(a, b, c, d):
+            self.tris.append((a, b, c, d))
+            self.tags.append(tag)
+            return
         if flip_diag:
             self.tris += [(a, b, d), (b, c, d)]
         else:
@@ -123,21 +144,22 @@ def _box_surface(bld, size, n, jitter, rng, terminal_faces, cond_tag):
 
 def bar(length=10e-3, width=1e-3, height=1e-3, n_w=5, n_h=5, n_l=50,
         jitter=0.05, seed=1, sigma=5.8e7, thickness=None,
-        freqs=(1e3, 1e5, 1e7, 1e9), offset=(0.0, 0.0, 0.0)) -> Mesh:
+        freqs=(1e3, 1e5, 1e7, 1e9), offset=(0.0, 0.0, 0.0), rect=False) -> Mesh:
     """Straight rectangular bar along z with the two end faces as terminals.
 
     Terminal 0 (z = length) is the source, terminal 1 (z = 0) the sink.
     The ESI thickness defaults to 2*(cross-section area)/(perimeter), which
-    makes the surface model's DC resistance equal rho*L/A.
+    makes the surface model's DC resistance equal rho*L/A.  With rect=True
+    (and jitter=0) every face is meshed with rectangles.
     """
     rng = np.random.default_rng(seed)
-    bld = _Builder()
+    bld = _Builder(rect)
     _box_surface(bld, (width, height, length), (n_w, n_h, n_l), jitter, rng,
                  {'z1': 0, 'z0': 1}, 0)
     if thickness is None:
         thickness = 2 * width * height / (2 * (width + height))
     xyz = np.array(bld.pts) + np.asarray(offset, float)
-    return Mesh(xyz=xyz, tri=np.array(bld.tris, np.int32),
+    return Mesh(xyz=xyz, tri=bld.panels(),
                 cond=np.zeros(len(bld.tris), np.int32),
                 term=np.array(bld.tags, np.int32), ports=[(0, 1)],
                 sigma=np.array([sigma]), thickness=np.array([thickness]),
@@ -155,9 +177,12 @@ def _merge(meshes, name):
     nv = 0
     nt = 0
     nc = 0
+    width = max(m.tri.shape[1] for m in meshes)
     for m in meshes:
         xyz.append(m.xyz)
-        tri.append(m.tri + nv)
+        t = np.full((m.tri.shape[0], width), -1, np.int64)
+        t[:, :m.tri.shape[1]] = m.tri
+        tri.append(np.where(t >= 0, t + nv, -1))
         cond.append(m.cond + nc)
         tt = m.term.copy()
         tt[tt >= 0] += nt
@@ -279,32 +304,52 @@ def _swept_trace(bld, corners, z0, w, t, n_w, n_t, step, tag_base, cond_tag, ter
 
 
 def coils(outer=5e-3, w=0.2e-3, t=35e-6, s=0.2e-3, turns=4, gap=0.5e-3, n_w=3, n_t=1,
-          step=0.075e-3, sigma=5.8e7, n_freq=32, fmin=100.0, fmax=1e10) -> Mesh:
+          step=0.075e-3, sigma=5.8e7, n_freq=32, fmin=100.0, fmax=1e10, rect=False,
+          n_coils=2) -> Mesh:
     """Two parallel square planar spiral coils stacked along z (edge gap `gap`).
 
     Each coil is one conductor with one port: source on the outer end cap,
     sink on the inner end cap (the external port branch closes the loop).
-    The ESI thickness of each trace is its physical thickness t.
+    The ESI thickness of each trace is its physical thickness t.  With
+    rect=True the straight runs are meshed with rectangles and the mitred
+    corner panels (trapezoids) with triangles; n_coils=1 keeps the lower coil.
     """
-    bld = _Builder()
+    bld = _Builder(rect)
     corners = _spiral_centerline(outer, w, s, turns)
     _swept_trace(bld, corners, 0.0, w, t, n_w, n_t, step, 0, 0, (0, 1))
     n0 = len(bld.tris)
-    _swept_trace(bld, corners, t + gap, w, t, n_w, n_t, step, 0, 1, (2, 3))
-    # the sweep above emits inward-facing triangles; reverse them to outward
-    tri = np.array(bld.tris, np.int32)[:, [0, 2, 1]]
+    if n_coils == 2:
+        _swept_trace(bld, corners, t + gap, w, t, n_w, n_t, step, 0, 1, (2, 3))
+    # the sweep above emits inward-facing panels; reverse them to outward
+    tri = bld.panels()
+    if tri.shape[1] == 3:
+        tri = tri[:, [0, 2, 1]]
+    else:
+        quad = tri[:, 3] >= 0
+        tri = np.where(quad[:, None], tri[:, [0, 3, 2, 1]], tri[:, [0, 2, 1, 3]]).astype(np.int32)
     cond = np.zeros(len(tri), np.int32)
     cond[n0:] = 1
     term = np.array(bld.tags, np.int32)
+    ports = [(0, 1), (2, 3)][:n_coils]
     return Mesh(xyz=np.array(bld.pts), tri=tri, cond=cond, term=term,
-                ports=[(0, 1), (2, 3)], sigma=np.array([sigma, sigma]),
-                thickness=np.array([t, t]),
+                ports=ports, sigma=np.array([sigma, sigma][:n_coils]),
+                thickness=np.array([t, t][:n_coils]),
                 freqs=np.geomspace(fmin, fmax, n_freq), name="coils")
 
 
+def panel_edges(tri):
+    """Directed edges (a, b) of every panel in vertex order, [n_edges, 2]."""
+    tri = np.asarray(tri)
+    out = []
+    for row in tri:
+        vs = [int(x) for x in row if x >= 0]
+        out += [(vs[k], vs[(k + 1) % len(vs)]) for k in range(len(vs))]
+    return np.array(out, np.int64)
+
+
 def crop_check(m: Mesh):
-    """Return (closed, oriented): every edge in exactly two triangles, used once each way."""
-    e = np.concatenate([m.tri[:, [0, 1]], m.tri[:, [1, 2]], m.tri[:, [2, 0]]])
+    """Return (closed, oriented): every edge in exactly two panels, used once each way."""
+    e = panel_edges(m.tri)
     und = np.sort(e, axis=1)
     _, cnt = np.unique(und, axis=0, return_counts=True)
     closed = bool(np.all(cnt == 2))

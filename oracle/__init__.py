@@ -15,6 +15,10 @@ Modules and what pins them (tests under tests/test_oracle_*.py):
   P (Sec. II-A eq. 6, Sec. II-C).  Pinned by brute-force adaptive quadrature,
   the Reynolds-transport edge identity for the self term, the point-charge
   limit, scaling P(s*geom) = P/s, symmetry and positive definiteness.
+  Rectangular panels of hybrid meshes (panels.Panels, P as the area-weighted
+  sum over the two triangles of each rectangle) are pinned by the closed-form
+  self and edge-adjacent integrals of coplanar rectangles and by a reduced
+  2-D quadrature of aligned rectangle pairs (tests/test_oracle_rect.py).
 * esi         -- the double-plane surface impedance (eq. 3).  Pinned by its
   DC and high-frequency limits and by the skin depths the paper prints.
 * circuit     -- PEEC branches, centroid-midpoint matrices A_t (Algorithm 1,

@@ -36,7 +36,7 @@ from collections import deque
 import numpy as np
 
 from .esi import zs
-from .panels import Geometry
+from .panels import Panels
 
 MU0_4PI = 1e-7
 
@@ -46,7 +46,7 @@ class Circuit:
         self.mesh = mesh
         tri = np.asarray(mesh.tri, np.int64)
         term = np.asarray(mesh.term, np.int64)
-        self.geom = Geometry(mesh.xyz, tri)
+        self.geom = Panels(mesh.xyz, tri)
         npan = tri.shape[0]
         self.panel_node = -np.ones(npan, np.int64)
         live = np.flatnonzero(term < 0)
@@ -56,9 +56,17 @@ class Circuit:
         self.n_term = int(term.max()) + 1 if term.size and term.max() >= 0 else 0
         self.n_nodes = self.n_live + self.n_term
 
-        # edges: unordered vertex pairs -> the two panels containing them
-        e_all = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]])
-        owner = np.concatenate([np.arange(npan)] * 3)
+        # edges: unordered vertex pairs -> the two panels containing them (a
+        # triangle has 3 edges, a rectangle 4; its diagonal is not an edge)
+        e_all = []
+        owner = []
+        for k in range(npan):
+            vs = [int(x) for x in tri[k] if x >= 0]
+            for i in range(len(vs)):
+                e_all.append((vs[i], vs[(i + 1) % len(vs)]))
+                owner.append(k)
+        e_all = np.array(e_all, np.int64)
+        owner = np.array(owner, np.int64)
         und = np.sort(e_all, axis=1)
         keys, inv, cnt = np.unique(und, axis=0, return_inverse=True, return_counts=True)
         inv = inv.ravel()

@@ -21,6 +21,18 @@ q = d / (r_k + r_l), and (lo, hi) = (min(k, l), max(k, l)):
   3 <= q < 10       point product rule collapsed(4) x collapsed(4), lo outer
   q >= 10           point product rule collapsed(3) x collapsed(3), lo outer
 
+Rectangular panels (Sec. II-A: "triangular and rectangular supports") are
+parallelograms (v0, v1, v2, v3).  The integral over a rectangle is the sum of
+the integrals over its two triangles (v0, v1, v2) and (v0, v2, v3), so with
+sub-triangle areas a_i and panel areas A_k
+
+  P_kl = sum_{i in k} sum_{j in l} (a_i / A_k) (a_j / A_l) P^tri_ij,
+
+where P^tri is the triangle rule table above applied to the sub-triangles
+(numbered panel by panel, so (lo, hi) follows the panel order).  The two
+halves of one rectangle share its diagonal and take the shared-edge rule.
+For a triangle-only mesh the weights are exactly 1 and P = P^tri.
+
 "Semi-analytic" means the inner integral is the closed-form potential of a
 uniformly charged flat triangle (tri_potential) evaluated at the outer rule's
 points.  The rule table gives per-entry errors <= 2e-8 relative (measured
@@ -240,3 +252,94 @@ def rows_P(G, rows, chunk=200000):
     for s in range(0, K.shape[0], chunk):
         vals[s:s + chunk] = pair_values(G, K[s:s + chunk], L[s:s + chunk])
     return vals.reshape(rows.shape[0], N)
+
+
+class Panels:
+    """Hybrid triangle/rectangle panels (Sec. II-A) as sub-triangles.
+
+    pan: [N, 3] triangles, or [N, 4] with -1 in the last column for a
+    triangle; a 4-vertex panel must be a parallelogram.  Attributes: c
+    (vertex mean = centroid of a triangle or a parallelogram), area, normal,
+    radius (max centroid-vertex distance), nv (3 or 4), sub (Geometry of the
+    sub-triangles), sub_of (panel of each sub-triangle), w (a_i / A_k).
+    """
+
+    def __init__(self, xyz, pan):
+        pan = np.asarray(pan, np.int64)
+        if pan.shape[1] == 3:
+            pan = np.hstack([pan, -np.ones((pan.shape[0], 1), np.int64)])
+        self.pan = pan
+        self.nv = np.where(pan[:, 3] >= 0, 4, 3)
+        xyz = np.asarray(xyz, float)
+        quad = self.nv == 4
+        V = xyz[np.where(pan >= 0, pan, 0)]                  # [N, 4, 3]
+        if np.any(quad):
+            d = V[quad, 0] + V[quad, 2] - V[quad, 1] - V[quad, 3]
+            span = np.linalg.norm(V[quad, 2] - V[quad, 0], axis=1)
+            if np.any(np.linalg.norm(d, axis=1) > 1e-9 * span):
+                raise ValueError("a rectangular panel is not a parallelogram")
+        c3 = (V[:, 0] + V[:, 1] + V[:, 2]) / 3.0
+        c4 = (((V[:, 0] + V[:, 1]) + V[:, 2]) + V[:, 3]) / 4.0
+        self.c = np.where(quad[:, None], c4, c3)
+        subs = []
+        sub_of = []
+        for k in range(pan.shape[0]):
+            a, b, cc, dd = pan[k]
+            subs.append((a, b, cc))
+            sub_of.append(k)
+            if dd >= 0:
+                subs.append((a, cc, dd))
+                sub_of.append(k)
+        self.sub = Geometry(xyz, np.array(subs, np.int64))
+        self.sub_of = np.array(sub_of, np.int64)
+        self.area = np.bincount(self.sub_of, weights=self.sub.area, minlength=pan.shape[0])
+        self.w = self.sub.area / self.area[self.sub_of]
+        first = np.searchsorted(self.sub_of, np.arange(pan.shape[0]))
+        self.normal = self.sub.normal[first]
+        dist = np.linalg.norm(V - self.c[:, None, :], axis=2)
+        dist[:, 3] = np.where(quad, dist[:, 3], 0.0)
+        self.radius = dist.max(axis=1)
+
+    @property
+    def n(self):
+        return self.pan.shape[0]
+
+    @property
+    def tri(self):
+        """[N, 3] vertex ids of a triangle-only mesh."""
+        if np.any(self.nv == 4):
+            raise AttributeError("hybrid mesh: use pan")
+        return self.pan[:, :3]
+
+    @property
+    def v(self):
+        """[N, 3, 3] vertices of a triangle-only mesh."""
+        return self.sub.v if not np.any(self.nv == 4) else None
+
+    def weights(self):
+        """W [N, N_sub] sparse, W[k, i] = a_i / A_k for the sub-triangles of k."""
+        from scipy import sparse
+        return sparse.csr_matrix((self.w, (self.sub_of, np.arange(self.sub_of.shape[0]))),
+                                 shape=(self.n, self.sub_of.shape[0]))
+
+
+def dense_P_panels(H, chunk=200000):
+    """Full symmetric P over hybrid panels: W P^tri W^T."""
+    W = H.weights()
+    Ps = dense_P(H.sub, chunk)
+    Pp = np.asarray((W @ (W @ Ps).T).T)
+    return np.triu(Pp) + np.triu(Pp, 1).T          # exactly symmetric (upper triangle mirrored)
+
+
+def rows_P_panels(H, rows, chunk=200000):
+    """Selected rows of the hybrid P, shape [len(rows), N]."""
+    rows = np.asarray(rows, np.int64)
+    W = H.weights()
+    sub_rows = np.flatnonzero(np.isin(H.sub_of, rows))
+    R = rows_P(H.sub, sub_rows, chunk)                 # [n_sub_rows, N_sub]
+    Rp = np.asarray((W @ R.T).T)                       # [n_sub_rows, N]
+    out = np.zeros((rows.shape[0], H.n))
+    pos = {int(r): i for i, r in enumerate(rows)}
+    for t, si in enumerate(sub_rows):
+        out[pos[int(H.sub_of[si])]] += H.w[si] * Rp[t]
+    return out

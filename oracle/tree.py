@@ -5,7 +5,8 @@ defers the tree to refs [22], [23]; the definitions below are the ones the
 GPU library documents, written independently here so that its lists can be
 compared bit for bit:
 
-* root cube: lo = per-axis minimum of the centroids (c = (v0 + v1 + v2) / 3),
+* root cube: lo = per-axis minimum of the centroids (c = (v0 + v1 + v2) / 3,
+  (((v0 + v1) + v2) + v3) / 4 for a rectangular panel),
   side = largest per-axis extent * (1 + 2^-20);
 * cell q = floor((c - lo) / side * 2^21), clipped to [0, 2^21 - 1]; the
   Morton key puts bit b of x, y, z at bits 3b, 3b + 1, 3b + 2;
@@ -23,9 +24,25 @@ compared bit for bit:
 import numpy as np
 
 
+def _vertices(xyz, tri):
+    """[N, 4, 3] vertices (the 4th repeats v0 for a triangle) and the quad mask."""
+    tri = np.asarray(tri, np.int64)
+    if tri.shape[1] == 3:
+        tri = np.hstack([tri, tri[:, :1]])
+        quad = np.zeros(tri.shape[0], bool)
+    else:
+        quad = tri[:, 3] >= 0
+        tri = np.where(tri >= 0, tri, tri[:, :1])
+    return np.asarray(xyz, float)[tri], quad
+
+
 def centroids(xyz, tri):
-    v = np.asarray(xyz, float)[np.asarray(tri)]
-    return (v[:, 0] + v[:, 1] + v[:, 2]) / 3.0
+    """Vertex mean of each panel: (v0 + v1 + v2) / 3, or (((v0 + v1) + v2) + v3) / 4
+    for a rectangle (its centroid, rectangles being parallelograms)."""
+    v, quad = _vertices(xyz, tri)
+    c3 = (v[:, 0] + v[:, 1] + v[:, 2]) / 3.0
+    c4 = (((v[:, 0] + v[:, 1]) + v[:, 2]) + v[:, 3]) / 4.0
+    return np.where(quad[:, None], c4, c3)
 
 
 def morton(q):
@@ -64,7 +81,7 @@ def keys(xyz, tri):
 def build(xyz, tri, leaf_target=32, ws=2):
     k = keys(xyz, tri)
     c, _, side = root(xyz, tri)
-    v = np.asarray(xyz, float)[np.asarray(tri)]
+    v, _ = _vertices(xyz, tri)
     rmax = np.max(np.sqrt(np.sum((v - c[:, None, :]) ** 2, axis=2)))
     N = k.shape[0]
     perm = np.lexsort((np.arange(N), k))
