@@ -85,13 +85,25 @@ void xrl_default_options(xrl_options* opt);
  * GPU is present. */
 xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out);
 
-/* Conductor surface mesh (Sec. II-A: hybrid panels; this library takes
- * triangles).  xyz: [n_vert][3] vertex coordinates in metres; tri: [n_tri][3]
- * vertex indices (any orientation); cond_id: [n_tri] conductor index per panel
- * (0-based, NULL = all 0).  Each edge must be shared by exactly two triangles;
- * this is checked in xrl_setup (XRL_ETOPO). */
+/* Conductor surface mesh of triangles.  xyz: [n_vert][3] vertex coordinates
+ * in metres; tri: [n_tri][3] vertex indices (any orientation); cond_id:
+ * [n_tri] conductor index per panel (0-based, NULL = all 0).  Each edge must
+ * be shared by exactly two panels; this is checked in xrl_setup (XRL_ETOPO).
+ * The arrays are copied; the caller keeps ownership. */
 xrl_status xrl_set_mesh(xrl_ctx* ctx, int64_t n_vert, const double* xyz, int64_t n_tri,
                         const int32_t* tri, const int32_t* cond_id);
+
+/* Hybrid triangle/rectangle mesh (Sec. II-A, Figs. 1-2: currents on
+ * "triangular and rectangular supports").  pan: [n_panels][4] vertex indices
+ * in cyclic order; a triangle has -1 in its 4th slot.  A 4-vertex panel must be
+ * a parallelogram (|v0 + v2 - v1 - v3| <= 1e-9 |v2 - v0|, else XRL_EINVAL): its
+ * centroid is the vertex mean, its current a pulse (Sec. II-A, eq. 4) and its
+ * integrals the sums over its triangles (v0, v1, v2) and (v0, v2, v3).  Its
+ * four edges are branches of the PEEC graph (Algorithm 1); the diagonal is not.
+ * Other arguments and errors as xrl_set_mesh; a repeated vertex in a panel is
+ * XRL_ETOPO. */
+xrl_status xrl_set_mesh_panels(xrl_ctx* ctx, int64_t n_vert, const double* xyz, int64_t n_panels,
+                               const int32_t* pan, const int32_t* cond_id);
 
 /* Material of each conductor: sigma [n_cond] in S/m and the thickness
  * varsigma [n_cond] in metres of the double-plane ESI model, eq. 3

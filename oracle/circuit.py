@@ -326,10 +326,12 @@ def precond_matrix_L(circ, f, P_full, M=None):
     return R + 1j * 2 * np.pi * f * MU0_4PI * ((Mc * Ld[None, :]) @ Mc.T)
 
 
-def precond_matrix(circ, f, P_full):
+def precond_matrix(circ, f, P_full, M=None):
     """Diagonal-of-P preconditioner of eq. 10 (Sec. II-D), dense:
-    Q(f) = sum_t (M A_t) diag(Z_s/A + j omega mu0/4pi P_ll) (M A_t)^T."""
+    Q(f) = sum_t (M A_t) diag(Z_s/A + j omega mu0/4pi P_ll) (M A_t)^T.
+    M: another loop basis over the same branches (default: the oracle's)."""
     pd = np.diag(P_full)[circ.live]
     d = circ.zs_panels(f) + 1j * 2 * np.pi * f * MU0_4PI * pd
-    MA = circ.ma()
+    Mc = (circ.M if M is None else np.asarray(M))[:, :circ.n_cb]
+    MA = np.stack([Mc @ circ.A[t] for t in range(3)])
     return sum((MA[t] * d[None, :]) @ MA[t].T for t in range(3))

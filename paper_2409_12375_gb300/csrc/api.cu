@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <new>
+#include <numeric>
 
 #include "xrl_internal.hpp"
 
@@ -36,19 +37,35 @@ double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-double self_term_host(const double* a, const double* b, const double* c) {
-  auto d = [](const double* x, const double* y) {
-    return std::sqrt((x[0] - y[0]) * (x[0] - y[0]) + (x[1] - y[1]) * (x[1] - y[1]) + (x[2] - y[2]) * (x[2] - y[2]));
-  };
-  double la = d(b, c), lb = d(c, a), lc = d(a, b);
-  double s = la + lb + lc;
-  return (4.0 / 3.0) * (std::log(s / (s - 2 * la)) / la + std::log(s / (s - 2 * lb)) / lb +
-                        std::log(s / (s - 2 * lc)) / lc);
-}
-
 }  // namespace
 
 namespace xrl {
+
+void panel_centroid_host(const std::vector<double>& xyz, const std::vector<int32_t>& pan, int p, double c[3]) {
+  const int32_t* t = &pan[4 * (size_t)p];
+  for (int k = 0; k < 3; ++k) {
+    double s = (xyz[3 * (size_t)t[0] + k] + xyz[3 * (size_t)t[1] + k]) + xyz[3 * (size_t)t[2] + k];
+    c[k] = t[3] >= 0 ? (s + xyz[3 * (size_t)t[3] + k]) / 4.0 : s / 3.0;
+  }
+}
+
+static double tri_area_host(const double* a, const double* b, const double* c) {
+  double e1[3], e2[3];
+  for (int k = 0; k < 3; ++k) {
+    e1[k] = b[k] - a[k];
+    e2[k] = c[k] - a[k];
+  }
+  double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+  return 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+}
+
+double panel_area_host(const std::vector<double>& xyz, const std::vector<int32_t>& pan, int p) {
+  const int32_t* t = &pan[4 * (size_t)p];
+  auto X = [&](int v) { return &xyz[3 * (size_t)v]; };
+  double a = tri_area_host(X(t[0]), X(t[1]), X(t[2]));
+  if (t[3] >= 0) a += tri_area_host(X(t[0]), X(t[2]), X(t[3]));
+  return a;
+}
 
 // Inside a stream capture a plain record only marks a dependency; an
 // external record becomes a graph node that fires on every replay.
@@ -209,28 +226,69 @@ xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {
   return XRL_OK;
 }
 
+// shared by both mesh entry points: pan4 [n][4] with -1 in slot 3 for a triangle
+static void set_mesh_common(xrl_ctx* c, int64_t n_vert, const double* xyz, int64_t n, const int32_t* pan4,
+                            const int32_t* cond_id) {
+  XRL_CHECK(xyz && pan4 && n_vert > 0 && n > 0 && n < (1LL << 30) && n_vert < (1LL << 31), XRL_EINVAL,
+            "bad mesh arguments");
+  for (int64_t i = 0; i < 3 * n_vert; ++i) XRL_CHECK(std::isfinite(xyz[i]), XRL_EINVAL, "non-finite vertex");
+  for (int64_t p = 0; p < n; ++p) {
+    const int32_t* t = pan4 + 4 * p;
+    const int nv = t[3] >= 0 ? 4 : 3;
+    XRL_CHECK(t[3] >= -1, XRL_EINVAL, "the 4th vertex of a triangle must be -1");
+    for (int k = 0; k < nv; ++k) {
+      XRL_CHECK(t[k] >= 0 && t[k] < n_vert, XRL_EINVAL, "panel vertex index out of range");
+      for (int j = 0; j < k; ++j) XRL_CHECK(t[j] != t[k], XRL_ETOPO, "degenerate panel (repeated vertex)");
+    }
+    if (nv == 4) {
+      // a rectangular panel must be a parallelogram: v0 + v2 = v1 + v3
+      double d2 = 0.0, s2 = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        double d = xyz[3 * (size_t)t[0] + k] + xyz[3 * (size_t)t[2] + k] - xyz[3 * (size_t)t[1] + k] -
+                   xyz[3 * (size_t)t[3] + k];
+        double e = xyz[3 * (size_t)t[2] + k] - xyz[3 * (size_t)t[0] + k];
+        d2 += d * d;
+        s2 += e * e;
+      }
+      XRL_CHECK(d2 <= 1e-18 * s2, XRL_EINVAL, "a 4-vertex panel is not a parallelogram");
+    }
+  }
+  c->xyz.assign(xyz, xyz + 3 * n_vert);
+  c->pan.assign(pan4, pan4 + 4 * n);
+  c->cond.assign(n, 0);
+  if (cond_id)
+    for (int64_t i = 0; i < n; ++i) {
+      XRL_CHECK(cond_id[i] >= 0, XRL_EINVAL, "negative conductor id");
+      c->cond[i] = cond_id[i];
+    }
+  c->N = (int)n;
+  c->have_mesh = true;
+  c->ready = false;
+  c->port_src.clear();
+  c->port_sink.clear();
+}
+
 xrl_status xrl_set_mesh(xrl_ctx* c, int64_t n_vert, const double* xyz, int64_t n_tri, const int32_t* tri,
                         const int32_t* cond_id) {
   if (!c) return XRL_EINVAL;
   return guarded(c, [&] {
-    XRL_CHECK(xyz && tri && n_vert > 0 && n_tri > 0 && n_tri < (1LL << 30), XRL_EINVAL, "bad mesh arguments");
-    for (int64_t i = 0; i < 3 * n_vert; ++i) XRL_CHECK(std::isfinite(xyz[i]), XRL_EINVAL, "non-finite vertex");
-    for (int64_t i = 0; i < 3 * n_tri; ++i)
-      XRL_CHECK(tri[i] >= 0 && tri[i] < n_vert, XRL_EINVAL, "triangle vertex index out of range");
-    c->xyz.assign(xyz, xyz + 3 * n_vert);
-    c->tri.assign(tri, tri + 3 * n_tri);
-    c->cond.assign(n_tri, 0);
-    if (cond_id)
-      for (int64_t i = 0; i < n_tri; ++i) {
-        XRL_CHECK(cond_id[i] >= 0, XRL_EINVAL, "negative conductor id");
-        c->cond[i] = cond_id[i];
+    XRL_CHECK(tri && n_tri > 0 && n_tri < (1LL << 30), XRL_EINVAL, "bad mesh arguments");
+    std::vector<int32_t> pan4(4 * (size_t)n_tri);
+    for (int64_t p = 0; p < n_tri; ++p) {
+      for (int k = 0; k < 3; ++k) {
+        XRL_CHECK(tri[3 * p + k] >= 0, XRL_EINVAL, "triangle vertex index out of range");
+        pan4[4 * p + k] = tri[3 * p + k];
       }
-    c->N = (int)n_tri;
-    c->have_mesh = true;
-    c->ready = false;
-    c->port_src.clear();
-    c->port_sink.clear();
+      pan4[4 * p + 3] = -1;
+    }
+    set_mesh_common(c, n_vert, xyz, n_tri, pan4.data(), cond_id);
   });
+}
+
+xrl_status xrl_set_mesh_panels(xrl_ctx* c, int64_t n_vert, const double* xyz, int64_t n_panels,
+                               const int32_t* pan, const int32_t* cond_id) {
+  if (!c) return XRL_EINVAL;
+  return guarded(c, [&] { set_mesh_common(c, n_vert, xyz, n_panels, pan, cond_id); });
 }
 
 xrl_status xrl_set_conductors(xrl_ctx* c, int32_t n_cond, const double* sigma, const double* thickness) {
@@ -285,14 +343,10 @@ xrl_status xrl_setup(xrl_ctx* c) {
     launch_near_fill(c);
     launch_moments(c);
     fmm_prepare(c);
-    std::vector<double> pdiag(c->N, 0.0);
-    for (int p = 0; p < c->N; ++p) {
-      const double* v0 = &c->xyz[3 * (size_t)c->tri[3 * p]];
-      const double* v1 = &c->xyz[3 * (size_t)c->tri[3 * p + 1]];
-      const double* v2 = &c->xyz[3 * (size_t)c->tri[3 * p + 2]];
-      pdiag[p] = self_term_host(v0, v1, v2);
-    }
     const double tq = now_ms();
+    std::vector<int32_t> iota(c->N);
+    std::iota(iota.begin(), iota.end(), 0);
+    const std::vector<double> pdiag = pair_entries(c, iota, iota);   // P_pp with the rule table
     if (c->opt.precond == 3) {
       // diagonal-of-L: the P entry between the two panels of every interior conductor branch
       const Topo& T = c->topo;

@@ -116,39 +116,60 @@ __device__ double product(int r0, int nq, V3 a0, V3 a1, V3 a2, V3 b0, V3 b1, V3 
 }
 
 struct PanelView {
-  const double* vtx;     // [N][9]
+  const double* vtx;     // [N][12] (a triangle's 4th vertex unused)
   const double* cen;     // [N][3]
   const double* area;
   const double* radius;
-  const int32_t* tri;    // [N][3]
+  const int32_t* tri;    // [N][4], -1 in slot 3 for a triangle
   const int32_t* cidx;   // [N]
 };
 
-// P entry for Morton ranks k, l
-__device__ double p_entry(const PanelView& pv, int k, int l) {
-  if (k == l) {
-    const double* v = pv.vtx + 9 * (size_t)k;
-    return self_term(ld3(v), ld3(v + 3), ld3(v + 6));
+// One triangle of the rule table: a triangle panel itself, or half s of a
+// rectangle (v0, v1, v2) / (v0, v2, v3), with its own area, centroid and radius.
+struct SubTri {
+  V3 v[3];
+  int32_t id[3];
+  double area, r;
+  V3 c;
+};
+
+__device__ __forceinline__ int n_sub(const PanelView& pv, int k) { return pv.tri[4 * (size_t)k + 3] >= 0 ? 2 : 1; }
+
+__device__ SubTri sub_tri(const PanelView& pv, int k, int s) {
+  const double* v = pv.vtx + 12 * (size_t)k;
+  const int32_t* t = pv.tri + 4 * (size_t)k;
+  const int i1 = s == 0 ? 1 : 2, i2 = s == 0 ? 2 : 3;
+  SubTri st;
+  st.v[0] = ld3(v);
+  st.v[1] = ld3(v + 3 * i1);
+  st.v[2] = ld3(v + 3 * i2);
+  st.id[0] = t[0];
+  st.id[1] = t[i1];
+  st.id[2] = t[i2];
+  if (t[3] < 0) {
+    st.area = pv.area[k];
+    st.c = ld3(pv.cen + 3 * (size_t)k);
+    st.r = pv.radius[k];
+  } else {
+    st.c = {__ddiv_rn(__dadd_rn(__dadd_rn(st.v[0].x, st.v[1].x), st.v[2].x), 3.0),
+            __ddiv_rn(__dadd_rn(__dadd_rn(st.v[0].y, st.v[1].y), st.v[2].y), 3.0),
+            __ddiv_rn(__dadd_rn(__dadd_rn(st.v[0].z, st.v[1].z), st.v[2].z), 3.0)};
+    st.area = 0.5 * nrm(cross(sub(st.v[1], st.v[0]), sub(st.v[2], st.v[0])));
+    st.r = fmax(fmax(nrm(sub(st.v[0], st.c)), nrm(sub(st.v[1], st.c))), nrm(sub(st.v[2], st.c)));
   }
-  int a = k, b = l;
-  if (pv.cidx[k] > pv.cidx[l]) {
-    a = l;
-    b = k;
-  }
-  const double* va = pv.vtx + 9 * (size_t)a;
-  const double* vb = pv.vtx + 9 * (size_t)b;
-  const int32_t* ta = pv.tri + 3 * (size_t)a;
-  const int32_t* tb = pv.tri + 3 * (size_t)b;
+  return st;
+}
+
+// rule-table entry of two distinct triangles, A the lower one in the caller order
+__device__ double p_tri(const SubTri& A, const SubTri& B) {
   bool sa[3], sb[3];
   int ns = 0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    sa[i] = (ta[i] == tb[0]) || (ta[i] == tb[1]) || (ta[i] == tb[2]);
-    sb[i] = (tb[i] == ta[0]) || (tb[i] == ta[1]) || (tb[i] == ta[2]);
+    sa[i] = (A.id[i] == B.id[0]) || (A.id[i] == B.id[1]) || (A.id[i] == B.id[2]);
+    sb[i] = (B.id[i] == A.id[0]) || (B.id[i] == A.id[1]) || (B.id[i] == A.id[2]);
     ns += sa[i] ? 1 : 0;
   }
-  V3 A[3] = {ld3(va), ld3(va + 3), ld3(va + 6)};
-  V3 B[3] = {ld3(vb), ld3(vb + 3), ld3(vb + 6)};
   if (ns >= 1) {
     bool edge = (ns == 2);
     // edge rule: start at the non-shared vertex; vertex rule: at the shared vertex
@@ -159,38 +180,77 @@ __device__ double p_entry(const PanelView& pv, int k, int l) {
       if (edge ? !sb[i] : sb[i]) fb = i;
     }
     int r0 = edge ? kRE : kRV;
-    double s1 = semi(r0, 100, A[fa], A[(fa + 1) % 3], A[(fa + 2) % 3], B[0], B[1], B[2], pv.area[b]);
-    double s2 = semi(r0, 100, B[fb], B[(fb + 1) % 3], B[(fb + 2) % 3], A[0], A[1], A[2], pv.area[a]);
+    double s1 = semi(r0, 100, A.v[fa], A.v[(fa + 1) % 3], A.v[(fa + 2) % 3], B.v[0], B.v[1], B.v[2], B.area);
+    double s2 = semi(r0, 100, B.v[fb], B.v[(fb + 1) % 3], B.v[(fb + 2) % 3], A.v[0], A.v[1], A.v[2], A.area);
     return (s1 + s2) * 0.5;
   }
-  const double* ca = pv.cen + 3 * (size_t)a;
-  const double* cb = pv.cen + 3 * (size_t)b;
-  double dx = __dsub_rn(ca[0], cb[0]), dy = __dsub_rn(ca[1], cb[1]), dz = __dsub_rn(ca[2], cb[2]);
+  double dx = __dsub_rn(A.c.x, B.c.x), dy = __dsub_rn(A.c.y, B.c.y), dz = __dsub_rn(A.c.z, B.c.z);
   double d = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-  double q = __ddiv_rn(d, __dadd_rn(pv.radius[a], pv.radius[b]));
-  if (q < kQNear) return semi(kR8, 64, A[0], A[1], A[2], B[0], B[1], B[2], pv.area[b]);
-  if (q < kQSemi) return semi(kR5, 25, A[0], A[1], A[2], B[0], B[1], B[2], pv.area[b]);
-  if (q < kQFar) return product(kR4, 16, A[0], A[1], A[2], B[0], B[1], B[2]);
-  return product(kR3, 9, A[0], A[1], A[2], B[0], B[1], B[2]);
+  double q = __ddiv_rn(d, __dadd_rn(A.r, B.r));
+  if (q < kQNear) return semi(kR8, 64, A.v[0], A.v[1], A.v[2], B.v[0], B.v[1], B.v[2], B.area);
+  if (q < kQSemi) return semi(kR5, 25, A.v[0], A.v[1], A.v[2], B.v[0], B.v[1], B.v[2], B.area);
+  if (q < kQFar) return product(kR4, 16, A.v[0], A.v[1], A.v[2], B.v[0], B.v[1], B.v[2]);
+  return product(kR3, 9, A.v[0], A.v[1], A.v[2], B.v[0], B.v[1], B.v[2]);
+}
+
+// P entry for Morton ranks k, l.  A rectangle's entries are the area-weighted
+// sums over its two triangles, P_kl = sum_i sum_j (a_i/A_k)(a_j/A_l) P_ij.
+__device__ double p_entry(const PanelView& pv, int k, int l) {
+  if (k == l) {
+    if (n_sub(pv, k) == 1) {
+      const double* v = pv.vtx + 12 * (size_t)k;
+      return self_term(ld3(v), ld3(v + 3), ld3(v + 6));
+    }
+    const SubTri s0 = sub_tri(pv, k, 0), s1 = sub_tri(pv, k, 1);
+    const double w0 = s0.area / pv.area[k], w1 = s1.area / pv.area[k];
+    return w0 * w0 * self_term(s0.v[0], s0.v[1], s0.v[2]) + 2.0 * w0 * w1 * p_tri(s0, s1) +
+           w1 * w1 * self_term(s1.v[0], s1.v[1], s1.v[2]);
+  }
+  int a = k, b = l;
+  if (pv.cidx[k] > pv.cidx[l]) {
+    a = l;
+    b = k;
+  }
+  const int na = n_sub(pv, a), nb = n_sub(pv, b);
+  if (na == 1 && nb == 1) return p_tri(sub_tri(pv, a, 0), sub_tri(pv, b, 0));
+  double acc = 0.0;
+  for (int i = 0; i < na; ++i) {
+    const SubTri A = sub_tri(pv, a, i);
+    const double wa = A.area / pv.area[a];
+    for (int j = 0; j < nb; ++j) {
+      const SubTri B = sub_tri(pv, b, j);
+      acc += wa * (B.area / pv.area[b]) * p_tri(A, B);
+    }
+  }
+  return acc;
 }
 
 // ---- kernels -------------------------------------------------------------------------
-__global__ void k_geometry(int N, const double* __restrict__ xyz, const int32_t* __restrict__ tri,
+__global__ void k_geometry(int N, const double* __restrict__ xyz, const int32_t* __restrict__ pan,
                            double* __restrict__ cen, double* __restrict__ area, double* __restrict__ radius) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
-  const double* v0 = xyz + 3 * (size_t)tri[3 * p];
-  const double* v1 = xyz + 3 * (size_t)tri[3 * p + 1];
-  const double* v2 = xyz + 3 * (size_t)tri[3 * p + 2];
+  const int32_t* t = pan + 4 * (size_t)p;
+  const int nv = t[3] >= 0 ? 4 : 3;
+  const double* vs[4];
+  for (int i = 0; i < nv; ++i) vs[i] = xyz + 3 * (size_t)t[i];
+  // vertex mean, FMA-free: ((v0 + v1) + v2) / 3, or (((v0 + v1) + v2) + v3) / 4
   double c[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) c[k] = __ddiv_rn(__dadd_rn(__dadd_rn(v0[k], v1[k]), v2[k]), 3.0);
-  V3 e1 = {v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2]};
-  V3 e2 = {v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2]};
-  area[p] = 0.5 * nrm(cross(e1, e2));
+  for (int k = 0; k < 3; ++k) {
+    double s3 = __dadd_rn(__dadd_rn(vs[0][k], vs[1][k]), vs[2][k]);
+    c[k] = nv == 4 ? __ddiv_rn(__dadd_rn(s3, vs[3][k]), 4.0) : __ddiv_rn(s3, 3.0);
+  }
+  V3 e1 = {vs[1][0] - vs[0][0], vs[1][1] - vs[0][1], vs[1][2] - vs[0][2]};
+  V3 e2 = {vs[2][0] - vs[0][0], vs[2][1] - vs[0][1], vs[2][2] - vs[0][2]};
+  double ar = 0.5 * nrm(cross(e1, e2));
+  if (nv == 4) {
+    V3 e3 = {vs[3][0] - vs[0][0], vs[3][1] - vs[0][1], vs[3][2] - vs[0][2]};
+    ar += 0.5 * nrm(cross(e2, e3));
+  }
+  area[p] = ar;
   double r = 0.0;
-  const double* vs[3] = {v0, v1, v2};
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < nv; ++i) {
     V3 d = {vs[i][0] - c[0], vs[i][1] - c[1], vs[i][2] - c[2]};
     r = fmax(r, nrm(d));
   }
@@ -263,10 +323,10 @@ __global__ void k_gather_panels(int N, const int32_t* __restrict__ perm, const d
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   int p = perm[r];
-  for (int v = 0; v < 3; ++v) {
-    int id = tri_in[3 * (size_t)p + v];
-    tri[3 * (size_t)r + v] = id;
-    for (int k = 0; k < 3; ++k) vtx[9 * (size_t)r + 3 * v + k] = xyz[3 * (size_t)id + k];
+  for (int v = 0; v < 4; ++v) {
+    int id = tri_in[4 * (size_t)p + v];
+    tri[4 * (size_t)r + v] = id;
+    for (int k = 0; k < 3; ++k) vtx[12 * (size_t)r + 3 * v + k] = id >= 0 ? xyz[3 * (size_t)id + k] : 0.0;
   }
   for (int k = 0; k < 3; ++k) cen[3 * (size_t)r + k] = cen_in[3 * (size_t)p + k];
   area[r] = area_in[p];
@@ -327,7 +387,9 @@ __global__ void k_direct(PanelView pv, int N, int nc, const double* __restrict__
 }
 
 // moments S[i][(n,m,re/im)] = (1/A) int_i conj(Y_n^m((y - c_leaf)/h)) dS (exact with the rule)
-__global__ void k_moments(int N, int p, const double* __restrict__ vtx, const int32_t* __restrict__ leaf_of,
+// (a rectangle integrates its two triangles, each weighted by its share of the area)
+__global__ void k_moments(int N, int p, const double* __restrict__ vtx, const int32_t* __restrict__ tri,
+                          const double* __restrict__ area, const int32_t* __restrict__ leaf_of,
                           const double* __restrict__ leaf_ctr, double inv_h, const double* __restrict__ rule,
                           int nq, double* __restrict__ S) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -336,12 +398,22 @@ __global__ void k_moments(int N, int p, const double* __restrict__ vtx, const in
   double acc[169];
   double yr[13][13], yi[13][13];
   for (int k = 0; k < nc; ++k) acc[k] = 0.0;
-  const double* v = vtx + 9 * (size_t)i;
+  const double* pv = vtx + 12 * (size_t)i;
   const double* c = leaf_ctr + 3 * (size_t)leaf_of[i];
-  for (int q = 0; q < nq; ++q) {
-    const double* r = rule + 4 * q;
+  const int nsub = tri[4 * (size_t)i + 3] >= 0 ? 2 : 1;
+  for (int q = 0; q < nq * nsub; ++q) {
+    const int s = q / nq;
+    const double* r = rule + 4 * (q - s * nq);
+    const double* v0 = pv;
+    const double* v1 = pv + 3 * (1 + s);
+    const double* v2 = pv + 3 * (2 + s);
+    double ws = 1.0;
+    if (nsub == 2) {
+      V3 e1 = {v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2]}, e2 = {v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2]};
+      ws = 0.5 * nrm(cross(e1, e2)) / area[i];
+    }
     double x[3];
-    for (int k = 0; k < 3; ++k) x[k] = ((r[0] * v[k] + r[1] * v[3 + k] + r[2] * v[6 + k]) - c[k]) * inv_h;
+    for (int k = 0; k < 3; ++k) x[k] = ((r[0] * v0[k] + r[1] * v1[k] + r[2] * v2[k]) - c[k]) * inv_h;
     double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     // regular harmonics, m >= 0 (Condon-Shortley phase): Y_m^m = -(x+iy)/(2m) Y_{m-1}^{m-1}
     yr[0][0] = 1.0;
@@ -359,7 +431,7 @@ __global__ void k_moments(int N, int p, const double* __restrict__ vtx, const in
         yi[n][m] = ((2.0 * n - 1.0) * x[2] * yi[n - 1][m] - r2 * p2i) / den;
       }
     }
-    double w = r[3];
+    double w = r[3] * ws;
     for (int n = 0; n <= p; ++n) {
       acc[n * n] += w * yr[n][0];
       for (int m = 1; m <= n; ++m) {
@@ -425,7 +497,7 @@ void launch_geometry(xrl_ctx* c) {
   DBuf<double> xyz;
   xyz.upload(c->alloc, c->xyz);
   DBuf<int32_t> tri;
-  tri.upload(c->alloc, c->tri);
+  tri.upload(c->alloc, c->pan);
   DBuf<double> cen0, area0, rad0, box;
   cen0.alloc(c->alloc, 3 * (size_t)N);
   area0.alloc(c->alloc, N);
@@ -444,11 +516,11 @@ void launch_geometry(xrl_ctx* c) {
   c->tree.side = hbox[3];
   build_tree(c, keys);
   c->d.perm.upload(c->alloc, c->tree.perm);
-  c->d.vtx.alloc(c->alloc, 9 * (size_t)N);
+  c->d.vtx.alloc(c->alloc, 12 * (size_t)N);
   c->d.cen.alloc(c->alloc, 3 * (size_t)N);
   c->d.area.alloc(c->alloc, N);
   c->d.radius.alloc(c->alloc, N);
-  c->d.tri.alloc(c->alloc, 3 * (size_t)N);
+  c->d.tri.alloc(c->alloc, 4 * (size_t)N);
   c->d.cidx.alloc(c->alloc, N);
   k_gather_panels<<<nb, 256, 0, c->stream>>>(N, c->d.perm.p, xyz.p, tri.p, cen0.p, area0.p, rad0.p, c->d.vtx.p,
                                              c->d.cen.p, c->d.area.p, c->d.radius.p, c->d.tri.p, c->d.cidx.p);
@@ -520,8 +592,8 @@ void launch_moments(xrl_ctx* c) {
   DBuf<int32_t> leaf_of;
   leaf_of.upload(c->alloc, t.leaf_of);
   c->d.mom.alloc(c->alloc, (size_t)N * c->ncoef);
-  k_moments<<<(N + 127) / 128, 128, 0, c->stream>>>(N, p, c->d.vtx.p, leaf_of.p, dctr.p, 1.0 / h, drule.p,
-                                                     qm * qm, c->d.mom.p);
+  k_moments<<<(N + 127) / 128, 128, 0, c->stream>>>(N, p, c->d.vtx.p, c->d.tri.p, c->d.area.p, leaf_of.p, dctr.p,
+                                                     1.0 / h, drule.p, qm * qm, c->d.mom.p);
   XRL_CUDA(cudaGetLastError());
   XRL_CUDA(cudaStreamSynchronize(c->stream));
 }

@@ -52,12 +52,12 @@ __global__ void k_panel_currents(int N, int nsys, int nloop, int nport, const in
   int r = (int)(idx % N), s = (int)(idx / N);
   const cplx* xs = x + (size_t)s * nloop;
   cplx ip[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
-  for (int k = 0; k < 3; ++k) {
-    int b = pan_br[3 * r + k];
+  for (int k = 0; k < kPanEdges; ++k) {
+    int b = pan_br[kPanEdges * r + k];
     if (b < 0) continue;
     cplx ie = make_double2(0, 0);
     for (int q = mt_ptr[b]; q < mt_ptr[b + 1]; ++q) ie = mt_val[q] > 0 ? cadd(ie, xs[mt_col[q]]) : csub(ie, xs[mt_col[q]]);
-    for (int t = 0; t < 3; ++t) ip[t] = cadd(ip[t], cscale(ie, pan_rho[9 * (size_t)r + 3 * k + t]));
+    for (int t = 0; t < 3; ++t) ip[t] = cadd(ip[t], cscale(ie, pan_rho[3 * kPanEdges * (size_t)r + 3 * k + t]));
   }
   cplx sc = make_double2(1.0, 0.0);
   if (normalize) {
@@ -87,7 +87,7 @@ __global__ void k_features(int N, int nf, int np, const int32_t* __restrict__ pe
   int s = (int)(idx / N);
   int f = s / np, q = s % np;
   int p = perm[r];
-  const double* v = vtx + 9 * (size_t)r;
+  const double* v = vtx + 12 * (size_t)r;   // the normal from the first three vertices (panels are planar)
   double e1[3] = {v[3] - v[0], v[4] - v[1], v[5] - v[2]}, e2[3] = {v[6] - v[0], v[7] - v[1], v[8] - v[2]};
   double nr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
   double nn = sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
@@ -95,12 +95,12 @@ __global__ void k_features(int N, int nf, int np, const int32_t* __restrict__ pe
   // curvature proxy: mean (1 - |n . n_j|) over the panels sharing a branch with this one
   double curv = 0.0;
   int ncur = 0;
-  for (int k = 0; k < 3; ++k) {
-    int b = pan_br[3 * r + k];
+  for (int k = 0; k < kPanEdges; ++k) {
+    int b = pan_br[kPanEdges * r + k];
     if (b < 0) continue;
     int o = br_pan[2 * b] == r ? br_pan[2 * b + 1] : br_pan[2 * b];
     if (o < 0) continue;
-    const double* w = vtx + 9 * (size_t)o;
+    const double* w = vtx + 12 * (size_t)o;
     double a1[3] = {w[3] - w[0], w[4] - w[1], w[5] - w[2]}, a2[3] = {w[6] - w[0], w[7] - w[1], w[8] - w[2]};
     double m[3] = {a1[1] * a2[2] - a1[2] * a2[1], a1[2] * a2[0] - a1[0] * a2[2], a1[0] * a2[1] - a1[1] * a2[0]};
     double mm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);

@@ -36,6 +36,7 @@ namespace xrl {
 
 constexpr int kMaxBand = 63;     // window (b+1)^2 complex in shared memory
 constexpr int kMaxBorder = 16;
+constexpr double kNullPivot2 = 1e-20;   // (|pivot| / |original diagonal|)^2 below which a pivot is null
 
 // ---- asynchronous global -> shared copies (16 bytes each) ----------------------------------
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -312,7 +313,9 @@ __global__ void k_band_finish(int nf, int n, int b, cplx* __restrict__ fac, cplx
   const size_t fbase = rowg - i;        // f * n
   const int rs32 = band_rs<float2>(b);
   if (t == b) {
-    cplx inv = cdiv(make_double2(1.0, 0.0), fac[e]);
+    // a stored pivot of exactly 0 is a deflated null pivot (k_band_factor_blk): 1/D := 0
+    const cplx d = fac[e];
+    cplx inv = (d.x == 0.0 && d.y == 0.0) ? make_double2(0.0, 0.0) : cdiv(make_double2(1.0, 0.0), d);
     fac[e] = inv;
     facT[e] = inv;
     if (fac32) {
@@ -442,7 +445,18 @@ __global__ void k_band_factor_blk(int n, int b, int P, int m, int nmat, const do
   __syncwarp();
   for (int k = 0; k < mm; ++k) {
     const int sk = k % nb1;
-    const cplx inv = cdiv(make_double2(1.0, 0.0), win[sk * nb1 + b]);
+    // Null pivot: a pivot at rounding level of the row's own diagonal marks a
+    // null direction of Q (loop currents with no panel current, e.g. the
+    // checkerboard pattern of vertex loops on a grid of rectangles, which the
+    // pulse basis of eq. 4 cannot see; Z shares it and the port right-hand
+    // sides are orthogonal to it).  It is deflated: no elimination with it and
+    // a stored pivot of 0 (1/D := 0), so the solve leaves that direction at zero.
+    const cplx dk = win[sk * nb1 + b];
+    const cplx a0 = pencil(band_val + (size_t)(s0 + k) * nb1 + b, stride, nmat, z, wp);
+    const bool null_pivot = dk.x * dk.x + dk.y * dk.y <= kNullPivot2 * (a0.x * a0.x + a0.y * a0.y);
+    const cplx inv = null_pivot ? make_double2(0.0, 0.0) : cdiv(make_double2(1.0, 0.0), dk);
+    __syncwarp();
+    if (null_pivot && lane == 0) win[sk * nb1 + b] = make_double2(0.0, 0.0);
     for (int t = lane; t < b; t += 32) {
       const int i = k + 1 + t;
       cplx o = make_double2(0.0, 0.0);

@@ -95,8 +95,8 @@ __global__ void k_gather(int N, int nsys, int nloop, const int32_t* __restrict__
   int r = (int)(idx / nsys), s = (int)(idx % nsys);
   const cplx* vs = v + (size_t)s * nloop;
   C ip[3] = {cmk<C>((T)0, (T)0), cmk<C>((T)0, (T)0), cmk<C>((T)0, (T)0)};
-  for (int k = 0; k < 3; ++k) {
-    int b = pan_br[3 * r + k];
+  for (int k = 0; k < kPanEdges; ++k) {
+    int b = pan_br[kPanEdges * r + k];
     if (b < 0) continue;
     C ie = cmk<C>((T)0, (T)0);
     for (int q = mt_ptr[b]; q < mt_ptr[b + 1]; ++q) {
@@ -104,7 +104,7 @@ __global__ void k_gather(int N, int nsys, int nloop, const int32_t* __restrict__
       const C xc = cmk<C>((T)x.x, (T)x.y);
       ie = mt_val[q] > 0 ? cadd_t(ie, xc) : csub_t(ie, xc);
     }
-    const double* rho = pan_rho + 9 * (size_t)r + 3 * k;
+    const double* rho = pan_rho + 3 * kPanEdges * (size_t)r + 3 * k;
     for (int t = 0; t < 3; ++t) ip[t] = cadd_t(ip[t], cscale_t(ie, (T)rho[t]));
   }
   T* out = X + (size_t)r * 6 * nsys + 6 * s;
@@ -577,8 +577,8 @@ void solver_prepare(xrl_ctx* c) {
   Topo& T = c->topo;
   Tree& tr = c->tree;
   const int N = c->N;
-  std::vector<int32_t> pan_br(3 * (size_t)N, -1), pan_mat(N, -1), br_pan(2 * (size_t)T.n_cb, -1);
-  std::vector<double> pan_rho(9 * (size_t)N, 0.0), br_rho(6 * (size_t)T.n_cb, 0.0);
+  std::vector<int32_t> pan_br(kPanEdges * (size_t)N, -1), pan_mat(N, -1), br_pan(2 * (size_t)T.n_cb, -1);
+  std::vector<double> pan_rho(3 * kPanEdges * (size_t)N, 0.0), br_rho(6 * (size_t)T.n_cb, 0.0);
   std::vector<int> slot(N, 0);
   for (int b = 0; b < T.n_cb; ++b)
     for (int side = 0; side < 2; ++side) {
@@ -586,12 +586,12 @@ void solver_prepare(xrl_ctx* c) {
       if (p < 0) continue;
       int r = tr.rank[p];
       int k = slot[p]++;
-      XRL_CHECK(k < 3, XRL_ETOPO, "internal: a panel has more than three branches");
-      pan_br[3 * (size_t)r + k] = b;
+      XRL_CHECK(k < kPanEdges, XRL_ETOPO, "internal: a panel has more branches than edges");
+      pan_br[kPanEdges * (size_t)r + k] = b;
       br_pan[2 * (size_t)b + side] = r;
       for (int t = 0; t < 3; ++t) {
         double v = T.br_rho[side][3 * (size_t)b + t];
-        pan_rho[9 * (size_t)r + 3 * k + t] = v;
+        pan_rho[3 * kPanEdges * (size_t)r + 3 * k + t] = v;
         br_rho[6 * (size_t)b + 3 * side + t] = v;
       }
     }

@@ -60,7 +60,8 @@ void build_topology(xrl_ctx* c) {
   Topo& T = c->topo;
   const int N = c->N;
   const int nv = (int)(c->xyz.size() / 3);
-  const auto& tri = c->tri;
+  const auto& pan = c->pan;
+  auto nvert = [&](int p) { return panel_nv(pan, p); };
   // terminals from port panel lists (identical lists share a terminal)
   std::vector<int> term(N, -1);
   std::map<std::vector<int32_t>, int> term_id;
@@ -98,13 +99,15 @@ void build_topology(xrl_ctx* c) {
     int a, b, p;
   };
   std::vector<HE> he;
-  he.reserve(3 * (size_t)N);
-  for (int p = 0; p < N; ++p)
-    for (int e = 0; e < 3; ++e) {
-      int a = tri[3 * p + e], b = tri[3 * p + (e + 1) % 3];
-      XRL_CHECK(a != b, XRL_ETOPO, "degenerate triangle");
+  he.reserve(kPanEdges * (size_t)N);
+  for (int p = 0; p < N; ++p) {
+    const int nvp = nvert(p);
+    for (int e = 0; e < nvp; ++e) {   // a rectangle's diagonal is not an edge
+      int a = pan[4 * p + e], b = pan[4 * p + (e + 1) % nvp];
+      XRL_CHECK(a != b, XRL_ETOPO, "degenerate panel");
       he.push_back({std::min(a, b), std::max(a, b), p});
     }
+  }
   std::sort(he.begin(), he.end(), [](const HE& x, const HE& y) {
     return x.a != y.a ? x.a < y.a : (x.b != y.b ? x.b < y.b : x.p < y.p);
   });
@@ -113,7 +116,7 @@ void build_topology(xrl_ctx* c) {
     XRL_CHECK(he[2 * e].a == he[2 * e + 1].a && he[2 * e].b == he[2 * e + 1].b &&
                   (2 * e + 2 >= (int)he.size() || he[2 * e + 2].a != he[2 * e].a ||
                    he[2 * e + 2].b != he[2 * e].b),
-              XRL_ETOPO, "mesh is not a closed 2-manifold (an edge is not shared by exactly two triangles)");
+              XRL_ETOPO, "mesh is not a closed 2-manifold (an edge is not shared by exactly two panels)");
   }
   std::vector<int> edge_p(2 * ne), edge_v(2 * ne), edge_branch(ne, -1);
   for (int e = 0; e < ne; ++e) {
@@ -125,9 +128,7 @@ void build_topology(xrl_ctx* c) {
   // panel centroids (host copy, for rho)
   auto X = [&](int v, int k) { return c->xyz[3 * (size_t)v + k]; };
   std::vector<double> cen(3 * (size_t)N);
-  for (int p = 0; p < N; ++p)
-    for (int k = 0; k < 3; ++k)
-      cen[3 * p + k] = (X(tri[3 * p], k) + X(tri[3 * p + 1], k) + X(tri[3 * p + 2], k)) / 3.0;
+  for (int p = 0; p < N; ++p) panel_centroid_host(c->xyz, pan, p, &cen[3 * (size_t)p]);
 
   T.br_tail.clear();
   T.br_head.clear();
@@ -181,9 +182,10 @@ void build_topology(xrl_ctx* c) {
     }
     auto dir = [&](int p, int a, int b) {   // +1 if p (as stored, then flipped) traverses a->b
       int s = 0;
-      for (int k = 0; k < 3; ++k)
-        if (tri[3 * p + k] == a && tri[3 * p + (k + 1) % 3] == b) s = 1;
-        else if (tri[3 * p + k] == b && tri[3 * p + (k + 1) % 3] == a) s = -1;
+      const int nvp = nvert(p);
+      for (int k = 0; k < nvp; ++k)
+        if (pan[4 * p + k] == a && pan[4 * p + (k + 1) % nvp] == b) s = 1;
+        else if (pan[4 * p + k] == b && pan[4 * p + (k + 1) % nvp] == a) s = -1;
       return flip[p] ? -s : s;
     };
     for (int r = 0; r < N; ++r) {
@@ -208,10 +210,11 @@ void build_topology(xrl_ctx* c) {
     }
   }
   auto follows = [&](int p, int v, int a) {   // in oriented panel p, does a directly follow v?
-    int o[3] = {tri[3 * p], tri[3 * p + 1], tri[3 * p + 2]};
-    if (flip[p]) std::swap(o[1], o[2]);
-    for (int k = 0; k < 3; ++k)
-      if (o[k] == v) return o[(k + 1) % 3] == a;
+    const int nvp = nvert(p);
+    int o[4] = {pan[4 * p], pan[4 * p + 1], pan[4 * p + 2], pan[4 * p + 3]};
+    if (flip[p]) std::swap(o[1], o[nvp - 1]);   // reversed cycle (v0, v_last, ..., v1)
+    for (int k = 0; k < nvp; ++k)
+      if (o[k] == v) return o[(k + 1) % nvp] == a;
     return false;
   };
 
@@ -417,7 +420,6 @@ void build_precond_pattern(xrl_ctx* c, const std::vector<double>& pdiag, const s
   const int N = c->N;
   const int nm = T.n_mat;
   const int W = nm + 1;
-  auto X = [&](int v, int k) { return c->xyz[3 * (size_t)v + k]; };
   auto dot3 = [](const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
   std::unordered_map<uint64_t, std::vector<double>> acc;
   acc.reserve((size_t)T.n_loops * 24);
@@ -441,14 +443,7 @@ void build_precond_pattern(xrl_ctx* c, const std::vector<double>& pdiag, const s
       if (T.br_pan[s][b] >= 0) pb[T.br_pan[s][b]].push_back({b, s});
   for (int p = 0; p < N; ++p) {
     if (T.live_of_panel[p] < 0) continue;
-    const int32_t* t = &c->tri[3 * p];
-    double e1[3], e2[3];
-    for (int k = 0; k < 3; ++k) {
-      e1[k] = X(t[1], k) - X(t[0], k);
-      e2[k] = X(t[2], k) - X(t[0], k);
-    }
-    double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-    const double area = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    const double area = panel_area_host(c->xyz, c->pan, p);
     const int mat = T.mat_of_cond[c->cond[p]];
     for (auto& bi : pb[p])
       for (auto& bj : pb[p]) {

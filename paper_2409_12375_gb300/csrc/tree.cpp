@@ -94,11 +94,10 @@ void build_tree(xrl_ctx* c, const std::vector<uint64_t>& keys) {
   // size cap: side / 2^l >= 2 r_max
   double rmax = 0.0;
   for (int p = 0; p < N; ++p) {
-    const int32_t* tv = &c->tri[3 * (size_t)p];
+    const int32_t* tv = &c->pan[4 * (size_t)p];
     double cc[3];
-    for (int k = 0; k < 3; ++k)
-      cc[k] = (c->xyz[3 * (size_t)tv[0] + k] + c->xyz[3 * (size_t)tv[1] + k] + c->xyz[3 * (size_t)tv[2] + k]) / 3.0;
-    for (int v = 0; v < 3; ++v) {
+    panel_centroid_host(c->xyz, c->pan, p, cc);
+    for (int v = 0; v < panel_nv(c->pan, p); ++v) {
       double d2 = 0.0;
       for (int k = 0; k < 3; ++k) {
         double d = c->xyz[3 * (size_t)tv[v] + k] - cc[k];

@@ -111,6 +111,16 @@ constexpr double kQNear = 1.5, kQSemi = 3.0, kQFar = 10.0;
 constexpr int kEdgeN = 10, kEdgeK = 3, kVertN = 10, kVertK = 3;
 constexpr int kNearQ = 8, kSemiQ = 5, kMidQ = 4, kFarQ = 3;
 
+// Panels are triangles or rectangles (parallelograms): at most four edges, and a
+// rectangle (v0, v1, v2, v3) is integrated as its triangles (v0, v1, v2), (v0, v2, v3).
+constexpr int kPanEdges = 4;
+
+// Host geometry of caller panel p (vertex ids pan[4p..4p+3], -1 in slot 3 for a triangle):
+// vertex count, vertex-mean centroid (the centroid of a triangle or a parallelogram) and area.
+inline int panel_nv(const std::vector<int32_t>& pan, int p) { return pan[4 * (size_t)p + 3] >= 0 ? 4 : 3; }
+void panel_centroid_host(const std::vector<double>& xyz, const std::vector<int32_t>& pan, int p, double c[3]);
+double panel_area_host(const std::vector<double>& xyz, const std::vector<int32_t>& pan, int p);
+
 // ---- host-side setup products -------------------------------------------------
 struct Tree {
   int L = 0;                                   // leaf level; levels 0..L
@@ -169,11 +179,11 @@ struct Topo {
 // ---- device-resident state ------------------------------------------------------
 struct Dev {
   // Morton-ordered panel data
-  DBuf<double> vtx;        // [N][9] vertices (caller vertex order)
+  DBuf<double> vtx;        // [N][12] vertices (caller vertex order; a triangle's 4th is unused)
   DBuf<double> cen;        // [N][3]
   DBuf<double> area;       // [N]
   DBuf<double> radius;     // [N]
-  DBuf<int32_t> tri;       // [N][3] vertex ids
+  DBuf<int32_t> tri;       // [N][4] vertex ids (-1 in the 4th slot: triangle)
   DBuf<int32_t> cidx;      // [N] caller index
   DBuf<int32_t> perm;      // [N] Morton rank -> caller
   DBuf<uint64_t> keys;     // [N] per caller panel
@@ -216,8 +226,8 @@ struct Dev {
   DBuf<double> X, Y, Mexp, Lexp;
   DBuf<float> X32, Y32, M32, L32;
   // operator data
-  DBuf<int32_t> pan_br;      // [N][3] branch ids per Morton panel (-1 none)
-  DBuf<double> pan_rho;      // [N][3][3] signed rho per (panel, slot)
+  DBuf<int32_t> pan_br;      // [N][kPanEdges] branch ids per Morton panel (-1 none)
+  DBuf<double> pan_rho;      // [N][kPanEdges][3] signed rho per (panel, slot)
   DBuf<int32_t> pan_mat;     // [N] material id (-1 terminal)
   DBuf<int32_t> pan_cond_mat;  // [N] material id of every panel (features)
   DBuf<int32_t> br_pan;      // [B][2] Morton panel (-1 terminal)
@@ -270,7 +280,7 @@ struct xrl_ctx {
   xrl::DevAlloc alloc;
   // inputs
   std::vector<double> xyz;
-  std::vector<int32_t> tri, cond;
+  std::vector<int32_t> pan, cond;   // pan [N][4] vertex ids, -1 in the 4th slot for a triangle
   std::vector<double> sigma, thick;
   std::vector<std::vector<int32_t>> port_src, port_sink;
   bool have_mesh = false, have_cond = false, ready = false;

@@ -59,6 +59,7 @@ SIGNATURES = {
     "xrl_default_options": (None, [ctypes.POINTER(Options)]),
     "xrl_create": (ctypes.c_int, [ctypes.POINTER(Options), ctypes.POINTER(_P)]),
     "xrl_set_mesh": (ctypes.c_int, [_P, ctypes.c_int64, _D, ctypes.c_int64, _I, _I]),
+    "xrl_set_mesh_panels": (ctypes.c_int, [_P, ctypes.c_int64, _D, ctypes.c_int64, _I, _I]),
     "xrl_set_conductors": (ctypes.c_int, [_P, ctypes.c_int32, _D, _D]),
     "xrl_add_port": (ctypes.c_int, [_P, ctypes.c_int64, _I, ctypes.c_int64, _I, _I]),
     "xrl_setup": (ctypes.c_int, [_P]),
@@ -162,12 +163,14 @@ class XRL:
 
     # ---- problem definition -------------------------------------------------
     def set_mesh(self, xyz, tri, cond=None):
+        """tri: [n, 3] triangles, or [n, 4] hybrid panels (-1 in the 4th slot of a triangle)."""
         xyz = np.ascontiguousarray(xyz, np.float64)
         tri = np.ascontiguousarray(tri, np.int32)
         c = None if cond is None else np.ascontiguousarray(cond, np.int32)
         self.n_tri = tri.shape[0]
-        self._check(lib().xrl_set_mesh(self.h, xyz.shape[0], _dp(xyz), tri.shape[0], _ip(tri),
-                                       None if c is None else _ip(c)), self.h)
+        fn = lib().xrl_set_mesh_panels if tri.shape[1] == 4 else lib().xrl_set_mesh
+        self._check(fn(self.h, xyz.shape[0], _dp(xyz), tri.shape[0], _ip(tri),
+                       None if c is None else _ip(c)), self.h)
 
     def set_conductors(self, sigma, thickness):
         s = np.ascontiguousarray(sigma, np.float64)
