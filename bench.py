@@ -447,6 +447,28 @@ def main():
                 xa.close()
             abl["tol_%g" % tol] = row
 
+    # the same coils meshed with rectangles on the straight runs (Sec. II-A hybrid panels), untimed:
+    # same FMM configuration and frequencies; R, L against the triangle sweep above
+    hyb = None
+    if not args.no_ablation and world == 1:
+        import meshgen
+        mh = meshgen.coils(rect=True)
+        mh.freqs = m.freqs
+        xh = pkg.XRL.from_mesh(mh, **opts)
+        xh.solve(mh.freqs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Rh, Lh = xh.solve(mh.freqs)
+        th = time.perf_counter() - t0
+        sh = xh.stats()
+        nf = len(m.freqs)
+        dR = np.max(np.abs(Rh - R).reshape(nf, -1).max(1) / np.abs(R).reshape(nf, -1).max(1))
+        dL = np.max(np.abs(Lh - L).reshape(nf, -1).max(1) / np.abs(L).reshape(nf, -1).max(1))
+        hyb = {"n_panels": sh["n_panels"], "n_rectangles": int(np.sum(mh.tri[:, 3] >= 0)), "n_loops": sh["n_loops"],
+               "fgmres_iters": sh["total_iters"], "s_per_freq_port": th / nsys,
+               "rel_diff_R_vs_triangles": float(dR), "rel_diff_L_vs_triangles": float(dL)}
+        xh.close()
+
     if rank == 0:
         cb = None
         if world == 1 and not args.no_cpu_baseline:
@@ -459,7 +481,7 @@ def main():
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * len(m.freqs),
                         "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * 4},
                 "gpu_launches": launches, "clocks": ck, "roofline": roof, "roofline_phases": roofs, "cpu_baseline": cb,
-                "fmm_mvm_panel_cols_per_s": mvm, "plain_fp64": plain, "precond_ablation": abl,
+                "fmm_mvm_panel_cols_per_s": mvm, "plain_fp64": plain, "precond_ablation": abl, "hybrid_panels": hyb,
                 "solve": {"fgmres_iters": iters, "max_rel_residual": res, "setup_ms": st["setup_ms"],
                           "n_loops": st["n_loops"], "peak_device_bytes": x.stats()["peak_device_bytes"]},
                 "phases_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}

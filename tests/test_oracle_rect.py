@@ -162,3 +162,26 @@ def test_hybrid_coil_topology_and_P():
     Pd = P.dense_P_panels(c.geom)
     assert np.array_equal(Pd, Pd.T)
     assert np.linalg.eigvalsh(Pd).min() > 0
+
+
+def test_rect_grid_null_loop_mode_carries_no_panel_current(rect_bar):
+    """On a grid of rectangles the pulse basis (eq. 4) cannot see the
+    checkerboard circulation: the loop matrix Z of eq. 7 is singular, its
+    null vector gives zero current on every panel (so Z_s and P both miss
+    it), and the port right-hand side is orthogonal to it (the system stays
+    consistent).  The triangulated bar has no such mode."""
+    c = C.Circuit(rect_bar)
+    Pd = P.dense_P_panels(c.geom)
+    Z = c.loop_matrix(1e5, c.potential_part(Pd[np.ix_(c.live, c.live)]))
+    u, s, vh = np.linalg.svd(Z)
+    assert s[-1] < 1e-14 * s[0] and s[-2] > 1e-8 * s[0]
+    x = vh[-1].conj()
+    ip = c.panel_currents(x[:, None])[:, :, 0]          # [3, n_live]
+    ie = c.M[:, :c.n_cb].T @ x
+    assert np.abs(ip).max() < 1e-10 * np.abs(ie).max() * np.abs(c.A).max()
+    assert abs(c.port_rhs()[:, 0] @ x) < 1e-12
+    tri_bar = meshgen.bar(jitter=0.0, n_l=20)
+    ct = C.Circuit(tri_bar)
+    Pt = P.dense_P(P.Geometry(tri_bar.xyz, tri_bar.tri))
+    st = np.linalg.svd(ct.loop_matrix(1e5, ct.potential_part(Pt[np.ix_(ct.live, ct.live)])), compute_uv=False)
+    assert st[-1] > 1e-6 * st[0]
