@@ -195,16 +195,26 @@ def peaks():
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the unchanged kernel on this workload's launch
 # configuration (profiles/top_kernels_coil_sweep.md); None where none exists
-NCU_TRAFFIC = {"m2l": 130.051e6 + 48.901888e6, "m2l64": 295.576e6 + 125.270784e6}
-PHASE_KERNEL = {
-    "p2p": "k_tcp_pack_x + k_xlate_tc<96> (tcgen05 near field, 3-piece BF16)",
-    "m2l": "k_tc_pack_a + k_xlate_tc<96> (tcgen05, 3-piece BF16, 6 products)",
-    "p2p64": "k_ozp_pack_x + k_xlate_oz (tcgen05 near field, 5 integer slices)",
-    "m2l64": "k_oz_pack_a + k_xlate_oz (tcgen05, 5 integer slices, 15 products)",
-    "precond": "k_spike_y/z/x/out apply + k_band_factor_blk/k_spike_cols/k_spike_reduce factor",
-    "operator": "k_gather + k_scatter + k_loop_reduce(_long)",
-    "p2m": "k_p2m_tiled<6>", "l2p": "k_l2p_tiled", "m2m": "k_m2l_tiled<6,0> (list form)",
-    "l2l": "k_m2l_tiled<6,1> (list form)"}
+# ncu DRAM bytes (read + write) per launch of the dominant kernels at the bench's
+# configuration; None until a capture of the current kernels exists
+NCU_TRAFFIC = {"m2l": None, "m2l64": None}
+
+
+def phase_kernel(name, p):
+    """Kernels behind a profiling phase of the mixed-precision sweep at order p."""
+    np_ = ((p + 1) ** 2 + 15) // 16 * 16
+    tc = "k_xlate_tc<%d>" % (64 if np_ <= 64 else 96)
+    return {
+        "p2p": "k_tcp_pack_x + k_xlate_tc<96> (tcgen05 near field, 3-piece BF16)",
+        "m2l": ("k_tc_pack_a + k_xlate_tc2 (tcgen05, two sibling targets per CTA, N = 128, 3-piece BF16, "
+                "6 products)" if np_ == 64 else "k_tc_pack_a + k_xlate_tc<96> (tcgen05, 3-piece BF16, 6 products)"),
+        "p2m": tc + " mode 2 (tcgen05 P2M from the near field's transposed-X image)",
+        "m2m": "k_tc_pack_a + " + tc + " mode 0 over the 8 M2M tables (tcgen05)",
+        "p2p64": "k_ozp_pack_x + k_xlate_oz (tcgen05 near field, 5 integer slices)",
+        "m2l64": "k_oz_pack_a + k_xlate_oz (tcgen05, 5 integer slices, 15 products)",
+        "precond": "k_spike_y/z/x/out apply + k_band_factor_blk/k_spike_cols/k_spike_reduce factor",
+        "operator": "k_gather + k_scatter + k_loop_reduce(_long)",
+        "l2p": "k_l2p_tiled", "l2l": "k_m2l_tiled<6,1> (list form)"}.get(name, name)
 
 
 def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0):
@@ -214,7 +224,7 @@ def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0):
     avg_ms = d["ms"] / max(1, d["launches"])
     mixed = precision == "mixed"
     alg = d["flops"] / (d["ms"] * 1e-3) / 1e12          # algorithmic TFLOP/s
-    out = {"kernel": PHASE_KERNEL.get(name, name), "avg_launch_ms": avg_ms, "launches": d["launches"],
+    out = {"kernel": phase_kernel(name, p), "avg_launch_ms": avg_ms, "launches": d["launches"],
            "traffic": NCU_TRAFFIC.get(name) if mixed else None}
     ncoef = (p + 1) ** 2
     pad = lambda v: (v + 15) // 16 * 16

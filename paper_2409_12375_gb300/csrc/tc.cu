@@ -28,6 +28,8 @@
 // frees its tensor memory.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <vector>
 
@@ -466,6 +468,239 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc(TcArgs a) {
   if (*bad) {
     if (threadIdx.x == 0) atomicExch(a.err, 1);
     // drain this CTA's own copies still in flight
+    if (warp == 0 && lane == 0)
+      for (int it = issued > TC_STAGES ? issued - TC_STAGES : 0; it < issued; ++it)
+        mbar_wait(&full[it % TC_STAGES], (it / TC_STAGES) & 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512) : "memory");
+  }
+}
+
+// ---- M2L for two sibling targets per CTA (coefficients padded to 64) --------------------
+// Sibling boxes share most of their V-list, so one CTA takes a pair of them
+// (t1, t2) and walks the merged list of their sources: per source, the A
+// image (the source's multipoles, 128 columns) is fetched once and multiplied
+// by [B(off1) | B(off2)] with N = 128 (both targets: t1 in D columns 0..63,
+// t2 in 64..127), or by the one table present with N = 64.  Per MMA that is
+// twice the output columns for the same A operand, and one shared-memory A
+// read serves both targets.  Same pieces, products, TMEM buffers (big at
+// 256 q, small at 256 q + 128), per-entry promotion and bounded waits as
+// k_xlate_tc; a target absent from an entry has its half of D skipped by the
+// MMAs and by the drain.
+struct Tc2Args {
+  int nc, nct, Kp, ncoef, src0;
+  size_t a_img, b_img;                 // bytes of one (box, tile) A image / one table image
+  const int32_t* gptr;                 // merged list of group g: [gptr[g], gptr[g + 1])
+  const int32_t* gsrc;                 // source box (global id)
+  const int16_t* goff1;                // table of (t1 - src), -1: t1 absent
+  const int16_t* goff2;                // table of (t2 - src), -1: t2 absent
+  const int32_t* gt1;                  // target boxes of group g (gt2 = -1: single target)
+  const int32_t* gt2;
+  const char* aimg;
+  const char* bimg;
+  float* out;
+  int32_t* err;
+};
+
+// acc[OFF + n] += both accumulators (small first) of one target half, n < 64
+template <int OFF>
+__device__ __forceinline__ void drain_half(float (&acc)[128], uint32_t taddr) {
+#pragma unroll
+  for (int s = 1; s >= 0; --s) {
+#pragma unroll
+    for (int h = 0; h < 64; h += 32) {
+      uint32_t r[32];
+#pragma unroll
+      for (int n0 = 0; n0 < 32; n0 += 16)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+            "[%16];"
+            : "=r"(r[n0 + 0]), "=r"(r[n0 + 1]), "=r"(r[n0 + 2]), "=r"(r[n0 + 3]), "=r"(r[n0 + 4]),
+              "=r"(r[n0 + 5]), "=r"(r[n0 + 6]), "=r"(r[n0 + 7]), "=r"(r[n0 + 8]), "=r"(r[n0 + 9]),
+              "=r"(r[n0 + 10]), "=r"(r[n0 + 11]), "=r"(r[n0 + 12]), "=r"(r[n0 + 13]), "=r"(r[n0 + 14]),
+              "=r"(r[n0 + 15])
+            : "r"(taddr + 128u * s + (uint32_t)(h + n0))
+            : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int n = 0; n < 32; ++n) acc[OFF + h + n] += __uint_as_float(r[n]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
+  constexpr int NH = 64;   // coefficients per target (padded)
+  extern __shared__ uint8_t tc_smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
+  const int a_stage = tc_chunk_bytes(TC_ROWS, TC_KC);
+  const int stage_bytes = a_stage + tc_chunk_bytes(2 * NH, TC_KC);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + TC_STAGES * stage_bytes);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* tfull = empty + TC_STAGES;
+  uint64_t* tfree = tfull + 2;
+  uint64_t* mdone = tfree + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
+  int* bad = reinterpret_cast<int*>(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ct = blockIdx.x, g = blockIdx.y;
+  const int vs = a.gptr[g], ve = a.gptr[g + 1];
+  const int nv = ve - vs;
+  const int nch = (a.Kp + TC_KC - 1) / TC_KC;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&tfull[q], 1);
+      mbar_init(&tfree[q], 4);
+    }
+    mbar_init(mdone, 1);
+    *bad = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_u32(tslot)), "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  int issued = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      bool stop = false;
+      for (int v = vs; v < ve && !stop; ++v) {
+        const size_t aoff = ((size_t)(a.gsrc[v] - a.src0) * a.nct + ct) * a.a_img;
+        const int o[2] = {a.goff1[v], a.goff2[v]};
+        for (int c = 0; c < nch; ++c, ++it) {
+          const int st = it % TC_STAGES, u = it / TC_STAGES;
+          if (u > 0 && !mbar_wait(&empty[st], (u - 1) & 1)) {
+            atomicExch(bad, 1);
+            stop = true;
+            break;
+          }
+          const int kc = min(TC_KC, a.Kp - TC_KC * c);
+          const uint32_t ab = tc_chunk_bytes(TC_ROWS, kc), pbytes = NH * kc * 2;
+          uint8_t* sa = base + (size_t)st * stage_bytes;
+          uint8_t* sb = sa + a_stage;
+          mbar_expect_tx(&full[st], ab + ((o[0] >= 0) + (o[1] >= 0)) * TC_PIECES * pbytes);
+          bulk_g2s(sa, a.aimg + aoff + (size_t)a_stage * c, ab, &full[st]);
+          // B: piece h of target t's table chunk -> rows 64 t .. 64 t + 63 of merged piece h
+          for (int t = 0; t < 2; ++t) {
+            if (o[t] < 0) continue;
+            const char* bsrc = a.bimg + (size_t)o[t] * a.b_img + (size_t)tc_chunk_bytes(NH, TC_KC) * c;
+            for (int h = 0; h < TC_PIECES; ++h)
+              bulk_g2s(sb + (size_t)h * 2 * pbytes + (size_t)t * pbytes, bsrc + (size_t)h * pbytes, pbytes,
+                       &full[st]);
+          }
+          issued = it + 1;
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_ROWS >> 4) << 24);
+      const uint32_t id128 = id0 | ((uint32_t)((2 * NH) >> 3) << 17), id64 = id0 | ((uint32_t)(NH >> 3) << 17);
+      int it = 0;
+      bool stop = false;
+      for (int v = vs, j = 0; v < ve && !stop; ++v, ++j) {
+        const bool p1 = a.goff1[v] >= 0, p2 = a.goff2[v] >= 0;
+        const int q = j & 1;
+        if (j >= 2 && !mbar_wait(&tfree[q], ((j >> 1) - 1) & 1)) {
+          atomicExch(bad, 1);
+          break;
+        }
+        const uint32_t idesc = (p1 && p2) ? id128 : id64;
+        // an entry with t2 alone writes the upper half of D
+        const uint32_t dcol = (!p1 && p2) ? (uint32_t)NH : 0u;
+        for (int c = 0; c < nch; ++c, ++it) {
+          const int st = it % TC_STAGES, u = it / TC_STAGES;
+          if (!mbar_wait(&full[st], u & 1)) {
+            atomicExch(bad, 1);
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const int kc = min(TC_KC, a.Kp - TC_KC * c);
+          const uint32_t sa = sm_u32(base + (size_t)st * stage_bytes);
+          const uint32_t sb = sa + a_stage + ((!p1 && p2) ? (uint32_t)(NH * kc * 2) : 0u);
+          const uint32_t pa = TC_ROWS * kc * 2, pb = 2 * NH * kc * 2;   // piece strides
+          const uint32_t sbo = 16 * kc;
+          const uint32_t dbig = tbase + 256u * q + dcol, dsmall = dbig + 128u;
+          const uint64_t dA = sdesc(sa, 128, sbo), dB = sdesc(sb, 128, sbo);
+          const uint64_t pa16 = pa >> 4, pb16 = pb >> 4;
+#pragma unroll
+          for (int ks = 0; ks < TC_KC / 16; ++ks) {
+            if (ks * 16 >= kc) break;
+            const uint64_t k16 = 16u * ks;
+            const uint64_t a0 = dA + k16, a1 = a0 + pa16, a2 = a1 + pa16;
+            const uint64_t b0 = dB + k16, b1 = b0 + pb16, b2 = b1 + pb16;
+            const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
+            mma_bf16(dbig, a0, b0, idesc, accum);
+            mma_bf16(dsmall, a1, b1, idesc, accum);
+            mma_bf16(dsmall, a0, b2, idesc, 1u);
+            mma_bf16(dsmall, a2, b0, idesc, 1u);
+            mma_bf16(dsmall, a0, b1, idesc, 1u);
+            mma_bf16(dsmall, a1, b0, idesc, 1u);
+          }
+          tc_commit(&empty[st]);
+          if (c == nch - 1) tc_commit(&tfull[q]);
+        }
+      }
+      tc_commit(mdone);
+      if (!mbar_wait(mdone, 0)) atomicExch(bad, 1);
+    }
+    __syncwarp();
+  } else {
+    const int quarter = warp & 3;
+    const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+    float acc[2 * NH];
+#pragma unroll
+    for (int n = 0; n < 2 * NH; ++n) acc[n] = 0.f;
+    for (int j = 0; j < nv; ++j) {
+      const int q = j & 1;
+      const bool p1 = a.goff1[vs + j] >= 0, p2 = a.goff2[vs + j] >= 0;
+      bool ok = mbar_wait(&tfull[q], (j >> 1) & 1);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        atomicExch(bad, 1);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t tq = tbase + lane_base + 256u * q;
+      if (p1) drain_half<0>(acc, tq);
+      if (p2) drain_half<NH>(acc, tq + (uint32_t)NH);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tfree[q]);
+    }
+    const int col = ct * TC_ROWS + 32 * quarter + lane;
+    if (col < a.nc) {
+      const int t1 = a.gt1[g], t2 = a.gt2[g];
+      float* o1 = a.out + (size_t)t1 * a.ncoef * a.nc + col;
+#pragma unroll
+      for (int n = 0; n < NH; ++n)
+        if (n < a.ncoef) o1[(size_t)n * a.nc] = acc[n];
+      if (t2 >= 0) {
+        float* o2 = a.out + (size_t)t2 * a.ncoef * a.nc + col;
+#pragma unroll
+        for (int n = 0; n < NH; ++n)
+          if (n < a.ncoef) o2[(size_t)n * a.nc] = acc[NH + n];
+      }
+    }
+  }
+  __syncthreads();
+  if (*bad) {
+    if (threadIdx.x == 0) atomicExch(a.err, 1);
     if (warp == 0 && lane == 0)
       for (int it = issued > TC_STAGES ? issued - TC_STAGES : 0; it < issued; ++it)
         mbar_wait(&full[it % TC_STAGES], (it / TC_STAGES) & 1);
@@ -1094,6 +1329,37 @@ static void tcm_prepare(xrl_ctx* c) {
   XRL_CUDA(cudaGetLastError());
 }
 
+// Sibling pairs for k_xlate_tc2: at every level >= 2, consecutive boxes with
+// the same parent are taken two at a time (a lone last sibling is a group of
+// one); each group's V-lists (sorted by source box) are merged by source.
+static void m2l_groups(xrl_ctx* c) {
+  const Tree& t = c->tree;
+  std::vector<int32_t> gptr{0}, gsrc, gt1, gt2;
+  std::vector<int16_t> go1, go2;
+  for (int b = t.level_off[2]; b < t.n_boxes();) {
+    int b2 = (b + 1 < t.n_boxes() && t.parent[b + 1] == t.parent[b]) ? b + 1 : -1;
+    gt1.push_back(b);
+    gt2.push_back(b2);
+    int64_t i = t.v_ptr[b], ie = t.v_ptr[b + 1];
+    int64_t j = b2 >= 0 ? t.v_ptr[b2] : 0, je = b2 >= 0 ? t.v_ptr[b2 + 1] : 0;
+    while (i < ie || j < je) {
+      const int si = i < ie ? t.v_src[i] : INT32_MAX, sj = j < je ? t.v_src[j] : INT32_MAX;
+      const int sm = std::min(si, sj);
+      gsrc.push_back(sm);
+      go1.push_back(si == sm ? t.v_off[i++] : (int16_t)-1);
+      go2.push_back(sj == sm ? t.v_off[j++] : (int16_t)-1);
+    }
+    gptr.push_back((int32_t)gsrc.size());
+    b = b2 >= 0 ? b2 + 1 : b + 1;
+  }
+  c->d.m2l_gptr.upload(c->alloc, gptr);
+  c->d.m2l_gsrc.upload(c->alloc, gsrc);
+  c->d.m2l_gt1.upload(c->alloc, gt1);
+  c->d.m2l_gt2.upload(c->alloc, gt2);
+  c->d.m2l_goff1.upload(c->alloc, go1);
+  c->d.m2l_goff2.upload(c->alloc, go2);
+}
+
 void tc_prepare(xrl_ctx* c) {
   const int ncoef = c->ncoef;
   if (c->opt.tensor_cores == 0) return;
@@ -1107,6 +1373,7 @@ void tc_prepare(xrl_ctx* c) {
   c->d.tc_bimg.alloc(c->alloc, (size_t)noff * TC_PIECES * Np * Kp);
   k_tc_pack_b<<<noff, 256, 0, c->stream>>>(ncoef, Kp, Np, c->d.t_m2l.p, c->d.tc_bimg.p);
   XRL_CUDA(cudaGetLastError());
+  if (Np == 64) m2l_groups(c);
   if (c->d.tcp_vimg.n > 0) tcm_prepare(c);
 }
 
@@ -1174,6 +1441,34 @@ void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cud
   const int nsrc = t.n_boxes() - src0;
   c->d.tc_aimg.ensure(c->alloc, (size_t)nsrc * nct * TC_PIECES * TC_ROWS * Kp);
   k_tc_pack_a<<<dim3(nsrc, nct), 256, 0, s>>>(nc, ncoef, Kp, src0, Mx, c->d.tc_aimg.p);
+  if (Np == 64 && c->d.m2l_gptr.n > 1 && b0 == src0 && nbx == nsrc) {
+    Tc2Args g;
+    g.nc = nc;
+    g.nct = nct;
+    g.Kp = Kp;
+    g.ncoef = ncoef;
+    g.src0 = src0;
+    g.a_img = (size_t)TC_PIECES * 2 * TC_ROWS * Kp;
+    g.b_img = (size_t)TC_PIECES * 2 * Np * Kp;
+    g.gptr = c->d.m2l_gptr.p;
+    g.gsrc = c->d.m2l_gsrc.p;
+    g.goff1 = c->d.m2l_goff1.p;
+    g.goff2 = c->d.m2l_goff2.p;
+    g.gt1 = c->d.m2l_gt1.p;
+    g.gt2 = c->d.m2l_gt2.p;
+    g.aimg = reinterpret_cast<const char*>(c->d.tc_aimg.p);
+    g.bimg = reinterpret_cast<const char*>(c->d.tc_bimg.p);
+    g.out = Lx;
+    g.err = c->d.tc_err.p;
+    const size_t smem = (size_t)TC_STAGES * (tc_chunk_bytes(TC_ROWS, TC_KC) + tc_chunk_bytes(128, TC_KC)) + 1024 + 128;
+    static bool set = false;
+    if (!set) {
+      XRL_CUDA(cudaFuncSetAttribute(k_xlate_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      set = true;
+    }
+    k_xlate_tc2<<<dim3(nct, (unsigned)(c->d.m2l_gptr.n - 1)), 192, smem, s>>>(g);
+    return;
+  }
   TcArgs a;
   a.pr = m2l_pairs(c, b0, nct, TC_PIECES, (size_t)TC_PIECES * 2 * TC_ROWS * Kp, (size_t)TC_PIECES * 2 * Np * Kp);
   a.nc = nc;

@@ -206,6 +206,9 @@ struct Dev {
   DBuf<int16_t> box_oct16;  // octant as a translation index
   DBuf<uint16_t> tc_bimg;   // packed 3-piece BF16 images of the M2L tables (tensor-core path)
   DBuf<uint16_t> tc_aimg;   // packed 3-piece BF16 images of the FP32 multipoles, per product
+  // M2L by sibling pairs (k_xlate_tc2): per group its targets and merged V-list
+  DBuf<int32_t> m2l_gptr, m2l_gsrc, m2l_gt1, m2l_gt2;
+  DBuf<int16_t> m2l_goff1, m2l_goff2;
   DBuf<int32_t> tc_err;     // set by a tensor-core kernel that timed out
   DBuf<uint16_t> oz_bimg;   // integer-slice BF16 images of the M2L tables (FP64-accurate path)
   DBuf<uint16_t> oz_aimg;   // integer-slice BF16 images of the FP64 multipoles, per product

@@ -174,22 +174,27 @@ def test_fp32_product_matches_dense_oracle(bar_ctx, bar_ctx_scalar, bar_dense_P,
         assert err < FP32_TOL, (ctx.opts.tensor_cores, err)
 
 
-def test_fp32_tensor_core_m2l_full_size_coils(coils_ctx, coils_mesh, lib):
+@pytest.mark.parametrize("p", [8, 7])
+def test_fp32_tensor_core_m2l_full_size_coils(coils_ctx, coils_mesh, lib, p):
     """Coils (24,792 panels) at 384 columns, the launch configuration of the
     solver's 64-system block: the tensor-core FP32 product against the FP64
     product (itself checked on sampled oracle rows above), column by column.
     With random-sign x the FP32 error of a row sum is ~u sqrt(n) |y|-relative
     (n ~ 5e3 near-field terms: ~4e-6), so the bound here is 2e-5 and the
-    tensor-core path must be no worse than 1.5x the CUDA-core FP32 path."""
+    tensor-core path must be no worse than 1.5x the CUDA-core FP32 path.
+    At order 7 (64 coefficients) the M2L runs two sibling targets per CTA."""
     rng = np.random.default_rng(7)
     x = rng.standard_normal((384, coils_mesh.n_tri)).astype(np.float32).astype(np.float64)
-    y64 = coils_ctx.fmm_mvm(x)
-    y32 = _fp32_product(coils_ctx, x)
-    sc = lib.XRL.from_mesh(coils_mesh, fmm_order=8, tensor_cores=0)
+    ctx = coils_ctx if p == 8 else lib.XRL.from_mesh(coils_mesh, fmm_order=p)
+    sc = lib.XRL.from_mesh(coils_mesh, fmm_order=p, tensor_cores=0)
     try:
+        y64 = ctx.fmm_mvm(x)
+        y32 = _fp32_product(ctx, x)
         ys = _fp32_product(sc, x)
     finally:
         sc.close()
+        if ctx is not coils_ctx:
+            ctx.close()
     nrm = np.linalg.norm(y64, axis=1)
     e_tc = (np.linalg.norm(y32 - y64, axis=1) / nrm).max()
     e_sc = (np.linalg.norm(ys - y64, axis=1) / nrm).max()
