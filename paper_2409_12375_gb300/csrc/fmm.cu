@@ -609,13 +609,13 @@ __global__ void __launch_bounds__(128) k_p2m_tiled(int nc, int ncoef, int box0, 
   }
 }
 
-// L2P, FP32, shared-memory tiled: Y[i][c] += (1/h) sum_k w_k S[i][k] L[leaf][k][c],
-// w = 1 for the m = 0 coefficients (k a perfect square n^2) and 2 otherwise.
+// L2P, FP32, shared-memory tiled: Y[i][c] += sum_k W[i][k] L[leaf][k][c] with the
+// weighted moments W = (1/h) w_k S[i][k] (k_l2p_weights).
 // One CTA per (leaf, 64-column tile, 64-panel block), 128 threads as 16 panel
 // groups (i = ty + 16 q, q < 4) x 8 column groups; coefficients in chunks of 32.
-__global__ void __launch_bounds__(128) k_l2p_tiled(int nc, int ncoef, int box0, float inv_h,
+__global__ void __launch_bounds__(128) k_l2p_tiled(int nc, int ncoef, int box0,
                                                    const int32_t* __restrict__ leaf_first,
-                                                   const int32_t* __restrict__ leaf_count, const float* __restrict__ S,
+                                                   const int32_t* __restrict__ leaf_count, const float* __restrict__ W,
                                                    const float* __restrict__ L, float* __restrict__ Y) {
   constexpr int CT = 64, KC = 32, RB = 64;
   __shared__ __align__(16) float As[KC][RB];
@@ -636,15 +636,7 @@ __global__ void __launch_bounds__(128) k_l2p_tiled(int nc, int ncoef, int box0, 
     __syncthreads();
     for (int e = threadIdx.x; e < KC * RB; e += 128) {
       const int i = e / KC, k = e % KC;
-      float v = 0.f;
-      if (i < nr && k < kn) {
-        const int kk = k0 + k;
-        int sq = (int)sqrtf((float)kk);
-        while ((sq + 1) * (sq + 1) <= kk) ++sq;
-        while (sq * sq > kk) --sq;
-        v = S[(size_t)(f0 + rb0 + i) * ncoef + kk] * (kk == sq * sq ? inv_h : 2.f * inv_h);
-      }
-      As[k][i] = v;
+      As[k][i] = (i < nr && k < kn) ? W[(size_t)(f0 + rb0 + i) * ncoef + k0 + k] : 0.f;
     }
     for (int e = threadIdx.x; e < KC * CT; e += 128) {
       const int k = e / CT, cc = e % CT;
@@ -735,6 +727,17 @@ __global__ void k_cast(size_t n, const double* __restrict__ a, T* __restrict__ b
   if (i < n) b[i] = (T)a[i];
 }
 
+// L2P weights folded into an FP32 copy of the moments: w[i][k] = S[i][k] (1 or 2) / h,
+// 1 for the m = 0 coefficients (k = n^2), 2 otherwise (the m < 0 half of the expansion)
+__global__ void k_l2p_weights(size_t n, int ncoef, double inv_h, const double* __restrict__ S, float* __restrict__ w) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k = (int)(i % ncoef);
+  int r = 0;
+  while ((r + 1) * (r + 1) <= k) ++r;
+  w[i] = (float)(S[i] * (r * r == k ? inv_h : 2.0 * inv_h));
+}
+
 // ---- host side ---------------------------------------------------------------------------
 void fmm_prepare(xrl_ctx* c) {
   const Tree& t = c->tree;
@@ -787,6 +790,10 @@ void fmm_prepare(xrl_ctx* c) {
   cast(c->d.t_m2l, c->d.t_m2l32);
   cast(c->d.near_val, c->d.near_val32);
   cast(c->d.mom, c->d.mom32);
+  c->d.mom32w.alloc(c->alloc, c->d.mom.n);
+  if (c->d.mom.n)
+    k_l2p_weights<<<(unsigned)((c->d.mom.n + 255) / 256), 256, 0, c->stream>>>(
+        c->d.mom.n, c->ncoef, (double)(1 << t.L) / t.side, c->d.mom.p, c->d.mom32w.p);
   XRL_CUDA(cudaGetLastError());
   XRL_CUDA(cudaStreamSynchronize(c->stream));
 }
@@ -912,8 +919,7 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   ev = prof_begin(c, s);
   if (sizeof(T) == 4 && nc >= 32)
     k_l2p_tiled<<<dim3(nl, (nc + 63) / 64, (c->max_leaf + 63) / 64), 128, 0, s>>>(
-        nc, ncoef, leaf0, (float)(1.0 / h), c->d.leaf_first.p, c->d.leaf_count.p, (const float*)mom,
-        (const float*)Lx, (float*)Y);
+        nc, ncoef, leaf0, c->d.leaf_first.p, c->d.leaf_count.p, c->d.mom32w.p, (const float*)Lx, (float*)Y);
   else
     k_l2p<T><<<dim3(nl, ecols), 128, 0, s>>>(nc, ct_e, ncoef, leaf0, (T)(1.0 / h), c->d.leaf_first.p,
                                              c->d.leaf_count.p, mom, Lx, Y);

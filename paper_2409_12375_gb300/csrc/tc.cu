@@ -480,33 +480,75 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc(TcArgs a) {
   }
 }
 
-// ---- M2L for two sibling targets per CTA (coefficients padded to 64) --------------------
-// Sibling boxes share most of their V-list, so one CTA takes a pair of them
-// (t1, t2) and walks the merged list of their sources: per source, the A
-// image (the source's multipoles, 128 columns) is fetched once and multiplied
-// by [B(off1) | B(off2)] with N = 128 (both targets: t1 in D columns 0..63,
-// t2 in 64..127), or by the one table present with N = 64.  Per MMA that is
-// twice the output columns for the same A operand, and one shared-memory A
-// read serves both targets.  Same pieces, products, TMEM buffers (big at
-// 256 q, small at 256 q + 128), per-entry promotion and bounded waits as
-// k_xlate_tc; a target absent from an entry has its half of D skipped by the
-// MMAs and by the drain.
+// ---- two sibling targets per CTA (M2L at 64 coefficients; the near field) --------------
+// Sibling targets share most of their interaction lists, so one CTA takes a
+// pair of them (t1, t2) and walks the merged list of their sources: per
+// source, the A image (the source's multipoles, or its transposed X rows, for
+// 128 columns) is fetched once and multiplied by [B1 | B2] with N = N1 + N2
+// (t1 in D columns [0, N1), t2 in [64, 64 + N2)), or by the
+// one B present.  Per MMA that is up to twice the output columns for the same
+// A operand, and one shared-memory A read serves both targets.  t2 always
+// starts at row / column 64 (so N1, N2 <= 64 when a group has two targets;
+// t1's rows [N1, 64) of B are not loaded and its D columns there are never
+// read).  Same pieces, products, TMEM buffers (big at 256 q, small at
+// 256 q + 128), per-entry promotion and bounded waits as k_xlate_tc; a target
+// absent from an entry has its columns of D skipped by the MMAs and the drain.
+//  * mode 0 (M2L): targets and sources are boxes, N1 = N2 = 64, entry
+//    operands: A of source box gsrc (K = Kp), B = table image gv_t.
+//  * mode 1 (P2P): targets and sources are leaves, N_t = the target's padded
+//    panel count, A = transposed-X rows of source leaf gsrc (K = its padded
+//    panel count), B = near-block image of U-list pair gv_t.
 struct Tc2Args {
-  int nc, nct, Kp, ncoef, src0;
-  size_t a_img, b_img;                 // bytes of one (box, tile) A image / one table image
+  int mode, nc, nct, Kp, ncoef, src0, sum_pc;
+  size_t a_img, b_img;                 // mode 0: bytes of one (box, tile) A image / one table image
+  int a_row_bytes;                     // mode 1: bytes per K element of the X image
   const int32_t* gptr;                 // merged list of group g: [gptr[g], gptr[g + 1])
-  const int32_t* gsrc;                 // source box (global id)
-  const int16_t* goff1;                // table of (t1 - src), -1: t1 absent
-  const int16_t* goff2;                // table of (t2 - src), -1: t2 absent
-  const int32_t* gt1;                  // target boxes of group g (gt2 = -1: single target)
+  const int32_t* gsrc;                 // source box (mode 0, global id) or leaf (mode 1)
+  const int32_t* gv1;                  // t1's table (mode 0) or U-list pair (mode 1), -1: absent
+  const int32_t* gv2;
+  const int32_t* gt1;                  // target box / leaf of group g (gt2 = -1: single target)
   const int32_t* gt2;
+  const int32_t* leaf_a0;              // mode 1: padded panel offset, padded count, first panel, count
+  const int32_t* leaf_pc;
+  const int32_t* leaf_f0;
+  const int32_t* leaf_n;
+  const int64_t* pair_boff;            // mode 1: byte offset of each pair's near-block image
   const char* aimg;
   const char* bimg;
   float* out;
   int32_t* err;
 };
 
-// acc[OFF + n] += both accumulators (small first) of one target half, n < 64
+// acc[n] += both accumulators (small first) for the columns n in [0, n1) and
+// [64, 64 + n2) (n1 = 0 / n2 = 0: that target absent; a group's lone target
+// may have n1 > 64)
+__device__ __forceinline__ void drain_range(float (&acc)[128], uint32_t taddr, int n1, int n2) {
+#pragma unroll
+  for (int s = 1; s >= 0; --s) {
+#pragma unroll
+    for (int h = 0; h < 128; h += 32) {
+      if (!(h < n1 || (n2 > 0 && h + 32 > 64 && h < 64 + n2))) continue;   // warp-uniform
+      uint32_t r[32];
+#pragma unroll
+      for (int n0 = 0; n0 < 32; n0 += 16)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+            "[%16];"
+            : "=r"(r[n0 + 0]), "=r"(r[n0 + 1]), "=r"(r[n0 + 2]), "=r"(r[n0 + 3]), "=r"(r[n0 + 4]),
+              "=r"(r[n0 + 5]), "=r"(r[n0 + 6]), "=r"(r[n0 + 7]), "=r"(r[n0 + 8]), "=r"(r[n0 + 9]),
+              "=r"(r[n0 + 10]), "=r"(r[n0 + 11]), "=r"(r[n0 + 12]), "=r"(r[n0 + 13]), "=r"(r[n0 + 14]),
+              "=r"(r[n0 + 15])
+            : "r"(taddr + 128u * s + (uint32_t)(h + n0))
+            : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int n = 0; n < 32; ++n)
+        if (h + n < n1 || (h + n >= 64 && h + n - 64 < n2)) acc[h + n] += __uint_as_float(r[n]);
+    }
+  }
+}
+
+// acc[OFF + n] += both accumulators (small first) of one 64-column half
 template <int OFF>
 __device__ __forceinline__ void drain_half(float (&acc)[128], uint32_t taddr) {
 #pragma unroll
@@ -532,12 +574,12 @@ __device__ __forceinline__ void drain_half(float (&acc)[128], uint32_t taddr) {
   }
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
-  constexpr int NH = 64;   // coefficients per target (padded)
   extern __shared__ uint8_t tc_smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
   const int a_stage = tc_chunk_bytes(TC_ROWS, TC_KC);
-  const int stage_bytes = a_stage + tc_chunk_bytes(2 * NH, TC_KC);
+  const int stage_bytes = a_stage + tc_chunk_bytes(128, TC_KC);
   uint64_t* full = reinterpret_cast<uint64_t*>(base + TC_STAGES * stage_bytes);
   uint64_t* empty = full + TC_STAGES;
   uint64_t* tfull = empty + TC_STAGES;
@@ -549,7 +591,10 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
   const int ct = blockIdx.x, g = blockIdx.y;
   const int vs = a.gptr[g], ve = a.gptr[g + 1];
   const int nv = ve - vs;
-  const int nch = (a.Kp + TC_KC - 1) / TC_KC;
+  const int t1 = a.gt1[g], t2 = a.gt2[g];
+  const int N1 = MODE == 0 ? 64 : a.leaf_pc[t1];
+  const int N2 = t2 < 0 ? 0 : (MODE == 0 ? 64 : a.leaf_pc[t2]);
+  const int PW = t2 < 0 ? N1 : 64 + N2;   // rows of a merged B piece
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -578,28 +623,38 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
       int it = 0;
       bool stop = false;
       for (int v = vs; v < ve && !stop; ++v) {
-        const size_t aoff = ((size_t)(a.gsrc[v] - a.src0) * a.nct + ct) * a.a_img;
-        const int o[2] = {a.goff1[v], a.goff2[v]};
-        for (int c = 0; c < nch; ++c, ++it) {
+        const int S = a.gsrc[v];
+        const size_t aoff = MODE == 0 ? ((size_t)(S - a.src0) * a.nct + ct) * a.a_img
+                                        : ((size_t)ct * a.sum_pc + a.leaf_a0[S]) * (size_t)a.a_row_bytes;
+        const int K = MODE == 0 ? a.Kp : a.leaf_pc[S];
+        const int vt[2] = {a.gv1[v], a.gv2[v]};
+        const int Nt[2] = {N1, N2};
+        const int nchv = (K + TC_KC - 1) / TC_KC;
+        for (int c = 0; c < nchv; ++c, ++it) {
           const int st = it % TC_STAGES, u = it / TC_STAGES;
           if (u > 0 && !mbar_wait(&empty[st], (u - 1) & 1)) {
             atomicExch(bad, 1);
             stop = true;
             break;
           }
-          const int kc = min(TC_KC, a.Kp - TC_KC * c);
-          const uint32_t ab = tc_chunk_bytes(TC_ROWS, kc), pbytes = NH * kc * 2;
+          const int kc = min(TC_KC, K - TC_KC * c);
+          const uint32_t ab = tc_chunk_bytes(TC_ROWS, kc);
           uint8_t* sa = base + (size_t)st * stage_bytes;
           uint8_t* sb = sa + a_stage;
-          mbar_expect_tx(&full[st], ab + ((o[0] >= 0) + (o[1] >= 0)) * TC_PIECES * pbytes);
+          uint32_t bb = 0;
+          for (int t = 0; t < 2; ++t)
+            if (vt[t] >= 0) bb += TC_PIECES * Nt[t] * kc * 2;
+          mbar_expect_tx(&full[st], ab + bb);
           bulk_g2s(sa, a.aimg + aoff + (size_t)a_stage * c, ab, &full[st]);
-          // B: piece h of target t's table chunk -> rows 64 t .. 64 t + 63 of merged piece h
+          // piece h of target t's B chunk -> rows [64 t, 64 t + N_t) of merged piece h
           for (int t = 0; t < 2; ++t) {
-            if (o[t] < 0) continue;
-            const char* bsrc = a.bimg + (size_t)o[t] * a.b_img + (size_t)tc_chunk_bytes(NH, TC_KC) * c;
+            if (vt[t] < 0) continue;
+            const uint32_t pbytes = Nt[t] * kc * 2;
+            const char* bsrc = a.bimg + (MODE == 0 ? (size_t)vt[t] * a.b_img : (size_t)a.pair_boff[vt[t]]) +
+                               (size_t)tc_chunk_bytes(Nt[t], TC_KC) * c;
+            uint8_t* bdst = sb + (size_t)t * 64 * kc * 2;
             for (int h = 0; h < TC_PIECES; ++h)
-              bulk_g2s(sb + (size_t)h * 2 * pbytes + (size_t)t * pbytes, bsrc + (size_t)h * pbytes, pbytes,
-                       &full[st]);
+              bulk_g2s(bdst + (size_t)h * PW * kc * 2, bsrc + (size_t)h * pbytes, pbytes, &full[st]);
           }
           issued = it + 1;
         }
@@ -609,20 +664,21 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t id0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_ROWS >> 4) << 24);
-      const uint32_t id128 = id0 | ((uint32_t)((2 * NH) >> 3) << 17), id64 = id0 | ((uint32_t)(NH >> 3) << 17);
       int it = 0;
       bool stop = false;
       for (int v = vs, j = 0; v < ve && !stop; ++v, ++j) {
-        const bool p1 = a.goff1[v] >= 0, p2 = a.goff2[v] >= 0;
+        const bool p1 = a.gv1[v] >= 0, p2 = a.gv2[v] >= 0;
+        const int K = MODE == 0 ? a.Kp : a.leaf_pc[a.gsrc[v]];
+        const int nchv = (K + TC_KC - 1) / TC_KC;
         const int q = j & 1;
         if (j >= 2 && !mbar_wait(&tfree[q], ((j >> 1) - 1) & 1)) {
           atomicExch(bad, 1);
           break;
         }
-        const uint32_t idesc = (p1 && p2) ? id128 : id64;
-        // an entry with t2 alone writes the upper half of D
-        const uint32_t dcol = (!p1 && p2) ? (uint32_t)NH : 0u;
-        for (int c = 0; c < nch; ++c, ++it) {
+        const int Nm = p1 && p2 ? 64 + N2 : (p1 ? N1 : N2);
+        const uint32_t idesc = id0 | ((uint32_t)(Nm >> 3) << 17);
+        const uint32_t dcol = p1 ? 0u : 64u;   // t2 alone: rows and columns from 64
+        for (int c = 0; c < nchv; ++c, ++it) {
           const int st = it % TC_STAGES, u = it / TC_STAGES;
           if (!mbar_wait(&full[st], u & 1)) {
             atomicExch(bad, 1);
@@ -630,10 +686,10 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
             break;
           }
           tc_fence_after();
-          const int kc = min(TC_KC, a.Kp - TC_KC * c);
+          const int kc = min(TC_KC, K - TC_KC * c);
           const uint32_t sa = sm_u32(base + (size_t)st * stage_bytes);
-          const uint32_t sb = sa + a_stage + ((!p1 && p2) ? (uint32_t)(NH * kc * 2) : 0u);
-          const uint32_t pa = TC_ROWS * kc * 2, pb = 2 * NH * kc * 2;   // piece strides
+          const uint32_t sb = sa + a_stage + dcol * kc * 2;
+          const uint32_t pa = TC_ROWS * kc * 2, pb = PW * kc * 2;   // piece strides
           const uint32_t sbo = 16 * kc;
           const uint32_t dbig = tbase + 256u * q + dcol, dsmall = dbig + 128u;
           const uint64_t dA = sdesc(sa, 128, sbo), dB = sdesc(sb, 128, sbo);
@@ -653,7 +709,7 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
             mma_bf16(dsmall, a1, b0, idesc, 1u);
           }
           tc_commit(&empty[st]);
-          if (c == nch - 1) tc_commit(&tfull[q]);
+          if (c == nchv - 1) tc_commit(&tfull[q]);
         }
       }
       tc_commit(mdone);
@@ -663,12 +719,12 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
   } else {
     const int quarter = warp & 3;
     const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
-    float acc[2 * NH];
+    float acc[128];
 #pragma unroll
-    for (int n = 0; n < 2 * NH; ++n) acc[n] = 0.f;
+    for (int n = 0; n < 128; ++n) acc[n] = 0.f;
     for (int j = 0; j < nv; ++j) {
       const int q = j & 1;
-      const bool p1 = a.goff1[vs + j] >= 0, p2 = a.goff2[vs + j] >= 0;
+      const bool p1 = a.gv1[vs + j] >= 0, p2 = a.gv2[vs + j] >= 0;
       bool ok = mbar_wait(&tfull[q], (j >> 1) & 1);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
@@ -677,24 +733,31 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
       }
       tc_fence_after();
       const uint32_t tq = tbase + lane_base + 256u * q;
-      if (p1) drain_half<0>(acc, tq);
-      if (p2) drain_half<NH>(acc, tq + (uint32_t)NH);
+      if (MODE == 0) {   // both halves 64 wide: compile-time columns
+        if (p1) drain_half<0>(acc, tq);
+        if (p2) drain_half<64>(acc, tq + 64u);
+      } else {
+        drain_range(acc, tq, p1 ? N1 : 0, p2 ? N2 : 0);
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tfree[q]);
     }
     const int col = ct * TC_ROWS + 32 * quarter + lane;
     if (col < a.nc) {
-      const int t1 = a.gt1[g], t2 = a.gt2[g];
-      float* o1 = a.out + (size_t)t1 * a.ncoef * a.nc + col;
+      const int nr1 = MODE == 0 ? a.ncoef : a.leaf_n[t1];
+      const int nr2 = t2 < 0 ? 0 : (MODE == 0 ? a.ncoef : a.leaf_n[t2]);
+      const size_t r1 = MODE == 0 ? (size_t)t1 * a.ncoef : (size_t)a.leaf_f0[t1];
+      const size_t r2 = t2 < 0 ? 0 : (MODE == 0 ? (size_t)t2 * a.ncoef : (size_t)a.leaf_f0[t2]);
+      float* o1 = a.out + r1 * a.nc + col;
+      float* o2 = a.out + r2 * a.nc + col;
 #pragma unroll
-      for (int n = 0; n < NH; ++n)
-        if (n < a.ncoef) o1[(size_t)n * a.nc] = acc[n];
-      if (t2 >= 0) {
-        float* o2 = a.out + (size_t)t2 * a.ncoef * a.nc + col;
-#pragma unroll
-        for (int n = 0; n < NH; ++n)
-          if (n < a.ncoef) o2[(size_t)n * a.nc] = acc[NH + n];
+      for (int n = 0; n < 128; ++n) {
+        if (t2 < 0 || n < 64) {
+          if (n < nr1) o1[(size_t)n * a.nc] = acc[n];
+        } else if (n - 64 < nr2) {
+          o2[(size_t)(n - 64) * a.nc] = acc[n];
+        }
       }
     }
   }
@@ -711,6 +774,27 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512) : "memory");
   }
+}
+
+static size_t tc2_smem() {
+  return (size_t)TC_STAGES * (tc_chunk_bytes(TC_ROWS, TC_KC) + tc_chunk_bytes(128, TC_KC)) + 1024 + 128;
+}
+
+template <int MODE>
+static void launch_tc2_m(dim3 grid, const Tc2Args& g, cudaStream_t s) {
+  static bool set = false;
+  if (!set) {
+    XRL_CUDA(cudaFuncSetAttribute(k_xlate_tc2<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2_smem()));
+    set = true;
+  }
+  k_xlate_tc2<MODE><<<grid, 192, tc2_smem(), s>>>(g);
+}
+
+static void launch_tc2(dim3 grid, const Tc2Args& g, cudaStream_t s) {
+  if (g.mode == 0)
+    launch_tc2_m<0>(grid, g, s);
+  else
+    launch_tc2_m<1>(grid, g, s);
 }
 
 // ---- FP64-accurate translation (Ozaki-style integer slices) ------------------------------
@@ -1257,6 +1341,8 @@ static void launch_oz(int Np, dim3 g, const OzArgs& a, cudaStream_t s) {
     launch_oz_np<96>(g, a, s);
 }
 
+static void p2p_groups(xrl_ctx* c, const std::vector<int32_t>& pc);
+
 // Near-field layout for the tensor cores: leaves padded to 16 panels, the
 // pair offsets of the near-block images, and the FP32 images themselves.
 static void tcp_prepare(xrl_ctx* c) {
@@ -1301,6 +1387,7 @@ static void tcp_prepare(xrl_ctx* c) {
   c->d.tcp_boff.upload(c->alloc, boff);
   c->d.ozp_boff.upload(c->alloc, zoff);
   c->d.tcp_vimg.alloc(c->alloc, (size_t)(b / 2));
+  p2p_groups(c, pc);
   k_tcp_pack_v<<<(unsigned)np, 256, 0, c->stream>>>(c->d.tcp_tgt.p, c->d.u_src.p, c->d.tcp_col.p, c->d.leaf_count.p,
                                                     c->d.tcp_pc.p, c->d.near_off.p, c->d.near_w.p, c->d.tcp_boff.p,
                                                     c->d.near_val.p, c->d.tcp_vimg.p);
@@ -1329,35 +1416,58 @@ static void tcm_prepare(xrl_ctx* c) {
   XRL_CUDA(cudaGetLastError());
 }
 
-// Sibling pairs for k_xlate_tc2: at every level >= 2, consecutive boxes with
-// the same parent are taken two at a time (a lone last sibling is a group of
-// one); each group's V-lists (sorted by source box) are merged by source.
-static void m2l_groups(xrl_ctx* c) {
-  const Tree& t = c->tree;
-  std::vector<int32_t> gptr{0}, gsrc, gt1, gt2;
-  std::vector<int16_t> go1, go2;
-  for (int b = t.level_off[2]; b < t.n_boxes();) {
-    int b2 = (b + 1 < t.n_boxes() && t.parent[b + 1] == t.parent[b]) ? b + 1 : -1;
+// Sibling pairs for k_xlate_tc2: consecutive targets with the same parent
+// are taken two at a time when `pairable` allows (else alone); each group's
+// lists (sorted by source) are merged by source.  lptr/lsrc: the targets'
+// interaction lists; an entry's value is `val(i)` for list position i.
+template <class Parent, class Pairable, class Val>
+static void build_groups(int n_t, int t0, const std::vector<int64_t>& lptr, const std::vector<int32_t>& lsrc,
+                         Parent parent, Pairable pairable, Val val, xrl_ctx* c, DBuf<int32_t>& dptr,
+                         DBuf<int32_t>& dsrc, DBuf<int32_t>& dt1, DBuf<int32_t>& dt2, DBuf<int32_t>& dv1,
+                         DBuf<int32_t>& dv2) {
+  std::vector<int32_t> gptr{0}, gsrc, gt1, gt2, gv1, gv2;
+  for (int b = t0; b < t0 + n_t;) {
+    const int b2 = (b + 1 < t0 + n_t && parent(b + 1) == parent(b) && pairable(b, b + 1)) ? b + 1 : -1;
     gt1.push_back(b);
     gt2.push_back(b2);
-    int64_t i = t.v_ptr[b], ie = t.v_ptr[b + 1];
-    int64_t j = b2 >= 0 ? t.v_ptr[b2] : 0, je = b2 >= 0 ? t.v_ptr[b2 + 1] : 0;
+    int64_t i = lptr[b], ie = lptr[b + 1];
+    int64_t j = b2 >= 0 ? lptr[b2] : 0, je = b2 >= 0 ? lptr[b2 + 1] : 0;
     while (i < ie || j < je) {
-      const int si = i < ie ? t.v_src[i] : INT32_MAX, sj = j < je ? t.v_src[j] : INT32_MAX;
+      const int si = i < ie ? lsrc[i] : INT32_MAX, sj = j < je ? lsrc[j] : INT32_MAX;
       const int sm = std::min(si, sj);
       gsrc.push_back(sm);
-      go1.push_back(si == sm ? t.v_off[i++] : (int16_t)-1);
-      go2.push_back(sj == sm ? t.v_off[j++] : (int16_t)-1);
+      gv1.push_back(si == sm ? val(i++) : -1);
+      gv2.push_back(sj == sm ? val(j++) : -1);
     }
     gptr.push_back((int32_t)gsrc.size());
     b = b2 >= 0 ? b2 + 1 : b + 1;
   }
-  c->d.m2l_gptr.upload(c->alloc, gptr);
-  c->d.m2l_gsrc.upload(c->alloc, gsrc);
-  c->d.m2l_gt1.upload(c->alloc, gt1);
-  c->d.m2l_gt2.upload(c->alloc, gt2);
-  c->d.m2l_goff1.upload(c->alloc, go1);
-  c->d.m2l_goff2.upload(c->alloc, go2);
+  dptr.upload(c->alloc, gptr);
+  dsrc.upload(c->alloc, gsrc);
+  dt1.upload(c->alloc, gt1);
+  dt2.upload(c->alloc, gt2);
+  dv1.upload(c->alloc, gv1);
+  dv2.upload(c->alloc, gv2);
+}
+
+// M2L groups over all boxes of levels >= 2 (entry value: the table index)
+static void m2l_groups(xrl_ctx* c) {
+  const Tree& t = c->tree;
+  const int b0 = t.level_off[2];
+  build_groups(t.n_boxes() - b0, b0, t.v_ptr, t.v_src, [&](int b) { return t.parent[b]; },
+               [](int, int) { return true; }, [&](int64_t i) { return (int32_t)t.v_off[i]; }, c, c->d.m2l_gptr,
+               c->d.m2l_gsrc, c->d.m2l_gt1, c->d.m2l_gt2, c->d.m2l_gv1, c->d.m2l_gv2);
+}
+
+// near-field groups over the leaves (entry value: the U-list pair index);
+// two leaves share a CTA when both have at most 64 padded panels
+static void p2p_groups(xrl_ctx* c, const std::vector<int32_t>& pc) {
+  const Tree& t = c->tree;
+  const int leaf0 = t.level_off[t.L];
+  build_groups(t.n_leaves(), 0, t.u_ptr, t.u_src, [&](int T) { return t.parent[leaf0 + T]; },
+               [&](int T1, int T2) { return pc[T1] <= 64 && pc[T2] <= 64; },
+               [](int64_t q) { return (int32_t)q; }, c, c->d.p2p_gptr, c->d.p2p_gsrc, c->d.p2p_gt1,
+               c->d.p2p_gt2, c->d.p2p_gv1, c->d.p2p_gv2);
 }
 
 void tc_prepare(xrl_ctx* c) {
@@ -1442,7 +1552,8 @@ void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cud
   c->d.tc_aimg.ensure(c->alloc, (size_t)nsrc * nct * TC_PIECES * TC_ROWS * Kp);
   k_tc_pack_a<<<dim3(nsrc, nct), 256, 0, s>>>(nc, ncoef, Kp, src0, Mx, c->d.tc_aimg.p);
   if (Np == 64 && c->d.m2l_gptr.n > 1 && b0 == src0 && nbx == nsrc) {
-    Tc2Args g;
+    Tc2Args g = {};
+    g.mode = 0;
     g.nc = nc;
     g.nct = nct;
     g.Kp = Kp;
@@ -1452,21 +1563,15 @@ void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cud
     g.b_img = (size_t)TC_PIECES * 2 * Np * Kp;
     g.gptr = c->d.m2l_gptr.p;
     g.gsrc = c->d.m2l_gsrc.p;
-    g.goff1 = c->d.m2l_goff1.p;
-    g.goff2 = c->d.m2l_goff2.p;
+    g.gv1 = c->d.m2l_gv1.p;
+    g.gv2 = c->d.m2l_gv2.p;
     g.gt1 = c->d.m2l_gt1.p;
     g.gt2 = c->d.m2l_gt2.p;
     g.aimg = reinterpret_cast<const char*>(c->d.tc_aimg.p);
     g.bimg = reinterpret_cast<const char*>(c->d.tc_bimg.p);
     g.out = Lx;
     g.err = c->d.tc_err.p;
-    const size_t smem = (size_t)TC_STAGES * (tc_chunk_bytes(TC_ROWS, TC_KC) + tc_chunk_bytes(128, TC_KC)) + 1024 + 128;
-    static bool set = false;
-    if (!set) {
-      XRL_CUDA(cudaFuncSetAttribute(k_xlate_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      set = true;
-    }
-    k_xlate_tc2<<<dim3(nct, (unsigned)(c->d.m2l_gptr.n - 1)), 192, smem, s>>>(g);
+    launch_tc2(dim3(nct, (unsigned)(c->d.m2l_gptr.n - 1)), g, s);
     return;
   }
   TcArgs a;
@@ -1528,6 +1633,31 @@ void tc_p2p(xrl_ctx* c, int nc, const float* X, float* Y, cudaStream_t s) {
   c->d.tcp_ximg.ensure(c->alloc, (size_t)nct * c->tcp_sum_pc * TC_PIECES * TC_ROWS);
   k_tcp_pack_x<<<dim3(nl, nct), 256, 0, s>>>(nc, c->tcp_sum_pc, c->d.leaf_first.p, c->d.leaf_count.p, c->d.tcp_a0.p,
                                              c->d.tcp_pc.p, X, c->d.tcp_ximg.p);
+  if (c->d.p2p_gptr.n > 1) {
+    Tc2Args g = {};
+    g.mode = 1;
+    g.nc = nc;
+    g.nct = nct;
+    g.sum_pc = c->tcp_sum_pc;
+    g.a_row_bytes = TC_PIECES * TC_ROWS * 2;
+    g.gptr = c->d.p2p_gptr.p;
+    g.gsrc = c->d.p2p_gsrc.p;
+    g.gv1 = c->d.p2p_gv1.p;
+    g.gv2 = c->d.p2p_gv2.p;
+    g.gt1 = c->d.p2p_gt1.p;
+    g.gt2 = c->d.p2p_gt2.p;
+    g.leaf_a0 = c->d.tcp_a0.p;
+    g.leaf_pc = c->d.tcp_pc.p;
+    g.leaf_f0 = c->d.leaf_first.p;
+    g.leaf_n = c->d.leaf_count.p;
+    g.pair_boff = c->d.tcp_boff.p;
+    g.aimg = reinterpret_cast<const char*>(c->d.tcp_ximg.p);
+    g.bimg = reinterpret_cast<const char*>(c->d.tcp_vimg.p);
+    g.out = Y;
+    g.err = c->d.tc_err.p;
+    launch_tc2(dim3(nct, (unsigned)(c->d.p2p_gptr.n - 1)), g, s);
+    return;
+  }
   TcArgs a;
   a.pr = p2p_pairs(c, nct, TC_PIECES, c->d.tcp_boff.p);
   a.nc = nc;

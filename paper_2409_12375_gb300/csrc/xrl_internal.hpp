@@ -199,6 +199,7 @@ struct Dev {
   DBuf<int32_t> near_src;                             // per leaf: Morton index of each near column
   DBuf<double> mom;                                  // [N][ncoef] P2M moments (leaf-scaled)
   DBuf<float> mom32;
+  DBuf<float> mom32w;      // FP32 moments with the L2P weights folded in (k_l2p_weights)
   DBuf<double> t_m2m, t_l2l, t_m2l;                  // translation matrices (transposed)
   DBuf<float> t_m2m32, t_l2l32, t_m2l32;
   DBuf<int32_t> box_parent, box_oct, box_child_ptr, box_child;  // tree arrays (global ids)
@@ -206,9 +207,10 @@ struct Dev {
   DBuf<int16_t> box_oct16;  // octant as a translation index
   DBuf<uint16_t> tc_bimg;   // packed 3-piece BF16 images of the M2L tables (tensor-core path)
   DBuf<uint16_t> tc_aimg;   // packed 3-piece BF16 images of the FP32 multipoles, per product
-  // M2L by sibling pairs (k_xlate_tc2): per group its targets and merged V-list
-  DBuf<int32_t> m2l_gptr, m2l_gsrc, m2l_gt1, m2l_gt2;
-  DBuf<int16_t> m2l_goff1, m2l_goff2;
+  // M2L and near field by sibling pairs (k_xlate_tc2): per group its two
+  // targets and the merged list (source, entry of t1 or -1, entry of t2 or -1)
+  DBuf<int32_t> m2l_gptr, m2l_gsrc, m2l_gt1, m2l_gt2, m2l_gv1, m2l_gv2;
+  DBuf<int32_t> p2p_gptr, p2p_gsrc, p2p_gt1, p2p_gt2, p2p_gv1, p2p_gv2;
   DBuf<int32_t> tc_err;     // set by a tensor-core kernel that timed out
   DBuf<uint16_t> oz_bimg;   // integer-slice BF16 images of the M2L tables (FP64-accurate path)
   DBuf<uint16_t> oz_aimg;   // integer-slice BF16 images of the FP64 multipoles, per product
