@@ -197,7 +197,10 @@ def peaks():
 # configuration (profiles/top_kernels_coil_sweep.md); None where none exists
 # ncu DRAM bytes (read + write) per launch of the dominant kernels at the bench's
 # configuration; None until a capture of the current kernels exists
-NCU_TRAFFIC = {"m2l": None, "m2l64": None}
+NCU_TRAFFIC = {"m2l": 84.400128e6 + 31.16032e6,        # k_xlate_tc2<0>, order 7, 384 columns
+               "p2p": 437.365248e6 + 33.278464e6,      # k_xlate_tc2<1>
+               "m2l64": 232.165888e6 + 85.900032e6,    # k_xlate_oz<64>
+               "p2p64": 750.134272e6 + 82.493184e6}    # k_xlate_oz<96> (near field)
 
 
 def phase_kernel(name, p):
@@ -205,16 +208,17 @@ def phase_kernel(name, p):
     np_ = ((p + 1) ** 2 + 15) // 16 * 16
     tc = "k_xlate_tc<%d>" % (64 if np_ <= 64 else 96)
     return {
-        "p2p": "k_tcp_pack_x + k_xlate_tc<96> (tcgen05 near field, 3-piece BF16)",
+        "p2p": "k_tcp_pack_x + k_xlate_tc2<1> (tcgen05 near field, two sibling leaves per CTA, 3-piece BF16)",
         "m2l": ("k_tc_pack_a + k_xlate_tc2 (tcgen05, two sibling targets per CTA, N = 128, 3-piece BF16, "
                 "6 products)" if np_ == 64 else "k_tc_pack_a + k_xlate_tc<96> (tcgen05, 3-piece BF16, 6 products)"),
-        "p2m": tc + " mode 2 (tcgen05 P2M from the near field's transposed-X image)",
-        "m2m": "k_tc_pack_a + " + tc + " mode 0 over the 8 M2M tables (tcgen05)",
+        "p2m": tc + " mode 2 (tcgen05 P2M from the near field's transposed-X image) + k_p2m_df64 (residuals)",
+        "m2m": "k_tc_pack_a + " + tc + " mode 0 over the 8 M2M tables (tcgen05) + k_m2l_df64<0> (residuals)",
         "p2p64": "k_ozp_pack_x + k_xlate_oz (tcgen05 near field, 5 integer slices)",
         "m2l64": "k_oz_pack_a + k_xlate_oz (tcgen05, 5 integer slices, 15 products)",
         "precond": "k_spike_y/z/x/out apply + k_band_factor_blk/k_spike_cols/k_spike_reduce factor",
         "operator": "k_gather + k_scatter + k_loop_reduce(_long)",
-        "l2p": "k_l2p_tiled", "l2l": "k_m2l_tiled<6,1> (list form)"}.get(name, name)
+        "l2p": "k_l2p_tiled + k_l2p_df64 (residuals)",
+        "l2l": "k_m2l_tiled<%d,1> list form + k_m2l_df64<1> (residuals)" % ((np_ + 15) // 16)}.get(name, name)
 
 
 def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0):

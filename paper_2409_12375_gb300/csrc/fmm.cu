@@ -721,6 +721,151 @@ __global__ void k_l2p(int nc, int ct, int ncoef, int box0, T inv_h, const int32_
   }
 }
 
+// P2M and L2P in FP64 accuracy on the FP32 pipes (the residual operator of the
+// mixed mode): the tilings of k_p2m_tiled / k_l2p_tiled with double-float
+// operands and the accumulation of k_p2p_df64 (exact products by FMA, sums as
+// unevaluated float pairs, ~2^-44 per operation).
+__device__ __forceinline__ float2 split_df(double x) {
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float2 a, float2 b) {
+  const float p = a.x * b.x;
+  const float pe = fmaf(a.x, b.x, -p);
+  const float cr = fmaf(a.x, b.y, a.y * b.x);
+  const float t = sh + p;
+  const float bp = t - sh;
+  const float e = (sh - (t - bp)) + (p - bp);
+  sl += e + pe + cr;
+  sh = t;
+}
+
+// M[leaf][k][c] = sum_i S[i][k] X[i][c]; S pre-split, X split on load
+template <int RI>
+__global__ void __launch_bounds__(128) k_p2m_df64(int nc, int ncoef, int box0, const int32_t* __restrict__ leaf_first,
+                                                  const int32_t* __restrict__ leaf_count, const float2* __restrict__ S,
+                                                  const double* __restrict__ X, double* __restrict__ M) {
+  constexpr int CT = 64, KC = 16, LD = 16 * RI;
+  __shared__ __align__(16) float2 Ss[KC][LD];
+  __shared__ __align__(16) float2 Xs[KC][CT];
+  const int B = blockIdx.x, c0 = blockIdx.y * CT;
+  const int f0 = leaf_first[B], n = leaf_count[B];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  float sh[RI][8], sl[RI][8];
+#pragma unroll
+  for (int i = 0; i < RI; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sh[i][j] = sl[i][j] = 0.f;
+  for (int j0 = 0; j0 < n; j0 += KC) {
+    const int kn = min(KC, n - j0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < KC * LD; e += 128) {
+      const int j = e / LD, k = e % LD;
+      Ss[j][k] = (j < kn && k < ncoef) ? S[(size_t)(f0 + j0 + j) * ncoef + k] : make_float2(0.f, 0.f);
+    }
+    for (int e = threadIdx.x; e < KC * CT; e += 128) {
+      const int j = e / CT, cc = e % CT;
+      Xs[j][cc] = (j < kn && c0 + cc < nc) ? split_df(X[(size_t)(f0 + j0 + j) * nc + c0 + cc]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int j = 0; j < KC; ++j) {
+      float2 x[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        x[q] = Xs[j][4 * tx + q];
+        x[4 + q] = Xs[j][32 + 4 * tx + q];
+      }
+#pragma unroll
+      for (int i = 0; i < RI; ++i) {
+        const float2 t = Ss[j][ty + 16 * i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) df_fma(sh[i][q], sl[i][q], t, x[q]);
+      }
+    }
+  }
+  double* out = M + (size_t)(box0 + B) * ncoef * nc + c0;
+#pragma unroll
+  for (int i = 0; i < RI; ++i) {
+    const int k = ty + 16 * i;
+    if (k >= ncoef) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int cc = (j < 4) ? 4 * tx + j : 32 + 4 * tx + (j - 4);
+      if (c0 + cc < nc) out[(size_t)k * nc + cc] = (double)sh[i][j] + (double)sl[i][j];
+    }
+  }
+}
+
+// Y[i][c] += sum_k W[i][k] L[leaf][k][c]; W (weighted moments) pre-split, L split on load
+__global__ void __launch_bounds__(128) k_l2p_df64(int nc, int ncoef, int box0, const int32_t* __restrict__ leaf_first,
+                                                  const int32_t* __restrict__ leaf_count, const float2* __restrict__ W,
+                                                  const double* __restrict__ L, double* __restrict__ Y) {
+  constexpr int CT = 64, KC = 16, RB = 64;
+  __shared__ __align__(16) float2 As[KC][RB];
+  __shared__ __align__(16) float2 Ls[KC][CT];
+  const int B = blockIdx.x, c0 = blockIdx.y * CT, rb0 = blockIdx.z * RB;
+  const int f0 = leaf_first[B], n = leaf_count[B];
+  if (rb0 >= n) return;
+  const int nr = min(RB, n - rb0);
+  const double* lb = L + (size_t)(box0 + B) * ncoef * nc;
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  float sh[4][8], sl[4][8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sh[q][j] = sl[q][j] = 0.f;
+  for (int k0 = 0; k0 < ncoef; k0 += KC) {
+    const int kn = min(KC, ncoef - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < KC * RB; e += 128) {
+      const int i = e / KC, k = e % KC;
+      As[k][i] = (i < nr && k < kn) ? W[(size_t)(f0 + rb0 + i) * ncoef + k0 + k] : make_float2(0.f, 0.f);
+    }
+    for (int e = threadIdx.x; e < KC * CT; e += 128) {
+      const int k = e / CT, cc = e % CT;
+      Ls[k][cc] = (k < kn && c0 + cc < nc) ? split_df(lb[(size_t)(k0 + k) * nc + c0 + cc]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int k = 0; k < KC; ++k) {
+      float2 l[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        l[q] = Ls[k][4 * tx + q];
+        l[4 + q] = Ls[k][32 + 4 * tx + q];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 w = As[k][ty + 16 * q];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) df_fma(sh[q][j], sl[q][j], w, l[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = ty + 16 * q;
+    if (i >= nr) continue;
+    double* yr = Y + (size_t)(f0 + rb0 + i) * nc + c0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int cc = (j < 4) ? 4 * tx + j : 32 + 4 * tx + (j - 4);
+      if (c0 + cc < nc) yr[cc] += (double)sh[q][j] + (double)sl[q][j];
+    }
+  }
+}
+
+// split of the weighted moments (1 or 2) S / h for k_l2p_df64
+__global__ void k_l2p_weights_df(size_t n, int ncoef, double inv_h, const double* __restrict__ S,
+                                 float2* __restrict__ w) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k = (int)(i % ncoef);
+  int r = 0;
+  while ((r + 1) * (r + 1) <= k) ++r;
+  w[i] = split_df(S[i] * (r * r == k ? inv_h : 2.0 * inv_h));
+}
+
 template <class T>
 __global__ void k_cast(size_t n, const double* __restrict__ a, T* __restrict__ b) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -790,6 +935,14 @@ void fmm_prepare(xrl_ctx* c) {
   cast(c->d.t_m2l, c->d.t_m2l32);
   cast(c->d.near_val, c->d.near_val32);
   cast(c->d.mom, c->d.mom32);
+  c->d.mom_hl.alloc(c->alloc, c->d.mom.n);
+  c->d.momw_hl.alloc(c->alloc, c->d.mom.n);
+  if (c->d.mom.n) {
+    const unsigned nb = (unsigned)((c->d.mom.n + 255) / 256);
+    k_split_df<<<nb, 256, 0, c->stream>>>(c->d.mom.n, c->d.mom.p, c->d.mom_hl.p);
+    k_l2p_weights_df<<<nb, 256, 0, c->stream>>>(c->d.mom.n, c->ncoef, (double)(1 << t.L) / t.side, c->d.mom.p,
+                                               c->d.momw_hl.p);
+  }
   c->d.mom32w.alloc(c->alloc, c->d.mom.n);
   if (c->d.mom.n)
     k_l2p_weights<<<(unsigned)((c->d.mom.n + 255) / 256), 256, 0, c->stream>>>(
@@ -860,6 +1013,9 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   else if (sizeof(T) == 4 && nc >= 32 && ncoef <= 96)
     k_p2m_tiled<6><<<dim3(nl, (nc + 63) / 64), 128, 0, s>>>(nc, ncoef, leaf0, c->d.leaf_first.p, c->d.leaf_count.p,
                                                             (const float*)mom, (const float*)X, (float*)Mx);
+  else if (sizeof(T) == 8 && c->df64_m2l && nc >= 32 && ncoef <= 96)
+    k_p2m_df64<6><<<dim3(nl, (nc + 63) / 64), 128, 0, s>>>(nc, ncoef, leaf0, c->d.leaf_first.p, c->d.leaf_count.p,
+                                                           c->d.mom_hl.p, (const double*)X, (double*)Mx);
   else
     k_p2m<T><<<dim3(nl, ecols), 256, 0, s>>>(nc, ct_e, ncoef, leaf0, c->d.leaf_first.p, c->d.leaf_count.p, mom, X,
                                              Mx);
@@ -920,6 +1076,9 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   if (sizeof(T) == 4 && nc >= 32)
     k_l2p_tiled<<<dim3(nl, (nc + 63) / 64, (c->max_leaf + 63) / 64), 128, 0, s>>>(
         nc, ncoef, leaf0, c->d.leaf_first.p, c->d.leaf_count.p, c->d.mom32w.p, (const float*)Lx, (float*)Y);
+  else if (sizeof(T) == 8 && c->df64_m2l && nc >= 32)
+    k_l2p_df64<<<dim3(nl, (nc + 63) / 64, (c->max_leaf + 63) / 64), 128, 0, s>>>(
+        nc, ncoef, leaf0, c->d.leaf_first.p, c->d.leaf_count.p, c->d.momw_hl.p, (const double*)Lx, (double*)Y);
   else
     k_l2p<T><<<dim3(nl, ecols), 128, 0, s>>>(nc, ct_e, ncoef, leaf0, (T)(1.0 / h), c->d.leaf_first.p,
                                              c->d.leaf_count.p, mom, Lx, Y);

@@ -200,6 +200,7 @@ struct Dev {
   DBuf<double> mom;                                  // [N][ncoef] P2M moments (leaf-scaled)
   DBuf<float> mom32;
   DBuf<float> mom32w;      // FP32 moments with the L2P weights folded in (k_l2p_weights)
+  DBuf<float2> mom_hl, momw_hl;   // double-float splits of the moments and of the weighted moments
   DBuf<double> t_m2m, t_l2l, t_m2l;                  // translation matrices (transposed)
   DBuf<float> t_m2m32, t_l2l32, t_m2l32;
   DBuf<int32_t> box_parent, box_oct, box_child_ptr, box_child;  // tree arrays (global ids)
