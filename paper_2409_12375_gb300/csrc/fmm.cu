@@ -1022,10 +1022,13 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   prof_end(c, s, ev, PH_P2M, 1, 2.0 * N * ncoef * nc, N * ncoef * sz + N * nc * sz + nl * ebytes);
   ev = prof_begin(c, s);
   const bool tiled = xlate_tiled<T>(c, nc);
+  const bool tcm64 = sizeof(T) == 8 && c->df64_m2l && tc64_usable(c, nc);
   for (int l = L - 1; l >= 2; --l) {
     int nbx = t.level_off[l + 1] - t.level_off[l];
     if (tcm)
       tc_m2m(c, l, nc, (float*)Mx, s);
+    else if (tcm64)
+      tc_m2m64(c, l, nc, (double*)Mx, s);
     else if (tiled)
       launch_xlate<T>(nbx, t.level_off[l], nc, ncoef, c->d.box_child_ptr.p, c->d.box_iota.p, c->d.box_oct16.p, tm2m,
                       Mx, Mx, false, s);
@@ -1036,7 +1039,7 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   {
     double nch = (double)(t.level_off[L + 1] - t.level_off[std::min(3, L + 1)]);
     double npar = (double)(t.level_off[L] - t.level_off[2]);
-    prof_end(c, s, ev, PH_M2M, std::max(0, L - 2) * (tcm ? 2 : 1), e2 * nch, (nch + npar) * ebytes);
+    prof_end(c, s, ev, PH_M2M, std::max(0, L - 2) * (tcm || tcm64 ? 2 : 1), e2 * nch, (nch + npar) * ebytes);
   }
   {
     int b0 = t.level_off[2];

@@ -373,10 +373,38 @@ __global__ void k_arnoldi_norm(int n, int nsys, int j, int m, cplx* __restrict__
   if (!active[s]) return;
   const int ldh = m + 1;
   cplx* ws = w + (size_t)s * n;
+  // eight independent loads in flight per thread: one CTA per system streams
+  // the vector, so memory-level parallelism, not bandwidth, sets the time
+  constexpr int U = 8;
+  double part[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) part[u] = 0.0;
+  for (int e0 = threadIdx.x; e0 < n; e0 += U * blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < n) part[u] += cabs2(ws[e]);
+    }
+  }
   cplx acc = make_double2(0, 0);
-  for (int e = threadIdx.x; e < n; e += blockDim.x) acc.x += cabs2(ws[e]);
+#pragma unroll
+  for (int u = 0; u < U; ++u) acc.x += part[u];
   double nw = sqrt(block_sum(acc, sh).x);
-  for (int e = threadIdx.x; e < n; e += blockDim.x) Vnext[(size_t)s * n + e] = nw > 0 ? cscale(ws[e], 1.0 / nw) : make_double2(0, 0);
+  const double inv = nw > 0 ? 1.0 / nw : 0.0;
+  cplx* vn = Vnext + (size_t)s * n;
+  for (int e0 = threadIdx.x; e0 < n; e0 += U * blockDim.x) {
+    cplx v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      v[u] = e < n ? ws[e] : make_double2(0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < n) vn[e] = cscale(v[u], inv);
+    }
+  }
   if (threadIdx.x == 0) {
     cplx* Hs = H + (size_t)s * (m + 1) * m;
     for (int i = 0; i <= j; ++i) Hs[i * m + j] = cadd(h1[(size_t)s * ldh + i], h2[(size_t)s * ldh + i]);

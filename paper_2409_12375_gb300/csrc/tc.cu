@@ -1588,6 +1588,55 @@ bool tc64_usable(const xrl_ctx* c, int nc) {
   return c->opt.tensor_cores != 0 && nc >= 64 && tc_npad(c->ncoef) <= 96 && c->d.tc_err.n > 0;
 }
 
+// One-time images of the FP64-accurate pass: the equilibration exponents d_k
+// (from the panel moments, the P2M operator: typical size of M[k]) and the
+// integer-slice images of the M2L and the 8 M2M tables.
+static void oz_prepare(xrl_ctx* c, cudaStream_t s) {
+  if (c->d.oz_bimg.n != 0) return;
+  const Tree& t = c->tree;
+  const int ncoef = c->ncoef, Kp = tc_kpad(ncoef), Np = tc_npad(ncoef) <= 64 ? 64 : 96;
+  std::vector<double> mom = c->d.mom.download();
+  std::vector<int32_t> dk(ncoef, 0);
+  for (int k = 0; k < ncoef; ++k) {
+    double mx = 0.0;
+    for (size_t i = 0; i < (size_t)c->N; ++i) mx = std::max(mx, std::fabs(mom[i * ncoef + k]));
+    dk[k] = mx > 0.0 ? std::ilogb(mx) : 0;
+  }
+  c->d.oz_dk.upload(c->alloc, dk);
+  const int noff = (int)(t.m2l_offsets.size() / 3);
+  c->d.oz_bimg.alloc(c->alloc, (size_t)noff * OZ_S * Np * Kp);
+  k_oz_pack_b<<<noff, 256, 0, s>>>(ncoef, Kp, Np, c->d.oz_dk.p, c->d.t_m2l.p, c->d.oz_bimg.p);
+  c->d.oz_m2m_img.alloc(c->alloc, (size_t)8 * OZ_S * Np * Kp);
+  k_oz_pack_b<<<8, 256, 0, s>>>(ncoef, Kp, Np, c->d.oz_dk.p, c->d.t_m2m.p, c->d.oz_m2m_img.p);
+  count_launch(c, 2);
+}
+
+// one level of the FP64-accurate M2M (parents at level l from their children
+// at l + 1), integer slices as the M2L below: with M'[k] = 2^-d_k M[k] and
+// T'[k] = 2^d_k T[k] the slices' product is T^T M exactly; two launches
+void tc_m2m64(xrl_ctx* c, int l, int nc, double* Mx, cudaStream_t s) {
+  const Tree& t = c->tree;
+  const int ncoef = c->ncoef, Kp = tc_kpad(ncoef), Np = tc_npad(ncoef) <= 64 ? 64 : 96;
+  const int nct = (nc + TC_ROWS - 1) / TC_ROWS;
+  const int s0 = t.level_off[l + 1], ns = t.level_off[l + 2] - s0;
+  const int nt = t.level_off[l + 1] - t.level_off[l];
+  oz_prepare(c, s);
+  c->d.oz_aimg.ensure(c->alloc, (size_t)ns * nct * OZ_S * TC_ROWS * Kp);
+  k_oz_pack_a<<<dim3(ns, nct), 256, 0, s>>>(nc, ncoef, Kp, s0, c->d.oz_dk.p, Mx, c->d.oz_aimg.p);
+  OzArgs a;
+  a.pr = m2l_pairs(c, t.level_off[l], nct, OZ_S, (size_t)OZ_S * 2 * TC_ROWS * Kp, (size_t)OZ_S * 2 * Np * Kp);
+  a.pr.src0 = s0;
+  a.pr.ptr = c->d.box_child_ptr.p;
+  a.pr.src = c->d.box_iota.p;
+  a.pr.off = c->d.box_oct16.p;
+  a.nc = nc;
+  a.aimg = reinterpret_cast<const char*>(c->d.oz_aimg.p);
+  a.bimg = reinterpret_cast<const char*>(c->d.oz_m2m_img.p);
+  a.out = Mx;
+  a.err = c->d.tc_err.p;
+  launch_oz(Np, dim3(nct, nt), a, s);
+}
+
 // FP64-accurate M2L of the refinement residuals (in = M, out = L, FP64)
 void tc_m2l64(xrl_ctx* c, int nbx, int b0, int nc, const double* Mx, double* Lx, cudaStream_t s) {
   const Tree& t = c->tree;
@@ -1595,21 +1644,7 @@ void tc_m2l64(xrl_ctx* c, int nbx, int b0, int nc, const double* Mx, double* Lx,
   const int nct = (nc + TC_ROWS - 1) / TC_ROWS;
   const int src0 = t.level_off[2];
   const int nsrc = t.n_boxes() - src0;
-  if (c->d.oz_bimg.n == 0) {
-    // d_k from the panel moments (the P2M operator): typical size of M[k]
-    std::vector<double> mom = c->d.mom.download();
-    std::vector<int32_t> dk(ncoef, 0);
-    for (int k = 0; k < ncoef; ++k) {
-      double mx = 0.0;
-      for (size_t i = 0; i < (size_t)c->N; ++i) mx = std::max(mx, std::fabs(mom[i * ncoef + k]));
-      dk[k] = mx > 0.0 ? std::ilogb(mx) : 0;
-    }
-    c->d.oz_dk.upload(c->alloc, dk);
-    const int noff = (int)(t.m2l_offsets.size() / 3);
-    c->d.oz_bimg.alloc(c->alloc, (size_t)noff * OZ_S * Np * Kp);
-    k_oz_pack_b<<<noff, 256, 0, s>>>(ncoef, Kp, Np, c->d.oz_dk.p, c->d.t_m2l.p, c->d.oz_bimg.p);
-    count_launch(c);
-  }
+  oz_prepare(c, s);
   c->d.oz_aimg.ensure(c->alloc, (size_t)nsrc * nct * OZ_S * TC_ROWS * Kp);
   k_oz_pack_a<<<dim3(nsrc, nct), 256, 0, s>>>(nc, ncoef, Kp, src0, c->d.oz_dk.p, Mx, c->d.oz_aimg.p);
   OzArgs a;

@@ -215,6 +215,7 @@ struct Dev {
   DBuf<int32_t> tc_err;     // set by a tensor-core kernel that timed out
   DBuf<uint16_t> oz_bimg;   // integer-slice BF16 images of the M2L tables (FP64-accurate path)
   DBuf<uint16_t> oz_aimg;   // integer-slice BF16 images of the FP64 multipoles, per product
+  DBuf<uint16_t> oz_m2m_img;   // integer-slice BF16 images of the 8 M2M tables
   DBuf<int32_t> oz_dk;      // power-of-two equilibration exponents per coefficient index
   // near field on the tensor cores: leaves padded to 16 panels
   DBuf<int32_t> tcp_a0, tcp_pc;         // per leaf: padded panel offset and count
@@ -361,6 +362,7 @@ void tc_p2p64(xrl_ctx* c, int ncols, const double* X, double* Y, cudaStream_t s)
 bool tcm_usable(const xrl_ctx* c, int ncols);
 void tc_p2m(xrl_ctx* c, int ncols, float* M, cudaStream_t s);
 void tc_m2m(xrl_ctx* c, int level, int ncols, float* M, cudaStream_t s);
+void tc_m2m64(xrl_ctx* c, int level, int ncols, double* M, cudaStream_t s);   // FP64-accurate, integer slices
 void tc_m2l64(xrl_ctx* c, int nbx, int b0, int ncols, const double* M, double* L, cudaStream_t s);
 // solve.cu
 void solver_prepare(xrl_ctx* c);
