@@ -754,111 +754,124 @@ __device__ __forceinline__ void warp_copy_async(void* dst, const void* src, size
 }
 
 // Stage 2: the reduced block-tridiagonal system for z_j = (u_j, t_{j+1}),
-// forward then backward; one warp per system.  All interface rows of x and
-// h_j (then z_j) live in shared memory (h is written to hb[s][j][2b] at the
-// end); the records R[f][j] stream through a ring of kZDepth buffers with
-// cp.async (one commit group per step, empty at the tail), so a step waits on
-// shared memory only.  kZDepth = 4, or 2 where four records do not fit.
+// forward then backward; one CTA of four warps per system.  All interface rows
+// of x and h_j (then z_j) live in shared memory (h is written to hb[s][j][2b]
+// at the end); the records R[f][j] stream through a ring of kZDepth buffers
+// with cp.async issued by warp 0 (one commit group per step, empty at the
+// tail), so a step waits on shared memory only.  Each 2b x 2b product of a
+// step is split over 128 threads: row r = tid % 64, column half tid / 64,
+// partial sums combined through shared memory (2b <= 48).  kZDepth = 4, or 2
+// where four records do not fit.
 template <class C, int kZDepth>
-__global__ void k_spike_z(int n, int b, int P, int m, int nper, const C* __restrict__ R, const C* __restrict__ xb,
-                          size_t xs, C* __restrict__ hb, const int* __restrict__ active) {
+__global__ void __launch_bounds__(128) k_spike_z(int n, int b, int P, int m, int nper, const C* __restrict__ R,
+                                                 const C* __restrict__ xb, size_t xs, C* __restrict__ hb,
+                                                 const int* __restrict__ active) {
   extern __shared__ __align__(16) unsigned char zsm_raw[];
   const int B2 = 2 * b;
   const size_t RS = (size_t)6 * b * b;
   C* rbuf = reinterpret_cast<C*>(zsm_raw);   // [kZDepth][6 b^2]
   C* hs = rbuf + kZDepth * RS;               // [(P-1)][2b]
   C* gs = hs + (size_t)(P - 1) * B2;         // [(P-1)][2b] interface rows of x
-  __shared__ C hp[32], tt[32];
+  __shared__ C hp[32], tt[32], part[128];
   const int s = blockIdx.x;
   if (P < 2 || (active && !active[s])) return;
-  const int f = s / nper, lane = threadIdx.x;
+  const int f = s / nper, tid = threadIdx.x, warp = tid >> 5;
+  const int r = tid & 63, half = tid >> 6;
   const int nst = P - 1;
   const C* Rf = R + (size_t)f * nst * RS;
   const C* x = xb + (size_t)s * xs;
   C* h = hb + (size_t)s * nst * B2;
   // forward records 0 .. kZDepth-2 in flight, one group each
-  for (int q = 0; q < kZDepth - 1; ++q) {
-    if (q < nst) warp_copy_async(rbuf + (size_t)(q % kZDepth) * RS, Rf + (size_t)q * RS, RS * sizeof(C));
-    else cp_commit();
-  }
-  for (int e = lane; e < nst * B2; e += 32) {
-    const int j = e / B2, r = e % B2;
-    gs[e] = x[(j + 1) * m - b + r];
+  if (warp == 0)
+    for (int q = 0; q < kZDepth - 1; ++q) {
+      if (q < nst) warp_copy_async(rbuf + (size_t)(q % kZDepth) * RS, Rf + (size_t)q * RS, RS * sizeof(C));
+      else cp_commit();
+    }
+  for (int e = tid; e < nst * B2; e += blockDim.x) {
+    const int j = e / B2, rr = e % B2;
+    gs[e] = x[(j + 1) * m - b + rr];
   }
   for (int j = 0; j < nst; ++j) {
     // keep kZDepth - 1 groups ahead: issue record j + kZDepth - 1 (or an empty group)
-    const int jn = j + kZDepth - 1;
-    if (jn < nst) warp_copy_async(rbuf + (size_t)(jn % kZDepth) * RS, Rf + (size_t)jn * RS, RS * sizeof(C));
-    else cp_commit();
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kZDepth - 1) : "memory");
-    __syncwarp();
+    if (warp == 0) {
+      const int jn = j + kZDepth - 1;
+      if (jn < nst) warp_copy_async(rbuf + (size_t)(jn % kZDepth) * RS, Rf + (size_t)jn * RS, RS * sizeof(C));
+      else cp_commit();
+      asm volatile("cp.async.wait_group %0;\n" ::"n"(kZDepth - 1) : "memory");
+    }
+    __syncthreads();
     const C* Ej = rbuf + (size_t)(j % kZDepth) * RS;
     const C* Wj = Ej + 4 * b * b;
     C* g = gs + j * B2;
-    if (j > 0)
-      for (int r = lane; r < b; r += 32) {
-        C acc = czero<C>();
-        for (int c = 0; c < b; ++c) acc = cfma(Wj[c * b + r], hp[c], acc);
-        g[r] = csubT(g[r], acc);
-      }
-    __syncwarp();
-    for (int r = lane; r < B2; r += 32) {
-      C a0 = czero<C>(), a1 = czero<C>(), a2 = czero<C>(), a3 = czero<C>();
-      int c = 0;
-      for (; c + 4 <= B2; c += 4) {
-        a0 = cfma(Ej[c * B2 + r], g[c], a0);
-        a1 = cfma(Ej[(c + 1) * B2 + r], g[c + 1], a1);
-        a2 = cfma(Ej[(c + 2) * B2 + r], g[c + 2], a2);
-        a3 = cfma(Ej[(c + 3) * B2 + r], g[c + 3], a3);
-      }
-      for (; c < B2; ++c) a0 = cfma(Ej[c * B2 + r], g[c], a0);
-      const C acc = caddT(caddT(a0, a1), caddT(a2, a3));
-      hs[j * B2 + r] = acc;
-      if (r < b) hp[r] = acc;
+    if (j > 0 && tid < b) {
+      C acc = czero<C>();
+      for (int c = 0; c < b; ++c) acc = cfma(Wj[c * b + tid], hp[c], acc);
+      g[tid] = csubT(g[tid], acc);
     }
-    __syncwarp();
+    __syncthreads();
+    {
+      C a0 = czero<C>(), a1 = czero<C>();
+      if (r < B2) {
+        const int c0 = half * b;
+        int c = 0;
+        for (; c + 2 <= b; c += 2) {
+          a0 = cfma(Ej[(c0 + c) * B2 + r], g[c0 + c], a0);
+          a1 = cfma(Ej[(c0 + c + 1) * B2 + r], g[c0 + c + 1], a1);
+        }
+        for (; c < b; ++c) a0 = cfma(Ej[(c0 + c) * B2 + r], g[c0 + c], a0);
+      }
+      part[tid] = caddT(a0, a1);
+    }
+    __syncthreads();
+    if (tid < B2) {
+      const C acc = caddT(part[tid], part[64 + tid]);
+      hs[j * B2 + tid] = acc;
+      if (tid < b) hp[tid] = acc;
+    }
   }
-  cp_wait_all();
-  __syncwarp();
+  if (warp == 0) cp_wait_all();
+  __syncthreads();
   if (nst >= 2) {
     // backward over j = nst - 2 .. 0 (record j), the same ring
     const int nb = nst - 1;
-    for (int q = 0; q < kZDepth - 1; ++q) {
-      if (q < nb) warp_copy_async(rbuf + (size_t)(q % kZDepth) * RS, Rf + (size_t)(nb - 1 - q) * RS, RS * sizeof(C));
-      else cp_commit();
-    }
+    if (warp == 0)
+      for (int q = 0; q < kZDepth - 1; ++q) {
+        if (q < nb) warp_copy_async(rbuf + (size_t)(q % kZDepth) * RS, Rf + (size_t)(nb - 1 - q) * RS, RS * sizeof(C));
+        else cp_commit();
+      }
     for (int q = 0; q < nb; ++q) {
       const int j = nb - 1 - q;
-      const int qn = q + kZDepth - 1;
-      if (qn < nb) warp_copy_async(rbuf + (size_t)(qn % kZDepth) * RS, Rf + (size_t)(nb - 1 - qn) * RS, RS * sizeof(C));
-      else cp_commit();
-      asm volatile("cp.async.wait_group %0;\n" ::"n"(kZDepth - 1) : "memory");
-      __syncwarp();
+      if (warp == 0) {
+        const int qn = q + kZDepth - 1;
+        if (qn < nb) warp_copy_async(rbuf + (size_t)(qn % kZDepth) * RS, Rf + (size_t)(nb - 1 - qn) * RS, RS * sizeof(C));
+        else cp_commit();
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kZDepth - 1) : "memory");
+      }
+      __syncthreads();
       const C* Ej = rbuf + (size_t)(q % kZDepth) * RS;
       const C* Vt = Ej + 5 * b * b;
       const C* zn = hs + (j + 1) * B2 + b;
-      for (int r = lane; r < b; r += 32) {
+      if (tid < b) {
         C acc = czero<C>();
-        for (int c = 0; c < b; ++c) acc = cfma(Vt[c * b + r], zn[c], acc);
-        tt[r] = acc;
+        for (int c = 0; c < b; ++c) acc = cfma(Vt[c * b + tid], zn[c], acc);
+        tt[tid] = acc;
       }
-      __syncwarp();
-      for (int r = lane; r < B2; r += 32) {
-        C a0 = czero<C>(), a1 = czero<C>();
-        int c = 0;
-        for (; c + 2 <= b; c += 2) {
-          a0 = cfma(Ej[(size_t)(b + c) * B2 + r], tt[c], a0);
-          a1 = cfma(Ej[(size_t)(b + c + 1) * B2 + r], tt[c + 1], a1);
+      __syncthreads();
+      {
+        C a0 = czero<C>();
+        if (r < B2) {
+          const int c0 = half * ((b + 1) / 2), c1 = half ? b : (b + 1) / 2;
+          for (int c = c0; c < c1; ++c) a0 = cfma(Ej[(size_t)(b + c) * B2 + r], tt[c], a0);
         }
-        for (; c < b; ++c) a0 = cfma(Ej[(size_t)(b + c) * B2 + r], tt[c], a0);
-        hs[j * B2 + r] = csubT(hs[j * B2 + r], caddT(a0, a1));
+        part[tid] = a0;
       }
-      __syncwarp();
+      __syncthreads();
+      if (tid < B2) hs[j * B2 + tid] = csubT(hs[j * B2 + tid], caddT(part[tid], part[64 + tid]));
     }
-    cp_wait_all();
+    if (warp == 0) cp_wait_all();
   }
-  __syncwarp();
-  for (int e = lane; e < nst * B2; e += 32) h[e] = hs[e];
+  __syncthreads();
+  for (int e = tid; e < nst * B2; e += blockDim.x) h[e] = hs[e];
 }
 
 constexpr int kSpikeRows = 1024;   // rows per CTA of the correction kernels
@@ -1061,11 +1074,11 @@ static int spike_stages(xrl_ctx* c, const BandWork& bw, int nsys, int nper, int 
     if (deep) {
       if (zsm > 48 * 1024)
         XRL_CUDA(cudaFuncSetAttribute(k_spike_z<C, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm));
-      k_spike_z<C, 4><<<nsys, 32, zsm, s>>>(n, b, P, m, nper, R, xb, xs, hb, active);
+      k_spike_z<C, 4><<<nsys, 128, zsm, s>>>(n, b, P, m, nper, R, xb, xs, hb, active);
     } else {
       if (zsm > 48 * 1024)
         XRL_CUDA(cudaFuncSetAttribute(k_spike_z<C, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm));
-      k_spike_z<C, 2><<<nsys, 32, zsm, s>>>(n, b, P, m, nper, R, xb, xs, hb, active);
+      k_spike_z<C, 2><<<nsys, 128, zsm, s>>>(n, b, P, m, nper, R, xb, xs, hb, active);
     }
     ++launches;
   }
