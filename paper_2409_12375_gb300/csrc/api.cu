@@ -217,6 +217,9 @@ xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {
     c->device = c->opt.device;
     XRL_CUDA(cudaSetDevice(c->device));
     XRL_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    XRL_CUDA(cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking));
+    XRL_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    XRL_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   });
   if (st != XRL_OK) {
     delete c;
@@ -732,7 +735,11 @@ void xrl_destroy(xrl_ctx* c) {
     prof_collect(c);
   } catch (...) {
   }
+  if (c->stream2) cudaStreamSynchronize(c->stream2);
   c->d = Dev();
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->stream2) cudaStreamDestroy(c->stream2);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

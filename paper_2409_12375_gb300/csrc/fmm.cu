@@ -970,8 +970,17 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   dim3 gp(nl, (nc + ct_p - 1) / ct_p);
   cudaEvent_t ev = prof_begin(c, s);
   int nl_p2p = 1;
+  // FP32 pass with the tensor-core near field and upward pass: the near field
+  // runs on a second stream beside P2M -> M2M -> M2L -> L2L (it only reads
+  // the packed X image that P2M also reads) and joins before the L2P adds
+  // into Y, so its CTAs fill the SMs that the small far-field kernels leave
+  // idle.  With the phase profiler on, the passes run in sequence so that each
+  // phase's events time it alone.
+  const bool fork =
+      sizeof(T) == 4 && tcp_usable(c, nc) && tcm_usable(c, nc) && c->stream2 != nullptr && !c->prof.on;
+  cudaStream_t sp = fork ? c->stream2 : s;
   if (sizeof(T) == 4 && tcp_usable(c, nc)) {
-    tc_p2p(c, nc, (const float*)X, (float*)Y, s);
+    tc_p2p_fork(c, nc, (const float*)X, (float*)Y, s, sp);
     nl_p2p = 2;
   } else if (sizeof(T) == 8 && c->df64_m2l && tcp_usable(c, nc)) {
     tc_p2p64(c, nc, (const double*)X, (double*)Y, s);
@@ -999,7 +1008,8 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     k_p2p<T><<<gp, 128, 0, s>>>(nc, ct_p, c->d.leaf_first.p, c->d.leaf_count.p, c->d.u_ptr32.p, c->d.u_src.p,
                                 c->d.near_off.p, c->d.near_w.p, near, X, Y);
   }
-  prof_end(c, s, ev, sizeof(T) == 8 ? PH_P2P64 : PH_P2P, nl_p2p, 2.0 * nne * nc, nne * sz + 2.0 * N * nc * sz);
+  prof_end(c, sp, ev, sizeof(T) == 8 ? PH_P2P64 : PH_P2P, nl_p2p, 2.0 * nne * nc, nne * sz + 2.0 * N * nc * sz);
+  if (fork) XRL_CUDA(cudaEventRecord(c->ev_join, sp));
   const int ecols = (nc + ct_e - 1) / ct_e;
   const int leaf0 = t.level_off[L];
   // FP32 pass: P2M and M2M on the tensor cores too (P2M reuses the
@@ -1075,6 +1085,7 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     double nch = (double)(t.level_off[L + 1] - t.level_off[std::min(3, L + 1)]);
     prof_end(c, s, ev, PH_L2L, std::max(0, L - 2), e2 * nch, 2.0 * nch * ebytes);
   }
+  if (fork) XRL_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
   ev = prof_begin(c, s);
   if (sizeof(T) == 4 && nc >= 32)
     k_l2p_tiled<<<dim3(nl, (nc + 63) / 64, (c->max_leaf + 63) / 64), 128, 0, s>>>(

@@ -1662,12 +1662,19 @@ bool tcp_usable(const xrl_ctx* c, int nc) {
 }
 
 // FP32 near field Y = P_near X on the tensor cores (two launches)
-void tc_p2p(xrl_ctx* c, int nc, const float* X, float* Y, cudaStream_t s) {
+void tc_p2p(xrl_ctx* c, int nc, const float* X, float* Y, cudaStream_t s) { tc_p2p_fork(c, nc, X, Y, s, s); }
+
+void tc_p2p_fork(xrl_ctx* c, int nc, const float* X, float* Y, cudaStream_t s, cudaStream_t s2) {
   const int nl = c->tree.n_leaves();
   const int nct = (nc + TC_ROWS - 1) / TC_ROWS;
   c->d.tcp_ximg.ensure(c->alloc, (size_t)nct * c->tcp_sum_pc * TC_PIECES * TC_ROWS);
   k_tcp_pack_x<<<dim3(nl, nct), 256, 0, s>>>(nc, c->tcp_sum_pc, c->d.leaf_first.p, c->d.leaf_count.p, c->d.tcp_a0.p,
                                              c->d.tcp_pc.p, X, c->d.tcp_ximg.p);
+  if (s2 != s) {
+    XRL_CUDA(cudaEventRecord(c->ev_fork, s));
+    XRL_CUDA(cudaStreamWaitEvent(s2, c->ev_fork, 0));
+    s = s2;
+  }
   if (c->d.p2p_gptr.n > 1) {
     Tc2Args g = {};
     g.mode = 1;

@@ -284,6 +284,8 @@ struct xrl_ctx {
   std::string err;
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t stream2 = nullptr;              // the FP32 near field runs here beside the far field
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   xrl::DevAlloc alloc;
   // inputs
   std::vector<double> xyz;
@@ -358,6 +360,8 @@ void tc_check(xrl_ctx* c, cudaStream_t s);
 bool tc64_usable(const xrl_ctx* c, int ncols);
 bool tcp_usable(const xrl_ctx* c, int ncols);
 void tc_p2p(xrl_ctx* c, int ncols, const float* X, float* Y, cudaStream_t s);
+// pack X on s, then the near field on s2 after a fork event (joined by the caller)
+void tc_p2p_fork(xrl_ctx* c, int ncols, const float* X, float* Y, cudaStream_t s, cudaStream_t s2);
 void tc_p2p64(xrl_ctx* c, int ncols, const double* X, double* Y, cudaStream_t s);
 bool tcm_usable(const xrl_ctx* c, int ncols);
 void tc_p2m(xrl_ctx* c, int ncols, float* M, cudaStream_t s);
