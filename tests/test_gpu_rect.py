@@ -159,3 +159,63 @@ def test_full_size_hybrid_coils_sampled_rows(lib):
     ref = v @ Pr.T
     err = np.linalg.norm(y[:, rows] - ref) / np.linalg.norm(ref)
     assert err < 1e-6, err
+
+
+def test_hybrid_mesh_argument_errors(lib):
+    """xrl_set_mesh_panels: a 4-vertex panel that is not a parallelogram is
+    XRL_EINVAL, a repeated vertex in a panel XRL_ETOPO, and a 4th slot below -1
+    XRL_EINVAL; the context stays usable for a valid mesh afterwards."""
+    m = _rect_bar()
+    x = lib.XRL()
+    try:
+        bad = np.asarray(m.xyz).copy()
+        q = int(np.flatnonzero(m.tri[:, 3] >= 0)[0])
+        bad[m.tri[q, 2]] += np.array([1e-5, 2e-5, 0.0])
+        with pytest.raises(lib.XRLError) as e:
+            x.set_mesh(bad, m.tri, m.cond)
+        assert e.value.code == 1
+        rep = m.tri.copy()
+        rep[q, 1] = rep[q, 0]
+        with pytest.raises(lib.XRLError) as e:
+            x.set_mesh(m.xyz, rep, m.cond)
+        assert e.value.code == 2
+        neg = m.tri.copy()
+        neg[q, 3] = -2
+        with pytest.raises(lib.XRLError) as e:
+            x.set_mesh(m.xyz, neg, m.cond)
+        assert e.value.code == 1
+        x.set_mesh(m.xyz, m.tri, m.cond)
+        x.set_conductors(m.sigma, m.thickness)
+        term = np.asarray(m.term)
+        for s_, k in m.ports:
+            x.add_port(np.flatnonzero(term == s_), np.flatnonzero(term == k))
+        x.setup()
+        assert x.stats()["n_panels"] == m.n_tri
+    finally:
+        x.close()
+    with pytest.raises(lib.XRLError) as e:
+        lib.XRL(precond=4)
+    assert e.value.code == 1
+
+
+def test_full_size_hybrid_coils_fp32_tensor_core_product(lib):
+    """The FP32 product of the full hybrid coils at 384 columns (every leaf has
+    at most 64 padded panels, so every sibling pair shares a CTA in the near
+    field and the M2L): against the FP64 product, column by column, with the
+    bound of the triangle coils' test."""
+    import torch
+    m = meshgen.coils(rect=True)
+    x = lib.XRL.from_mesh(m, fmm_order=7)
+    try:
+        rng = np.random.default_rng(34)
+        v = rng.standard_normal((384, m.n_tri)).astype(np.float32)
+        y64 = x.fmm_mvm(v.astype(np.float64))
+        xd = torch.tensor(v, device="cuda:0")
+        yd = torch.empty_like(xd)
+        x.fmm_mvm32_device(xd, yd)
+        torch.cuda.synchronize()
+        y32 = yd.cpu().numpy().astype(np.float64)
+    finally:
+        x.close()
+    e = (np.linalg.norm(y32 - y64, axis=1) / np.linalg.norm(y64, axis=1)).max()
+    assert e < 2e-5, e
