@@ -83,12 +83,13 @@ __device__ __forceinline__ C cmul_t(C a, C b) {
 template <class C, class R>
 __device__ __forceinline__ C cscale_t(C a, R s) { a.x *= s; a.y *= s; return a; }
 
-// X[r][6s + 2t + ri] = (A_t^T M^T v_s)(r)
+// X[r][6s + 2t + ri] = (A_t^T M^T v_s)(r); v is [nsys][nloop], or [nloop][nsys]
+// with loop_major (then the threads of one panel read one contiguous row)
 template <class T>
 __global__ void k_gather(int N, int nsys, int nloop, const int32_t* __restrict__ pan_br,
                          const double* __restrict__ pan_rho, const int32_t* __restrict__ mt_ptr,
                          const int32_t* __restrict__ mt_col, const int8_t* __restrict__ mt_val,
-                         const cplx* __restrict__ v, T* __restrict__ X) {
+                         const cplx* __restrict__ v, T* __restrict__ X, int loop_major) {
   typedef typename CT<T>::type C;
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)N * nsys) return;
@@ -100,7 +101,7 @@ __global__ void k_gather(int N, int nsys, int nloop, const int32_t* __restrict__
     if (b < 0) continue;
     C ie = cmk<C>((T)0, (T)0);
     for (int q = mt_ptr[b]; q < mt_ptr[b + 1]; ++q) {
-      const cplx x = vs[mt_col[q]];
+      const cplx x = loop_major ? v[(size_t)mt_col[q] * nsys + s] : vs[mt_col[q]];
       const C xc = cmk<C>((T)x.x, (T)x.y);
       ie = mt_val[q] > 0 ? cadd_t(ie, xc) : csub_t(ie, xc);
     }
@@ -111,6 +112,21 @@ __global__ void k_gather(int N, int nsys, int nloop, const int32_t* __restrict__
   for (int t = 0; t < 3; ++t) {
     out[2 * t] = ip[t].x;
     out[2 * t + 1] = ip[t].y;
+  }
+}
+
+// out[l][s] = in[s][l] (systems fastest), 32 x 32 tiles through shared memory
+__global__ void k_to_loop_major(int n, int nsys, const cplx* __restrict__ in, cplx* __restrict__ out) {
+  __shared__ cplx tile[32][33];
+  const int l0 = blockIdx.x * 32, s0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int sy = s0 + k, lx = l0 + threadIdx.x;
+    if (sy < nsys && lx < n) tile[k][threadIdx.x] = in[(size_t)sy * n + lx];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int ly = l0 + k, sx = s0 + threadIdx.x;
+    if (ly < n && sx < nsys) out[(size_t)ly * nsys + sx] = tile[threadIdx.x][k];
   }
 }
 
@@ -704,7 +720,7 @@ static void sys_consts(xrl_ctx* c, Work& wk, int nsys, int nport, int nf, const 
 // w = Z(f_s) v_s for all systems (eq. 8); the FMM runs in FP64, or in FP32
 // for the inner iterations of the mixed-precision mode (low = true)
 template <class T>
-static void apply_A_t(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, T* X, T* Y) {
+static void apply_A_t(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, T* X, T* Y, bool loop_major) {
   const Topo& T_ = c->topo;
   const int N = c->N;
   const int nc = 6 * nsys;
@@ -712,7 +728,8 @@ static void apply_A_t(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, T*
   wk.Vb.ensure(c->alloc, (size_t)nsys * T_.n_cb);
   cudaEvent_t ev = prof_begin(c, s);
   k_gather<T><<<nblk((size_t)N * nsys), 256, 0, s>>>(N, nsys, T_.n_loops, c->d.pan_br.p, c->d.pan_rho.p,
-                                                     c->d.mt_ptr.p, c->d.mt_col.p, c->d.mt_val.p, v, X);
+                                                     c->d.mt_ptr.p, c->d.mt_col.p, c->d.mt_val.p, v, X,
+                                                     loop_major ? 1 : 0);
   const double nnzm = (double)T_.m_col.size();
   prof_end(c, s, ev, PH_OPER, 1, 8.0 * nnzm * nsys + 18.0 * N * nsys, nsys * (16.0 * nnzm + 6.0 * sizeof(T) * N));
   if (sizeof(T) == 8)
@@ -731,16 +748,18 @@ static void apply_A_t(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, T*
   c->stats.n_mvm++;
 }
 
-static void apply_A(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, bool low = false) {
+// v is [nsys][n_loops], or [n_loops][nsys] with loop_major; w always [nsys][n_loops]
+static void apply_A(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, bool low = false,
+                    bool loop_major = false) {
   const size_t n = (size_t)c->N * 6 * nsys;
   if (low) {
     wk.X32.ensure(c->alloc, n);
     wk.Y32.ensure(c->alloc, n);
-    apply_A_t<float>(c, wk, nsys, v, w, wk.X32.p, wk.Y32.p);
+    apply_A_t<float>(c, wk, nsys, v, w, wk.X32.p, wk.Y32.p, loop_major);
   } else {
     wk.X.ensure(c->alloc, n);
     wk.Y.ensure(c->alloc, n);
-    apply_A_t<double>(c, wk, nsys, v, w, wk.X.p, wk.Y.p);
+    apply_A_t<double>(c, wk, nsys, v, w, wk.X.p, wk.Y.p, loop_major);
   }
 }
 
@@ -954,15 +973,17 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
       if (!use_graph) {
         apply_A(c, wk, nsys, zj, wk.w.p, mixed);
       } else {
-        XRL_CUDA(cudaMemcpyAsync(wk.zst.p, zj, sizeof(cplx) * tot, cudaMemcpyDeviceToDevice, s));
+        // staged loop-major, so that the gather reads one contiguous row per loop
+        k_to_loop_major<<<dim3((n + 31) / 32, (nsys + 31) / 32), dim3(32, 8), 0, s>>>(n, nsys, zj, wk.zst.p);
+        count_launch(c);
         if (graph_state == 0) {
-          apply_A(c, wk, nsys, wk.zst.p, wk.w.p, mixed);
+          apply_A(c, wk, nsys, wk.zst.p, wk.w.p, mixed, true);
           graph_state = 1;
         } else {
           if (graph_state == 1) {
             c->prof.capturing = true;
             XRL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            apply_A(c, wk, nsys, wk.zst.p, wk.w.p, mixed);
+            apply_A(c, wk, nsys, wk.zst.p, wk.w.p, mixed, true);
             XRL_CUDA(cudaStreamEndCapture(s, &graph));
             c->prof.capturing = false;
             XRL_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
