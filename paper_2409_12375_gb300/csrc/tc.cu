@@ -26,6 +26,11 @@
 // accumulators (warp w reads TMEM lanes 32 (w % 4) .. + 31).  Every wait is
 // bounded; on a timeout the kernel raises *err, drains its own copies and
 // frees its tensor memory.
+//
+// Kernels: k_xlate_tc (one target per CTA: M2L at order 8, P2M, the M2M
+// levels), k_xlate_tc2 (two sibling targets per CTA over their merged list:
+// the M2L at <= 64 coefficients and the near field), k_xlate_oz (the
+// FP64-accurate M2L, M2M and near field in integer slices).
 #include <cuda_bf16.h>
 
 #include <algorithm>

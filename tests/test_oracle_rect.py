@@ -185,3 +185,25 @@ def test_rect_grid_null_loop_mode_carries_no_panel_current(rect_bar):
     Pt = P.dense_P(P.Geometry(tri_bar.xyz, tri_bar.tri))
     st = np.linalg.svd(ct.loop_matrix(1e5, ct.potential_part(Pt[np.ix_(ct.live, ct.live)])), compute_uv=False)
     assert st[-1] > 1e-6 * st[0]
+
+
+@pytest.mark.parametrize("name", ["bar", "coils", "coil1"])
+def test_hybrid_generator_closed_oriented_parallelograms(name):
+    """The rect=True meshes: closed and consistently oriented, every 4-vertex
+    panel a parallelogram, and the same vertices and loop count as the
+    triangulated mesh of the same lattice (the rectangles only merge pairs of
+    triangles)."""
+    if name == "bar":
+        m, t = meshgen.bar(jitter=0.0, rect=True, n_l=10), meshgen.bar(jitter=0.0, n_l=10)
+    elif name == "coils":
+        m, t = meshgen.coils(rect=True), meshgen.coils()
+    else:
+        kw = dict(outer=2e-3, turns=1, n_w=2, step=0.2e-3, n_coils=1)
+        m, t = meshgen.coils(rect=True, **kw), meshgen.coils(**kw)
+    assert meshgen.crop_check(m) == (True, True)
+    quad = m.tri[:, 3] >= 0
+    V = np.asarray(m.xyz)[np.where(m.tri >= 0, m.tri, 0)]
+    d = np.linalg.norm(V[quad, 0] + V[quad, 2] - V[quad, 1] - V[quad, 3], axis=1)
+    assert np.all(d <= 1e-9 * np.linalg.norm(V[quad, 2] - V[quad, 0], axis=1))
+    assert m.xyz.shape == t.xyz.shape
+    assert m.n_tri + int(quad.sum()) == t.n_tri
