@@ -72,9 +72,11 @@ typedef struct {
                           near field; default 2 (see xrl_export_lists) */
   int32_t use_graphs;  /* 1 (default): the inner operator of every Arnoldi step is replayed from a
                           CUDA graph captured once per solve; 0: plain launches */
-  int32_t tensor_cores; /* 1 (default): the M2L translations of the FP32 products (precision 1) run
-                           on the tcgen05 tensor cores in split TF32 (hi/lo, three products,
-                           ~FP32 accuracy) for n_cols >= 64; 0: FP32 CUDA-core kernels only */
+  int32_t tensor_cores; /* 1 (default): for n_cols >= 64 the FP32 products of the mixed mode run
+                           their near field, P2M, M2M and M2L on the tcgen05 tensor cores (three
+                           BF16 pieces, six products, ~FP32 accuracy) and the FP64-accurate
+                           residuals their near field, M2M and M2L in 7-bit integer slices
+                           (exact FP32 accumulation); 0: CUDA-core kernels only */
 } xrl_options;
 
 /* Fill `opt` with the defaults listed above. */
@@ -142,8 +144,9 @@ xrl_status xrl_fmm_mvm_device(xrl_ctx* ctx, int32_t n_cols, const double* d_x, d
                               void* stream);
 
 /* The FP32 product of the mixed-precision solver's inner iterations (Sec.
- * II-C evaluated in FP32: near field and expansions in FP32, M2L on the
- * tensor cores when opt.tensor_cores and n_cols >= 64): y = P x on DEVICE
+ * II-C evaluated in FP32: near field, P2M, M2M and M2L on the tensor cores
+ * when opt.tensor_cores and n_cols >= 64, the near field on a second stream
+ * of the context beside the far field; L2L and L2P FP32): y = P x on DEVICE
  * buffers d_x, d_y ([n_cols][n_tri], float32) enqueued on `stream` (NULL =
  * the context's stream).  Relative accuracy ~1e-6 (FP32 rounding plus the
  * order-p truncation).  Synchronises the stream on return to check the
@@ -231,7 +234,8 @@ xrl_status xrl_apply_operator(xrl_ctx* ctx, int32_t n_sys, const double* freq, c
                               double* w);
 
 /* Preconditioner action for parity checks: w_s = Q(f_s) v_s with Q of eq. 10
- * (the sparse matrix itself, not its inverse); layout as xrl_apply_operator. */
+ * (opt.precond = 1 or 2) or the diagonal-of-L Q_L (opt.precond = 3), the
+ * sparse matrix itself, not its inverse; layout as xrl_apply_operator. */
 xrl_status xrl_apply_precond_matrix(xrl_ctx* ctx, int32_t n_sys, const double* freq,
                                     const double* v, double* w);
 
