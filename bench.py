@@ -349,7 +349,8 @@ def main():
     if not args.no_autotune:
         leaf, order, ms, err = x.autotune(6 * len(m.freqs) * len(m.ports), 1e-6, opts["precision"])
         opts["leaf_target"], opts["fmm_order"] = leaf, order
-        tuned = {"leaf_target": leaf, "fmm_order": order, "product_ms": ms, "product_err": err}
+        tuned = {"leaf_target": leaf, "fmm_order": order, "product_ms": ms, "product_err": err,
+                 "tc_targets_per_cta": x.stats()["tc_targets_per_cta"]}
     st = x.stats()
     ext = torch.cuda.ExternalStream(x.stream_handle())
     nsys = len(m.freqs) * len(m.ports)

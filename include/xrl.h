@@ -196,6 +196,9 @@ typedef struct {
                                16 panels); 0 when that path is off */
   double precond_setup_ms;  /* host + device time of the last setup spent building the preconditioner
                                pencil (P entries, loop pattern, band ordering and band values) */
+  int32_t tc_targets_per_cta; /* targets per CTA of the FP32 tensor-core M2L and near field (2: sibling
+                                 pairs share a CTA where the coefficients / padded leaves are <= 64;
+                                 1: one each), as xrl_autotune chose it; 2 before any autotune */
 } xrl_stats;
 
 /* FMM autotuner: tries leaf_target in {16, 32, 64} x fmm_order in {6, 7, 8}
@@ -204,8 +207,10 @@ typedef struct {
  * two seeded random columns to mvm_tol (relative 2-norm).  Among admissible
  * candidates, the one with the fastest product at n_cols columns is kept,
  * timed with CUDA events in the precision the solver's inner iterations use
- * (FP32 if `precision` = 1, else FP64).  The context ends set up with it, and
- * its options are updated.  Outputs (host, may be NULL): the chosen
+ * (FP32 if `precision` = 1, else FP64); in FP32 each candidate is timed with
+ * one and with two sibling targets per tensor-core CTA and keeps the faster
+ * (xrl_stats.tc_targets_per_cta).  The context ends set up with it, and its
+ * options are updated.  Outputs (host, may be NULL): the chosen
  * leaf_target, fmm_order, its product time in ms, and its error.
  * XRL_ENOCONV if no candidate meets mvm_tol (the context is left set up with
  * the most accurate one). */

@@ -384,6 +384,7 @@ xrl_status xrl_setup(xrl_ctx* c) {
     c->stats.n_boxes = c->tree.n_boxes();
     c->stats.n_vertex_loops = T.n_vertex_loops;
     c->stats.n_global_loops = T.n_global_loops;
+    c->stats.tc_targets_per_cta = c->tc_targets;
     c->stats.setup_ms = now_ms() - t0;
     c->ready = true;
   });
@@ -500,6 +501,7 @@ xrl_status xrl_autotune(xrl_ctx* c, int32_t nc, double tol, int32_t precision, i
     struct Cand {
       int leaf, p;
       double err, ms;
+      int tct;   // targets per CTA of the FP32 tensor-core M2L and near field
     };
     std::vector<Cand> res;
     for (int p : {6, 7, 8})
@@ -515,8 +517,10 @@ xrl_status xrl_autotune(xrl_ctx* c, int32_t nc, double tol, int32_t precision, i
         for (size_t k = 0; k < y.size(); ++k) en += (y[k] - ref[k]) * (y[k] - ref[k]);
         double err = std::sqrt(en) / rn;
         double ms = -1.0;
+        int tct = 2;
         if (err <= tol) {
           // time the product at nc columns in the solver's inner precision
+          // (FP32: with one and with two sibling targets per tensor-core CTA)
           size_t n = (size_t)N * nc;
           cudaEvent_t a, b;
           XRL_CUDA(cudaEventCreate(&a));
@@ -526,10 +530,20 @@ xrl_status xrl_autotune(xrl_ctx* c, int32_t nc, double tol, int32_t precision, i
             X.alloc(c->alloc, n);
             Y.alloc(c->alloc, n);
             XRL_CUDA(cudaMemsetAsync(X.p, 0, n * sizeof(float), c->stream));
-            fmm_apply32(c, nc, X.p, Y.p, c->stream);
-            XRL_CUDA(cudaEventRecord(a, c->stream));
-            for (int r = 0; r < 3; ++r) fmm_apply32(c, nc, X.p, Y.p, c->stream);
-            XRL_CUDA(cudaEventRecord(b, c->stream));
+            for (int t : {1, 2}) {
+              c->tc_targets = t;
+              fmm_apply32(c, nc, X.p, Y.p, c->stream);
+              XRL_CUDA(cudaEventRecord(a, c->stream));
+              for (int r = 0; r < 3; ++r) fmm_apply32(c, nc, X.p, Y.p, c->stream);
+              XRL_CUDA(cudaEventRecord(b, c->stream));
+              XRL_CUDA(cudaEventSynchronize(b));
+              float f = 0.f;
+              XRL_CUDA(cudaEventElapsedTime(&f, a, b));
+              if (ms < 0 || f / 3.0 < ms) {
+                ms = f / 3.0;
+                tct = t;
+              }
+            }
           } else {
             DBuf<double> X, Y;
             X.alloc(c->alloc, n);
@@ -540,10 +554,12 @@ xrl_status xrl_autotune(xrl_ctx* c, int32_t nc, double tol, int32_t precision, i
             for (int r = 0; r < 3; ++r) fmm_apply(c, nc, X.p, Y.p, c->stream);
             XRL_CUDA(cudaEventRecord(b, c->stream));
           }
-          XRL_CUDA(cudaEventSynchronize(b));
-          float f = 0.f;
-          XRL_CUDA(cudaEventElapsedTime(&f, a, b));
-          ms = f / 3.0;
+          if (precision != 1) {
+            XRL_CUDA(cudaEventSynchronize(b));
+            float f = 0.f;
+            XRL_CUDA(cudaEventElapsedTime(&f, a, b));
+            ms = f / 3.0;
+          }
           cudaEventDestroy(a);
           cudaEventDestroy(b);
           c->d.X32.release();
@@ -553,7 +569,7 @@ xrl_status xrl_autotune(xrl_ctx* c, int32_t nc, double tol, int32_t precision, i
           c->d.Mexp.release();
           c->d.Lexp.release();
         }
-        res.push_back({leaf, p, err, ms});
+        res.push_back({leaf, p, err, ms, tct});
       }
     int best = -1;
     for (size_t k = 0; k < res.size(); ++k)
@@ -565,6 +581,7 @@ xrl_status xrl_autotune(xrl_ctx* c, int32_t nc, double tol, int32_t precision, i
     }
     c->opt.fmm_order = res[best].p;
     c->opt.leaf_target = res[best].leaf;
+    c->tc_targets = res[best].tct;
     c->ready = false;
     if (xrl_setup(c) != XRL_OK) throw Error(XRL_EINVAL, c->err);
     if (best_leaf) *best_leaf = res[best].leaf;

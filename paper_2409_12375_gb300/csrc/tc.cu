@@ -1556,7 +1556,7 @@ void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cud
   const int nsrc = t.n_boxes() - src0;
   c->d.tc_aimg.ensure(c->alloc, (size_t)nsrc * nct * TC_PIECES * TC_ROWS * Kp);
   k_tc_pack_a<<<dim3(nsrc, nct), 256, 0, s>>>(nc, ncoef, Kp, src0, Mx, c->d.tc_aimg.p);
-  if (Np == 64 && c->d.m2l_gptr.n > 1 && b0 == src0 && nbx == nsrc) {
+  if (Np == 64 && c->tc_targets == 2 && c->d.m2l_gptr.n > 1 && b0 == src0 && nbx == nsrc) {
     Tc2Args g = {};
     g.mode = 0;
     g.nc = nc;
@@ -1680,7 +1680,7 @@ void tc_p2p_fork(xrl_ctx* c, int nc, const float* X, float* Y, cudaStream_t s, c
     XRL_CUDA(cudaStreamWaitEvent(s2, c->ev_fork, 0));
     s = s2;
   }
-  if (c->d.p2p_gptr.n > 1) {
+  if (c->tc_targets == 2 && c->d.p2p_gptr.n > 1) {
     Tc2Args g = {};
     g.mode = 1;
     g.nc = nc;

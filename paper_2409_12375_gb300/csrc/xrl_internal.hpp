@@ -296,6 +296,7 @@ struct xrl_ctx {
   int N = 0, ncoef = 0, p = 0, max_leaf = 0;
   bool df64_m2l = false;   // FP64 M2L on the FP32 pipes (set inside mixed-precision solves)
   int tcp_sum_pc = 0;                   // padded panels of all leaves (tensor-core near field)
+  int tc_targets = 2;                   // targets per CTA of the FP32 tensor-core M2L / near field (autotuned)
   int64_t tcp_img_bytes = 0, ozp_img_bytes = 0;
   int last_nsys = 0, last_nport = 0;
   std::vector<int32_t> last_port_loop;

@@ -41,7 +41,8 @@ class Stats(ctypes.Structure):
                 ("total_iters", ctypes.c_int32), ("total_inner", ctypes.c_int32), ("n_mvm", ctypes.c_int32),
                 ("max_rel_res", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("mvm_ms", ctypes.c_double), ("peak_device_bytes", ctypes.c_int64),
-                ("near_nnz_padded", ctypes.c_int64), ("precond_setup_ms", ctypes.c_double)]
+                ("near_nnz_padded", ctypes.c_int64), ("precond_setup_ms", ctypes.c_double),
+                ("tc_targets_per_cta", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -27,6 +27,7 @@ def test_autotune_meets_bound_and_keeps_parity(lib, bar_mesh, bar_dense_P):
         leaf, order, ms, err = x.autotune(n_cols=6, mvm_tol=1e-6, precision=1)
         assert leaf in (16, 32, 64) and order in (6, 7, 8)
         assert 0.0 <= err <= 1e-6 and ms > 0.0
+        assert x.stats()["tc_targets_per_cta"] in (1, 2)
         # the context is left set up with the choice: tree and product parity
         ref = tree.build(bar_mesh.xyz, bar_mesh.tri, leaf_target=leaf, ws=2)
         keys, perm, _ = x.export_tree()
@@ -62,5 +63,29 @@ def test_autotune_unreachable_bound(lib, bar_mesh, bar_dense_P):
         y = x.fmm_mvm(v)
         yr = bar_dense_P @ v
         assert np.linalg.norm(y - yr) / np.linalg.norm(yr) < 1e-6
+    finally:
+        x.close()
+
+
+def test_autotune_targets_per_cta_keeps_parity(lib, bar_mesh, bar_dense_P):
+    """At 64 columns (the tensor-core paths) the autotuner also chooses one or
+    two sibling targets per CTA; the FP32 product of the chosen configuration
+    matches the oracle within the FP32 bound either way."""
+    import torch
+    x = lib.XRL.from_mesh(bar_mesh, precision=1)
+    try:
+        leaf, order, ms, err = x.autotune(n_cols=64, mvm_tol=1e-6, precision=1)
+        t = x.stats()["tc_targets_per_cta"]
+        assert t in (1, 2)
+        rng = np.random.default_rng(8)
+        v = rng.standard_normal((64, bar_dense_P.shape[0])).astype(np.float32)
+        xd = torch.tensor(v, device="cuda:0")
+        yd = torch.empty_like(xd)
+        x.fmm_mvm32_device(xd, yd)
+        torch.cuda.synchronize()
+        ref = v.astype(np.float64) @ bar_dense_P.T
+        e32 = np.linalg.norm(yd.cpu().numpy().astype(np.float64) - ref) / np.linalg.norm(ref)
+        e64 = np.linalg.norm(x.fmm_mvm(v.astype(np.float64)) - ref) / np.linalg.norm(ref)
+        assert e32 < e64 + 2e-6, (t, e32, e64)
     finally:
         x.close()
