@@ -195,8 +195,10 @@ def peaks():
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the unchanged kernel on this workload's launch
 # configuration (profiles/top_kernels_coil_sweep.md); None where none exists
-# ncu DRAM bytes (read + write) per launch of the dominant kernels at the bench's
-# configuration; None until a capture of the current kernels exists
+# ncu DRAM bytes (read + write) per launch of the dominant kernels, captured at
+# order 7, leaf target 32, 384 columns on the coils (profiles/top_kernels_coil_sweep.md);
+# reported only when the bench runs that configuration
+NCU_TRAFFIC_CFG = (7, 32)
 NCU_TRAFFIC = {"m2l": 84.400128e6 + 31.16032e6,        # k_xlate_tc2<0>, order 7, 384 columns
                "p2p": 437.365248e6 + 33.278464e6,      # k_xlate_tc2<1>
                "m2l64": 232.165888e6 + 85.900032e6,    # k_xlate_oz<64>
@@ -221,7 +223,7 @@ def phase_kernel(name, p):
         "l2l": "k_m2l_tiled<%d,1> list form + k_m2l_df64<1> (residuals)" % ((np_ + 15) // 16)}.get(name, name)
 
 
-def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0):
+def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0, leaf=32):
     """Roofline entry of one profiling phase: algorithmic flops (or bytes) per
     launch over the phase's CUDA-event time per launch, against the peak of the
     unit that executes it."""
@@ -229,7 +231,7 @@ def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0):
     mixed = precision == "mixed"
     alg = d["flops"] / (d["ms"] * 1e-3) / 1e12          # algorithmic TFLOP/s
     out = {"kernel": phase_kernel(name, p), "avg_launch_ms": avg_ms, "launches": d["launches"],
-           "traffic": NCU_TRAFFIC.get(name) if mixed else None}
+           "traffic": NCU_TRAFFIC.get(name) if mixed and (p, leaf) == NCU_TRAFFIC_CFG and nc == 384 else None}
     ncoef = (p + 1) ** 2
     pad = lambda v: (v + 15) // 16 * 16
     tile_pad = (pad(ncoef) * pad(ncoef)) / float(ncoef * ncoef) * (128 * ((nc + 127) // 128)) / float(nc)
@@ -399,7 +401,8 @@ def main():
     # roofline of every major phase; "roofline" is the dominant one
     pk = peaks()
     near_pad = st["near_nnz_padded"] / float(st["near_nnz"]) if st.get("near_nnz_padded") else 0.0
-    roofs = {k: phase_roofline(k, prof[k], pk, args.precision, opts["fmm_order"], 6 * nsys, near_pad)
+    roofs = {k: phase_roofline(k, prof[k], pk, args.precision, opts["fmm_order"], 6 * nsys, near_pad,
+                               opts["leaf_target"])
              for k in ("p2p", "m2l", "p2p64", "m2l64", "precond", "operator", "p2m", "l2p", "m2m", "l2l")
              if k in prof and prof[k]["ms"] > 0}
     dom = max(roofs, key=lambda k: prof[k]["ms"])
