@@ -213,3 +213,36 @@ def test_precond_L_symmetric_positive_and_distinct_from_diag_P(two_circ, two_bar
     S = (touch.astype(float) @ touch.T.astype(float)) > 0
     assert not np.any((QL != 0) & ~S) and not np.any((Q != 0) & ~S)
     assert np.max(np.abs(QL.imag - Q.imag)) > 1e-3 * np.max(np.abs(Q.imag))
+
+
+def test_both_preconditioners_cut_gmres_iterations(bar_circ, bar_dense_P):
+    """Dense restarted GMRES (restart 50, relative residual 1e-8) on the bar's
+    loop system at 10 MHz: the diagonal-of-P (eq. 10) and the diagonal-of-L
+    preconditioners, applied exactly, each need under a fifth of the
+    unpreconditioned iterations.  (Their own counts differ by about one here:
+    both keep the loop-space Z_s whole, so they differ only in the inductive
+    couplings of branches that share a panel.)"""
+    import scipy.linalg as la
+    import scipy.sparse.linalg as sla
+    c = bar_circ
+    f = 1e7
+    Pl = bar_dense_P[np.ix_(c.live, c.live)]
+    Z = c.loop_matrix(f, c.potential_part(Pl))
+    b = c.port_rhs()[:, 0].astype(complex)
+
+    def iters(Q):
+        n = [0]
+        M = None
+        if Q is not None:
+            lu = la.lu_factor(Q)
+            M = sla.LinearOperator(Z.shape, matvec=lambda v: la.lu_solve(lu, v), dtype=complex)
+        x, info = sla.gmres(Z, b, M=M, rtol=1e-8, restart=50, maxiter=20,
+                            callback=lambda r: n.__setitem__(0, n[0] + 1), callback_type="pr_norm")
+        assert info == 0
+        assert np.linalg.norm(Z @ x - b) <= 1e-7 * np.linalg.norm(b)
+        return n[0]
+
+    n0 = iters(None)
+    nP = iters(C.precond_matrix(c, f, bar_dense_P))
+    nL = iters(C.precond_matrix_L(c, f, bar_dense_P))
+    assert nP < 0.2 * n0 and nL < 0.2 * n0, (n0, nP, nL)
