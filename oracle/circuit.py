@@ -42,7 +42,14 @@ MU0_4PI = 1e-7
 
 
 class Circuit:
-    def __init__(self, mesh):
+    """PEEC graph, A_t and M of a mesh.
+
+    sparse=True stores A_t as three scipy CSR matrices (the same entries,
+    at most two per branch row) instead of one dense [3, n_cb, n_live]
+    array, so that meshes of tens of thousands of panels fit in memory;
+    every method accepts either form."""
+
+    def __init__(self, mesh, sparse=False):
         self.mesh = mesh
         tri = np.asarray(mesh.tri, np.int64)
         term = np.asarray(mesh.term, np.int64)
@@ -105,17 +112,31 @@ class Circuit:
         self.head = np.array(heads, np.int64)
         self.n_branch = self.tail.shape[0]
 
-        # centroid-midpoint matrices A_t (Algorithm 1): [n_cb, n_live] x 3
+        # centroid-midpoint matrices A_t (Algorithm 1): [n_cb, n_live] x 3,
+        # A_t(b, tail) = +rho_t, A_t(b, head) = -rho_t, rho = m_e - c_p
         G = self.geom
         xyz = np.asarray(mesh.xyz, float)
-        self.A = np.zeros((3, self.n_cb, self.n_live))
+        rows, cols, vals = [], [], []
         for b, (e, a, h) in enumerate(ridx):
             mid = 0.5 * (xyz[keys[e, 0]] + xyz[keys[e, 1]])
-            rho_a = mid - G.c[a]
-            self.A[:, b, self.panel_node[a]] += rho_a
+            rows.append(b)
+            cols.append(self.panel_node[a])
+            vals.append(mid - G.c[a])
             if h >= 0:
-                rho_h = mid - G.c[h]
-                self.A[:, b, self.panel_node[h]] -= rho_h
+                rows.append(b)
+                cols.append(self.panel_node[h])
+                vals.append(-(mid - G.c[h]))
+        rows = np.array(rows, np.int64)
+        cols = np.array(cols, np.int64)
+        vals = np.array(vals, float).reshape(-1, 3)
+        if sparse:
+            from scipy import sparse as sp
+            self.A = [sp.csr_matrix((vals[:, t], (rows, cols)), shape=(self.n_cb, self.n_live))
+                      for t in range(3)]
+        else:
+            self.A = np.zeros((3, self.n_cb, self.n_live))
+            for t in range(3):
+                np.add.at(self.A[t], (rows, cols), vals[:, t])
         self.branch_edge = np.array([r[0] for r in ridx], np.int64)
         self.M = self._loops()
 
@@ -207,31 +228,58 @@ class Circuit:
     def ma(self):
         """M A_t restricted to conductor branches: [3, n_loops, n_live]."""
         Mc = self.M[:, :self.n_cb]
-        return np.stack([Mc @ self.A[t] for t in range(3)])
+        return np.stack([np.asarray(Mc @ self.A[t]) for t in range(3)])
 
-    def potential_part(self, P_live):
+    def potential_part(self, P_live, MA=None):
         """G = sum_t (M A_t) P (M A_t)^T, real and frequency independent."""
-        MA = self.ma()
+        MA = self.ma() if MA is None else MA
         return sum(MA[t] @ P_live @ MA[t].T for t in range(3))
 
-    def loop_matrix(self, f, Gpot):
-        """Z_loop(f) = sum_t (M A_t) diag(Z_s/A) (M A_t)^T + j omega mu0/4pi G."""
-        MA = self.ma()
-        d = self.zs_panels(f)
-        R = sum((MA[t] * d[None, :]) @ MA[t].T for t in range(3))
+    def resistive_parts(self, MA=None):
+        """The resistive part of eq. 8 grouped by material.
+
+        Z_s of eq. 3 depends only on a conductor's (sigma, thickness), so
+        sum_t (M A_t) diag(Z_s/A) (M A_t)^T = sum_m Z_s^m(f) K_m with the
+        frequency-independent K_m = sum_t (M A_t) diag(1/A_l [l in m]) (M A_t)^T
+        over the distinct materials m.  Returns [(sigma, thickness, K_m)]."""
+        MA = self.ma() if MA is None else MA
+        cond = np.asarray(self.mesh.cond)[self.live]
+        sig = np.asarray(self.mesh.sigma, float)[cond]
+        thk = np.asarray(self.mesh.thickness, float)[cond]
+        inv_a = 1.0 / self.geom.area[self.live]
+        out = []
+        for s_, t_ in sorted(set(zip(sig.tolist(), thk.tolist()))):
+            w = np.where((sig == s_) & (thk == t_), inv_a, 0.0)
+            out.append((s_, t_, sum((MA[t] * w[None, :]) @ MA[t].T for t in range(3))))
+        return out
+
+    def loop_matrix(self, f, Gpot, parts=None):
+        """Z_loop(f) = sum_t (M A_t) diag(Z_s/A) (M A_t)^T + j omega mu0/4pi G
+        (parts: resistive_parts(), the same sum grouped by material)."""
+        if parts is None:
+            MA = self.ma()
+            d = self.zs_panels(f)
+            R = sum((MA[t] * d[None, :]) @ MA[t].T for t in range(3))
+        else:
+            R = sum(complex(zs(f, s_, t_)) * K for s_, t_, K in parts)
         return R + 1j * 2 * np.pi * f * MU0_4PI * Gpot
 
     def solve(self, freqs, P_full):
         """Port R, L per frequency by dense direct solve; also loop currents."""
         P_live = P_full[np.ix_(self.live, self.live)]
-        Gpot = self.potential_part(P_live)
+        MA = self.ma()
+        Gpot = self.potential_part(P_live, MA)
+        del P_live
+        parts = self.resistive_parts(MA)
+        del MA
         B = self.port_rhs()
         R = []
         L = []
         X = []
         for f in freqs:
-            Z = self.loop_matrix(f, Gpot)
+            Z = self.loop_matrix(f, Gpot, parts)
             x = np.linalg.solve(Z, B.astype(complex))
+            del Z
             Y = B.T @ x
             Zp = np.linalg.inv(Y)
             R.append(Zp.real)

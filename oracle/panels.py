@@ -242,6 +242,50 @@ def dense_P(G, chunk=200000):
     return P
 
 
+_POOL_G = None
+
+
+def _pool_init(xyz, tri):
+    global _POOL_G
+    _POOL_G = Geometry(xyz, tri)
+
+
+def _pool_rows(args):
+    """Upper-triangle entries P[r, r:] for rows r0..r1-1 of the pool's mesh."""
+    r0, r1 = args
+    N = _POOL_G.n
+    K = np.concatenate([np.full(N - r, r, np.int64) for r in range(r0, r1)])
+    L = np.concatenate([np.arange(r, N, dtype=np.int64) for r in range(r0, r1)])
+    vals = np.empty(K.shape[0])
+    for s in range(0, K.shape[0], 100000):
+        vals[s:s + 100000] = pair_values(_POOL_G, K[s:s + 100000], L[s:s + 100000])
+    return r0, r1, vals
+
+
+def dense_P_parallel(xyz, tri, workers, block=48):
+    """dense_P of a triangle mesh with the upper triangle's rows spread over a
+    pool of `workers` processes (multiprocessing 'spawn', so that it may run
+    next to a CUDA context); every entry is pair_values of its (row, column)
+    pair as in dense_P, and the lower triangle mirrors the upper one."""
+    import multiprocessing as mp
+    tri = np.asarray(tri, np.int64)
+    N = tri.shape[0]
+    P = np.zeros((N, N))
+    tasks = [(r, min(N, r + block)) for r in range(0, N, block)]
+    with mp.get_context("spawn").Pool(workers, initializer=_pool_init, initargs=(xyz, tri)) as pool:
+        for r0, r1, vals in pool.imap_unordered(_pool_rows, tasks, chunksize=1):
+            o = 0
+            for r in range(r0, r1):
+                P[r, r:] = vals[o:o + N - r]
+                o += N - r
+    for r0 in range(0, N, 1024):
+        r1 = min(N, r0 + 1024)
+        blk = P[r0:r1, r0:r1]
+        P[r0:r1, r0:r1] = np.triu(blk) + np.triu(blk, 1).T
+        P[r1:, r0:r1] = P[r0:r1, r1:].T
+    return P
+
+
 def rows_P(G, rows, chunk=200000):
     """Selected rows of P, shape [len(rows), N]."""
     rows = np.asarray(rows, np.int64)
