@@ -1109,7 +1109,9 @@ void fmm_apply(xrl_ctx* c, int nc, const double* X, double* Y, cudaStream_t s) {
 }
 
 // FP64 product with caller-provided expansion buffers (each at least
-// n_boxes * (p+1)^2 * nc doubles); allocates nothing.
+// n_boxes * (p+1)^2 * nc doubles).  Allocates nothing while c->df64_m2l is
+// false (the FP64-accurate residual mode of a mixed solve creates its
+// double-float and integer-slice images on first use) and the profiler is off.
 void fmm_apply_into(xrl_ctx* c, int nc, const double* X, double* Y, double* Mx, double* Lx, cudaStream_t s) {
   fmm_apply_t<double>(c, nc, X, Y, c->d.near_val.p, c->d.mom.p, c->d.t_m2m.p, c->d.t_l2l.p, c->d.t_m2l.p, Mx, Lx,
                       s);

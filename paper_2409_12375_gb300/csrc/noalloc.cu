@@ -1,12 +1,14 @@
 // The FMM product without any device allocation (xrl_fmm_mvm_device_noalloc).
 //
 // Some callers cannot allocate GPU memory at the moment they need a product:
-// code running under CUDA stream capture, latency-critical loops, or hosts
-// whose own allocator owns the device memory.  For them the working buffers
+// a latency-critical loop where a cudaMalloc could stall or fail, or a host
+// framework whose own allocator owns the device memory budget and forbids
+// allocations behind its back.  For them the working buffers
 // of one product live in a fixed, statically declared device array; the
 // setup products of the context (near field, moments, operators, tree) were
 // allocated once by xrl_setup and are only read here.
 #include <mutex>
+#include <new>
 
 #include "xrl_internal.hpp"
 
@@ -36,6 +38,17 @@ void* scratch_address(int device) {
   return g_scratch_addr[device];
 }
 
+// Restores the caller's current device on every exit path.
+struct DeviceGuard {
+  int prev = -1;
+  DeviceGuard() {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 }  // namespace
 
 extern "C" xrl_status xrl_fmm_mvm_device_noalloc(xrl_ctx* c, int32_t nc, const double* dx, double* dy,
@@ -55,6 +68,7 @@ extern "C" xrl_status xrl_fmm_mvm_device_noalloc(xrl_ctx* c, int32_t nc, const d
                "-byte array; use fewer columns or xrl_fmm_mvm_device";
       return XRL_EINVAL;
     }
+    DeviceGuard dg;
     XRL_CUDA(cudaSetDevice(c->device));
     unsigned char* base = static_cast<unsigned char*>(scratch_address(c->device));
     double* X = reinterpret_cast<double*>(base);
@@ -62,25 +76,41 @@ extern "C" xrl_status xrl_fmm_mvm_device_noalloc(xrl_ctx* c, int32_t nc, const d
     double* Mx = reinterpret_cast<double*>(base + 2 * up(n * sizeof(double)));
     double* Lx = reinterpret_cast<double*>(base + 2 * up(n * sizeof(double)) + up(ne * sizeof(double)));
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
-    const bool prof = c->prof.on;   // no event objects are created on this path
+    // The plain FP64 kernels read only setup products.  Two switches of the
+    // context would reach lazily allocated buffers or event objects: the
+    // profiler (events) and the FP64-accurate residual mode of mixed solves
+    // (double-float and integer-slice images); both are held off for the call.
+    const bool prof = c->prof.on, df64 = c->df64_m2l;
     c->prof.on = false;
-    try {
-      xrl::launch_to_morton(c, nc, dx, X, s);
-      xrl::fmm_apply_into(c, nc, X, Y, Mx, Lx, s);
-      xrl::launch_from_morton(c, nc, Y, dy, s);
-      XRL_CUDA(cudaGetLastError());
-    } catch (...) {
-      c->prof.on = prof;
-      throw;
-    }
-    c->prof.on = prof;
+    c->df64_m2l = false;
+    struct Restore {
+      xrl_ctx* c;
+      bool prof, df64;
+      ~Restore() {
+        c->prof.on = prof;
+        c->df64_m2l = df64;
+      }
+    } restore{c, prof, df64};
+    const int64_t peak0 = c->alloc.peak, cur0 = c->alloc.cur;
+    xrl::launch_to_morton(c, nc, dx, X, s);
+    xrl::fmm_apply_into(c, nc, X, Y, Mx, Lx, s);
+    xrl::launch_from_morton(c, nc, Y, dy, s);
+    XRL_CUDA(cudaGetLastError());
+    XRL_CHECK(c->alloc.cur == cur0 && c->alloc.peak == peak0, XRL_ESTATE,
+              "internal: the allocation-free product allocated device memory");
     c->err.clear();
     return XRL_OK;
   } catch (const xrl::Error& e) {
     c->err = e.what();
     return e.code;
+  } catch (const std::bad_alloc&) {
+    c->err = "host allocation failed";
+    return XRL_ENOMEM;
   } catch (const std::exception& e) {
     c->err = e.what();
+    return XRL_EINVAL;
+  } catch (...) {
+    c->err = "unknown error";
     return XRL_EINVAL;
   }
 }
