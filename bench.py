@@ -1,15 +1,23 @@
 #!/usr/bin/env python3
 """Benchmark of the broadband R/L sweep on GB300.
 
-Workload (default): two stacked 4-turn square planar copper coils, about
-25,000 triangles, 2 ports x 32 log-spaced frequencies from 100 Hz to 10 GHz,
-all 64 (frequency, port) systems solved as one multi-RHS block to a relative
-residual of 1e-8.  The FMM's leaf size and order come from the library's
-autotuner (untimed, before the warm-up): the fastest inner product whose FP64
-product stays within 1e-6 of the direct sum.  One STEP = one full sweep (FMM products, preconditioner,
-FGMRES, port reduction to R and L).  The metric is seconds per
-(frequency, port) solve (lower is better); FMM product throughput in
-panel-columns per second is reported beside it.
+Workload (default): two stacked 4-turn square planar copper coils, 24,792
+triangles, 2 ports x 32 log-spaced frequencies from 100 Hz to 10 GHz, all 64
+(frequency, port) systems solved as one multi-RHS block to a relative residual
+of 1e-8.  The FMM's leaf size and order come from the library's autotuner
+(untimed, before the warm-up): the fastest product at the sweep's column
+count whose FP64 product stays within 1e-6 of the direct sum.  One STEP = one
+full sweep (FMM products, preconditioner, FGMRES, port reduction to R and L).
+The metric is seconds per (frequency, port) solve (lower is better); FMM
+product throughput in panel-columns per second is reported beside it.
+
+Arms, each autotuned for its own precision and timed the same way (W warm-up
+sweeps, then K sweeps between CUDA events on the context's stream):
+  chosen      mixed precision (FP32 tensor-core FMM inside FP64 FGMRES-IR)
+  fp64_tc     FP64-accurate products throughout on the tensor cores and FP32
+              pipes (integer-slice M2L/M2M/near field, double-float P2M/L2P),
+              no FP32 inner iterations
+  plain_fp64  FP64 CUDA-core kernels throughout
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
                   [--no-autotune --fmm-order P --leaf-target L]
@@ -124,8 +132,8 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-# ---------------------------------------------------------------- CPU oracle sample
-def oracle_sample(m, budget_rows=24):
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(m, n_loops, budget_rows=24):
     """Time the CPU oracle on a bounded sample of this workload and scale it to
     seconds per (frequency, port) solve of the full workload.
 
@@ -134,7 +142,9 @@ def oracle_sample(m, budget_rows=24):
     solve of the n_loops x n_loops loop system per frequency.  Sample: P rows
     for `budget_rows` random panels with the oracle's own rule table, and the
     oracle's two library primitives (np.matmul real, np.linalg.solve complex)
-    at n = 2048; each measured rate is scaled to the full sizes."""
+    at n = 2048; each measured rate is scaled to the full sizes.  n_loops is
+    the loop count of this mesh (the cycle-space dimension, the same for the
+    oracle's fundamental cycles and the library's basis)."""
     from oracle import panels
     G = panels.Geometry(m.xyz, m.tri)
     N = G.n
@@ -155,11 +165,11 @@ def oracle_sample(m, budget_rows=24):
     np.linalg.solve(z, bb)
     lu_time = time.perf_counter() - t0
     n_live = int(np.sum(np.asarray(m.term) < 0))
-    n_loops = n_live // 2   # closed surfaces: loops ~ vertices ~ panels / 2
     n_f = len(m.freqs)
     n_p = len(m.ports)
     t_P = t_entry * N * N / 2.0
-    t_G = 3 * (2.0 * n_loops * n_live * n_live + 2.0 * n_loops * n_loops * n_live) / gemm_rate
+    # G and the per-material resistive matrix: 3 x (MA P, (MA P) MA^T, (MA w) MA^T)
+    t_G = 3 * (2.0 * n_loops * n_live * n_live + 4.0 * n_loops * n_loops * n_live) / gemm_rate
     t_LU = n_f * lu_time * (n_loops / n) ** 3
     total = t_P + t_G + t_LU
     return {"value": total / (n_f * n_p), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -168,7 +178,38 @@ def oracle_sample(m, budget_rows=24):
                        "scaled to n_loops=%d, %d frequencies; estimated full oracle solve %.0f s "
                        "(P %.0f s, G %.0f s, LU %.0f s)" % (budget_rows, t_rows, t_entry, N * N / 2.0,
                                                           n_loops, n_f, total, t_P, t_G, t_LU)),
-            "measured_s": t_rows + lu_time}
+            "measured_s": t_rows + lu_time, "estimated_total_s": total}
+
+
+def oracle_c1_full():
+    """The full oracle on the small case (the 2,100-triangle bar, 1 port, 4
+    frequencies) timed for real: P by the rule table over every host core
+    (process pool), the fundamental-cycle loop system and its dense solves."""
+    import meshgen
+    from oracle import circuit, panels
+    m = meshgen.bar()
+    w = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    P = panels.dense_P_parallel(m.xyz, m.tri, w)
+    t1 = time.perf_counter()
+    circuit.Circuit(m).solve(m.freqs, P)
+    t2 = time.perf_counter()
+    return {"workload": "bar 1x1x10 mm, %d triangles, 1 port x %d freqs" % (m.n_tri, len(m.freqs)),
+            "s_per_freq_port": (t2 - t0) / len(m.freqs), "total_s": t2 - t0, "P_s": t1 - t0,
+            "solve_s": t2 - t1, "cores": w}
+
+
+def oracle_c2_recorded():
+    """The full oracle's time on the benchmark's coils, measured once by
+    tests/golden/make_coils_rl.py (its host is named in the record)."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "coils_rl_c2.json")) as f:
+            g = json.load(f)
+    except Exception:
+        return None
+    nsys = len(g["freqs_hz"]) * g["n_ports"]
+    return {"s_per_freq_port": g["oracle_seconds"]["total"] / nsys, "total_s": g["oracle_seconds"]["total"],
+            "host": g["host"], "command": g["command"]}
 
 
 # ---------------------------------------------------------------- peaks
@@ -182,27 +223,43 @@ def peaks():
     sm_max = float(p.get("sm_max_mhz", 2070.0))
     return {
         "hbm_gbs": float(p.get("hbm_gbs", 6800.0)),
-        "hbm_src": "measured" if "hbm_gbs" in p else "fallback",
-        # SIMT peaks from unit counts and the maximum SM clock: 152 SMs x 128
-        # FP32 lanes x 2 flops; FP64 at the nominal GB300 rate
+        "hbm_src": "measured (MEASURED_PEAKS.json)" if "hbm_gbs" in p else "fallback",
+        # FP32 SIMT peak from unit counts and the maximum SM clock: 152 SMs x
+        # 128 FP32 lanes x 2 flops
         "fp32_tflops": 152 * 128 * 2 * sm_max * 1e6 / 1e12,
-        "fp64_tflops": 1.25,
         "bf16_sust": float(p.get("bf16_tflops_sustained", 1700.0)),
+        "bf16_src": "measured bf16 sustained (MEASURED_PEAKS.json)" if "bf16_tflops_sustained" in p
+        else "fallback",
     }
 
 
+def measure_fp64_peak():
+    """FP64 rate of this GPU, measured: the best of 5 cuBLAS DGEMMs (torch.matmul,
+    float64, 8192^3) timed with CUDA events."""
+    import torch
+    n = 8192
+    a = torch.randn(n, n, device="cuda", dtype=torch.float64)
+    b = torch.randn(n, n, device="cuda", dtype=torch.float64)
+    c = a @ b
+    best = None
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b, c
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
 # ---------------------------------------------------------------- rooflines
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu capture of the unchanged kernel on this workload's launch
-# configuration (profiles/top_kernels_coil_sweep.md); None where none exists
-# ncu DRAM bytes (read + write) per launch of the dominant kernels, captured at
-# order 7, leaf target 32, 384 columns on the coils (profiles/top_kernels_coil_sweep.md);
-# reported only when the bench runs that configuration
-NCU_TRAFFIC_CFG = (7, 32)
-NCU_TRAFFIC = {"m2l": 84.400128e6 + 31.16032e6,        # k_xlate_tc2<0>, order 7, 384 columns
-               "p2p": 437.365248e6 + 33.278464e6,      # k_xlate_tc2<1>
-               "m2l64": 232.165888e6 + 85.900032e6,    # k_xlate_oz<64>
-               "p2p64": 750.134272e6 + 82.493184e6}    # k_xlate_oz<96> (near field)
+# ncu DRAM bytes (read + write) per launch of the dominant kernels at one
+# configuration of this workload: (order, leaf target, targets per CTA, columns)
+# -> {phase: bytes}.  Reported only when the bench runs that configuration.
+NCU_TRAFFIC = {}
 
 
 def phase_kernel(name, p):
@@ -223,15 +280,17 @@ def phase_kernel(name, p):
         "l2l": "k_m2l_tiled<%d,1> list form + k_m2l_df64<1> (residuals)" % ((np_ + 15) // 16)}.get(name, name)
 
 
-def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0, leaf=32):
-    """Roofline entry of one profiling phase: algorithmic flops (or bytes) per
+def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0, traffic=None):
+    """Roofline entry of one profiling phase: ALGORITHMIC flops (or bytes) per
     launch over the phase's CUDA-event time per launch, against the peak of the
-    unit that executes it."""
+    unit that executes them.  For the tensor-core phases the FP32 (or
+    FP64-accurate) contraction runs as several BF16 products; the rate of
+    those issued products is reported beside it, not as `achieved`."""
     avg_ms = d["ms"] / max(1, d["launches"])
     mixed = precision == "mixed"
     alg = d["flops"] / (d["ms"] * 1e-3) / 1e12          # algorithmic TFLOP/s
     out = {"kernel": phase_kernel(name, p), "avg_launch_ms": avg_ms, "launches": d["launches"],
-           "traffic": NCU_TRAFFIC.get(name) if mixed and (p, leaf) == NCU_TRAFFIC_CFG and nc == 384 else None}
+           "traffic": traffic.get(name) if traffic else None}
     ncoef = (p + 1) ** 2
     pad = lambda v: (v + 15) // 16 * 16
     tile_pad = (pad(ncoef) * pad(ncoef)) / float(ncoef * ncoef) * (128 * ((nc + 127) // 128)) / float(nc)
@@ -240,17 +299,12 @@ def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0, leaf=32):
         products = 6 if name in ("m2l", "p2p") else 15
         padf = tile_pad if name.startswith("m2l") else near_pad * col_pad
         issued = alg * products * padf                    # BF16 MMA TFLOP/s actually issued
-        out.update({"bound": "tensor", "achieved": issued, "peak": pk["bf16_sust"], "unit": "TFLOP/s",
-                    "frac": issued / pk["bf16_sust"], "algorithmic_tflops": alg,
-                    "peak_src": "measured bf16 sustained (MEASURED_PEAKS.json)",
-                    "note": "achieved = %d BF16 products x padding %.3f x algorithmic FP%s flops"
-                            % (products, padf, "32" if name in ("m2l", "p2p") else "64")})
-    elif mixed and name == "p2p64":
-        ops = alg * 11.0 / 2.0                            # ~11 FP32 operations per double-float multiply-add
-        out.update({"bound": "alu", "achieved": ops, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
-                    "frac": ops / pk["fp32_tflops"], "algorithmic_tflops": alg,
-                    "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                    "note": "achieved = FP32 operations/s, 11 per FP64-accurate multiply-add"})
+        out.update({"bound": "tensor", "achieved": alg, "peak": pk["bf16_sust"], "unit": "TFLOP/s",
+                    "frac": alg / pk["bf16_sust"], "peak_src": pk["bf16_src"],
+                    "issued_bf16_tflops": issued, "issued_frac": issued / pk["bf16_sust"],
+                    "note": "achieved = algorithmic FP%s flops/s; the tensor pipe issues %d BF16 products x "
+                            "padding %.3f per algorithmic flop" % ("32" if name in ("m2l", "p2p") else "64",
+                                                                   products, padf)})
     elif name in ("precond", "operator"):
         gbs = d["bytes"] / (d["ms"] * 1e-3) / 1e9
         out.update({"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -260,26 +314,86 @@ def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0, leaf=32):
     else:
         fp64 = not mixed or name.endswith("64")
         peak = pk["fp64_tflops"] if fp64 else pk["fp32_tflops"]
+        if mixed and fp64:
+            # FP64-accurate work on the FP32 pipes (double-float): ~11 FP32 operations per multiply-add
+            peak = pk["fp32_tflops"] * 2.0 / 11.0
+            src = "derived: FP32 SIMT peak x 2/11 (double-float multiply-add on the FP32 pipes)"
+        else:
+            src = pk["fp64_src"] if fp64 else "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
         out.update({"bound": "alu", "achieved": alg, "peak": peak, "unit": "TFLOP/s", "frac": alg / peak,
-                    "peak_src": "nominal GB300 FP64 (1.25 TFLOP/s)" if fp64 else
-                    "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"})
+                    "peak_src": src})
     return out
 
 
+def product_roofline(flops, byts, ms, pk):
+    """FP64 product: algorithmic flops and bytes over its event time, against
+    the measured FP64 rate and HBM bandwidth; `frac` is that of the binding one
+    (the larger of the two lower bounds on the time)."""
+    tf = flops / (ms * 1e-3) / 1e12
+    gbs = byts / (ms * 1e-3) / 1e9
+    ff, fb = tf / pk["fp64_tflops"], gbs / pk["hbm_gbs"]
+    return {"achieved_tflops": tf, "peak_tflops": pk["fp64_tflops"], "flop_frac": ff,
+            "achieved_gbs": gbs, "peak_gbs": pk["hbm_gbs"], "hbm_frac": fb,
+            "bound": "fp64" if ff >= fb else "hbm", "frac": max(ff, fb), "ms": ms,
+            "algorithmic_gflop": flops / 1e9, "algorithmic_gb": byts / 1e9, "peak_src": pk["fp64_src"]}
+
+
 # ---------------------------------------------------------------- reference arm
+def loop_count(m):
+    """Dimension of the loop space of a mesh's PEEC graph (branches - nodes +
+    connected components): nodes are the live panels and one node per
+    terminal, branches the edges between two live panels, the rim edges from
+    a live panel to a terminal, and one external branch per port."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    tri = np.asarray(m.tri)
+    term = np.asarray(m.term)
+    e, own = [], []
+    for k in range(tri.shape[1]):
+        a_ = tri[:, k]
+        b_ = tri[:, (k + 1) % tri.shape[1]]
+        if tri.shape[1] == 4:      # hybrid panels: a triangle's 4th slot is -1
+            b_ = np.where(b_ < 0, tri[:, 0], b_)
+            ok = a_ >= 0
+        else:
+            ok = np.ones(tri.shape[0], bool)
+        e.append(np.sort(np.stack([a_[ok], b_[ok]], 1), axis=1))
+        own.append(np.flatnonzero(ok))
+    e = np.vstack(e)
+    own = np.concatenate(own)
+    _, inv = np.unique(e, axis=0, return_inverse=True)
+    order = np.argsort(inv.ravel(), kind="stable")
+    pan = own[order].reshape(-1, 2)
+    n_live = int(np.sum(term < 0))
+    n_term = int(term.max()) + 1 if term.max() >= 0 else 0
+    node = np.full(tri.shape[0], -1)
+    node[term < 0] = np.arange(n_live)
+    node[term >= 0] = n_live + term[term >= 0]
+    tp, tq = term[pan[:, 0]], term[pan[:, 1]]
+    keep = (tp < 0) | (tq < 0)
+    u = np.concatenate([node[pan[keep, 0]], [n_live + s_ for s_, _ in m.ports]])
+    v = np.concatenate([node[pan[keep, 1]], [n_live + k_ for _, k_ in m.ports]])
+    nn = n_live + n_term
+    g = coo_matrix((np.ones(u.shape[0]), (u, v)), shape=(nn, nn))
+    ncomp = connected_components(g, directed=False)[0]
+    return int(u.shape[0] - nn + ncomp)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     m = workload(0, 1)
+    n_loops = loop_count(m)
     t0 = time.perf_counter()
     samples = []
     for _ in range(max(1, args.steps)):
-        samples.append(oracle_sample(m, budget_rows=8))
+        samples.append(oracle_sample(m, n_loops, budget_rows=8))
     wall = time.perf_counter() - t0
-    v = float(np.median([s["value"] for s in samples]))
+    v = float(np.median([s_["value"] for s_ in samples]))
     cb = dict(samples[-1])
     cb["value"] = v
+    cb["c2_full_oracle_recorded"] = oracle_c2_recorded()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -322,18 +436,126 @@ def kernel_case(args):
 
 
 # ---------------------------------------------------------------- our arm
+PREC = {"fp64": 0, "mixed": 1, "fp64_tc": 2}
+
+
+def make_ctx(pkg, m, opts, precision, autotune, nsys):
+    """Context for one arm; autotuned for its own precision unless disabled."""
+    x = pkg.XRL.from_mesh(m, **dict(opts, precision=PREC[precision]))
+    tuned = None
+    if autotune:
+        leaf, order, ms, err = x.autotune(6 * nsys, 1e-6, PREC[precision])
+        tuned = {"leaf_target": leaf, "fmm_order": order, "product_ms": ms, "product_err": err,
+                 "tc_targets_per_cta": x.stats()["tc_targets_per_cta"]}
+    return x, tuned
+
+
+def time_sweeps(x, freqs, warmup, steps, clocks=None, barrier=lambda: None):
+    """W untimed sweeps, then K sweeps between CUDA events on the context's
+    stream (device time) and host clocks around each call (end to end: host
+    frequencies in, host R and L out)."""
+    import torch
+    ext = torch.cuda.ExternalStream(x.stream_handle())
+    for _ in range(warmup):
+        x.solve(freqs)
+    barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    l0 = x.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    host = []
+    e0.record(ext)
+    R = L = None
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        R, L = x.solve(freqs)
+        host.append(time.perf_counter() - t0)
+    e1.record(ext)
+    torch.cuda.synchronize()
+    barrier()
+    st = x.stats()
+    return {"dev_ms": e0.elapsed_time(e1), "host_s": float(np.sum(host)), "R": R, "L": L,
+            "launches": x.kernel_launches() - l0, "iters": st["total_iters"], "res": st["max_rel_res"]}
+
+
+def rl_diff(R, L, Rr, Lr):
+    """Per frequency: max |a - b| over the port matrix / max |b|; worst frequency."""
+    nf = R.shape[0]
+    eR = np.max(np.abs(R - Rr).reshape(nf, -1).max(1) / np.abs(Rr).reshape(nf, -1).max(1))
+    eL = np.max(np.abs(L - Lr).reshape(nf, -1).max(1) / np.abs(Lr).reshape(nf, -1).max(1))
+    return float(eR), float(eL)
+
+
+def oracle_rl_error(m, R, L):
+    """Element-wise relative error of R11, R22, L11, L22, L12 against the dense
+    FP64 oracle of the coils (tests/golden/coils_rl_c2.json), worst over the sweep."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "coils_rl_c2.json")) as f:
+            g = json.load(f)
+    except Exception:
+        return None
+    if g["n_panels"] != m.n_tri or len(g["freqs_hz"]) != len(m.freqs) or \
+            not np.allclose(g["freqs_hz"], m.freqs, rtol=1e-12, atol=0):
+        return None
+    Ro, Lo = np.asarray(g["R"]), np.asarray(g["L"])
+    out = {}
+    for name, a, b in (("R11", R[:, 0, 0], Ro[:, 0, 0]), ("R22", R[:, 1, 1], Ro[:, 1, 1]),
+                       ("L11", L[:, 0, 0], Lo[:, 0, 0]), ("L22", L[:, 1, 1], Lo[:, 1, 1]),
+                       ("L12", L[:, 0, 1], Lo[:, 0, 1])):
+        out[name] = float(np.max(np.abs(a - b) / np.abs(b)))
+    return out
+
+
+def fp64_products(pkg, x, m, pk, ext):
+    """The raw FP64 product (xrl_fmm_mvm_device) at 1, 6 and 384 columns:
+    panel-columns/s from CUDA events over repeated products, and its roofline
+    from the library's algorithmic flops and bytes (profiler counters of one
+    product)."""
+    import torch
+    out = {}
+    for nc in (1, 6, 384):
+        xv = torch.randn(nc, m.n_tri, device="cuda", dtype=torch.float64)
+        yv = torch.empty_like(xv)
+        x.reset_profile()
+        x.set_profiling(True)
+        x.fmm_mvm_device(xv, yv)
+        torch.cuda.synchronize()
+        prof = x.profile()
+        x.set_profiling(False)
+        flops = sum(v["flops"] for v in prof.values())
+        byts = sum(v["bytes"] for v in prof.values())
+        x.fmm_mvm_device(xv, yv)
+        torch.cuda.synchronize()
+        a_ = torch.cuda.Event(enable_timing=True)
+        b_ = torch.cuda.Event(enable_timing=True)
+        reps = 3 if nc == 384 else 20
+        a_.record(ext)
+        for _ in range(reps):
+            x.fmm_mvm_device(xv, yv)
+        b_.record(ext)
+        torch.cuda.synchronize()
+        ms = a_.elapsed_time(b_) / reps
+        out["nc%d" % nc] = dict(product_roofline(flops, byts, ms, pk), panel_cols_per_s=m.n_tri * nc / (ms * 1e-3))
+        del xv, yv
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.kernel_case:
         return kernel_case(args)
-    import torch
-    import torch.distributed as dist
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    c1_oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        c1_oracle = oracle_c1_full()          # process pool started before the first GPU call
+    import torch
+    import torch.distributed as dist
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -344,40 +566,16 @@ def main():
             dist.barrier()
 
     m = workload(rank, world)
-    opts = dict(fmm_order=args.fmm_order, separation=2, leaf_target=args.leaf_target, device=local,
-                precision=1 if args.precision == "mixed" else 0)
-    x = pkg.XRL.from_mesh(m, **opts)
-    tuned = None
-    if not args.no_autotune:
-        leaf, order, ms, err = x.autotune(6 * len(m.freqs) * len(m.ports), 1e-6, opts["precision"])
-        opts["leaf_target"], opts["fmm_order"] = leaf, order
-        tuned = {"leaf_target": leaf, "fmm_order": order, "product_ms": ms, "product_err": err,
-                 "tc_targets_per_cta": x.stats()["tc_targets_per_cta"]}
-    st = x.stats()
-    ext = torch.cuda.ExternalStream(x.stream_handle())
     nsys = len(m.freqs) * len(m.ports)
-    for _ in range(args.warmup):
-        x.solve(m.freqs)
-    # ---- timed region
-    barrier()
-    torch.cuda.synchronize()
+    opts = dict(fmm_order=args.fmm_order, separation=2, leaf_target=args.leaf_target, device=local)
+    x, tuned = make_ctx(pkg, m, opts, args.precision, not args.no_autotune, nsys)
+    st = x.stats()
+    cfg_opts = dict(opts, fmm_order=x.opts.fmm_order, leaf_target=x.opts.leaf_target)
+    # ---- timed region (chosen arm)
     clocks = Clocks()
-    clocks.start()
-    l0 = x.kernel_launches()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    host = []
-    e0.record(ext)
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        R, L = x.solve(m.freqs)          # host freq in, host R/L out
-        host.append(time.perf_counter() - t0)
-    e1.record(ext)
-    torch.cuda.synchronize()
-    barrier()
-    dev_ms = e0.elapsed_time(e1)
-    launches = x.kernel_launches() - l0
+    tm = time_sweeps(x, m.freqs, args.warmup, args.steps, clocks, barrier)
     ck = clocks.stop(local)
+    R, L = tm["R"], tm["L"]
     # phase breakdown: the same K sweeps again with the phase profiler on (CUDA
     # events per phase on the library's stream; the near field then runs in
     # sequence with the far field instead of beside it, so each phase is timed alone)
@@ -388,9 +586,7 @@ def main():
     torch.cuda.synchronize()
     prof = x.profile()
     x.set_profiling(False)
-    iters = x.stats()["total_iters"]
-    res = x.stats()["max_rel_res"]
-    t_dev = torch.tensor([dev_ms, float(np.sum(host))], device="cuda", dtype=torch.float64)
+    t_dev = torch.tensor([tm["dev_ms"], tm["host_s"]], device="cuda", dtype=torch.float64)
     if world > 1:
         dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
     dev_ms, host_s = float(t_dev[0]), float(t_dev[1])
@@ -400,57 +596,48 @@ def main():
 
     # roofline of every major phase; "roofline" is the dominant one
     pk = peaks()
+    pk["fp64_tflops"] = measure_fp64_peak()
+    pk["fp64_src"] = "measured: cuBLAS DGEMM 8192^3 (torch.matmul float64), best of 5, CUDA events"
     near_pad = st["near_nnz_padded"] / float(st["near_nnz"]) if st.get("near_nnz_padded") else 0.0
-    roofs = {k: phase_roofline(k, prof[k], pk, args.precision, opts["fmm_order"], 6 * nsys, near_pad,
-                               opts["leaf_target"])
+    key = (cfg_opts["fmm_order"], cfg_opts["leaf_target"], x.stats()["tc_targets_per_cta"], 6 * nsys)
+    traffic = NCU_TRAFFIC.get(key) if args.precision == "mixed" else None
+    roofs = {k: phase_roofline(k, prof[k], pk, args.precision, cfg_opts["fmm_order"], 6 * nsys, near_pad, traffic)
              for k in ("p2p", "m2l", "p2p64", "m2l64", "precond", "operator", "p2m", "l2p", "m2m", "l2l")
              if k in prof and prof[k]["ms"] > 0}
     dom = max(roofs, key=lambda k: prof[k]["ms"])
     roof = roofs[dom]
 
-    # FMM product throughput (FP64 entry point, device buffers), panel-columns/s
-    mvm = {}
-    for nc in (1, 6, 384):
-        xv = torch.randn(nc, m.n_tri, device="cuda", dtype=torch.float64)
-        yv = torch.empty_like(xv)
-        x.fmm_mvm_device(xv, yv)
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        reps = 3 if nc == 384 else 10
-        a.record(ext)
-        for _ in range(reps):
-            x.fmm_mvm_device(xv, yv)
-        b.record(ext)
-        torch.cuda.synchronize()
-        mvm["fp64_nc%d" % nc] = m.n_tri * nc * reps / (a.elapsed_time(b) * 1e-3)
-        del xv, yv
+    # the raw FP64 product (the paper's fmm_mvm) at 1, 6 and 384 columns
+    ext = torch.cuda.ExternalStream(x.stream_handle())
+    mvm = fp64_products(pkg, x, m, pk, ext)
 
-    plain = None
-    if not args.no_plain and args.precision == "mixed":
-        xp = pkg.XRL.from_mesh(m, **dict(opts, precision=0))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Rp, Lp = xp.solve(m.freqs)
-        tp = time.perf_counter() - t0
-        # per frequency: max |chosen - plain| over the port matrix / max |plain|
-        eR = np.max(np.abs(R - Rp).reshape(len(m.freqs), -1).max(1) / np.abs(Rp).reshape(len(m.freqs), -1).max(1))
-        eL = np.max(np.abs(L - Lp).reshape(len(m.freqs), -1).max(1) / np.abs(Lp).reshape(len(m.freqs), -1).max(1))
-        plain = {"s_per_freq_port": tp / nsys, "iters": xp.stats()["total_iters"],
-                 "speedup_chosen_vs_plain": (tp / nsys) / value,
-                 "rel_err_R_chosen_vs_plain": float(eR), "rel_err_L_chosen_vs_plain": float(eL)}
-        xp.close()
+    # comparison arms, each autotuned for its own precision, timed like the chosen arm
+    arms = {}
+    if world == 1 and not args.no_plain and args.precision == "mixed":
+        for name in ("fp64_tc", "fp64"):
+            xa, ta = make_ctx(pkg, m, opts, name, not args.no_autotune, nsys)
+            ra = time_sweeps(xa, m.freqs, args.warmup, args.steps)
+            spf = ra["dev_ms"] / 1e3 / (args.steps * nsys)
+            eR, eL = rl_diff(R, L, ra["R"], ra["L"])
+            arms["plain_fp64" if name == "fp64" else name] = {
+                "s_per_freq_port": spf, "e2e_s_per_freq_port": ra["host_s"] / (args.steps * nsys),
+                "fgmres_iters": ra["iters"], "max_rel_residual": ra["res"], "autotune": ta,
+                "speedup_chosen_vs_this": spf / value,
+                "rel_err_R_chosen_vs_this": eR, "rel_err_L_chosen_vs_this": eL,
+                "oracle_rl_error": oracle_rl_error(m, ra["R"], ra["L"])}
+            xa.close()
 
     # preconditioner comparison outside the timed region (Sec. II-D, Table IV): the same sweep with
     # the diagonal-of-P (eq. 10) and the diagonal-of-L preconditioners at the table's tolerance 1e-6
     # and at the bench's 1e-8; setup = the pencil build (P entries, pattern, band ordering)
     abl = None
+    po = dict(cfg_opts, precision=PREC[args.precision])
     if not args.no_ablation and world == 1:
         abl = {}
         for tol in (1e-6, 1e-8):
             row = {}
             for name, pc in (("diag_P", 1), ("diag_L", 3)):
-                xa = pkg.XRL.from_mesh(m, **dict(opts, precond=pc, tol=tol))
+                xa = pkg.XRL.from_mesh(m, **dict(po, precond=pc, tol=tol))
                 sa = xa.stats()
                 try:
                     xa.solve(m.freqs)
@@ -478,36 +665,40 @@ def main():
         import meshgen
         mh = meshgen.coils(rect=True)
         mh.freqs = m.freqs
-        xh = pkg.XRL.from_mesh(mh, **opts)
+        xh = pkg.XRL.from_mesh(mh, **po)
         xh.solve(mh.freqs)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Rh, Lh = xh.solve(mh.freqs)
         th = time.perf_counter() - t0
         sh = xh.stats()
-        nf = len(m.freqs)
-        dR = np.max(np.abs(Rh - R).reshape(nf, -1).max(1) / np.abs(R).reshape(nf, -1).max(1))
-        dL = np.max(np.abs(Lh - L).reshape(nf, -1).max(1) / np.abs(L).reshape(nf, -1).max(1))
+        dR, dL = rl_diff(Rh, Lh, R, L)
         hyb = {"n_panels": sh["n_panels"], "n_rectangles": int(np.sum(mh.tri[:, 3] >= 0)), "n_loops": sh["n_loops"],
                "fgmres_iters": sh["total_iters"], "s_per_freq_port": th / nsys,
-               "rel_diff_R_vs_triangles": float(dR), "rel_diff_L_vs_triangles": float(dL)}
+               "rel_diff_R_vs_triangles": dR, "rel_diff_L_vs_triangles": dL}
         xh.close()
 
     if rank == 0:
         cb = None
         if world == 1 and not args.no_cpu_baseline:
-            cb = oracle_sample(m)
+            cb = oracle_sample(m, st["n_loops"])
+            cb["c1_full_oracle"] = c1_oracle
+            cb["c2_full_oracle_recorded"] = oracle_c2_recorded()
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32/f64 mixed (FP32 FMM in FP64 FGMRES-IR)" if args.precision == "mixed" else "f64",
-                "data": "synthetic", "config": dict(config_dict(m, args.precision, opts), autotune=tuned),
+                "data": "synthetic", "config": dict(config_dict(m, args.precision, cfg_opts), autotune=tuned),
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * len(m.freqs),
-                        "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * 4},
-                "gpu_launches": launches, "clocks": ck, "roofline": roof, "roofline_phases": roofs, "cpu_baseline": cb,
-                "fmm_mvm_panel_cols_per_s": mvm, "plain_fp64": plain, "precond_ablation": abl, "hybrid_panels": hyb,
-                "solve": {"fgmres_iters": iters, "max_rel_residual": res, "setup_ms": st["setup_ms"],
-                          "n_loops": st["n_loops"], "peak_device_bytes": x.stats()["peak_device_bytes"]},
+                        "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * len(m.ports) ** 2},
+                "gpu_launches": tm["launches"], "clocks": ck, "roofline": roof, "roofline_phases": roofs,
+                "cpu_baseline": cb, "fmm_mvm_fp64": mvm, "arms": arms,
+                "oracle_rl_error": oracle_rl_error(m, R, L),
+                "precond_ablation": abl, "hybrid_panels": hyb,
+                "solve": {"fgmres_iters": tm["iters"], "max_rel_residual": tm["res"], "setup_ms": st["setup_ms"],
+                          "n_loops": st["n_loops"], "near_nnz": st["near_nnz"],
+                          "near_per_panel": st["near_nnz"] / float(st["n_panels"]),
+                          "peak_device_bytes": x.stats()["peak_device_bytes"]},
                 "phases_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
         print(json.dumps(line))
     x.close()

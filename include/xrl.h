@@ -53,7 +53,10 @@ typedef struct {
   int32_t leaf_target; /* mean panels per non-empty leaf used to pick the tree depth, default 32
                           (the depth is also capped so that leaf sides are >= 2x the largest
                           panel radius) */
-  int32_t precision;   /* 0: FP64 everywhere; 1: mixed (FP32 FMM/near field inside FP64 refinement) */
+  int32_t precision;   /* 0: FP64 everywhere (CUDA-core FP64 kernels); 1: mixed (FP32 FMM/near field
+                          inside FP64 refinement); 2: FP64-accurate products throughout on the tensor
+                          cores and FP32 pipes (the integer-slice and double-float kernels of mode 1's
+                          residuals), no FP32 inner iterations */
   int32_t precond;     /* 0: none; 1: diagonal-of-P preconditioner of eq. 10 applied exactly (banded
                           LDL^T of the RCM-ordered vertex loops + Schur border; falls back to 2 when
                           the band is not usable); 2: eq. 10 applied inexactly by Jacobi-preconditioned
@@ -154,23 +157,24 @@ xrl_status xrl_fmm_mvm_device(xrl_ctx* ctx, int32_t n_cols, const double* d_x, d
 xrl_status xrl_fmm_mvm32_device(xrl_ctx* ctx, int32_t n_cols, const float* d_x, float* d_y, void* stream);
 
 /* Same product as xrl_fmm_mvm_device, for callers that must not allocate GPU
- * memory: code running while a CUDA stream is being captured into a graph,
- * a real-time loop where a cudaMalloc could stall or fail, or a host
+ * memory: a real-time loop where a cudaMalloc could stall or fail, or a host
  * framework whose own allocator owns the device memory budget.  This call
  * allocates nothing: its working buffers (the Morton-ordered copies of x and
  * y and the multipole/local expansions, 2 N n_cols + 2 n_boxes (p+1)^2 n_cols
  * doubles) live in one fixed device array of XRL_NOALLOC_SCRATCH_BYTES
  * (32 MiB) that the library declares statically; every GPU the library is
  * loaded on holds that array until the process exits.  Sizes that do not
- * fit return XRL_EINVAL (nothing is launched).  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress, no
- * allocation), so make that first call before capturing a stream.  All
- * calls share the one array: two calls whose work overlaps on the GPU
- * (different streams, or different contexts on the same device) race and
- * corrupt each other's results, so serialise them.  The array keeps the
- * last call's contents; nothing in it needs to start at zero.  Profiling
- * (xrl_set_profiling) is not recorded for this call.  The paper has no
- * counterpart: this is an interface variant only.  d_x and d_y as for
+ * fit return XRL_EINVAL (nothing is launched).  It always runs the plain
+ * FP64 kernels (also in a precision = 1 context), which read only what
+ * xrl_setup built.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress, no allocation), so make that first
+ * call before any stream capture.  All calls share the one array: two calls
+ * whose work overlaps on the GPU (different streams, or different contexts
+ * on the same device) race and corrupt each other's results, so serialise
+ * them.  The array keeps the last call's contents; nothing in it needs to
+ * start at zero.  Profiling (xrl_set_profiling) is not recorded for this
+ * call.  The caller's current device is restored on return.  The paper has
+ * no counterpart: this is an interface variant only.  d_x and d_y as for
  * xrl_fmm_mvm_device. */
 #define XRL_NOALLOC_SCRATCH_BYTES (32u << 20)
 xrl_status xrl_fmm_mvm_device_noalloc(xrl_ctx* ctx, int32_t n_cols, const double* d_x, double* d_y,
@@ -201,17 +205,19 @@ typedef struct {
                                  1: one each), as xrl_autotune chose it; 2 before any autotune */
 } xrl_stats;
 
-/* FMM autotuner: tries leaf_target in {16, 32, 64} x fmm_order in {6, 7, 8}
+/* FMM autotuner: tries leaf_target in {16, 32, 64} x fmm_order in {4, 6, 7, 8}
  * (separation 2), re-running xrl_setup for each.  A candidate is admissible
  * when its FP64 product matches the FP64 direct sum (xrl_direct_mvm_device) on
- * two seeded random columns to mvm_tol (relative 2-norm).  Among admissible
- * candidates, the one with the fastest product at n_cols columns is kept,
- * timed with CUDA events in the precision the solver's inner iterations use
- * (FP32 if `precision` = 1, else FP64); in FP32 each candidate is timed with
- * one and with two sibling targets per tensor-core CTA and keeps the faster
- * (xrl_stats.tc_targets_per_cta).  The context ends set up with it, and its
- * options are updated.  Outputs (host, may be NULL): the chosen
- * leaf_target, fmm_order, its product time in ms, and its error.
+ * two seeded random columns to mvm_tol (relative 2-norm).  Each admissible
+ * candidate's product at n_cols columns is timed with CUDA events in the
+ * precision the solver's products use (FP32 if `precision` = 1, the
+ * FP64-accurate tensor-core product if 2, else FP64); in FP32 each candidate
+ * is timed with one and with two sibling targets per tensor-core CTA and
+ * keeps the faster (xrl_stats.tc_targets_per_cta).  Among the candidates
+ * within 3% of the fastest time, the one with the smallest product error is
+ * kept (so that timing noise does not flip the choice).  The context ends set
+ * up with it, and its options are updated.  Outputs (host, may be NULL): the
+ * chosen leaf_target, fmm_order, its product time in ms, and its error.
  * XRL_ENOCONV if no candidate meets mvm_tol (the context is left set up with
  * the most accurate one). */
 xrl_status xrl_autotune(xrl_ctx* ctx, int32_t n_cols, double mvm_tol, int32_t precision, int32_t* leaf_target,

@@ -851,13 +851,15 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
   wk.thr.alloc(c->alloc, nsys);
   const bool mixed = c->opt.precision == 1;
   const double tau = mixed ? 1e-5 : 0.0;
-  // refinement residuals of the mixed mode: FP64-accurate M2L on the FP32 pipes
+  // FP64-accurate products on the tensor cores (integer slices) and FP32 pipes
+  // (double-float): the refinement residuals of the mixed mode, and every
+  // product of precision 2
   struct Df64Guard {
     xrl_ctx* c;
     bool old;
     ~Df64Guard() { c->df64_m2l = old; }
   } df64_guard{c, c->df64_m2l};
-  c->df64_m2l = mixed;
+  c->df64_m2l = c->opt.precision >= 1;
   wk.resid.alloc(c->alloc, nsys);
   wk.active.alloc(c->alloc, nsys);
   wk.iters.alloc(c->alloc, nsys);
@@ -1077,7 +1079,7 @@ void apply_operator_host(xrl_ctx* c, int nsys, const double* freq, const double*
     bool old;
     ~Df64Guard() { c->df64_m2l = old; }
   } df64_guard{c, c->df64_m2l};
-  c->df64_m2l = c->opt.precision == 1;
+  c->df64_m2l = c->opt.precision >= 1;
   Work wk;
   // one port per "system": each system is its own frequency here
   sys_consts(c, wk, nsys, 1, nsys, freq);

@@ -1481,7 +1481,9 @@ void tc_prepare(xrl_ctx* c) {
   c->d.tc_err.alloc(c->alloc, 1);
   XRL_CUDA(cudaMemsetAsync(c->d.tc_err.p, 0, sizeof(int32_t), c->stream));
   tcp_prepare(c);
-  if (tc_npad(ncoef) > 96) return;
+  // expansions of 49..96 coefficients (orders 6-8) take the 64- and 96-wide
+  // tiles; smaller orders stay on the CUDA-core translation kernels
+  if (tc_npad(ncoef) > 96 || tc_npad(ncoef) < 64) return;
   const int Kp = tc_kpad(ncoef), Np = tc_npad(ncoef);
   const int noff = (int)(c->tree.m2l_offsets.size() / 3);
   if (noff == 0) return;
@@ -1590,7 +1592,8 @@ void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cud
 }
 
 bool tc64_usable(const xrl_ctx* c, int nc) {
-  return c->opt.tensor_cores != 0 && nc >= 64 && tc_npad(c->ncoef) <= 96 && c->d.tc_err.n > 0;
+  return c->opt.tensor_cores != 0 && nc >= 64 && tc_npad(c->ncoef) <= 96 && tc_npad(c->ncoef) >= 64 &&
+         c->d.tc_err.n > 0;
 }
 
 // One-time images of the FP64-accurate pass: the equilibration exponents d_k
