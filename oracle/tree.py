@@ -15,11 +15,18 @@ compared bit for bit:
   boxes is <= leaf_target (else 20), capped at the deepest level whose box
   side is >= 2 r_max (r_max = largest centroid-to-vertex distance), and at
   least 2;
-* with the separation ws (1 or 2), boxes of one level are neighbours when
-  their cells differ by at most ws in every direction; U-list of a leaf:
-  non-empty neighbouring leaves; V-list of a box (level >= 2): non-empty
-  children of the parent's neighbours (parent included) that are not
-  neighbours of the box; lists sorted by box index.
+* build(): with the separation ws (1 or 2), boxes of one level are
+  neighbours when their cells differ by at most ws in every direction;
+  U-list of a leaf: non-empty neighbouring leaves; V-list of a box (level
+  >= 2): non-empty children of the parent's neighbours (parent included)
+  that are not neighbours of the box; lists sorted by box index;
+* build_mac(): boxes are well separated when the spheres about their
+  centres that hold all of their panels' vertices satisfy
+  rho_t + rho_s <= theta |c_t - c_s|; near lists are refined level by
+  level from the parent's near list (see its docstring).  This rule bounds
+  the ratio that governs the convergence of the translated expansions for
+  panels of any size, which the cell-distance rule cannot when panels stick
+  out of their boxes.
 """
 import numpy as np
 
@@ -143,3 +150,116 @@ def build(xyz, tri, leaf_target=32, ws=2):
             Vl.append(sorted(lst))
         V[lev] = Vl
     return {"keys": k, "perm": perm, "L": L, "levels": levels, "leaf_of": leaf_of, "U": U, "V": V}
+
+
+def _panel_vertices(xyz, tri):
+    """Vertex coordinates [N, 4, 3] and per-panel vertex count (3 or 4)."""
+    tri = np.asarray(tri, np.int64)
+    if tri.shape[1] == 3:
+        tri = np.hstack([tri, -np.ones((tri.shape[0], 1), np.int64)])
+    nv = np.where(tri[:, 3] >= 0, 4, 3)
+    v = np.asarray(xyz, float)[np.where(tri >= 0, tri, tri[:, :1])]
+    return v, nv
+
+
+def box_geometry(xyz, tri, sk_perm, levels, lo, side, L):
+    """Centre and radius of every box of levels 0..L.
+
+    Centre c_b = lo + (cell + 1/2) h_l per axis (h_l = side / 2^l); radius
+    rho_b = max over the box's panels and their vertices of |v - c_b| (a flat
+    panel lies in the convex hull of its vertices, so its whole surface is
+    within rho_b of c_b).  Squared distances are summed x, y, z in that order."""
+    xyz = np.asarray(xyz, float)
+    v, nv = _panel_vertices(xyz, tri)
+    keys_sorted, perm = sk_perm
+    vs = v[perm]
+    nvs = nv[perm]
+    out = {}
+    for lev in range(L + 1):
+        h = side / float(1 << lev)
+        bk = levels[lev]
+        cell = decode(bk)
+        ctr = np.stack([lo[a] + (cell[:, a] + 0.5) * h for a in range(3)], axis=1)
+        bidx = np.searchsorted(bk, keys_sorted >> np.uint64(3 * (21 - lev)))
+        r2 = np.zeros(bk.shape[0])
+        for j in range(4):
+            dx = vs[:, j, 0] - ctr[bidx, 0]
+            dy = vs[:, j, 1] - ctr[bidx, 1]
+            dz = vs[:, j, 2] - ctr[bidx, 2]
+            d2 = dx * dx + dy * dy + dz * dz
+            d2 = np.where(nvs > j, d2, 0.0)
+            np.maximum.at(r2, bidx, d2)
+        out[lev] = (ctr, np.sqrt(r2), bidx)
+    return out
+
+
+def build_mac(xyz, tri, leaf_target=32, theta=0.5, cap=2.0):
+    """Uniform-depth octree with interaction lists from a bounding-sphere
+    admissibility test (the FMM of Sec. II-C defers to refs [22], [23]; this
+    separation rule is the multipole acceptance criterion used with
+    expansions about box centres):
+
+    * root cube, keys, panel order and leaf level L as in build(); the depth
+      cap side / 2^L >= cap * r_max applies when cap > 0;
+    * box centres and radii as in box_geometry();
+    * two boxes t, s of one level are well separated when
+      rho_t + rho_s <= theta * |c_t - c_s|, with |c_t - c_s| the square root
+      of the squared centre distance summed x, y, z;
+    * at level 1 every pair is near; at level l >= 2 the candidates of box t
+      are the children of the near boxes of t's parent: the well-separated
+      ones form t's V-list, the others its near list; the near lists of the
+      leaf level are the U-lists;
+    * lists sorted by box index.  V offsets (target - source cell) are not
+      bounded by a fixed window.
+    Returns the dict of build() plus 'centre', 'radius' per level."""
+    k = keys(xyz, tri)
+    c, lo, side = root(xyz, tri)
+    v, _ = _vertices(xyz, tri)
+    rmax = np.max(np.sqrt(np.sum((v - c[:, None, :]) ** 2, axis=2)))
+    N = k.shape[0]
+    perm = np.lexsort((np.arange(N), k))
+    sk = k[perm]
+    L = 20
+    for lev in range(2, 21):
+        sh = np.uint64(3 * (21 - lev))
+        cnt = np.unique(sk >> sh).shape[0]
+        if N / cnt <= leaf_target:
+            L = lev
+            break
+    if cap > 0:
+        lsize = 2
+        for lev in range(2, 21):
+            if side / float(1 << lev) >= cap * rmax:
+                lsize = lev
+        L = min(L, lsize)
+    L = max(2, L)
+    levels = [np.unique(sk >> np.uint64(3 * (21 - lev))) for lev in range(L + 1)]
+    geo = box_geometry(xyz, tri, (sk, perm), levels, lo, side, L)
+    leaf_of = geo[L][2]
+    near = [list(range(levels[1].shape[0])) for _ in range(levels[1].shape[0])]
+    V = {}
+    for lev in range(2, L + 1):
+        ctr, rad, _ = geo[lev]
+        bk = levels[lev]
+        par = np.searchsorted(levels[lev - 1], bk >> np.uint64(3))
+        first = np.searchsorted(bk >> np.uint64(3), levels[lev - 1], side="left")
+        last = np.searchsorted(bk >> np.uint64(3), levels[lev - 1], side="right")
+        Vl, nl = [], []
+        for t in range(bk.shape[0]):
+            vl, nn = [], []
+            for sp in near[par[t]]:
+                for s in range(first[sp], last[sp]):
+                    dx = ctr[t, 0] - ctr[s, 0]
+                    dy = ctr[t, 1] - ctr[s, 1]
+                    dz = ctr[t, 2] - ctr[s, 2]
+                    dist = np.sqrt(dx * dx + dy * dy + dz * dz)
+                    if s != t and rad[t] + rad[s] <= theta * dist:
+                        vl.append(s)
+                    else:
+                        nn.append(s)
+            Vl.append(sorted(vl))
+            nl.append(sorted(nn))
+        V[lev] = Vl
+        near = nl
+    return {"keys": k, "perm": perm, "L": L, "levels": levels, "leaf_of": leaf_of, "U": near, "V": V,
+            "centre": {lev: geo[lev][0] for lev in geo}, "radius": {lev: geo[lev][1] for lev in geo}}
