@@ -51,8 +51,8 @@ typedef enum {
 typedef struct {
   int32_t fmm_order;   /* expansion order p of the solid-harmonic FMM (2..12), default 8 */
   int32_t leaf_target; /* mean panels per non-empty leaf used to pick the tree depth, default 32
-                          (the depth is also capped so that leaf sides are >= 2x the largest
-                          panel radius) */
+                          (with mac_theta = 0 the depth is also capped so that leaf sides are >= 2x
+                          the largest panel radius) */
   int32_t precision;   /* 0: FP64 everywhere (CUDA-core FP64 kernels); 1: mixed (FP32 FMM/near field
                           inside FP64 refinement); 2: FP64-accurate products throughout on the tensor
                           cores and FP32 pipes (the integer-slice and double-float kernels of mode 1's
@@ -71,8 +71,8 @@ typedef struct {
   double tol;          /* relative residual ||b - Ax|| / ||b|| per system, default 1e-8 */
   double inner_tol;    /* inner COCG relative residual, default 1e-3 */
   int32_t device;      /* CUDA device ordinal, default 0 */
-  int32_t separation;  /* well-separatedness ws of the octree (1 or 2): leaves within ws cells are
-                          near field; default 2 (see xrl_export_lists) */
+  int32_t separation;  /* with mac_theta = 0: well-separatedness ws of the octree (1 or 2), leaves
+                          within ws cells are near field; default 2 (see xrl_export_lists) */
   int32_t use_graphs;  /* 1 (default): the inner operator of every Arnoldi step is replayed from a
                           CUDA graph captured once per solve; 0: plain launches */
   int32_t tensor_cores; /* 1 (default): for n_cols >= 64 the FP32 products of the mixed mode run
@@ -80,6 +80,11 @@ typedef struct {
                            BF16 pieces, six products, ~FP32 accuracy) and the FP64-accurate
                            residuals their near field, M2M and M2L in 7-bit integer slices
                            (exact FP32 accumulation); 0: CUDA-core kernels only */
+  double mac_theta;    /* > 0 (default 0.66): two boxes of one octree level are far enough apart for
+                          the expansions when rho_t + rho_s <= mac_theta |c_t - c_s| (c = box centre,
+                          rho = largest distance from it to a vertex of the box's panels), and the
+                          near field holds the rest; must be < 1.  0: the cell-distance rule of
+                          `separation` (with its leaf-size cap, see xrl_export_lists) */
 } xrl_options;
 
 /* Fill `opt` with the defaults listed above. */
@@ -206,7 +211,7 @@ typedef struct {
 } xrl_stats;
 
 /* FMM autotuner: tries leaf_target in {16, 32, 64} x fmm_order in {4, 6, 7, 8}
- * (separation 2), re-running xrl_setup for each.  A candidate is admissible
+ * (with the context's separation rule), re-running xrl_setup for each.  A candidate is admissible
  * when its FP64 product matches the FP64 direct sum (xrl_direct_mvm_device) on
  * two seeded random columns to mvm_tol (relative 2-norm).  Each admissible
  * candidate's product at n_cols columns is timed with CUDA events in the
@@ -267,13 +272,19 @@ xrl_status xrl_export_tree(const xrl_ctx* ctx, uint64_t* keys, int32_t* perm, in
 xrl_status xrl_export_branches(const xrl_ctx* ctx, int32_t* tail, int32_t* head);
 xrl_status xrl_export_loops(const xrl_ctx* ctx, int64_t* row_ptr, int32_t* col, int8_t* val);
 
-/* Interaction lists of the octree (uniform depth; U-list = leaves within
- * `separation` cells in every direction, V-list = children of the parent's
- * near boxes that are not near the box):
- * for level l in [2, n_levels), box counts, Morton keys of the occupied boxes
- * and the V-list (multipole-to-local) pairs as CSR over target boxes, and
- * for the leaf level the U-list (near field) as CSR.  Sizes via the counts
- * query (pass NULL arrays). */
+/* Interaction lists of the octree (uniform depth).  With mac_theta > 0 two
+ * boxes of one level are well separated when rho_t + rho_s <= mac_theta
+ * |c_t - c_s| (c = centre of the box's cell, rho = largest distance from c to
+ * a vertex of the box's panels); at level 1 every pair is near, at level
+ * l >= 2 the candidates of a box are the children of its parent's near
+ * boxes, split into the V-list (well separated) and the near list, and the
+ * leaf level's near lists are the U-lists (near field).  With mac_theta = 0:
+ * U-list = leaves within `separation` cells in every direction, V-list =
+ * children of the parent's near boxes that are not near the box.  Output,
+ * for level l in [2, n_levels): box counts, Morton keys of the occupied boxes
+ * and the V-list (multipole-to-local) pairs as CSR over target boxes, and for
+ * the leaf level the U-list as CSR.  Sizes via the counts query (pass NULL
+ * arrays). */
 xrl_status xrl_export_lists(const xrl_ctx* ctx, int32_t level, int32_t* n_boxes, uint64_t* box_keys,
                             int64_t* v_ptr, int32_t* v_src, int64_t* u_ptr, int32_t* u_src);
 

@@ -12,7 +12,10 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+# host code without FMA contraction: the tree's separation test must round as
+# written (it is compared bit for bit with an independent implementation)
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler",
+         "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
 
 

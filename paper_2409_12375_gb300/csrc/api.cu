@@ -191,6 +191,7 @@ void xrl_default_options(xrl_options* o) {
   o->separation = 2;
   o->use_graphs = 1;
   o->tensor_cores = 1;
+  o->mac_theta = 0.66;
 }
 
 xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {
@@ -209,6 +210,7 @@ xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {
     XRL_CHECK(c->opt.fmm_order >= 2 && c->opt.fmm_order <= 12, XRL_EINVAL, "fmm_order must be in [2, 12]");
     XRL_CHECK(c->opt.leaf_target >= 1, XRL_EINVAL, "leaf_target must be >= 1");
     XRL_CHECK(c->opt.separation == 1 || c->opt.separation == 2, XRL_EINVAL, "separation must be 1 or 2");
+    XRL_CHECK(c->opt.mac_theta >= 0.0 && c->opt.mac_theta < 1.0, XRL_EINVAL, "mac_theta must be in [0, 1)");
     XRL_CHECK(c->opt.precond >= 0 && c->opt.precond <= 3, XRL_EINVAL, "precond must be in [0, 3]");
     XRL_CHECK(c->opt.precision >= 0 && c->opt.precision <= 2, XRL_EINVAL, "precision must be 0, 1 or 2");
     XRL_CHECK(c->opt.tol > 0 && c->opt.restart >= 1 && c->opt.max_iters >= 1, XRL_EINVAL, "bad solver options");
@@ -485,7 +487,6 @@ xrl_status xrl_autotune(xrl_ctx* c, int32_t nc, double tol, int32_t precision, i
       t ^= t >> 31;
       v = (double)(t >> 11) * (2.0 / 9007199254740992.0) - 1.0;
     }
-    c->opt.separation = 2;
     if (!c->ready) {
       if (xrl_setup(c) != XRL_OK) throw Error(XRL_EINVAL, c->err);
     }

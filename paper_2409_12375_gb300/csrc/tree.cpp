@@ -9,23 +9,35 @@
 //  - panels sorted by (key, caller index);
 //  - uniform depth: the leaf level L is the smallest level >= 2 at which the
 //    mean occupancy of the non-empty boxes is <= leaf_target (at most 20),
-//    but no deeper than the deepest level whose box side is >= 2 r_max
-//    (r_max = largest centroid-to-vertex distance of any panel; panels that
-//    stick out of their leaf by more than half a box would spoil the
-//    expansions' convergence), and never above level 2;
+//    and never above level 2;
 //  - only non-empty boxes exist; a box's children are the non-empty boxes of
 //    the next level with its key as prefix;
-//  - with the separation ws (1 or 2), two boxes of one level are NEIGHBOURS
-//    when their integer coordinates differ by at most ws in every direction;
-//  - U-list of a leaf: non-empty neighbouring leaves (itself included);
-//  - V-list of a box at level >= 2: non-empty children of the parent's
-//    neighbours (the parent included) that are not neighbours of the box;
-//    (target - source) offsets lie in [-(2ws+1), 2ws+1]^3 and are numbered in
-//    order of first use in lexicographic (dx, dy, dz) order;
-//  - every list is sorted by box index (= Morton order within a level).
-// Every panel pair is then covered exactly once: by the U-list of its leaf
-// pair, or by the V-list pair at the unique level where the two ancestors
-// stop being adjacent.
+//  - every list is sorted by box index (= Morton order within a level);
+//    distinct (target - source) V-list cell offsets are numbered in
+//    lexicographic (dx, dy, dz) order.
+// Two rules decide which pairs of boxes are far enough apart for the
+// translated expansions:
+//  - bounding spheres (mac_theta > 0): box centre c_b = lo + (cell + 1/2) h_l,
+//    radius rho_b = largest distance from c_b to a vertex of a panel in the
+//    box (panels may stick out of their box; their surfaces lie within
+//    rho_b); boxes t, s of one level are well separated when
+//    rho_t + rho_s <= mac_theta |c_t - c_s|.  Every level-1 pair is near; at
+//    level l >= 2 the candidates of t are the children of the near boxes of
+//    t's parent, split into t's V-list (well separated) and its near list;
+//    the leaf level's near lists are the U-lists.  Distances are summed
+//    x, y, z in that order (host code is built without FMA contraction) so
+//    that a second implementation of the same rule can agree bit for bit;
+//  - cell distance (mac_theta = 0, separation ws = 1 or 2): two boxes of one
+//    level are NEIGHBOURS when their cells differ by at most ws in every
+//    direction; U-list of a leaf: non-empty neighbouring leaves (itself
+//    included); V-list of a box at level >= 2: non-empty children of the
+//    parent's neighbours (the parent included) that are not neighbours of
+//    the box.  This rule also caps the depth so that leaf sides are >= 2 r_max
+//    (r_max = largest centroid-to-vertex distance), since it cannot see
+//    panels that stick out of their boxes.
+// Either way every panel pair is covered exactly once: by the U-list of its
+// leaf pair, or by the V-list pair at the unique level where its two
+// ancestors first count as well separated.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -63,6 +75,124 @@ int64_t find_key(const std::vector<uint64_t>& keys, int64_t lo, int64_t hi, uint
   auto it = std::lower_bound(b, e, k);
   if (it != e && *it == k) return it - keys.begin();
   return -1;
+}
+
+// Interaction lists by the bounding-sphere rule (see the file header).
+void mac_lists(xrl_ctx* c, const std::vector<uint64_t>& sk, const std::vector<std::vector<int32_t>>& first_of,
+               double theta) {
+  Tree& t = c->tree;
+  const int L = t.L, N = (int)sk.size(), nb = t.n_boxes();
+  // box centres and radii
+  std::vector<double> ctr(3 * (size_t)nb), rad(nb, 0.0);
+  std::vector<int32_t> cell(3 * (size_t)nb);
+  for (int l = 0; l <= L; ++l) {
+    const double h = t.side / (double)(1u << l);
+    const int b0 = t.level_off[l], nbl = t.level_off[l + 1] - b0;
+    for (int i = 0; i < nbl; ++i) {
+      const int b = b0 + i;
+      uint32_t x, y, z;
+      morton_decode(t.box_key[b], &x, &y, &z);
+      cell[3 * (size_t)b] = (int32_t)x;
+      cell[3 * (size_t)b + 1] = (int32_t)y;
+      cell[3 * (size_t)b + 2] = (int32_t)z;
+      const double cc[3] = {t.lo[0] + ((double)x + 0.5) * h, t.lo[1] + ((double)y + 0.5) * h,
+                            t.lo[2] + ((double)z + 0.5) * h};
+      for (int k = 0; k < 3; ++k) ctr[3 * (size_t)b + k] = cc[k];
+      const int r0 = first_of[l][i], r1 = (i + 1 < nbl) ? first_of[l][i + 1] : N;
+      double r2 = 0.0;
+      for (int r = r0; r < r1; ++r) {
+        const int p = t.perm[r];
+        for (int v = 0; v < panel_nv(c->pan, p); ++v) {
+          const double* X = &c->xyz[3 * (size_t)c->pan[4 * (size_t)p + v]];
+          const double dx = X[0] - cc[0], dy = X[1] - cc[1], dz = X[2] - cc[2];
+          const double d2 = dx * dx + dy * dy + dz * dz;
+          if (d2 > r2) r2 = d2;
+        }
+      }
+      rad[b] = std::sqrt(r2);
+    }
+  }
+  // children of a box are contiguous at the next level
+  std::vector<int32_t> cfirst(nb, 0), clast(nb, 0);
+  for (int b = t.level_off[1]; b < nb; ++b) {
+    const int P = t.parent[b];
+    if (clast[P] == 0) cfirst[P] = b;
+    clast[P] = b + 1;
+  }
+  auto separated = [&](int a, int b) {
+    const double dx = ctr[3 * (size_t)a] - ctr[3 * (size_t)b];
+    const double dy = ctr[3 * (size_t)a + 1] - ctr[3 * (size_t)b + 1];
+    const double dz = ctr[3 * (size_t)a + 2] - ctr[3 * (size_t)b + 2];
+    const double dist = std::sqrt(dx * dx + dy * dy + dz * dz);
+    return a != b && rad[a] + rad[b] <= theta * dist;
+  };
+  // near lists of the current level (global ids), starting with level 1: all pairs
+  std::vector<int64_t> nptr{0};
+  std::vector<int32_t> nsrc;
+  {
+    const int b0 = t.level_off[1], b1 = t.level_off[2];
+    for (int a = b0; a < b1; ++a) {
+      for (int b = b0; b < b1; ++b) nsrc.push_back(b);
+      nptr.push_back((int64_t)nsrc.size());
+    }
+  }
+  t.v_ptr.assign(nb + 1, 0);
+  t.v_src.clear();
+  std::vector<int64_t> vcode;
+  const int64_t K = 1 << 20;
+  auto code_of = [&](int tg, int sc) {
+    const int64_t dx = cell[3 * (size_t)tg] - cell[3 * (size_t)sc], dy = cell[3 * (size_t)tg + 1] - cell[3 * (size_t)sc + 1],
+                  dz = cell[3 * (size_t)tg + 2] - cell[3 * (size_t)sc + 2];
+    return ((dx + K) << 42) | ((dy + K) << 21) | (dz + K);
+  };
+  for (int l = 2; l <= L; ++l) {
+    const int b0 = t.level_off[l], b1 = t.level_off[l + 1], pb0 = t.level_off[l - 1];
+    std::vector<int64_t> mptr{0};
+    std::vector<int32_t> msrc;
+    for (int tg = b0; tg < b1; ++tg) {
+      const int P = t.parent[tg] - pb0;
+      std::vector<int32_t> vl, nl;
+      for (int64_t k = nptr[P]; k < nptr[P + 1]; ++k) {
+        const int sp = nsrc[k];
+        for (int sc = cfirst[sp]; sc < clast[sp]; ++sc) (separated(tg, sc) ? vl : nl).push_back(sc);
+      }
+      std::sort(vl.begin(), vl.end());
+      std::sort(nl.begin(), nl.end());
+      for (int sc : vl) {
+        t.v_src.push_back(sc);
+        vcode.push_back(code_of(tg, sc));
+      }
+      t.v_ptr[tg + 1] = (int64_t)t.v_src.size();
+      msrc.insert(msrc.end(), nl.begin(), nl.end());
+      mptr.push_back((int64_t)msrc.size());
+    }
+    nptr.swap(mptr);
+    nsrc.swap(msrc);
+  }
+  // boxes of levels 0, 1 have empty V-lists: carry the pointer forward
+  for (int b = 0; b < nb; ++b) t.v_ptr[b + 1] = std::max(t.v_ptr[b + 1], t.v_ptr[b]);
+  // U-lists: the leaf level's near lists, leaf-local
+  const int leaf0 = t.level_off[L], nl = t.n_leaves();
+  t.u_ptr.assign(nl + 1, 0);
+  t.u_src.clear();
+  for (int i = 0; i < nl; ++i) {
+    for (int64_t k = nptr[i]; k < nptr[i + 1]; ++k) t.u_src.push_back(nsrc[k] - leaf0);
+    t.u_ptr[i + 1] = (int64_t)t.u_src.size();
+  }
+  // compact offset table
+  std::vector<int64_t> used(vcode);
+  std::sort(used.begin(), used.end());
+  used.erase(std::unique(used.begin(), used.end()), used.end());
+  XRL_CHECK(used.size() < 32768, XRL_EINVAL, "too many M2L offsets");
+  t.m2l_offsets.clear();
+  for (int64_t code : used) {
+    const int dz = (int)((code & ((1 << 21) - 1)) - K), dy = (int)(((code >> 21) & ((1 << 21) - 1)) - K),
+              dx = (int)((code >> 42) - K);
+    t.m2l_offsets.insert(t.m2l_offsets.end(), {dx, dy, dz});
+  }
+  t.v_off.resize(vcode.size());
+  for (size_t k = 0; k < vcode.size(); ++k)
+    t.v_off[k] = (int16_t)(std::lower_bound(used.begin(), used.end(), vcode[k]) - used.begin());
 }
 
 }  // namespace
@@ -109,7 +239,8 @@ void build_tree(xrl_ctx* c, const std::vector<uint64_t>& keys) {
   int Lsize = 2;
   for (int l = 2; l <= 20; ++l)
     if (t.side / (double)(1 << l) >= 2.0 * rmax) Lsize = l;
-  t.L = std::max(2, std::min(L, Lsize));
+  const double theta = c->opt.mac_theta;
+  t.L = theta > 0 ? std::max(2, L) : std::max(2, std::min(L, Lsize));
   L = t.L;
 
   // boxes per level
@@ -147,6 +278,10 @@ void build_tree(xrl_ctx* c, const std::vector<uint64_t>& keys) {
     int end = (i + 1 < nl) ? first_of[L][i + 1] : N;
     t.leaf_count[i] = end - t.leaf_first[i];
     for (int r = t.leaf_first[i]; r < end; ++r) t.leaf_of[r] = i;
+  }
+  if (theta > 0) {
+    mac_lists(c, sk, first_of, theta);
+    return;
   }
   const int ws = c->opt.separation;
   // U-lists

@@ -30,7 +30,8 @@ class Options(ctypes.Structure):
                 ("inner_iters", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("device", ctypes.c_int32), ("separation", ctypes.c_int32),
-                ("use_graphs", ctypes.c_int32), ("tensor_cores", ctypes.c_int32)]
+                ("use_graphs", ctypes.c_int32), ("tensor_cores", ctypes.c_int32),
+                ("mac_theta", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):

@@ -40,7 +40,11 @@ def coils_ctx(lib, coils_mesh):
 
 
 def _check_tree(ctx, mesh):
-    ref = tree.build(mesh.xyz, mesh.tri, leaf_target=ctx.opts.leaf_target, ws=ctx.opts.separation)
+    if ctx.opts.mac_theta > 0:
+        ref = tree.build_mac(mesh.xyz, mesh.tri, leaf_target=ctx.opts.leaf_target, theta=ctx.opts.mac_theta,
+                             cap=0.0)
+    else:
+        ref = tree.build(mesh.xyz, mesh.tri, leaf_target=ctx.opts.leaf_target, ws=ctx.opts.separation)
     keys, perm, leaf = ctx.export_tree()
     assert np.array_equal(keys, ref["keys"])
     assert np.array_equal(perm, ref["perm"])
@@ -63,6 +67,17 @@ def test_tree_bit_exact_bar(bar_ctx, bar_mesh):
 
 def test_tree_bit_exact_coils(coils_ctx, coils_mesh):
     _check_tree(coils_ctx, coils_mesh)
+
+
+@pytest.mark.parametrize("opts", [dict(mac_theta=0.0, separation=2), dict(mac_theta=0.0, separation=1),
+                                  dict(mac_theta=0.5, leaf_target=16)])
+def test_tree_bit_exact_other_rules(lib, coils_mesh, opts):
+    """The cell-distance rule (ws = 1, 2) and a tighter bounding-sphere rule."""
+    x = lib.XRL.from_mesh(coils_mesh, **opts)
+    try:
+        _check_tree(x, coils_mesh)
+    finally:
+        x.close()
 
 
 def _dev(a):

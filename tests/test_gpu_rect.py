@@ -49,7 +49,11 @@ def _dev(a):
 
 
 def _check_tree(ctx, mesh):
-    ref = tree.build(mesh.xyz, mesh.tri, leaf_target=ctx.opts.leaf_target, ws=ctx.opts.separation)
+    if ctx.opts.mac_theta > 0:
+        ref = tree.build_mac(mesh.xyz, mesh.tri, leaf_target=ctx.opts.leaf_target, theta=ctx.opts.mac_theta,
+                             cap=0.0)
+    else:
+        ref = tree.build(mesh.xyz, mesh.tri, leaf_target=ctx.opts.leaf_target, ws=ctx.opts.separation)
     keys, perm, leaf = ctx.export_tree()
     assert np.array_equal(keys, ref["keys"])
     assert np.array_equal(perm, ref["perm"])
