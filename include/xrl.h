@@ -80,11 +80,12 @@ typedef struct {
                            BF16 pieces, six products, ~FP32 accuracy) and the FP64-accurate
                            residuals their near field, M2M and M2L in 7-bit integer slices
                            (exact FP32 accumulation); 0: CUDA-core kernels only */
-  double mac_theta;    /* > 0 (default 0.66): two boxes of one octree level are far enough apart for
-                          the expansions when rho_t + rho_s <= mac_theta |c_t - c_s| (c = box centre,
-                          rho = largest distance from it to a vertex of the box's panels), and the
-                          near field holds the rest; must be < 1.  0: the cell-distance rule of
-                          `separation` (with its leaf-size cap, see xrl_export_lists) */
+  double mac_theta;    /* > 0: two boxes of one octree level are far enough apart for the expansions
+                          when rho_t + rho_s <= mac_theta |c_t - c_s| (c = box centre, rho = largest
+                          distance from it to a vertex of the box's panels), the near field holds the
+                          rest, and the depth has no leaf-size cap; must be < 1.  0 (default): the
+                          cell-distance rule of `separation` with its leaf-size cap (see
+                          xrl_export_lists) */
 } xrl_options;
 
 /* Fill `opt` with the defaults listed above. */

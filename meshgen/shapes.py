@@ -356,3 +356,205 @@ def crop_check(m: Mesh):
     _, dcnt = np.unique(e, axis=0, return_counts=True)
     oriented = bool(np.all(dcnt == 1))
     return closed, oriented
+
+
+# ---------------------------------------------------------------- package (BGA-like)
+def _hole_centres(rng, size, n, r, gap, margin):
+    """n seeded hole centres in [margin, size - margin]^2, pairwise >= 2r + gap apart."""
+    out = []
+    tries = 0
+    while len(out) < n:
+        tries += 1
+        if tries > 200000:
+            raise ValueError("cannot place %d holes of radius %g in %g" % (n, r, size))
+        p = rng.uniform(margin, size - margin, 2)
+        if all((p[0] - q[0]) ** 2 + (p[1] - q[1]) ** 2 >= (2 * r + gap) ** 2 for q in out):
+            out.append(p)
+    return np.array(out).reshape(-1, 2)
+
+
+def _perforated_face(size, holes, r, h, rng, jitter=0.2):
+    """Conforming triangulation of the square [0, size]^2 minus circular holes.
+
+    Boundary points: the square's edges at spacing ~h and each circle at
+    n_seg = max(8, ceil(2 pi r / h)) points; interior points: a jittered grid
+    at spacing h kept 0.6 h away from every boundary.  The Delaunay
+    triangulation of all points (scipy.spatial.Delaunay) holds every boundary
+    segment as an edge when no interior point is near it; the triangles whose
+    centroid lies inside a hole are removed.  Returns points [n, 2], triangles
+    [m, 3] (counter-clockwise), the square boundary loop and one point loop per
+    hole (counter-clockwise around the hole)."""
+    from scipy.spatial import Delaunay
+    ne = max(2, int(math.ceil(size / h)))
+    t = np.linspace(0.0, size, ne + 1)
+    sq = ([(x, 0.0) for x in t[:-1]] + [(size, y) for y in t[:-1]] +
+          [(x, size) for x in t[::-1][:-1]] + [(0.0, y) for y in t[::-1][:-1]])
+    pts = list(sq)
+    n_sq = len(sq)
+    nseg = max(8, int(math.ceil(2 * math.pi * r / h)))
+    hole_loops = []
+    for (cx, cy) in holes:
+        i0 = len(pts)
+        for k in range(nseg):
+            a = 2 * math.pi * k / nseg
+            pts.append((cx + r * math.cos(a), cy + r * math.sin(a)))
+        hole_loops.append(list(range(i0, i0 + nseg)))
+    g = np.arange(h / 2, size, h)
+    gx, gy = np.meshgrid(g, g, indexing="ij")
+    cand = np.stack([gx.ravel(), gy.ravel()], 1) + rng.uniform(-jitter, jitter, (gx.size, 2)) * h
+    keep = np.all((cand > 0.6 * h) & (cand < size - 0.6 * h), axis=1)
+    for (cx, cy) in holes:
+        keep &= (cand[:, 0] - cx) ** 2 + (cand[:, 1] - cy) ** 2 > (r + 0.6 * h) ** 2
+    pts = np.vstack([np.array(pts), cand[keep]])
+    tri = Delaunay(pts).simplices.astype(np.int64)
+    cen = pts[tri].mean(axis=1)
+    inside = np.zeros(tri.shape[0], bool)
+    for (cx, cy) in holes:
+        inside |= (cen[:, 0] - cx) ** 2 + (cen[:, 1] - cy) ** 2 < r * r
+    tri = tri[~inside]
+    # counter-clockwise
+    a, b, c = pts[tri[:, 0]], pts[tri[:, 1]], pts[tri[:, 2]]
+    cw = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0]) < 0
+    tri[cw] = tri[cw][:, [0, 2, 1]]
+    # every boundary segment must be an edge of exactly one triangle
+    e = np.sort(np.vstack([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]]), axis=1)
+    ek, cnt = np.unique(e, axis=0, return_counts=True)
+    edges = {tuple(x): int(n) for x, n in zip(ek, cnt)}
+    loops = [list(range(n_sq))] + hole_loops
+    for lp in loops:
+        for k in range(len(lp)):
+            s = tuple(sorted((lp[k], lp[(k + 1) % len(lp)])))
+            if edges.get(s) != 1:
+                raise ValueError("boundary segment missing from the triangulation; change the seed or h")
+    if np.any(cnt > 2):
+        raise ValueError("non-manifold triangulation")
+    return pts, tri, loops[0], loops[1:]
+
+
+def _plane(bld, size, t, z0, holes, r, h, rng, cond_tag, origin=(0.0, 0.0)):
+    """Closed surface of a perforated plate [0,size]^2 x [z0 - t/2, z0 + t/2]:
+    top and bottom faces, the hole walls and the outer rim (one layer each)."""
+    pts, tri, sq, hl = _perforated_face(size, holes, r, h, rng)
+    ox, oy = origin
+    top = [bld.vid((cond_tag, 'pt', i), (ox + p[0], oy + p[1], z0 + t / 2)) for i, p in enumerate(pts)]
+    bot = [bld.vid((cond_tag, 'pb', i), (ox + p[0], oy + p[1], z0 - t / 2)) for i, p in enumerate(pts)]
+    for a, b, c in tri:
+        bld.tris.append((top[a], top[b], top[c]))      # +z outward
+        bld.tags.append(-1)
+        bld.tris.append((bot[a], bot[c], bot[b]))      # -z outward
+        bld.tags.append(-1)
+    # outer rim: square loop counter-clockwise seen from +z, outward = away from the square
+    for k in range(len(sq)):
+        a, b = sq[k], sq[(k + 1) % len(sq)]
+        bld.quad(bot[a], bot[b], top[b], top[a], -1)
+    # hole walls: loops counter-clockwise around the hole, outward = towards the hole axis
+    for lp in hl:
+        for k in range(len(lp)):
+            a, b = lp[k], lp[(k + 1) % len(lp)]
+            bld.quad(bot[b], bot[a], top[a], top[b], -1)
+
+
+def _icosphere(bld, centre, r, level, cond_tag):
+    """Closed sphere: an icosahedron subdivided `level` times, vertices on the sphere."""
+    p = (1 + 5 ** 0.5) / 2
+    v = [(-1, p, 0), (1, p, 0), (-1, -p, 0), (1, -p, 0), (0, -1, p), (0, 1, p), (0, -1, -p), (0, 1, -p),
+         (p, 0, -1), (p, 0, 1), (-p, 0, -1), (-p, 0, 1)]
+    v = [np.array(x, float) / np.linalg.norm(x) for x in v]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+         (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11),
+         (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        mid = {}
+        nf = []
+
+        def m(a, b):
+            k = (min(a, b), max(a, b))
+            if k not in mid:
+                x = v[a] + v[b]
+                v.append(x / np.linalg.norm(x))
+                mid[k] = len(v) - 1
+            return mid[k]
+        for a, b, c in f:
+            ab, bc, ca = m(a, b), m(b, c), m(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        f = nf
+    ids = [bld.vid((cond_tag, 's', i), np.asarray(centre) + r * x) for i, x in enumerate(v)]
+    for a, b, c in f:
+        bld.tris.append((ids[a], ids[b], ids[c]))
+        bld.tags.append(-1)
+
+
+def package(size=10e-3, t=35e-6, n_holes=400, r_hole=0.1e-3, hole_gap=0.05e-3, n_balls=8, r_ball=0.15e-3,
+            pitch=0.8e-3, ball_gap=0.05e-3, n_traces=16, trace_w=50e-6, trace_lift=0.1e-3, trace_len=(3e-3, 8e-3),
+            n_ports=8, h=42e-6, sphere_level=2, sigma=5.8e7, n_freq=16, fmin=1e6, fmax=5e9, seed=3) -> Mesh:
+    """BGA-like package: a perforated ground plane, an array of solder balls
+    below it and straight signal traces above it (the package workload of
+    Sec. III-B, synthetic).
+
+    * plane: size x size, thickness t, n_holes seeded circular holes of radius
+      r_hole at least hole_gap apart (rejection sampling), panels ~h;
+    * n_balls x n_balls spheres of radius r_ball at `pitch`, centred under the
+      plane, ball_gap below it (floating conductors, no port);
+    * n_traces straight traces trace_w x t, trace_lift above the plane, along
+      x or y, lengths U(trace_len), placed on free lanes; the first n_ports
+      carry a port (source: the far end cap, sink: the near end cap).
+    ESI thickness: t for the plane and the traces' 2A/P for the traces,
+    2 r_ball / 3 for the balls.  Conductor ids: 0 plane, 1.. balls, then traces."""
+    rng = np.random.default_rng(seed)
+    bld = _Builder(False)
+    holes = _hole_centres(rng, size, n_holes, r_hole, hole_gap, r_hole + hole_gap)
+    _plane(bld, size, t, 0.0, holes, r_hole, h, rng, 0)
+    conds = [0] * len(bld.tris)
+    thick = [t]
+    # solder balls
+    off = (size - (n_balls - 1) * pitch) / 2
+    cid = 1
+    for i in range(n_balls):
+        for j in range(n_balls):
+            n0 = len(bld.tris)
+            _icosphere(bld, (off + i * pitch, off + j * pitch, -t / 2 - ball_gap - r_ball), r_ball, sphere_level, cid)
+            conds += [cid] * (len(bld.tris) - n0)
+            thick.append(2 * r_ball / 3)
+            cid += 1
+    # traces on lanes: alternate x- and y-directed, lanes at a spacing of 4 widths
+    ports = []
+    tid = 0
+    lanes_x = list(np.arange(0.5e-3, size - 0.5e-3, 4 * trace_w * 3))
+    lanes_y = list(lanes_x)
+    rng.shuffle(lanes_x)
+    rng.shuffle(lanes_y)
+    z_tr = t / 2 + trace_lift + t / 2
+    for k in range(n_traces):
+        L = rng.uniform(*trace_len)
+        if k % 2 == 0:
+            y = lanes_x.pop()
+            x0 = rng.uniform(0.2e-3, size - 0.2e-3 - L)
+            corners = [(x0, y), (x0 + L, y)]
+            z = z_tr
+        else:
+            x = lanes_y.pop()
+            y0 = rng.uniform(0.2e-3, size - 0.2e-3 - L)
+            corners = [(x, y0), (x, y0 + L)]
+            z = z_tr + 2 * t          # y traces one layer higher: no crossing with the x traces
+        n0 = len(bld.tris)
+        _swept_trace(bld, corners, z, trace_w, t, 1, 1, h, 0, cid, (2 * tid, 2 * tid + 1))
+        conds += [cid] * (len(bld.tris) - n0)
+        thick.append(2 * trace_w * t / (2 * (trace_w + t)))
+        if k < n_ports:
+            ports.append((2 * tid + 1, 2 * tid))
+        tid += 1
+        cid += 1
+    tri = np.array(bld.tris, np.int64)
+    tags = np.array(bld.tags, np.int64)
+    # the swept traces emit inward-facing panels (see coils): reverse them
+    is_trace = np.array(conds) >= 1 + n_balls * n_balls
+    tri[is_trace] = tri[is_trace][:, [0, 2, 1]]
+    # terminals are numbered per trace (2 per trace); drop those of port-less traces
+    term = tags.copy()
+    used = sorted({s for s, _ in ports} | {k_ for _, k_ in ports})
+    remap = {o: n for n, o in enumerate(used)}
+    term = np.array([remap.get(int(x), -1) if x >= 0 else -1 for x in term], np.int32)
+    ports = [(remap[s], remap[k_]) for s, k_ in ports]
+    return Mesh(xyz=np.array(bld.pts), tri=tri.astype(np.int32), cond=np.array(conds, np.int32), term=term,
+                ports=ports, sigma=np.full(cid, sigma), thickness=np.array(thick),
+                freqs=np.geomspace(fmin, fmax, n_freq), name="package")

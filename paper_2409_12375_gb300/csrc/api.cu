@@ -191,7 +191,7 @@ void xrl_default_options(xrl_options* o) {
   o->separation = 2;
   o->use_graphs = 1;
   o->tensor_cores = 1;
-  o->mac_theta = 0.66;
+  o->mac_theta = 0.0;
 }
 
 xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {

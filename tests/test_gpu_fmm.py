@@ -69,15 +69,38 @@ def test_tree_bit_exact_coils(coils_ctx, coils_mesh):
     _check_tree(coils_ctx, coils_mesh)
 
 
-@pytest.mark.parametrize("opts", [dict(mac_theta=0.0, separation=2), dict(mac_theta=0.0, separation=1),
+@pytest.mark.parametrize("opts", [dict(mac_theta=0.0, separation=1), dict(mac_theta=0.66, leaf_target=32),
                                   dict(mac_theta=0.5, leaf_target=16)])
 def test_tree_bit_exact_other_rules(lib, coils_mesh, opts):
-    """The cell-distance rule (ws = 1, 2) and a tighter bounding-sphere rule."""
+    """The cell-distance rule at ws = 1 and the bounding-sphere rule."""
     x = lib.XRL.from_mesh(coils_mesh, **opts)
     try:
         _check_tree(x, coils_mesh)
     finally:
         x.close()
+
+
+def test_bounding_sphere_lists_cut_the_near_field(lib, coils_mesh):
+    """Bounding-sphere rule at theta = 0.6 without the leaf-size cap (leaf
+    target 32): the near field drops below 450 entries per panel (the
+    cell-distance rule with its cap holds ~2,060) and the FP64 product at
+    order 8 stays within 1e-6 of the direct sum."""
+    import torch
+    x = lib.XRL.from_mesh(coils_mesh, mac_theta=0.6, leaf_target=32, fmm_order=8)
+    try:
+        st = x.stats()
+        assert st["near_nnz"] / st["n_panels"] < 450, st["near_nnz"] / st["n_panels"]
+        rng = np.random.default_rng(8)
+        xv = _dev(rng.standard_normal((2, coils_mesh.n_tri)))
+        yd = torch.empty_like(xv)
+        yf = torch.empty_like(xv)
+        x.direct_mvm_device(xv, yd)
+        x.fmm_mvm_device(xv, yf)
+        torch.cuda.synchronize()
+        err = float(torch.linalg.norm(yf - yd) / torch.linalg.norm(yd))
+    finally:
+        x.close()
+    assert err < 1e-6, err
 
 
 def _dev(a):
