@@ -537,7 +537,8 @@ def fp64_products(pkg, x, m, pk, ext):
         b_.record(ext)
         torch.cuda.synchronize()
         ms = a_.elapsed_time(b_) / reps
-        out["nc%d" % nc] = dict(product_roofline(flops, byts, ms, pk), panel_cols_per_s=m.n_tri * nc / (ms * 1e-3))
+        out["nc%d" % nc] = dict(product_roofline(flops, byts, ms, pk), panel_cols_per_s=m.n_tri * nc / (ms * 1e-3),
+                                phases_ms={k: round(v["ms"], 4) for k, v in prof.items() if v["ms"] > 0})
         del xv, yv
     return out
 

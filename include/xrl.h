@@ -67,7 +67,10 @@ typedef struct {
   int32_t restart;     /* FGMRES restart length m, default 50 (Sec. III uses restart 50) */
   int32_t max_iters;   /* total outer iterations per solve, default 500 */
   int32_t inner_iters; /* max inner COCG iterations per preconditioner apply, default 60 */
-  int32_t warm_start;  /* 0: zero initial guess; 1: previous frequency's solution where available */
+  int32_t warm_start;  /* 0: zero initial guess; 1: with rhs_chunk, every frequency of a chunk starts
+                          from the previous chunk's last-frequency solution of the same port, scaled
+                          per system by the complex factor minimising the FP64 residual and kept only
+                          where it lowers ||b - A x0|| by more than 1 % (the first chunk starts at 0) */
   double tol;          /* relative residual ||b - Ax|| / ||b|| per system, default 1e-8 */
   double inner_tol;    /* inner COCG relative residual, default 1e-3 */
   int32_t device;      /* CUDA device ordinal, default 0 */
@@ -86,6 +89,11 @@ typedef struct {
                           rest, and the depth has no leaf-size cap; must be < 1.  0 (default): the
                           cell-distance rule of `separation` with its leaf-size cap (see
                           xrl_export_lists) */
+  int32_t rhs_chunk;   /* 0 (default): all (frequency, port) systems of xrl_solve form one multi-RHS
+                          block; > 0: the frequencies are solved in consecutive chunks of at most
+                          max(1, rhs_chunk / n_ports) frequencies (all ports of a frequency in one
+                          chunk), which bounds the Krylov basis to (2 restart + 1) x n_loops x chunk
+                          complex values */
 } xrl_options;
 
 /* Fill `opt` with the defaults listed above. */
@@ -235,7 +243,9 @@ xrl_status xrl_get_stats(const xrl_ctx* ctx, xrl_stats* out);
 /* Broadband sweep (Sec. II-D, Sec. III): for each frequency f in freq_hz
  * [n_freq] (f > 0), all ports are excited one at a time and the loop system
  * of eq. 7-8 is solved by right-preconditioned flexible GMRES with the FMM
- * product; all (frequency, port) systems form one multi-RHS block.  Output:
+ * product; all (frequency, port) systems form one multi-RHS block, or blocks
+ * of opt.rhs_chunk systems (then xrl_stats.total_iters sums the blocks'
+ * iteration counts).  Output:
  * R, L [n_freq][n_ports][n_ports], R = Re Z_port (ohm), L = Im Z_port / omega
  * (henry), Z_port = Y^-1 with Y the short-circuit port admittance.  Returns
  * XRL_ENOCONV (outputs still written) if some system did not reach opt.tol. */

@@ -192,6 +192,7 @@ void xrl_default_options(xrl_options* o) {
   o->use_graphs = 1;
   o->tensor_cores = 1;
   o->mac_theta = 0.0;
+  o->rhs_chunk = 0;
 }
 
 xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {
@@ -211,6 +212,8 @@ xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {
     XRL_CHECK(c->opt.leaf_target >= 1, XRL_EINVAL, "leaf_target must be >= 1");
     XRL_CHECK(c->opt.separation == 1 || c->opt.separation == 2, XRL_EINVAL, "separation must be 1 or 2");
     XRL_CHECK(c->opt.mac_theta >= 0.0 && c->opt.mac_theta < 1.0, XRL_EINVAL, "mac_theta must be in [0, 1)");
+    XRL_CHECK(c->opt.rhs_chunk >= 0, XRL_EINVAL, "rhs_chunk must be >= 0");
+    XRL_CHECK(c->opt.warm_start == 0 || c->opt.warm_start == 1, XRL_EINVAL, "warm_start must be 0 or 1");
     XRL_CHECK(c->opt.precond >= 0 && c->opt.precond <= 3, XRL_EINVAL, "precond must be in [0, 3]");
     XRL_CHECK(c->opt.precision >= 0 && c->opt.precision <= 2, XRL_EINVAL, "precision must be 0, 1 or 2");
     XRL_CHECK(c->opt.tol > 0 && c->opt.restart >= 1 && c->opt.max_iters >= 1, XRL_EINVAL, "bad solver options");
@@ -629,7 +632,36 @@ xrl_status xrl_solve(xrl_ctx* c, int32_t nf, const double* freq, double* R, doub
     for (int i = 0; i < nf; ++i) XRL_CHECK(std::isfinite(freq[i]) && freq[i] > 0, XRL_EINVAL, "frequencies must be > 0");
     double t0 = now_ms();
     try {
-      run_solve(c, nf, freq, R, L);
+      const int np = (int)c->port_src.size();
+      const int chunk = c->opt.rhs_chunk > 0 ? std::max(1, c->opt.rhs_chunk / std::max(1, np)) : nf;
+      if (chunk >= nf) {
+        run_solve(c, nf, freq, R, L);
+      } else {
+        // frequency chunks of at most rhs_chunk systems, in order; with
+        // warm_start = 1 each chunk starts from the previous one's last frequency
+        int iters = 0, nmvm = 0, inner = 0;
+        double res = 0.0;
+        bool noconv = false;
+        for (int f0 = 0; f0 < nf; f0 += chunk) {
+          const int k = std::min(chunk, nf - f0);
+          const size_t o = (size_t)f0 * np * np;
+          try {
+            run_solve(c, k, freq + f0, R + o, L + o, nullptr, nullptr, nullptr, f0 > 0 && c->opt.warm_start == 1);
+          } catch (const Error& e) {
+            if (e.code != XRL_ENOCONV) throw;
+            noconv = true;   // outputs of this chunk are written; go on with the next
+          }
+          iters += c->stats.total_iters;
+          nmvm += c->stats.n_mvm;
+          inner += c->stats.total_inner;
+          res = std::max(res, c->stats.max_rel_res);
+        }
+        c->stats.total_iters = iters;
+        c->stats.n_mvm = nmvm;
+        c->stats.total_inner = inner;
+        c->stats.max_rel_res = res;
+        XRL_CHECK(!noconv, XRL_ENOCONV, "FGMRES did not reach the tolerance in max_iters in some chunk");
+      }
     } catch (...) {
       c->stats.solve_ms = now_ms() - t0;
       throw;

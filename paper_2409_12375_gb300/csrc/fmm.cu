@@ -78,23 +78,19 @@ __global__ void k_p2p(int nc, int ct, const int32_t* __restrict__ leaf_first, co
   const int cn = min(ct, nc - c0);
   const int nB = leaf_count[B], f0 = leaf_first[B], w = near_w[B];
   const T* vb = val + near_off[B];
-  __shared__ int s_first[125], s_cnt[125];
+  // U-lists have no fixed length (the bounding-sphere rule can make them
+  // long): their entries are read from global memory, the same for all threads
   const int us = u_ptr[B], ue = u_ptr[B + 1];
-  for (int q = threadIdx.x; q < ue - us; q += blockDim.x) {
-    s_first[q] = leaf_first[u_src[us + q]];
-    s_cnt[q] = leaf_count[u_src[us + q]];
-  }
-  __syncthreads();
-  const int nu = ue - us;
   for (int t = threadIdx.x; t < nB * ct; t += blockDim.x) {
     int ii = t / ct, cc = t % ct;
     if (cc >= cn) continue;
     const T* row = vb + (size_t)ii * w;
     T acc = 0;
     int jj = 0;
-    for (int s = 0; s < nu; ++s) {
-      const T* xs = X + (size_t)s_first[s] * nc + c0 + cc;
-      const int n = s_cnt[s];
+    for (int s = us; s < ue; ++s) {
+      const int S = __ldg(u_src + s);
+      const T* xs = X + (size_t)__ldg(leaf_first + S) * nc + c0 + cc;
+      const int n = __ldg(leaf_count + S);
       for (int j = 0; j < n; ++j) acc += row[jj + j] * xs[(size_t)j * nc];
       jj += n;
     }

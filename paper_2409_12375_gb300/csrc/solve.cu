@@ -809,8 +809,18 @@ static void apply_Qinv(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* z) {
   c->stats.total_inner += c->opt.inner_iters;
 }
 
+// x0[f * nport + p] = prev[(nf_prev - 1) * nport + p]: every frequency of a chunk
+// starts from the last frequency of the previous chunk (same port)
+__global__ void k_seed_from_prev(int n, int nsys, int nport, int last0, const cplx* __restrict__ prev,
+                                 cplx* __restrict__ x) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * nsys) return;
+  const int s = (int)(idx / n), e = (int)(idx % n);
+  x[idx] = prev[(size_t)(last0 + s % nport) * n + e];
+}
+
 void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, const float* shape, int* accepted,
-               double* guess_res) {
+               double* guess_res, bool from_prev) {
   const Topo& T = c->topo;
   const int np = T.n_port;
   XRL_CHECK(np > 0, XRL_ESTATE, "no ports defined");
@@ -917,6 +927,20 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
     if (accepted) XRL_CUDA(cudaMemcpyAsync(accepted, dacc.p, sizeof(int) * nsys, cudaMemcpyDeviceToHost, s));
     if (guess_res) XRL_CUDA(cudaMemcpyAsync(guess_res, dgain.p, sizeof(double) * nsys, cudaMemcpyDeviceToHost, s));
     XRL_CUDA(cudaStreamSynchronize(s));
+    have_guess = true;
+  } else if (from_prev && c->last_nsys > 0 && c->last_nport == np && c->d.last_x.n >= (size_t)c->last_nsys * n) {
+    // previous-frequency start: the last frequency's solutions of the previous
+    // block, scaled per system by the complex factor that minimises the FP64
+    // residual, kept only where that lowers ||b - A x0|| by more than 1 %
+    k_seed_from_prev<<<nblk(tot), 256, 0, s>>>(n, nsys, np, c->last_nsys - np, c->d.last_x.p, wk.x.p);
+    count_launch(c);
+    apply_A(c, wk, nsys, wk.x.p, wk.w.p);
+    DBuf<int> dacc;
+    DBuf<double> dgain;
+    dacc.alloc(c->alloc, nsys);
+    dgain.alloc(c->alloc, nsys);
+    k_guess_scale<<<nsys, 256, 0, s>>>(n, nsys, wk.b.p, wk.x.p, wk.w.p, dacc.p, dgain.p);
+    count_launch(c);
     have_guess = true;
   }
   // The inner operator (gather -> FMM -> scatter -> loop reduce, ~14 kernels)

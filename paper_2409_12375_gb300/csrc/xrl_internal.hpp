@@ -372,7 +372,7 @@ void tc_m2l64(xrl_ctx* c, int nbx, int b0, int ncols, const double* M, double* L
 // solve.cu
 void solver_prepare(xrl_ctx* c);
 void run_solve(xrl_ctx* c, int nf, const double* f, double* R, double* L, const float* shape = nullptr,
-               int* accepted = nullptr, double* guess_res = nullptr);
+               int* accepted = nullptr, double* guess_res = nullptr, bool from_prev = false);
 void panel_currents(xrl_ctx* c, bool normalize, double* host_out);
 void panel_features(xrl_ctx* c, int nf, const double* freq, double f0, const double* d_ip0, float* d_feat,
                     double* h_scale, cudaStream_t s);
