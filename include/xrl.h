@@ -217,12 +217,17 @@ typedef struct {
   int32_t tc_targets_per_cta; /* targets per CTA of the FP32 tensor-core M2L and near field (2: sibling
                                  pairs share a CTA where the coefficients / padded leaves are <= 64;
                                  1: one each), as xrl_autotune chose it; 2 before any autotune */
+  double setup_phase_ms[6]; /* the last setup's host wall time by phase: 0 PEEC topology and loops,
+                               1 panel geometry, Morton order and octree, 2 near-field fill, 3 moments
+                               and translation operators (incl. tensor-core images), 4 preconditioner
+                               pencil and band, 5 solver operator data */
 } xrl_stats;
 
 /* FMM autotuner: tries leaf_target in {16, 32, 64} x fmm_order in {4, 6, 7, 8}
  * (with the context's separation rule), re-running xrl_setup for each.  A candidate is admissible
  * when its FP64 product matches the FP64 direct sum (xrl_direct_mvm_device) on
- * two seeded random columns to mvm_tol (relative 2-norm).  Each admissible
+ * two seeded random columns to mvm_tol (relative 2-norm; above 32,768 panels
+ * the norm is taken over 1024 spread rows, whose direct sums are computed).  Each admissible
  * candidate's product at n_cols columns is timed with CUDA events in the
  * precision the solver's products use (FP32 if `precision` = 1, the
  * FP64-accurate tensor-core product if 2, else FP64); in FP32 each candidate

@@ -346,12 +346,22 @@ xrl_status xrl_setup(xrl_ctx* c) {
     c->p = c->opt.fmm_order;
     c->ncoef = (c->p + 1) * (c->p + 1);
     c->d = Dev();
+    double tp = now_ms();
+    auto lap = [&](int k) {
+      const double t = now_ms();
+      c->stats.setup_phase_ms[k] = t - tp;
+      tp = t;
+    };
     build_topology(c);
+    lap(0);
     upload_rule_tables(c);
     launch_geometry(c);
+    lap(1);
     launch_near_fill(c);
+    lap(2);
     launch_moments(c);
     fmm_prepare(c);
+    lap(3);
     const double tq = now_ms();
     std::vector<int32_t> iota(c->N);
     std::iota(iota.begin(), iota.end(), 0);
@@ -377,8 +387,10 @@ xrl_status xrl_setup(xrl_ctx* c) {
     band_prepare(c);
     XRL_CUDA(cudaStreamSynchronize(c->stream));
     c->stats.precond_setup_ms = now_ms() - tq;
+    lap(4);
     solver_prepare(c);
     XRL_CUDA(cudaStreamSynchronize(c->stream));
+    lap(5);
     const Topo& T = c->topo;
     c->stats.n_panels = c->N;
     c->stats.n_live = T.n_live;
@@ -495,11 +507,31 @@ xrl_status xrl_autotune(xrl_ctx* c, int32_t nc, double tol, int32_t precision, i
     }
     DBuf<double> dx, dref, dy;
     dx.upload(c->alloc, hx);
-    dref.alloc(c->alloc, hx.size());
     dy.alloc(c->alloc, hx.size());
-    XRL_CHECK(xrl_direct_mvm_device(c, nref, dx.p, dref.p, nullptr) == XRL_OK, XRL_ECUDA, c->err);
-    XRL_CUDA(cudaStreamSynchronize(c->stream));
-    std::vector<double> ref = dref.download();
+    // reference: the whole direct sum, or for large meshes (an O(N^2) sum of
+    // minutes) the direct sum at 1024 spread target rows
+    const bool sampled = N > 32768;
+    std::vector<int32_t> rows;   // caller indices of the reference rows
+    std::vector<double> ref;     // sampled: [row][nref]; else [nref][N] caller order
+    if (sampled) {
+      const int nr = 1024;
+      const int64_t stride = 1000003;   // prime: distinct rows for any N < stride * nr
+      for (int i = 0; i < nr; ++i) rows.push_back((int32_t)(((int64_t)i * stride + 17) % N));
+      std::vector<int32_t> mr(nr);
+      for (int i = 0; i < nr; ++i) mr[i] = c->tree.rank[rows[i]];
+      DBuf<int32_t> drows;
+      drows.upload(c->alloc, mr);
+      c->d.X.ensure(c->alloc, (size_t)N * nref);
+      dref.alloc(c->alloc, (size_t)nr * nref);
+      launch_to_morton(c, nref, dx.p, c->d.X.p, c->stream);
+      launch_direct_rows(c, nr, drows.p, nref, c->d.X.p, dref.p, c->stream);
+      XRL_CUDA(cudaStreamSynchronize(c->stream));
+    } else {
+      dref.alloc(c->alloc, hx.size());
+      XRL_CHECK(xrl_direct_mvm_device(c, nref, dx.p, dref.p, nullptr) == XRL_OK, XRL_ECUDA, c->err);
+      XRL_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    ref = dref.download();
     double rn = 0.0;
     for (double v : ref) rn += v * v;
     rn = std::sqrt(rn);
@@ -519,7 +551,15 @@ xrl_status xrl_autotune(xrl_ctx* c, int32_t nc, double tol, int32_t precision, i
         XRL_CUDA(cudaStreamSynchronize(c->stream));
         std::vector<double> y = dy.download();
         double en = 0.0;
-        for (size_t k = 0; k < y.size(); ++k) en += (y[k] - ref[k]) * (y[k] - ref[k]);
+        if (sampled) {
+          for (size_t i = 0; i < rows.size(); ++i)
+            for (int q = 0; q < nref; ++q) {
+              const double d = y[(size_t)q * N + rows[i]] - ref[i * nref + q];
+              en += d * d;
+            }
+        } else {
+          for (size_t k = 0; k < y.size(); ++k) en += (y[k] - ref[k]) * (y[k] - ref[k]);
+        }
         double err = std::sqrt(en) / rn;
         double ms = -1.0;
         int tct = 2;

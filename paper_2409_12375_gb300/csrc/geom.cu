@@ -361,9 +361,12 @@ __global__ void k_near_fill(PanelView pv, const int32_t* __restrict__ leaf_first
   }
 }
 
-// FP64 direct sum with the rule table: one block per target (Morton rank k)
-__global__ void k_direct(PanelView pv, int N, int nc, const double* __restrict__ X, double* __restrict__ Y) {
-  int k = blockIdx.x;
+// FP64 direct sum with the rule table: one block per target, Morton rank
+// k = rows[blockIdx.x] (rows = NULL: k = blockIdx.x), output row blockIdx.x
+__global__ void k_direct(PanelView pv, int N, int nc, const int32_t* __restrict__ rows, const double* __restrict__ X,
+                         double* __restrict__ Y) {
+  const int k = rows ? rows[blockIdx.x] : (int)blockIdx.x;
+  const int ko = blockIdx.x;
   extern __shared__ double red[];
   double acc[8];
   for (int c0 = 0; c0 < nc; c0 += 8) {
@@ -380,7 +383,7 @@ __global__ void k_direct(PanelView pv, int N, int nc, const double* __restrict__
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
       }
-      if (threadIdx.x == 0) Y[(size_t)k * nc + c0 + c] = red[0];
+      if (threadIdx.x == 0) Y[(size_t)ko * nc + c0 + c] = red[0];
       __syncthreads();
     }
   }
@@ -627,7 +630,14 @@ std::vector<double> pair_entries(xrl_ctx* c, const std::vector<int32_t>& k, cons
 }
 
 void launch_direct(xrl_ctx* c, int nc, const double* X, double* Y, cudaStream_t s) {
-  k_direct<<<c->N, 256, 256 * sizeof(double), s>>>(view(c), c->N, nc, X, Y);
+  k_direct<<<c->N, 256, 256 * sizeof(double), s>>>(view(c), c->N, nc, nullptr, X, Y);
+  XRL_CUDA(cudaGetLastError());
+}
+
+void launch_direct_rows(xrl_ctx* c, int nrows, const int32_t* rows, int nc, const double* X, double* Y,
+                        cudaStream_t s) {
+  if (nrows <= 0) return;
+  k_direct<<<nrows, 256, 256 * sizeof(double), s>>>(view(c), c->N, nc, rows, X, Y);
   XRL_CUDA(cudaGetLastError());
 }
 

@@ -341,6 +341,9 @@ void launch_geometry(xrl_ctx* c);              // computes panel data + keys (ca
 void launch_near_fill(xrl_ctx* c);             // near-field blocks (rule table)
 void launch_moments(xrl_ctx* c);               // P2M/L2P moment table
 void launch_direct(xrl_ctx* c, int ncols, const double* x, double* y, cudaStream_t s);
+// rows [nrows] Morton ranks; Y [nrows][nc]
+void launch_direct_rows(xrl_ctx* c, int nrows, const int32_t* rows, int nc, const double* X, double* Y,
+                        cudaStream_t s);
 std::vector<double> pair_entries(xrl_ctx* c, const std::vector<int32_t>& k_caller,
                                  const std::vector<int32_t>& l_caller);   // P entries of panel pairs
 void upload_rule_tables(xrl_ctx* c);

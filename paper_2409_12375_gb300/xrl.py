@@ -43,10 +43,12 @@ class Stats(ctypes.Structure):
                 ("max_rel_res", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("mvm_ms", ctypes.c_double), ("peak_device_bytes", ctypes.c_int64),
                 ("near_nnz_padded", ctypes.c_int64), ("precond_setup_ms", ctypes.c_double),
-                ("tc_targets_per_cta", ctypes.c_int32)]
+                ("tc_targets_per_cta", ctypes.c_int32), ("setup_phase_ms", ctypes.c_double * 6)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {k: getattr(self, k) for k, _ in self._fields_}
+        out["setup_phase_ms"] = list(self.setup_phase_ms)
+        return out
 
 
 def library_path():
