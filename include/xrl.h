@@ -58,12 +58,15 @@ typedef struct {
                           cores and FP32 pipes (the integer-slice and double-float kernels of mode 1's
                           residuals), no FP32 inner iterations */
   int32_t precond;     /* 0: none; 1: diagonal-of-P preconditioner of eq. 10 applied exactly (banded
-                          LDL^T of the RCM-ordered vertex loops + Schur border; falls back to 2 when
-                          the band is not usable); 2: eq. 10 applied inexactly by Jacobi-preconditioned
+                          LDL^T of the RCM-ordered vertex loops + Schur border); 2: eq. 10 applied
+                          inexactly by Jacobi-preconditioned
                           COCG; 3: the diagonal-of-L preconditioner of Sec. II-D / Table IV,
                           Z_s + j omega L_d (loop-space surface impedance of eq. 8 kept whole, L_d the
                           diagonal of the branch-branch inductance sum_t A_t mu0/4pi P A_t^T), applied
-                          like 1 (COCG when the band is not usable) */
+                          like 1; 4: eq. 10 applied by one smoothed-aggregation multigrid V-cycle
+                          (FP32).  1 and 3 take the multigrid V-cycle of their own matrix where the
+                          band form is not usable (band wider than 63 or more than 16 global loops,
+                          as on planes with many holes) */
   int32_t restart;     /* FGMRES restart length m, default 50 (Sec. III uses restart 50) */
   int32_t max_iters;   /* total outer iterations per solve, default 500 */
   int32_t inner_iters; /* max inner COCG iterations per preconditioner apply, default 60 */
@@ -221,6 +224,8 @@ typedef struct {
                                1 panel geometry, Morton order and octree, 2 near-field fill, 3 moments
                                and translation operators (incl. tensor-core images), 4 preconditioner
                                pencil and band, 5 solver operator data */
+  int32_t mg_levels;        /* levels of the multigrid hierarchy of Q (0: none built) */
+  int32_t mg_coarse_n;      /* unknowns of its coarsest level */
 } xrl_stats;
 
 /* FMM autotuner: tries leaf_target in {16, 32, 64} x fmm_order in {4, 6, 7, 8}

@@ -558,3 +558,11 @@ def package(size=10e-3, t=35e-6, n_holes=400, r_hole=0.1e-3, hole_gap=0.05e-3, n
     return Mesh(xyz=np.array(bld.pts), tri=tri.astype(np.int32), cond=np.array(conds, np.int32), term=term,
                 ports=ports, sigma=np.full(cid, sigma), thickness=np.array(thick),
                 freqs=np.geomspace(fmin, fmax, n_freq), name="package")
+
+
+def package_crop(seed=3) -> Mesh:
+    """A 2.8 x 2.8 mm window of the package family at the same panel size and
+    feature densities (31 holes, 3 x 3 balls, 4 traces with 2 ports; ~21k
+    triangles), small enough for the dense oracle."""
+    return package(size=2.8e-3, n_holes=31, n_balls=3, n_traces=4, n_ports=2, trace_len=(1.0e-3, 2.2e-3),
+                   seed=seed)

@@ -214,7 +214,7 @@ xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {
     XRL_CHECK(c->opt.mac_theta >= 0.0 && c->opt.mac_theta < 1.0, XRL_EINVAL, "mac_theta must be in [0, 1)");
     XRL_CHECK(c->opt.rhs_chunk >= 0, XRL_EINVAL, "rhs_chunk must be >= 0");
     XRL_CHECK(c->opt.warm_start == 0 || c->opt.warm_start == 1, XRL_EINVAL, "warm_start must be 0 or 1");
-    XRL_CHECK(c->opt.precond >= 0 && c->opt.precond <= 3, XRL_EINVAL, "precond must be in [0, 3]");
+    XRL_CHECK(c->opt.precond >= 0 && c->opt.precond <= 4, XRL_EINVAL, "precond must be in [0, 4]");
     XRL_CHECK(c->opt.precision >= 0 && c->opt.precision <= 2, XRL_EINVAL, "precision must be 0, 1 or 2");
     XRL_CHECK(c->opt.tol > 0 && c->opt.restart >= 1 && c->opt.max_iters >= 1, XRL_EINVAL, "bad solver options");
     int n = 0;
@@ -385,6 +385,10 @@ xrl_status xrl_setup(xrl_ctx* c) {
     }
     build_band(c);
     band_prepare(c);
+    if (c->opt.precond == 4 || ((c->opt.precond == 1 || c->opt.precond == 3) && !band_usable(c)))
+      amg_prepare(c);
+    else
+      c->amg = AmgHier();
     XRL_CUDA(cudaStreamSynchronize(c->stream));
     c->stats.precond_setup_ms = now_ms() - tq;
     lap(4);
@@ -403,6 +407,8 @@ xrl_status xrl_setup(xrl_ctx* c) {
     c->stats.n_vertex_loops = T.n_vertex_loops;
     c->stats.n_global_loops = T.n_global_loops;
     c->stats.tc_targets_per_cta = c->tc_targets;
+    c->stats.mg_levels = (int)c->amg.lv.size();
+    c->stats.mg_coarse_n = c->amg.lv.empty() ? 0 : c->amg.lv.back().n;
     c->stats.setup_ms = now_ms() - t0;
     c->ready = true;
   });
@@ -841,6 +847,7 @@ void xrl_destroy(xrl_ctx* c) {
   }
   if (c->stream2) cudaStreamSynchronize(c->stream2);
   c->d = Dev();
+  c->amg = AmgHier();
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->stream2) cudaStreamDestroy(c->stream2);

@@ -691,8 +691,9 @@ struct Work {
   DBuf<double> freq, wp, wpf;
   DBuf<cplx> zs, zsf;
   BandWork bw;
+  AmgWork aw;
   int nport = 1;
-  bool banded = false;
+  bool banded = false, use_amg = false;
   DBuf<cplx> b, x, w, tmp, V, Z, H, h1, h2, cs, sn, g, y, Vb, dinv, zst;
   DBuf<cplx> cz, cr, cp, cq, crho;
   DBuf<double> X, Y, bnorm, resid, cvn, thr;
@@ -787,6 +788,12 @@ static void apply_Qinv(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* z) {
     band_apply(c, wk.bw, nsys, wk.nport, wk.zsf.p, wk.wpf.p, v, z, wk.active.p, s);
     return;
   }
+  if (wk.use_amg) {
+    cudaEvent_t ev = prof_begin(c, s);
+    amg_apply(c, wk.aw, nsys, wk.nport, v, z, s);
+    prof_end(c, s, ev, PH_PREC, 0, 0.0, 0.0);
+    return;
+  }
   const size_t tot = (size_t)n * nsys;
   wk.cr.ensure(c->alloc, tot);
   wk.cp.ensure(c->alloc, tot);
@@ -875,9 +882,13 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
   wk.iters.alloc(c->alloc, nsys);
   wk.kcols.alloc(c->alloc, nsys);
   wk.banded = (c->opt.precond == 1 || c->opt.precond == 3) && band_usable(c);
+  wk.use_amg = !wk.banded && c->opt.precond != 0 && c->opt.precond != 2 && c->amg.ready;
   if (wk.banded) {
     band_alloc(c, wk.bw, nf, nsys, mixed);
     band_factor(c, wk.bw, wk.zsf.p, wk.wpf.p, s);
+  } else if (wk.use_amg) {
+    amg_factor(c, wk.aw, nf, nsys, wk.zsf.p, wk.wpf.p, s);
+    amg_check(c, wk.aw, s);
   } else if (c->opt.precond) {
     wk.dinv.alloc(c->alloc, tot);
     apply_Qmat(c, wk, nsys, nullptr, wk.w.p, 1);

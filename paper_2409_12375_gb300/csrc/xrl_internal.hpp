@@ -253,6 +253,32 @@ struct Dev {
   DBuf<double2> last_x;      // loop currents of the last solve [nsys][n_loops]
 };
 
+// Multigrid hierarchy of the preconditioner pencil (amg.cu): per level the
+// pencil [nnz][n_mat + 1] over its unknowns and the transfer to the next level.
+struct AmgLevel {
+  int n = 0, nc = 0;
+  int64_t nnz = 0;
+  bool coarsest = false;
+  DBuf<int32_t> ptr, col;
+  DBuf<double> pen;
+  DBuf<int64_t> dpos;                      // position of each row's diagonal (-1 none)
+  DBuf<int32_t> p_ptr, p_col, r_ptr, r_col;
+  DBuf<float> p_val, r_val;
+};
+struct AmgHier {
+  std::vector<AmgLevel> lv;
+  int W = 0;
+  bool ready = false;
+};
+struct AmgLevelWork {
+  DBuf<float2> vals, dinv, x, b, r, aug;
+};
+struct AmgWork {
+  int nf = 0;
+  std::vector<AmgLevelWork> lv;
+  DBuf<int32_t> err;
+};
+
 // Phase profiler: CUDA event pairs on the launching stream plus algorithmic work.
 enum Phase { PH_P2P = 0, PH_P2M, PH_M2M, PH_M2L, PH_L2L, PH_L2P, PH_OPER, PH_PREC, PH_KRYLOV, PH_P2P64, PH_M2L64,
              PH_COUNT };
@@ -303,6 +329,7 @@ struct xrl_ctx {
   xrl::Tree tree;
   xrl::Topo topo;
   xrl::Dev d;
+  xrl::AmgHier amg;
   xrl_stats stats;
   xrl::Prof prof;
   std::vector<double> gl_nodes;   // host GL tables for the rule table (set in setup)
@@ -395,4 +422,9 @@ void band_alloc(xrl_ctx* c, BandWork& bw, int nf, int nsys, bool mixed);
 void band_factor(xrl_ctx* c, BandWork& bw, const double2* zs, const double* wp, cudaStream_t s);
 void band_apply(xrl_ctx* c, BandWork& bw, int nsys, int nport, const double2* zs, const double* wp,
                 const double2* v, double2* z, const int* active, cudaStream_t s);
+// amg.cu: multigrid V-cycle for Q^-1 where the band form is not usable
+void amg_prepare(xrl_ctx* c);
+void amg_factor(xrl_ctx* c, AmgWork& w, int nf, int nsys, const double2* zsf, const double* wpf, cudaStream_t s);
+void amg_apply(xrl_ctx* c, AmgWork& w, int nsys, int nport, const double2* v, double2* z, cudaStream_t s);
+void amg_check(xrl_ctx* c, AmgWork& w, cudaStream_t s);
 }  // namespace xrl
