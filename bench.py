@@ -77,6 +77,21 @@ def workload(rank=0, world=1):
     return m
 
 
+def gather_sweep(R, L, world):
+    """R, L of the whole sweep on every rank, in frequency order: rank r
+    solved frequencies r, r + world, ... of the longer sweep (workload())."""
+    import torch.distributed as dist
+    parts = [None] * world
+    dist.all_gather_object(parts, (np.asarray(R), np.asarray(L)))
+    nf = sum(p[0].shape[0] for p in parts)
+    Ra = np.empty((nf,) + parts[0][0].shape[1:])
+    La = np.empty_like(Ra)
+    for r, (Rr, Lr) in enumerate(parts):
+        Ra[r::world] = Rr
+        La[r::world] = Lr
+    return Ra, La
+
+
 def config_dict(m, precision, opts):
     return {"workload": "two 4-turn square planar copper coils, %d triangles, 2 ports x %d freqs "
                         "(100 Hz-10 GHz), one 64-RHS block, tol 1e-8" % (m.n_tri, len(m.freqs)),
@@ -591,6 +606,10 @@ def main():
     if world > 1:
         dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
     dev_ms, host_s = float(t_dev[0]), float(t_dev[1])
+    gathered = None
+    if world > 1:
+        Ra, La = gather_sweep(R, L, world)
+        gathered = {"n_freqs": int(Ra.shape[0]), "R_fmax": Ra[-1].tolist(), "L_fmax": La[-1].tolist()}
     units = args.steps * nsys * world
     value = (dev_ms / 1e3) / units
     e2e = host_s / units
@@ -694,7 +713,7 @@ def main():
                         "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * len(m.ports) ** 2},
                 "gpu_launches": tm["launches"], "clocks": ck, "roofline": roof, "roofline_phases": roofs,
                 "cpu_baseline": cb, "fmm_mvm_fp64": mvm, "arms": arms,
-                "oracle_rl_error": oracle_rl_error(m, R, L),
+                "oracle_rl_error": oracle_rl_error(m, R, L), "sweep_gathered": gathered,
                 "precond_ablation": abl, "hybrid_panels": hyb,
                 "solve": {"fgmres_iters": tm["iters"], "max_rel_residual": tm["res"], "setup_ms": st["setup_ms"],
                           "n_loops": st["n_loops"], "near_nnz": st["near_nnz"],

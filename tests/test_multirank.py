@@ -1,7 +1,8 @@
 """The N > 1 benchmark path on CPU with gloo, world size 2: each rank takes a
 disjoint frequency chunk of an N-times longer sweep (replicas over
-frequencies, no collective on the data path), and the step time is the
-maximum over ranks."""
+frequencies, no collective on the data path), the step time is the
+maximum over ranks, and the ranks' R and L gather into the one-rank sweep's
+frequency order."""
 import os
 import socket
 
@@ -30,8 +31,12 @@ def _worker(rank, world, port, out):
     dist.all_gather(gathered, f)
     t = torch.tensor([1.0 + rank], dtype=torch.float64)      # stand-in step times
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    # stand-in R, L [n_f][2][2] of this rank's frequencies, a known function of f
+    R = np.stack([np.full((2, 2), f) for f in m.freqs])
+    L = np.stack([np.full((2, 2), 1.0 / f) for f in m.freqs])
+    Ra, La = bench.gather_sweep(R, L, world)
     if rank == 0:
-        out.put((torch.cat(gathered).numpy(), float(t[0]), m.n_tri))
+        out.put((torch.cat(gathered).numpy(), float(t[0]), m.n_tri, Ra, La))
     dist.destroy_process_group()
 
 
@@ -42,10 +47,13 @@ def test_two_ranks_split_the_sweep():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    allf, tmax, ntri = q.get(timeout=300)
+    allf, tmax, ntri, Ra, La = q.get(timeout=300)
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
     ref = np.geomspace(100.0, 1e10, 64)
     assert np.array_equal(np.sort(allf), ref)       # disjoint and complete
     assert len(allf) == 64 and tmax == 2.0
+    # the gathered sweep is the one-rank sweep, in its frequency order
+    assert Ra.shape == (64, 2, 2)
+    assert np.array_equal(Ra[:, 0, 0], ref) and np.array_equal(La[:, 1, 1], 1.0 / ref)
