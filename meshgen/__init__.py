@@ -5,4 +5,4 @@ material constants and frequency lists that both the CUDA library and the CPU
 oracle consume.  It contains geometry construction only: no panel integral,
 no impedance, no topology of the PEEC graph and no solver arithmetic.
 """
-from .shapes import Mesh, bar, two_bars, coils, package, package_crop, crop_check, panel_edges  # noqa: F401
+from .shapes import Mesh, bar, two_bars, coils, package, package_crop, pop, crop_check, panel_edges  # noqa: F401

@@ -566,3 +566,72 @@ def package_crop(seed=3) -> Mesh:
     triangles), small enough for the dense oracle."""
     return package(size=2.8e-3, n_holes=31, n_balls=3, n_traces=4, n_ports=2, trace_len=(1.0e-3, 2.2e-3),
                    seed=seed)
+
+
+def pop(size=15e-3, t=35e-6, plane_gap=0.2e-3, n_holes=1000, r_hole=0.1e-3, hole_gap=0.05e-3, n_balls=12,
+        r_ball=0.2e-3, pitch=1.0e-3, stack_gap=0.5e-3, n_traces=64, trace_w=50e-6, trace_lift=0.1e-3,
+        trace_len=(4e-3, 10e-3), n_ports=16, h=42e-6, sphere_level=2, sigma=5.8e7, n_freq=64, fmin=1e3,
+        fmax=1e10, seed=5) -> Mesh:
+    """Package-on-package stack: two substrates, each with two perforated
+    ground planes (plane_gap apart; n_holes seeded holes over the four
+    planes), an n_balls x n_balls solder-ball array between the substrates,
+    and n_traces straight traces, half above each substrate; the first
+    n_ports traces carry a port (far end cap source, near end cap sink).
+    Conductor ids: the four planes, the balls, then the traces."""
+    rng = np.random.default_rng(seed)
+    bld = _Builder(False)
+    conds, thick = [], []
+    cid = 0
+    per = n_holes // 4
+    # substrate s: planes at z_s and z_s + plane_gap + t; the upper substrate
+    # sits above the balls
+    sub_h = plane_gap + 2 * t
+    z_sub = [0.0, sub_h + stack_gap + 2 * r_ball]
+    for zs in z_sub:
+        for zp in (zs, zs + plane_gap + t):
+            n0 = len(bld.tris)
+            holes = _hole_centres(rng, size, per, r_hole, hole_gap, r_hole + hole_gap)
+            _plane(bld, size, t, zp, holes, r_hole, h, rng, cid)
+            conds += [cid] * (len(bld.tris) - n0)
+            thick.append(t)
+            cid += 1
+    off = (size - (n_balls - 1) * pitch) / 2
+    zb = z_sub[0] + plane_gap + t + t / 2 + stack_gap / 2 + r_ball
+    for i in range(n_balls):
+        for j in range(n_balls):
+            n0 = len(bld.tris)
+            _icosphere(bld, (off + i * pitch, off + j * pitch, zb), r_ball, sphere_level, cid)
+            conds += [cid] * (len(bld.tris) - n0)
+            thick.append(2 * r_ball / 3)
+            cid += 1
+    ports = []
+    lanes = list(np.arange(0.5e-3, size - 0.5e-3, 4 * trace_w * 3))
+    lane_pool = {(s_, d): list(rng.permutation(lanes)) for s_ in range(2) for d in range(2)}
+    first_trace = cid
+    for k in range(n_traces):
+        s_ = k % 2                      # substrate
+        d = (k // 2) % 2                # direction: x or y
+        L = rng.uniform(*trace_len)
+        top = z_sub[s_] + plane_gap + t + t / 2
+        z = top + trace_lift + t / 2 + (2 * t if d else 0.0)
+        lane = lane_pool[(s_, d)].pop()
+        a0 = rng.uniform(0.2e-3, size - 0.2e-3 - L)
+        corners = [(a0, lane), (a0 + L, lane)] if d == 0 else [(lane, a0), (lane, a0 + L)]
+        n0 = len(bld.tris)
+        _swept_trace(bld, corners, z, trace_w, t, 1, 1, h, 0, cid, (2 * k, 2 * k + 1))
+        conds += [cid] * (len(bld.tris) - n0)
+        thick.append(2 * trace_w * t / (2 * (trace_w + t)))
+        if k < n_ports:
+            ports.append((2 * k + 1, 2 * k))
+        cid += 1
+    tri = np.array(bld.tris, np.int64)
+    tags = np.array(bld.tags, np.int64)
+    is_trace = np.array(conds) >= first_trace
+    tri[is_trace] = tri[is_trace][:, [0, 2, 1]]
+    used = sorted({s_ for s_, _ in ports} | {k_ for _, k_ in ports})
+    remap = {o: n for n, o in enumerate(used)}
+    term = np.array([remap.get(int(x), -1) if x >= 0 else -1 for x in tags], np.int32)
+    ports = [(remap[s_], remap[k_]) for s_, k_ in ports]
+    return Mesh(xyz=np.array(bld.pts), tri=tri.astype(np.int32), cond=np.array(conds, np.int32), term=term,
+                ports=ports, sigma=np.full(cid, sigma), thickness=np.array(thick),
+                freqs=np.geomspace(fmin, fmax, n_freq), name="pop")

@@ -25,8 +25,8 @@
 // Apply (device, FP32 complex): per frequency the level matrices' values and
 // Jacobi diagonals are combined from the pencils once per solve, and the
 // coarsest matrix is inverted (Gauss-Jordan with partial pivoting, one CTA per
-// frequency); one V-cycle per preconditioner application with nu damped
-// Jacobi sweeps before and after the coarse correction.
+// frequency); per preconditioner application opt.mg_cycles V-cycles, each
+// with kSweeps damped Jacobi sweeps before and after the coarse correction.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -511,6 +511,10 @@ void amg_factor(xrl_ctx* c, AmgWork& w, int nf, int nsys, const cplx* zsf, const
     k_amg_vals<<<dim3(nb256(L.nnz), nf), 256, 0, s>>>(L.nnz, H.W, nf, L.pen.p, zsf, wpf, K.vals.p);
     k_amg_dinv<<<dim3(nb256(L.n), nf), 256, 0, s>>>(L.n, L.nnz, L.dpos.p, K.vals.p, K.dinv.p);
     count_launch(c, 2);
+    if (l == 0 && c->opt.mg_cycles > 1) {
+      w.bsave.alloc(c->alloc, (size_t)nsys * L.n);
+      w.xacc.alloc(c->alloc, (size_t)nsys * L.n);
+    }
     if (L.coarsest && L.n <= kCoarse) {
       K.aug.alloc(c->alloc, (size_t)nf * L.n * 2 * L.n);
       k_amg_dense<<<dim3(std::min(L.n, 1024), nf), 256, 0, s>>>(L.n, L.nnz, L.ptr.p, L.col.p, K.vals.p, K.aug.p);
@@ -523,13 +527,15 @@ void amg_factor(xrl_ctx* c, AmgWork& w, int nf, int nsys, const cplx* zsf, const
   XRL_CUDA(cudaGetLastError());
 }
 
-// z ~= Q^-1 v: one V-cycle per system (v, z [nsys][n_loops] FP64 complex)
-void amg_apply(xrl_ctx* c, AmgWork& w, int nsys, int nport, const cplx* v, cplx* z, cudaStream_t s) {
+__global__ void k_amg_axpy(size_t n, const float2* __restrict__ a, float2* __restrict__ b, int init) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = init ? a[i] : fadd(b[i], a[i]);
+}
+
+// one V-cycle: w.lv[0].x = V(w.lv[0].b)
+static void vcycle(xrl_ctx* c, AmgWork& w, int nsys, int nport, cudaStream_t s) {
   AmgHier& H = c->amg;
   const int nl = (int)H.lv.size();
-  const size_t n0 = (size_t)H.lv[0].n * nsys;
-  k_amg_to32<<<nb256(n0), 256, 0, s>>>(n0, v, w.lv[0].b.p);
-  count_launch(c);
   // downward: pre-smooth, restrict the residual
   for (int l = 0; l < nl; ++l) {
     AmgLevel& L = H.lv[l];
@@ -576,7 +582,36 @@ void amg_apply(xrl_ctx* c, AmgWork& w, int nsys, int nport, const cplx* v, cplx*
     }
     count_launch(c, 1 + 2 * kSweeps);
   }
-  k_amg_to64<<<nb256(n0), 256, 0, s>>>(n0, w.lv[0].x.p, z);
+  XRL_CUDA(cudaGetLastError());
+}
+
+// z ~= Q^-1 v by opt.mg_cycles V-cycles (the later ones on the level-0
+// residual); v, z [nsys][n_loops] FP64 complex
+void amg_apply(xrl_ctx* c, AmgWork& w, int nsys, int nport, const cplx* v, cplx* z, cudaStream_t s) {
+  AmgHier& H = c->amg;
+  AmgLevel& L0 = H.lv[0];
+  AmgLevelWork& K0 = w.lv[0];
+  const size_t n0 = (size_t)L0.n * nsys;
+  const int ncyc = std::max(1, c->opt.mg_cycles);
+  k_amg_to32<<<nb256(n0), 256, 0, s>>>(n0, v, ncyc > 1 ? w.bsave.p : K0.b.p);
+  count_launch(c);
+  if (ncyc > 1) {
+    k_amg_axpy<<<nb256(n0), 256, 0, s>>>(n0, w.bsave.p, K0.b.p, 1);
+    count_launch(c);
+  }
+  vcycle(c, w, nsys, nport, s);
+  for (int cy = 1; cy < ncyc; ++cy) {
+    k_amg_axpy<<<nb256(n0), 256, 0, s>>>(n0, K0.x.p, w.xacc.p, cy == 1);
+    k_amg_resid<<<nb256(n0), 256, 0, s>>>(L0.n, nsys, nport, L0.nnz, L0.ptr.p, L0.col.p, K0.vals.p, w.bsave.p,
+                                          w.xacc.p, K0.b.p);
+    count_launch(c, 2);
+    vcycle(c, w, nsys, nport, s);
+  }
+  if (ncyc > 1) {
+    k_amg_axpy<<<nb256(n0), 256, 0, s>>>(n0, K0.x.p, w.xacc.p, 0);
+    count_launch(c);
+  }
+  k_amg_to64<<<nb256(n0), 256, 0, s>>>(n0, ncyc > 1 ? w.xacc.p : K0.x.p, z);
   count_launch(c);
   XRL_CUDA(cudaGetLastError());
 }

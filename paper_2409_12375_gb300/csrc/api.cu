@@ -193,6 +193,7 @@ void xrl_default_options(xrl_options* o) {
   o->tensor_cores = 1;
   o->mac_theta = 0.0;
   o->rhs_chunk = 0;
+  o->mg_cycles = 1;
 }
 
 xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {
@@ -213,6 +214,7 @@ xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {
     XRL_CHECK(c->opt.separation == 1 || c->opt.separation == 2, XRL_EINVAL, "separation must be 1 or 2");
     XRL_CHECK(c->opt.mac_theta >= 0.0 && c->opt.mac_theta < 1.0, XRL_EINVAL, "mac_theta must be in [0, 1)");
     XRL_CHECK(c->opt.rhs_chunk >= 0, XRL_EINVAL, "rhs_chunk must be >= 0");
+    XRL_CHECK(c->opt.mg_cycles >= 1 && c->opt.mg_cycles <= 8, XRL_EINVAL, "mg_cycles must be in [1, 8]");
     XRL_CHECK(c->opt.warm_start == 0 || c->opt.warm_start == 1, XRL_EINVAL, "warm_start must be 0 or 1");
     XRL_CHECK(c->opt.precond >= 0 && c->opt.precond <= 4, XRL_EINVAL, "precond must be in [0, 4]");
     XRL_CHECK(c->opt.precision >= 0 && c->opt.precision <= 2, XRL_EINVAL, "precision must be 0, 1 or 2");

@@ -334,31 +334,82 @@ __global__ void k_gather_panels(int N, const int32_t* __restrict__ perm, const d
   cidx[r] = p;
 }
 
-// near-field fill: one block per leaf, one thread per (target, source) entry
-__global__ void k_near_fill(PanelView pv, const int32_t* __restrict__ leaf_first, const int32_t* __restrict__ leaf_count,
+// Near-field fill in three passes, so that the threads of a warp evaluate
+// entries of one class of the rule table (its classes differ in cost by two
+// orders of magnitude; mixed in one warp, every warp paid for the dearest):
+//  1. k_near_count: per leaf, the number of its entries in each class;
+//  2. k_near_list: the entries (value position, target, source) in lists
+//     ordered by class, then leaf (within a leaf in any order);
+//  3. k_near_eval: every listed entry by p_entry, the same function as before,
+//     so the values do not depend on the grouping.
+// Classes: 0 self, 1 triangles sharing a vertex, 2 q < kQNear, 3 q < kQSemi,
+// 4 q < kQFar, 5 far, 6 a rectangle involved (general path).
+constexpr int kNearClasses = 7;
+
+__device__ int near_class(const PanelView& pv, int k, int j) {
+  if (k == j) return 0;
+  if (n_sub(pv, k) > 1 || n_sub(pv, j) > 1) return 6;
+  const int32_t* tk = pv.tri + 4 * (size_t)k;
+  const int32_t* tj = pv.tri + 4 * (size_t)j;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      if (tk[a] == tj[b]) return 1;
+  const double* ck = pv.cen + 3 * (size_t)k;
+  const double* cj = pv.cen + 3 * (size_t)j;
+  const double dx = __dsub_rn(ck[0], cj[0]), dy = __dsub_rn(ck[1], cj[1]), dz = __dsub_rn(ck[2], cj[2]);
+  const double d = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+  const double q = __ddiv_rn(d, __dadd_rn(pv.radius[k], pv.radius[j]));
+  return q < kQNear ? 2 : q < kQSemi ? 3 : q < kQFar ? 4 : 5;
+}
+
+// one block per leaf: its entries, U-list source by U-list source
+__global__ void k_near_count(PanelView pv, const int32_t* __restrict__ leaf_first, const int32_t* __restrict__ leaf_count,
+                             const int32_t* __restrict__ u_ptr, const int32_t* __restrict__ u_src,
+                             int32_t* __restrict__ cnt) {
+  __shared__ int sc[kNearClasses];
+  const int B = blockIdx.x;
+  if (threadIdx.x < kNearClasses) sc[threadIdx.x] = 0;
+  __syncthreads();
+  const int nB = leaf_count[B], f0 = leaf_first[B];
+  for (int s = u_ptr[B]; s < u_ptr[B + 1]; ++s) {
+    const int S = u_src[s], nS = leaf_count[S], fS = leaf_first[S];
+    for (int e = threadIdx.x; e < nB * nS; e += blockDim.x)
+      atomicAdd(&sc[near_class(pv, f0 + e / nS, fS + e % nS)], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < kNearClasses) cnt[(size_t)B * kNearClasses + threadIdx.x] = sc[threadIdx.x];
+}
+
+__global__ void k_near_list(PanelView pv, const int32_t* __restrict__ leaf_first, const int32_t* __restrict__ leaf_count,
                             const int32_t* __restrict__ u_ptr, const int32_t* __restrict__ u_src,
                             const int64_t* __restrict__ near_off, const int32_t* __restrict__ near_w,
-                            double* __restrict__ val) {
-  int B = blockIdx.x;
-  int nB = leaf_count[B], f0 = leaf_first[B];
-  int w = near_w[B];
-  int64_t off = near_off[B];
-  int total = nB * w;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    int ii = e / w, jj = e % w;
-    // source panel of column jj: walk the U-list
-    int j = -1, acc = 0;
-    for (int s = u_ptr[B]; s < u_ptr[B + 1]; ++s) {
-      int S = u_src[s];
-      int n = leaf_count[S];
-      if (jj < acc + n) {
-        j = leaf_first[S] + (jj - acc);
-        break;
-      }
-      acc += n;
+                            const int64_t* __restrict__ base, int64_t* __restrict__ lpos, int32_t* __restrict__ lk,
+                            int32_t* __restrict__ lj) {
+  __shared__ unsigned long long slot[kNearClasses];
+  const int B = blockIdx.x;
+  if (threadIdx.x < kNearClasses) slot[threadIdx.x] = (unsigned long long)base[(size_t)B * kNearClasses + threadIdx.x];
+  __syncthreads();
+  const int nB = leaf_count[B], f0 = leaf_first[B], w = near_w[B];
+  const int64_t off = near_off[B];
+  int col = 0;
+  for (int s = u_ptr[B]; s < u_ptr[B + 1]; ++s) {
+    const int S = u_src[s], nS = leaf_count[S], fS = leaf_first[S];
+    for (int e = threadIdx.x; e < nB * nS; e += blockDim.x) {
+      const int ii = e / nS, jl = e % nS;
+      const int k = f0 + ii, j = fS + jl;
+      const unsigned long long i = atomicAdd(&slot[near_class(pv, k, j)], 1ull);
+      lpos[i] = off + (int64_t)ii * w + col + jl;
+      lk[i] = k;
+      lj[i] = j;
     }
-    val[off + e] = p_entry(pv, f0 + ii, j);
+    col += nS;
   }
+}
+
+__global__ void k_near_eval(PanelView pv, int64_t n, const int64_t* __restrict__ lpos, const int32_t* __restrict__ lk,
+                            const int32_t* __restrict__ lj, double* __restrict__ val) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) val[lpos[i]] = p_entry(pv, lk[i], lj[i]);
 }
 
 // FP64 direct sum with the rule table: one block per target, Morton rank
@@ -565,9 +616,34 @@ void launch_near_fill(xrl_ctx* c) {
   off.pop_back();
   c->d.near_off.upload(c->alloc, off);
   c->d.near_w.upload(c->alloc, w);
-  c->d.near_val.alloc(c->alloc, (size_t)c->stats.near_nnz);
-  k_near_fill<<<nl, 256, 0, c->stream>>>(view(c), c->d.leaf_first.p, c->d.leaf_count.p, c->d.u_ptr32.p,
-                                          c->d.u_src.p, c->d.near_off.p, c->d.near_w.p, c->d.near_val.p);
+  const int64_t nnz = c->stats.near_nnz;
+  c->d.near_val.alloc(c->alloc, (size_t)nnz);
+  if (nnz == 0) return;
+  DBuf<int32_t> cnt;
+  cnt.alloc(c->alloc, (size_t)nl * kNearClasses);
+  k_near_count<<<nl, 256, 0, c->stream>>>(view(c), c->d.leaf_first.p, c->d.leaf_count.p, c->d.u_ptr32.p,
+                                           c->d.u_src.p, cnt.p);
+  XRL_CUDA(cudaGetLastError());
+  const std::vector<int32_t> hc = cnt.download();
+  // list start of (leaf, class): classes in order, leaves in order within a class
+  std::vector<int64_t> base((size_t)nl * kNearClasses);
+  int64_t run = 0;
+  for (int k = 0; k < kNearClasses; ++k)
+    for (int i = 0; i < nl; ++i) {
+      base[(size_t)i * kNearClasses + k] = run;
+      run += hc[(size_t)i * kNearClasses + k];
+    }
+  XRL_CHECK(run == nnz, XRL_EINVAL, "internal: near-field class counts do not add up");
+  DBuf<int64_t> dbase, lpos;
+  DBuf<int32_t> lk, lj;
+  dbase.upload(c->alloc, base);
+  lpos.alloc(c->alloc, (size_t)nnz);
+  lk.alloc(c->alloc, (size_t)nnz);
+  lj.alloc(c->alloc, (size_t)nnz);
+  k_near_list<<<nl, 256, 0, c->stream>>>(view(c), c->d.leaf_first.p, c->d.leaf_count.p, c->d.u_ptr32.p,
+                                          c->d.u_src.p, c->d.near_off.p, c->d.near_w.p, dbase.p, lpos.p, lk.p, lj.p);
+  k_near_eval<<<(unsigned)((nnz + 255) / 256), 256, 0, c->stream>>>(view(c), nnz, lpos.p, lk.p, lj.p,
+                                                                      c->d.near_val.p);
   XRL_CUDA(cudaGetLastError());
   XRL_CUDA(cudaStreamSynchronize(c->stream));
 }

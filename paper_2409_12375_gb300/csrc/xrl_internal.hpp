@@ -276,6 +276,7 @@ struct AmgLevelWork {
 struct AmgWork {
   int nf = 0;
   std::vector<AmgLevelWork> lv;
+  DBuf<float2> bsave, xacc;   // right-hand side and summed correction of repeated V-cycles
   DBuf<int32_t> err;
 };
 

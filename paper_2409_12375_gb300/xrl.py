@@ -31,7 +31,7 @@ class Options(ctypes.Structure):
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("device", ctypes.c_int32), ("separation", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("tensor_cores", ctypes.c_int32),
-                ("mac_theta", ctypes.c_double), ("rhs_chunk", ctypes.c_int32)]
+                ("mac_theta", ctypes.c_double), ("mg_cycles", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

@@ -198,7 +198,7 @@ def test_hybrid_mesh_argument_errors(lib):
     finally:
         x.close()
     with pytest.raises(lib.XRLError) as e:
-        lib.XRL(precond=4)
+        lib.XRL(precond=5)
     assert e.value.code == 1
 
 
