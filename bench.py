@@ -61,6 +61,14 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --fmm-order/--leaf-target as given instead of xrl_autotune's choice (FP64 product "
                          "within 1e-6 of the direct sum, fastest inner product at the sweep's column count)")
+    ap.add_argument("--workload", default="coils", choices=["coils", "package", "package_crop", "pop"],
+                    help="coils: the default sweep; package: the BGA-like package (~250k triangles, 8 ports x 16 "
+                         "freqs); package_crop: its 2.8 mm window; pop: the package-on-package stack (~2.1M "
+                         "triangles, 16 ports x 64 freqs, frequency chunks of 64 systems)")
+    ap.add_argument("--restart", type=int, default=150, help="FGMRES restart of the package workloads")
+    ap.add_argument("--tol", type=float, default=1e-6, help="relative residual of the package workloads")
+    ap.add_argument("--freqs", type=int, default=0, help="package workloads: solve only the first N frequencies")
+    ap.add_argument("--fp64tc-arm", action="store_true", help="package workloads: one FP64-accurate sweep too")
     ap.add_argument("--kernel-case", action="store_true",
                     help="profiling case: only the FMM products of one sweep's launch configuration "
                          "(FP32 inner product and the mixed mode's FP64 residual operator, 64 systems), 3 each")
@@ -558,10 +566,102 @@ def fp64_products(pkg, x, m, pk, ext):
     return out
 
 
+def package_run(args):
+    """The package workloads (Sec. III-B, III-C stand-ins) on one GPU: the
+    chosen configuration (mixed precision, the multigrid-applied diagonal-of-P
+    preconditioner, autotuned FMM on sampled oracle-free reference rows),
+    W untimed and K timed sweeps between CUDA events, plus the FP64 and FP32
+    product rates.  The FP64 CUDA-core sweep is not run (its product at the
+    sweep's column count is timed instead: hundreds of them per sweep)."""
+    import torch
+    import meshgen
+    import paper_2409_12375_gb300 as pkg
+    m = {"package": meshgen.package, "package_crop": meshgen.package_crop, "pop": meshgen.pop}[args.workload]()
+    if args.freqs:
+        m.freqs = m.freqs[:args.freqs]
+    nport = len(m.ports)
+    nsys = len(m.freqs) * nport
+    chunk = 64 if nsys > 128 else 0
+    opts = dict(fmm_order=args.fmm_order, leaf_target=args.leaf_target, precision=1, precond=1,
+                restart=args.restart, tol=args.tol, max_iters=2000, rhs_chunk=chunk, warm_start=1 if chunk else 0)
+    t0 = time.perf_counter()
+    x = pkg.XRL.from_mesh(m, **opts)
+    setup_s = time.perf_counter() - t0
+    ncols = 6 * (min(nsys, chunk) if chunk else nsys)
+    tuned = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        leaf, order, ms, err = x.autotune(ncols, 1e-6, 1)
+        tuned = {"leaf_target": leaf, "fmm_order": order, "product_ms": ms, "product_err": err,
+                 "tc_targets_per_cta": x.stats()["tc_targets_per_cta"], "autotune_s": time.perf_counter() - t0}
+    st = x.stats()
+    clocks = Clocks()
+    tm = time_sweeps(x, m.freqs, args.warmup, args.steps, clocks)
+    ck = clocks.stop(0)
+    value = tm["dev_ms"] / 1e3 / (args.steps * nsys)
+    ext = torch.cuda.ExternalStream(x.stream_handle())
+    prod = {}
+    for nc, prec in ((1, 64), (6, 64), (ncols, 32), (ncols, 64)):
+        dt = torch.float64 if prec == 64 else torch.float32
+        a = torch.randn(nc, m.n_tri, device="cuda", dtype=dt)
+        b = torch.empty_like(a)
+        fn = x.fmm_mvm_device if prec == 64 else x.fmm_mvm32_device
+        fn(a, b)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 1 if (prec == 64 and nc > 6) else 3
+        e0.record(ext)
+        for _ in range(reps):
+            fn(a, b)
+        e1.record(ext)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        prod["fp%d_nc%d" % (prec, nc)] = {"ms": ms, "panel_cols_per_s": m.n_tri * nc / (ms * 1e-3)}
+        del a, b
+    ora = None
+    if args.workload == "package_crop":
+        with open(os.path.join(ROOT, "tests", "golden", "package_crop_rl.json")) as f:
+            g = json.load(f)
+        Ro, Lo = np.asarray(g["R"])[:len(m.freqs)], np.asarray(g["L"])[:len(m.freqs)]
+        R, L = tm["R"], tm["L"]
+        ora = {"R_self": float(max(np.max(np.abs(R[:, i, i] - Ro[:, i, i]) / np.abs(Ro[:, i, i])) for i in range(nport))),
+               "L_self": float(max(np.max(np.abs(L[:, i, i] - Lo[:, i, i]) / np.abs(Lo[:, i, i])) for i in range(nport)))}
+    arm = None
+    if args.fp64tc_arm:
+        xa = pkg.XRL.from_mesh(m, **dict(opts, precision=2, fmm_order=x.opts.fmm_order, leaf_target=x.opts.leaf_target))
+        ra = time_sweeps(xa, m.freqs, 0, 1)
+        eR, eL = rl_diff(tm["R"], tm["L"], ra["R"], ra["L"])
+        arm = {"s_per_freq_port": ra["dev_ms"] / 1e3 / nsys, "fgmres_iters": ra["iters"], "max_rel_residual": ra["res"],
+               "rel_err_R_chosen_vs_this": eR, "rel_err_L_chosen_vs_this": eL}
+        xa.close()
+    st2 = x.stats()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tm["dev_ms"] / args.steps, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/f64 mixed (FP32 FMM in FP64 FGMRES-IR)", "data": "synthetic",
+            "config": {"workload": "%s: %d triangles, %d conductors, %d ports x %d freqs, tol %g, restart %d%s"
+                                   % (args.workload, m.n_tri, int(m.cond.max()) + 1, nport, len(m.freqs), args.tol,
+                                      args.restart, ", chunks of %d systems" % chunk if chunk else ""),
+                       "autotune": tuned, "fmm_order": x.opts.fmm_order, "leaf_target": x.opts.leaf_target},
+            "e2e": {"value": tm["host_s"] / (args.steps * nsys), "unit": UNIT, "h2d_bytes_per_step": 8 * len(m.freqs),
+                    "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * nport ** 2},
+            "gpu_launches": tm["launches"], "clocks": ck, "products": prod, "oracle_rl_error": ora, "fp64_tc": arm,
+            "solve": {"fgmres_iters": tm["iters"], "max_rel_residual": tm["res"], "setup_s": setup_s,
+                      "setup_phase_ms": st["setup_phase_ms"], "n_loops": st["n_loops"],
+                      "n_global_loops": st["n_global_loops"], "near_per_panel": st["near_nnz"] / st["n_panels"],
+                      "mg_levels": st["mg_levels"], "mg_coarse_n": st["mg_coarse_n"],
+                      "peak_device_bytes": st2["peak_device_bytes"]}}
+    print(json.dumps(line))
+    x.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "coils":
+        return package_run(args)
     if args.kernel_case:
         return kernel_case(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -2,7 +2,7 @@
 (oracle, test infrastructure only).
 
 Follows Sec. II-A (Fig. 1, Algorithm 1, eq. 4-6), Sec. II-B (eq. 7),
-Sec. II-C (eq. 8-9) and Sec. III (ports "just like Q3D", eq. 12).
+Sec. II-C (eq. 8-9) and Sec. III (ports placed as in Q3D, eq. 12).
 
 Readings taken where the paper is silent or garbled:
 

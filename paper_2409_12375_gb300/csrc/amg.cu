@@ -39,7 +39,7 @@ namespace xrl {
 
 namespace {
 
-constexpr int kCoarse = 1024;     // coarsest level size for the dense inverse
+constexpr int kCoarse = 2560;     // coarsest level size for the dense inverse
 constexpr int kMaxLevels = 12;
 constexpr int kSweeps = 2;        // Jacobi sweeps before and after the coarse correction
 constexpr float kOmegaJ = 0.6f;   // Jacobi damping
@@ -156,8 +156,13 @@ Csr transpose1(const Csr& P) {
   return R;
 }
 
-// smoothed-aggregation prolongator of one level; returns false when no coarsening happened
-bool prolongator(const Csr& A, int W, int level, Csr& P) {
+// smoothed-aggregation prolongator of one level; returns false when no
+// coarsening happened.  `special` marks the global (homology and port) loops:
+// each stays a singleton aggregate, so that it reaches the coarsest level and
+// its dense solve unchanged, and the local aggregation ignores its long rows
+// (a global loop taken into a local aggregate would drag that aggregate along
+// its whole path).  On return `special` marks the coarse singletons.
+bool prolongator(const Csr& A, int W, int level, Csr& P, std::vector<char>& special) {
   const int n = A.n;
   const std::vector<double> s = strength_values(A, W);
   std::vector<double> diag(n, 0.0);
@@ -167,10 +172,16 @@ bool prolongator(const Csr& A, int W, int level, Csr& P) {
   const double eps = 0.08 / (double)(1 << level);
   auto strong = [&](int i, int64_t q) {
     const int j = A.col[q];
-    return j != i && std::fabs(s[q]) >= eps * std::sqrt(std::fabs(diag[i] * diag[j]));
+    return j != i && !special[j] && std::fabs(s[q]) >= eps * std::sqrt(std::fabs(diag[i] * diag[j]));
   };
   std::vector<int32_t> agg(n, -1);
   int na = 0;
+  std::vector<char> cspecial;
+  for (int i = 0; i < n; ++i)
+    if (special[i]) {
+      agg[i] = na++;
+      cspecial.push_back(1);
+    }
   // pass 1: nodes whose strong neighbourhood is entirely free
   for (int i = 0; i < n; ++i) {
     if (agg[i] >= 0) continue;
@@ -185,6 +196,7 @@ bool prolongator(const Csr& A, int W, int level, Csr& P) {
     for (int64_t q = A.ptr[i]; q < A.ptr[i + 1]; ++q)
       if (strong(i, q)) agg[A.col[q]] = na;
     ++na;
+    cspecial.push_back(0);
   }
   // pass 2: join the strongest aggregated neighbour
   std::vector<int32_t> agg2(agg);
@@ -205,6 +217,7 @@ bool prolongator(const Csr& A, int W, int level, Csr& P) {
     for (int64_t q = A.ptr[i]; q < A.ptr[i + 1]; ++q)
       if (strong(i, q) && agg[A.col[q]] < 0) agg[A.col[q]] = na;
     ++na;
+    cspecial.push_back(0);
   }
   if (na >= n || na == 0) return false;
   // lambda_max(D^-1 A) by power iteration on the strength matrix
@@ -256,6 +269,7 @@ bool prolongator(const Csr& A, int W, int level, Csr& P) {
       }
     P.ptr[i + 1] = (int64_t)P.col.size();
   }
+  special.swap(cspecial);
   return true;
 }
 
@@ -455,6 +469,8 @@ void amg_prepare(xrl_ctx* c) {
   A.ptr = T.q_ptr;
   A.col = T.q_col;
   A.val = T.q_val;
+  std::vector<char> special(A.n, 0);   // the global loops, numbered after the vertex loops
+  for (int i = T.n_vertex_loops; i < A.n; ++i) special[i] = 1;
   for (int lev = 0; lev < kMaxLevels; ++lev) {
     AmgLevel L;
     L.n = A.n;
@@ -470,7 +486,7 @@ void amg_prepare(xrl_ctx* c) {
     L.pen.upload(c->alloc, A.val);
     L.dpos.upload(c->alloc, dpos);
     Csr P;
-    const bool last = A.n <= kCoarse || lev == kMaxLevels - 1 || !prolongator(A, W, lev, P) ||
+    const bool last = A.n <= kCoarse || lev == kMaxLevels - 1 || !prolongator(A, W, lev, P, special) ||
                       P.m > (int)(0.85 * A.n);
     if (last) {
       L.coarsest = true;

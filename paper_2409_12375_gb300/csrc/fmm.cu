@@ -98,6 +98,49 @@ __global__ void k_p2p(int nc, int ct, const int32_t* __restrict__ leaf_first, co
   }
 }
 
+// Near field for few columns (nc <= 8): one warp per target row.  The lanes
+// stride along the row's values (coalesced) with the Morton index of each
+// near column (near_src), accumulate all nc columns, and reduce by shuffles.
+template <class T, int NC>
+__global__ void __launch_bounds__(128) k_p2p_rows(int nc, const int32_t* __restrict__ leaf_first,
+                                                  const int32_t* __restrict__ leaf_count,
+                                                  const int64_t* __restrict__ near_off,
+                                                  const int32_t* __restrict__ near_w,
+                                                  const int64_t* __restrict__ col_off,
+                                                  const int32_t* __restrict__ near_src, const T* __restrict__ val,
+                                                  const T* __restrict__ X, T* __restrict__ Y) {
+  const int B = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ii = blockIdx.y * 4 + warp;
+  if (ii >= leaf_count[B]) return;
+  const int w = near_w[B];
+  const T* row = val + near_off[B] + (size_t)ii * w;
+  const int32_t* src = near_src + col_off[B];
+  T acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = 0;
+  for (int jj = lane; jj < w; jj += 32) {
+    const T v = row[jj];
+    const T* xs = X + (size_t)src[jj] * nc;
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (c < nc) acc[c] += v * xs[c];
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    T a = acc[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    acc[c] = a;
+  }
+  if (lane == 0) {
+    T* y = Y + (size_t)(leaf_first[B] + ii) * nc;
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (c < nc) y[c] = acc[c];
+  }
+}
+
 // FP32 near field, shared-memory tiled: one block per (leaf, 64-column tile,
 // 64-row block), 128 threads as 16 row groups x 8 column groups; thread
 // (ty, tx) owns rows ty + 16 i (i < 4) and columns 4 tx + j, 32 + 4 tx + j
@@ -319,6 +362,61 @@ __global__ void k_m2l(int nc, int ct, int ncoef, int b0, const int32_t* __restri
       for (int j = 0; j < ncoef; ++j) acc += tm[(size_t)j * ncoef + k] * ms[(size_t)j * nc];
     }
     L[(size_t)Bx * ne + (size_t)k * nc + c0 + cc] = acc;
+  }
+}
+
+// M2L for few columns (ct <= 4 per column tile): one block per (target box,
+// column tile), 8 warps splitting the V-list; lane l owns output
+// coefficients l, l + 32, ... (coalesced table reads), and the warps' partial
+// sums are added in shared memory.  ncoef <= 128.
+template <class T>
+__global__ void __launch_bounds__(256) k_m2l_warps(int nc, int ct, int ncoef, int b0,
+                                                   const int32_t* __restrict__ v_ptr,
+                                                   const int32_t* __restrict__ v_src,
+                                                   const int16_t* __restrict__ v_off, const T* __restrict__ Tt,
+                                                   const T* __restrict__ M, T* __restrict__ L) {
+  __shared__ T part[8][128][4];
+  const int Bx = b0 + blockIdx.x;
+  const int c0 = blockIdx.y * ct;
+  const int cn = min(ct, nc - c0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int vs = v_ptr[Bx], ve = v_ptr[Bx + 1];
+  const size_t ne = (size_t)ncoef * nc;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[i][c] = 0;
+  for (int v = vs + warp; v < ve; v += 8) {
+    const T* tm = Tt + (size_t)v_off[v] * ncoef * ncoef;
+    const T* ms = M + (size_t)v_src[v] * ne + c0;
+    for (int j = 0; j < ncoef; ++j) {
+      T mj[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) mj[c] = c < cn ? ms[(size_t)j * nc + c] : (T)0;
+      const T* tr = tm + (size_t)j * ncoef;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = lane + 32 * i;
+        if (k < ncoef) {
+          const T t = tr[k];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[i][c] += t * mj[c];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) part[warp][lane + 32 * i][c] = acc[i][c];
+  __syncthreads();
+  for (int t = threadIdx.x; t < ncoef * cn; t += blockDim.x) {
+    const int k = t % ncoef, c = t / ncoef;
+    T sum = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) sum += part[w][k][c];
+    L[(size_t)Bx * ne + (size_t)k * nc + c0 + c] = sum;
   }
 }
 
@@ -1001,6 +1099,15 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
                                   c->d.near_col_off.p, c->d.near_src.p, c->d.near_hl.p, c->d.x_hl.p, (double*)Y);
     count_launch(c);
   } else {
+    if (nc <= 8) {
+      dim3 gr(nl, (c->max_leaf + 3) / 4);
+      if (nc == 1)
+        k_p2p_rows<T, 1><<<gr, 128, 0, s>>>(nc, c->d.leaf_first.p, c->d.leaf_count.p, c->d.near_off.p, c->d.near_w.p,
+                                            c->d.near_col_off.p, c->d.near_src.p, near, X, Y);
+      else
+        k_p2p_rows<T, 8><<<gr, 128, 0, s>>>(nc, c->d.leaf_first.p, c->d.leaf_count.p, c->d.near_off.p, c->d.near_w.p,
+                                            c->d.near_col_off.p, c->d.near_src.p, near, X, Y);
+    } else
     k_p2p<T><<<gp, 128, 0, s>>>(nc, ct_p, c->d.leaf_first.p, c->d.leaf_count.p, c->d.u_ptr32.p, c->d.u_src.p,
                                 c->d.near_off.p, c->d.near_w.p, near, X, Y);
   }
@@ -1061,6 +1168,10 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     } else if (tiled) {
       launch_xlate<T>(nbx, b0, nc, ncoef, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p, tm2l, Mx, Lx, false, s);
     } else {
+      if (ncoef <= 128 && nc <= 16)
+        k_m2l_warps<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, b0, c->d.v_ptr32.p, c->d.v_src.p,
+                                                        c->d.v_off.p, tm2l, Mx, Lx);
+      else
       k_m2l<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, b0, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p,
                                                 tm2l, Mx, Lx);
     }
