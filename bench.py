@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6, help="relative residual of the package workloads")
     ap.add_argument("--freqs", type=int, default=0, help="package workloads: solve only the first N frequencies")
     ap.add_argument("--fp64tc-arm", action="store_true", help="package workloads: one FP64-accurate sweep too")
+    ap.add_argument("--sweep-case", action="store_true",
+                    help="profiling case: one warm-up and one timed sweep of the coils at --fmm-order/--leaf-target "
+                         "(mixed precision), no autotune, no comparison arms")
     ap.add_argument("--kernel-case", action="store_true",
                     help="profiling case: only the FMM products of one sweep's launch configuration "
                          "(FP32 inner product and the mixed mode's FP64 residual operator, 64 systems), 3 each")
@@ -664,6 +667,15 @@ def main():
         return package_run(args)
     if args.kernel_case:
         return kernel_case(args)
+    if args.sweep_case:
+        import paper_2409_12375_gb300 as pkg
+        m = workload(0, 1)
+        x = pkg.XRL.from_mesh(m, fmm_order=args.fmm_order, leaf_target=args.leaf_target, precision=1)
+        x.solve(m.freqs)
+        x.solve(m.freqs)
+        print(json.dumps({"sweep_case": "ok", "iters": x.stats()["total_iters"]}))
+        x.close()
+        return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -92,7 +92,7 @@ typedef struct {
                           rest, and the depth has no leaf-size cap; must be < 1.  0 (default): the
                           cell-distance rule of `separation` with its leaf-size cap (see
                           xrl_export_lists) */
-  int32_t mg_cycles;   /* V-cycles per multigrid preconditioner application (1..8), default 1 */
+  int32_t mg_cycles;   /* V-cycles per multigrid preconditioner application (1..8), default 3 */
   int32_t rhs_chunk;   /* 0 (default): all (frequency, port) systems of xrl_solve form one multi-RHS
                           block; > 0: the frequencies are solved in consecutive chunks of at most
                           max(1, rhs_chunk / n_ports) frequencies (all ports of a frequency in one

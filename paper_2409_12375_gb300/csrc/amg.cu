@@ -27,6 +27,12 @@
 // coarsest matrix is inverted (Gauss-Jordan with partial pivoting, one CTA per
 // frequency); per preconditioner application opt.mg_cycles V-cycles, each
 // with kSweeps damped Jacobi sweeps before and after the coarse correction.
+// The global (homology and port) loops have long rows that spoil
+// aggregation; up to kCoarse of them are eliminated instead: the hierarchy is
+// built on the vertex-loop block A_vv only, and per frequency the Schur
+// complement S = A_gg - A_gv A_vv^-1 A_vg (dense, ng x ng, A_vv^-1 by V-cycles
+// on the columns of A_vg) is inverted, so that an application is two
+// multigrid solves around an exact solve of the global loops.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -464,13 +470,56 @@ void amg_prepare(xrl_ctx* c) {
   H = AmgHier();
   const int W = T.n_mat + 1;
   H.W = W;
-  Csr A;
-  A.n = A.m = T.n_loops;
-  A.ptr = T.q_ptr;
-  A.col = T.q_col;
-  A.val = T.q_val;
-  std::vector<char> special(A.n, 0);   // the global loops, numbered after the vertex loops
-  for (int i = T.n_vertex_loops; i < A.n; ++i) special[i] = 1;
+  // split Q = [A_vv A_vg; A_gv A_gg]: vertex loops first, then the global
+  // loops (their long rows are eliminated by the Schur complement, or, when
+  // there are more than kCoarse of them, kept as singleton aggregates)
+  const int n = T.n_loops, nv = T.n_vertex_loops, ng = n - nv;
+  const bool schur = ng > 0 && ng <= kCoarse && nv > 0;
+  Csr A, Avg, Agv, Agg;
+  auto block = [&](Csr& B, int r0, int r1, int c0, int c1) {
+    B.n = r1 - r0;
+    B.m = c1 - c0;
+    B.ptr.assign(B.n + 1, 0);
+    for (int i = r0; i < r1; ++i) {
+      for (int64_t q = T.q_ptr[i]; q < T.q_ptr[i + 1]; ++q) {
+        const int j = T.q_col[q];
+        if (j < c0 || j >= c1) continue;
+        B.col.push_back(j - c0);
+        for (int k = 0; k < W; ++k) B.val.push_back(T.q_val[(size_t)q * W + k]);
+      }
+      B.ptr[i - r0 + 1] = (int64_t)B.col.size();
+    }
+  };
+  std::vector<char> special;
+  if (schur) {
+    block(A, 0, nv, 0, nv);
+    block(Avg, 0, nv, nv, n);
+    block(Agv, nv, n, 0, nv);
+    block(Agg, nv, n, nv, n);
+    special.assign(nv, 0);
+    auto up = [&](const Csr& B, AmgBlock& D) {
+      D.n = B.n;
+      D.nnz = (int64_t)B.col.size();
+      XRL_CHECK(B.col.size() < (size_t)INT32_MAX, XRL_ENOMEM, "global-loop block too large for 32-bit indices");
+      D.ptr.upload(c->alloc, std::vector<int32_t>(B.ptr.begin(), B.ptr.end()));
+      D.col.upload(c->alloc, B.col);
+      D.pen.upload(c->alloc, B.val);
+    };
+    up(Avg, H.vg);
+    up(Agv, H.gv);
+    up(Agg, H.gg);
+    H.nv = nv;
+    H.ng = ng;
+  } else {
+    A.n = A.m = n;
+    A.ptr = T.q_ptr;
+    A.col = T.q_col;
+    A.val = T.q_val;
+    special.assign(n, 0);
+    for (int i = nv; i < n; ++i) special[i] = 1;
+    H.nv = n;
+    H.ng = 0;
+  }
   for (int lev = 0; lev < kMaxLevels; ++lev) {
     AmgLevel L;
     L.n = A.n;
@@ -509,36 +558,161 @@ void amg_prepare(xrl_ctx* c) {
   H.ready = true;
 }
 
-// per-solve values: level matrices for nf frequencies, Jacobi diagonals, the coarsest inverse
+// y[s][i] = (b ? b[s][i] : 0) - sum_q B_f(s)[i][col q] x[s][col q] for a CSR
+// block B of `rows` rows over vectors x of length m (system s at frequency s / nport)
+__global__ void k_amg_bmv(int rows, int m, int nsys, int nport, int64_t nnz, const int32_t* __restrict__ ptr,
+                          const int32_t* __restrict__ col, const float2* __restrict__ vals,
+                          const float2* __restrict__ b, const float2* __restrict__ x, float2* __restrict__ y) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)rows * nsys) return;
+  const int s = (int)(idx / rows), i = (int)(idx % rows);
+  const float2* va = vals + (size_t)(s / nport) * nnz;
+  const float2* xs = x + (size_t)s * m;
+  float2 acc = b ? b[idx] : make_float2(0.f, 0.f);
+  for (int q = ptr[i]; q < ptr[i + 1]; ++q) acc = fsub(acc, fmul(va[q], xs[col[q]]));
+  y[idx] = acc;
+}
+
+// columns j0 .. j0 + ch - 1 of A_vg(f) as right-hand sides B[f ch + jj][i] (B zeroed before)
+__global__ void k_amg_gather_cols(int nv, int nf, int j0, int ch, int64_t nnz, const int32_t* __restrict__ ptr,
+                                  const int32_t* __restrict__ col, const float2* __restrict__ vals,
+                                  float2* __restrict__ B) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)nv * nf) return;
+  const int f = (int)(idx / nv), i = (int)(idx % nv);
+  for (int q = ptr[i]; q < ptr[i + 1]; ++q) {
+    const int j = col[q] - j0;
+    if (j >= 0 && j < ch) B[((size_t)f * ch + j) * nv + i] = vals[(size_t)f * nnz + q];
+  }
+}
+
+// out[i][s] = in[s][i]  (S systems of length n)
+__global__ void k_amg_transpose(int S, int n, const float2* __restrict__ in, float2* __restrict__ out) {
+  __shared__ float2 t[32][33];
+  const int i0 = blockIdx.x * 32, s0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int sv = s0 + r, iv = i0 + threadIdx.x;
+    if (sv < S && iv < n) t[r][threadIdx.x] = in[(size_t)sv * n + iv];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int iv = i0 + r, sv = s0 + threadIdx.x;
+    if (sv < S && iv < n) out[(size_t)iv * S + sv] = t[threadIdx.x][r];
+  }
+}
+
+// Schur columns: aug[f][i][j0 + jj] -= sum_k A_gv(f)[i][k] Y[k][f ch + jj]  (Y transposed, [nv][nf ch])
+__global__ void k_amg_schur(int ng, int nf, int j0, int ch, int64_t nnz, const int32_t* __restrict__ ptr,
+                            const int32_t* __restrict__ col, const float2* __restrict__ vals,
+                            const float2* __restrict__ Yt, float2* __restrict__ aug) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)nf * ng * ch) return;
+  const int jj = (int)(idx % ch);
+  const size_t r = idx / ch;
+  const int i = (int)(r % ng), f = (int)(r / ng);
+  const float2* va = vals + (size_t)f * nnz;
+  const size_t S = (size_t)nf * ch;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int q = ptr[i]; q < ptr[i + 1]; ++q) acc = fadd(acc, fmul(va[q], Yt[(size_t)col[q] * S + (size_t)f * ch + jj]));
+  float2* e = aug + ((size_t)f * ng + i) * 2 * ng + j0 + jj;
+  *e = fsub(*e, acc);
+}
+
+__global__ void k_amg_split(int n, int nv, int nsys, const cplx* __restrict__ v, float2* __restrict__ bv,
+                            float2* __restrict__ bg) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * nsys) return;
+  const int s = (int)(idx / n), i = (int)(idx % n);
+  const float2 x = make_float2((float)v[idx].x, (float)v[idx].y);
+  if (i < nv)
+    bv[(size_t)s * nv + i] = x;
+  else
+    bg[(size_t)s * (n - nv) + i - nv] = x;
+}
+
+__global__ void k_amg_join(int n, int nv, int nsys, const float2* __restrict__ zv, const float2* __restrict__ zg,
+                           cplx* __restrict__ z) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * nsys) return;
+  const int s = (int)(idx / n), i = (int)(idx % n);
+  const float2 x = i < nv ? zv[(size_t)s * nv + i] : zg[(size_t)s * (n - nv) + i - nv];
+  z[idx] = make_double2((double)x.x, (double)x.y);
+}
+
+__global__ void k_amg_axpy(size_t n, const float2* __restrict__ a, float2* __restrict__ b, int init);
+static const float2* mg_solve(xrl_ctx* c, AmgWork& w, int nsys, int nport, int ncyc, cudaStream_t s);
+
+// per-solve values: level matrices for nf frequencies, Jacobi diagonals, the
+// coarsest inverse, and with global loops the inverted Schur complement
+// S(f) = A_gg - A_gv A_vv^-1 A_vg (A_vv^-1 by max(2, mg_cycles) V-cycles on the
+// columns of A_vg, ch of them per pass)
 void amg_factor(xrl_ctx* c, AmgWork& w, int nf, int nsys, const cplx* zsf, const double* wpf, cudaStream_t s) {
   AmgHier& H = c->amg;
   XRL_CHECK(H.ready, XRL_ESTATE, "multigrid hierarchy not built");
   const int nl = (int)H.lv.size();
+  const int ng = H.ng, nv = H.nv;
+  const int ch = ng > 0 ? std::min(ng, std::max(1, (int)(((int64_t)1 << 29) / ((int64_t)nf * nv * 8)))) : 0;
   w.nf = nf;
+  w.cap = std::max(nsys, nf * ch);
   w.lv.resize(nl);
+  w.err.alloc(c->alloc, 1);
+  XRL_CUDA(cudaMemsetAsync(w.err.p, 0, sizeof(int32_t), s));
+  const int ncyc = std::max(1, c->opt.mg_cycles);
   for (int l = 0; l < nl; ++l) {
     AmgLevel& L = H.lv[l];
     AmgLevelWork& K = w.lv[l];
     K.vals.alloc(c->alloc, (size_t)nf * L.nnz);
     K.dinv.alloc(c->alloc, (size_t)nf * L.n);
-    K.x.alloc(c->alloc, (size_t)nsys * L.n);
-    K.b.alloc(c->alloc, (size_t)nsys * L.n);
-    K.r.alloc(c->alloc, (size_t)nsys * L.n);
+    K.x.alloc(c->alloc, (size_t)w.cap * L.n);
+    K.b.alloc(c->alloc, (size_t)w.cap * L.n);
+    K.r.alloc(c->alloc, (size_t)w.cap * L.n);
     k_amg_vals<<<dim3(nb256(L.nnz), nf), 256, 0, s>>>(L.nnz, H.W, nf, L.pen.p, zsf, wpf, K.vals.p);
     k_amg_dinv<<<dim3(nb256(L.n), nf), 256, 0, s>>>(L.n, L.nnz, L.dpos.p, K.vals.p, K.dinv.p);
     count_launch(c, 2);
-    if (l == 0 && c->opt.mg_cycles > 1) {
-      w.bsave.alloc(c->alloc, (size_t)nsys * L.n);
-      w.xacc.alloc(c->alloc, (size_t)nsys * L.n);
+    if (l == 0 && (ncyc > 1 || ng > 0)) {
+      w.bsave.alloc(c->alloc, (size_t)w.cap * L.n);
+      w.xacc.alloc(c->alloc, (size_t)w.cap * L.n);
     }
     if (L.coarsest && L.n <= kCoarse) {
       K.aug.alloc(c->alloc, (size_t)nf * L.n * 2 * L.n);
       k_amg_dense<<<dim3(std::min(L.n, 1024), nf), 256, 0, s>>>(L.n, L.nnz, L.ptr.p, L.col.p, K.vals.p, K.aug.p);
-      w.err.alloc(c->alloc, 1);
-      XRL_CUDA(cudaMemsetAsync(w.err.p, 0, sizeof(int32_t), s));
       k_amg_gauss_jordan<<<nf, 1024, 0, s>>>(L.n, K.aug.p, w.err.p);
       count_launch(c, 2);
     }
+  }
+  if (ng > 0) {
+    auto vals = [&](const AmgBlock& B, DBuf<float2>& out) {
+      out.alloc(c->alloc, (size_t)nf * B.nnz);
+      if (B.nnz) k_amg_vals<<<dim3(nb256(B.nnz), nf), 256, 0, s>>>(B.nnz, H.W, nf, B.pen.p, zsf, wpf, out.p);
+      count_launch(c);
+    };
+    vals(H.vg, w.vg_vals);
+    vals(H.gv, w.gv_vals);
+    vals(H.gg, w.gg_vals);
+    w.saug.alloc(c->alloc, (size_t)nf * ng * 2 * ng);
+    k_amg_dense<<<dim3(std::min(ng, 1024), nf), 256, 0, s>>>(ng, H.gg.nnz, H.gg.ptr.p, H.gg.col.p, w.gg_vals.p,
+                                                             w.saug.p);
+    count_launch(c);
+    DBuf<float2> Yt;
+    Yt.alloc(c->alloc, (size_t)nf * ch * nv);
+    AmgLevelWork& K0 = w.lv[0];
+    for (int j0 = 0; j0 < ng; j0 += ch) {
+      const int cj = std::min(ch, ng - j0);
+      const int S = nf * cj;
+      XRL_CUDA(cudaMemsetAsync(K0.b.p, 0, sizeof(float2) * (size_t)S * nv, s));
+      k_amg_gather_cols<<<nb256((size_t)nv * nf), 256, 0, s>>>(nv, nf, j0, cj, H.vg.nnz, H.vg.ptr.p, H.vg.col.p,
+                                                               w.vg_vals.p, K0.b.p);
+      const float2* Y = mg_solve(c, w, S, cj, std::max(2, ncyc), s);
+      k_amg_transpose<<<dim3((nv + 31) / 32, (S + 31) / 32), dim3(32, 8), 0, s>>>(S, nv, Y, Yt.p);
+      k_amg_schur<<<nb256((size_t)nf * ng * cj), 256, 0, s>>>(ng, nf, j0, cj, H.gv.nnz, H.gv.ptr.p, H.gv.col.p,
+                                                              w.gv_vals.p, Yt.p, w.saug.p);
+      count_launch(c, 3);
+    }
+    k_amg_gauss_jordan<<<nf, 1024, 0, s>>>(ng, w.saug.p, w.err.p);
+    w.u.alloc(c->alloc, (size_t)nsys * nv);
+    w.tg.alloc(c->alloc, (size_t)nsys * ng);
+    w.zg.alloc(c->alloc, (size_t)nsys * ng);
+    count_launch(c);
   }
   XRL_CUDA(cudaGetLastError());
 }
@@ -601,21 +775,19 @@ static void vcycle(xrl_ctx* c, AmgWork& w, int nsys, int nport, cudaStream_t s) 
   XRL_CUDA(cudaGetLastError());
 }
 
-// z ~= Q^-1 v by opt.mg_cycles V-cycles (the later ones on the level-0
-// residual); v, z [nsys][n_loops] FP64 complex
-void amg_apply(xrl_ctx* c, AmgWork& w, int nsys, int nport, const cplx* v, cplx* z, cudaStream_t s) {
+// ncyc V-cycles on w.lv[0].b (the later ones on the level-0 residual); returns
+// the buffer holding the solution
+static const float2* mg_solve(xrl_ctx* c, AmgWork& w, int nsys, int nport, int ncyc, cudaStream_t s) {
   AmgHier& H = c->amg;
   AmgLevel& L0 = H.lv[0];
   AmgLevelWork& K0 = w.lv[0];
   const size_t n0 = (size_t)L0.n * nsys;
-  const int ncyc = std::max(1, c->opt.mg_cycles);
-  k_amg_to32<<<nb256(n0), 256, 0, s>>>(n0, v, ncyc > 1 ? w.bsave.p : K0.b.p);
-  count_launch(c);
   if (ncyc > 1) {
-    k_amg_axpy<<<nb256(n0), 256, 0, s>>>(n0, w.bsave.p, K0.b.p, 1);
+    k_amg_axpy<<<nb256(n0), 256, 0, s>>>(n0, K0.b.p, w.bsave.p, 1);
     count_launch(c);
   }
   vcycle(c, w, nsys, nport, s);
+  if (ncyc == 1) return K0.x.p;
   for (int cy = 1; cy < ncyc; ++cy) {
     k_amg_axpy<<<nb256(n0), 256, 0, s>>>(n0, K0.x.p, w.xacc.p, cy == 1);
     k_amg_resid<<<nb256(n0), 256, 0, s>>>(L0.n, nsys, nport, L0.nnz, L0.ptr.p, L0.col.p, K0.vals.p, w.bsave.p,
@@ -623,11 +795,45 @@ void amg_apply(xrl_ctx* c, AmgWork& w, int nsys, int nport, const cplx* v, cplx*
     count_launch(c, 2);
     vcycle(c, w, nsys, nport, s);
   }
-  if (ncyc > 1) {
-    k_amg_axpy<<<nb256(n0), 256, 0, s>>>(n0, K0.x.p, w.xacc.p, 0);
-    count_launch(c);
+  k_amg_axpy<<<nb256(n0), 256, 0, s>>>(n0, K0.x.p, w.xacc.p, 0);
+  count_launch(c);
+  return w.xacc.p;
+}
+
+// z ~= Q^-1 v; v, z [nsys][n_loops] FP64 complex.  Without global loops:
+// opt.mg_cycles V-cycles.  With them, block elimination with the Schur
+// complement of amg_factor:
+//   u = A_vv^-1 v_v,  z_g = S^-1 (v_g - A_gv u),  z_v = A_vv^-1 (v_v - A_vg z_g)
+void amg_apply(xrl_ctx* c, AmgWork& w, int nsys, int nport, const cplx* v, cplx* z, cudaStream_t s) {
+  AmgHier& H = c->amg;
+  AmgLevelWork& K0 = w.lv[0];
+  const int nv = H.nv, ng = H.ng, n = nv + ng;
+  const int ncyc = std::max(1, c->opt.mg_cycles);
+  const size_t nvs = (size_t)nv * nsys, tot = (size_t)n * nsys;
+  if (ng == 0) {
+    k_amg_to32<<<nb256(nvs), 256, 0, s>>>(nvs, v, K0.b.p);
+    const float2* x = mg_solve(c, w, nsys, nport, ncyc, s);
+    k_amg_to64<<<nb256(nvs), 256, 0, s>>>(nvs, x, z);
+    count_launch(c, 2);
+    XRL_CUDA(cudaGetLastError());
+    return;
   }
-  k_amg_to64<<<nb256(n0), 256, 0, s>>>(n0, ncyc > 1 ? w.xacc.p : K0.x.p, z);
+  k_amg_split<<<nb256(tot), 256, 0, s>>>(n, nv, nsys, v, w.bsave.p, w.tg.p);
+  k_amg_axpy<<<nb256(nvs), 256, 0, s>>>(nvs, w.bsave.p, K0.b.p, 1);
+  count_launch(c, 2);
+  const float2* u = mg_solve(c, w, nsys, nport, ncyc, s);
+  k_amg_axpy<<<nb256(nvs), 256, 0, s>>>(nvs, u, w.u.p, 1);
+  const size_t ngs = (size_t)ng * nsys;
+  k_amg_bmv<<<nb256(ngs), 256, 0, s>>>(ng, nv, nsys, nport, H.gv.nnz, H.gv.ptr.p, H.gv.col.p, w.gv_vals.p, w.tg.p,
+                                       w.u.p, w.tg.p);
+  k_amg_dense_apply<<<nb256(ngs), 256, 0, s>>>(ng, nsys, nport, w.saug.p, w.tg.p, w.zg.p);
+  // bsave still holds v_v: mg_solve only reads its saved right-hand side
+  count_launch(c, 3);
+  k_amg_bmv<<<nb256(nvs), 256, 0, s>>>(nv, ng, nsys, nport, H.vg.nnz, H.vg.ptr.p, H.vg.col.p, w.vg_vals.p,
+                                       w.bsave.p, w.zg.p, K0.b.p);
+  count_launch(c);
+  const float2* zv = mg_solve(c, w, nsys, nport, ncyc, s);
+  k_amg_join<<<nb256(tot), 256, 0, s>>>(n, nv, nsys, zv, w.zg.p, z);
   count_launch(c);
   XRL_CUDA(cudaGetLastError());
 }

@@ -193,7 +193,7 @@ void xrl_default_options(xrl_options* o) {
   o->tensor_cores = 1;
   o->mac_theta = 0.0;
   o->rhs_chunk = 0;
-  o->mg_cycles = 1;
+  o->mg_cycles = 3;
 }
 
 xrl_status xrl_create(const xrl_options* opt, xrl_ctx** out) {

@@ -265,18 +265,30 @@ struct AmgLevel {
   DBuf<int32_t> p_ptr, p_col, r_ptr, r_col;
   DBuf<float> p_val, r_val;
 };
+// a CSR pencil block of Q (A_vg, A_gv, A_gg of the Schur elimination)
+struct AmgBlock {
+  int n = 0;
+  int64_t nnz = 0;
+  DBuf<int32_t> ptr, col;
+  DBuf<double> pen;
+};
 struct AmgHier {
-  std::vector<AmgLevel> lv;
+  std::vector<AmgLevel> lv;   // hierarchy of A_vv (or of all of Q when ng = 0)
   int W = 0;
+  int nv = 0, ng = 0;         // vertex loops (multigrid) and global loops (Schur complement)
+  AmgBlock vg, gv, gg;
   bool ready = false;
 };
 struct AmgLevelWork {
   DBuf<float2> vals, dinv, x, b, r, aug;
 };
 struct AmgWork {
-  int nf = 0;
+  int nf = 0, cap = 0;        // frequencies; systems the level buffers hold
   std::vector<AmgLevelWork> lv;
   DBuf<float2> bsave, xacc;   // right-hand side and summed correction of repeated V-cycles
+  // Schur elimination of the global loops: block values per frequency, the
+  // inverted complement [nf][ng][2 ng], and apply buffers
+  DBuf<float2> vg_vals, gv_vals, gg_vals, saug, u, tg, zg;
   DBuf<int32_t> err;
 };
 
