@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6, help="relative residual of the package workloads")
     ap.add_argument("--freqs", type=int, default=0, help="package workloads: solve only the first N frequencies")
     ap.add_argument("--fp64tc-arm", action="store_true", help="package workloads: one FP64-accurate sweep too")
+    ap.add_argument("--mac", type=float, default=0.0, help="package workloads: bounding-sphere separation theta "
+                                                           "(0: the cell-distance rule)")
     ap.add_argument("--sweep-case", action="store_true",
                     help="profiling case: one warm-up and one timed sweep of the coils at --fmm-order/--leaf-target "
                          "(mixed precision), no autotune, no comparison arms")
@@ -285,7 +287,8 @@ def measure_fp64_peak():
 # ncu DRAM bytes (read + write) per launch of the dominant kernels at one
 # configuration of this workload: (order, leaf target, targets per CTA, columns)
 # -> {phase: bytes}.  Reported only when the bench runs that configuration.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {(7, 16, 2, 384): {"m2l": 83.342848e6 + 30.363904e6,     # k_xlate_tc2<0>
+                                  "p2p": 438.394624e6 + 33.091072e6}}   # k_xlate_tc2<1>
 
 
 def phase_kernel(name, p):
@@ -585,7 +588,7 @@ def package_run(args):
     nport = len(m.ports)
     nsys = len(m.freqs) * nport
     chunk = 64 if nsys > 128 else 0
-    opts = dict(fmm_order=args.fmm_order, leaf_target=args.leaf_target, precision=1, precond=1,
+    opts = dict(fmm_order=args.fmm_order, leaf_target=args.leaf_target, precision=1, precond=1, mac_theta=args.mac,
                 restart=args.restart, tol=args.tol, max_iters=2000, rhs_chunk=chunk, warm_start=1 if chunk else 0)
     t0 = time.perf_counter()
     x = pkg.XRL.from_mesh(m, **opts)
@@ -645,6 +648,7 @@ def package_run(args):
             "config": {"workload": "%s: %d triangles, %d conductors, %d ports x %d freqs, tol %g, restart %d%s"
                                    % (args.workload, m.n_tri, int(m.cond.max()) + 1, nport, len(m.freqs), args.tol,
                                       args.restart, ", chunks of %d systems" % chunk if chunk else ""),
+                       "mac_theta": args.mac, "mg_cycles": x.opts.mg_cycles,
                        "autotune": tuned, "fmm_order": x.opts.fmm_order, "leaf_target": x.opts.leaf_target},
             "e2e": {"value": tm["host_s"] / (args.steps * nsys), "unit": UNIT, "h2d_bytes_per_step": 8 * len(m.freqs),
                     "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * nport ** 2},
