@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6, help="relative residual of the package workloads")
     ap.add_argument("--freqs", type=int, default=0, help="package workloads: solve only the first N frequencies")
     ap.add_argument("--fp64tc-arm", action="store_true", help="package workloads: one FP64-accurate sweep too")
+    ap.add_argument("--chunk", type=int, default=64, help="package workloads: systems per frequency chunk when "
+                                                           "the sweep has more than 128")
     ap.add_argument("--mac", type=float, default=0.0, help="package workloads: bounding-sphere separation theta "
                                                            "(0: the cell-distance rule)")
     ap.add_argument("--sweep-case", action="store_true",
@@ -587,7 +589,8 @@ def package_run(args):
         m.freqs = m.freqs[:args.freqs]
     nport = len(m.ports)
     nsys = len(m.freqs) * nport
-    chunk = 64 if nsys > 128 else 0
+    chunk = args.chunk if nsys > 128 or args.freqs else 0
+    chunk = chunk if chunk and chunk < nsys else 0
     opts = dict(fmm_order=args.fmm_order, leaf_target=args.leaf_target, precision=1, precond=1, mac_theta=args.mac,
                 restart=args.restart, tol=args.tol, max_iters=2000, rhs_chunk=chunk, warm_start=1 if chunk else 0)
     t0 = time.perf_counter()

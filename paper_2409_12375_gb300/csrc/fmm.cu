@@ -420,6 +420,65 @@ __global__ void __launch_bounds__(256) k_m2l_warps(int nc, int ct, int ncoef, in
   }
 }
 
+// M2L for few columns (nc <= 8) grouped by translation offset: one block per
+// (offset, chunk of kOffChunk of its V-list pairs) stages that offset's
+// table in shared memory once, and each warp applies it to one pair at a
+// time (lane l owns output coefficients l, l + 32, ...), adding into the
+// local expansions with atomics (L zeroed before).  At one column a table is
+// 8 (p+1)^4 bytes for 2 (p+1)^4 flops per pair; read per pair, as in the
+// list form, it made the product L2-bound, staged once per offset it is
+// reused by every pair of that offset.
+constexpr int kOffChunk = 64;
+template <class T, int NC>
+__global__ void __launch_bounds__(256) k_m2l_offsets(int nc, int ncoef, const int32_t* __restrict__ op_ptr,
+                                                     const int32_t* __restrict__ op_tgt,
+                                                     const int32_t* __restrict__ op_src, const T* __restrict__ Tt,
+                                                     const T* __restrict__ M, T* __restrict__ L) {
+  extern __shared__ __align__(16) unsigned char sm_off[];
+  T* Ts = reinterpret_cast<T*>(sm_off);          // [ncoef][ncoef], [in][out]
+  const int o = blockIdx.x;
+  const int p0 = op_ptr[o] + blockIdx.y * kOffChunk;
+  const int p1 = min(op_ptr[o + 1], p0 + kOffChunk);
+  if (p0 >= p1) return;
+  const T* tm = Tt + (size_t)o * ncoef * ncoef;
+  for (int e = threadIdx.x; e < ncoef * ncoef; e += blockDim.x) Ts[e] = tm[e];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t ne = (size_t)ncoef * nc;
+  for (int q = p0 + warp; q < p1; q += 8) {
+    const T* ms = M + (size_t)op_src[q] * ne;
+    T acc[6][NC];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[i][c] = 0;
+    for (int j = 0; j < ncoef; ++j) {
+      T mj[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) mj[c] = c < nc ? ms[(size_t)j * nc + c] : (T)0;
+      const T* tr = Ts + (size_t)j * ncoef;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const int k = lane + 32 * i;
+        if (k < ncoef) {
+          const T t = tr[k];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[i][c] += t * mj[c];
+        }
+      }
+    }
+    T* lt = L + (size_t)op_tgt[q] * ne;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const int k = lane + 32 * i;
+      if (k < ncoef)
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (c < nc) atomicAdd(lt + (size_t)k * nc + c, acc[i][c]);
+    }
+  }
+}
+
 // M2L, FP32, shared-memory tiled: one block per (target box, 64-column tile),
 // 128 threads as 16 row groups x 8 column groups; thread (ty, tx) owns rows
 // ty + 16 i (i < RI) and columns 4 tx + j, 32 + 4 tx + j (j < 4).  Per
@@ -1016,6 +1075,35 @@ void fmm_prepare(xrl_ctx* c) {
   c->d.box_oct16.upload(c->alloc, oct16);
   std::vector<int32_t> vptr(t.v_ptr.begin(), t.v_ptr.end());
   c->d.v_ptr32.upload(c->alloc, vptr);
+  {
+    // V-list pairs grouped by offset (for the few-column M2L)
+    const int noff = (int)(t.m2l_offsets.size() / 3);
+    std::vector<int32_t> optr(noff + 1, 0), otgt(t.v_src.size()), osrc(t.v_src.size());
+    for (size_t k = 0; k < t.v_off.size(); ++k) optr[t.v_off[k] + 1]++;
+    c->max_off_pairs = 0;
+    for (int o = 0; o < noff; ++o) {
+      c->max_off_pairs = std::max(c->max_off_pairs, optr[o + 1]);
+      optr[o + 1] += optr[o];
+    }
+    std::vector<int32_t> pos(optr.begin(), optr.end() - 1);
+    for (int b = 0; b < nb; ++b)
+      for (int64_t k = t.v_ptr[b]; k < t.v_ptr[b + 1]; ++k) {
+        const int q = pos[t.v_off[k]]++;
+        otgt[q] = b;
+        osrc[q] = t.v_src[k];
+      }
+    c->d.op_ptr.upload(c->alloc, optr);
+    c->d.op_tgt.upload(c->alloc, otgt);
+    c->d.op_src.upload(c->alloc, osrc);
+    // the offset table in shared memory (opt-in above 48 KB), set here, outside any stream capture
+    const int s8 = (int)(sizeof(double) * c->ncoef * c->ncoef), s4 = s8 / 2;
+    if (c->ncoef <= 192) {
+      XRL_CUDA(cudaFuncSetAttribute(k_m2l_offsets<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8));
+      XRL_CUDA(cudaFuncSetAttribute(k_m2l_offsets<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8));
+      XRL_CUDA(cudaFuncSetAttribute(k_m2l_offsets<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4));
+      XRL_CUDA(cudaFuncSetAttribute(k_m2l_offsets<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4));
+    }
+  }
   c->d.v_src.upload(c->alloc, t.v_src);
   c->d.v_off.upload(c->alloc, t.v_off);
   tc_prepare(c);
@@ -1168,7 +1256,20 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     } else if (tiled) {
       launch_xlate<T>(nbx, b0, nc, ncoef, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p, tm2l, Mx, Lx, false, s);
     } else {
-      if (ncoef <= 128 && nc <= 16)
+      if (nc <= 8 && ncoef <= 192 && c->d.op_ptr.n > 0) {
+        const int noff = (int)(t.m2l_offsets.size() / 3);
+        const size_t smem = sizeof(T) * (size_t)ncoef * ncoef;
+        XRL_CUDA(cudaMemsetAsync(Lx + (size_t)b0 * ncoef * nc, 0, sizeof(T) * (size_t)nbx * ncoef * nc, s));
+        const dim3 g(noff, (c->max_off_pairs + kOffChunk - 1) / kOffChunk);
+        if (nc == 1) {
+          k_m2l_offsets<T, 1><<<g, 256, smem, s>>>(nc, ncoef, c->d.op_ptr.p, c->d.op_tgt.p, c->d.op_src.p, tm2l, Mx,
+                                                   Lx);
+        } else {
+          k_m2l_offsets<T, 8><<<g, 256, smem, s>>>(nc, ncoef, c->d.op_ptr.p, c->d.op_tgt.p, c->d.op_src.p, tm2l, Mx,
+                                                   Lx);
+        }
+        count_launch(c);
+      } else if (ncoef <= 128 && nc <= 16)
         k_m2l_warps<T><<<dim3(nbx, ecols), 256, 0, s>>>(nc, ct_e, ncoef, b0, c->d.v_ptr32.p, c->d.v_src.p,
                                                         c->d.v_off.p, tm2l, Mx, Lx);
       else

@@ -227,6 +227,7 @@ struct Dev {
   DBuf<int64_t> tcm_boff2;      // per leaf: byte offset of its P2M moment image
   DBuf<uint16_t> tcm_p2m_img;   // leaf moment images (coefficients x panels)
   DBuf<int32_t> v_ptr32, v_src;
+  DBuf<int32_t> op_ptr, op_tgt, op_src;               // V-list pairs grouped by M2L offset
   DBuf<int16_t> v_off;
   DBuf<int32_t> lvl_boxes;                            // per level: global ids of its boxes (same as range)
   // FMM work buffers (resized to the column count)
@@ -333,6 +334,7 @@ struct xrl_ctx {
   std::vector<std::vector<int32_t>> port_src, port_sink;
   bool have_mesh = false, have_cond = false, ready = false;
   int N = 0, ncoef = 0, p = 0, max_leaf = 0;
+  int max_off_pairs = 0;                // most V-list pairs of one M2L offset
   bool df64_m2l = false;   // FP64 M2L on the FP32 pipes (set inside mixed-precision solves)
   int tcp_sum_pc = 0;                   // padded panels of all leaves (tensor-core near field)
   int tc_targets = 2;                   // targets per CTA of the FP32 tensor-core M2L / near field (autotuned)

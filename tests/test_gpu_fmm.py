@@ -146,7 +146,9 @@ def test_fmm_host_entry_equals_device_entry(bar_ctx):
     yd = torch.empty_like(xd)
     bar_ctx.fmm_mvm_device(xd, yd)
     torch.cuda.synchronize()
-    assert np.array_equal(yh, yd.cpu().numpy())
+    # at <= 8 columns the M2L accumulates with atomics: equal up to rounding order
+    yv = yd.cpu().numpy()
+    assert np.max(np.abs(yh - yv)) <= 1e-13 * np.max(np.abs(yh))
 
 
 def test_fmm_zero_and_linearity(bar_ctx):
