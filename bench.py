@@ -637,22 +637,24 @@ def package_run(args):
         ora = {"R_self": float(max(np.max(np.abs(R[:, i, i] - Ro[:, i, i]) / np.abs(Ro[:, i, i])) for i in range(nport))),
                "L_self": float(max(np.max(np.abs(L[:, i, i] - Lo[:, i, i]) / np.abs(Lo[:, i, i])) for i in range(nport)))}
     arm = None
+    st2 = x.stats()
+    order, leaf, mg = x.opts.fmm_order, x.opts.leaf_target, x.opts.mg_cycles
+    x.close()                         # frees its device memory (and allocation cache) before the next context
     if args.fp64tc_arm:
-        xa = pkg.XRL.from_mesh(m, **dict(opts, precision=2, fmm_order=x.opts.fmm_order, leaf_target=x.opts.leaf_target))
+        xa = pkg.XRL.from_mesh(m, **dict(opts, precision=2, fmm_order=order, leaf_target=leaf))
         ra = time_sweeps(xa, m.freqs, 0, 1)
         eR, eL = rl_diff(tm["R"], tm["L"], ra["R"], ra["L"])
         arm = {"s_per_freq_port": ra["dev_ms"] / 1e3 / nsys, "fgmres_iters": ra["iters"], "max_rel_residual": ra["res"],
                "rel_err_R_chosen_vs_this": eR, "rel_err_L_chosen_vs_this": eL}
         xa.close()
-    st2 = x.stats()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tm["dev_ms"] / args.steps, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32/f64 mixed (FP32 FMM in FP64 FGMRES-IR)", "data": "synthetic",
             "config": {"workload": "%s: %d triangles, %d conductors, %d ports x %d freqs, tol %g, restart %d%s"
                                    % (args.workload, m.n_tri, int(m.cond.max()) + 1, nport, len(m.freqs), args.tol,
                                       args.restart, ", chunks of %d systems" % chunk if chunk else ""),
-                       "mac_theta": args.mac, "mg_cycles": x.opts.mg_cycles,
-                       "autotune": tuned, "fmm_order": x.opts.fmm_order, "leaf_target": x.opts.leaf_target},
+                       "mac_theta": args.mac, "mg_cycles": mg,
+                       "autotune": tuned, "fmm_order": order, "leaf_target": leaf},
             "e2e": {"value": tm["host_s"] / (args.steps * nsys), "unit": UNIT, "h2d_bytes_per_step": 8 * len(m.freqs),
                     "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * nport ** 2},
             "gpu_launches": tm["launches"], "clocks": ck, "products": prod, "oracle_rl_error": ora, "fp64_tc": arm,
@@ -662,7 +664,6 @@ def package_run(args):
                       "mg_levels": st["mg_levels"], "mg_coarse_n": st["mg_coarse_n"],
                       "peak_device_bytes": st2["peak_device_bytes"]}}
     print(json.dumps(line))
-    x.close()
     return 0
 
 

@@ -348,6 +348,8 @@ xrl_status xrl_setup(xrl_ctx* c) {
     c->p = c->opt.fmm_order;
     c->ncoef = (c->p + 1) * (c->p + 1);
     c->d = Dev();
+    c->amg = AmgHier();
+    c->alloc.trim();
     double tp = now_ms();
     auto lap = [&](int k) {
       const double t = now_ms();

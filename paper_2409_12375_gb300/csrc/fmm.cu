@@ -1095,13 +1095,17 @@ void fmm_prepare(xrl_ctx* c) {
     c->d.op_ptr.upload(c->alloc, optr);
     c->d.op_tgt.upload(c->alloc, otgt);
     c->d.op_src.upload(c->alloc, osrc);
-    // the offset table in shared memory (opt-in above 48 KB), set here, outside any stream capture
+    // the offset table in shared memory (opt-in above 48 KB), set here, outside any stream capture.
+    // The attribute belongs to the kernel, not to this context: it only ever grows, so that a
+    // context of lower order cannot shrink it below what another context's launches need.
+    static int s8_set = 0;
     const int s8 = (int)(sizeof(double) * c->ncoef * c->ncoef), s4 = s8 / 2;
-    if (c->ncoef <= 192) {
+    if (c->ncoef <= 192 && s8 > s8_set) {
       XRL_CUDA(cudaFuncSetAttribute(k_m2l_offsets<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8));
       XRL_CUDA(cudaFuncSetAttribute(k_m2l_offsets<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8));
       XRL_CUDA(cudaFuncSetAttribute(k_m2l_offsets<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4));
       XRL_CUDA(cudaFuncSetAttribute(k_m2l_offsets<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4));
+      s8_set = s8;
     }
   }
   c->d.v_src.upload(c->alloc, t.v_src);
@@ -1256,7 +1260,7 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     } else if (tiled) {
       launch_xlate<T>(nbx, b0, nc, ncoef, c->d.v_ptr32.p, c->d.v_src.p, c->d.v_off.p, tm2l, Mx, Lx, false, s);
     } else {
-      if (nc <= 8 && ncoef <= 192 && c->d.op_ptr.n > 0) {
+      if (nc <= 8 && ncoef <= 192 && c->d.op_ptr.n > 0 && (c->max_off_pairs + kOffChunk - 1) / kOffChunk <= 65535) {
         const int noff = (int)(t.m2l_offsets.size() / 3);
         const size_t smem = sizeof(T) * (size_t)ncoef * ncoef;
         XRL_CUDA(cudaMemsetAsync(Lx + (size_t)b0 * ncoef * nc, 0, sizeof(T) * (size_t)nbx * ncoef * nc, s));

@@ -1015,6 +1015,7 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
         count_launch(c);
         if (graph_state == 0) {
           apply_A(c, wk, nsys, wk.zst.p, wk.w.p, mixed, true);
+          XRL_CUDA(cudaGetLastError());   // a bad launch shows here, not as an invalidated capture
           graph_state = 1;
         } else {
           if (graph_state == 1) {

@@ -72,6 +72,7 @@ __host__ __device__ inline size_t oz_img_off(int R, int Kp, int r, int k, int h,
          (r & 7) * 16 + (k & 7) * 2;
 }
 
+constexpr unsigned kMaxGridY = 65535u;   // grid.y limit: larger target counts launch in slices
 constexpr int OZ_S = 5;          // integer slices of 7 bits
 constexpr int OZ_STAGES = 3;
 
@@ -213,6 +214,7 @@ __global__ void k_tc_pack_b(int ncoef, int Kp, int Np, const double* __restrict_
 //    out[box b0 + L][k][col].
 struct XlPairs {
   int mode, b0, src0, nct, Kp, sum_pc, ncoef;
+  int y0;                // first target of this launch (grid.y is capped at 65535)
   size_t a_img, b_img;   // mode 0: bytes of one (box, tile) A image and of one table image
   int a_row_bytes;       // bytes per K element of an A image (pieces x 128 x 2)
   const int32_t* ptr;
@@ -242,21 +244,21 @@ __device__ __forceinline__ void xl_pair(const XlPairs& p, int v, int ct, size_t&
 __device__ __forceinline__ void xl_target(const XlPairs& p, int NPmax, int& vs, int& ve, int& N, int& nrows,
                                           size_t& row0) {
   if (p.mode == 0) {
-    const int Bx = p.b0 + blockIdx.y;
+    const int Bx = p.b0 + p.y0 + (int)blockIdx.y;
     vs = p.ptr[Bx];
     ve = p.ptr[Bx + 1];
     N = NPmax;
     nrows = p.ncoef;
     row0 = (size_t)Bx * p.ncoef;
   } else if (p.mode == 1) {
-    const int T = blockIdx.y;
+    const int T = p.y0 + (int)blockIdx.y;
     vs = p.ptr[T];
     ve = p.ptr[T + 1];
     nrows = p.leaf_n[T];
     N = (nrows + 15) & ~15;
     row0 = (size_t)p.leaf_f0[T];
   } else {
-    const int L = blockIdx.y;
+    const int L = p.y0 + (int)blockIdx.y;
     vs = L;
     ve = L + 1;
     N = NPmax;
@@ -505,6 +507,7 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc(TcArgs a) {
 //    panel count), B = near-block image of U-list pair gv_t.
 struct Tc2Args {
   int mode, nc, nct, Kp, ncoef, src0, sum_pc;
+  int y0;                              // first group of this launch (grid.y is capped at 65535)
   size_t a_img, b_img;                 // mode 0: bytes of one (box, tile) A image / one table image
   int a_row_bytes;                     // mode 1: bytes per K element of the X image
   const int32_t* gptr;                 // merged list of group g: [gptr[g], gptr[g + 1])
@@ -593,7 +596,7 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
   int* bad = reinterpret_cast<int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ct = blockIdx.x, g = blockIdx.y;
+  const int ct = blockIdx.x, g = a.y0 + (int)blockIdx.y;
   const int vs = a.gptr[g], ve = a.gptr[g + 1];
   const int nv = ve - vs;
   const int t1 = a.gt1[g], t2 = a.gt2[g];
@@ -786,20 +789,25 @@ static size_t tc2_smem() {
 }
 
 template <int MODE>
-static void launch_tc2_m(dim3 grid, const Tc2Args& g, cudaStream_t s) {
+static void launch_tc2_m(xrl_ctx* c, dim3 grid, const Tc2Args& g, cudaStream_t s) {
   static bool set = false;
   if (!set) {
     XRL_CUDA(cudaFuncSetAttribute(k_xlate_tc2<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2_smem()));
     set = true;
   }
-  k_xlate_tc2<MODE><<<grid, 192, tc2_smem(), s>>>(g);
+  Tc2Args a = g;
+  for (unsigned y0 = 0; y0 < grid.y; y0 += kMaxGridY) {
+    a.y0 = (int)y0;
+    k_xlate_tc2<MODE><<<dim3(grid.x, std::min(kMaxGridY, grid.y - y0)), 192, tc2_smem(), s>>>(a);
+    if (y0 > 0) count_launch(c);   // callers count one launch per translation
+  }
 }
 
-static void launch_tc2(dim3 grid, const Tc2Args& g, cudaStream_t s) {
+static void launch_tc2(xrl_ctx* c, dim3 grid, const Tc2Args& g, cudaStream_t s) {
   if (g.mode == 0)
-    launch_tc2_m<0>(grid, g, s);
+    launch_tc2_m<0>(c, grid, g, s);
   else
-    launch_tc2_m<1>(grid, g, s);
+    launch_tc2_m<1>(c, grid, g, s);
 }
 
 // ---- FP64-accurate translation (Ozaki-style integer slices) ------------------------------
@@ -1317,18 +1325,23 @@ static XlPairs p2p_pairs(const xrl_ctx* c, int nct, int pieces, const int64_t* b
 }
 
 template <int NP>
-static void launch_tc(dim3 g, const TcArgs& a, cudaStream_t s) {
+static void launch_tc(xrl_ctx* c, dim3 g, const TcArgs& a, cudaStream_t s) {
   const size_t smem = (size_t)TC_STAGES * (tc_chunk_bytes(TC_ROWS, TC_KC) + tc_chunk_bytes(NP, TC_KC)) + 1024 + 128;
   static bool set = false;
   if (!set) {
     XRL_CUDA(cudaFuncSetAttribute(k_xlate_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     set = true;
   }
-  k_xlate_tc<NP><<<g, 192, smem, s>>>(a);
+  TcArgs b = a;
+  for (unsigned y0 = 0; y0 < g.y; y0 += kMaxGridY) {
+    b.pr.y0 = (int)y0;
+    k_xlate_tc<NP><<<dim3(g.x, std::min(kMaxGridY, g.y - y0)), 192, smem, s>>>(b);
+    if (y0 > 0) count_launch(c);   // callers count one launch per translation
+  }
 }
 
 template <int NP>
-static void launch_oz_np(dim3 g, const OzArgs& a, cudaStream_t s) {
+static void launch_oz_np(xrl_ctx* c, dim3 g, const OzArgs& a, cudaStream_t s) {
   const size_t smem =
       (size_t)OZ_STAGES * (oz_chunk_bytes(TC_ROWS, TC_KC, OZ_S) + oz_chunk_bytes(NP, TC_KC, OZ_S)) + 1024 + 128;
   static bool set = false;
@@ -1336,14 +1349,19 @@ static void launch_oz_np(dim3 g, const OzArgs& a, cudaStream_t s) {
     XRL_CUDA(cudaFuncSetAttribute(k_xlate_oz<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     set = true;
   }
-  k_xlate_oz<NP><<<g, 320, smem, s>>>(a);
+  OzArgs b = a;
+  for (unsigned y0 = 0; y0 < g.y; y0 += kMaxGridY) {
+    b.pr.y0 = (int)y0;
+    k_xlate_oz<NP><<<dim3(g.x, std::min(kMaxGridY, g.y - y0)), 320, smem, s>>>(b);
+    if (y0 > 0) count_launch(c);   // callers count one launch per translation
+  }
 }
 
-static void launch_oz(int Np, dim3 g, const OzArgs& a, cudaStream_t s) {
+static void launch_oz(xrl_ctx* c, int Np, dim3 g, const OzArgs& a, cudaStream_t s) {
   if (Np <= 64)
-    launch_oz_np<64>(g, a, s);
+    launch_oz_np<64>(c, g, a, s);
   else
-    launch_oz_np<96>(g, a, s);
+    launch_oz_np<96>(c, g, a, s);
 }
 
 static void p2p_groups(xrl_ctx* c, const std::vector<int32_t>& pc);
@@ -1498,11 +1516,11 @@ bool tcm_usable(const xrl_ctx* c, int nc) {
   return tc_usable(c, nc) && tcp_usable(c, nc) && c->d.tcm_p2m_img.n > 0;
 }
 
-static void launch_tc_np(int Np, dim3 g, const TcArgs& a, cudaStream_t s) {
+static void launch_tc_np(xrl_ctx* c, int Np, dim3 g, const TcArgs& a, cudaStream_t s) {
   if (Np <= 64)
-    launch_tc<64>(g, a, s);
+    launch_tc<64>(c, g, a, s);
   else
-    launch_tc<96>(g, a, s);
+    launch_tc<96>(c, g, a, s);
 }
 
 // M = S^T X for the leaves (mode 2); the transposed-X image of the near
@@ -1520,7 +1538,7 @@ void tc_p2m(xrl_ctx* c, int nc, float* Mx, cudaStream_t s) {
   a.bimg = reinterpret_cast<const char*>(c->d.tcm_p2m_img.p);
   a.out = Mx;
   a.err = c->d.tc_err.p;
-  launch_tc_np(tc_npad(c->ncoef), dim3(nct, t.n_leaves()), a, s);
+  launch_tc_np(c, tc_npad(c->ncoef), dim3(nct, t.n_leaves()), a, s);
 }
 
 // one level of M2M (parents at level l from their children at l + 1): pack
@@ -1545,7 +1563,7 @@ void tc_m2m(xrl_ctx* c, int l, int nc, float* Mx, cudaStream_t s) {
   a.bimg = reinterpret_cast<const char*>(c->d.tc_m2m_img.p);
   a.out = Mx;
   a.err = c->d.tc_err.p;
-  launch_tc_np(Np, dim3(nct, nt), a, s);
+  launch_tc_np(c, Np, dim3(nct, nt), a, s);
 }
 
 // M2L of the FP32 pass: in = M, out = L over all target boxes [b0, b0 + nbx);
@@ -1578,7 +1596,7 @@ void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cud
     g.bimg = reinterpret_cast<const char*>(c->d.tc_bimg.p);
     g.out = Lx;
     g.err = c->d.tc_err.p;
-    launch_tc2(dim3(nct, (unsigned)(c->d.m2l_gptr.n - 1)), g, s);
+    launch_tc2(c, dim3(nct, (unsigned)(c->d.m2l_gptr.n - 1)), g, s);
     return;
   }
   TcArgs a;
@@ -1588,7 +1606,7 @@ void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cud
   a.bimg = reinterpret_cast<const char*>(c->d.tc_bimg.p);
   a.out = Lx;
   a.err = c->d.tc_err.p;
-  launch_tc_np(Np, dim3(nct, nbx), a, s);
+  launch_tc_np(c, Np, dim3(nct, nbx), a, s);
 }
 
 bool tc64_usable(const xrl_ctx* c, int nc) {
@@ -1642,7 +1660,7 @@ void tc_m2m64(xrl_ctx* c, int l, int nc, double* Mx, cudaStream_t s) {
   a.bimg = reinterpret_cast<const char*>(c->d.oz_m2m_img.p);
   a.out = Mx;
   a.err = c->d.tc_err.p;
-  launch_oz(Np, dim3(nct, nt), a, s);
+  launch_oz(c, Np, dim3(nct, nt), a, s);
 }
 
 // FP64-accurate M2L of the refinement residuals (in = M, out = L, FP64)
@@ -1662,7 +1680,7 @@ void tc_m2l64(xrl_ctx* c, int nbx, int b0, int nc, const double* Mx, double* Lx,
   a.bimg = reinterpret_cast<const char*>(c->d.oz_bimg.p);
   a.out = Lx;
   a.err = c->d.tc_err.p;
-  launch_oz(Np, dim3(nct, nbx), a, s);
+  launch_oz(c, Np, dim3(nct, nbx), a, s);
 }
 
 bool tcp_usable(const xrl_ctx* c, int nc) {
@@ -1705,7 +1723,7 @@ void tc_p2p_fork(xrl_ctx* c, int nc, const float* X, float* Y, cudaStream_t s, c
     g.bimg = reinterpret_cast<const char*>(c->d.tcp_vimg.p);
     g.out = Y;
     g.err = c->d.tc_err.p;
-    launch_tc2(dim3(nct, (unsigned)(c->d.p2p_gptr.n - 1)), g, s);
+    launch_tc2(c, dim3(nct, (unsigned)(c->d.p2p_gptr.n - 1)), g, s);
     return;
   }
   TcArgs a;
@@ -1715,7 +1733,7 @@ void tc_p2p_fork(xrl_ctx* c, int nc, const float* X, float* Y, cudaStream_t s, c
   a.bimg = reinterpret_cast<const char*>(c->d.tcp_vimg.p);
   a.out = Y;
   a.err = c->d.tc_err.p;
-  launch_tc<96>(dim3(nct, nl), a, s);
+  launch_tc<96>(c, dim3(nct, nl), a, s);
 }
 
 // FP64-accurate near field on the tensor cores (integer slices; two launches,
@@ -1741,7 +1759,7 @@ void tc_p2p64(xrl_ctx* c, int nc, const double* X, double* Y, cudaStream_t s) {
   a.bimg = reinterpret_cast<const char*>(c->d.ozp_vimg.p);
   a.out = Y;
   a.err = c->d.tc_err.p;
-  launch_oz(96, dim3(nct, nl), a, s);
+  launch_oz(c, 96, dim3(nct, nl), a, s);
 }
 
 // raises XRL_ETIMEOUT if a tensor-core kernel gave up a wait since the last check

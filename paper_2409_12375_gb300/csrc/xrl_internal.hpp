@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <complex>
+#include <map>
 #include <cstring>
 #include <stdexcept>
 #include <string>
@@ -35,22 +36,63 @@ struct Error : std::runtime_error {
   } while (0)
 
 // ---- device memory with a high-water mark -----------------------------------
+// Freed blocks are kept, by size, and handed out again for a request of the
+// same size: a sweep allocates the same work arrays every time, and a
+// cudaMalloc per array per chunk left the GPU idle.  A block may still be in
+// use by kernels in flight when it is freed, so the first reuse after a free
+// synchronises the device, as cudaFree itself would have.  The cache is
+// released when an allocation fails, at every setup and when the context is
+// destroyed.  `peak` counts cached blocks too (they hold device memory).
+// A launch error still pending when an allocation is made is raised here, so
+// that the retry below cannot clear it.
 struct DevAlloc {
-  int64_t cur = 0, peak = 0;
+  int64_t cur = 0, peak = 0, cached = 0;
+  bool dirty = false;   // a block was freed since the last synchronisation
+  std::multimap<size_t, void*> cache;
   void* get(size_t bytes) {
-    void* p = nullptr;
     if (bytes == 0) return nullptr;
-    XRL_CUDA(cudaMalloc(&p, bytes));
+    const cudaError_t pend = cudaGetLastError();
+    if (pend != cudaSuccess) throw Error(XRL_ECUDA, std::string("pending CUDA error: ") + cudaGetErrorString(pend));
+    auto it = cache.find(bytes);
+    if (it != cache.end()) {
+      if (dirty) {
+        XRL_CUDA(cudaDeviceSynchronize());
+        dirty = false;
+      }
+      void* p = it->second;
+      cache.erase(it);
+      cached -= (int64_t)bytes;
+      cur += (int64_t)bytes;
+      return p;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaErrorMemoryAllocation && !cache.empty()) {
+      cudaGetLastError();
+      trim();
+      e = cudaMalloc(&p, bytes);
+    }
+    if (e != cudaSuccess)
+      throw Error(e == cudaErrorMemoryAllocation ? XRL_ENOMEM : XRL_ECUDA,
+                  std::string("cudaMalloc(&p, bytes): ") + cudaGetErrorString(e));
     cur += (int64_t)bytes;
-    if (cur > peak) peak = cur;
+    if (cur + cached > peak) peak = cur + cached;
     return p;
   }
   void put(void* p, size_t bytes) {
-    if (p) {
-      cudaFree(p);
-      cur -= (int64_t)bytes;
-    }
+    if (!p) return;
+    cur -= (int64_t)bytes;
+    cache.emplace(bytes, p);
+    cached += (int64_t)bytes;
+    dirty = true;
   }
+  void trim() {
+    for (auto& kv : cache) cudaFree(kv.second);
+    cache.clear();
+    cached = 0;
+    dirty = false;
+  }
+  ~DevAlloc() { trim(); }
 };
 
 template <class T>

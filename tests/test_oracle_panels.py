@@ -170,3 +170,13 @@ def test_rows_match_dense(two_bars_mesh, two_bars_dense_P):
     G = P.Geometry(two_bars_mesh.xyz, two_bars_mesh.tri)
     rows = [0, 17, G.n - 1]
     np.testing.assert_array_equal(P.rows_P(G, rows), two_bars_dense_P[rows])
+
+
+def test_parallel_dense_matches_serial(two_bars_mesh, two_bars_dense_P):
+    """The spawn-pool evaluator of the stored package sweep: the serial dense
+    P's entries, with a block size that leaves a ragged last block.  The pair
+    batches differ in size, and numpy's vectorised sums may round a batch
+    differently (seen: 1 ulp on 0.01% of the entries), so rtol 1e-14."""
+    Pp = P.dense_P_parallel(two_bars_mesh.xyz, two_bars_mesh.tri, workers=2, block=37)
+    np.testing.assert_allclose(Pp, two_bars_dense_P, rtol=1e-14, atol=0)
+    np.testing.assert_array_equal(Pp, Pp.T)
