@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--restart", type=int, default=150, help="FGMRES restart of the package workloads")
     ap.add_argument("--tol", type=float, default=1e-6, help="relative residual of the package workloads")
     ap.add_argument("--freqs", type=int, default=0, help="package workloads: solve only the first N frequencies")
+    ap.add_argument("--freq-stride", type=int, default=1,
+                    help="package workloads with --freqs: take every k-th frequency of the sweep, then the first N")
     ap.add_argument("--fp64tc-arm", action="store_true", help="package workloads: one FP64-accurate sweep too")
     ap.add_argument("--chunk", type=int, default=64, help="package workloads: systems per frequency chunk when "
                                                            "the sweep has more than 128")
@@ -293,14 +295,23 @@ NCU_TRAFFIC = {(7, 16, 2, 384): {"m2l": 83.342848e6 + 30.363904e6,     # k_xlate
                                   "p2p": 438.394624e6 + 33.091072e6}}   # k_xlate_tc2<1>
 
 
-def phase_kernel(name, p):
+def m2l_products(p, targets):
+    """Tensor-core products per algorithmic flop of the FP32 M2L: the two-target
+    kernel (64-coefficient tiles) runs 2-piece FP16 operands, 3 products; the
+    one-target kernel 3-piece BF16, 6 products."""
+    np_ = ((p + 1) ** 2 + 15) // 16 * 16
+    return 3 if (np_ == 64 and targets == 2) else 6
+
+
+def phase_kernel(name, p, targets=2):
     """Kernels behind a profiling phase of the mixed-precision sweep at order p."""
     np_ = ((p + 1) ** 2 + 15) // 16 * 16
     tc = "k_xlate_tc<%d>" % (64 if np_ <= 64 else 96)
     return {
         "p2p": "k_tcp_pack_x + k_xlate_tc2<1> (tcgen05 near field, two sibling leaves per CTA, 3-piece BF16)",
-        "m2l": ("k_tc_pack_a + k_xlate_tc2 (tcgen05, two sibling targets per CTA, N = 128, 3-piece BF16, "
-                "6 products)" if np_ == 64 else "k_tc_pack_a + k_xlate_tc<96> (tcgen05, 3-piece BF16, 6 products)"),
+        "m2l": ("k_tch_pack_a + k_xlate_tc2<0> (tcgen05, two sibling targets per CTA, N = 128, 2-piece FP16, "
+                "3 products)" if m2l_products(p, targets) == 3 else
+                "k_tc_pack_a + %s (tcgen05, one target per CTA, 3-piece BF16, 6 products)" % tc),
         "p2m": tc + " mode 2 (tcgen05 P2M from the near field's transposed-X image) + k_p2m_df64 (residuals)",
         "m2m": "k_tc_pack_a + " + tc + " mode 0 over the 8 M2M tables (tcgen05) + k_m2l_df64<0> (residuals)",
         "p2p64": "k_ozp_pack_x + k_xlate_oz (tcgen05 near field, 5 integer slices)",
@@ -311,7 +322,7 @@ def phase_kernel(name, p):
         "l2l": "k_m2l_tiled<%d,1> list form + k_m2l_df64<1> (residuals)" % ((np_ + 15) // 16)}.get(name, name)
 
 
-def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0, traffic=None):
+def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0, traffic=None, targets=2):
     """Roofline entry of one profiling phase: ALGORITHMIC flops (or bytes) per
     launch over the phase's CUDA-event time per launch, against the peak of the
     unit that executes them.  For the tensor-core phases the FP32 (or
@@ -320,20 +331,20 @@ def phase_roofline(name, d, pk, precision, p, nc, near_pad=0.0, traffic=None):
     avg_ms = d["ms"] / max(1, d["launches"])
     mixed = precision == "mixed"
     alg = d["flops"] / (d["ms"] * 1e-3) / 1e12          # algorithmic TFLOP/s
-    out = {"kernel": phase_kernel(name, p), "avg_launch_ms": avg_ms, "launches": d["launches"],
+    out = {"kernel": phase_kernel(name, p, targets), "avg_launch_ms": avg_ms, "launches": d["launches"],
            "traffic": traffic.get(name) if traffic else None}
     ncoef = (p + 1) ** 2
     pad = lambda v: (v + 15) // 16 * 16
     tile_pad = (pad(ncoef) * pad(ncoef)) / float(ncoef * ncoef) * (128 * ((nc + 127) // 128)) / float(nc)
     col_pad = (128 * ((nc + 127) // 128)) / float(nc)
     if mixed and (name in ("m2l", "m2l64") or (name in ("p2p", "p2p64") and near_pad > 0)):
-        products = 6 if name in ("m2l", "p2p") else 15
+        products = m2l_products(p, targets) if name == "m2l" else (6 if name == "p2p" else 15)
         padf = tile_pad if name.startswith("m2l") else near_pad * col_pad
         issued = alg * products * padf                    # BF16 MMA TFLOP/s actually issued
         out.update({"bound": "tensor", "achieved": alg, "peak": pk["bf16_sust"], "unit": "TFLOP/s",
                     "frac": alg / pk["bf16_sust"], "peak_src": pk["bf16_src"],
-                    "issued_bf16_tflops": issued, "issued_frac": issued / pk["bf16_sust"],
-                    "note": "achieved = algorithmic FP%s flops/s; the tensor pipe issues %d BF16 products x "
+                    "issued_mma_tflops": issued, "issued_frac": issued / pk["bf16_sust"],
+                    "note": "achieved = algorithmic FP%s flops/s; the tensor pipe issues %d 16-bit products x "
                             "padding %.3f per algorithmic flop" % ("32" if name in ("m2l", "p2p") else "64",
                                                                    products, padf)})
     elif name in ("precond", "operator"):
@@ -586,7 +597,7 @@ def package_run(args):
     import paper_2409_12375_gb300 as pkg
     m = {"package": meshgen.package, "package_crop": meshgen.package_crop, "pop": meshgen.pop}[args.workload]()
     if args.freqs:
-        m.freqs = m.freqs[:args.freqs]
+        m.freqs = m.freqs[::max(1, args.freq_stride)][:args.freqs]
     nport = len(m.ports)
     nsys = len(m.freqs) * nport
     chunk = args.chunk if nsys > 128 or args.freqs else 0
@@ -604,8 +615,20 @@ def package_run(args):
         tuned = {"leaf_target": leaf, "fmm_order": order, "product_ms": ms, "product_err": err,
                  "tc_targets_per_cta": x.stats()["tc_targets_per_cta"], "autotune_s": time.perf_counter() - t0}
     st = x.stats()
+    print("setup %.1f s: %d panels, %d loops, %d leaves, %d near entries, peak %.1f GB" %
+          (setup_s, st["n_panels"], st["n_loops"], st["n_leaves"], st["near_nnz"], st["peak_device_bytes"] / 1e9),
+          file=sys.stderr, flush=True)
+    print("after setup: %.1f GB held, %.1f GB cached" % (st["device_bytes"] / 1e9, st["cached_device_bytes"] / 1e9),
+          file=sys.stderr, flush=True)
     clocks = Clocks()
-    tm = time_sweeps(x, m.freqs, args.warmup, args.steps, clocks)
+    try:
+        tm = time_sweeps(x, m.freqs, args.warmup, args.steps, clocks)
+    except Exception:
+        sf = x.stats()
+        print("solve failed: %.1f GB held, %.1f GB cached, peak %.1f GB" %
+              (sf["device_bytes"] / 1e9, sf["cached_device_bytes"] / 1e9, sf["peak_device_bytes"] / 1e9),
+              file=sys.stderr, flush=True)
+        raise
     ck = clocks.stop(0)
     value = tm["dev_ms"] / 1e3 / (args.steps * nsys)
     ext = torch.cuda.ExternalStream(x.stream_handle())
@@ -653,7 +676,7 @@ def package_run(args):
             "config": {"workload": "%s: %d triangles, %d conductors, %d ports x %d freqs, tol %g, restart %d%s"
                                    % (args.workload, m.n_tri, int(m.cond.max()) + 1, nport, len(m.freqs), args.tol,
                                       args.restart, ", chunks of %d systems" % chunk if chunk else ""),
-                       "mac_theta": args.mac, "mg_cycles": mg,
+                       "freqs_hz": [float(f) for f in m.freqs], "mac_theta": args.mac, "mg_cycles": mg,
                        "autotune": tuned, "fmm_order": order, "leaf_target": leaf},
             "e2e": {"value": tm["host_s"] / (args.steps * nsys), "unit": UNIT, "h2d_bytes_per_step": 8 * len(m.freqs),
                     "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * nport ** 2},
@@ -741,7 +764,9 @@ def main():
     near_pad = st["near_nnz_padded"] / float(st["near_nnz"]) if st.get("near_nnz_padded") else 0.0
     key = (cfg_opts["fmm_order"], cfg_opts["leaf_target"], x.stats()["tc_targets_per_cta"], 6 * nsys)
     traffic = NCU_TRAFFIC.get(key) if args.precision == "mixed" else None
-    roofs = {k: phase_roofline(k, prof[k], pk, args.precision, cfg_opts["fmm_order"], 6 * nsys, near_pad, traffic)
+    tct = x.stats()["tc_targets_per_cta"]
+    roofs = {k: phase_roofline(k, prof[k], pk, args.precision, cfg_opts["fmm_order"], 6 * nsys, near_pad, traffic,
+                               tct)
              for k in ("p2p", "m2l", "p2p64", "m2l64", "precond", "operator", "p2m", "l2p", "m2m", "l2l")
              if k in prof and prof[k]["ms"] > 0}
     dom = max(roofs, key=lambda k: prof[k]["ms"])

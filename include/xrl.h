@@ -227,6 +227,9 @@ typedef struct {
                                pencil and band, 5 solver operator data */
   int32_t mg_levels;        /* levels of the multigrid hierarchy of Q (0: none built) */
   int32_t mg_coarse_n;      /* unknowns of its coarsest level */
+  int64_t device_bytes;     /* device memory the context's buffers hold now */
+  int64_t cached_device_bytes; /* freed blocks the context keeps for reuse (released when an
+                                  allocation fails, at every setup and at destroy) */
 } xrl_stats;
 
 /* FMM autotuner: tries leaf_target in {16, 32, 64} x fmm_order in {4, 6, 7, 8}

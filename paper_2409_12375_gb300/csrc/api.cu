@@ -671,6 +671,8 @@ xrl_status xrl_get_stats(const xrl_ctx* c, xrl_stats* out) {
   if (!c || !out) return XRL_EINVAL;
   *out = c->stats;
   out->peak_device_bytes = c->alloc.peak;
+  out->device_bytes = c->alloc.cur;
+  out->cached_device_bytes = c->alloc.cached;
   return XRL_OK;
 }
 

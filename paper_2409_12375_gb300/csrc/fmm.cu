@@ -1119,7 +1119,9 @@ void fmm_prepare(xrl_ctx* c) {
   cast(c->d.t_m2m, c->d.t_m2m32);
   cast(c->d.t_l2l, c->d.t_l2l32);
   cast(c->d.t_m2l, c->d.t_m2l32);
-  cast(c->d.near_val, c->d.near_val32);
+  // the FP32 near-field copy is made on first use: products on the tensor
+  // cores (>= 64 columns) read the near-block image instead
+  c->d.near_val32 = DBuf<float>();
   cast(c->d.mom, c->d.mom32);
   c->d.mom_hl.alloc(c->alloc, c->d.mom.n);
   c->d.momw_hl.alloc(c->alloc, c->d.mom.n);
@@ -1135,6 +1137,20 @@ void fmm_prepare(xrl_ctx* c) {
         c->d.mom.n, c->ncoef, (double)(1 << t.L) / t.side, c->d.mom.p, c->d.mom32w.p);
   XRL_CUDA(cudaGetLastError());
   XRL_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+// The FP64-accurate near field of the mixed solver's residuals reads an extra
+// image of the near blocks: integer slices (~10 B per padded entry) or the
+// double-float split (8 B per entry), made on first use.  Each is made only
+// if it fits beside what the context holds (free device memory plus the
+// context's cached blocks, less a reserve for the products' work buffers);
+// otherwise the residual takes the next path down, and at the end the plain
+// FP64 kernel, which reads the FP64 values themselves.
+static bool image_fits(xrl_ctx* c, double bytes) {
+  size_t fr = 0, tot = 0;
+  XRL_CUDA(cudaMemGetInfo(&fr, &tot));
+  const double reserve = std::max(8e9, 0.05 * (double)tot);
+  return bytes <= (double)fr + (double)c->alloc.cached - reserve;
 }
 
 template <class T>
@@ -1168,7 +1184,8 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
   if (sizeof(T) == 4 && tcp_usable(c, nc)) {
     tc_p2p_fork(c, nc, (const float*)X, (float*)Y, s, sp);
     nl_p2p = 2;
-  } else if (sizeof(T) == 8 && c->df64_m2l && tcp_usable(c, nc)) {
+  } else if (sizeof(T) == 8 && c->df64_m2l && tcp_usable(c, nc) &&
+             (c->d.ozp_vimg.n > 0 || image_fits(c, (double)c->ozp_img_bytes))) {
     tc_p2p64(c, nc, (const double*)X, (double*)Y, s);
     nl_p2p = 2;
   } else if (sizeof(T) == 4 && nc >= 32) {
@@ -1176,7 +1193,8 @@ static void fmm_apply_t(xrl_ctx* c, int nc, const T* X, T* Y, const T* near, con
     k_p2p_tiled<<<gt, 128, 0, s>>>(nc, c->d.leaf_first.p, c->d.leaf_count.p, c->d.near_off.p, c->d.near_w.p,
                                    c->d.near_col_off.p, c->d.near_src.p, (const float*)near, (const float*)X,
                                    (float*)Y);
-  } else if (sizeof(T) == 8 && c->df64_m2l && nc >= 32) {
+  } else if (sizeof(T) == 8 && c->df64_m2l && nc >= 32 &&
+             (c->d.near_hl.n > 0 || image_fits(c, 8.0 * (double)c->d.near_val.n))) {
     if (c->d.near_hl.n == 0) {
       c->d.near_hl.alloc(c->alloc, c->d.near_val.n);
       k_split_df<<<(unsigned)((c->d.near_val.n + 255) / 256), 256, 0, s>>>(c->d.near_val.n, c->d.near_val.p,
@@ -1330,6 +1348,12 @@ void fmm_apply_into(xrl_ctx* c, int nc, const double* X, double* Y, double* Mx, 
 }
 
 void fmm_apply32(xrl_ctx* c, int nc, const float* X, float* Y, cudaStream_t s) {
+  if (!tcp_usable(c, nc) && c->d.near_val32.n == 0 && c->d.near_val.n > 0) {
+    c->d.near_val32.alloc(c->alloc, c->d.near_val.n);
+    k_cast<float><<<(unsigned)((c->d.near_val.n + 255) / 256), 256, 0, s>>>(c->d.near_val.n, c->d.near_val.p,
+                                                                          c->d.near_val32.p);
+    count_launch(c);
+  }
   size_t ne = (size_t)c->tree.n_boxes() * c->ncoef * nc;
   c->d.M32.ensure(c->alloc, ne);
   c->d.L32.ensure(c->alloc, ne);

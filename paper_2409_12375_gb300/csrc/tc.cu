@@ -9,8 +9,11 @@
 // accuracy comes from a three-piece BF16 split x = x0 + x1 + x2 (x0 = bf16(x),
 // x1 = bf16(x - x0), x2 = bf16(x - x0 - x1); residual ~2^-27 |x|) and the six
 // products x_i y_j with i + j <= 2 (the dropped ones are ~2^-27 relative), all
-// exact in FP32 and accumulated in FP32 by the tensor core.  (A two-piece TF32
-// split keeps only ~2^-21 per product, measurably worse than FP32.)
+// exact in FP32 and accumulated in FP32 by the tensor core.  The two-target
+// M2L (64-coefficient tiles) instead splits power-of-two-scaled operands into
+// two FP16 pieces (22 bits) and runs three products: ~2^-21 per term, below
+// the expansion's own truncation, in half the MMAs (see k_tch_pack_a).  (A
+// two-piece TF32 split reaches the same ~2^-21 at half the FP16 rate.)
 //
 // Operands live in global memory as "packed images" in the tensor core's
 // K-major, no-swizzle shared-memory layout, so that one pipeline stage is two
@@ -32,6 +35,7 @@
 // the M2L at <= 64 coefficients and the near field), k_xlate_oz (the
 // FP64-accurate M2L, M2M and near field in integer slices).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <climits>
@@ -48,6 +52,8 @@ constexpr int TC_ROWS = 128;     // columns per tile (MMA M)
 constexpr int TC_KC = 32;        // K chunk per pipeline stage (elements)
 constexpr int TC_STAGES = 4;
 constexpr int TC_PIECES = 3;
+constexpr int TCH_PIECES = 2;     // FP16 pieces of the two-target M2L operands
+constexpr int TCH_TOP = 14;       // scaled operands stay below 2^14 (FP16 max 65504)
 constexpr long long TC_WAIT_CYCLES = 4000000000ll;   // ~2 s at the maximum SM clock
 
 // bytes of one K chunk (all pieces) of an operand of R rows
@@ -80,6 +86,8 @@ __device__ __forceinline__ uint32_t sm_u32(const void* p) { return (uint32_t)__c
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float bf16_val(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+__device__ __forceinline__ uint16_t f16_bits(float x) { return __half_as_ushort(__float2half_rn(x)); }
+__device__ __forceinline__ float f16_val(uint16_t b) { return __half2float(__ushort_as_half(b)); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_u32(b)), "r"(count) : "memory");
@@ -195,6 +203,96 @@ __global__ void k_tc_pack_b(int ncoef, int Kp, int Np, const double* __restrict_
     *reinterpret_cast<uint16_t*>(dst + tc_img_off(Np, Kp, r, k, 0)) = b0;
     *reinterpret_cast<uint16_t*>(dst + tc_img_off(Np, Kp, r, k, 1)) = b1;
     *reinterpret_cast<uint16_t*>(dst + tc_img_off(Np, Kp, r, k, 2)) = b2;
+  }
+}
+
+// ---- two-piece FP16 operands of the two-target M2L ------------------------------------
+// x = x0 + x1 with x0 = fp16(x), x1 = fp16(x - x0) keeps 22 significant bits;
+// the three products x0 y0, x0 y1, x1 y0 leave ~2^-21 relative per term, below
+// the order-7 truncation of the expansion (~1e-6), in half the MMAs of the
+// three-piece BF16 split.  FP16 has a 5-bit exponent, so both operands are
+// scaled by powers of two (exact): the coefficient equilibration 2^-d_k (A)
+// and 2^d_k (B) of the FP64-accurate path, then per A row (one right-hand
+// side column of one source box) 2^(TCH_TOP - e_A) and per B column (one
+// output coefficient n, over all tables) 2^(TCH_TOP - e_n), with 2^e the
+// power of two above the row's / column's largest entry.  The epilogue
+// multiplies each pair's partial sums by its row scale 2^(e_A - TCH_TOP) and
+// the finished sum by 2^(e_n - TCH_TOP).  Entries far below their row or
+// column maximum keep fewer bits (FP16 subnormals), an absolute error below
+// 2^-38 of that maximum.
+
+// Pack FP32 multipoles in[box][k][col] (boxes [b0, b0 + gridDim.x), column
+// tile blockIdx.y) into the two-piece FP16 A image; ascale[tile][r] receives
+// the row's 2^(e_A - TCH_TOP).  Columns >= nc and k >= ncoef are zero.
+__global__ void k_tch_pack_a(int nc, int ncoef, int Kp, int b0, const int32_t* __restrict__ dk,
+                             const float* __restrict__ in, uint16_t* __restrict__ img, float* __restrict__ ascale) {
+  __shared__ int eA[TC_ROWS];
+  const int ct = blockIdx.y;
+  const size_t tile = (size_t)blockIdx.x * gridDim.y + ct;
+  const float* src = in + (size_t)(b0 + blockIdx.x) * ncoef * nc + (size_t)ct * TC_ROWS;
+  char* dst = reinterpret_cast<char*>(img) + tile * (size_t)(TCH_PIECES * 2 * TC_ROWS * Kp);
+  for (int r = threadIdx.x; r < TC_ROWS; r += blockDim.x) {
+    float mx = 0.f;
+    if (ct * TC_ROWS + r < nc)
+      for (int k = 0; k < ncoef; ++k) mx = fmaxf(mx, fabsf(ldexpf(src[(size_t)k * nc + r], -dk[k])));
+    const int e = mx > 0.f ? ilogbf(mx) + 1 : 0;
+    eA[r] = e;
+    ascale[tile * TC_ROWS + r] = ldexpf(1.f, e - TCH_TOP);
+  }
+  __syncthreads();
+  const int nq = Kp >> 3;
+  for (int e = threadIdx.x; e < TC_ROWS * nq; e += blockDim.x) {
+    const int r = e & (TC_ROWS - 1), kq = e >> 7;
+    const bool col_ok = ct * TC_ROWS + r < nc;
+    const int sh = TCH_TOP - eA[r];
+    uint16_t p0[8], p1[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = 8 * kq + q;
+      const float x = (col_ok && k < ncoef) ? ldexpf(src[(size_t)k * nc + r], sh - dk[k]) : 0.f;
+      p0[q] = f16_bits(x);
+      p1[q] = f16_bits(x - f16_val(p0[q]));
+    }
+    uint4 v0, v1;
+    v0.x = p0[0] | (uint32_t)p0[1] << 16; v0.y = p0[2] | (uint32_t)p0[3] << 16;
+    v0.z = p0[4] | (uint32_t)p0[5] << 16; v0.w = p0[6] | (uint32_t)p0[7] << 16;
+    v1.x = p1[0] | (uint32_t)p1[1] << 16; v1.y = p1[2] | (uint32_t)p1[3] << 16;
+    v1.z = p1[4] | (uint32_t)p1[5] << 16; v1.w = p1[6] | (uint32_t)p1[7] << 16;
+    *reinterpret_cast<uint4*>(dst + oz_img_off(TC_ROWS, Kp, r, 8 * kq, 0, TCH_PIECES)) = v0;
+    *reinterpret_cast<uint4*>(dst + oz_img_off(TC_ROWS, Kp, r, 8 * kq, 1, TCH_PIECES)) = v1;
+  }
+}
+
+// Pack the FP64 M2L tables T[o][k_in][n_out] into two-piece FP16 B images (Np
+// rows n by Kp), T'[k][n] = T[k][n] 2^(d_k + TCH_TOP - en[n]).
+__global__ void k_tch_pack_b(int ncoef, int Kp, int Np, const int32_t* __restrict__ dk, const int32_t* __restrict__ en,
+                             const double* __restrict__ T, uint16_t* __restrict__ img) {
+  const int o = blockIdx.x;
+  const double* tm = T + (size_t)o * ncoef * ncoef;
+  char* dst = reinterpret_cast<char*>(img) + (size_t)o * (size_t)(TCH_PIECES * 2 * Np * Kp);
+  for (int e = threadIdx.x; e < Np * Kp; e += blockDim.x) {
+    const int r = e % Np, k = e / Np;
+    const double x = (r < ncoef && k < ncoef) ? ldexp(tm[(size_t)k * ncoef + r], dk[k] + TCH_TOP - en[r]) : 0.0;
+    const uint16_t b0 = f16_bits(__double2float_rn(x));
+    const uint16_t b1 = f16_bits(__double2float_rn(x - (double)f16_val(b0)));
+    *reinterpret_cast<uint16_t*>(dst + oz_img_off(Np, Kp, r, k, 0, TCH_PIECES)) = b0;
+    *reinterpret_cast<uint16_t*>(dst + oz_img_off(Np, Kp, r, k, 1, TCH_PIECES)) = b1;
+  }
+}
+
+// Largest |S[i][k]| per coefficient k of the panel moments (positive doubles
+// order as their bit patterns); out[] zeroed by the caller.
+__global__ void k_colmax_abs(size_t n, int ncoef, const double* __restrict__ S, unsigned long long* __restrict__ out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    atomicMax(out + (i % ncoef), (unsigned long long)__double_as_longlong(fabs(S[i])));
+}
+
+// Largest |T[o][k][n] 2^d_k| per output coefficient n over all tables.
+__global__ void k_tch_colmax(size_t n, int ncoef, const int32_t* __restrict__ dk, const double* __restrict__ T,
+                             unsigned long long* __restrict__ out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)((i / ncoef) % ncoef);
+    atomicMax(out + (i % ncoef), (unsigned long long)__double_as_longlong(fabs(ldexp(T[i], dk[k]))));
   }
 }
 
@@ -521,6 +619,8 @@ struct Tc2Args {
   const int32_t* leaf_f0;
   const int32_t* leaf_n;
   const int64_t* pair_boff;            // mode 1: byte offset of each pair's near-block image
+  const float* ascale;                 // mode 0: 2^(e_A - TCH_TOP) per (source box, tile, row)
+  const float* oscale;                 // mode 0: 2^(e_n - TCH_TOP) per output coefficient n
   const char* aimg;
   const char* bimg;
   float* out;
@@ -582,12 +682,43 @@ __device__ __forceinline__ void drain_half(float (&acc)[128], uint32_t taddr) {
   }
 }
 
+// acc[OFF + n] += sc * (both accumulators, small first) of one 64-column half
+template <int OFF>
+__device__ __forceinline__ void drain_half_scaled(float (&acc)[128], uint32_t taddr, float sc) {
+#pragma unroll
+  for (int s = 1; s >= 0; --s) {
+#pragma unroll
+    for (int h = 0; h < 64; h += 32) {
+      uint32_t r[32];
+#pragma unroll
+      for (int n0 = 0; n0 < 32; n0 += 16)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+            "[%16];"
+            : "=r"(r[n0 + 0]), "=r"(r[n0 + 1]), "=r"(r[n0 + 2]), "=r"(r[n0 + 3]), "=r"(r[n0 + 4]),
+              "=r"(r[n0 + 5]), "=r"(r[n0 + 6]), "=r"(r[n0 + 7]), "=r"(r[n0 + 8]), "=r"(r[n0 + 9]),
+              "=r"(r[n0 + 10]), "=r"(r[n0 + 11]), "=r"(r[n0 + 12]), "=r"(r[n0 + 13]), "=r"(r[n0 + 14]),
+              "=r"(r[n0 + 15])
+            : "r"(taddr + 128u * s + (uint32_t)(h + n0))
+            : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int n = 0; n < 32; ++n) acc[OFF + h + n] = fmaf(__uint_as_float(r[n]), sc, acc[OFF + h + n]);
+    }
+  }
+}
+
+// MODE 0 (M2L): two-piece FP16 operands, three products (x0 y0 into the big
+// accumulator, x0 y1 + x1 y0 into the small one), per-pair row scales and a
+// per-coefficient output scale.  MODE 1 (near field): three-piece BF16, six
+// products.
 template <int MODE>
 __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
+  constexpr int PC = MODE == 0 ? TCH_PIECES : TC_PIECES;
   extern __shared__ uint8_t tc_smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
-  const int a_stage = tc_chunk_bytes(TC_ROWS, TC_KC);
-  const int stage_bytes = a_stage + tc_chunk_bytes(128, TC_KC);
+  const int a_stage = oz_chunk_bytes(TC_ROWS, TC_KC, PC);
+  const int stage_bytes = a_stage + oz_chunk_bytes(128, TC_KC, PC);
   uint64_t* full = reinterpret_cast<uint64_t*>(base + TC_STAGES * stage_bytes);
   uint64_t* empty = full + TC_STAGES;
   uint64_t* tfull = empty + TC_STAGES;
@@ -646,12 +777,12 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
             break;
           }
           const int kc = min(TC_KC, K - TC_KC * c);
-          const uint32_t ab = tc_chunk_bytes(TC_ROWS, kc);
+          const uint32_t ab = oz_chunk_bytes(TC_ROWS, kc, PC);
           uint8_t* sa = base + (size_t)st * stage_bytes;
           uint8_t* sb = sa + a_stage;
           uint32_t bb = 0;
           for (int t = 0; t < 2; ++t)
-            if (vt[t] >= 0) bb += TC_PIECES * Nt[t] * kc * 2;
+            if (vt[t] >= 0) bb += PC * Nt[t] * kc * 2;
           mbar_expect_tx(&full[st], ab + bb);
           bulk_g2s(sa, a.aimg + aoff + (size_t)a_stage * c, ab, &full[st]);
           // piece h of target t's B chunk -> rows [64 t, 64 t + N_t) of merged piece h
@@ -659,9 +790,9 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
             if (vt[t] < 0) continue;
             const uint32_t pbytes = Nt[t] * kc * 2;
             const char* bsrc = a.bimg + (MODE == 0 ? (size_t)vt[t] * a.b_img : (size_t)a.pair_boff[vt[t]]) +
-                               (size_t)tc_chunk_bytes(Nt[t], TC_KC) * c;
+                               (size_t)oz_chunk_bytes(Nt[t], TC_KC, PC) * c;
             uint8_t* bdst = sb + (size_t)t * 64 * kc * 2;
-            for (int h = 0; h < TC_PIECES; ++h)
+            for (int h = 0; h < PC; ++h)
               bulk_g2s(bdst + (size_t)h * PW * kc * 2, bsrc + (size_t)h * pbytes, pbytes, &full[st]);
           }
           issued = it + 1;
@@ -671,7 +802,9 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t id0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_ROWS >> 4) << 24);
+      // D F32; A, B BF16 (MODE 1) or F16 (MODE 0, type code 0); K-major
+      const uint32_t id0 =
+          (1u << 4) | (MODE == 0 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(TC_ROWS >> 4) << 24);
       int it = 0;
       bool stop = false;
       for (int v = vs, j = 0; v < ve && !stop; ++v, ++j) {
@@ -710,11 +843,16 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
             const uint64_t b0 = dB + k16, b1 = b0 + pb16, b2 = b1 + pb16;
             const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
             mma_bf16(dbig, a0, b0, idesc, accum);
-            mma_bf16(dsmall, a1, b1, idesc, accum);
-            mma_bf16(dsmall, a0, b2, idesc, 1u);
-            mma_bf16(dsmall, a2, b0, idesc, 1u);
-            mma_bf16(dsmall, a0, b1, idesc, 1u);
-            mma_bf16(dsmall, a1, b0, idesc, 1u);
+            if (MODE == 0) {
+              mma_bf16(dsmall, a0, b1, idesc, accum);
+              mma_bf16(dsmall, a1, b0, idesc, 1u);
+            } else {
+              mma_bf16(dsmall, a1, b1, idesc, accum);
+              mma_bf16(dsmall, a0, b2, idesc, 1u);
+              mma_bf16(dsmall, a2, b0, idesc, 1u);
+              mma_bf16(dsmall, a0, b1, idesc, 1u);
+              mma_bf16(dsmall, a1, b0, idesc, 1u);
+            }
           }
           tc_commit(&empty[st]);
           if (c == nchv - 1) tc_commit(&tfull[q]);
@@ -741,9 +879,11 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
       }
       tc_fence_after();
       const uint32_t tq = tbase + lane_base + 256u * q;
-      if (MODE == 0) {   // both halves 64 wide: compile-time columns
-        if (p1) drain_half<0>(acc, tq);
-        if (p2) drain_half<64>(acc, tq + 64u);
+      if (MODE == 0) {   // both halves 64 wide: compile-time columns; this row's scale for the source box
+        const float sc =
+            a.ascale[((size_t)(a.gsrc[vs + j] - a.src0) * a.nct + ct) * TC_ROWS + 32 * quarter + lane];
+        if (p1) drain_half_scaled<0>(acc, tq, sc);
+        if (p2) drain_half_scaled<64>(acc, tq + 64u, sc);
       } else {
         drain_range(acc, tq, p1 ? N1 : 0, p2 ? N2 : 0);
       }
@@ -759,6 +899,10 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
       const size_t r2 = t2 < 0 ? 0 : (MODE == 0 ? (size_t)t2 * a.ncoef : (size_t)a.leaf_f0[t2]);
       float* o1 = a.out + r1 * a.nc + col;
       float* o2 = a.out + r2 * a.nc + col;
+      if (MODE == 0) {
+#pragma unroll
+        for (int n = 0; n < 128; ++n) acc[n] *= __ldg(a.oscale + (n & 63));
+      }
 #pragma unroll
       for (int n = 0; n < 128; ++n) {
         if (t2 < 0 || n < 64) {
@@ -784,21 +928,24 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
   }
 }
 
+template <int MODE>
 static size_t tc2_smem() {
-  return (size_t)TC_STAGES * (tc_chunk_bytes(TC_ROWS, TC_KC) + tc_chunk_bytes(128, TC_KC)) + 1024 + 128;
+  constexpr int PC = MODE == 0 ? TCH_PIECES : TC_PIECES;
+  return (size_t)TC_STAGES * (oz_chunk_bytes(TC_ROWS, TC_KC, PC) + oz_chunk_bytes(128, TC_KC, PC)) + 1024 + 128;
 }
 
 template <int MODE>
 static void launch_tc2_m(xrl_ctx* c, dim3 grid, const Tc2Args& g, cudaStream_t s) {
   static bool set = false;
   if (!set) {
-    XRL_CUDA(cudaFuncSetAttribute(k_xlate_tc2<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2_smem()));
+    XRL_CUDA(
+        cudaFuncSetAttribute(k_xlate_tc2<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc2_smem<MODE>()));
     set = true;
   }
   Tc2Args a = g;
   for (unsigned y0 = 0; y0 < grid.y; y0 += kMaxGridY) {
     a.y0 = (int)y0;
-    k_xlate_tc2<MODE><<<dim3(grid.x, std::min(kMaxGridY, grid.y - y0)), 192, tc2_smem(), s>>>(a);
+    k_xlate_tc2<MODE><<<dim3(grid.x, std::min(kMaxGridY, grid.y - y0)), 192, tc2_smem<MODE>(), s>>>(a);
     if (y0 > 0) count_launch(c);   // callers count one launch per translation
   }
 }
@@ -1493,6 +1640,8 @@ static void p2p_groups(xrl_ctx* c, const std::vector<int32_t>& pc) {
                c->d.p2p_gt2, c->d.p2p_gv1, c->d.p2p_gv2);
 }
 
+static void tch_prepare(xrl_ctx* c, int noff);
+
 void tc_prepare(xrl_ctx* c) {
   const int ncoef = c->ncoef;
   if (c->opt.tensor_cores == 0) return;
@@ -1508,7 +1657,10 @@ void tc_prepare(xrl_ctx* c) {
   c->d.tc_bimg.alloc(c->alloc, (size_t)noff * TC_PIECES * Np * Kp);
   k_tc_pack_b<<<noff, 256, 0, c->stream>>>(ncoef, Kp, Np, c->d.t_m2l.p, c->d.tc_bimg.p);
   XRL_CUDA(cudaGetLastError());
-  if (Np == 64) m2l_groups(c);
+  if (Np == 64) {
+    m2l_groups(c);
+    tch_prepare(c, noff);
+  }
   if (c->d.tcp_vimg.n > 0) tcm_prepare(c);
 }
 
@@ -1574,9 +1726,13 @@ void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cud
   const int nct = (nc + TC_ROWS - 1) / TC_ROWS;
   const int src0 = t.level_off[2];
   const int nsrc = t.n_boxes() - src0;
-  c->d.tc_aimg.ensure(c->alloc, (size_t)nsrc * nct * TC_PIECES * TC_ROWS * Kp);
-  k_tc_pack_a<<<dim3(nsrc, nct), 256, 0, s>>>(nc, ncoef, Kp, src0, Mx, c->d.tc_aimg.p);
-  if (Np == 64 && c->tc_targets == 2 && c->d.m2l_gptr.n > 1 && b0 == src0 && nbx == nsrc) {
+  if (Np == 64 && c->tc_targets == 2 && c->d.m2l_gptr.n > 1 && c->d.tch_bimg.n > 0 && b0 == src0 &&
+      nbx == nsrc) {
+    // two sibling targets per CTA, two-piece FP16 operands
+    c->d.tch_aimg.ensure(c->alloc, (size_t)nsrc * nct * TCH_PIECES * TC_ROWS * Kp);
+    c->d.tch_ascale.ensure(c->alloc, (size_t)nsrc * nct * TC_ROWS);
+    k_tch_pack_a<<<dim3(nsrc, nct), 256, 0, s>>>(nc, ncoef, Kp, src0, c->d.oz_dk.p, Mx, c->d.tch_aimg.p,
+                                                 c->d.tch_ascale.p);
     Tc2Args g = {};
     g.mode = 0;
     g.nc = nc;
@@ -1584,21 +1740,25 @@ void tc_m2l(xrl_ctx* c, int nbx, int b0, int nc, const float* Mx, float* Lx, cud
     g.Kp = Kp;
     g.ncoef = ncoef;
     g.src0 = src0;
-    g.a_img = (size_t)TC_PIECES * 2 * TC_ROWS * Kp;
-    g.b_img = (size_t)TC_PIECES * 2 * Np * Kp;
+    g.a_img = (size_t)TCH_PIECES * 2 * TC_ROWS * Kp;
+    g.b_img = (size_t)TCH_PIECES * 2 * Np * Kp;
     g.gptr = c->d.m2l_gptr.p;
     g.gsrc = c->d.m2l_gsrc.p;
     g.gv1 = c->d.m2l_gv1.p;
     g.gv2 = c->d.m2l_gv2.p;
     g.gt1 = c->d.m2l_gt1.p;
     g.gt2 = c->d.m2l_gt2.p;
-    g.aimg = reinterpret_cast<const char*>(c->d.tc_aimg.p);
-    g.bimg = reinterpret_cast<const char*>(c->d.tc_bimg.p);
+    g.ascale = c->d.tch_ascale.p;
+    g.oscale = c->d.tch_oscale.p;
+    g.aimg = reinterpret_cast<const char*>(c->d.tch_aimg.p);
+    g.bimg = reinterpret_cast<const char*>(c->d.tch_bimg.p);
     g.out = Lx;
     g.err = c->d.tc_err.p;
     launch_tc2(c, dim3(nct, (unsigned)(c->d.m2l_gptr.n - 1)), g, s);
     return;
   }
+  c->d.tc_aimg.ensure(c->alloc, (size_t)nsrc * nct * TC_PIECES * TC_ROWS * Kp);
+  k_tc_pack_a<<<dim3(nsrc, nct), 256, 0, s>>>(nc, ncoef, Kp, src0, Mx, c->d.tc_aimg.p);
   TcArgs a;
   a.pr = m2l_pairs(c, b0, nct, TC_PIECES, (size_t)TC_PIECES * 2 * TC_ROWS * Kp, (size_t)TC_PIECES * 2 * Np * Kp);
   a.nc = nc;
@@ -1617,24 +1777,75 @@ bool tc64_usable(const xrl_ctx* c, int nc) {
 // One-time images of the FP64-accurate pass: the equilibration exponents d_k
 // (from the panel moments, the P2M operator: typical size of M[k]) and the
 // integer-slice images of the M2L and the 8 M2M tables.
+// Largest |x| per coefficient of an [*][ncoef] (or [o][k][ncoef]) FP64 array,
+// by a device reduction; the exponents are then taken on the host.
+static std::vector<double> colmax(xrl_ctx* c, size_t n, const double* x, const int32_t* dk, cudaStream_t s) {
+  const int ncoef = c->ncoef;
+  DBuf<unsigned long long> mx;
+  mx.alloc(c->alloc, ncoef);
+  XRL_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long) * ncoef, s));
+  if (n) {
+    const unsigned nb = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 64);
+    if (dk)
+      k_tch_colmax<<<nb, 256, 0, s>>>(n, ncoef, dk, x, mx.p);
+    else
+      k_colmax_abs<<<nb, 256, 0, s>>>(n, ncoef, x, mx.p);
+    count_launch(c);
+  }
+  std::vector<unsigned long long> h(ncoef);
+  XRL_CUDA(cudaMemcpyAsync(h.data(), mx.p, sizeof(unsigned long long) * ncoef, cudaMemcpyDeviceToHost, s));
+  XRL_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> out(ncoef);
+  for (int k = 0; k < ncoef; ++k) std::memcpy(&out[k], &h[k], sizeof(double));
+  return out;
+}
+
+// The power-of-two equilibration exponents d_k of the FP64-accurate and the
+// FP16 translations: 2^d_k is the size of the largest panel moment of index k
+// (the P2M operator), i.e. the typical size of the multipole coefficient k.
+static void ensure_dk(xrl_ctx* c, cudaStream_t s) {
+  if (c->d.oz_dk.n != 0) return;
+  const std::vector<double> mx = colmax(c, c->d.mom.n, c->d.mom.p, nullptr, s);
+  std::vector<int32_t> dk(c->ncoef, 0);
+  for (int k = 0; k < c->ncoef; ++k) dk[k] = mx[k] > 0.0 ? std::ilogb(mx[k]) : 0;
+  c->d.oz_dk.upload(c->alloc, dk);
+}
+
+// One-time images of the FP64-accurate pass: the equilibration exponents d_k
+// and the integer-slice images of the M2L and the 8 M2M tables.
 static void oz_prepare(xrl_ctx* c, cudaStream_t s) {
   if (c->d.oz_bimg.n != 0) return;
   const Tree& t = c->tree;
   const int ncoef = c->ncoef, Kp = tc_kpad(ncoef), Np = tc_npad(ncoef) <= 64 ? 64 : 96;
-  std::vector<double> mom = c->d.mom.download();
-  std::vector<int32_t> dk(ncoef, 0);
-  for (int k = 0; k < ncoef; ++k) {
-    double mx = 0.0;
-    for (size_t i = 0; i < (size_t)c->N; ++i) mx = std::max(mx, std::fabs(mom[i * ncoef + k]));
-    dk[k] = mx > 0.0 ? std::ilogb(mx) : 0;
-  }
-  c->d.oz_dk.upload(c->alloc, dk);
+  ensure_dk(c, s);
   const int noff = (int)(t.m2l_offsets.size() / 3);
   c->d.oz_bimg.alloc(c->alloc, (size_t)noff * OZ_S * Np * Kp);
   k_oz_pack_b<<<noff, 256, 0, s>>>(ncoef, Kp, Np, c->d.oz_dk.p, c->d.t_m2l.p, c->d.oz_bimg.p);
   c->d.oz_m2m_img.alloc(c->alloc, (size_t)8 * OZ_S * Np * Kp);
   k_oz_pack_b<<<8, 256, 0, s>>>(ncoef, Kp, Np, c->d.oz_dk.p, c->d.t_m2m.p, c->d.oz_m2m_img.p);
   count_launch(c, 2);
+}
+
+// The two-piece FP16 images of the M2L tables (64-coefficient tiles) and the
+// per-coefficient output scales of the two-target M2L.
+static void tch_prepare(xrl_ctx* c, int noff) {
+  const int ncoef = c->ncoef, Kp = tc_kpad(ncoef), Np = 64;
+  cudaStream_t s = c->stream;
+  ensure_dk(c, s);
+  const std::vector<double> mx = colmax(c, (size_t)noff * ncoef * ncoef, c->d.t_m2l.p, c->d.oz_dk.p, s);
+  std::vector<int32_t> en(Np, 0);
+  std::vector<float> osc(Np, 1.f);
+  for (int n = 0; n < ncoef; ++n) {
+    en[n] = mx[n] > 0.0 ? std::ilogb(mx[n]) + 1 : 0;
+    osc[n] = std::ldexp(1.f, en[n] - TCH_TOP);
+  }
+  DBuf<int32_t> den;
+  den.upload(c->alloc, en);
+  c->d.tch_oscale.upload(c->alloc, osc);
+  c->d.tch_bimg.alloc(c->alloc, (size_t)noff * TCH_PIECES * Np * Kp);
+  k_tch_pack_b<<<noff, 256, 0, s>>>(ncoef, Kp, Np, c->d.oz_dk.p, den.p, c->d.t_m2l.p, c->d.tch_bimg.p);
+  XRL_CUDA(cudaGetLastError());
+  XRL_CUDA(cudaStreamSynchronize(s));   // den is released on return
 }
 
 // one level of the FP64-accurate M2M (parents at level l from their children

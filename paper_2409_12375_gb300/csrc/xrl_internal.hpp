@@ -74,7 +74,8 @@ struct DevAlloc {
     }
     if (e != cudaSuccess)
       throw Error(e == cudaErrorMemoryAllocation ? XRL_ENOMEM : XRL_ECUDA,
-                  std::string("cudaMalloc(&p, bytes): ") + cudaGetErrorString(e));
+                  std::string("cudaMalloc of ") + std::to_string(bytes >> 20) + " MiB with " +
+                      std::to_string(cur >> 20) + " MiB held: " + cudaGetErrorString(e));
     cur += (int64_t)bytes;
     if (cur + cached > peak) peak = cur + cached;
     return p;
@@ -250,6 +251,10 @@ struct Dev {
   DBuf<int16_t> box_oct16;  // octant as a translation index
   DBuf<uint16_t> tc_bimg;   // packed 3-piece BF16 images of the M2L tables (tensor-core path)
   DBuf<uint16_t> tc_aimg;   // packed 3-piece BF16 images of the FP32 multipoles, per product
+  DBuf<uint16_t> tch_bimg;  // two-piece FP16 images of the M2L tables (two-target M2L)
+  DBuf<uint16_t> tch_aimg;  // two-piece FP16 images of the FP32 multipoles, per product
+  DBuf<float> tch_ascale;   // their row scales 2^(e_A - 14), per (box, tile, row)
+  DBuf<float> tch_oscale;   // output scales 2^(e_n - 14) per coefficient
   // M2L and near field by sibling pairs (k_xlate_tc2): per group its two
   // targets and the merged list (source, entry of t1 or -1, entry of t2 or -1)
   DBuf<int32_t> m2l_gptr, m2l_gsrc, m2l_gt1, m2l_gt2, m2l_gv1, m2l_gv2;

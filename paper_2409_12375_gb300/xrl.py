@@ -44,7 +44,8 @@ class Stats(ctypes.Structure):
                 ("mvm_ms", ctypes.c_double), ("peak_device_bytes", ctypes.c_int64),
                 ("near_nnz_padded", ctypes.c_int64), ("precond_setup_ms", ctypes.c_double),
                 ("tc_targets_per_cta", ctypes.c_int32), ("setup_phase_ms", ctypes.c_double * 6),
-                ("mg_levels", ctypes.c_int32), ("mg_coarse_n", ctypes.c_int32)]
+                ("mg_levels", ctypes.c_int32), ("mg_coarse_n", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64), ("cached_device_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         out = {k: getattr(self, k) for k, _ in self._fields_}
