@@ -55,33 +55,58 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison step")
     ap.add_argument("--no-ablation", action="store_true",
                     help="skip the preconditioner comparison (diagonal-of-P vs diagonal-of-L, untimed)")
-    ap.add_argument("--fmm-order", type=int, default=7,
-                    help="expansion order p of the FMM with --no-autotune (7: the autotuner's choice here)")
-    ap.add_argument("--leaf-target", type=int, default=32, help="target panels per octree leaf")
+    ap.add_argument("--fmm-order", type=int, default=None,
+                    help="expansion order p of the FMM with --no-autotune (default 7: the autotuner's choice on the "
+                         "coils)")
+    ap.add_argument("--leaf-target", type=int, default=None,
+                    help="target panels per octree leaf (default 32; 64 on the PoP stack)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --fmm-order/--leaf-target as given instead of xrl_autotune's choice (FP64 product "
-                         "within 1e-6 of the direct sum, fastest inner product at the sweep's column count)")
-    ap.add_argument("--workload", default="coils", choices=["coils", "package", "package_crop", "pop"],
-                    help="coils: the default sweep; package: the BGA-like package (~250k triangles, 8 ports x 16 "
-                         "freqs); package_crop: its 2.8 mm window; pop: the package-on-package stack (~2.1M "
-                         "triangles, 16 ports x 64 freqs, frequency chunks of 64 systems)")
-    ap.add_argument("--restart", type=int, default=150, help="FGMRES restart of the package workloads")
+                         "within 1e-6 of the direct sum, fastest inner product at the sweep's column count); the "
+                         "PoP stack never autotunes (one setup per candidate is 1.5 min there)")
+    ap.add_argument("--workload", default="pop", choices=["coils", "package", "package_crop", "pop"],
+                    help="pop (default): the package-on-package stack (~2.1M triangles, 16 ports), the largest "
+                         "configuration that fits one GPU, at --freqs of its 64 frequencies; coils: the two-coil "
+                         "sweep (2 ports x 32 freqs, one 64-RHS block) with the comparison arms; package: the "
+                         "BGA-like package (~250k triangles, 8 ports x 16 freqs); package_crop: its 2.8 mm window")
+    ap.add_argument("--restart", type=int, default=None, help="FGMRES restart of the package workloads "
+                                                              "(default 150; 50 on the PoP stack)")
     ap.add_argument("--tol", type=float, default=1e-6, help="relative residual of the package workloads")
-    ap.add_argument("--freqs", type=int, default=0, help="package workloads: solve only the first N frequencies")
-    ap.add_argument("--freq-stride", type=int, default=1,
-                    help="package workloads with --freqs: take every k-th frequency of the sweep, then the first N")
+    ap.add_argument("--freqs", type=int, default=None,
+                    help="package workloads: solve N frequencies spread evenly over the sweep, both ends included "
+                         "(default: all; 2 on the PoP stack: 1 kHz and 10 GHz, one 16-system chunk each)")
     ap.add_argument("--fp64tc-arm", action="store_true", help="package workloads: one FP64-accurate sweep too")
-    ap.add_argument("--chunk", type=int, default=64, help="package workloads: systems per frequency chunk when "
-                                                           "the sweep has more than 128")
-    ap.add_argument("--mac", type=float, default=0.0, help="package workloads: bounding-sphere separation theta "
-                                                           "(0: the cell-distance rule)")
+    ap.add_argument("--chunk", type=int, default=None, help="package workloads: systems per frequency chunk when "
+                                                             "the sweep has more than 128 (default 64; 16 on the "
+                                                             "PoP stack)")
+    ap.add_argument("--mac", type=float, default=None, help="package workloads: bounding-sphere separation theta "
+                                                            "(0: the cell-distance rule; default 0, 0.6 on the PoP "
+                                                            "stack)")
     ap.add_argument("--sweep-case", action="store_true",
                     help="profiling case: one warm-up and one timed sweep of the coils at --fmm-order/--leaf-target "
                          "(mixed precision), no autotune, no comparison arms")
     ap.add_argument("--kernel-case", action="store_true",
                     help="profiling case: only the FMM products of one sweep's launch configuration "
                          "(FP32 inner product and the mixed mode's FP64 residual operator, 64 systems), 3 each")
-    return ap.parse_args()
+    a = ap.parse_args()
+    pop = a.workload == "pop" and not (a.sweep_case or a.kernel_case)
+    for k, v in (("fmm_order", 7), ("leaf_target", 64 if pop else 32), ("restart", 50 if pop else 150),
+                 ("freqs", 2 if pop else 0), ("chunk", 16 if pop else 64), ("mac", 0.6 if pop else 0.0)):
+        if getattr(a, k) is None:
+            setattr(a, k, v)
+    if pop:
+        a.no_autotune = True
+    return a
+
+
+def spread(freqs, n, world=1, rank=0):
+    """n * world frequencies spread evenly over a sweep (both ends included),
+    rank r taking every world-th of them (weak scaling: n per rank)."""
+    freqs = np.asarray(freqs)
+    if not n:
+        return freqs[rank::world]
+    idx = np.unique(np.round(np.linspace(0, len(freqs) - 1, min(len(freqs), n * world))).astype(int))
+    return freqs[idx][rank::world]
 
 
 # ---------------------------------------------------------------- workload
@@ -289,10 +314,12 @@ def measure_fp64_peak():
 
 # ---------------------------------------------------------------- rooflines
 # ncu DRAM bytes (read + write) per launch of the dominant kernels at one
-# configuration of this workload: (order, leaf target, targets per CTA, columns)
-# -> {phase: bytes}.  Reported only when the bench runs that configuration.
-NCU_TRAFFIC = {(7, 16, 2, 384): {"m2l": 83.342848e6 + 30.363904e6,     # k_xlate_tc2<0>
-                                  "p2p": 438.394624e6 + 33.091072e6}}   # k_xlate_tc2<1>
+# configuration: (order, stored near-field entries (the tree), targets per CTA,
+# columns) -> {phase: bytes}.  Reported only when the bench runs that
+# configuration with the kernels the counters were taken of; on the coils the
+# leaf targets 16, 32 and 64 give the same tree.
+NCU_TRAFFIC = {(7, 51031728, 2, 384): {"m2l": 56.103168e6 + 21.513216e6,     # k_xlate_tc2<0>
+                                        "p2p": 437.047552e6 + 32.495872e6}}   # k_xlate_tc2<1>
 
 
 def m2l_products(p, targets):
@@ -422,26 +449,40 @@ def loop_count(m):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle (this repository's dense FP64 solver,
+    as it stands) timed on the host cores on a bounded sample of the same
+    workload (oracle_sample), each step one sample; rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    m = workload(0, 1)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload == "coils":
+        m = workload(0, 1)
+        rows = 8
+        cfg = config_dict(m, "fp64 (CPU oracle)", {"fmm_order": None, "separation": None, "leaf_target": None})
+    else:
+        import meshgen
+        m = {"package": meshgen.package, "package_crop": meshgen.package_crop, "pop": meshgen.pop}[args.workload]()
+        m.freqs = spread(m.freqs, args.freqs, world, 0)
+        rows = max(1, int(2e6 // m.n_tri))
+        cfg = {"workload": "%s: %d triangles, %d conductors, %d ports x %d freqs per GPU (spread over the sweep)"
+                           % (args.workload, m.n_tri, int(m.cond.max()) + 1, len(m.ports), len(m.freqs)),
+               "freqs_hz_rank0": [float(f) for f in m.freqs], "precision": "fp64 (CPU oracle)"}
     n_loops = loop_count(m)
     t0 = time.perf_counter()
     samples = []
     for _ in range(max(1, args.steps)):
-        samples.append(oracle_sample(m, n_loops, budget_rows=8))
+        samples.append(oracle_sample(m, n_loops, budget_rows=rows))
     wall = time.perf_counter() - t0
     v = float(np.median([s_["value"] for s_ in samples]))
     cb = dict(samples[-1])
     cb["value"] = v
-    cb["c2_full_oracle_recorded"] = oracle_c2_recorded()
+    if args.workload == "coils":
+        cb["c2_full_oracle_recorded"] = oracle_c2_recorded()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(m, "fp64 (CPU oracle)", {"fmm_order": None, "separation": None,
-                                                                              "leaf_target": None}),
-            "cpu_baseline": cb,
+            "data": "synthetic", "config": cfg, "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -586,24 +627,43 @@ def fp64_products(pkg, x, m, pk, ext):
 
 
 def package_run(args):
-    """The package workloads (Sec. III-B, III-C stand-ins) on one GPU: the
-    chosen configuration (mixed precision, the multigrid-applied diagonal-of-P
-    preconditioner, autotuned FMM on sampled oracle-free reference rows),
-    W untimed and K timed sweeps between CUDA events, plus the FP64 and FP32
-    product rates.  The FP64 CUDA-core sweep is not run (its product at the
-    sweep's column count is timed instead: hundreds of them per sweep)."""
-    import torch
+    """The package workloads (Sec. III-B, III-C stand-ins): the chosen
+    configuration (mixed precision, batched multi-RHS frequency chunks, the
+    multigrid-applied diagonal-of-P preconditioner), W untimed and K timed
+    sweeps of the frequency slice between CUDA events on the library's stream,
+    max over ranks (each rank its own slice: weak scaling, no collective on the
+    data path).  Then, untimed: one profiled sweep for the phase rooflines, the
+    FP64 and FP32 product rates, the plain FP64 product at the sweep's column
+    count (the plain FP64 sweep itself is not run: hundreds of those products),
+    and the CPU oracle on a bounded sample."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
     import meshgen
-    import paper_2409_12375_gb300 as pkg
     m = {"package": meshgen.package, "package_crop": meshgen.package_crop, "pop": meshgen.pop}[args.workload]()
-    if args.freqs:
-        m.freqs = m.freqs[::max(1, args.freq_stride)][:args.freqs]
+    m.freqs = spread(m.freqs, args.freqs, world, rank)
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # before the first GPU call; rows bounded to ~2e6 oracle entries
+        cb = oracle_sample(m, loop_count(m), budget_rows=max(1, int(2e6 // m.n_tri)))
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2409_12375_gb300 as pkg
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
     nport = len(m.ports)
     nsys = len(m.freqs) * nport
     chunk = args.chunk if nsys > 128 or args.freqs else 0
     chunk = chunk if chunk and chunk < nsys else 0
     opts = dict(fmm_order=args.fmm_order, leaf_target=args.leaf_target, precision=1, precond=1, mac_theta=args.mac,
-                restart=args.restart, tol=args.tol, max_iters=2000, rhs_chunk=chunk, warm_start=1 if chunk else 0)
+                restart=args.restart, tol=args.tol, max_iters=2000, rhs_chunk=chunk, warm_start=1 if chunk else 0,
+                device=local)
     t0 = time.perf_counter()
     x = pkg.XRL.from_mesh(m, **opts)
     setup_s = time.perf_counter() - t0
@@ -615,22 +675,48 @@ def package_run(args):
         tuned = {"leaf_target": leaf, "fmm_order": order, "product_ms": ms, "product_err": err,
                  "tc_targets_per_cta": x.stats()["tc_targets_per_cta"], "autotune_s": time.perf_counter() - t0}
     st = x.stats()
-    print("setup %.1f s: %d panels, %d loops, %d leaves, %d near entries, peak %.1f GB" %
-          (setup_s, st["n_panels"], st["n_loops"], st["n_leaves"], st["near_nnz"], st["peak_device_bytes"] / 1e9),
-          file=sys.stderr, flush=True)
-    print("after setup: %.1f GB held, %.1f GB cached" % (st["device_bytes"] / 1e9, st["cached_device_bytes"] / 1e9),
-          file=sys.stderr, flush=True)
+    print("setup %.1f s: %d panels, %d loops, %d leaves, %d near entries, peak %.1f GB; %.1f GB held, %.1f GB cached"
+          % (setup_s, st["n_panels"], st["n_loops"], st["n_leaves"], st["near_nnz"], st["peak_device_bytes"] / 1e9,
+             st["device_bytes"] / 1e9, st["cached_device_bytes"] / 1e9), file=sys.stderr, flush=True)
     clocks = Clocks()
     try:
-        tm = time_sweeps(x, m.freqs, args.warmup, args.steps, clocks)
+        tm = time_sweeps(x, m.freqs, args.warmup, args.steps, clocks, barrier)
     except Exception:
         sf = x.stats()
         print("solve failed: %.1f GB held, %.1f GB cached, peak %.1f GB" %
               (sf["device_bytes"] / 1e9, sf["cached_device_bytes"] / 1e9, sf["peak_device_bytes"] / 1e9),
               file=sys.stderr, flush=True)
         raise
-    ck = clocks.stop(0)
-    value = tm["dev_ms"] / 1e3 / (args.steps * nsys)
+    ck = clocks.stop(local)
+    t_dev = torch.tensor([tm["dev_ms"], tm["host_s"]], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
+    dev_ms, host_s = float(t_dev[0]), float(t_dev[1])
+    units = args.steps * nsys * world
+    value = dev_ms / 1e3 / units
+    st = x.stats()
+    order, leaf = x.opts.fmm_order, x.opts.leaf_target
+
+    # phase breakdown: one more sweep with the phase profiler on
+    x.reset_profile()
+    x.set_profiling(True)
+    x.solve(m.freqs)
+    torch.cuda.synchronize()
+    prof = x.profile()
+    x.set_profiling(False)
+    pk = peaks()
+    pk["fp64_tflops"] = measure_fp64_peak()
+    pk["fp64_src"] = "measured: cuBLAS DGEMM 8192^3 (torch.matmul float64), best of 5, CUDA events"
+    near_pad = st["near_nnz_padded"] / float(st["near_nnz"]) if st.get("near_nnz_padded") else 0.0
+    tct = st["tc_targets_per_cta"]
+    traffic = NCU_TRAFFIC.get((order, st["near_nnz"], tct, ncols))
+    roofs = {k: phase_roofline(k, prof[k], pk, "mixed", order, ncols, near_pad, traffic, tct)
+             for k in ("p2p", "m2l", "p2p64", "m2l64", "precond", "operator", "p2m", "l2p", "m2m", "l2l")
+             if k in prof and prof[k]["ms"] > 0}
+    dom = max(roofs, key=lambda k: prof[k]["ms"])
+
+    # product rates (untimed by the bench clock): FP64 at 1 and 6 columns, FP32 and the
+    # plain FP64 product at the sweep's column count (one each)
     ext = torch.cuda.ExternalStream(x.stream_handle())
     prod = {}
     for nc, prec in ((1, 64), (6, 64), (ncols, 32), (ncols, 64)):
@@ -651,42 +737,61 @@ def package_run(args):
         ms = e0.elapsed_time(e1) / reps
         prod["fp%d_nc%d" % (prec, nc)] = {"ms": ms, "panel_cols_per_s": m.n_tri * nc / (ms * 1e-3)}
         del a, b
+    prod["plain_fp64_over_fp32_product_at_%d_cols" % ncols] = (prod["fp64_nc%d" % ncols]["ms"] /
+                                                               prod["fp32_nc%d" % ncols]["ms"])
     ora = None
     if args.workload == "package_crop":
         with open(os.path.join(ROOT, "tests", "golden", "package_crop_rl.json")) as f:
             g = json.load(f)
-        Ro, Lo = np.asarray(g["R"])[:len(m.freqs)], np.asarray(g["L"])[:len(m.freqs)]
+        fo = np.asarray(g["freqs_hz"]) if "freqs_hz" in g and isinstance(g["freqs_hz"], list) else None
+        Ro, Lo = np.asarray(g["R"]), np.asarray(g["L"])
+        if fo is not None:
+            sel = [int(np.argmin(np.abs(fo - f))) for f in m.freqs]
+            Ro, Lo = Ro[sel], Lo[sel]
         R, L = tm["R"], tm["L"]
         ora = {"R_self": float(max(np.max(np.abs(R[:, i, i] - Ro[:, i, i]) / np.abs(Ro[:, i, i])) for i in range(nport))),
                "L_self": float(max(np.max(np.abs(L[:, i, i] - Lo[:, i, i]) / np.abs(Lo[:, i, i])) for i in range(nport)))}
     arm = None
     st2 = x.stats()
-    order, leaf, mg = x.opts.fmm_order, x.opts.leaf_target, x.opts.mg_cycles
+    mg = x.opts.mg_cycles
     x.close()                         # frees its device memory (and allocation cache) before the next context
-    if args.fp64tc_arm:
+    if args.fp64tc_arm and world == 1:
         xa = pkg.XRL.from_mesh(m, **dict(opts, precision=2, fmm_order=order, leaf_target=leaf))
         ra = time_sweeps(xa, m.freqs, 0, 1)
         eR, eL = rl_diff(tm["R"], tm["L"], ra["R"], ra["L"])
         arm = {"s_per_freq_port": ra["dev_ms"] / 1e3 / nsys, "fgmres_iters": ra["iters"], "max_rel_residual": ra["res"],
                "rel_err_R_chosen_vs_this": eR, "rel_err_L_chosen_vs_this": eL}
         xa.close()
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": tm["dev_ms"] / args.steps, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32/f64 mixed (FP32 FMM in FP64 FGMRES-IR)", "data": "synthetic",
-            "config": {"workload": "%s: %d triangles, %d conductors, %d ports x %d freqs, tol %g, restart %d%s"
-                                   % (args.workload, m.n_tri, int(m.cond.max()) + 1, nport, len(m.freqs), args.tol,
-                                      args.restart, ", chunks of %d systems" % chunk if chunk else ""),
-                       "freqs_hz": [float(f) for f in m.freqs], "mac_theta": args.mac, "mg_cycles": mg,
-                       "autotune": tuned, "fmm_order": order, "leaf_target": leaf},
-            "e2e": {"value": tm["host_s"] / (args.steps * nsys), "unit": UNIT, "h2d_bytes_per_step": 8 * len(m.freqs),
-                    "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * nport ** 2},
-            "gpu_launches": tm["launches"], "clocks": ck, "products": prod, "oracle_rl_error": ora, "fp64_tc": arm,
-            "solve": {"fgmres_iters": tm["iters"], "max_rel_residual": tm["res"], "setup_s": setup_s,
-                      "setup_phase_ms": st["setup_phase_ms"], "n_loops": st["n_loops"],
-                      "n_global_loops": st["n_global_loops"], "near_per_panel": st["near_nnz"] / st["n_panels"],
-                      "mg_levels": st["mg_levels"], "mg_coarse_n": st["mg_coarse_n"],
-                      "peak_device_bytes": st2["peak_device_bytes"]}}
-    print(json.dumps(line))
+    if rank == 0:
+        if cb is not None:
+            cb["sample"] = "%s workload: %s" % (args.workload, cb["sample"])
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed (FP32 FMM in FP64 FGMRES-IR)",
+                "data": "synthetic",
+                "config": {"workload": "%s: %d triangles, %d conductors, %d ports x %d freqs per GPU (spread over "
+                                       "the sweep), tol %g, restart %d%s"
+                                       % (args.workload, m.n_tri, int(m.cond.max()) + 1, nport, len(m.freqs),
+                                          args.tol, args.restart, ", chunks of %d systems" % chunk if chunk else ""),
+                           "freqs_hz_rank0": [float(f) for f in m.freqs], "mac_theta": args.mac, "mg_cycles": mg,
+                           "autotune": tuned, "fmm_order": order, "leaf_target": leaf, "precision": "mixed",
+                           "parallelism": "replicas over frequencies" if world > 1 else "1 GPU",
+                           "l2": "working set > L2 (near field and Krylov basis, tens of GB): no flush needed"},
+                "e2e": {"value": host_s / units, "unit": UNIT, "h2d_bytes_per_step": 8 * len(m.freqs),
+                        "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * nport ** 2},
+                "gpu_launches": tm["launches"], "clocks": ck, "roofline": roofs[dom], "roofline_phases": roofs,
+                "cpu_baseline": cb, "products": prod, "oracle_rl_error": ora, "fp64_tc": arm,
+                "plain_fp64": {"run": False, "why": "its product at the sweep's column count is timed instead "
+                                                    "(products.fp64_nc%d); the sweep takes hundreds of them" % ncols},
+                "solve": {"fgmres_iters": tm["iters"], "max_rel_residual": tm["res"], "setup_s": setup_s,
+                          "setup_phase_ms": st["setup_phase_ms"], "n_loops": st["n_loops"],
+                          "n_global_loops": st["n_global_loops"], "near_per_panel": st["near_nnz"] / st["n_panels"],
+                          "mg_levels": st["mg_levels"], "mg_coarse_n": st["mg_coarse_n"],
+                          "peak_device_bytes": st2["peak_device_bytes"]},
+                "phases_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
@@ -694,10 +799,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload != "coils":
-        return package_run(args)
     if args.kernel_case:
         return kernel_case(args)
+    if args.workload != "coils" and not args.sweep_case:
+        return package_run(args)
     if args.sweep_case:
         import paper_2409_12375_gb300 as pkg
         m = workload(0, 1)
@@ -762,7 +867,7 @@ def main():
     pk["fp64_tflops"] = measure_fp64_peak()
     pk["fp64_src"] = "measured: cuBLAS DGEMM 8192^3 (torch.matmul float64), best of 5, CUDA events"
     near_pad = st["near_nnz_padded"] / float(st["near_nnz"]) if st.get("near_nnz_padded") else 0.0
-    key = (cfg_opts["fmm_order"], cfg_opts["leaf_target"], x.stats()["tc_targets_per_cta"], 6 * nsys)
+    key = (cfg_opts["fmm_order"], st["near_nnz"], x.stats()["tc_targets_per_cta"], 6 * nsys)
     traffic = NCU_TRAFFIC.get(key) if args.precision == "mixed" else None
     tct = x.stats()["tc_targets_per_cta"]
     roofs = {k: phase_roofline(k, prof[k], pk, args.precision, cfg_opts["fmm_order"], 6 * nsys, near_pad, traffic,

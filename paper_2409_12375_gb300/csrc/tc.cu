@@ -627,83 +627,33 @@ struct Tc2Args {
   int32_t* err;
 };
 
-// acc[n] += both accumulators (small first) for the columns n in [0, n1) and
-// [64, 64 + n2) (n1 = 0 / n2 = 0: that target absent; a group's lone target
-// may have n1 > 64)
-__device__ __forceinline__ void drain_range(float (&acc)[128], uint32_t taddr, int n1, int n2) {
+// acc[n] += (sc *) both accumulators (small first) for the columns n < ncol
+// (warp-uniform) of one 64-column half at taddr; 32 columns per wait
+template <bool SCALE>
+__device__ __forceinline__ void drain_cols(float (&acc)[64], uint32_t taddr, int ncol, float sc) {
 #pragma unroll
   for (int s = 1; s >= 0; --s) {
 #pragma unroll
-    for (int h = 0; h < 128; h += 32) {
-      if (!(h < n1 || (n2 > 0 && h + 32 > 64 && h < 64 + n2))) continue;   // warp-uniform
+    for (int h = 0; h < 64; h += 32) {
+      if (h >= ncol) break;
       uint32_t r[32];
 #pragma unroll
       for (int n0 = 0; n0 < 32; n0 += 16)
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-            "[%16];"
-            : "=r"(r[n0 + 0]), "=r"(r[n0 + 1]), "=r"(r[n0 + 2]), "=r"(r[n0 + 3]), "=r"(r[n0 + 4]),
-              "=r"(r[n0 + 5]), "=r"(r[n0 + 6]), "=r"(r[n0 + 7]), "=r"(r[n0 + 8]), "=r"(r[n0 + 9]),
-              "=r"(r[n0 + 10]), "=r"(r[n0 + 11]), "=r"(r[n0 + 12]), "=r"(r[n0 + 13]), "=r"(r[n0 + 14]),
-              "=r"(r[n0 + 15])
-            : "r"(taddr + 128u * s + (uint32_t)(h + n0))
-            : "memory");
+        if (h + n0 < ncol)
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];"
+              : "=r"(r[n0 + 0]), "=r"(r[n0 + 1]), "=r"(r[n0 + 2]), "=r"(r[n0 + 3]), "=r"(r[n0 + 4]),
+                "=r"(r[n0 + 5]), "=r"(r[n0 + 6]), "=r"(r[n0 + 7]), "=r"(r[n0 + 8]), "=r"(r[n0 + 9]),
+                "=r"(r[n0 + 10]), "=r"(r[n0 + 11]), "=r"(r[n0 + 12]), "=r"(r[n0 + 13]), "=r"(r[n0 + 14]),
+                "=r"(r[n0 + 15])
+              : "r"(taddr + 128u * s + (uint32_t)(h + n0))
+              : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
       for (int n = 0; n < 32; ++n)
-        if (h + n < n1 || (h + n >= 64 && h + n - 64 < n2)) acc[h + n] += __uint_as_float(r[n]);
-    }
-  }
-}
-
-// acc[OFF + n] += both accumulators (small first) of one 64-column half
-template <int OFF>
-__device__ __forceinline__ void drain_half(float (&acc)[128], uint32_t taddr) {
-#pragma unroll
-  for (int s = 1; s >= 0; --s) {
-#pragma unroll
-    for (int h = 0; h < 64; h += 32) {
-      uint32_t r[32];
-#pragma unroll
-      for (int n0 = 0; n0 < 32; n0 += 16)
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-            "[%16];"
-            : "=r"(r[n0 + 0]), "=r"(r[n0 + 1]), "=r"(r[n0 + 2]), "=r"(r[n0 + 3]), "=r"(r[n0 + 4]),
-              "=r"(r[n0 + 5]), "=r"(r[n0 + 6]), "=r"(r[n0 + 7]), "=r"(r[n0 + 8]), "=r"(r[n0 + 9]),
-              "=r"(r[n0 + 10]), "=r"(r[n0 + 11]), "=r"(r[n0 + 12]), "=r"(r[n0 + 13]), "=r"(r[n0 + 14]),
-              "=r"(r[n0 + 15])
-            : "r"(taddr + 128u * s + (uint32_t)(h + n0))
-            : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int n = 0; n < 32; ++n) acc[OFF + h + n] += __uint_as_float(r[n]);
-    }
-  }
-}
-
-// acc[OFF + n] += sc * (both accumulators, small first) of one 64-column half
-template <int OFF>
-__device__ __forceinline__ void drain_half_scaled(float (&acc)[128], uint32_t taddr, float sc) {
-#pragma unroll
-  for (int s = 1; s >= 0; --s) {
-#pragma unroll
-    for (int h = 0; h < 64; h += 32) {
-      uint32_t r[32];
-#pragma unroll
-      for (int n0 = 0; n0 < 32; n0 += 16)
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-            "[%16];"
-            : "=r"(r[n0 + 0]), "=r"(r[n0 + 1]), "=r"(r[n0 + 2]), "=r"(r[n0 + 3]), "=r"(r[n0 + 4]),
-              "=r"(r[n0 + 5]), "=r"(r[n0 + 6]), "=r"(r[n0 + 7]), "=r"(r[n0 + 8]), "=r"(r[n0 + 9]),
-              "=r"(r[n0 + 10]), "=r"(r[n0 + 11]), "=r"(r[n0 + 12]), "=r"(r[n0 + 13]), "=r"(r[n0 + 14]),
-              "=r"(r[n0 + 15])
-            : "r"(taddr + 128u * s + (uint32_t)(h + n0))
-            : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int n = 0; n < 32; ++n) acc[OFF + h + n] = fmaf(__uint_as_float(r[n]), sc, acc[OFF + h + n]);
+        if (h + n < ncol)
+          acc[h + n] = SCALE ? fmaf(__uint_as_float(r[n]), sc, acc[h + n]) : acc[h + n] + __uint_as_float(r[n]);
     }
   }
 }
@@ -713,7 +663,7 @@ __device__ __forceinline__ void drain_half_scaled(float (&acc)[128], uint32_t ta
 // per-coefficient output scale.  MODE 1 (near field): three-piece BF16, six
 // products.
 template <int MODE>
-__global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
+__global__ void __launch_bounds__(320, 1) k_xlate_tc2(Tc2Args a) {
   constexpr int PC = MODE == 0 ? TCH_PIECES : TC_PIECES;
   extern __shared__ uint8_t tc_smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -741,7 +691,7 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
     }
     for (int q = 0; q < 2; ++q) {
       mbar_init(&tfull[q], 1);
-      mbar_init(&tfree[q], 4);
+      mbar_init(&tfree[q], 8);
     }
     mbar_init(mdone, 1);
     *bad = 0;
@@ -863,11 +813,14 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
     }
     __syncwarp();
   } else {
-    const int quarter = warp & 3;
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its columns of the right-hand
+    // sides) and accumulator columns [64 h, 64 h + 64), h = (w - 2) / 4: target
+    // t1 (h = 0) or t2 (h = 1), or rows 64 h.. of a lone target
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
     const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
-    float acc[128];
+    float acc[64];
 #pragma unroll
-    for (int n = 0; n < 128; ++n) acc[n] = 0.f;
+    for (int n = 0; n < 64; ++n) acc[n] = 0.f;
     for (int j = 0; j < nv; ++j) {
       const int q = j & 1;
       const bool p1 = a.gv1[vs + j] >= 0, p2 = a.gv2[vs + j] >= 0;
@@ -878,39 +831,35 @@ __global__ void __launch_bounds__(192, 1) k_xlate_tc2(Tc2Args a) {
         break;
       }
       tc_fence_after();
-      const uint32_t tq = tbase + lane_base + 256u * q;
-      if (MODE == 0) {   // both halves 64 wide: compile-time columns; this row's scale for the source box
-        const float sc =
-            a.ascale[((size_t)(a.gsrc[vs + j] - a.src0) * a.nct + ct) * TC_ROWS + 32 * quarter + lane];
-        if (p1) drain_half_scaled<0>(acc, tq, sc);
-        if (p2) drain_half_scaled<64>(acc, tq + 64u, sc);
-      } else {
-        drain_range(acc, tq, p1 ? N1 : 0, p2 ? N2 : 0);
+      int ncol;
+      if (MODE == 0)
+        ncol = (half == 0 ? p1 : p2) ? 64 : 0;
+      else if (t2 < 0)
+        ncol = p1 ? min(64, N1 - 64 * half) : 0;
+      else
+        ncol = half == 0 ? (p1 ? N1 : 0) : (p2 ? N2 : 0);
+      if (ncol > 0) {
+        const uint32_t tq = tbase + lane_base + 256u * q + 64u * half;
+        if (MODE == 0)   // this row's scale for the pair's source box
+          drain_cols<true>(acc, tq, 64,
+                           a.ascale[((size_t)(a.gsrc[vs + j] - a.src0) * a.nct + ct) * TC_ROWS + 32 * quarter + lane]);
+        else
+          drain_cols<false>(acc, tq, ncol, 1.f);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tfree[q]);
     }
     const int col = ct * TC_ROWS + 32 * quarter + lane;
-    if (col < a.nc) {
-      const int nr1 = MODE == 0 ? a.ncoef : a.leaf_n[t1];
-      const int nr2 = t2 < 0 ? 0 : (MODE == 0 ? a.ncoef : a.leaf_n[t2]);
-      const size_t r1 = MODE == 0 ? (size_t)t1 * a.ncoef : (size_t)a.leaf_f0[t1];
-      const size_t r2 = t2 < 0 ? 0 : (MODE == 0 ? (size_t)t2 * a.ncoef : (size_t)a.leaf_f0[t2]);
-      float* o1 = a.out + r1 * a.nc + col;
-      float* o2 = a.out + r2 * a.nc + col;
-      if (MODE == 0) {
+    const int tg = (t2 < 0 || half == 0) ? t1 : t2;          // this half's target
+    const int r0 = (t2 < 0) ? 64 * half : 0;                 // its first row in this half
+    if (col < a.nc && !(MODE == 0 && t2 < 0 && half == 1)) {
+      const int nr = (MODE == 0 ? a.ncoef : a.leaf_n[tg]) - r0;
+      const size_t row = MODE == 0 ? (size_t)tg * a.ncoef : (size_t)a.leaf_f0[tg] + r0;
+      float* o = a.out + row * a.nc + col;
 #pragma unroll
-        for (int n = 0; n < 128; ++n) acc[n] *= __ldg(a.oscale + (n & 63));
-      }
-#pragma unroll
-      for (int n = 0; n < 128; ++n) {
-        if (t2 < 0 || n < 64) {
-          if (n < nr1) o1[(size_t)n * a.nc] = acc[n];
-        } else if (n - 64 < nr2) {
-          o2[(size_t)(n - 64) * a.nc] = acc[n];
-        }
-      }
+      for (int n = 0; n < 64; ++n)
+        if (n < nr) o[(size_t)n * a.nc] = MODE == 0 ? acc[n] * __ldg(a.oscale + n) : acc[n];
     }
   }
   __syncthreads();
@@ -945,7 +894,7 @@ static void launch_tc2_m(xrl_ctx* c, dim3 grid, const Tc2Args& g, cudaStream_t s
   Tc2Args a = g;
   for (unsigned y0 = 0; y0 < grid.y; y0 += kMaxGridY) {
     a.y0 = (int)y0;
-    k_xlate_tc2<MODE><<<dim3(grid.x, std::min(kMaxGridY, grid.y - y0)), 192, tc2_smem<MODE>(), s>>>(a);
+    k_xlate_tc2<MODE><<<dim3(grid.x, std::min(kMaxGridY, grid.y - y0)), 320, tc2_smem<MODE>(), s>>>(a);
     if (y0 > 0) count_launch(c);   // callers count one launch per translation
   }
 }
