@@ -73,8 +73,11 @@ def parse():
                                                               "(default 150; 50 on the PoP stack)")
     ap.add_argument("--tol", type=float, default=1e-6, help="relative residual of the package workloads")
     ap.add_argument("--freqs", type=int, default=None,
-                    help="package workloads: solve N frequencies spread evenly over the sweep, both ends included "
-                         "(default: all; 2 on the PoP stack: 1 kHz and 10 GHz, one 16-system chunk each)")
+                    help="package workloads: solve the first N frequencies of the sweep (default: all; 2 on the PoP "
+                         "stack: 1 kHz and 1.29 kHz, one 16-system chunk each)")
+    ap.add_argument("--spread", action="store_true",
+                    help="with --freqs: N frequencies spread evenly over the sweep, both ends included, instead of "
+                         "the first N")
     ap.add_argument("--fp64tc-arm", action="store_true", help="package workloads: one FP64-accurate sweep too")
     ap.add_argument("--chunk", type=int, default=None, help="package workloads: systems per frequency chunk when "
                                                              "the sweep has more than 128 (default 64; 16 on the "
@@ -99,14 +102,18 @@ def parse():
     return a
 
 
-def spread(freqs, n, world=1, rank=0):
-    """n * world frequencies spread evenly over a sweep (both ends included),
-    rank r taking every world-th of them (weak scaling: n per rank)."""
+def spread(freqs, n, world=1, rank=0, even=False):
+    """n * world frequencies of a sweep, the first ones or (even) spread evenly
+    over it with both ends included; rank r takes every world-th of them (weak
+    scaling: n per rank)."""
     freqs = np.asarray(freqs)
     if not n:
         return freqs[rank::world]
-    idx = np.unique(np.round(np.linspace(0, len(freqs) - 1, min(len(freqs), n * world))).astype(int))
-    return freqs[idx][rank::world]
+    k = min(len(freqs), n * world)
+    if even:
+        idx = np.unique(np.round(np.linspace(0, len(freqs) - 1, k)).astype(int))
+        return freqs[idx][rank::world]
+    return freqs[:k][rank::world]
 
 
 # ---------------------------------------------------------------- workload
@@ -463,10 +470,11 @@ def run_reference(args):
     else:
         import meshgen
         m = {"package": meshgen.package, "package_crop": meshgen.package_crop, "pop": meshgen.pop}[args.workload]()
-        m.freqs = spread(m.freqs, args.freqs, world, 0)
+        m.freqs = spread(m.freqs, args.freqs, world, 0, args.spread)
         rows = max(1, int(2e6 // m.n_tri))
-        cfg = {"workload": "%s: %d triangles, %d conductors, %d ports x %d freqs per GPU (spread over the sweep)"
-                           % (args.workload, m.n_tri, int(m.cond.max()) + 1, len(m.ports), len(m.freqs)),
+        cfg = {"workload": "%s: %d triangles, %d conductors, %d ports x %d freqs per GPU (%s of its sweep)"
+                           % (args.workload, m.n_tri, int(m.cond.max()) + 1, len(m.ports), len(m.freqs),
+                              "spread over" if args.spread else "the first"),
                "freqs_hz_rank0": [float(f) for f in m.freqs], "precision": "fp64 (CPU oracle)"}
     n_loops = loop_count(m)
     t0 = time.perf_counter()
@@ -641,7 +649,7 @@ def package_run(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     import meshgen
     m = {"package": meshgen.package, "package_crop": meshgen.package_crop, "pop": meshgen.pop}[args.workload]()
-    m.freqs = spread(m.freqs, args.freqs, world, rank)
+    m.freqs = spread(m.freqs, args.freqs, world, rank, args.spread)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # before the first GPU call; rows bounded to ~2e6 oracle entries
@@ -769,10 +777,11 @@ def package_run(args):
                 "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed (FP32 FMM in FP64 FGMRES-IR)",
                 "data": "synthetic",
-                "config": {"workload": "%s: %d triangles, %d conductors, %d ports x %d freqs per GPU (spread over "
-                                       "the sweep), tol %g, restart %d%s"
+                "config": {"workload": "%s: %d triangles, %d conductors, %d ports x %d freqs per GPU (%s of its "
+                                       "sweep), tol %g, restart %d%s"
                                        % (args.workload, m.n_tri, int(m.cond.max()) + 1, nport, len(m.freqs),
-                                          args.tol, args.restart, ", chunks of %d systems" % chunk if chunk else ""),
+                                          "spread over" if args.spread else "the first", args.tol, args.restart,
+                                          ", chunks of %d systems" % chunk if chunk else ""),
                            "freqs_hz_rank0": [float(f) for f in m.freqs], "mac_theta": args.mac, "mg_cycles": mg,
                            "autotune": tuned, "fmm_order": order, "leaf_target": leaf, "precision": "mixed",
                            "parallelism": "replicas over frequencies" if world > 1 else "1 GPU",

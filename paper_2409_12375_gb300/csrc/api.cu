@@ -398,6 +398,9 @@ xrl_status xrl_setup(xrl_ctx* c) {
     lap(4);
     solver_prepare(c);
     XRL_CUDA(cudaStreamSynchronize(c->stream));
+    // setup's temporaries (near-field lists, factor scratch) have sizes no
+    // later call asks for: hand them back instead of keeping them cached
+    c->alloc.trim();
     lap(5);
     const Topo& T = c->topo;
     c->stats.n_panels = c->N;

@@ -452,18 +452,42 @@ __global__ void __launch_bounds__(256) k_m2l_offsets(int nc, int ncoef, const in
     for (int i = 0; i < 6; ++i)
 #pragma unroll
       for (int c = 0; c < NC; ++c) acc[i][c] = 0;
-    for (int j = 0; j < ncoef; ++j) {
-      T mj[NC];
+    if (NC == 1) {
+      // one column: the source expansion in registers (lane l holds
+      // coefficients l, l + 32, ...), broadcast by shuffles, so the inner loop
+      // reads only shared memory
+      T mreg[6];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) mj[c] = c < nc ? ms[(size_t)j * nc + c] : (T)0;
-      const T* tr = Ts + (size_t)j * ncoef;
+      for (int i = 0; i < 6; ++i) mreg[i] = lane + 32 * i < ncoef ? ms[lane + 32 * i] : (T)0;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        const int k = lane + 32 * i;
-        if (k < ncoef) {
-          const T t = tr[k];
+      for (int jb = 0; jb < 6; ++jb) {
+        if (32 * jb >= ncoef) break;
+        const int jn = min(32, ncoef - 32 * jb);
+        for (int jj = 0; jj < jn; ++jj) {
+          const T mj = __shfl_sync(0xffffffffu, mreg[jb], jj);
+          const T* tr = Ts + (size_t)(32 * jb + jj) * ncoef;
 #pragma unroll
-          for (int c = 0; c < NC; ++c) acc[i][c] += t * mj[c];
+          for (int i = 0; i < 6; ++i) {
+            const int k = lane + 32 * i;
+            if (k < ncoef) acc[i][0] += tr[k] * mj;
+          }
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int j = 0; j < ncoef; ++j) {
+        T mj[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) mj[c] = c < nc ? ms[(size_t)j * nc + c] : (T)0;
+        const T* tr = Ts + (size_t)j * ncoef;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          const int k = lane + 32 * i;
+          if (k < ncoef) {
+            const T t = tr[k];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[i][c] += t * mj[c];
+          }
         }
       }
     }

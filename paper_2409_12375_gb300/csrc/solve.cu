@@ -481,6 +481,11 @@ __global__ void k_update_x(int n, int nsys, int m, const int* __restrict__ kcols
   x[idx] = acc;
 }
 
+__global__ void k_cadd(size_t n, const cplx* __restrict__ z, cplx* __restrict__ x) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n) x[idx] = cadd(x[idx], z[idx]);
+}
+
 // r = b - Ax ; beta = ||r||; v0 = r / beta; g = (beta, 0, ...)
 // thr[s] = max(tol ||b||, tau ||r||): the inner cycle's stopping level (tau > 0 in
 // the mixed-precision mode, where the cycle's operator is only FP32-accurate)
@@ -777,7 +782,7 @@ static void apply_Qmat(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* w, i
 }
 
 // z ~= Q^-1 v by Jacobi-COCG with a fixed budget (or z = v without preconditioner)
-static void apply_Qinv(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* z) {
+static void apply_Qinv(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* z, bool all = false) {
   const int n = c->topo.n_loops;
   cudaStream_t s = c->stream;
   if (c->opt.precond == 0) {
@@ -785,7 +790,7 @@ static void apply_Qinv(xrl_ctx* c, Work& wk, int nsys, const cplx* v, cplx* z) {
     return;
   }
   if (wk.banded) {
-    band_apply(c, wk.bw, nsys, wk.nport, wk.zsf.p, wk.wpf.p, v, z, wk.active.p, s);
+    band_apply(c, wk.bw, nsys, wk.nport, wk.zsf.p, wk.wpf.p, v, z, all ? nullptr : wk.active.p, s);
     return;
   }
   if (wk.use_amg) {
@@ -856,7 +861,12 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
   wk.x.alloc(c->alloc, tot);
   wk.w.alloc(c->alloc, tot);
   wk.V.alloc(c->alloc, tot * (m + 1));
-  wk.Z.alloc(c->alloc, tot * m);
+  // With a fixed preconditioner (all but the inner COCG iteration) the
+  // flexible variant's Z_j = M^-1 v_j need not be kept: the cycle ends with
+  // x += M^-1 (V y), one more preconditioner application, and Z is one
+  // scratch vector instead of m (half the Krylov memory).
+  const bool zfree = c->opt.precond != 2;
+  wk.Z.alloc(c->alloc, zfree ? tot : tot * m);
   wk.H.alloc(c->alloc, (size_t)nsys * (m + 1) * m);
   wk.h1.alloc(c->alloc, (size_t)nsys * (m + 1));
   wk.h2.alloc(c->alloc, (size_t)nsys * (m + 1));
@@ -1004,7 +1014,7 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
     int j = 0;
     for (; j < m && total < c->opt.max_iters; ++j, ++total) {
       cplx* vj = wk.V.p + (size_t)j * tot;
-      cplx* zj = wk.Z.p + (size_t)j * tot;
+      cplx* zj = wk.Z.p + (zfree ? (size_t)0 : (size_t)j * tot);
       apply_Qinv(c, wk, nsys, vj, zj);
       bool replayed = false;
       if (!use_graph) {
@@ -1062,8 +1072,19 @@ void run_solve(xrl_ctx* c, int nf, const double* freq, double* R, double* L, con
     XRL_CUDA(cudaMemcpyAsync(wk.kcols.p, hk.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
     cudaEvent_t evu = prof_begin(c, s);
     k_trisolve<<<nblk(nsys, 64), 64, 0, s>>>(nsys, m, wk.kcols.p, wk.H.p, wk.g.p, wk.y.p);
-    k_update_x<<<nblk(tot), 256, 0, s>>>(n, nsys, m, wk.kcols.p, wk.Z.p, wk.y.p, wk.x.p);
-    prof_end(c, s, evu, PH_KRYLOV, 2, 8.0 * j * tot, 16.0 * (j + 2) * tot);
+    if (zfree) {
+      // w = V y (w is free at the end of a cycle), z = M^-1 w, x += z
+      XRL_CUDA(cudaMemsetAsync(wk.w.p, 0, sizeof(cplx) * tot, s));
+      k_update_x<<<nblk(tot), 256, 0, s>>>(n, nsys, m, wk.kcols.p, wk.V.p, wk.y.p, wk.w.p);
+      prof_end(c, s, evu, PH_KRYLOV, 2, 8.0 * j * tot, 16.0 * (j + 2) * tot);
+      apply_Qinv(c, wk, nsys, wk.w.p, wk.Z.p, true);
+      cudaEvent_t eva = prof_begin(c, s);
+      k_cadd<<<nblk(tot), 256, 0, s>>>(tot, wk.Z.p, wk.x.p);
+      prof_end(c, s, eva, PH_KRYLOV, 1, 2.0 * tot, 48.0 * tot);
+    } else {
+      k_update_x<<<nblk(tot), 256, 0, s>>>(n, nsys, m, wk.kcols.p, wk.Z.p, wk.y.p, wk.x.p);
+      prof_end(c, s, evu, PH_KRYLOV, 2, 8.0 * j * tot, 16.0 * (j + 2) * tot);
+    }
     XRL_CUDA(cudaGetLastError());
     if (total >= c->opt.max_iters) {
       // final true residual for the stats
