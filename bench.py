@@ -70,7 +70,7 @@ def parse():
                          "sweep (2 ports x 32 freqs, one 64-RHS block) with the comparison arms; package: the "
                          "BGA-like package (~250k triangles, 8 ports x 16 freqs); package_crop: its 2.8 mm window")
     ap.add_argument("--restart", type=int, default=None, help="FGMRES restart of the package workloads "
-                                                              "(default 150; 50 on the PoP stack)")
+                                                              "(default 150; 100 on the PoP stack)")
     ap.add_argument("--tol", type=float, default=1e-6, help="relative residual of the package workloads")
     ap.add_argument("--freqs", type=int, default=None,
                     help="package workloads: solve the first N frequencies of the sweep (default: all; 2 on the PoP "
@@ -79,6 +79,9 @@ def parse():
                     help="with --freqs: N frequencies spread evenly over the sweep, both ends included, instead of "
                          "the first N")
     ap.add_argument("--fp64tc-arm", action="store_true", help="package workloads: one FP64-accurate sweep too")
+    ap.add_argument("--precond-ablation", action="store_true",
+                    help="package workloads: one more sweep (untimed by the bench clock) with the diagonal-of-L "
+                         "preconditioner, against the chosen diagonal-of-P (Table IV's comparison)")
     ap.add_argument("--chunk", type=int, default=None, help="package workloads: systems per frequency chunk when "
                                                              "the sweep has more than 128 (default 64; 16 on the "
                                                              "PoP stack)")
@@ -93,7 +96,7 @@ def parse():
                          "(FP32 inner product and the mixed mode's FP64 residual operator, 64 systems), 3 each")
     a = ap.parse_args()
     pop = a.workload == "pop" and not (a.sweep_case or a.kernel_case)
-    for k, v in (("fmm_order", 7), ("leaf_target", 64 if pop else 32), ("restart", 50 if pop else 150),
+    for k, v in (("fmm_order", 7), ("leaf_target", 64 if pop else 32), ("restart", 100 if pop else 150),
                  ("freqs", 2 if pop else 0), ("chunk", 16 if pop else 64), ("mac", 0.6 if pop else 0.0)):
         if getattr(a, k) is None:
             setattr(a, k, v)
@@ -763,6 +766,25 @@ def package_run(args):
     st2 = x.stats()
     mg = x.opts.mg_cycles
     x.close()                         # frees its device memory (and allocation cache) before the next context
+    abl = None
+    if args.precond_ablation and world == 1:
+        # Table IV on the package: diagonal-of-P (the chosen sweep above) against diagonal-of-L,
+        # same FMM, tolerance and chunks; host wall time of one sweep after the setup
+        abl = {"diag_P": {"fgmres_iters": tm["iters"], "s_per_freq_port": tm["host_s"] / (args.steps * nsys),
+                          "precond_setup_ms": st["precond_setup_ms"], "max_rel_residual": tm["res"]}}
+        xl = pkg.XRL.from_mesh(m, **dict(opts, precond=3, fmm_order=order, leaf_target=leaf))
+        sl = xl.stats()
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xl.solve(m.freqs)
+            tl = time.perf_counter() - t0
+            sl2 = xl.stats()
+            abl["diag_L"] = {"fgmres_iters": sl2["total_iters"], "s_per_freq_port": tl / nsys,
+                             "precond_setup_ms": sl["precond_setup_ms"], "max_rel_residual": sl2["max_rel_res"]}
+        except pkg.XRLError as e:
+            abl["diag_L"] = {"error": str(e), "precond_setup_ms": sl["precond_setup_ms"]}
+        xl.close()
     if args.fp64tc_arm and world == 1:
         xa = pkg.XRL.from_mesh(m, **dict(opts, precision=2, fmm_order=order, leaf_target=leaf))
         ra = time_sweeps(xa, m.freqs, 0, 1)
@@ -790,6 +812,7 @@ def package_run(args):
                         "d2h_bytes_per_step": 2 * 8 * len(m.freqs) * nport ** 2},
                 "gpu_launches": tm["launches"], "clocks": ck, "roofline": roofs[dom], "roofline_phases": roofs,
                 "cpu_baseline": cb, "products": prod, "oracle_rl_error": ora, "fp64_tc": arm,
+                "precond_ablation": abl,
                 "plain_fp64": {"run": False, "why": "its product at the sweep's column count is timed instead "
                                                     "(products.fp64_nc%d); the sweep takes hundreds of them" % ncols},
                 "solve": {"fgmres_iters": tm["iters"], "max_rel_residual": tm["res"], "setup_s": setup_s,

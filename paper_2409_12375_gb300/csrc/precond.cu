@@ -977,9 +977,9 @@ __global__ void __launch_bounds__(256) k_spike_out(int n, int nper, int nloop, i
 }
 
 // ---- host ---------------------------------------------------------------------------------
-bool band_usable(const xrl_ctx* c) {
-  return c->topo.band <= kMaxBand && c->topo.n_border <= kMaxBorder && c->topo.n_band > 0;
-}
+bool band_fits(int band, int n_border) { return band <= kMaxBand && n_border <= kMaxBorder; }
+
+bool band_usable(const xrl_ctx* c) { return band_fits(c->topo.band, c->topo.n_border) && c->topo.n_band > 0; }
 
 void band_prepare(xrl_ctx* c) {
   const Topo& T = c->topo;

@@ -566,6 +566,13 @@ void build_band(xrl_ctx* c) {
       if (cidx < nv) b = std::max(b, std::abs(pos[r] - pos[cidx]));
     }
   T.band = b;
+  T.band_val.clear();
+  T.border_vg.clear();
+  T.border_gg.clear();
+  // a band or border too wide for the banded solver is never factorised (the
+  // multigrid takes Q instead): its values, W nv (b + 1) + W nv ng doubles,
+  // would only take memory (tens of GB on the package stacks)
+  if (!band_fits(b, ng)) return;
   T.band_val.assign((size_t)W * nv * (b + 1), 0.0);
   T.border_vg.assign((size_t)W * nv * ng, 0.0);
   T.border_gg.assign((size_t)W * ng * ng, 0.0);

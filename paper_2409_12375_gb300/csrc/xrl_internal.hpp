@@ -471,6 +471,7 @@ void panel_features(xrl_ctx* c, int nf, const double* freq, double f0, const dou
 void apply_operator_host(xrl_ctx* c, int nsys, const double* f, const double* v, double* w, int mode);
 // precond.cu
 bool band_usable(const xrl_ctx* c);
+bool band_fits(int band, int n_border);   // within the banded solver's limits
 void band_prepare(xrl_ctx* c);
 // Factor and work arrays of the banded preconditioner for nf frequencies,
 // partitioned into P blocks of m rows (see precond.cu).
