@@ -1171,16 +1171,17 @@ __global__ void __launch_bounds__(320, 1) k_xlate_oz(OzArgs a) {
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          // sum_s 2^-7s D_s from the smallest class up, as a float pair
-          float h = ldexpf(__uint_as_float(r[4][q]), -28), l = 0.f, e;
-          two_sum(ldexpf(__uint_as_float(r[3][q]), -21), h, h, e);
-          l += e;
-          two_sum(ldexpf(__uint_as_float(r[2][q]), -14), h, h, e);
-          l += e;
-          two_sum(ldexpf(__uint_as_float(r[1][q]), -7), h, h, e);
-          l += e;
-          two_sum(__uint_as_float(r[0][q]), h, h, e);
-          l += e;
+          // sum_s 2^-7s D_s as a float pair.  Classes 2-4 (below 2^-14 of the
+          // leading class) are summed in plain FP32: their rounding, ~2^-24 of
+          // their sum, is ~2^-38 of the result, under the slices' own 2^-35
+          // truncation.  Classes 0 and 1 and the running sum take error-free
+          // additions.  (Scaling by a power of two is exact, as is the product
+          // by the constant.)
+          const float t = fmaf(__uint_as_float(r[4][q]), 0x1p-28f,
+                               fmaf(__uint_as_float(r[3][q]), 0x1p-21f, __uint_as_float(r[2][q]) * 0x1p-14f));
+          float h, e;
+          two_sum(__uint_as_float(r[0][q]), __uint_as_float(r[1][q]) * 0x1p-7f, h, e);
+          const float l = e + t;
           two_sum(ah[n0 + q], h, ah[n0 + q], e);
           al[n0 + q] += e + l;
         }
