@@ -57,3 +57,22 @@ def test_two_ranks_split_the_sweep():
     # the gathered sweep is the one-rank sweep, in its frequency order
     assert Ra.shape == (64, 2, 2)
     assert np.array_equal(Ra[:, 0, 0], ref) and np.array_equal(La[:, 1, 1], 1.0 / ref)
+
+
+def test_package_slices_split_over_ranks():
+    """The package workloads' frequency slice (bench.spread): N per rank of the
+    first N * world frequencies, or of N * world spread over the sweep with
+    both ends included; the ranks' slices are disjoint and make up the slice
+    one rank would solve at N * world."""
+    import bench
+    freqs = np.geomspace(1e3, 1e10, 64)
+    for even in (False, True):
+        for world in (1, 2, 4):
+            parts = [bench.spread(freqs, 2, world, r, even) for r in range(world)]
+            assert all(len(p) == 2 for p in parts)
+            allf = np.sort(np.concatenate(parts))
+            assert len(np.unique(allf)) == 2 * world
+            assert np.array_equal(allf, np.sort(bench.spread(freqs, 2 * world, 1, 0, even)))
+    assert np.array_equal(bench.spread(freqs, 2), freqs[:2])
+    assert np.array_equal(bench.spread(freqs, 2, even=True), freqs[[0, 63]])
+    assert np.array_equal(bench.spread(freqs, 0), freqs)
