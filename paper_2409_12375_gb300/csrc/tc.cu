@@ -25,8 +25,10 @@
 // split is that of the exact table); the expansions once per product.
 //
 // Warp roles: warp 0 lane 0 issues the bulk copies, warp 1 lane 0 issues the
-// MMAs (one thread, as tcgen05.mma requires), warps 2..5 drain the
-// accumulators (warp w reads TMEM lanes 32 (w % 4) .. + 31).  Every wait is
+// MMAs (one thread, as tcgen05.mma requires), the other warps drain the
+// accumulators (warp w reads TMEM lanes 32 (w % 4) .. + 31): warps 2..5 in
+// k_xlate_tc, warps 2..9 in k_xlate_tc2 and k_xlate_oz (one half of the
+// accumulator columns each).  Every wait is
 // bounded; on a timeout the kernel raises *err, drains its own copies and
 // frees its tensor memory.
 //
